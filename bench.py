@@ -1,0 +1,320 @@
+"""Benchmark of the phiks hot path on one GB300 (or N replicas).
+
+Workload: d = 3 advection-diffusion-reaction operator, n = 64 per mode
+(N = 262144), FP64, linear combination exp(tau K) v_0 + sum_{l=1}^{4}
+phi_l(tau K) v_l with outputs at tau, tau/2, tau/4 (three phi-actions per
+step), tau = 5e-4, v_l ~ N(0, 1) seeded.  One step = one phiks_apply_ex call:
+norms, parameter selection, the small FP64 exponentials (recomputed every
+step), quadrature, squaring and the scale outputs.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+(Taylor action of the augmented matrix) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wk  # noqa: E402
+
+WORKLOAD = dict(n=64, p=4, nscales=3, tau=5e-4)
+METRIC = "phi-actions/s"
+PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x flop/FMA x max SM clock
+
+
+def workload():
+    return wk.adr3d_lincomb(WORKLOAD["n"], tau=WORKLOAD["tau"], p=WORKLOAD["p"],
+                            nscales=WORKLOAD["nscales"])
+
+
+def config_dict(wl, extra=None):
+    c = {"workload": wl.name, "d": len(wl.A), "n": wl.n, "N": wl.N, "p": wl.p, "mode": wl.mode,
+         "nscales": wl.nscales, "tau": wl.tau, "operator": "FD ADR eps=1 alpha=(10,-20,5) rho=2",
+         "parallelism": "replicas"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def time_oracle_call(wl):
+    from oracle import taylor_action as ta
+    t0 = time.perf_counter()
+    outs = [ta.lincomb(wl.A, wl.tau, wl.vs, 2.0 ** -L) for L in range(wl.nscales)]
+    return time.perf_counter() - t0, outs
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = workload()
+    for _ in range(args.warmup):
+        time_oracle_call(wl)
+    tot = 0.0
+    for _ in range(args.steps):
+        dt, _ = time_oracle_call(wl)
+        tot += dt
+    value = wl.nscales * args.steps / tot
+    cores = oracle_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "phi-actions/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(wl),
+        "cpu_baseline": {"value": value, "unit": "phi-actions/s", "cores": cores, "kind": "oracle",
+                         "sample": "one full call per step (3 scale outputs), O3 Taylor action"},
+        "e2e": {"value": value, "unit": "phi-actions/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_phiks(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    import paper_2210_07667_gb300 as pk
+    pk.load(build_if_missing=True)
+
+    wl = workload()
+    N = wl.N
+    plan = pk.Plan(wl.A, pk.PHIKS_FP64)
+    stream = torch.cuda.Stream()
+    vs = [torch.from_numpy(v).cuda() for v in wl.vs]
+    out = torch.empty(wl.nscales * N, device="cuda", dtype=torch.float64)
+    flush = torch.empty(256 << 20, device="cuda", dtype=torch.uint8)   # 256 MiB > 129 MB L2
+    opts = pk.make_options(nscales=wl.nscales, no_cache=1)
+
+    def step():
+        pk.phiks_apply_ex(plan.handle, wl.tau, wl.p, vs, out, stream, opts=opts)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            step()
+    torch.cuda.synchronize()
+    s_, q_, T_, tuckers = plan.last_params()
+
+    # ---- timed region: K steps, L2 flushed before each (flush not timed)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = pk.phiks_kernel_launches()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    launches = pk.phiks_kernel_launches() - launches0
+    barrier()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t[0])
+    ms_step = ms / args.steps
+    value = ws * wl.nscales * args.steps / (ms * 1e-3)
+    gpu_out = out.cpu().numpy().copy()
+
+    # ---- kernel-level pass: events around every mu-mode product launch
+    pk.phiks_profile_enable(plan.handle, True)
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            step()
+    kms, klaunch, kflops = pk.phiks_profile_read(plan.handle)
+    pk.phiks_profile_enable(plan.handle, False)
+    per_launch_ms = kms / max(klaunch, 1)
+    achieved = kflops / max(kms, 1e-9) / 1e9          # TFLOP/s (flops / ms / 1e9)
+    step_flops = kflops / args.steps
+
+    # ---- cached small exponentials (steady state of a fixed-step integrator)
+    opts_c = pk.make_options(nscales=wl.nscales)
+    with torch.cuda.stream(stream):
+        pk.phiks_apply_ex(plan.handle, wl.tau, wl.p, vs, out, stream, opts=opts_c)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cms = 0.0
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+            e0.record(stream)
+            pk.phiks_apply_ex(plan.handle, wl.tau, wl.p, vs, out, stream, opts=opts_c)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        cms += e0.elapsed_time(e1)
+
+    # ---- end to end through the C ABI with host buffers
+    hv = [torch.from_numpy(v).pin_memory() for v in wl.vs]
+    hout = torch.empty(wl.nscales * N, dtype=torch.float64).pin_memory()
+    dv = [torch.empty(N, device="cuda", dtype=torch.float64) for _ in wl.vs]
+    e2e_ms = 0.0
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+            e0.record(stream)
+            for h, d in zip(hv, dv):
+                d.copy_(h, non_blocking=True)
+            pk.phiks_apply_ex(plan.handle, wl.tau, wl.p, dv, out, stream, opts=opts)
+            hout.copy_(out, non_blocking=True)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    h2d = sum(v.nbytes for v in wl.vs)
+    d2h = hout.numel() * 8
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "phi-actions/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": config_dict(wl, {"s": s_, "q": q_, "T#": T_, "tuckers_per_step": tuckers,
+                                   "l2": "flushed before every timed step (256 MiB write, untimed)",
+                                   "small_exponentials": "recomputed every step"}),
+        "mu_mode_tflops": step_flops / (ms_step * 1e-3) / 1e12,
+        "value_cached_exponentials": ws * wl.nscales * args.steps / (cms * 1e-3),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / PEAK_FP64_TFLOPS, "traffic": None,
+                     "kernel": "mode_product_f64_kernel", "per_launch_ms": per_launch_ms,
+                     "flops_per_launch": kflops / max(klaunch, 1),
+                     "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
+        "e2e": {"value": ws * wl.nscales * args.steps / (e2e_ms * 1e-3), "unit": "phi-actions/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "wall_s_timed": t_wall,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        dt, outs = time_oracle_call(wl)
+        err = max(float(np.abs(gpu_out[L * N:(L + 1) * N] - outs[L]).max() / np.abs(outs[L]).max())
+                  for L in range(wl.nscales))
+        line["rel_err_vs_oracle"] = err
+        line["cpu_baseline"] = {"value": wl.nscales / dt, "unit": "phi-actions/s",
+                                "cores": oracle_threads(), "kind": "oracle",
+                                "sample": "one full call (3 scale outputs), O3 Taylor action, %.1f s" % dt}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="phiks", choices=["phiks", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_phiks(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * phiks.h - C ABI of the GB300 (sm_103a) library for actions of phi-functions
+ * of Kronecker sums (Caliari, Cassini, Zivcovich, "A mu-mode approach for
+ * exponential integrators: actions of phi-functions of Kronecker sums",
+ * arXiv 2210.07667).
+ *
+ * Problem (Sec. 1, eq. kronsum, eq. diffphi, eq. lincomb): for
+ * K = A_d (+) ... (+) A_1 = sum_mu I_d x ... x A_mu x ... x I_1 (never formed),
+ * compute either the same-vector set
+ *     { phi_0(tau K) v, phi_1(tau K) v, ..., phi_p(tau K) v }
+ * or the linear combination
+ *     exp(tau K) v_0 + phi_1(tau K) v_1 + ... + phi_p(tau K) v_p,
+ * optionally also at the time scales tau / 2^(j-1), j = 1..nscales
+ * (eq. scaldiffphi, eq. scallincomb).
+ *
+ * Layout (Lemma 1 of Sec. 2): a vector of length N = n_1 * ... * n_d is the
+ * column-major vec of an n_1 x ... x n_d tensor (mode 1 fastest).  Matrices
+ * A_mu are n_mu x n_mu, column-major, real.
+ *
+ * Conventions for every entry point:
+ *   - pointers named "host" are CPU memory, all other buffers are device
+ *     memory on the device that was current when the plan was made;
+ *   - the caller owns every buffer it passes; the plan owns its device copies
+ *     of A_mu, the cached small exponentials and its default workspace;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *     apply calls are asynchronous on that stream except where stated;
+ *   - nothing throws: each call returns a phiks_status and records a message
+ *     that phiks_last_error() returns (thread-local);
+ *   - a plan is not safe for concurrent applies unless each apply passes its
+ *     own workspace through phiks_options.
+ */
+#ifndef PHIKS_H
+#define PHIKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PHIKS_MAX_D 8   /* largest tensor order d */
+#define PHIKS_MAX_P 8   /* largest phi order p */
+
+typedef struct phiks_plan_s* phiks_plan_t;
+
+typedef enum {
+  PHIKS_OK = 0,
+  PHIKS_ERR_INVALID = 1,      /* bad argument (null pointer, size, p, nv ...) */
+  PHIKS_ERR_OOM = 2,          /* device or host allocation failed */
+  PHIKS_ERR_UNSUPPORTED = 3,  /* valid request this build does not implement */
+  PHIKS_ERR_NO_PARAMS = 4,    /* no (s, q) meets the tolerance (Sec. 3.3) */
+  PHIKS_ERR_CUDA = 5,         /* a CUDA runtime call failed */
+  PHIKS_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up */
+} phiks_status;
+
+/* Arithmetic of the mu-mode products.  FP64: vectors are double.  The split
+ * types keep vectors in float and run the products on the tensor cores:
+ * TF32 (one product), TF32X3 and BF16X3 (three-term compensated products,
+ * hi*hi + hi*lo + lo*hi, FP32 accumulation).  Small exponentials, their
+ * squaring and the doubling-formula combination stay FP64 in every type. */
+typedef enum { PHIKS_FP64 = 0, PHIKS_TF32 = 1, PHIKS_TF32X3 = 2, PHIKS_BF16X3 = 3 } phiks_dtype;
+
+/* Quadrature rule for the phi integral (Sec. 3.3): Gauss-Lobatto-Legendre
+ * (default; theta_1 = 0 and theta_q = 1 save one Tucker operator each) or
+ * Gauss-Legendre. */
+typedef enum { PHIKS_RULE_GLL = 0, PHIKS_RULE_GL = 1 } phiks_rule;
+
+typedef struct {
+  double tol;            /* delta of Sec. 3.3: ||R_q|| ||v|| <= delta (absolute,
+                            2-norm).  Default 2^-53. */
+  int nscales;           /* s-hat >= 1: outputs at tau, tau/2, ... tau/2^(nscales-1) */
+  int rule;              /* phiks_rule */
+  int qmin, qmax;        /* node-count range, default [3, 12] */
+  int skip_phi0;         /* same-vector task: omit the phi_0 = exp(tau K) v blocks */
+  int force_s, force_q;  /* >= 0: use this scaling / node count instead of the
+                            selection of Sec. 3.3 (both or neither) */
+  const double* vnorms;  /* host, nv entries ||v_l||_2 (0 for NULL vectors), or
+                            NULL: the norms are computed on the device and the
+                            call synchronises `stream` once to read them */
+  void* workspace;       /* device workspace of >= phiks_workspace_size bytes,
+                            or NULL for the plan's own */
+  size_t workspace_bytes;
+  int no_cache;          /* recompute the small exponentials on every call */
+  int reserved[7];
+} phiks_options;
+
+/* Fill `opt` with the defaults above. */
+void phiks_options_init(phiks_options* opt);
+
+/* Build a plan for K = A_d (+) ... (+) A_1 (Sec. 1, eq. kronsum).
+ *   d        tensor order, 1 <= d <= PHIKS_MAX_D
+ *   n        host, d entries, n_mu >= 1
+ *   A        host, d pointers to column-major n_mu x n_mu doubles (copied)
+ *   dtype    arithmetic of the mu-mode products (phiks_dtype)
+ *   out      receives the plan; NULL on failure
+ * Computes on the host the shifts sigma_mu = tr(A_mu)/n_mu (Remark of Sec. 3.1)
+ * and the numerical-range rectangles Xi_mu (Sec. 3.3), and uploads A_mu. */
+phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dtype,
+                        phiks_plan_t* out);
+
+/* phiks_apply_ex with default options (one scale, tolerance 2^-53). */
+phiks_status phiks_apply(phiks_plan_t plan, double tau, int p, const void* const* v, int nv,
+                         void* out, void* stream);
+
+/* Actions of phi-functions of tau K (Sec. 3.1 for nv == 1, Sec. 3.2 for
+ * nv == p + 1).
+ *   tau      time step (any nonzero real)
+ *   p        highest phi order, 0 <= p <= PHIKS_MAX_P
+ *   v        host array of nv device pointers to N elements each (double for
+ *            PHIKS_FP64, float otherwise); in the linear combination any v[l]
+ *            may be NULL (a zero vector; v[0] == NULL skips the exp Tuckers)
+ *   nv       1: same vector;  p + 1: linear combination
+ *   out      device, written (not accumulated):
+ *            same vector: nscales blocks, block j (j = 0..nscales-1) holds
+ *              phi_0..phi_p (tau K / 2^j) v, each N elements, phi_0 first
+ *              (phi_1..phi_p only when skip_phi0);
+ *            linear combination: nscales blocks of N elements, block j =
+ *              exp(c tau K) v_0 + sum_l c^l phi_l(c tau K) v_l, c = 2^-j
+ *              (the c^l convention of eq. scallincomb).
+ * The first call for a given (tau, s, q) builds the small exponentials
+ * exp((1 - theta_i) tau A_mu / 2^s) on the device and caches them in the plan.
+ * Without opt->vnorms the call synchronises `stream` once (norms of v). */
+phiks_status phiks_apply_ex(phiks_plan_t plan, double tau, int p, const void* const* v, int nv,
+                            const phiks_options* opt, void* out, void* stream);
+
+/* Device workspace bytes an apply with these arguments needs (for
+ * phiks_options.workspace).  Host only. */
+phiks_status phiks_workspace_size(phiks_plan_t plan, int p, int nv, int nscales, size_t* bytes);
+
+/* The (s, q) the selection of Sec. 3.3 picks, and T# of eq. (Tpsv) / eq. (Tlcp),
+ * for the given norms (host, nv entries).  Host only, no GPU work. */
+phiks_status phiks_select_params(phiks_plan_t plan, double tau, int p, int nv,
+                                 const double* vnorms, const phiks_options* opt,
+                                 int* s, int* q, int* tcount);
+
+/* Same selection without a plan and without any GPU work: the operators are
+ * passed as in phiks_plan (host, column-major, not retained).  Useful to
+ * inspect the cost T# of a problem before planning it. */
+phiks_status phiks_choose_params(int d, const int64_t* n, const double* const* A, double tau,
+                                 int p, int nv, const double* vnorms, const phiks_options* opt,
+                                 int* s, int* q, int* tcount);
+
+/* (s, q, T#, Tucker operators launched) of the last successful apply. */
+phiks_status phiks_last_params(phiks_plan_t plan, int* s, int* q, int* tcount, int* tuckers);
+
+/* Tucker operator W = V x_1 L_1 x_2 ... x_d L_d (Sec. 2) in the plan's dtype.
+ *   V, W     device, N elements each (may not alias)
+ *   L        host array of d device pointers to column-major n_mu x n_mu
+ *            doubles (converted on the fly for the split dtypes) */
+phiks_status phiks_tucker(phiks_plan_t plan, const void* V, void* W, const double* const* L,
+                          void* stream);
+
+/* Batched FP64 matrix exponential E_b = exp(X_b) (the small exponentials of
+ * Sec. 3.1 / Sec. 4 intro), by truncated Taylor series with scaling and
+ * squaring.  X and E: device, `batch` column-major n x n matrices stored
+ * back to back; X is not modified; X and E may not alias. */
+phiks_status phiks_expm(int batch, int n, const double* X, double* E, void* stream);
+
+/* Kernel timing for measurement tools.  While enabled, every mu-mode product
+ * the plan launches is bracketed by two CUDA events on its stream.
+ * phiks_profile_read synchronises the plan's device, returns the summed
+ * milliseconds of those launches, their count and their algorithmic flops
+ * (2 N n_mu each), and resets the sums. */
+phiks_status phiks_profile_enable(phiks_plan_t plan, int enable);
+phiks_status phiks_profile_read(phiks_plan_t plan, double* ms, int64_t* launches, double* flops);
+
+/* Number of kernels this library has launched in this process (all plans). */
+uint64_t phiks_kernel_launches(void);
+
+/* Release the plan and its device memory (synchronises its device). */
+void phiks_destroy(phiks_plan_t plan);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* phiks_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PHIKS_H */

@@ -1,0 +1,290 @@
+"""Python binding of the phiks C ABI (include/phiks.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libphiks.so.  Device buffers are torch tensors (their data_ptr is
+passed through), streams are torch.cuda.Stream objects (their cuda_stream
+handle is passed through).  If the library is missing or fails to load this
+module raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+__all__ = [
+    "PHIKS_FP64", "PHIKS_TF32", "PHIKS_TF32X3", "PHIKS_BF16X3", "PHIKS_RULE_GLL", "PHIKS_RULE_GL",
+    "PhiksError", "Options", "lib", "library_path", "load",
+    "phiks_plan", "phiks_apply", "phiks_apply_ex", "phiks_workspace_size",
+    "phiks_select_params", "phiks_choose_params", "phiks_last_params", "phiks_tucker", "phiks_expm",
+    "phiks_profile_enable", "phiks_profile_read", "phiks_kernel_launches",
+    "phiks_destroy", "phiks_last_error", "Plan", "EXPORTED",
+]
+
+PHIKS_FP64, PHIKS_TF32, PHIKS_TF32X3, PHIKS_BF16X3 = 0, 1, 2, 3
+PHIKS_RULE_GLL, PHIKS_RULE_GL = 0, 1
+DTYPES = {"fp64": PHIKS_FP64, "tf32": PHIKS_TF32, "tf32x3": PHIKS_TF32X3, "bf16x3": PHIKS_BF16X3}
+STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "UNSUPPORTED", 4: "NO_PARAMS", 5: "CUDA", 6: "TIMEOUT"}
+
+# every symbol include/phiks.h declares
+EXPORTED = [
+    "phiks_options_init", "phiks_plan", "phiks_apply", "phiks_apply_ex", "phiks_workspace_size",
+    "phiks_select_params", "phiks_choose_params", "phiks_last_params", "phiks_tucker", "phiks_expm",
+    "phiks_profile_enable", "phiks_profile_read", "phiks_kernel_launches", "phiks_destroy",
+    "phiks_last_error",
+]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def library_path() -> str:
+    return os.path.join(HERE, "libphiks.so")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("tol", ctypes.c_double),
+        ("nscales", ctypes.c_int),
+        ("rule", ctypes.c_int),
+        ("qmin", ctypes.c_int),
+        ("qmax", ctypes.c_int),
+        ("skip_phi0", ctypes.c_int),
+        ("force_s", ctypes.c_int),
+        ("force_q", ctypes.c_int),
+        ("vnorms", ctypes.POINTER(ctypes.c_double)),
+        ("workspace", ctypes.c_void_p),
+        ("workspace_bytes", ctypes.c_size_t),
+        ("no_cache", ctypes.c_int),
+        ("reserved", ctypes.c_int * 7),
+    ]
+
+
+class PhiksError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("phiks %s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libphiks.so (optionally building it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError("libphiks.so is not built; run __graft_entry__.build() or "
+                              "python paper_2210_07667_gb300/_build.py")
+        from . import _build
+        _build.build()
+    L = ctypes.CDLL(path)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    L.phiks_options_init.argtypes = [ctypes.POINTER(Options)]
+    L.phiks_options_init.restype = None
+    L.phiks_plan.argtypes = [i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_void_p), i,
+                             ctypes.POINTER(vp)]
+    L.phiks_apply.argtypes = [vp, d, i, ctypes.POINTER(vp), i, vp, vp]
+    L.phiks_apply_ex.argtypes = [vp, d, i, ctypes.POINTER(vp), i, ctypes.POINTER(Options), vp, vp]
+    L.phiks_workspace_size.argtypes = [vp, i, i, i, ctypes.POINTER(sz)]
+    L.phiks_select_params.argtypes = [vp, d, i, i, ctypes.POINTER(d), ctypes.POINTER(Options),
+                                      ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.phiks_choose_params.argtypes = [i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_void_p),
+                                      d, i, i, ctypes.POINTER(d), ctypes.POINTER(Options),
+                                      ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.phiks_last_params.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                                    ctypes.POINTER(i)]
+    L.phiks_tucker.argtypes = [vp, vp, vp, ctypes.POINTER(vp), vp]
+    L.phiks_expm.argtypes = [i, i, vp, vp, vp]
+    L.phiks_profile_enable.argtypes = [vp, i]
+    L.phiks_profile_enable.restype = ctypes.c_int
+    L.phiks_profile_read.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64),
+                                     ctypes.POINTER(d)]
+    L.phiks_profile_read.restype = ctypes.c_int
+    L.phiks_kernel_launches.argtypes = []
+    L.phiks_kernel_launches.restype = ctypes.c_uint64
+    L.phiks_destroy.argtypes = [vp]
+    L.phiks_destroy.restype = None
+    L.phiks_last_error.argtypes = []
+    L.phiks_last_error.restype = ctypes.c_char_p
+    for name in ["phiks_plan", "phiks_apply", "phiks_apply_ex", "phiks_workspace_size",
+                 "phiks_select_params", "phiks_choose_params", "phiks_last_params", "phiks_tucker",
+                 "phiks_expm"]:
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def lib() -> ctypes.CDLL:
+    return load()
+
+
+def phiks_last_error() -> str:
+    return load().phiks_last_error().decode()
+
+
+def _check(st: int):
+    if st != 0:
+        raise PhiksError(st, phiks_last_error())
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_options(**kw) -> Options:
+    o = Options()
+    load().phiks_options_init(ctypes.byref(o))
+    vn = kw.pop("vnorms", None)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    if vn is not None:
+        arr = (ctypes.c_double * len(vn))(*[float(x) for x in vn])
+        o.vnorms = ctypes.cast(arr, ctypes.POINTER(ctypes.c_double))
+        o._keep = arr
+    return o
+
+
+def phiks_plan(A: Sequence[np.ndarray], dtype: int = PHIKS_FP64) -> int:
+    """Plan for K = A_d (+) ... (+) A_1; A_mu host arrays (any order, copied
+    to column-major doubles)."""
+    d = len(A)
+    mats = [np.asfortranarray(np.asarray(a, dtype=np.float64)) for a in A]
+    n = (ctypes.c_int64 * d)(*[m.shape[0] for m in mats])
+    ptrs = (ctypes.c_void_p * d)(*[m.ctypes.data for m in mats])
+    out = ctypes.c_void_p()
+    _check(load().phiks_plan(d, n, ptrs, int(dtype), ctypes.byref(out)))
+    return out.value
+
+
+def _vptrs(vs):
+    arr = (ctypes.c_void_p * len(vs))(*[_ptr(v) for v in vs])
+    return arr
+
+
+def phiks_apply(plan: int, tau: float, p: int, vs, out, stream=None):
+    _check(load().phiks_apply(plan, float(tau), int(p), _vptrs(vs), len(vs), _ptr(out), _stream(stream)))
+
+
+def phiks_apply_ex(plan: int, tau: float, p: int, vs, out, stream=None, opts: Optional[Options] = None,
+                   **kw):
+    o = opts if opts is not None else make_options(**kw)
+    _check(load().phiks_apply_ex(plan, float(tau), int(p), _vptrs(vs), len(vs), ctypes.byref(o),
+                                 _ptr(out), _stream(stream)))
+
+
+def phiks_workspace_size(plan: int, p: int, nv: int, nscales: int = 1) -> int:
+    b = ctypes.c_size_t()
+    _check(load().phiks_workspace_size(plan, p, nv, nscales, ctypes.byref(b)))
+    return b.value
+
+
+def phiks_select_params(plan: int, tau: float, p: int, vnorms: Sequence[float], **kw):
+    o = make_options(**kw)
+    vn = (ctypes.c_double * len(vnorms))(*[float(x) for x in vnorms])
+    s, q, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().phiks_select_params(plan, float(tau), int(p), len(vnorms), vn, ctypes.byref(o),
+                                      ctypes.byref(s), ctypes.byref(q), ctypes.byref(t)))
+    return s.value, q.value, t.value
+
+
+def phiks_choose_params(A: Sequence[np.ndarray], tau: float, p: int, vnorms: Sequence[float], **kw):
+    """(s, q, T#) of Sec. 3.3 on the host, without a plan or a GPU."""
+    d = len(A)
+    mats = [np.asfortranarray(np.asarray(a, dtype=np.float64)) for a in A]
+    n = (ctypes.c_int64 * d)(*[m.shape[0] for m in mats])
+    ptrs = (ctypes.c_void_p * d)(*[m.ctypes.data for m in mats])
+    o = make_options(**kw)
+    vn = (ctypes.c_double * len(vnorms))(*[float(x) for x in vnorms])
+    s, q, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().phiks_choose_params(d, n, ptrs, float(tau), int(p), len(vnorms), vn, ctypes.byref(o),
+                                      ctypes.byref(s), ctypes.byref(q), ctypes.byref(t)))
+    return s.value, q.value, t.value
+
+
+def phiks_last_params(plan: int):
+    s, q, t, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().phiks_last_params(plan, ctypes.byref(s), ctypes.byref(q), ctypes.byref(t),
+                                    ctypes.byref(k)))
+    return s.value, q.value, t.value, k.value
+
+
+def phiks_tucker(plan: int, V, W, Ls, stream=None):
+    _check(load().phiks_tucker(plan, _ptr(V), _ptr(W), _vptrs(Ls), _stream(stream)))
+
+
+def phiks_expm(X, E, stream=None):
+    """X, E: device tensors of shape (batch, n, n) holding column-major
+    matrices (i.e. each [k] is the transpose in torch's row-major view)."""
+    batch, n = int(X.shape[0]), int(X.shape[-1])
+    _check(load().phiks_expm(batch, n, _ptr(X), _ptr(E), _stream(stream)))
+
+
+def phiks_profile_enable(plan: int, enable: bool = True):
+    _check(load().phiks_profile_enable(plan, int(bool(enable))))
+
+
+def phiks_profile_read(plan: int):
+    """(milliseconds, launches, flops) of the mu-mode products since the last read."""
+    ms, n, fl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+    _check(load().phiks_profile_read(plan, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl)))
+    return ms.value, n.value, fl.value
+
+
+def phiks_kernel_launches() -> int:
+    return int(load().phiks_kernel_launches())
+
+
+def phiks_destroy(plan: int):
+    if plan:
+        load().phiks_destroy(plan)
+
+
+class Plan:
+    """Owning wrapper: Plan(A_list, dtype).apply(...)."""
+
+    def __init__(self, A: Sequence[np.ndarray], dtype: int = PHIKS_FP64):
+        self.n = [int(np.asarray(a).shape[0]) for a in A]
+        self.N = int(np.prod(self.n))
+        self.dtype = dtype
+        self.handle = phiks_plan(A, dtype)
+
+    def apply(self, tau, p, vs, out, stream=None, **kw):
+        if kw:
+            phiks_apply_ex(self.handle, tau, p, vs, out, stream, **kw)
+        else:
+            phiks_apply(self.handle, tau, p, vs, out, stream)
+        return out
+
+    def last_params(self):
+        return phiks_last_params(self.handle)
+
+    def select_params(self, tau, p, vnorms, **kw):
+        return phiks_select_params(self.handle, tau, p, vnorms, **kw)
+
+    def close(self):
+        if self.handle:
+            phiks_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

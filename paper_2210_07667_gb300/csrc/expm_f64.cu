@@ -1,0 +1,96 @@
+// Small dense FP64 matrices: batched GEMM with an identity term and batched
+// scaling, the building blocks of the truncated-Taylor scaling-and-squaring
+// exponential of the small matrices (1 - theta_i) tau A_mu / 2^s (Sec. 3.1,
+// eq. Tuckerprod) and of the squaring chain exp(A_mu/2^(j-1)) =
+// exp(A_mu/2^j)^2 (eq. simul, eq. comb).
+#include "kernels.cuh"
+
+namespace phiks {
+namespace {
+
+constexpr int GT = 32, GK = 16, GNT = 256;
+constexpr int GR = 2;                  // 2 x 2 outputs per thread
+constexpr int GTHR = GT / GR;          // 16
+
+__global__ void __launch_bounds__(GNT) gemm_batch_f64_kernel(GemmBatch gb) {
+  const int k = blockIdx.z;
+  const int n = gb.n[k];
+  const int tiles = (n + GT - 1) / GT;
+  const int bi = blockIdx.x, bj = blockIdx.y;
+  if (bi >= tiles || bj >= tiles) return;
+  const double* __restrict__ A = gb.A[k];
+  const double* __restrict__ B = gb.B[k];
+  double* C = gb.C[k];
+  __shared__ double sA[GK][GT + 1];   // sA[kk][ii] = A[i0+ii, k0+kk]
+  __shared__ double sB[GK][GT + 1];   // sB[kk][jj] = B[k0+kk, j0+jj]
+  const int tid = threadIdx.x;
+  const int tj = tid % GTHR, ti = tid / GTHR;
+  const int i0 = bi * GT, j0 = bj * GT;
+  double acc[GR][GR] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int k0 = 0; k0 < n; k0 += GK) {
+    for (int e = tid; e < GT * GK; e += GNT) {
+      int ii = e % GT, kk = e / GT;
+      int i = i0 + ii, kc = k0 + kk;
+      sA[kk][ii] = (i < n && kc < n) ? A[i + (int64_t)n * kc] : 0.0;
+      int kr = k0 + (e % GK), jj = e / GK, j = j0 + jj;
+      sB[e % GK][jj] = (kr < n && j < n) ? B[kr + (int64_t)n * j] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      double a0 = sA[kk][ti], a1 = sA[kk][ti + GTHR];
+      double b0 = sB[kk][tj], b1 = sB[kk][tj + GTHR];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+  const double alpha = gb.alpha[k], beta = gb.beta_I[k];
+#pragma unroll
+  for (int r = 0; r < GR; ++r)
+#pragma unroll
+    for (int c = 0; c < GR; ++c) {
+      int i = i0 + ti + r * GTHR, j = j0 + tj + c * GTHR;
+      if (i < n && j < n) C[i + (int64_t)n * j] = alpha * acc[r][c] + (i == j ? beta : 0.0);
+    }
+}
+
+__global__ void scale_batch_f64_kernel(ScaleBatch sb) {
+  const int k = blockIdx.y;
+  const int n = sb.n[k];
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e % n, j = e / n;
+    double x = sb.X[k][e] - (i == j ? sb.shift[k] : 0.0);
+    sb.Y[k][e] = sb.alpha[k] * x;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_batch_f64(const GemmBatch& gb, int nmax, cudaStream_t st) {
+  if (gb.count <= 0) return cudaSuccess;
+  if (gb.count > kMaxBatch) return cudaErrorInvalidValue;
+  const int tiles = (nmax + GT - 1) / GT;
+  dim3 grid(tiles, tiles, gb.count);
+  count_launch();
+  gemm_batch_f64_kernel<<<grid, GNT, 0, st>>>(gb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_batch_f64(const ScaleBatch& sb, int nmax, cudaStream_t st) {
+  if (sb.count <= 0) return cudaSuccess;
+  if (sb.count > kMaxBatch) return cudaErrorInvalidValue;
+  int64_t nn = (int64_t)nmax * nmax;
+  int gx = (int)((nn + 255) / 256);
+  if (gx > 1024) gx = 1024;
+  dim3 grid(gx, sb.count);
+  count_launch();
+  scale_batch_f64_kernel<<<grid, 256, 0, st>>>(sb);
+  return cudaGetLastError();
+}
+
+}  // namespace phiks

@@ -1,0 +1,89 @@
+// Device-side building blocks of the phiks hot path and their launchers.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace phiks {
+
+// Process-wide count of kernels launched by this library.
+uint64_t kernel_launch_count();
+void count_launch();
+
+constexpr int kMaxSrc = 10;  // tensors one combination may read
+constexpr int kMaxOut = 8;   // tensors one epilogue may write
+
+// Input of a mu-mode product as a linear combination of tensors:
+//   x[idx] = sum_m coef[m] * src[m][idx]        (nsrc >= 1)
+// (the prologue of eq. integrandcomb; a plain input is nsrc = 1, coef = 1).
+struct Combo {
+  int nsrc;
+  int f32mask;                 // bit m set: src[m] holds float, else double
+  const double* src[kMaxSrc];  // typed by f32mask
+  double coef[kMaxSrc];
+};
+
+// Output stage shared by the Tucker epilogue and the elementwise kernel:
+//   out[t][idx] = b[t] * result + sum_m a[t][m] * src[m][idx],  t < nout.
+// With nout == 0 the result is stored to the kernel's plain output.  An out[t]
+// may equal a src[m]: each element is read before it is written by the same
+// thread.
+struct Epi {
+  int nout;
+  int nsrc;
+  int out_f32mask;             // bit t set: out[t] is float (FP64 arithmetic, rounded once)
+  int src_f32mask;             // bit m set: src[m] is float
+  double* out[kMaxOut];        // typed by out_f32mask
+  const double* src[kMaxSrc];
+  double b[kMaxOut];
+  double a[kMaxOut][kMaxSrc];
+};
+
+// Geometry of one mu-mode product on a tensor viewed as (a, n, b):
+// element (x, j, y) at x + a*j + a*n*y.
+struct ModeGeom {
+  int64_t a;   // product of n_nu for nu < mu
+  int n;       // n_mu
+  int64_t b;   // product of n_nu for nu > mu
+};
+
+// W = V x_mu L (FP64).  V given by `pro` (a combination), L column-major
+// n x n.  With epi == nullptr or epi->nout == 0 the result goes to W.
+cudaError_t launch_mode_product_f64(const Combo& pro, const double* L, ModeGeom g, double* W,
+                                    const Epi* epi, cudaStream_t st);
+
+// out[t][i] = sum_m a[t][m] src[m][i] over N elements (Epi with b ignored),
+// FP64 arithmetic; sources and outputs double or float as the masks say.
+cudaError_t launch_combine(const Epi& e, int64_t N, cudaStream_t st);
+
+// out[k] = ||x_k||_2^2 accumulated (out must be zeroed), k < count; x_k double
+// (is_f32 == 0) or float.
+cudaError_t launch_sumsq(const void* const* x, int count, int64_t N, int is_f32, double* out,
+                         cudaStream_t st);
+
+// ---- small dense FP64 matrices (the exponentials of Sec. 3) ---------------
+constexpr int kMaxBatch = 64;
+
+struct GemmBatch {
+  int count;
+  int n[kMaxBatch];
+  const double* A[kMaxBatch];
+  const double* B[kMaxBatch];
+  double* C[kMaxBatch];
+  double alpha[kMaxBatch];
+  double beta_I[kMaxBatch];  // C = alpha A B + beta_I I
+};
+// Batched C_k = alpha_k A_k B_k + beta_k I (column-major n_k x n_k).
+cudaError_t launch_gemm_batch_f64(const GemmBatch& gb, int nmax, cudaStream_t st);
+
+struct ScaleBatch {
+  int count;
+  int n[kMaxBatch];
+  const double* X[kMaxBatch];
+  double* Y[kMaxBatch];
+  double alpha[kMaxBatch];
+  double shift[kMaxBatch];  // Y = alpha (X - shift I)
+};
+cudaError_t launch_scale_batch_f64(const ScaleBatch& sb, int nmax, cudaStream_t st);
+
+}  // namespace phiks

@@ -1,0 +1,1061 @@
+// C ABI of the phiks library: plans, parameter selection, small exponentials
+// and the quadrature / squaring schedule of Sec. 3.1 (same vector) and
+// Sec. 3.2 (linear combination), driving the mu-mode kernels on one stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/phiks.h"
+#include "kernels.cuh"
+#include "planner.hpp"
+#include "tc.cuh"
+
+using namespace phiks;
+
+namespace {
+
+thread_local std::string g_err;
+
+phiks_status fail(phiks_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(e_ == cudaErrorMemoryAllocation ? PHIKS_ERR_OOM : PHIKS_ERR_CUDA,      \
+                  "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+#define TRY(call)                    \
+  do {                               \
+    phiks_status s_ = (call);        \
+    if (s_ != PHIKS_OK) return s_;   \
+  } while (0)
+
+double factorial(int k) {
+  double f = 1;
+  for (int i = 2; i <= k; ++i) f *= i;
+  return f;
+}
+
+Epi make_epi() {
+  Epi e;
+  std::memset(&e, 0, sizeof e);
+  return e;
+}
+
+Combo make_combo() {
+  Combo c;
+  std::memset(&c, 0, sizeof c);
+  return c;
+}
+
+// A cached set of small exponentials for one (tau, s, q, rule):
+// bank entry b holds exp((1 - theta_b) tau A_mu / 2^s) for every mu, b over the
+// nodes with theta < 1, plus (Gauss-Legendre only) theta = 0 for the squaring.
+struct Bank {
+  double tau = 0;
+  int s = -1, q = -1, rule = -1;
+  double* dev = nullptr;
+  std::vector<std::vector<size_t>> off;  // off[b][mu], in doubles
+  std::vector<int> node_bank;            // quadrature node -> bank entry, -1 for theta = 1
+  int b0 = -1;                           // entry of exp(tau A_mu / 2^s)
+  std::vector<double> theta, w;
+  uint64_t stamp = 0;
+};
+
+}  // namespace
+
+struct phiks_plan_s {
+  int device = 0;
+  int d = 0;
+  int64_t n[PHIKS_MAX_D] = {0};
+  int64_t N = 0;
+  int dtype = PHIKS_FP64;
+  std::vector<std::vector<double>> A;
+  double sigma[PHIKS_MAX_D] = {0};
+  double norm1_shifted[PHIKS_MAX_D] = {0};
+  Rect rect[PHIKS_MAX_D];
+  double* dAs = nullptr;  // device: A_mu - sigma_mu I, concatenated
+  size_t offA[PHIKS_MAX_D] = {0};
+  size_t sum_n2 = 0;
+  int nmax = 0;
+  std::vector<Bank> banks;
+  uint64_t clock = 0;
+  double* expm_scratch = nullptr;  // 3 x (q + 1) x sum_n2 doubles
+  size_t expm_scratch_elems = 0;
+  double* msq[2] = {nullptr, nullptr};  // squaring chain ping-pong, sum_n2 each
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  double* d_norms = nullptr;
+  double* h_norms = nullptr;  // pinned
+  std::map<std::tuple<double, int, int, int, int, double, int, int, std::vector<int>>, Selection>
+      param_cache;
+  int last_s = -1, last_q = -1, last_T = -1, last_tuckers = 0;
+  TcState* tc = nullptr;
+  // profiling: event pairs around mu-mode products
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  double prof_flops = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+int64_t mode_a(const phiks_plan_s* P, int mu) {
+  int64_t a = 1;
+  for (int nu = 0; nu < mu; ++nu) a *= P->n[nu];
+  return a;
+}
+int64_t mode_b(const phiks_plan_s* P, int mu) {
+  int64_t b = 1;
+  for (int nu = mu + 1; nu < P->d; ++nu) b *= P->n[nu];
+  return b;
+}
+
+size_t elt_size(const phiks_plan_s* P) { return P->dtype == PHIKS_FP64 ? 8 : 4; }
+
+// Workspace: p accumulators and two Tucker temporaries of N elements (FP64
+// accumulators even for the split dtypes, whose Tucker temporaries are float),
+// plus the split-operand staging of the tensor-core path.
+size_t workspace_bytes(const phiks_plan_s* P, int p) {
+  size_t N = (size_t)P->N;
+  size_t acc = (size_t)std::max(p, 1) * N * 8;
+  size_t tmp = 2 * N * 8;
+  size_t tcx = P->dtype == PHIKS_FP64 ? 0 : tc_workspace_bytes(P->N);
+  return acc + tmp + tcx + 256 * 4;
+}
+
+Rect tau_rect(const phiks_plan_s* P, double tau) {
+  Rect r;
+  for (int mu = 0; mu < P->d; ++mu) {
+    r.xlo += P->rect[mu].xlo;
+    r.xhi += P->rect[mu].xhi;
+    r.ylo += P->rect[mu].ylo;
+    r.yhi += P->rect[mu].yhi;
+  }
+  Rect o;
+  if (tau >= 0) {
+    o.xlo = tau * r.xlo; o.xhi = tau * r.xhi; o.ylo = tau * r.ylo; o.yhi = tau * r.yhi;
+  } else {
+    o.xlo = tau * r.xhi; o.xhi = tau * r.xlo; o.ylo = tau * r.yhi; o.yhi = tau * r.ylo;
+  }
+  return o;
+}
+
+// Norms are rounded up to the next power of 2^(1/8): a larger norm only makes
+// the selection more conservative, and nearby norms share one cache entry.
+int norm_bucket(double x) {
+  if (!(x > 0)) return -100000;
+  return (int)std::ceil(8.0 * std::log2(x));
+}
+
+phiks_status select_cached(phiks_plan_s* P, double tau, int p, int kind, const double* vnorms,
+                           int nv, const phiks_options& o, Selection* sel) {
+  std::vector<int> key_norms(nv);
+  std::vector<double> rounded(nv);
+  for (int i = 0; i < nv; ++i) {
+    key_norms[i] = norm_bucket(vnorms[i]);
+    rounded[i] = vnorms[i] > 0 ? std::exp2(key_norms[i] / 8.0) : 0.0;
+  }
+  auto key = std::make_tuple(tau, p, kind, o.nscales, o.rule, o.tol, o.qmin, o.qmax, key_norms);
+  auto it = P->param_cache.find(key);
+  if (it != P->param_cache.end()) {
+    *sel = it->second;
+    return PHIKS_OK;
+  }
+  Rect xi = tau_rect(P, tau);
+  if (!select_params(xi, p, kind, rounded.data(), o.nscales, o.tol, o.qmin, o.qmax, o.rule, sel))
+    return fail(PHIKS_ERR_NO_PARAMS, "no (s, q) with q in [%d, %d] meets tol %g", o.qmin, o.qmax,
+                o.tol);
+  P->param_cache[key] = *sel;
+  return PHIKS_OK;
+}
+
+// ---- small exponentials ----------------------------------------------------
+// E = e^{c sigma} T_14(X)^(2^t) with X = c (A - sigma I) / 2^t, ||X||_1 <= 1/2:
+// truncated Taylor series of degree 14 by Horner's rule (remainder below
+// 0.5^15/15! < 2.5e-17), then t squarings (scaling and squaring, Moler and
+// Van Loan's method 3).
+constexpr int kTaylorDeg = 14;
+
+struct ExpmJob {
+  int n;
+  const double* Ashift;  // device, A - sigma I
+  double c;              // scalar factor
+  double norm1;          // ||A - sigma I||_1
+  double esig;           // e^{c sigma}
+  double* out;           // device n x n
+};
+
+phiks_status run_expm_jobs(phiks_plan_s* P, std::vector<ExpmJob>& jobs, double* scratch,
+                           cudaStream_t st) {
+  // scratch: 3 buffers per job (X, T0, T1)
+  std::vector<size_t> offs(jobs.size());
+  size_t tot = 0;
+  int nmax = 1;
+  for (size_t k = 0; k < jobs.size(); ++k) {
+    offs[k] = tot;
+    tot += 3 * (size_t)jobs[k].n * jobs[k].n;
+    nmax = std::max(nmax, jobs[k].n);
+  }
+  std::vector<int> t(jobs.size());
+  int tmax = 0;
+  for (size_t k = 0; k < jobs.size(); ++k) {
+    double nx = std::fabs(jobs[k].c) * jobs[k].norm1;
+    t[k] = nx > 0.5 ? (int)std::ceil(std::log2(nx / 0.5)) : 0;
+    tmax = std::max(tmax, t[k]);
+  }
+  for (size_t k0 = 0; k0 < jobs.size(); k0 += kMaxBatch) {
+    const size_t k1 = std::min(jobs.size(), k0 + kMaxBatch);
+    const int cnt = (int)(k1 - k0);
+    auto X = [&](size_t k) { return scratch + offs[k]; };
+    auto T = [&](size_t k, int i) { return scratch + offs[k] + (size_t)(1 + i) * jobs[k].n * jobs[k].n; };
+    // X = (c / 2^t) (A - sigma I);  T0 = X/14 + I
+    ScaleBatch sb;
+    sb.count = cnt;
+    for (int i = 0; i < cnt; ++i) {
+      size_t k = k0 + i;
+      sb.n[i] = jobs[k].n;
+      sb.X[i] = jobs[k].Ashift;
+      sb.Y[i] = X(k);
+      sb.alpha[i] = std::ldexp(jobs[k].c, -t[k]);
+      sb.shift[i] = 0.0;
+    }
+    CK(launch_scale_batch_f64(sb, nmax, st));
+    for (int i = 0; i < cnt; ++i) {
+      size_t k = k0 + i;
+      sb.X[i] = X(k);
+      sb.Y[i] = T(k, 0);
+      sb.alpha[i] = 1.0 / kTaylorDeg;
+      sb.shift[i] = -(double)kTaylorDeg;
+    }
+    CK(launch_scale_batch_f64(sb, nmax, st));
+    int cur = 0;
+    for (int m = kTaylorDeg - 1; m >= 1; --m) {  // T <- I + X T / m
+      GemmBatch gb;
+      gb.count = cnt;
+      for (int i = 0; i < cnt; ++i) {
+        size_t k = k0 + i;
+        gb.n[i] = jobs[k].n;
+        gb.A[i] = X(k);
+        gb.B[i] = T(k, cur);
+        gb.C[i] = T(k, 1 - cur);
+        gb.alpha[i] = 1.0 / m;
+        gb.beta_I[i] = 1.0;
+      }
+      CK(launch_gemm_batch_f64(gb, nmax, st));
+      cur = 1 - cur;
+    }
+    // squarings: job k squares t[k] times; its current buffer alternates
+    std::vector<int> kcur(cnt, cur);
+    for (int r = 0; r < tmax; ++r) {
+      GemmBatch gb;
+      gb.count = 0;
+      for (int i = 0; i < cnt; ++i) {
+        size_t k = k0 + i;
+        if (t[k] <= r) continue;
+        int j = gb.count++;
+        gb.n[j] = jobs[k].n;
+        gb.A[j] = T(k, kcur[i]);
+        gb.B[j] = T(k, kcur[i]);
+        gb.C[j] = T(k, 1 - kcur[i]);
+        gb.alpha[j] = 1.0;
+        gb.beta_I[j] = 0.0;
+        kcur[i] = 1 - kcur[i];
+      }
+      if (gb.count) CK(launch_gemm_batch_f64(gb, nmax, st));
+    }
+    for (int i = 0; i < cnt; ++i) {
+      size_t k = k0 + i;
+      sb.n[i] = jobs[k].n;
+      sb.X[i] = T(k, kcur[i]);
+      sb.Y[i] = jobs[k].out;
+      sb.alpha[i] = jobs[k].esig;
+      sb.shift[i] = 0.0;
+    }
+    CK(launch_scale_batch_f64(sb, nmax, st));
+  }
+  return PHIKS_OK;
+}
+
+phiks_status ensure_expm_scratch(phiks_plan_s* P, size_t elems) {
+  if (P->expm_scratch_elems >= elems) return PHIKS_OK;
+  if (P->expm_scratch) {
+    CK(cudaDeviceSynchronize());
+    cudaFree(P->expm_scratch);
+  }
+  P->expm_scratch = nullptr;
+  P->expm_scratch_elems = 0;
+  CK(cudaMalloc(&P->expm_scratch, elems * 8));
+  P->expm_scratch_elems = elems;
+  return PHIKS_OK;
+}
+
+constexpr size_t kMaxBanks = 8;
+
+phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool no_cache,
+                      cudaStream_t st, Bank** out) {
+  P->clock++;
+  Bank* hit = nullptr;
+  for (auto& b : P->banks)
+    if (b.tau == tau && b.s == s && b.q == q && b.rule == rule) hit = &b;
+  if (hit && !no_cache) {
+    hit->stamp = P->clock;
+    *out = hit;
+    return PHIKS_OK;
+  }
+  Bank nb;
+  nb.tau = tau;
+  nb.s = s;
+  nb.q = q;
+  nb.rule = rule;
+  quad_rule(rule, q, nb.theta, nb.w);
+  std::vector<double> bank_theta;
+  for (int i = 0; i < q; ++i) {
+    if (nb.theta[i] == 1.0) {
+      nb.node_bank.push_back(-1);
+    } else {
+      nb.node_bank.push_back((int)bank_theta.size());
+      if (nb.theta[i] == 0.0) nb.b0 = (int)bank_theta.size();
+      bank_theta.push_back(nb.theta[i]);
+    }
+  }
+  if (nb.b0 < 0) {
+    nb.b0 = (int)bank_theta.size();
+    bank_theta.push_back(0.0);
+  }
+  const int nbk = (int)bank_theta.size();
+  nb.off.assign(nbk, std::vector<size_t>(P->d));
+  size_t tot = 0;
+  for (int b = 0; b < nbk; ++b)
+    for (int mu = 0; mu < P->d; ++mu) {
+      nb.off[b][mu] = tot;
+      tot += (size_t)P->n[mu] * P->n[mu];
+    }
+  if (hit) {
+    nb.dev = hit->dev;  // recompute in place (same layout: same q and rule)
+  } else {
+    if (P->banks.size() >= kMaxBanks) {  // evict the least recently used bank
+      auto lru = std::min_element(P->banks.begin(), P->banks.end(),
+                                  [](const Bank& x, const Bank& y) { return x.stamp < y.stamp; });
+      CK(cudaStreamSynchronize(st));
+      cudaFree(lru->dev);
+      P->banks.erase(lru);
+    }
+    CK(cudaMalloc(&nb.dev, tot * 8));
+  }
+  phiks_status es = ensure_expm_scratch(P, 3 * tot);
+  if (es != PHIKS_OK) {
+    if (!hit) cudaFree(nb.dev);
+    return es;
+  }
+  std::vector<ExpmJob> jobs;
+  const double scale = std::ldexp(tau, -s);
+  for (int b = 0; b < nbk; ++b)
+    for (int mu = 0; mu < P->d; ++mu) {
+      ExpmJob j;
+      j.n = (int)P->n[mu];
+      j.Ashift = P->dAs + P->offA[mu];
+      j.c = (1.0 - bank_theta[b]) * scale;
+      j.norm1 = P->norm1_shifted[mu];
+      j.esig = std::exp(j.c * P->sigma[mu]);
+      j.out = nb.dev + nb.off[b][mu];
+      jobs.push_back(j);
+    }
+  phiks_status stt = run_expm_jobs(P, jobs, P->expm_scratch, st);
+  if (stt != PHIKS_OK) {
+    if (!hit) cudaFree(nb.dev);
+    return stt;
+  }
+  nb.stamp = P->clock;
+  if (hit) {
+    *hit = nb;
+    *out = hit;
+  } else {
+    P->banks.push_back(nb);
+    *out = &P->banks.back();
+  }
+  return PHIKS_OK;
+}
+
+// ---- Tucker operator ---------------------------------------------------------
+struct Ctx {
+  phiks_plan_s* P;
+  cudaStream_t st;
+  double* tmp[2];
+  int tuckers = 0;
+};
+
+// W = (input combination) x_1 L_1 ... x_d L_d, last mode through `epi`
+// (plain store into W when epi is null).
+phiks_status tucker(Ctx& c, const Combo& in, const double* const* L, double* W, const Epi* epi) {
+  phiks_plan_s* P = c.P;
+  Combo cur = in;
+  for (int mu = 0; mu < P->d; ++mu) {
+    const bool last = (mu == P->d - 1);
+    double* out = last ? W : c.tmp[mu & 1];
+    ModeGeom g{mode_a(P, mu), (int)P->n[mu], mode_b(P, mu)};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (P->prof) {
+      while (P->ev_pool.size() < P->ev_used + 2) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        P->ev_pool.push_back(e);
+      }
+      e0 = P->ev_pool[P->ev_used++];
+      e1 = P->ev_pool[P->ev_used++];
+      CK(cudaEventRecord(e0, c.st));
+    }
+    if (P->dtype == PHIKS_FP64) {
+      CK(launch_mode_product_f64(cur, L[mu], g, out, last ? epi : nullptr, c.st));
+    } else {
+      CK(tc_mode_product(P->tc, P->dtype, cur, L[mu], g, out, last ? epi : nullptr, c.st));
+    }
+    if (P->prof) {
+      CK(cudaEventRecord(e1, c.st));
+      P->prof_flops += 2.0 * (double)P->N * (double)P->n[mu];
+    }
+    cur = make_combo();
+    cur.nsrc = 1;
+    cur.src[0] = out;
+    cur.coef[0] = 1.0;
+    cur.f32mask = P->dtype == PHIKS_FP64 ? 0 : 1;  // split path keeps float temporaries
+  }
+  c.tuckers++;
+  return PHIKS_OK;
+}
+
+Combo plain(const void* x, bool f32) {
+  Combo c = make_combo();
+  c.f32mask = f32 ? 1 : 0;
+  c.nsrc = 1;
+  c.src[0] = (const double*)x;
+  c.coef[0] = 1.0;
+  return c;
+}
+
+void bank_ptrs(const phiks_plan_s* P, const Bank* B, int b, const double** L) {
+  for (int mu = 0; mu < P->d; ++mu) L[mu] = B->dev + B->off[b][mu];
+}
+
+// Squaring chain: M <- M^2 for every mode.
+phiks_status square_modes(Ctx& c, const double** M, int& cur_buf) {
+  phiks_plan_s* P = c.P;
+  GemmBatch gb;
+  gb.count = P->d;
+  size_t off = 0;
+  for (int mu = 0; mu < P->d; ++mu) {
+    gb.n[mu] = (int)P->n[mu];
+    gb.A[mu] = M[mu];
+    gb.B[mu] = M[mu];
+    gb.C[mu] = P->msq[cur_buf] + off;
+    gb.alpha[mu] = 1.0;
+    gb.beta_I[mu] = 0.0;
+    off += (size_t)P->n[mu] * P->n[mu];
+  }
+  CK(launch_gemm_batch_f64(gb, P->nmax, c.st));
+  off = 0;
+  for (int mu = 0; mu < P->d; ++mu) {
+    M[mu] = P->msq[cur_buf] + off;
+    off += (size_t)P->n[mu] * P->n[mu];
+  }
+  cur_buf = 1 - cur_buf;
+  return PHIKS_OK;
+}
+
+phiks_status copy_elems(Ctx& c, void* dst, const void* src) {
+  CK(cudaMemcpyAsync(dst, src, (size_t)c.P->N * elt_size(c.P), cudaMemcpyDeviceToDevice, c.st));
+  return PHIKS_OK;
+}
+
+phiks_status combine(Ctx& c, const Epi& e) {
+  CK(launch_combine(e, c.P->N, c.st));
+  return PHIKS_OK;
+}
+
+// dst (plan element type) <- acc (double)
+phiks_status store_acc(Ctx& c, void* dst, const double* acc) {
+  if (c.P->dtype == PHIKS_FP64) return copy_elems(c, dst, acc);
+  Epi e = make_epi();
+  e.nout = 1;
+  e.nsrc = 1;
+  e.out[0] = (double*)dst;
+  e.out_f32mask = 1;
+  e.src[0] = acc;
+  e.a[0][0] = 1.0;
+  return combine(c, e);
+}
+
+// ---- same vector: eq. (integrandsimul), eq. (simul) -----------------------
+// acc[l-1] holds phi_l(K/2^j) v (FP64) for the current level j.
+phiks_status run_same(Ctx& c, const Bank* B, int s, int p, const void* v, const phiks_options& o,
+                      double** acc, void* out) {
+  phiks_plan_s* P = c.P;
+  const int64_t N = P->N;
+  const size_t es = elt_size(P);
+  const bool f32 = P->dtype != PHIKS_FP64;
+  const int per = p + (o.skip_phi0 ? 0 : 1);
+  const int q = (int)B->theta.size();
+  for (int l = 0; l < p; ++l) CK(cudaMemsetAsync(acc[l], 0, N * 8, c.st));
+  // quadrature at K/2^s: phi_l += w_i theta_i^(l-1)/(l-1)! exp((1-theta_i)K/2^s) v
+  for (int i = 0; i < q && p > 0; ++i) {
+    const double th = B->theta[i], w = B->w[i];
+    Epi e = make_epi();
+    e.nout = p;
+    e.nsrc = p;
+    for (int t = 0; t < p; ++t) {
+      e.out[t] = acc[t];
+      e.src[t] = acc[t];
+      e.a[t][t] = 1.0;
+      e.b[t] = w * std::pow(th, t) / factorial(t);
+    }
+    if (B->node_bank[i] < 0) {  // theta = 1: exp(0) = I, no Tucker
+      Epi f = e;
+      f.nsrc = p + 1;
+      f.src[p] = (const double*)v;
+      f.src_f32mask = f32 ? (1 << p) : 0;
+      for (int t = 0; t < p; ++t) f.a[t][p] = e.b[t];
+      TRY(combine(c, f));
+      continue;
+    }
+    const double* L[PHIKS_MAX_D];
+    bank_ptrs(P, B, B->node_bank[i], L);
+    TRY(tucker(c, plain(v, f32), L, nullptr, &e));
+  }
+  const double* M[PHIKS_MAX_D];
+  bank_ptrs(P, B, B->b0, M);
+  int mbuf = 0;
+  auto emit = [&](int Lv) -> phiks_status {
+    char* blk = (char*)out + (size_t)Lv * per * N * es;
+    int slot = 0;
+    if (!o.skip_phi0) {
+      Epi e = make_epi();  // phi_0 = exp(K/2^Lv) v
+      e.nout = 1;
+      e.out[0] = (double*)blk;
+      e.out_f32mask = f32 ? 1 : 0;
+      e.b[0] = 1.0;
+      TRY(tucker(c, plain(v, f32), M, nullptr, &e));
+      slot = 1;
+    }
+    for (int l = 0; l < p; ++l) TRY(store_acc(c, blk + (size_t)(slot + l) * N * es, acc[l]));
+    return PHIKS_OK;
+  };
+  if (s < o.nscales) TRY(emit(s));
+  for (int j = s; j >= 1; --j) {
+    // eq. (simul): phi_l(K/2^(j-1)) v = 2^-l (exp(K/2^j) phi_l + sum_k phi_k/(l-k)!), l = p..1
+    for (int l = p; l >= 1; --l) {
+      Epi e = make_epi();
+      e.nout = 1;
+      e.nsrc = l;
+      e.out[0] = acc[l - 1];
+      e.b[0] = std::ldexp(1.0, -l);
+      for (int k = 1; k <= l; ++k) {
+        e.src[k - 1] = acc[k - 1];
+        e.a[0][k - 1] = std::ldexp(1.0, -l) / factorial(l - k);
+      }
+      TRY(tucker(c, plain(acc[l - 1], false), M, nullptr, &e));
+    }
+    TRY(square_modes(c, M, mbuf));
+    if (j - 1 < o.nscales) TRY(emit(j - 1));
+  }
+  return PHIKS_OK;
+}
+
+// ---- linear combination: eq. (integrandcomb), eq. (comb) ------------------
+// acc[l-1] holds Phi_j(K) v_{p-l+1..p} (FP64) for the current level j.
+phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const* v,
+                         const phiks_options& o, double** acc, void* out) {
+  phiks_plan_s* P = c.P;
+  const int64_t N = P->N;
+  const size_t es = elt_size(P);
+  const bool f32 = P->dtype != PHIKS_FP64;
+  const int q = (int)B->theta.size();
+  for (int l = 0; l < p; ++l) CK(cudaMemsetAsync(acc[l], 0, N * 8, c.st));
+  for (int i = 0; i < q; ++i) {
+    const double th = B->theta[i], w = B->w[i];
+    for (int l = 1; l <= p; ++l) {
+      // input: sum_{k=1}^{l} theta^(l-k)/(l-k)! v_{p+1-k} / 2^((l-k+1) s)
+      Combo in = make_combo();
+      for (int k = 1; k <= l; ++k) {
+        const void* vk = v[p + 1 - k];
+        if (!vk) continue;
+        in.src[in.nsrc] = (const double*)vk;
+        in.coef[in.nsrc] = std::pow(th, l - k) / factorial(l - k) * std::ldexp(1.0, -(l - k + 1) * s);
+        if (f32) in.f32mask |= 1 << in.nsrc;
+        in.nsrc++;
+      }
+      if (in.nsrc == 0) continue;
+      if (B->node_bank[i] < 0) {  // theta = 1: acc_l += w * input
+        Epi f = make_epi();
+        f.nout = 1;
+        f.nsrc = in.nsrc + 1;
+        f.out[0] = acc[l - 1];
+        f.src[0] = acc[l - 1];
+        f.a[0][0] = 1.0;
+        for (int m = 0; m < in.nsrc; ++m) {
+          f.src[m + 1] = in.src[m];
+          f.a[0][m + 1] = w * in.coef[m];
+        }
+        f.src_f32mask = in.f32mask << 1;
+        TRY(combine(c, f));
+        continue;
+      }
+      Epi e = make_epi();
+      e.nout = 1;
+      e.nsrc = 1;
+      e.out[0] = acc[l - 1];
+      e.src[0] = acc[l - 1];
+      e.a[0][0] = 1.0;
+      e.b[0] = w;
+      const double* L[PHIKS_MAX_D];
+      bank_ptrs(P, B, B->node_bank[i], L);
+      TRY(tucker(c, in, L, nullptr, &e));
+    }
+  }
+  const double* M[PHIKS_MAX_D];
+  bank_ptrs(P, B, B->b0, M);
+  int mbuf = 0;
+  auto emit = [&](int Lv) -> phiks_status {
+    char* blk = (char*)out + (size_t)Lv * N * es;
+    if (v[0]) {  // exp(K/2^Lv) v_0 + Phi_Lv v_{1..p}
+      Epi e = make_epi();
+      e.nout = 1;
+      e.out[0] = (double*)blk;
+      e.out_f32mask = f32 ? 1 : 0;
+      e.b[0] = 1.0;
+      if (p > 0) {
+        e.nsrc = 1;
+        e.src[0] = acc[p - 1];
+        e.a[0][0] = 1.0;
+      }
+      TRY(tucker(c, plain(v[0], f32), M, nullptr, &e));
+    } else if (p > 0) {
+      TRY(store_acc(c, blk, acc[p - 1]));
+    } else {
+      CK(cudaMemsetAsync(blk, 0, N * es, c.st));
+    }
+    return PHIKS_OK;
+  };
+  if (s < o.nscales) TRY(emit(s));
+  for (int j = s; j >= 1; --j) {
+    // eq. (comb), l = p..1
+    for (int l = p; l >= 1; --l) {
+      Epi e = make_epi();
+      e.nout = 1;
+      e.nsrc = l;
+      e.out[0] = acc[l - 1];
+      e.b[0] = 1.0;
+      for (int k = 1; k <= l; ++k) {
+        e.src[k - 1] = acc[k - 1];
+        e.a[0][k - 1] = 1.0 / (factorial(l - k) * std::ldexp(1.0, (l - k) * j));
+      }
+      TRY(tucker(c, plain(acc[l - 1], false), M, nullptr, &e));
+    }
+    TRY(square_modes(c, M, mbuf));
+    if (j - 1 < o.nscales) TRY(emit(j - 1));
+  }
+  return PHIKS_OK;
+}
+
+phiks_status check_opts(const phiks_options& o) {
+  if (o.nscales < 1 || o.nscales > 64) return fail(PHIKS_ERR_INVALID, "nscales %d", o.nscales);
+  if (o.rule != PHIKS_RULE_GLL && o.rule != PHIKS_RULE_GL)
+    return fail(PHIKS_ERR_INVALID, "rule %d", o.rule);
+  const int qlo = o.rule == PHIKS_RULE_GLL ? 2 : 1;
+  if (o.qmin < qlo || o.qmax < o.qmin || o.qmax > 64)
+    return fail(PHIKS_ERR_INVALID, "q range [%d, %d]", o.qmin, o.qmax);
+  if (!(o.tol > 0)) return fail(PHIKS_ERR_INVALID, "tol %g", o.tol);
+  if ((o.force_s >= 0) != (o.force_q >= 0))
+    return fail(PHIKS_ERR_INVALID, "force_s and force_q go together");
+  if (o.force_q >= 0 && (o.force_q < qlo || o.force_q > 64 || o.force_s > 64))
+    return fail(PHIKS_ERR_INVALID, "forced (s, q) = (%d, %d)", o.force_s, o.force_q);
+  return PHIKS_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+void phiks_options_init(phiks_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof *opt);
+  opt->tol = std::ldexp(1.0, -53);
+  opt->nscales = 1;
+  opt->rule = PHIKS_RULE_GLL;
+  opt->qmin = 3;
+  opt->qmax = 12;
+  opt->force_s = -1;
+  opt->force_q = -1;
+}
+
+const char* phiks_last_error(void) { return g_err.c_str(); }
+
+phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dtype,
+                        phiks_plan_t* out) {
+  g_err.clear();
+  if (!out) return fail(PHIKS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (d < 1 || d > PHIKS_MAX_D) return fail(PHIKS_ERR_INVALID, "d = %d out of [1, %d]", d, PHIKS_MAX_D);
+  if (!n || !A) return fail(PHIKS_ERR_INVALID, "n or A is NULL");
+  if (dtype < PHIKS_FP64 || dtype > PHIKS_BF16X3) return fail(PHIKS_ERR_INVALID, "dtype %d", dtype);
+  std::unique_ptr<phiks_plan_s> P(new phiks_plan_s);
+  P->d = d;
+  P->dtype = dtype;
+  P->N = 1;
+  for (int mu = 0; mu < d; ++mu) {
+    if (n[mu] < 1 || n[mu] > 65536) return fail(PHIKS_ERR_INVALID, "n[%d] = %lld", mu, (long long)n[mu]);
+    if (!A[mu]) return fail(PHIKS_ERR_INVALID, "A[%d] is NULL", mu);
+    P->n[mu] = n[mu];
+    if (P->N > (int64_t(1) << 40) / n[mu]) return fail(PHIKS_ERR_INVALID, "N too large");
+    P->N *= n[mu];
+    P->nmax = std::max<int>(P->nmax, (int)n[mu]);
+  }
+  CK(cudaGetDevice(&P->device));
+  size_t tot = 0;
+  for (int mu = 0; mu < d; ++mu) {
+    const int64_t m = n[mu];
+    std::vector<double> a(A[mu], A[mu] + m * m);
+    for (double x : a)
+      if (!std::isfinite(x)) return fail(PHIKS_ERR_INVALID, "A[%d] has a non-finite entry", mu);
+    double tr = 0;
+    for (int64_t i = 0; i < m; ++i) tr += a[i + m * i];
+    P->sigma[mu] = tr / m;  // Remark of Sec. 3.1: sigma_mu = tr(A_mu)/n_mu
+    P->rect[mu] = numerical_range_rect(a.data(), m);
+    std::vector<double> sh(a);
+    for (int64_t i = 0; i < m; ++i) sh[i + m * i] -= P->sigma[mu];
+    P->norm1_shifted[mu] = norm1(sh.data(), m);
+    P->A.push_back(a);
+    P->offA[mu] = tot;
+    tot += (size_t)m * m;
+  }
+  P->sum_n2 = tot;
+  CK(cudaMalloc(&P->dAs, tot * 8));
+  for (int mu = 0; mu < d; ++mu) {
+    const int64_t m = n[mu];
+    std::vector<double> sh(P->A[mu]);
+    for (int64_t i = 0; i < m; ++i) sh[i + m * i] -= P->sigma[mu];
+    CK(cudaMemcpy(P->dAs + P->offA[mu], sh.data(), m * m * 8, cudaMemcpyHostToDevice));
+  }
+  CK(cudaMalloc(&P->msq[0], tot * 8));
+  CK(cudaMalloc(&P->msq[1], tot * 8));
+  CK(cudaMalloc(&P->d_norms, (PHIKS_MAX_P + 1) * 8));
+  CK(cudaMallocHost(&P->h_norms, (PHIKS_MAX_P + 1) * 8));
+  if (dtype != PHIKS_FP64) {
+    phiks_status st = tc_create(&P->tc, d, P->n, P->N);
+    if (st != PHIKS_OK) return fail(st, "%s", tc_last_error());
+  }
+  *out = P.release();
+  return PHIKS_OK;
+}
+
+phiks_status phiks_profile_enable(phiks_plan_t P, int enable) {
+  if (!P) return fail(PHIKS_ERR_INVALID, "NULL plan");
+  P->prof = enable != 0;
+  return PHIKS_OK;
+}
+
+phiks_status phiks_profile_read(phiks_plan_t P, double* ms, int64_t* launches, double* flops) {
+  if (!P) return fail(PHIKS_ERR_INVALID, "NULL plan");
+  DeviceGuard g(P->device);
+  CK(cudaDeviceSynchronize());
+  double tot = 0;
+  for (size_t i = 0; i + 1 < P->ev_used; i += 2) {
+    float m = 0;
+    CK(cudaEventElapsedTime(&m, P->ev_pool[i], P->ev_pool[i + 1]));
+    tot += m;
+  }
+  if (ms) *ms = tot;
+  if (launches) *launches = (int64_t)(P->ev_used / 2);
+  if (flops) *flops = P->prof_flops;
+  P->ev_used = 0;
+  P->prof_flops = 0;
+  return PHIKS_OK;
+}
+
+uint64_t phiks_kernel_launches(void) { return phiks::kernel_launch_count(); }
+
+void phiks_destroy(phiks_plan_t P) {
+  if (!P) return;
+  DeviceGuard g(P->device);
+  cudaDeviceSynchronize();
+  for (auto e : P->ev_pool) cudaEventDestroy(e);
+  for (auto& b : P->banks) cudaFree(b.dev);
+  cudaFree(P->dAs);
+  cudaFree(P->expm_scratch);
+  cudaFree(P->msq[0]);
+  cudaFree(P->msq[1]);
+  cudaFree(P->ws);
+  cudaFree(P->d_norms);
+  cudaFreeHost(P->h_norms);
+  if (P->tc) tc_destroy(P->tc);
+  delete P;
+}
+
+phiks_status phiks_workspace_size(phiks_plan_t P, int p, int nv, int nscales, size_t* bytes) {
+  g_err.clear();
+  if (!P || !bytes) return fail(PHIKS_ERR_INVALID, "NULL argument");
+  if (p < 0 || p > PHIKS_MAX_P) return fail(PHIKS_ERR_INVALID, "p = %d", p);
+  if (nv != 1 && nv != p + 1) return fail(PHIKS_ERR_INVALID, "nv must be 1 or p + 1");
+  (void)nscales;
+  *bytes = workspace_bytes(P, p);
+  return PHIKS_OK;
+}
+
+phiks_status phiks_select_params(phiks_plan_t P, double tau, int p, int nv, const double* vnorms,
+                                 const phiks_options* opt, int* s, int* q, int* tcount) {
+  g_err.clear();
+  if (!P || !vnorms) return fail(PHIKS_ERR_INVALID, "NULL argument");
+  phiks_options o;
+  if (opt) o = *opt; else phiks_options_init(&o);
+  TRY(check_opts(o));
+  if (p < 1 || p > PHIKS_MAX_P) return fail(PHIKS_ERR_INVALID, "p = %d", p);
+  if (nv != 1 && nv != p + 1) return fail(PHIKS_ERR_INVALID, "nv must be 1 or p + 1");
+  const int kind = nv == 1 ? 0 : 1;
+  Selection sel;
+  Rect xi = tau_rect(P, tau);
+  if (!select_params(xi, p, kind, vnorms, o.nscales, o.tol, o.qmin, o.qmax, o.rule, &sel))
+    return fail(PHIKS_ERR_NO_PARAMS, "no (s, q) meets the tolerance");
+  if (s) *s = sel.s;
+  if (q) *q = sel.q;
+  if (tcount) *tcount = sel.tcount;
+  return PHIKS_OK;
+}
+
+phiks_status phiks_choose_params(int d, const int64_t* n, const double* const* A, double tau,
+                                 int p, int nv, const double* vnorms, const phiks_options* opt,
+                                 int* s, int* q, int* tcount) {
+  g_err.clear();
+  if (d < 1 || d > PHIKS_MAX_D || !n || !A || !vnorms) return fail(PHIKS_ERR_INVALID, "bad argument");
+  phiks_options o;
+  if (opt) o = *opt; else phiks_options_init(&o);
+  TRY(check_opts(o));
+  if (p < 1 || p > PHIKS_MAX_P) return fail(PHIKS_ERR_INVALID, "p = %d", p);
+  if (nv != 1 && nv != p + 1) return fail(PHIKS_ERR_INVALID, "nv must be 1 or p + 1");
+  Rect r;
+  for (int mu = 0; mu < d; ++mu) {
+    if (n[mu] < 1 || !A[mu]) return fail(PHIKS_ERR_INVALID, "operator %d", mu);
+    Rect m = numerical_range_rect(A[mu], n[mu]);
+    r.xlo += m.xlo; r.xhi += m.xhi; r.ylo += m.ylo; r.yhi += m.yhi;
+  }
+  Rect xi;
+  if (tau >= 0) {
+    xi.xlo = tau * r.xlo; xi.xhi = tau * r.xhi; xi.ylo = tau * r.ylo; xi.yhi = tau * r.yhi;
+  } else {
+    xi.xlo = tau * r.xhi; xi.xhi = tau * r.xlo; xi.ylo = tau * r.yhi; xi.yhi = tau * r.ylo;
+  }
+  Selection sel;
+  if (!select_params(xi, p, nv == 1 ? 0 : 1, vnorms, o.nscales, o.tol, o.qmin, o.qmax, o.rule, &sel))
+    return fail(PHIKS_ERR_NO_PARAMS, "no (s, q) meets the tolerance");
+  if (s) *s = sel.s;
+  if (q) *q = sel.q;
+  if (tcount) *tcount = sel.tcount;
+  return PHIKS_OK;
+}
+
+phiks_status phiks_last_params(phiks_plan_t P, int* s, int* q, int* tcount, int* tuckers) {
+  if (!P) return fail(PHIKS_ERR_INVALID, "NULL plan");
+  if (s) *s = P->last_s;
+  if (q) *q = P->last_q;
+  if (tcount) *tcount = P->last_T;
+  if (tuckers) *tuckers = P->last_tuckers;
+  return PHIKS_OK;
+}
+
+phiks_status phiks_apply(phiks_plan_t P, double tau, int p, const void* const* v, int nv,
+                         void* out, void* stream) {
+  phiks_options o;
+  phiks_options_init(&o);
+  return phiks_apply_ex(P, tau, p, v, nv, &o, out, stream);
+}
+
+phiks_status phiks_apply_ex(phiks_plan_t P, double tau, int p, const void* const* v, int nv,
+                            const phiks_options* opt, void* out, void* stream) {
+  g_err.clear();
+  if (!P || !v || !out) return fail(PHIKS_ERR_INVALID, "NULL argument");
+  if (!std::isfinite(tau)) return fail(PHIKS_ERR_INVALID, "tau is not finite");
+  if (p < 0 || p > PHIKS_MAX_P) return fail(PHIKS_ERR_INVALID, "p = %d out of [0, %d]", p, PHIKS_MAX_P);
+  if (nv != 1 && nv != p + 1) return fail(PHIKS_ERR_INVALID, "nv = %d must be 1 or p + 1", nv);
+  phiks_options o;
+  if (opt) o = *opt; else phiks_options_init(&o);
+  TRY(check_opts(o));
+  const int kind = nv == 1 ? 0 : 1;  // nv == p + 1 with p == 0 is the exponential alone
+  if (kind == 0 && !v[0]) return fail(PHIKS_ERR_INVALID, "v[0] is NULL");
+  if (kind == 0 && p == 0 && o.skip_phi0) return fail(PHIKS_ERR_INVALID, "nothing to compute");
+  DeviceGuard g(P->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t N = P->N;
+  const size_t es = elt_size(P);
+
+  // vector norms (Sec. 3.3 uses ||v_l||_2)
+  double norms[PHIKS_MAX_P + 1] = {0};
+  if (o.vnorms) {
+    for (int i = 0; i < nv; ++i) norms[i] = o.vnorms[i];
+  } else {
+    const void* xs[PHIKS_MAX_P + 1];
+    int idx[PHIKS_MAX_P + 1], cnt = 0;
+    for (int i = 0; i < nv; ++i)
+      if (v[i]) {
+        idx[cnt] = i;
+        xs[cnt++] = v[i];
+      }
+    if (cnt) {
+      CK(cudaMemsetAsync(P->d_norms, 0, cnt * 8, st));
+      CK(launch_sumsq(xs, cnt, N, P->dtype != PHIKS_FP64, P->d_norms, st));
+      CK(cudaMemcpyAsync(P->h_norms, P->d_norms, cnt * 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int k = 0; k < cnt; ++k) norms[idx[k]] = std::sqrt(P->h_norms[k]);
+    }
+  }
+
+  // (s, q) of Sec. 3.3
+  int s, q, T;
+  if (p == 0) {
+    s = o.nscales - 1;  // exponential only: no quadrature
+    q = (o.rule == PHIKS_RULE_GLL) ? 2 : 1;
+    T = o.nscales;
+  } else if (o.force_s >= 0) {
+    s = std::max(o.force_s, o.nscales - 1);
+    q = o.force_q;
+    T = tucker_count(kind, s, o.nscales, q, p);
+  } else {
+    Selection sel;
+    TRY(select_cached(P, tau, p, kind, norms, nv, o, &sel));
+    s = sel.s;
+    q = sel.q;
+    T = sel.tcount;
+  }
+  // workspace
+  const size_t need = workspace_bytes(P, p);
+  char* ws = (char*)o.workspace;
+  if (ws) {
+    if (o.workspace_bytes < need)
+      return fail(PHIKS_ERR_INVALID, "workspace of %zu bytes, need %zu", o.workspace_bytes, need);
+  } else {
+    if (P->ws_bytes < need) {
+      if (P->ws) {
+        CK(cudaStreamSynchronize(st));
+        cudaFree(P->ws);
+      }
+      P->ws = nullptr;
+      P->ws_bytes = 0;
+      CK(cudaMalloc(&P->ws, need));
+      P->ws_bytes = need;
+    }
+    ws = (char*)P->ws;
+  }
+  double* acc[PHIKS_MAX_P];
+  for (int l = 0; l < std::max(p, 1); ++l) acc[l] = (double*)(ws + (size_t)l * N * 8);
+  Ctx c{P, st, {nullptr, nullptr}, 0};
+  c.tmp[0] = (double*)(ws + (size_t)std::max(p, 1) * N * 8);
+  c.tmp[1] = c.tmp[0] + N;
+  if (P->dtype != PHIKS_FP64) tc_bind_workspace(P->tc, ws + (size_t)(std::max(p, 1) + 2) * N * 8);
+
+  Bank* B = nullptr;
+  TRY(get_bank(P, tau, s, q, o.rule, o.no_cache != 0, st, &B));
+  if (kind == 0) {
+    TRY(run_same(c, B, s, p, v[0], o, acc, out));
+  } else {
+    TRY(run_lincomb(c, B, s, p, v, o, acc, out));
+  }
+  CK(cudaGetLastError());
+  P->last_s = s;
+  P->last_q = q;
+  P->last_T = T;
+  P->last_tuckers = c.tuckers;
+  (void)es;
+  return PHIKS_OK;
+}
+
+phiks_status phiks_tucker(phiks_plan_t P, const void* V, void* W, const double* const* L,
+                          void* stream) {
+  g_err.clear();
+  if (!P || !V || !W || !L) return fail(PHIKS_ERR_INVALID, "NULL argument");
+  if (V == W) return fail(PHIKS_ERR_INVALID, "V and W alias");
+  for (int mu = 0; mu < P->d; ++mu)
+    if (!L[mu]) return fail(PHIKS_ERR_INVALID, "L[%d] is NULL", mu);
+  DeviceGuard g(P->device);
+  const size_t need = workspace_bytes(P, 1);
+  if (P->ws_bytes < need) {
+    if (P->ws) {
+      CK(cudaDeviceSynchronize());
+      cudaFree(P->ws);
+    }
+    P->ws = nullptr;
+    P->ws_bytes = 0;
+    CK(cudaMalloc(&P->ws, need));
+    P->ws_bytes = need;
+  }
+  const int64_t N = P->N;
+  Ctx c{P, (cudaStream_t)stream, {nullptr, nullptr}, 0};
+  c.tmp[0] = (double*)((char*)P->ws + (size_t)N * 8);
+  c.tmp[1] = c.tmp[0] + N;
+  if (P->dtype != PHIKS_FP64) tc_bind_workspace(P->tc, (char*)P->ws + 3 * (size_t)N * 8);
+  const bool f32 = P->dtype != PHIKS_FP64;
+  Epi e = make_epi();
+  e.nout = 1;
+  e.out[0] = (double*)W;
+  e.out_f32mask = f32 ? 1 : 0;
+  e.b[0] = 1.0;
+  return tucker(c, plain(V, f32), L, nullptr, &e);
+}
+
+phiks_status phiks_expm(int batch, int n, const double* X, double* E, void* stream) {
+  g_err.clear();
+  if (batch < 0 || n < 1 || n > 65536) return fail(PHIKS_ERR_INVALID, "batch %d, n %d", batch, n);
+  if (batch == 0) return PHIKS_OK;
+  if (!X || !E || X == E) return fail(PHIKS_ERR_INVALID, "NULL or aliasing X / E");
+  cudaStream_t st = (cudaStream_t)stream;
+  // ||X_b||_1 on the host would need a copy; use the device matrices through a
+  // norm-free schedule instead: a small host copy of each matrix.
+  std::vector<double> h((size_t)batch * n * n);
+  CK(cudaMemcpyAsync(h.data(), X, h.size() * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<ExpmJob> jobs(batch);
+  for (int b = 0; b < batch; ++b) {
+    jobs[b].n = n;
+    jobs[b].Ashift = X + (size_t)b * n * n;
+    jobs[b].c = 1.0;
+    jobs[b].norm1 = norm1(h.data() + (size_t)b * n * n, n);
+    jobs[b].esig = 1.0;
+    jobs[b].out = E + (size_t)b * n * n;
+  }
+  double* scratch = nullptr;
+  CK(cudaMallocAsync((void**)&scratch, 3 * h.size() * 8, st));
+  phiks_plan_s dummy;
+  phiks_status r = run_expm_jobs(&dummy, jobs, scratch, st);
+  cudaFreeAsync(scratch, st);
+  return r;
+}
+
+}  // extern "C"

@@ -1,0 +1,217 @@
+// FP64 mu-mode product (Sec. 2): W = V x_mu L, with a fused input combination
+// (prologue, eq. integrandcomb) and a fused multi-output linear epilogue (the
+// quadrature accumulation of eq. integrandsimul / eq. integrandcomb and the
+// doubling combinations of eq. simul / eq. comb).
+//
+// On GB300 the FP64 pipe retires about 2 DFMA per clock per SM (1.19 TFLOP/s
+// measured over 152 SMs), two orders of magnitude below the shared-memory and
+// L2 bandwidth such a kernel needs, so the design goal is only to keep every
+// SM's DFMA pipe fed: many resident warps, independent accumulators per
+// thread, and as few FP64 instructions outside the contraction as possible.
+//
+// The tensor is viewed as (a, n, b) with element (x, j, y) at x + a j + a n y;
+// a CTA computes a TI x TC tile of outputs (rows i of L, "columns" c = x + a y)
+// by staging KC-deep slices of L and of the fibres V(x, :, y) in shared memory.
+#include <atomic>
+
+#include "kernels.cuh"
+
+namespace phiks {
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+}
+uint64_t kernel_launch_count() { return g_launches.load(); }
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+constexpr int TI = 32, TC = 64, KC = 16, NT = 256;
+constexpr int RI = 2, RC = 4;          // per-thread micro tile
+constexpr int TROWS = TI / RI;         // 16 thread rows
+constexpr int TCOLS = TC / RC;         // 16 thread columns
+static_assert(TROWS * TCOLS == NT, "thread layout");
+
+__device__ __forceinline__ double load_combo(const Combo& pro, int64_t idx, bool plain) {
+  if (plain) return __ldg(pro.src[0] + idx);
+  double v = pro.coef[0] * __ldg(pro.src[0] + idx);
+  for (int m = 1; m < pro.nsrc; ++m) v = fma(pro.coef[m], __ldg(pro.src[m] + idx), v);
+  return v;
+}
+
+__device__ __forceinline__ void store_epi(const Epi& epi, double* W, int64_t idx, double res) {
+  if (epi.nout == 0) {
+    W[idx] = res;
+    return;
+  }
+  double sv[kMaxSrc];
+  for (int m = 0; m < epi.nsrc; ++m) sv[m] = epi.src[m][idx];
+  for (int t = 0; t < epi.nout; ++t) {
+    double o = epi.b[t] * res;
+    for (int m = 0; m < epi.nsrc; ++m)
+      if (epi.a[t][m] != 0.0) o = fma(epi.a[t][m], sv[m], o);
+    epi.out[t][idx] = o;
+  }
+}
+
+template <bool XFAST>
+__global__ void __launch_bounds__(NT) mode_product_f64_kernel(Combo pro, const double* __restrict__ L,
+                                                              ModeGeom g, double* W, Epi epi) {
+  __shared__ double sL[KC][TI + 1];
+  __shared__ double sV[KC][TC + 1];
+  const int tid = threadIdx.x;
+  const int tc = tid % TCOLS;
+  const int ti = tid / TCOLS;
+  const int i0 = blockIdx.y * TI;
+  const int64_t c0 = (int64_t)blockIdx.x * TC;
+  const int64_t ncols = g.a * g.b;
+  const int n = g.n;
+  const int64_t an = g.a * (int64_t)n;
+  const bool plain = (pro.nsrc == 1 && pro.coef[0] == 1.0);
+
+  double acc[RI][RC];
+#pragma unroll
+  for (int r = 0; r < RI; ++r)
+#pragma unroll
+    for (int c = 0; c < RC; ++c) acc[r][c] = 0.0;
+
+  for (int k0 = 0; k0 < n; k0 += KC) {
+    for (int e = tid; e < TI * KC; e += NT) {
+      const int ii = e % TI, kk = e / TI;
+      const int i = i0 + ii, k = k0 + kk;
+      sL[kk][ii] = (i < n && k < n) ? __ldg(L + i + (int64_t)n * k) : 0.0;
+    }
+    for (int e = tid; e < TC * KC; e += NT) {
+      int cc, kk;
+      if (XFAST) {
+        cc = e % TC;
+        kk = e / TC;
+      } else {
+        kk = e % KC;
+        cc = e / KC;
+      }
+      const int64_t c = c0 + cc;
+      const int k = k0 + kk;
+      double val = 0.0;
+      if (c < ncols && k < n) {
+        const int64_t x = c % g.a, y = c / g.a;
+        val = load_combo(pro, x + g.a * k + an * y, plain);
+      }
+      sV[kk][cc] = val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      double lv[RI], vv[RC];
+#pragma unroll
+      for (int r = 0; r < RI; ++r) lv[r] = sL[kk][ti + r * TROWS];
+#pragma unroll
+      for (int c = 0; c < RC; ++c) vv[c] = sV[kk][tc + c * TCOLS];
+#pragma unroll
+      for (int r = 0; r < RI; ++r)
+#pragma unroll
+        for (int c = 0; c < RC; ++c) acc[r][c] = fma(lv[r], vv[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < RI; ++r) {
+    const int i = i0 + ti + r * TROWS;
+    if (i >= n) continue;
+#pragma unroll
+    for (int c = 0; c < RC; ++c) {
+      const int64_t col = c0 + tc + c * TCOLS;
+      if (col >= ncols) continue;
+      const int64_t x = col % g.a, y = col / g.a;
+      store_epi(epi, W, x + g.a * i + an * y, acc[r][c]);
+    }
+  }
+}
+
+__global__ void combine_kernel(Epi e, int64_t N) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    double sv[kMaxSrc];
+    for (int m = 0; m < e.nsrc; ++m)
+      sv[m] = ((e.src_f32mask >> m) & 1) ? (double)((const float*)e.src[m])[idx] : e.src[m][idx];
+    for (int t = 0; t < e.nout; ++t) {
+      double o = 0.0;
+      for (int m = 0; m < e.nsrc; ++m)
+        if (e.a[t][m] != 0.0) o = fma(e.a[t][m], sv[m], o);
+      if ((e.out_f32mask >> t) & 1) ((float*)e.out[t])[idx] = (float)o;
+      else e.out[t][idx] = o;
+    }
+  }
+}
+
+struct PtrArray {
+  const void* p[kMaxSrc];
+};
+
+__global__ void sumsq_kernel_arr(PtrArray xs, int64_t N, int is_f32, double* out) {
+  const int k = blockIdx.y;
+  double s = 0.0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    double v = is_f32 ? (double)((const float*)xs.p[k])[idx] : ((const double*)xs.p[k])[idx];
+    s = fma(v, v, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __shared__ double part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? part[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) atomicAdd(out + k, s);
+  }
+}
+
+int grid_for(int64_t N, int threads) {
+  int64_t g = (N + threads - 1) / threads;
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_mode_product_f64(const Combo& pro, const double* L, ModeGeom g, double* W,
+                                    const Epi* epi, cudaStream_t st) {
+  Epi e;
+  if (epi) {
+    e = *epi;
+  } else {
+    e.nout = 0;
+    e.nsrc = 0;
+  }
+  const int64_t ncols = g.a * g.b;
+  dim3 grid((unsigned)((ncols + TC - 1) / TC), (unsigned)((g.n + TI - 1) / TI));
+  count_launch();
+  if (g.a >= 32)
+    mode_product_f64_kernel<true><<<grid, NT, 0, st>>>(pro, L, g, W, e);
+  else
+    mode_product_f64_kernel<false><<<grid, NT, 0, st>>>(pro, L, g, W, e);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const Epi& e, int64_t N, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  count_launch();
+  combine_kernel<<<grid_for(N, 256), 256, 0, st>>>(e, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq(const void* const* x, int count, int64_t N, int is_f32, double* out,
+                         cudaStream_t st) {
+  if (count <= 0 || N <= 0) return cudaSuccess;
+  if (count > kMaxSrc) return cudaErrorInvalidValue;
+  PtrArray a;
+  for (int k = 0; k < count; ++k) a.p[k] = x[k];
+  dim3 grid(grid_for(N, 256) > 304 ? 304 : grid_for(N, 256), count);
+  count_launch();
+  sumsq_kernel_arr<<<grid, 256, 0, st>>>(a, N, is_f32, out);
+  return cudaGetLastError();
+}
+
+}  // namespace phiks

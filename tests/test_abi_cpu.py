@@ -1,0 +1,82 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every
+symbol include/phiks.h declares, and its parameter selection (Sec. 3.3) picks
+the same integers (s, q, T#) as the oracle's restatement."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as wk
+from oracle import params
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pk():
+    from paper_2210_07667_gb300 import _build
+    _build.build()
+    import paper_2210_07667_gb300 as m
+    m.load()
+    return m
+
+
+def test_exports_match_header(pk):
+    hdr = open(os.path.join(ROOT, "include", "phiks.h")).read()
+    declared = set(re.findall(r"\b(phiks_[a-z_0-9]+)\s*\(", hdr))
+    lib = pk.load()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(pk.EXPORTED)
+
+
+def _cases():
+    yield wk.small_same(32)
+    yield wk.adr3d_lincomb(64)
+    yield wk.adr3d_lincomb(p=4, dims=(10, 11, 12))
+    yield wk.adr3d_lincomb(p=2, dims=(40, 7), nscales=2, alpha=(3.0, -1.0), rho=-1.0)
+    w = wk.small_same(24, p=5, tau=5e-3)
+    w.nscales = 2
+    yield w
+    yield wk.cheb3d_same(n=24, nrhs=1, tau=2e-4)
+
+
+@pytest.mark.parametrize("case", list(range(6)))
+@pytest.mark.parametrize("rule", [0, 1])
+def test_parameter_selection_matches_oracle(pk, case, rule):
+    wl = list(_cases())[case]
+    vn = [float(np.linalg.norm(v)) for v in wl.vs[: (1 if wl.mode == "same" else wl.p + 1)]]
+    kind = "same" if wl.mode == "same" else "lincomb"
+    got = pk.phiks_choose_params(wl.A, wl.tau, wl.p, vn, nscales=wl.nscales, rule=rule)
+    ref = params.select(params.kron_sum_rect(wl.A, wl.tau), wl.p, kind, vn, wl.nscales,
+                        rule="gll" if rule == 0 else "gl")
+    assert got == (ref.s, ref.q, ref.tcount)
+
+
+def test_parameter_selection_tolerance_and_range(pk):
+    wl = wk.small_same(16)
+    vn = [float(np.linalg.norm(wl.vs[0]))]
+    for tol in (1e-6, 1e-10, 2.0 ** -53):
+        got = pk.phiks_choose_params(wl.A, wl.tau, wl.p, vn, tol=tol)
+        ref = params.select(params.kron_sum_rect(wl.A, wl.tau), wl.p, "same", vn, tol=tol)
+        assert got == (ref.s, ref.q, ref.tcount)
+    got = pk.phiks_choose_params(wl.A, wl.tau, wl.p, vn, qmin=4, qmax=6)
+    ref = params.select(params.kron_sum_rect(wl.A, wl.tau), wl.p, "same", vn, qmin=4, qmax=6)
+    assert got == (ref.s, ref.q, ref.tcount)
+
+
+def test_invalid_arguments_are_reported(pk):
+    A = [np.eye(3)]
+    with pytest.raises(pk.PhiksError) as e:
+        pk.phiks_choose_params(A, 1.0, 0, [1.0])
+    assert e.value.status == 1
+    with pytest.raises(pk.PhiksError):
+        pk.phiks_choose_params(A, 1.0, 2, [1.0, 1.0])          # nv neither 1 nor p + 1
+    with pytest.raises(pk.PhiksError):
+        pk.phiks_choose_params(A, 1.0, 2, [1.0], nscales=0)
+    with pytest.raises(pk.PhiksError):
+        pk.phiks_choose_params(A, 1.0, 2, [1.0], qmin=5, qmax=4)
+    with pytest.raises(pk.PhiksError) as e:
+        pk.phiks_choose_params(A, 1.0, 2, [1.0], force_s=2)    # force_s without force_q
+    assert "force" in str(e.value)
