@@ -168,6 +168,29 @@ phiks_status phiks_profile_read(phiks_plan_t plan, double* ms, int64_t* launches
 /* Number of kernels this library has launched in this process (all plans). */
 uint64_t phiks_kernel_launches(void);
 
+/* Tucker operator W = V x_1 L_1 x_2 ... x_d L_d in FP64 that allocates no
+ * memory, for callers that cannot call cudaMalloc: applications that give all
+ * device memory to their own pool up front, or latency-bound loops where
+ * cudaMalloc / cudaFree (driver locks, device-wide synchronisation) are not
+ * acceptable.  The paper has no counterpart; it is an addition of this
+ * library.
+ *   d        1 <= d <= PHIKS_MAX_D
+ *   n        host, d sizes; N = n_1 ... n_d must not exceed 1,048,576
+ *            (larger N returns PHIKS_ERR_INVALID)
+ *   V, W     device, N doubles each, column-major tensors, may not alias
+ *   L        host array of d device pointers to column-major n_mu x n_mu doubles
+ * No plan is needed.  The intermediate tensors live in a fixed 16 MiB
+ * __device__ array inside the library (two halves of 1,048,576 doubles) that
+ * every GPU loading the library keeps until the process exits.  All calls
+ * share that array, so calls whose kernels overlap on the GPU (different
+ * streams, or other host threads) race and give wrong results; serialise them
+ * on one stream.  Every intermediate is fully overwritten, so nothing is
+ * cleared between calls.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture begins.  Asynchronous on `stream`. */
+phiks_status phiks_tucker_noalloc(int d, const int64_t* n, const double* V, double* W,
+                                  const double* const* L, void* stream);
+
 /* Release the plan and its device memory (synchronises its device). */
 void phiks_destroy(phiks_plan_t plan);
 

@@ -19,7 +19,7 @@ __all__ = [
     "PhiksError", "Options", "lib", "library_path", "load",
     "phiks_plan", "phiks_apply", "phiks_apply_ex", "phiks_workspace_size",
     "phiks_select_params", "phiks_choose_params", "phiks_last_params", "phiks_tucker", "phiks_expm",
-    "phiks_profile_enable", "phiks_profile_read", "phiks_kernel_launches",
+    "phiks_profile_enable", "phiks_profile_read", "phiks_kernel_launches", "phiks_tucker_noalloc",
     "phiks_destroy", "phiks_last_error", "Plan", "EXPORTED",
 ]
 
@@ -32,8 +32,8 @@ STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "UNSUPPORTED", 4: "NO_PARAMS", 5: 
 EXPORTED = [
     "phiks_options_init", "phiks_plan", "phiks_apply", "phiks_apply_ex", "phiks_workspace_size",
     "phiks_select_params", "phiks_choose_params", "phiks_last_params", "phiks_tucker", "phiks_expm",
-    "phiks_profile_enable", "phiks_profile_read", "phiks_kernel_launches", "phiks_destroy",
-    "phiks_last_error",
+    "phiks_profile_enable", "phiks_profile_read", "phiks_kernel_launches", "phiks_tucker_noalloc",
+    "phiks_destroy", "phiks_last_error",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -107,6 +107,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.phiks_profile_read.restype = ctypes.c_int
     L.phiks_kernel_launches.argtypes = []
     L.phiks_kernel_launches.restype = ctypes.c_uint64
+    L.phiks_tucker_noalloc.argtypes = [i, ctypes.POINTER(ctypes.c_int64), vp, vp, ctypes.POINTER(vp), vp]
+    L.phiks_tucker_noalloc.restype = ctypes.c_int
     L.phiks_destroy.argtypes = [vp]
     L.phiks_destroy.restype = None
     L.phiks_last_error.argtypes = []
@@ -249,6 +251,14 @@ def phiks_profile_read(plan: int):
 
 def phiks_kernel_launches() -> int:
     return int(load().phiks_kernel_launches())
+
+
+def phiks_tucker_noalloc(dims: Sequence[int], V, W, Ls, stream=None):
+    """FP64 Tucker operator without any allocation (N <= 1,048,576): its
+    intermediates live in a fixed device array inside the library."""
+    d = len(dims)
+    n = (ctypes.c_int64 * d)(*[int(m) for m in dims])
+    _check(load().phiks_tucker_noalloc(d, n, _ptr(V), _ptr(W), _vptrs(Ls), _stream(stream)))
 
 
 def phiks_destroy(plan: int):

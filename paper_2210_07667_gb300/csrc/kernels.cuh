@@ -6,6 +6,9 @@
 
 namespace phiks {
 
+// Sets the message phiks_last_error() returns on this thread.
+void set_error_message(const char* msg);
+
 // Process-wide count of kernels launched by this library.
 uint64_t kernel_launch_count();
 void count_launch();

@@ -36,6 +36,12 @@ phiks_status fail(phiks_status st, const char* fmt, ...) {
   return st;
 }
 
+}  // namespace
+
+void phiks::set_error_message(const char* msg) { g_err = msg ? msg : ""; }
+
+namespace {
+
 #define CK(call)                                                                         \
   do {                                                                                   \
     cudaError_t e_ = (call);                                                             \
