@@ -26,12 +26,6 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 namespace {
 
-constexpr int TI = 32, TC = 64, KC = 16, NT = 256;
-constexpr int RI = 2, RC = 4;          // per-thread micro tile
-constexpr int TROWS = TI / RI;         // 16 thread rows
-constexpr int TCOLS = TC / RC;         // 16 thread columns
-static_assert(TROWS * TCOLS == NT, "thread layout");
-
 __device__ __forceinline__ double load_combo(const Combo& pro, int64_t idx, bool plain) {
   if (plain) return __ldg(pro.src[0] + idx);
   double v = pro.coef[0] * __ldg(pro.src[0] + idx);
@@ -54,9 +48,16 @@ __device__ __forceinline__ void store_epi(const Epi& epi, double* W, int64_t idx
   }
 }
 
-template <bool XFAST>
-__global__ void __launch_bounds__(NT) mode_product_f64_kernel(Combo pro, const double* __restrict__ L,
-                                                              ModeGeom g, double* W, Epi epi) {
+// CTA tile: TI rows of L x TC columns c = x + a y; RI x RC outputs per thread
+// (rows ti + r * TI/RI, columns tc + c * TC/RC, so a warp reads consecutive
+// shared-memory words); KC-deep slices of L and of the fibres, the next slice
+// fetched into registers while the current one is consumed.
+template <int TI, int TC, int RI, int RC, int KC, bool XFAST>
+__global__ void __launch_bounds__((TI / RI) * (TC / RC))
+    mode_product_f64_kernel(Combo pro, const double* __restrict__ L, ModeGeom g, double* W, Epi epi) {
+  constexpr int TROWS = TI / RI, TCOLS = TC / RC, NT = TROWS * TCOLS;
+  constexpr int LPT = (TI * KC + NT - 1) / NT;
+  constexpr int VPT = (TC * KC + NT - 1) / NT;
   __shared__ double sL[KC][TI + 1];
   __shared__ double sV[KC][TC + 1];
   const int tid = threadIdx.x;
@@ -69,37 +70,63 @@ __global__ void __launch_bounds__(NT) mode_product_f64_kernel(Combo pro, const d
   const int64_t an = g.a * (int64_t)n;
   const bool plain = (pro.nsrc == 1 && pro.coef[0] == 1.0);
 
+  double rl[LPT], rv[VPT];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int e = 0; e < LPT; ++e) {
+      const int idx = tid + e * NT;
+      const int ii = idx % TI, kk = idx / TI;
+      const int i = i0 + ii, k = k0 + kk;
+      rl[e] = (idx < TI * KC && i < n && k < n) ? __ldg(L + i + (int64_t)n * k) : 0.0;
+    }
+#pragma unroll
+    for (int e = 0; e < VPT; ++e) {
+      const int idx = tid + e * NT;
+      int cc, kk;
+      if (XFAST) {
+        cc = idx % TC;
+        kk = idx / TC;
+      } else {
+        kk = idx % KC;
+        cc = idx / KC;
+      }
+      const int64_t c = c0 + cc;
+      const int k = k0 + kk;
+      double val = 0.0;
+      if (idx < TC * KC && c < ncols && k < n) {
+        const int64_t x = c % g.a, y = c / g.a;
+        val = load_combo(pro, x + g.a * k + an * y, plain);
+      }
+      rv[e] = val;
+    }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int e = 0; e < LPT; ++e) {
+      const int idx = tid + e * NT;
+      if (idx < TI * KC) sL[idx / TI][idx % TI] = rl[e];
+    }
+#pragma unroll
+    for (int e = 0; e < VPT; ++e) {
+      const int idx = tid + e * NT;
+      if (idx < TC * KC) {
+        if (XFAST) sV[idx / TC][idx % TC] = rv[e];
+        else sV[idx % KC][idx / KC] = rv[e];
+      }
+    }
+  };
+
   double acc[RI][RC];
 #pragma unroll
   for (int r = 0; r < RI; ++r)
 #pragma unroll
     for (int c = 0; c < RC; ++c) acc[r][c] = 0.0;
 
+  fetch(0);
   for (int k0 = 0; k0 < n; k0 += KC) {
-    for (int e = tid; e < TI * KC; e += NT) {
-      const int ii = e % TI, kk = e / TI;
-      const int i = i0 + ii, k = k0 + kk;
-      sL[kk][ii] = (i < n && k < n) ? __ldg(L + i + (int64_t)n * k) : 0.0;
-    }
-    for (int e = tid; e < TC * KC; e += NT) {
-      int cc, kk;
-      if (XFAST) {
-        cc = e % TC;
-        kk = e / TC;
-      } else {
-        kk = e % KC;
-        cc = e / KC;
-      }
-      const int64_t c = c0 + cc;
-      const int k = k0 + kk;
-      double val = 0.0;
-      if (c < ncols && k < n) {
-        const int64_t x = c % g.a, y = c / g.a;
-        val = load_combo(pro, x + g.a * k + an * y, plain);
-      }
-      sV[kk][cc] = val;
-    }
+    stash();
     __syncthreads();
+    if (k0 + KC < n) fetch(k0 + KC);
 #pragma unroll
     for (int kk = 0; kk < KC; ++kk) {
       double lv[RI], vv[RC];
@@ -126,6 +153,18 @@ __global__ void __launch_bounds__(NT) mode_product_f64_kernel(Combo pro, const d
       store_epi(epi, W, x + g.a * i + an * y, acc[r][c]);
     }
   }
+}
+
+template <int TI, int TC, int RI, int RC, int KC>
+void launch_tiled(const Combo& pro, const double* L, ModeGeom g, double* W, const Epi& e,
+                  cudaStream_t st) {
+  constexpr int NT = (TI / RI) * (TC / RC);
+  const int64_t ncols = g.a * g.b;
+  dim3 grid((unsigned)((ncols + TC - 1) / TC), (unsigned)((g.n + TI - 1) / TI));
+  if (g.a >= TC)
+    mode_product_f64_kernel<TI, TC, RI, RC, KC, true><<<grid, NT, 0, st>>>(pro, L, g, W, e);
+  else
+    mode_product_f64_kernel<TI, TC, RI, RC, KC, false><<<grid, NT, 0, st>>>(pro, L, g, W, e);
 }
 
 __global__ void combine_kernel(Epi e, int64_t N) {
@@ -185,13 +224,15 @@ cudaError_t launch_mode_product_f64(const Combo& pro, const double* L, ModeGeom 
     e.nout = 0;
     e.nsrc = 0;
   }
-  const int64_t ncols = g.a * g.b;
-  dim3 grid((unsigned)((ncols + TC - 1) / TC), (unsigned)((g.n + TI - 1) / TI));
   count_launch();
-  if (g.a >= 32)
-    mode_product_f64_kernel<true><<<grid, NT, 0, st>>>(pro, L, g, W, e);
+  // Large problems: 32 x 64 tiles (256 threads, 8 outputs each).  Otherwise
+  // 16 x 16 tiles (64 threads, 4 outputs each), so that even N = 2^18 spreads
+  // over ~1000 CTAs and the 152 SMs' FP64 pipes stay evenly loaded.
+  const int64_t big_tiles = ((g.a * g.b + 63) / 64) * ((g.n + 31) / 32);
+  if (big_tiles >= 8 * 152)
+    launch_tiled<32, 64, 2, 4, 16>(pro, L, g, W, e, st);
   else
-    mode_product_f64_kernel<false><<<grid, NT, 0, st>>>(pro, L, g, W, e);
+    launch_tiled<16, 16, 2, 2, 32>(pro, L, g, W, e, st);
   return cudaGetLastError();
 }
 
