@@ -165,6 +165,12 @@ phiks_status phiks_expm(int batch, int n, const double* X, double* E, void* stre
 phiks_status phiks_profile_enable(phiks_plan_t plan, int enable);
 phiks_status phiks_profile_read(phiks_plan_t plan, double* ms, int64_t* launches, double* flops);
 
+/* Synchronises `stream` and reports whether any tensor-core kernel of the plan
+ * gave up a bounded device-side wait (then PHIKS_ERR_TIMEOUT, and the results
+ * of the calls since the last check are not valid).  The status is cleared by
+ * the read.  Every wait inside those kernels is limited to about a second. */
+phiks_status phiks_device_status(phiks_plan_t plan, void* stream);
+
 /* Number of kernels this library has launched in this process (all plans). */
 uint64_t phiks_kernel_launches(void);
 

@@ -20,7 +20,7 @@ __all__ = [
     "phiks_plan", "phiks_apply", "phiks_apply_ex", "phiks_workspace_size",
     "phiks_select_params", "phiks_choose_params", "phiks_last_params", "phiks_tucker", "phiks_expm",
     "phiks_profile_enable", "phiks_profile_read", "phiks_kernel_launches", "phiks_tucker_noalloc",
-    "phiks_destroy", "phiks_last_error", "Plan", "EXPORTED",
+    "phiks_device_status", "phiks_destroy", "phiks_last_error", "Plan", "EXPORTED",
 ]
 
 PHIKS_FP64, PHIKS_TF32, PHIKS_TF32X3, PHIKS_BF16X3 = 0, 1, 2, 3
@@ -33,7 +33,7 @@ EXPORTED = [
     "phiks_options_init", "phiks_plan", "phiks_apply", "phiks_apply_ex", "phiks_workspace_size",
     "phiks_select_params", "phiks_choose_params", "phiks_last_params", "phiks_tucker", "phiks_expm",
     "phiks_profile_enable", "phiks_profile_read", "phiks_kernel_launches", "phiks_tucker_noalloc",
-    "phiks_destroy", "phiks_last_error",
+    "phiks_device_status", "phiks_destroy", "phiks_last_error",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -107,6 +107,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.phiks_profile_read.restype = ctypes.c_int
     L.phiks_kernel_launches.argtypes = []
     L.phiks_kernel_launches.restype = ctypes.c_uint64
+    L.phiks_device_status.argtypes = [vp, vp]
+    L.phiks_device_status.restype = ctypes.c_int
     L.phiks_tucker_noalloc.argtypes = [i, ctypes.POINTER(ctypes.c_int64), vp, vp, ctypes.POINTER(vp), vp]
     L.phiks_tucker_noalloc.restype = ctypes.c_int
     L.phiks_destroy.argtypes = [vp]
@@ -251,6 +253,11 @@ def phiks_profile_read(plan: int):
 
 def phiks_kernel_launches() -> int:
     return int(load().phiks_kernel_launches())
+
+
+def phiks_device_status(plan: int, stream=None):
+    """Raise PhiksError(TIMEOUT) if a bounded device-side wait gave up."""
+    _check(load().phiks_device_status(plan, _stream(stream)))
 
 
 def phiks_tucker_noalloc(dims: Sequence[int], V, W, Ls, stream=None):

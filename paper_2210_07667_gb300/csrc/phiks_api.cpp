@@ -86,6 +86,8 @@ struct Bank {
   int b0 = -1;                           // entry of exp(tau A_mu / 2^s)
   std::vector<double> theta, w;
   uint64_t stamp = 0;
+  uint8_t* tcb = nullptr;                  // split path: B planes of every entry
+  std::vector<std::vector<size_t>> tcoff;  // tcoff[b][mu], bytes
 };
 
 }  // namespace
@@ -109,6 +111,10 @@ struct phiks_plan_s {
   double* expm_scratch = nullptr;  // 3 x (q + 1) x sum_n2 doubles
   size_t expm_scratch_elems = 0;
   double* msq[2] = {nullptr, nullptr};  // squaring chain ping-pong, sum_n2 each
+  uint8_t* msq_tcb[2] = {nullptr, nullptr};  // split path: B planes of msq
+  uint8_t* tucker_tcb = nullptr;             // split path: B planes for phiks_tucker
+  size_t tcb_off[PHIKS_MAX_D] = {0};         // per-mode offsets inside one plane set
+  size_t tcb_bytes = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
   double* d_norms = nullptr;
@@ -157,7 +163,7 @@ size_t workspace_bytes(const phiks_plan_s* P, int p) {
   size_t N = (size_t)P->N;
   size_t acc = (size_t)std::max(p, 1) * N * 8;
   size_t tmp = 2 * N * 8;
-  size_t tcx = P->dtype == PHIKS_FP64 ? 0 : tc_workspace_bytes(P->N);
+  size_t tcx = P->dtype == PHIKS_FP64 ? 0 : tc_workspace_bytes(P->N) + 1024;
   return acc + tmp + tcx + 256 * 4;
 }
 
@@ -376,6 +382,7 @@ phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool 
                                   [](const Bank& x, const Bank& y) { return x.stamp < y.stamp; });
       CK(cudaStreamSynchronize(st));
       cudaFree(lru->dev);
+      if (lru->tcb) cudaFree(lru->tcb);
       P->banks.erase(lru);
     }
     CK(cudaMalloc(&nb.dev, tot * 8));
@@ -403,6 +410,16 @@ phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool 
     if (!hit) cudaFree(nb.dev);
     return stt;
   }
+  if (P->dtype != PHIKS_FP64) {  // B-operand planes of every small exponential
+    nb.tcoff.assign(nbk, std::vector<size_t>(P->d));
+    if (hit) nb.tcb = hit->tcb;
+    else CK(cudaMalloc(&nb.tcb, (size_t)nbk * P->tcb_bytes));
+    for (int b = 0; b < nbk; ++b)
+      for (int mu = 0; mu < P->d; ++mu) {
+        nb.tcoff[b][mu] = (size_t)b * P->tcb_bytes + P->tcb_off[mu];
+        CK(tc_prepare_b(P->dtype, nb.dev + nb.off[b][mu], (int)P->n[mu], nb.tcb + nb.tcoff[b][mu], st));
+      }
+  }
   nb.stamp = P->clock;
   if (hit) {
     *hit = nb;
@@ -422,40 +439,65 @@ struct Ctx {
   int tuckers = 0;
 };
 
-// W = (input combination) x_1 L_1 ... x_d L_d, last mode through `epi`
-// (plain store into W when epi is null).
-phiks_status tucker(Ctx& c, const Combo& in, const double* const* L, double* W, const Epi* epi) {
+// The d matrices of one Tucker operator: FP64 (FP64 path) and their
+// B-operand planes (split path).
+struct Mats {
+  const double* L[PHIKS_MAX_D];
+  const void* B[PHIKS_MAX_D];
+};
+
+phiks_status prof_begin(Ctx& c, cudaEvent_t* e1) {
   phiks_plan_s* P = c.P;
+  *e1 = nullptr;
+  if (!P->prof) return PHIKS_OK;
+  while (P->ev_pool.size() < P->ev_used + 2) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    P->ev_pool.push_back(e);
+  }
+  cudaEvent_t e0 = P->ev_pool[P->ev_used++];
+  *e1 = P->ev_pool[P->ev_used++];
+  CK(cudaEventRecord(e0, c.st));
+  return PHIKS_OK;
+}
+
+phiks_status prof_end(Ctx& c, cudaEvent_t e1, double flops) {
+  if (!e1) return PHIKS_OK;
+  CK(cudaEventRecord(e1, c.st));
+  c.P->prof_flops += flops;
+  return PHIKS_OK;
+}
+
+// (input combination) x_1 L_1 ... x_d L_d, the last mode through `epi`.
+// FP64: one profiled launch per mode; split dtypes: one profiled tensor-core
+// Tucker (split pass + d GEMM passes).
+phiks_status tucker(Ctx& c, const Combo& in, const Mats& M, const Epi* epi) {
+  phiks_plan_s* P = c.P;
+  if (P->dtype != PHIKS_FP64) {
+    cudaEvent_t e1;
+    TRY(prof_begin(c, &e1));
+    cudaError_t e = tc_tucker(P->tc, in, M.B, *epi, c.st);
+    if (e != cudaSuccess)
+      return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), tc_last_error());
+    double fl = 0;
+    for (int mu = 0; mu < P->d; ++mu) fl += 2.0 * (double)P->N * (double)P->n[mu];
+    TRY(prof_end(c, e1, fl));
+    c.tuckers++;
+    return PHIKS_OK;
+  }
   Combo cur = in;
   for (int mu = 0; mu < P->d; ++mu) {
     const bool last = (mu == P->d - 1);
-    double* out = last ? W : c.tmp[mu & 1];
+    double* out = last ? nullptr : c.tmp[mu & 1];
     ModeGeom g{mode_a(P, mu), (int)P->n[mu], mode_b(P, mu)};
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (P->prof) {
-      while (P->ev_pool.size() < P->ev_used + 2) {
-        cudaEvent_t e;
-        CK(cudaEventCreate(&e));
-        P->ev_pool.push_back(e);
-      }
-      e0 = P->ev_pool[P->ev_used++];
-      e1 = P->ev_pool[P->ev_used++];
-      CK(cudaEventRecord(e0, c.st));
-    }
-    if (P->dtype == PHIKS_FP64) {
-      CK(launch_mode_product_f64(cur, L[mu], g, out, last ? epi : nullptr, c.st));
-    } else {
-      CK(tc_mode_product(P->tc, P->dtype, cur, L[mu], g, out, last ? epi : nullptr, c.st));
-    }
-    if (P->prof) {
-      CK(cudaEventRecord(e1, c.st));
-      P->prof_flops += 2.0 * (double)P->N * (double)P->n[mu];
-    }
+    cudaEvent_t e1;
+    TRY(prof_begin(c, &e1));
+    CK(launch_mode_product_f64(cur, M.L[mu], g, out, last ? epi : nullptr, c.st));
+    TRY(prof_end(c, e1, 2.0 * (double)P->N * (double)P->n[mu]));
     cur = make_combo();
     cur.nsrc = 1;
     cur.src[0] = out;
     cur.coef[0] = 1.0;
-    cur.f32mask = P->dtype == PHIKS_FP64 ? 0 : 1;  // split path keeps float temporaries
   }
   c.tuckers++;
   return PHIKS_OK;
@@ -470,20 +512,23 @@ Combo plain(const void* x, bool f32) {
   return c;
 }
 
-void bank_ptrs(const phiks_plan_s* P, const Bank* B, int b, const double** L) {
-  for (int mu = 0; mu < P->d; ++mu) L[mu] = B->dev + B->off[b][mu];
+void bank_ptrs(const phiks_plan_s* P, const Bank* B, int b, Mats* M) {
+  for (int mu = 0; mu < P->d; ++mu) {
+    M->L[mu] = B->dev + B->off[b][mu];
+    M->B[mu] = B->tcb ? (const void*)(B->tcb + B->tcoff[b][mu]) : nullptr;
+  }
 }
 
-// Squaring chain: M <- M^2 for every mode.
-phiks_status square_modes(Ctx& c, const double** M, int& cur_buf) {
+// Squaring chain: M <- M^2 for every mode (and the split planes of the result).
+phiks_status square_modes(Ctx& c, Mats& M, int& cur_buf) {
   phiks_plan_s* P = c.P;
   GemmBatch gb;
   gb.count = P->d;
   size_t off = 0;
   for (int mu = 0; mu < P->d; ++mu) {
     gb.n[mu] = (int)P->n[mu];
-    gb.A[mu] = M[mu];
-    gb.B[mu] = M[mu];
+    gb.A[mu] = M.L[mu];
+    gb.B[mu] = M.L[mu];
     gb.C[mu] = P->msq[cur_buf] + off;
     gb.alpha[mu] = 1.0;
     gb.beta_I[mu] = 0.0;
@@ -492,8 +537,13 @@ phiks_status square_modes(Ctx& c, const double** M, int& cur_buf) {
   CK(launch_gemm_batch_f64(gb, P->nmax, c.st));
   off = 0;
   for (int mu = 0; mu < P->d; ++mu) {
-    M[mu] = P->msq[cur_buf] + off;
+    M.L[mu] = P->msq[cur_buf] + off;
     off += (size_t)P->n[mu] * P->n[mu];
+    if (P->dtype != PHIKS_FP64) {
+      uint8_t* dst = P->msq_tcb[cur_buf] + P->tcb_off[mu];
+      CK(tc_prepare_b(P->dtype, M.L[mu], (int)P->n[mu], dst, c.st));
+      M.B[mu] = dst;
+    }
   }
   cur_buf = 1 - cur_buf;
   return PHIKS_OK;
@@ -554,12 +604,12 @@ phiks_status run_same(Ctx& c, const Bank* B, int s, int p, const void* v, const 
       TRY(combine(c, f));
       continue;
     }
-    const double* L[PHIKS_MAX_D];
-    bank_ptrs(P, B, B->node_bank[i], L);
-    TRY(tucker(c, plain(v, f32), L, nullptr, &e));
+    Mats L;
+    bank_ptrs(P, B, B->node_bank[i], &L);
+    TRY(tucker(c, plain(v, f32), L, &e));
   }
-  const double* M[PHIKS_MAX_D];
-  bank_ptrs(P, B, B->b0, M);
+  Mats M;
+  bank_ptrs(P, B, B->b0, &M);
   int mbuf = 0;
   auto emit = [&](int Lv) -> phiks_status {
     char* blk = (char*)out + (size_t)Lv * per * N * es;
@@ -570,7 +620,7 @@ phiks_status run_same(Ctx& c, const Bank* B, int s, int p, const void* v, const 
       e.out[0] = (double*)blk;
       e.out_f32mask = f32 ? 1 : 0;
       e.b[0] = 1.0;
-      TRY(tucker(c, plain(v, f32), M, nullptr, &e));
+      TRY(tucker(c, plain(v, f32), M, &e));
       slot = 1;
     }
     for (int l = 0; l < p; ++l) TRY(store_acc(c, blk + (size_t)(slot + l) * N * es, acc[l]));
@@ -589,7 +639,7 @@ phiks_status run_same(Ctx& c, const Bank* B, int s, int p, const void* v, const 
         e.src[k - 1] = acc[k - 1];
         e.a[0][k - 1] = std::ldexp(1.0, -l) / factorial(l - k);
       }
-      TRY(tucker(c, plain(acc[l - 1], false), M, nullptr, &e));
+      TRY(tucker(c, plain(acc[l - 1], false), M, &e));
     }
     TRY(square_modes(c, M, mbuf));
     if (j - 1 < o.nscales) TRY(emit(j - 1));
@@ -643,13 +693,13 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
       e.src[0] = acc[l - 1];
       e.a[0][0] = 1.0;
       e.b[0] = w;
-      const double* L[PHIKS_MAX_D];
-      bank_ptrs(P, B, B->node_bank[i], L);
-      TRY(tucker(c, in, L, nullptr, &e));
+      Mats L;
+      bank_ptrs(P, B, B->node_bank[i], &L);
+      TRY(tucker(c, in, L, &e));
     }
   }
-  const double* M[PHIKS_MAX_D];
-  bank_ptrs(P, B, B->b0, M);
+  Mats M;
+  bank_ptrs(P, B, B->b0, &M);
   int mbuf = 0;
   auto emit = [&](int Lv) -> phiks_status {
     char* blk = (char*)out + (size_t)Lv * N * es;
@@ -664,7 +714,7 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
         e.src[0] = acc[p - 1];
         e.a[0][0] = 1.0;
       }
-      TRY(tucker(c, plain(v[0], f32), M, nullptr, &e));
+      TRY(tucker(c, plain(v[0], f32), M, &e));
     } else if (p > 0) {
       TRY(store_acc(c, blk, acc[p - 1]));
     } else {
@@ -685,7 +735,7 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
         e.src[k - 1] = acc[k - 1];
         e.a[0][k - 1] = 1.0 / (factorial(l - k) * std::ldexp(1.0, (l - k) * j));
       }
-      TRY(tucker(c, plain(acc[l - 1], false), M, nullptr, &e));
+      TRY(tucker(c, plain(acc[l - 1], false), M, &e));
     }
     TRY(square_modes(c, M, mbuf));
     if (j - 1 < o.nscales) TRY(emit(j - 1));
@@ -778,8 +828,17 @@ phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dty
   CK(cudaMalloc(&P->d_norms, (PHIKS_MAX_P + 1) * 8));
   CK(cudaMallocHost(&P->h_norms, (PHIKS_MAX_P + 1) * 8));
   if (dtype != PHIKS_FP64) {
-    phiks_status st = tc_create(&P->tc, d, P->n, P->N);
+    phiks_status st = tc_create(&P->tc, dtype, d, P->n, P->N);
     if (st != PHIKS_OK) return fail(st, "%s", tc_last_error());
+    size_t tb = 0;
+    for (int mu = 0; mu < d; ++mu) {
+      P->tcb_off[mu] = tb;
+      tb += tc_bplanes_bytes(dtype, (int)n[mu]);
+    }
+    P->tcb_bytes = tb;
+    CK(cudaMalloc(&P->msq_tcb[0], tb));
+    CK(cudaMalloc(&P->msq_tcb[1], tb));
+    CK(cudaMalloc(&P->tucker_tcb, tb));
   }
   *out = P.release();
   return PHIKS_OK;
@@ -811,12 +870,32 @@ phiks_status phiks_profile_read(phiks_plan_t P, double* ms, int64_t* launches, d
 
 uint64_t phiks_kernel_launches(void) { return phiks::kernel_launch_count(); }
 
+phiks_status phiks_device_status(phiks_plan_t P, void* stream) {
+  g_err.clear();
+  if (!P) return fail(PHIKS_ERR_INVALID, "NULL plan");
+  DeviceGuard g(P->device);
+  if (!P->tc) {
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return PHIKS_OK;
+  }
+  int code = tc_read_status(P->tc, (cudaStream_t)stream);
+  if (code < 0) return fail(PHIKS_ERR_CUDA, "reading the device status failed");
+  if (code > 0) return fail(PHIKS_ERR_TIMEOUT, "a bounded device-side wait gave up (site %d)", code);
+  return PHIKS_OK;
+}
+
 void phiks_destroy(phiks_plan_t P) {
   if (!P) return;
   DeviceGuard g(P->device);
   cudaDeviceSynchronize();
   for (auto e : P->ev_pool) cudaEventDestroy(e);
-  for (auto& b : P->banks) cudaFree(b.dev);
+  for (auto& b : P->banks) {
+    cudaFree(b.dev);
+    if (b.tcb) cudaFree(b.tcb);
+  }
+  cudaFree(P->msq_tcb[0]);
+  cudaFree(P->msq_tcb[1]);
+  cudaFree(P->tucker_tcb);
   cudaFree(P->dAs);
   cudaFree(P->expm_scratch);
   cudaFree(P->msq[0]);
@@ -985,7 +1064,10 @@ phiks_status phiks_apply_ex(phiks_plan_t P, double tau, int p, const void* const
   Ctx c{P, st, {nullptr, nullptr}, 0};
   c.tmp[0] = (double*)(ws + (size_t)std::max(p, 1) * N * 8);
   c.tmp[1] = c.tmp[0] + N;
-  if (P->dtype != PHIKS_FP64) tc_bind_workspace(P->tc, ws + (size_t)(std::max(p, 1) + 2) * N * 8);
+  if (P->dtype != PHIKS_FP64) {
+    uintptr_t t = (uintptr_t)(ws + (size_t)(std::max(p, 1) + 2) * N * 8);
+    tc_bind_workspace(P->tc, (void*)((t + 1023) & ~(uintptr_t)1023));
+  }
 
   Bank* B = nullptr;
   TRY(get_bank(P, tau, s, q, o.rule, o.no_cache != 0, st, &B));
@@ -1026,14 +1108,27 @@ phiks_status phiks_tucker(phiks_plan_t P, const void* V, void* W, const double* 
   Ctx c{P, (cudaStream_t)stream, {nullptr, nullptr}, 0};
   c.tmp[0] = (double*)((char*)P->ws + (size_t)N * 8);
   c.tmp[1] = c.tmp[0] + N;
-  if (P->dtype != PHIKS_FP64) tc_bind_workspace(P->tc, (char*)P->ws + 3 * (size_t)N * 8);
   const bool f32 = P->dtype != PHIKS_FP64;
+  Mats M;
+  for (int mu = 0; mu < P->d; ++mu) {
+    M.L[mu] = L[mu];
+    M.B[mu] = nullptr;
+  }
+  if (f32) {
+    uintptr_t t = (uintptr_t)((char*)P->ws + 3 * (size_t)N * 8);
+    tc_bind_workspace(P->tc, (void*)((t + 1023) & ~(uintptr_t)1023));
+    for (int mu = 0; mu < P->d; ++mu) {
+      uint8_t* dst = P->tucker_tcb + P->tcb_off[mu];
+      CK(tc_prepare_b(P->dtype, L[mu], (int)P->n[mu], dst, c.st));
+      M.B[mu] = dst;
+    }
+  }
   Epi e = make_epi();
   e.nout = 1;
   e.out[0] = (double*)W;
   e.out_f32mask = f32 ? 1 : 0;
   e.b[0] = 1.0;
-  return tucker(c, plain(V, f32), L, nullptr, &e);
+  return tucker(c, plain(V, f32), M, &e);
 }
 
 phiks_status phiks_expm(int batch, int n, const double* X, double* E, void* stream) {

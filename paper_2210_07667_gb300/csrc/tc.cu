@@ -1,0 +1,656 @@
+// Tensor-core (tcgen05 / TMEM / TMA) mu-mode products for the split-precision
+// dtypes.  See tc.cuh for the data flow.
+//
+// One pass computes D[m, i] = sum_k X[k, m] L[i, k] for the unfolding X (n x M2,
+// column-major, the contracted mode contiguous) of the current tensor: M = 128
+// rows of X^T per tile, N = n_pad (all of L's rows), K = n in 128-byte chunks.
+// Both operands are K-major in shared memory with the 128-byte swizzle, which
+// is what TMA writes for a box whose inner extent is 128 bytes.
+//
+// Split products (FP32 accumulation in TMEM):
+//   TF32    D = hi(X) hi(L)                         one plane per operand
+//   TF32X3  D = hi hi + hi lo + lo hi, hi/lo tf32   two planes per operand
+//   BF16X3  D = hi hi + hi lo + lo hi, hi/lo bf16   two planes per operand
+//
+// CTA roles (192 threads): warp 0 issues TMA loads, warp 1 owns TMEM and
+// issues the MMAs (one elected lane), warps 2..5 drain TMEM (warp w reads TMEM
+// lanes 32 (w % 4) .. +31) and store.  Two TMEM accumulators alternate so the
+// epilogue of one tile overlaps the MMAs of the next.  Every mbarrier wait is
+// bounded (about one second); a wait that gives up records a code in a device
+// status word and the CTA unwinds, still freeing its TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "tc.cuh"
+
+namespace phiks {
+
+namespace {
+
+thread_local std::string g_tc_err;
+
+constexpr int BM = 128;
+constexpr int NTHREADS = 192;
+constexpr uint64_t kWaitNs = 1000000000ull;  // bounded waits: 1 s
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of `parity`; false (and *status set to `code`)
+// after about a second or as soon as another role has failed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, int code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (*(volatile int*)status != 0) return false;
+      if (globaltimer() - t0 > kWaitNs) {
+        atomicCAS(status, 0, code);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes in groups of 8 (stride 1024 bytes between groups).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulator, A/B format `fmt` (BF16 = 1,
+// TF32 = 2), both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_make(int fmt, int n) {
+  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t acc) {
+  if (KIND == 0) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Split of one FP32 value into the dtype's planes, in FP32 arithmetic
+// (x - hi is exact in FP32 for both hi formats).
+template <int KIND, int NP>
+__device__ __forceinline__ void split_store_f(void* p0, void* p1, int64_t idx, float x) {
+  if (KIND == 0) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+    ((__nv_bfloat16*)p0)[idx] = hi;
+    if (NP == 2) ((__nv_bfloat16*)p1)[idx] = __float2bfloat16_rn(x - __bfloat162float(hi));
+  } else {
+    const float hi = tf32_rna(x);
+    ((float*)p0)[idx] = hi;
+    if (NP == 2) ((float*)p1)[idx] = tf32_rna(x - hi);
+  }
+}
+
+// Split of one FP64 value (inputs and the small exponentials): hi from the
+// double, lo from the exact double residual.
+template <int KIND, int NP>
+__device__ __forceinline__ void split_store(void* p0, void* p1, int64_t idx, double x) {
+  if (KIND == 0) {
+    const __nv_bfloat16 hi = __double2bfloat16(x);
+    ((__nv_bfloat16*)p0)[idx] = hi;
+    if (NP == 2) ((__nv_bfloat16*)p1)[idx] = __double2bfloat16(x - (double)__bfloat162float(hi));
+  } else {
+    const float hi = tf32_rna((float)x);
+    ((float*)p0)[idx] = hi;
+    if (NP == 2) ((float*)p1)[idx] = tf32_rna((float)(x - (double)hi));
+  }
+}
+
+// ---------------------------------------------------------------------------
+struct GemmParams {
+  int n;          // contraction length and output columns
+  int n_pad;      // n rounded up to 16
+  int64_t M2;     // N / n
+  int nk;         // 128-byte K chunks
+  int num_tiles;  // ceil(M2 / 128)
+  int stages;
+  int tmem_cols;
+  int last;       // 0: write planes for the next pass; 1: final epilogue
+  void* out0;
+  void* out1;
+  Epi epi;
+  int* status;
+};
+
+template <int KIND, int NP>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
+                   const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1,
+                   GemmParams P) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int S = P.stages;
+  const uint32_t a_plane = BM * 128;                 // bytes of one A plane per stage
+  const uint32_t b_plane = (uint32_t)P.n_pad * 128;  // bytes of one B plane per stage
+  const uint32_t stage_bytes = NP * (a_plane + b_plane);
+  uint64_t* full = (uint64_t*)(smem + (size_t)S * stage_bytes);
+  uint64_t* empty = full + S;
+  uint64_t* tfull = empty + S;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4 * 32);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(P.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < P.num_tiles && ok; t += gridDim.x) {
+        const int m0 = t * BM;
+        for (int kc = 0; kc < P.nk && ok; ++kc) {
+          if (!mbar_wait(&empty[s], ph ^ 1, P.status, 1)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + (size_t)s * stage_bytes;
+          mbar_arrive_expect_tx(&full[s], stage_bytes);
+          const int x = kc * (128 / (KIND == 0 ? 2 : 4));
+          tma_load_2d(st, &mapA0, &full[s], x, m0);
+          if (NP == 2) tma_load_2d(st + a_plane, &mapA1, &full[s], x, m0);
+          tma_load_2d(st + NP * a_plane, &mapB0, &full[s], x, 0);
+          if (NP == 2) tma_load_2d(st + NP * a_plane + b_plane, &mapB1, &full[s], x, 0);
+          if (++s == S) {
+            s = 0;
+            ph ^= 1;
+          }
+        }
+      }
+      // let the copies already issued land before the CTA may leave
+      for (int k = 0; k < S; ++k) {
+        if (--s < 0) {
+          s = S - 1;
+          ph ^= 1;
+        }
+        (void)mbar_wait(&full[s], ph, P.status, 0);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_make(KIND == 0 ? 1 : 2, P.n_pad);
+      int s = 0;
+      uint32_t ph = 0;
+      int buf = 0;
+      uint32_t aph = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < P.num_tiles && ok; t += gridDim.x) {
+        if (!mbar_wait(&tempty[buf], aph ^ 1, P.status, 2)) break;
+        tc_fence_after();
+        const uint32_t dtm = tmem_base + (uint32_t)(buf * P.n_pad);
+        for (int kc = 0; kc < P.nk; ++kc) {
+          if (!mbar_wait(&full[s], ph, P.status, 3)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_u32(smem + (size_t)s * stage_bytes);
+          const uint32_t a0 = st, a1 = st + a_plane;
+          const uint32_t b0 = st + NP * a_plane, b1 = b0 + b_plane;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {  // 4 x 32-byte K steps per 128-byte chunk
+            const uint32_t off = kk * 32;
+            const uint32_t acc = (kc | kk) != 0;
+            umma<KIND>(dtm, sdesc_sw128(a0 + off), sdesc_sw128(b0 + off), idesc, acc);
+            if (NP == 2) {
+              umma<KIND>(dtm, sdesc_sw128(a0 + off), sdesc_sw128(b1 + off), idesc, 1);
+              umma<KIND>(dtm, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, 1);
+            }
+          }
+          umma_commit(&empty[s]);
+          if (++s == S) {
+            s = 0;
+            ph ^= 1;
+          }
+        }
+        if (!ok) break;
+        umma_commit(&tfull[buf]);
+        if (++buf == 2) {
+          buf = 0;
+          aph ^= 1;
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int row = q * 32 + lane;
+    int buf = 0;
+    uint32_t aph = 0;
+    for (int t = blockIdx.x; t < P.num_tiles; t += gridDim.x) {
+      if (!mbar_wait(&tfull[buf], aph, P.status, 4)) break;
+      tc_fence_after();
+      const int64_t col = (int64_t)t * BM + row;
+      const bool valid = col < P.M2;
+      for (int c0 = 0; c0 < P.n; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * P.n_pad + c0), v);
+        if (!valid) continue;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int i = c0 + j;
+          if (i >= P.n) break;
+          const int64_t idx = col + P.M2 * (int64_t)i;
+          if (!P.last) {
+            split_store_f<KIND, NP>(P.out0, P.out1, idx, v[j]);
+          } else {
+            const Epi& e = P.epi;
+            const double res = (double)v[j];
+            double sv[kMaxSrc];
+            for (int m = 0; m < e.nsrc; ++m)
+              sv[m] = ((e.src_f32mask >> m) & 1) ? (double)((const float*)e.src[m])[idx]
+                                                 : e.src[m][idx];
+            for (int tt = 0; tt < e.nout; ++tt) {
+              double o = e.b[tt] * res;
+              for (int m = 0; m < e.nsrc; ++m)
+                if (e.a[tt][m] != 0.0) o = fma(e.a[tt][m], sv[m], o);
+              if ((e.out_f32mask >> tt) & 1) ((float*)e.out[tt])[idx] = (float)o;
+              else e.out[tt][idx] = o;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[buf]);
+      if (++buf == 2) {
+        buf = 0;
+        aph ^= 1;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(P.tmem_cols)
+                 : "memory");
+  }
+}
+
+// x = sum_m coef_m src_m (float or double sources) split into planes.
+template <int KIND, int NP>
+__global__ void tc_split_kernel(Combo in, int64_t N, void* p0, void* p1) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    double x = 0.0;
+    for (int m = 0; m < in.nsrc; ++m) {
+      const double v = ((in.f32mask >> m) & 1) ? (double)((const float*)in.src[m])[idx] : in.src[m][idx];
+      x = fma(in.coef[m], v, x);
+    }
+    split_store<KIND, NP>(p0, p1, idx, x);
+  }
+}
+
+// B planes of an FP64 column-major n x n matrix: plane[i * n_pad + k] from L[i, k].
+template <int KIND, int NP>
+__global__ void tc_prep_b_kernel(const double* L, int n, int n_pad, void* p0, void* p1) {
+  const int64_t tot = (int64_t)n_pad * n_pad;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n_pad), k = (int)(e % n_pad);
+    const double x = (i < n && k < n) ? L[i + (int64_t)n * k] : 0.0;
+    split_store<KIND, NP>(p0, p1, e, x);
+  }
+}
+
+int planes_of(int dtype) { return dtype == PHIKS_TF32 ? 1 : 2; }
+int elt_of(int dtype) { return dtype == PHIKS_BF16X3 ? 2 : 4; }
+int pad16(int n) { return (n + 15) / 16 * 16; }
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                              CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                              CUtensorMapFloatOOBfill);
+
+EncodeFn g_encode = nullptr;
+
+bool get_encode() {
+  if (g_encode) return true;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+          cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return false;
+  g_encode = (EncodeFn)fn;
+  return true;
+}
+
+// 2D map over a row-major (rows x inner) array, box {128 bytes of inner, box_rows}.
+bool make_map(CUtensorMap* m, int dtype, const void* base, uint64_t inner, uint64_t rows,
+              uint32_t box_rows) {
+  const int elt = elt_of(dtype);
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {inner * (uint64_t)elt};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / elt), box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUtensorMapDataType t =
+      dtype == PHIKS_BF16X3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  CUresult r = g_encode(m, t, 2, const_cast<void*>(base), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+struct TcState {
+  int dtype = 0;
+  int d = 0;
+  int64_t n[PHIKS_MAX_D] = {0};
+  int64_t N = 0;
+  int* status = nullptr;  // device
+  uint8_t* ws = nullptr;
+  int smem_optin = 0;
+};
+
+size_t tc_workspace_bytes(int64_t N) {
+  // two plane sets of up to 2 planes x 4 bytes, each rounded to 1 KiB
+  const size_t plane = ((size_t)N * 4 + 1023) / 1024 * 1024;
+  return 4 * plane + 1024;
+}
+
+phiks_status tc_create(TcState** out, int dtype, int d, const int64_t* n, int64_t N) {
+  *out = nullptr;
+  for (int mu = 0; mu < d; ++mu) {
+    if (n[mu] > kTcMaxN) {
+      g_tc_err = "tensor-core path supports n_mu <= 256";
+      return PHIKS_ERR_UNSUPPORTED;
+    }
+    const int elt = elt_of(dtype);
+    if ((n[mu] * elt) % 16 != 0) {
+      g_tc_err = "tensor-core path needs n_mu * element size to be a multiple of 16 bytes";
+      return PHIKS_ERR_UNSUPPORTED;
+    }
+  }
+  if (!get_encode()) {
+    g_tc_err = "cuTensorMapEncodeTiled is not available";
+    return PHIKS_ERR_UNSUPPORTED;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess || prop.major < 10) {
+    g_tc_err = "tensor-core path needs an sm_100-class device";
+    return PHIKS_ERR_UNSUPPORTED;
+  }
+  TcState* s = new TcState;
+  s->dtype = dtype;
+  s->d = d;
+  for (int mu = 0; mu < d; ++mu) s->n[mu] = n[mu];
+  s->N = N;
+  s->smem_optin = (int)prop.sharedMemPerBlockOptin;
+  if (cudaMalloc(&s->status, sizeof(int)) != cudaSuccess ||
+      cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess) {
+    delete s;
+    g_tc_err = "status word allocation failed";
+    return PHIKS_ERR_OOM;
+  }
+  *out = s;
+  return PHIKS_OK;
+}
+
+void tc_destroy(TcState* s) {
+  if (!s) return;
+  cudaFree(s->status);
+  delete s;
+}
+
+const char* tc_last_error() { return g_tc_err.c_str(); }
+
+void tc_bind_workspace(TcState* s, void* ws) { s->ws = (uint8_t*)ws; }
+
+size_t tc_bplanes_bytes(int dtype, int n) {
+  const size_t p = (size_t)pad16(n) * pad16(n) * elt_of(dtype);
+  return planes_of(dtype) * ((p + 1023) / 1024 * 1024);
+}
+
+cudaError_t tc_prepare_b(int dtype, const double* L, int n, void* dst, cudaStream_t st) {
+  const int np = pad16(n);
+  const size_t p = ((size_t)np * np * elt_of(dtype) + 1023) / 1024 * 1024;
+  uint8_t* p0 = (uint8_t*)dst;
+  uint8_t* p1 = p0 + p;
+  const int64_t tot = (int64_t)np * np;
+  const int grid = (int)std::min<int64_t>((tot + 255) / 256, 1024);
+  count_launch();
+  switch (dtype) {
+    case PHIKS_BF16X3: tc_prep_b_kernel<0, 2><<<grid, 256, 0, st>>>(L, n, np, p0, p1); break;
+    case PHIKS_TF32X3: tc_prep_b_kernel<1, 2><<<grid, 256, 0, st>>>(L, n, np, p0, p1); break;
+    default: tc_prep_b_kernel<1, 1><<<grid, 256, 0, st>>>(L, n, np, p0, nullptr); break;
+  }
+  return cudaGetLastError();
+}
+
+namespace {
+
+template <int KIND, int NP>
+cudaError_t run_gemm(TcState* s, const CUtensorMap* mA, const CUtensorMap* mB, GemmParams& P,
+                     cudaStream_t st) {
+  const uint32_t stage_bytes = NP * (BM * 128 + (uint32_t)P.n_pad * 128);
+  const size_t extra = 1024 + 64 * 8 + 64;
+  int stages = (int)((size_t)(s->smem_optin - extra) / stage_bytes);
+  if (stages > 4) stages = 4;
+  if (stages < 2) return cudaErrorInvalidConfiguration;
+  P.stages = stages;
+  const size_t smem = (size_t)stages * stage_bytes + extra;
+  auto kern = tc_gemm_kernel<KIND, NP>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int grid = P.num_tiles < 152 ? P.num_tiles : 152;
+  count_launch();
+  kern<<<grid, NTHREADS, smem, st>>>(mA[0], mA[1], mB[0], mB[1], P);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t tc_tucker(TcState* s, const Combo& in, const void* const* Bp, const Epi& epi,
+                      cudaStream_t st) {
+  const int dtype = s->dtype;
+  const int NP = planes_of(dtype), elt = elt_of(dtype);
+  const int64_t N = s->N;
+  const size_t plane = ((size_t)N * 4 + 1023) / 1024 * 1024;
+  uint8_t* set[2][2] = {{s->ws, s->ws + plane}, {s->ws + 2 * plane, s->ws + 3 * plane}};
+  // split the (combined) input into planes: natural layout, mode 1 contiguous
+  {
+    const int grid = (int)std::min<int64_t>((N + 255) / 256, 152 * 8);
+    count_launch();
+    if (dtype == PHIKS_BF16X3) tc_split_kernel<0, 2><<<grid, 256, 0, st>>>(in, N, set[0][0], set[0][1]);
+    else if (dtype == PHIKS_TF32X3) tc_split_kernel<1, 2><<<grid, 256, 0, st>>>(in, N, set[0][0], set[0][1]);
+    else tc_split_kernel<1, 1><<<grid, 256, 0, st>>>(in, N, set[0][0], nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  int cur = 0;
+  for (int mu = 0; mu < s->d; ++mu) {
+    const int n = (int)s->n[mu], np = pad16(n);
+    const int64_t M2 = N / n;
+    CUtensorMap mA[2], mB[2];
+    std::memset(mA, 0, sizeof mA);
+    std::memset(mB, 0, sizeof mB);
+    const size_t bplane = ((size_t)np * np * elt + 1023) / 1024 * 1024;
+    for (int p = 0; p < NP; ++p) {
+      if (!make_map(&mA[p], dtype, set[cur][p], (uint64_t)n, (uint64_t)M2, BM)) {
+        g_tc_err = "tensor map for the A operand failed";
+        return cudaErrorInvalidValue;
+      }
+      if (!make_map(&mB[p], dtype, (const uint8_t*)Bp[mu] + p * bplane, (uint64_t)np, (uint64_t)np,
+                    (uint32_t)np)) {
+        g_tc_err = "tensor map for the B operand failed";
+        return cudaErrorInvalidValue;
+      }
+    }
+    if (NP == 1) {
+      mA[1] = mA[0];
+      mB[1] = mB[0];
+    }
+    GemmParams P;
+    std::memset(&P, 0, sizeof P);
+    P.n = n;
+    P.n_pad = np;
+    P.M2 = M2;
+    P.nk = (n * elt + 127) / 128;
+    P.num_tiles = (int)((M2 + BM - 1) / BM);
+    int cols = 32;
+    while (cols < 2 * np) cols <<= 1;
+    P.tmem_cols = cols;
+    P.last = (mu == s->d - 1);
+    P.out0 = set[1 - cur][0];
+    P.out1 = set[1 - cur][1];
+    P.epi = epi;
+    P.status = s->status;
+    cudaError_t e;
+    if (dtype == PHIKS_BF16X3) e = run_gemm<0, 2>(s, mA, mB, P, st);
+    else if (dtype == PHIKS_TF32X3) e = run_gemm<1, 2>(s, mA, mB, P, st);
+    else e = run_gemm<1, 1>(s, mA, mB, P, st);
+    if (e != cudaSuccess) return e;
+    cur = 1 - cur;
+  }
+  return cudaSuccess;
+}
+
+int tc_read_status(TcState* s, cudaStream_t st) {
+  int h = 0;
+  if (cudaMemcpyAsync(&h, s->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return -1;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+  if (h) cudaMemsetAsync(s->status, 0, sizeof(int), st);
+  return h;
+}
+
+}  // namespace phiks

@@ -1,0 +1,95 @@
+"""Split-precision tensor-core path (tcgen05 / TMEM / TMA) against the FP64
+oracle.
+
+Tolerances (relative infinity-norm), set from the representation error of
+each split and rounding of FP32 intermediates:
+  TF32    one tf32 product (11-bit significands)            5e-3
+  TF32X3  hi*hi + hi*lo + lo*hi with tf32 hi/lo (~22 bits)   2e-5
+  BF16X3  hi*hi + hi*lo + lo*hi with bf16 hi/lo (~16 bits)   2e-4
+for one Tucker operator, and 4x those for a whole phiks call (quadrature,
+squaring, FP64 combination).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2210_07667_gb300 as pk  # noqa: E402
+import workloads as wk  # noqa: E402
+from oracle import dense, kron, phiks_ref  # noqa: E402
+
+from gpu_util import dev, rel_inf, run_workload  # noqa: E402
+
+TOL = {pk.PHIKS_TF32: 5e-3, pk.PHIKS_TF32X3: 2e-5, pk.PHIKS_BF16X3: 2e-4}
+DTYPES = [pk.PHIKS_BF16X3, pk.PHIKS_TF32X3, pk.PHIKS_TF32]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pk.load(build_if_missing=True)
+
+
+def _tucker(dims, dtype, seed=0):
+    rng = np.random.default_rng(seed)
+    A = [np.eye(m) for m in dims]
+    plan = pk.Plan(A, dtype)
+    N = int(np.prod(dims))
+    V = rng.standard_normal(N)
+    Ls = [rng.standard_normal((m, m)) / np.sqrt(m) for m in dims]
+    W = torch.empty(N, device="cuda", dtype=torch.float32)
+    pk.phiks_tucker(plan.handle, dev(V, torch.float32), W, [dev(L.ravel(order="F")) for L in Ls])
+    pk.phiks_device_status(plan.handle)
+    ref = kron.vec(kron.tucker(kron.unvec(V.astype(np.float32).astype(np.float64), dims), Ls))
+    err = rel_inf(W.cpu().numpy(), ref)
+    plan.close()
+    return err
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_tucker_single_tile(dtype):
+    err = _tucker((32, 32), dtype)
+    print("tucker 32x32 dtype %d err %.3e" % (dtype, err))
+    assert err < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dims", [(64, 48, 40), (128, 16, 24), (96, 200), (16, 16, 16, 8), (256, 130)])
+def test_tucker_shapes(dtype, dims):
+    if dtype == pk.PHIKS_BF16X3 and any(m % 8 for m in dims):
+        pytest.skip("bf16 planes need n_mu % 8 == 0")
+    if any(m % 4 for m in dims):
+        pytest.skip("tf32 planes need n_mu % 4 == 0")
+    err = _tucker(dims, dtype, seed=len(dims))
+    print("tucker %s dtype %d err %.3e" % (dims, dtype, err))
+    assert err < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_same_vector_split(dtype):
+    A = [wk.fd_adr_dirichlet(m, 1.0, a, 0.3) for m, a in zip((48, 40, 32), (2.0, -3.0, 1.0))]
+    N = 48 * 40 * 32
+    v = wk.normal(3, N).astype(np.float32).astype(np.float64)
+    wl = wk.Workload("t", A, 2e-4, 3, "same", 2, [v])
+    out, plan = run_workload(wl, dtype=dtype)
+    pk.phiks_device_status(plan.handle)
+    s, q, T, _ = plan.last_params()
+    ref = phiks_ref.same(A, 2e-4, v, 3, s, q, nscales=2)
+    errs = [rel_inf(out[k], ref[k]) for k in range(out.shape[0])]
+    print("same dtype %d (s,q)=(%d,%d) errs %s" % (dtype, s, q, ["%.2e" % e for e in errs]))
+    assert max(errs) < 4 * TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_lincomb_split(dtype):
+    wl = wk.adr3d_lincomb(p=3, dims=(32, 24, 40), nscales=2)
+    vs = [v.astype(np.float32).astype(np.float64) for v in wl.vs]
+    w2 = wk.Workload("t", wl.A, wl.tau, 3, "lincomb", 2, vs)
+    out, plan = run_workload(w2, dtype=dtype)
+    pk.phiks_device_status(plan.handle)
+    ex = [dense.lincomb(wl.A, wl.tau, vs, 2.0 ** -L) for L in range(2)]
+    errs = [rel_inf(out[L], ex[L]) for L in range(2)]
+    print("lincomb dtype %d errs %s" % (dtype, ["%.2e" % e for e in errs]))
+    assert max(errs) < 4 * TOL[dtype]
