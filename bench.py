@@ -303,6 +303,100 @@ def run_phiks(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+PRECISION_DTYPES = ["fp64", "tf32", "tf32x3", "bf16x3"]
+# relative accuracy asked of the selection per dtype (tol = rel * ||v||)
+PRECISION_TOL = {"fp64": None, "tf32": 1e-4, "tf32x3": 1e-7, "bf16x3": 1e-6}
+
+
+def run_precision(args):
+    """The precision form: d = 3, n = 128 (N = 2,097,152), Chebyshev D^2
+    Dirichlet (tau = 5e-7) or FD Laplacian (tau = 1e-4), phi_1..phi_3 of 8
+    N(0,1) vectors per step, every dtype timed and compared with the FP64 GPU
+    result."""
+    import torch
+    import paper_2210_07667_gb300 as pk
+    pk.load(build_if_missing=True)
+    torch.cuda.set_device(0)
+    tau = 5e-7 if args.variant == "cheb" else 1e-4
+    wl = wk.cheb3d_same(n=args.n, nrhs=8, tau=tau, variant=args.variant)
+    N, p = wl.N, wl.p
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, device="cuda", dtype=torch.uint8)
+    results = {}
+    ref_out = None
+    dtypes = PRECISION_DTYPES if args.dtype == "all" else ["fp64", args.dtype]
+    for name in dtypes:
+        dt = pk.DTYPES[name]
+        tdt = torch.float64 if name == "fp64" else torch.float32
+        plan = pk.Plan(wl.A, dt)
+        vs = [torch.from_numpy(v).to(device="cuda", dtype=tdt) for v in wl.vs]
+        outs = [torch.empty(p * N, device="cuda", dtype=tdt) for _ in vs]
+        norms = [float(np.linalg.norm(v.astype(np.float32) if name != "fp64" else v)) for v in wl.vs]
+        kw = dict(skip_phi0=1, no_cache=1)
+        if PRECISION_TOL[name] is not None:
+            kw["tol"] = PRECISION_TOL[name] * max(norms)
+        opts = [pk.make_options(vnorms=[nv], **kw) for nv in norms]
+
+        def step():
+            for v, o, op in zip(vs, outs, opts):
+                pk.phiks_apply_ex(plan.handle, wl.tau, p, [v], o, stream, opts=op)
+
+        with torch.cuda.stream(stream):
+            for _ in range(max(args.warmup, 3)):
+                step()
+        torch.cuda.synchronize()
+        pk.phiks_device_status(plan.handle, stream)
+        s_, q_, T_, tk = plan.last_params()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        l0 = pk.phiks_kernel_launches()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+                ev[k][0].record(stream)
+                step()
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        launches = pk.phiks_kernel_launches() - l0
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        pk.phiks_device_status(plan.handle, stream)
+        pk.phiks_profile_enable(plan.handle, True)
+        with torch.cuda.stream(stream):
+            step()
+        kms, kl, kfl = pk.phiks_profile_read(plan.handle)
+        pk.phiks_profile_enable(plan.handle, False)
+        out = torch.stack(outs).double().cpu().numpy()
+        if name == "fp64":
+            ref_out = out
+            err = 0.0
+        else:
+            err = max(float(np.abs(out[k] - ref_out[k]).max() / np.abs(ref_out[k]).max())
+                      for k in range(len(outs)))
+        results[name] = {"ms_per_step": ms, "phi_actions_per_s": 3 * len(vs) / (ms * 1e-3),
+                         "rel_err_vs_fp64": err, "s": s_, "q": q_, "tuckers_per_call": tk,
+                         "tucker_tflops_algorithmic": kfl / max(kms, 1e-9) / 1e9,
+                         "tucker_ms_per_call": kms / len(vs), "gpu_launches_per_step": launches // args.steps}
+        plan.close()
+    base = results["fp64"]["ms_per_step"]
+    for r in results.values():
+        r["speedup_vs_fp64"] = base / r["ms_per_step"]
+    head = args.dtype if args.dtype != "all" else "bf16x3"
+    h = results[head]
+    line = {"metric": METRIC, "value": h["phi_actions_per_s"], "unit": "phi-actions/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": h["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"bf16x3": "bf16x3 (fp32 accumulate)", "tf32": "tf32", "tf32x3": "tf32x3",
+                      "fp64": "f64"}[head],
+            "data": "synthetic",
+            "config": {"workload": wl.name, "d": 3, "n": [args.n] * 3, "N": N, "p": 3, "mode": "same",
+                       "skip_phi0": True, "nrhs": 8, "tau": tau, "variant": args.variant,
+                       "l2": "flushed before every timed step (256 MiB write, untimed)"},
+            "rel_err_vs_fp64": h["rel_err_vs_fp64"], "per_dtype": results}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -310,9 +404,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="phiks", choices=["phiks", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", default="adr3d", choices=["adr3d", "precision"],
+                    help="adr3d: the headline FP64 workload; precision: the split-dtype form")
+    ap.add_argument("--dtype", default="all", choices=["all"] + PRECISION_DTYPES)
+    ap.add_argument("--variant", default="cheb", choices=["cheb", "fd"])
+    ap.add_argument("--n", type=int, default=128)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "precision":
+        return run_precision(args)
     return run_phiks(args)
 
 
