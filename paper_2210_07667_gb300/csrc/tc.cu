@@ -3,7 +3,8 @@
 //
 // One pass computes D[m, i] = sum_k X[k, m] L[i, k] for the unfolding X (n x M2,
 // column-major, the contracted mode contiguous) of the current tensor: M = 128
-// rows of X^T per tile, N = n_pad (all of L's rows), K = n in 128-byte chunks.
+// rows of X^T per tile, N = one N tile of L's rows (all n_pad of them when
+// n_pad <= 256, else ceil(n_pad / 256) equal tiles), K = n in 128-byte chunks.
 // Both operands are K-major in shared memory with the 128-byte swizzle, which
 // is what TMA writes for a box whose inner extent is 128 bytes.
 //
@@ -208,9 +209,11 @@ __device__ __forceinline__ void split_store(void* p0, void* p1, int64_t idx, dou
 struct GemmParams {
   int n;          // contraction length and output columns
   int n_pad;      // n rounded up to 16
+  int ntile;      // MMA N: rows of L per tile (multiple of 16, <= 256)
+  int n_ntiles;   // N tiles per row block
   int64_t M2;     // N / n
   int nk;         // 128-byte K chunks
-  int num_tiles;  // ceil(M2 / 128)
+  int num_tiles;  // ceil(M2 / 128) * n_ntiles
   int stages;
   int tmem_cols;
   int last;       // 0: write planes for the next pass; 1: final epilogue
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int S = P.stages;
   const uint32_t a_plane = BM * 128;                 // bytes of one A plane per stage
-  const uint32_t b_plane = (uint32_t)P.n_pad * 128;  // bytes of one B plane per stage
+  const uint32_t b_plane = (uint32_t)P.ntile * 128;  // bytes of one B plane per stage
   const uint32_t stage_bytes = NP * (a_plane + b_plane);
   uint64_t* full = (uint64_t*)(smem + (size_t)S * stage_bytes);
   uint64_t* empty = full + S;
@@ -271,7 +274,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t ph = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < P.num_tiles && ok; t += gridDim.x) {
-        const int m0 = t * BM;
+        const int m0 = (t / P.n_ntiles) * BM;
+        const int r0 = (t % P.n_ntiles) * P.ntile;
         for (int kc = 0; kc < P.nk && ok; ++kc) {
           if (!mbar_wait(&empty[s], ph ^ 1, P.status, 1)) {
             ok = false;
@@ -282,8 +286,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int x = kc * (128 / (KIND == 0 ? 2 : 4));
           tma_load_2d(st, &mapA0, &full[s], x, m0);
           if (NP == 2) tma_load_2d(st + a_plane, &mapA1, &full[s], x, m0);
-          tma_load_2d(st + NP * a_plane, &mapB0, &full[s], x, 0);
-          if (NP == 2) tma_load_2d(st + NP * a_plane + b_plane, &mapB1, &full[s], x, 0);
+          tma_load_2d(st + NP * a_plane, &mapB0, &full[s], x, r0);
+          if (NP == 2) tma_load_2d(st + NP * a_plane + b_plane, &mapB1, &full[s], x, r0);
           if (++s == S) {
             s = 0;
             ph ^= 1;
@@ -302,7 +306,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = idesc_make(KIND == 0 ? 1 : 2, P.n_pad);
+      const uint32_t idesc = idesc_make(KIND == 0 ? 1 : 2, P.ntile);
       int s = 0;
       uint32_t ph = 0;
       int buf = 0;
@@ -311,7 +315,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int t = blockIdx.x; t < P.num_tiles && ok; t += gridDim.x) {
         if (!mbar_wait(&tempty[buf], aph ^ 1, P.status, 2)) break;
         tc_fence_after();
-        const uint32_t dtm = tmem_base + (uint32_t)(buf * P.n_pad);
+        const uint32_t dtm = tmem_base + (uint32_t)(buf * P.ntile);
         for (int kc = 0; kc < P.nk; ++kc) {
           if (!mbar_wait(&full[s], ph, P.status, 3)) {
             ok = false;
@@ -354,15 +358,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int t = blockIdx.x; t < P.num_tiles; t += gridDim.x) {
       if (!mbar_wait(&tfull[buf], aph, P.status, 4)) break;
       tc_fence_after();
-      const int64_t col = (int64_t)t * BM + row;
+      const int64_t col = (int64_t)(t / P.n_ntiles) * BM + row;
+      const int r0 = (t % P.n_ntiles) * P.ntile;
       const bool valid = col < P.M2;
-      for (int c0 = 0; c0 < P.n; c0 += 16) {
+      const int cend = P.n - r0 < P.ntile ? P.n - r0 : P.ntile;
+      for (int c0 = 0; c0 < cend; c0 += 16) {
         float v[16];
-        tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * P.n_pad + c0), v);
+        tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * P.ntile + c0), v);
         if (!valid) continue;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const int i = c0 + j;
+          const int i = r0 + c0 + j;
           if (i >= P.n) break;
           const int64_t idx = col + P.M2 * (int64_t)i;
           if (!P.last) {
@@ -403,17 +409,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
-// x = sum_m coef_m src_m (float or double sources) split into planes.
+// x = sum_m coef_m src_m (float or double sources) split into planes.  The
+// combination is formed in FP64 only when it has more than one term or a
+// coefficient other than one; the split itself runs in FP32 (the planes carry
+// at most 22 significant bits, FP32 holds 24).
 template <int KIND, int NP>
 __global__ void tc_split_kernel(Combo in, int64_t N, void* p0, void* p1) {
+  const bool plain = in.nsrc == 1 && in.coef[0] == 1.0;
+  const bool f32 = in.f32mask & 1;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    double x = 0.0;
-    for (int m = 0; m < in.nsrc; ++m) {
-      const double v = ((in.f32mask >> m) & 1) ? (double)((const float*)in.src[m])[idx] : in.src[m][idx];
-      x = fma(in.coef[m], v, x);
+    float xf;
+    if (plain) {
+      xf = f32 ? ((const float*)in.src[0])[idx] : (float)in.src[0][idx];
+    } else {
+      double x = 0.0;
+      for (int m = 0; m < in.nsrc; ++m) {
+        const double v =
+            ((in.f32mask >> m) & 1) ? (double)((const float*)in.src[m])[idx] : in.src[m][idx];
+        x = fma(in.coef[m], v, x);
+      }
+      xf = (float)x;
     }
-    split_store<KIND, NP>(p0, p1, idx, x);
+    split_store_f<KIND, NP>(p0, p1, idx, xf);
   }
 }
 
@@ -490,7 +508,7 @@ phiks_status tc_create(TcState** out, int dtype, int d, const int64_t* n, int64_
   *out = nullptr;
   for (int mu = 0; mu < d; ++mu) {
     if (n[mu] > kTcMaxN) {
-      g_tc_err = "tensor-core path supports n_mu <= 256";
+      g_tc_err = "tensor-core path supports n_mu <= 1024";
       return PHIKS_ERR_UNSUPPORTED;
     }
     const int elt = elt_of(dtype);
@@ -562,7 +580,7 @@ namespace {
 template <int KIND, int NP>
 cudaError_t run_gemm(TcState* s, const CUtensorMap* mA, const CUtensorMap* mB, GemmParams& P,
                      cudaStream_t st) {
-  const uint32_t stage_bytes = NP * (BM * 128 + (uint32_t)P.n_pad * 128);
+  const uint32_t stage_bytes = NP * (BM * 128 + (uint32_t)P.ntile * 128);
   const size_t extra = 1024 + 64 * 8 + 64;
   int stages = (int)((size_t)(s->smem_optin - extra) / stage_bytes);
   if (stages > 4) stages = 4;
@@ -572,6 +590,8 @@ cudaError_t run_gemm(TcState* s, const CUtensorMap* mA, const CUtensorMap* mB, G
   auto kern = tc_gemm_kernel<KIND, NP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  // With 512 TMEM columns the shared memory (>= 4 x 34 KiB) already keeps a
+  // second CTA off the SM, so co-resident CTAs never oversubscribe TMEM.
   int grid = P.num_tiles < 152 ? P.num_tiles : 152;
   count_launch();
   kern<<<grid, NTHREADS, smem, st>>>(mA[0], mA[1], mB[0], mB[1], P);
@@ -601,6 +621,8 @@ cudaError_t tc_tucker(TcState* s, const Combo& in, const void* const* Bp, const 
   for (int mu = 0; mu < s->d; ++mu) {
     const int n = (int)s->n[mu], np = pad16(n);
     const int64_t M2 = N / n;
+    const int nnt = (np + 255) / 256;          // N tiles of at most 256 rows
+    const int ntile = pad16((np + nnt - 1) / nnt);
     CUtensorMap mA[2], mB[2];
     std::memset(mA, 0, sizeof mA);
     std::memset(mB, 0, sizeof mB);
@@ -611,7 +633,7 @@ cudaError_t tc_tucker(TcState* s, const Combo& in, const void* const* Bp, const 
         return cudaErrorInvalidValue;
       }
       if (!make_map(&mB[p], dtype, (const uint8_t*)Bp[mu] + p * bplane, (uint64_t)np, (uint64_t)np,
-                    (uint32_t)np)) {
+                    (uint32_t)ntile)) {
         g_tc_err = "tensor map for the B operand failed";
         return cudaErrorInvalidValue;
       }
@@ -624,11 +646,13 @@ cudaError_t tc_tucker(TcState* s, const Combo& in, const void* const* Bp, const 
     std::memset(&P, 0, sizeof P);
     P.n = n;
     P.n_pad = np;
+    P.ntile = ntile;
+    P.n_ntiles = nnt;
     P.M2 = M2;
     P.nk = (n * elt + 127) / 128;
-    P.num_tiles = (int)((M2 + BM - 1) / BM);
+    P.num_tiles = (int)((M2 + BM - 1) / BM) * nnt;
     int cols = 32;
-    while (cols < 2 * np) cols <<= 1;
+    while (cols < 2 * ntile) cols <<= 1;
     P.tmem_cols = cols;
     P.last = (mu == s->d - 1);
     P.out0 = set[1 - cur][0];

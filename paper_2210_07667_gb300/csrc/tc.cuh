@@ -43,7 +43,7 @@ cudaError_t tc_tucker(TcState* s, const Combo& in, const void* const* Bp, const 
 // flag is cleared by the read).  Synchronises the stream.
 int tc_read_status(TcState* s, cudaStream_t st);
 
-// Largest n_mu the tensor-core path handles.
-constexpr int kTcMaxN = 256;
+// Largest n_mu the tensor-core path handles (N tiles of <= 256 rows beyond 256).
+constexpr int kTcMaxN = 1024;
 
 }  // namespace phiks
