@@ -326,6 +326,8 @@ def run_precision(args):
     results = {}
     ref_out = None
     dtypes = PRECISION_DTYPES if args.dtype == "all" else ["fp64", args.dtype]
+    if args.no_ref:
+        dtypes = [d for d in dtypes if d != "fp64"]
     for name in dtypes:
         dt = pk.DTYPES[name]
         tdt = torch.float64 if name == "fp64" else torch.float32
@@ -370,6 +372,8 @@ def run_precision(args):
         if name == "fp64":
             ref_out = out
             err = 0.0
+        elif ref_out is None:
+            err = None
         else:
             err = max(float(np.abs(out[k] - ref_out[k]).max() / np.abs(ref_out[k]).max())
                       for k in range(len(outs)))
@@ -378,9 +382,10 @@ def run_precision(args):
                          "tucker_tflops_algorithmic": kfl / max(kms, 1e-9) / 1e9,
                          "tucker_ms_per_call": kms / len(vs), "gpu_launches_per_step": launches // args.steps}
         plan.close()
-    base = results["fp64"]["ms_per_step"]
-    for r in results.values():
-        r["speedup_vs_fp64"] = base / r["ms_per_step"]
+    if "fp64" in results:
+        base = results["fp64"]["ms_per_step"]
+        for r in results.values():
+            r["speedup_vs_fp64"] = base / r["ms_per_step"]
     head = args.dtype if args.dtype != "all" else "bf16x3"
     h = results[head]
     line = {"metric": METRIC, "value": h["phi_actions_per_s"], "unit": "phi-actions/s", "n_gpus": 1,
@@ -397,6 +402,123 @@ def run_precision(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+def run_batched(args):
+    """The batched form: uneven-size independent instances (half d = 2 with
+    n_mu in {64..512}, half d = 3 with n_mu in {16..96}), phi_1..phi_3 each.
+    Timed: the whole batch as one CUDA graph over worker streams (split dtype),
+    against the same instances one after another in FP64 on one stream.
+    Small exponentials are cached per instance (fixed step, as in an
+    integrator); their one-time cost is reported separately."""
+    import torch
+    import paper_2210_07667_gb300 as pk
+    pk.load(build_if_missing=True)
+    torch.cuda.set_device(0)
+    insts = wk.batched_instances(args.count)
+    name = "bf16x3" if args.dtype == "all" else args.dtype
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, device="cuda", dtype=torch.uint8)
+    phi_per_step = 3 * len(insts)
+
+    def setup(dname):
+        dt = pk.DTYPES[dname]
+        tdt = torch.float64 if dname == "fp64" else torch.float32
+        rows = []
+        for w in insts:
+            plan = pk.Plan(w.A, dt)
+            v = torch.from_numpy(w.vs[0]).to(device="cuda", dtype=tdt)
+            out = torch.empty(3 * w.N, device="cuda", dtype=tdt)
+            nv = float(np.linalg.norm(w.vs[0].astype(np.float32) if dname != "fp64" else w.vs[0]))
+            kw = dict(skip_phi0=1, vnorms=[nv])
+            if PRECISION_TOL[dname] is not None:
+                kw["tol"] = PRECISION_TOL[dname] * nv
+            rows.append((plan, w.tau, 3, [v], out, pk.make_options(**kw)))
+        return rows
+
+    def inst_tuple(rows):
+        return [(r[0].handle, r[1], r[2], r[3], r[4], r[5]) for r in rows]
+
+    def timed(fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for k in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+                ev[k][0].record(stream)
+                fn()
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+    res = {}
+    # split dtype, batch over worker streams, captured in one CUDA graph
+    t0 = time.perf_counter()
+    rows = setup(name)
+    batch = pk.Batch(args.streams)
+    insts_t = inst_tuple(rows)
+    with torch.cuda.stream(stream):
+        batch.apply(insts_t, stream)      # parameter selection, workspaces, small exponentials
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    with torch.cuda.stream(stream):
+        batch.apply(insts_t, stream)
+    torch.cuda.synchronize()
+    graph = batch.capture(insts_t, stream)
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            batch.launch(graph, stream)
+    torch.cuda.synchronize()
+    l0 = pk.phiks_kernel_launches()
+    ms_graph = timed(lambda: batch.launch(graph, stream), args.steps)
+    tucks = sum(r[0].last_params()[3] for r in rows)
+    for r in rows:
+        pk.phiks_device_status(r[0].handle, stream)
+    out_split = [r[4].double().cpu().numpy() for r in rows]
+    # same instances, split dtype, one stream, no graph
+    def seq(rr):
+        def f():
+            for r in rr:
+                pk.phiks_apply_ex(r[0].handle, r[1], r[2], r[3], r[4], stream, opts=r[5])
+        return f
+    ms_seq = timed(seq(rows), max(1, args.steps // 2))
+    res[name + "_graph"] = {"ms_per_step": ms_graph, "phi_actions_per_s": phi_per_step / (ms_graph * 1e-3),
+                            "streams": args.streams, "tuckers_per_step": tucks,
+                            "first_call_s": setup_s}
+    res[name + "_sequential"] = {"ms_per_step": ms_seq, "phi_actions_per_s": phi_per_step / (ms_seq * 1e-3)}
+    batch.destroy_graph(graph)
+    batch.close()
+    for r in rows:
+        r[0].close()
+    # FP64 reference path, one stream
+    if not args.no_ref:
+        rows64 = setup("fp64")
+        with torch.cuda.stream(stream):
+            seq(rows64)()
+        torch.cuda.synchronize()
+        ms64 = timed(seq(rows64), 1)
+        errs = []
+        for r, o in zip(rows64, out_split):
+            ref = r[4].cpu().numpy()
+            errs.append(float(np.abs(o - ref).max() / np.abs(ref).max()))
+        res["fp64_sequential"] = {"ms_per_step": ms64, "phi_actions_per_s": phi_per_step / (ms64 * 1e-3)}
+        res[name + "_graph"]["rel_err_vs_fp64_max"] = max(errs)
+        res[name + "_graph"]["speedup_vs_fp64"] = ms64 / ms_graph
+        for r in rows64:
+            r[0].close()
+    h = res[name + "_graph"]
+    line = {"metric": METRIC, "value": h["phi_actions_per_s"], "unit": "phi-actions/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": h["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": name,
+            "data": "synthetic",
+            "config": {"workload": "batched_adr_%d_instances" % len(insts), "instances": len(insts),
+                       "d2_n": "64..512 step 32", "d3_n": "16..96 step 8", "p": 3, "skip_phi0": True,
+                       "small_exponentials": "cached per instance",
+                       "l2": "flushed before every timed step (256 MiB write, untimed)"},
+            "per_variant": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,16 +526,21 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="phiks", choices=["phiks", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="adr3d", choices=["adr3d", "precision"],
+    ap.add_argument("--config", default="adr3d", choices=["adr3d", "precision", "batched"],
                     help="adr3d: the headline FP64 workload; precision: the split-dtype form")
     ap.add_argument("--dtype", default="all", choices=["all"] + PRECISION_DTYPES)
     ap.add_argument("--variant", default="cheb", choices=["cheb", "fd"])
     ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--no-ref", action="store_true", help="skip the FP64 reference path")
+    ap.add_argument("--count", type=int, default=256, help="batched form: instances")
+    ap.add_argument("--streams", type=int, default=16, help="batched form: worker streams")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.config == "precision":
         return run_precision(args)
+    if args.config == "batched":
+        return run_batched(args)
     return run_phiks(args)
 
 

@@ -43,6 +43,7 @@ extern "C" {
 #define PHIKS_MAX_P 8   /* largest phi order p */
 
 typedef struct phiks_plan_s* phiks_plan_t;
+typedef struct phiks_batch_s* phiks_batch_t;
 
 typedef enum {
   PHIKS_OK = 0,
@@ -196,6 +197,36 @@ uint64_t phiks_kernel_launches(void);
  * first call before any stream capture begins.  Asynchronous on `stream`. */
 phiks_status phiks_tucker_noalloc(int d, const int64_t* n, const double* V, double* W,
                                   const double* const* L, void* stream);
+
+/* Batches of independent applies (the batched form: many instances of
+ * different sizes, each with its own plan).  A batch object owns `nstreams`
+ * worker streams on the current device. */
+phiks_status phiks_batch_create(int nstreams, phiks_batch_t* out);
+void phiks_batch_destroy(phiks_batch_t batch);
+
+/* Apply every instance k (plans[k], taus[k], ps[k], nvs[k] vectors starting at
+ * v[nvs[0] + ... + nvs[k-1]], options opts[k] or defaults when opts is NULL,
+ * output outs[k]) exactly as phiks_apply_ex would.  The instances are spread
+ * over the batch's worker streams, largest first, after waiting for `stream`;
+ * `stream` waits for all of them before later work.  Plans must be distinct
+ * (each owns the workspace its instance uses). */
+phiks_status phiks_batch_apply(phiks_batch_t batch, int count, const phiks_plan_t* plans,
+                               const double* taus, const int* ps, const void* const* v,
+                               const int* nvs, const phiks_options* opts, void* const* outs,
+                               void* stream);
+
+/* Record the same work as phiks_batch_apply into one CUDA graph (stream
+ * capture of `stream`, which must not be the legacy default stream) and
+ * instantiate it; launch it with phiks_graph_launch.  Every instance must pass
+ * its norms in opts[k].vnorms, and every plan must have run this apply once
+ * (so that no allocation happens inside the capture).  The graph reads and
+ * writes the same buffers on every launch. */
+phiks_status phiks_batch_capture(phiks_batch_t batch, int count, const phiks_plan_t* plans,
+                                 const double* taus, const int* ps, const void* const* v,
+                                 const int* nvs, const phiks_options* opts, void* const* outs,
+                                 void* stream, void** graph_exec);
+phiks_status phiks_graph_launch(void* graph_exec, void* stream);
+void phiks_graph_destroy(void* graph_exec);
 
 /* Release the plan and its device memory (synchronises its device). */
 void phiks_destroy(phiks_plan_t plan);

@@ -20,7 +20,7 @@ __all__ = [
     "phiks_plan", "phiks_apply", "phiks_apply_ex", "phiks_workspace_size",
     "phiks_select_params", "phiks_choose_params", "phiks_last_params", "phiks_tucker", "phiks_expm",
     "phiks_profile_enable", "phiks_profile_read", "phiks_kernel_launches", "phiks_tucker_noalloc",
-    "phiks_device_status", "phiks_destroy", "phiks_last_error", "Plan", "EXPORTED",
+    "phiks_device_status", "phiks_destroy", "phiks_last_error", "Plan", "Batch", "EXPORTED",
 ]
 
 PHIKS_FP64, PHIKS_TF32, PHIKS_TF32X3, PHIKS_BF16X3 = 0, 1, 2, 3
@@ -33,7 +33,9 @@ EXPORTED = [
     "phiks_options_init", "phiks_plan", "phiks_apply", "phiks_apply_ex", "phiks_workspace_size",
     "phiks_select_params", "phiks_choose_params", "phiks_last_params", "phiks_tucker", "phiks_expm",
     "phiks_profile_enable", "phiks_profile_read", "phiks_kernel_launches", "phiks_tucker_noalloc",
-    "phiks_device_status", "phiks_destroy", "phiks_last_error",
+    "phiks_device_status", "phiks_batch_create", "phiks_batch_destroy", "phiks_batch_apply",
+    "phiks_batch_capture", "phiks_graph_launch", "phiks_graph_destroy", "phiks_destroy",
+    "phiks_last_error",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -107,6 +109,20 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.phiks_profile_read.restype = ctypes.c_int
     L.phiks_kernel_launches.argtypes = []
     L.phiks_kernel_launches.restype = ctypes.c_uint64
+    L.phiks_batch_create.argtypes = [i, ctypes.POINTER(vp)]
+    L.phiks_batch_create.restype = ctypes.c_int
+    L.phiks_batch_destroy.argtypes = [vp]
+    L.phiks_batch_destroy.restype = None
+    bargs = [vp, i, ctypes.POINTER(vp), ctypes.POINTER(d), ctypes.POINTER(i), ctypes.POINTER(vp),
+             ctypes.POINTER(i), ctypes.POINTER(Options), ctypes.POINTER(vp), vp]
+    L.phiks_batch_apply.argtypes = bargs
+    L.phiks_batch_apply.restype = ctypes.c_int
+    L.phiks_batch_capture.argtypes = bargs + [ctypes.POINTER(vp)]
+    L.phiks_batch_capture.restype = ctypes.c_int
+    L.phiks_graph_launch.argtypes = [vp, vp]
+    L.phiks_graph_launch.restype = ctypes.c_int
+    L.phiks_graph_destroy.argtypes = [vp]
+    L.phiks_graph_destroy.restype = None
     L.phiks_device_status.argtypes = [vp, vp]
     L.phiks_device_status.restype = ctypes.c_int
     L.phiks_tucker_noalloc.argtypes = [i, ctypes.POINTER(ctypes.c_int64), vp, vp, ctypes.POINTER(vp), vp]
@@ -266,6 +282,55 @@ def phiks_tucker_noalloc(dims: Sequence[int], V, W, Ls, stream=None):
     d = len(dims)
     n = (ctypes.c_int64 * d)(*[int(m) for m in dims])
     _check(load().phiks_tucker_noalloc(d, n, _ptr(V), _ptr(W), _vptrs(Ls), _stream(stream)))
+
+
+class Batch:
+    """Independent applies spread over worker streams (phiks_batch_*).
+
+    instances: list of (plan handle, tau, p, [vectors], out, Options)."""
+
+    def __init__(self, nstreams: int = 16):
+        h = ctypes.c_void_p()
+        _check(load().phiks_batch_create(int(nstreams), ctypes.byref(h)))
+        self.handle = h.value
+
+    @staticmethod
+    def _marshal(instances):
+        n = len(instances)
+        plans = (ctypes.c_void_p * n)(*[x[0] for x in instances])
+        taus = (ctypes.c_double * n)(*[float(x[1]) for x in instances])
+        ps = (ctypes.c_int * n)(*[int(x[2]) for x in instances])
+        flat = [_ptr(v) for x in instances for v in x[3]]
+        vs = (ctypes.c_void_p * max(len(flat), 1))(*flat)
+        nvs = (ctypes.c_int * n)(*[len(x[3]) for x in instances])
+        opts = (Options * n)(*[x[5] for x in instances])
+        outs = (ctypes.c_void_p * n)(*[_ptr(x[4]) for x in instances])
+        return n, plans, taus, ps, vs, nvs, opts, outs
+
+    def apply(self, instances, stream=None):
+        n, plans, taus, ps, vs, nvs, opts, outs = self._marshal(instances)
+        _check(load().phiks_batch_apply(self.handle, n, plans, taus, ps, vs, nvs, opts, outs,
+                                        _stream(stream)))
+
+    def capture(self, instances, stream):
+        n, plans, taus, ps, vs, nvs, opts, outs = self._marshal(instances)
+        g = ctypes.c_void_p()
+        _check(load().phiks_batch_capture(self.handle, n, plans, taus, ps, vs, nvs, opts, outs,
+                                          _stream(stream), ctypes.byref(g)))
+        return g.value
+
+    @staticmethod
+    def launch(graph, stream):
+        _check(load().phiks_graph_launch(graph, _stream(stream)))
+
+    @staticmethod
+    def destroy_graph(graph):
+        load().phiks_graph_destroy(graph)
+
+    def close(self):
+        if self.handle:
+            load().phiks_batch_destroy(self.handle)
+            self.handle = None
 
 
 def phiks_destroy(plan: int):

@@ -760,6 +760,14 @@ phiks_status check_opts(const phiks_options& o) {
 
 }  // namespace
 
+// ---- batches of independent applies ---------------------------------------
+struct phiks_batch_s {
+  int device = 0;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> done;
+  cudaEvent_t fork = nullptr;
+};
+
 // ============================================================================
 extern "C" {
 
@@ -882,6 +890,132 @@ phiks_status phiks_device_status(phiks_plan_t P, void* stream) {
   if (code < 0) return fail(PHIKS_ERR_CUDA, "reading the device status failed");
   if (code > 0) return fail(PHIKS_ERR_TIMEOUT, "a bounded device-side wait gave up (site %d)", code);
   return PHIKS_OK;
+}
+
+phiks_status phiks_batch_create(int nstreams, phiks_batch_t* out) {
+  g_err.clear();
+  if (!out || nstreams < 1 || nstreams > 256) return fail(PHIKS_ERR_INVALID, "nstreams %d", nstreams);
+  *out = nullptr;
+  std::unique_ptr<phiks_batch_s> B(new phiks_batch_s);
+  CK(cudaGetDevice(&B->device));
+  CK(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
+  for (int i = 0; i < nstreams; ++i) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    B->streams.push_back(st);
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    B->done.push_back(ev);
+  }
+  *out = B.release();
+  return PHIKS_OK;
+}
+
+void phiks_batch_destroy(phiks_batch_t B) {
+  if (!B) return;
+  DeviceGuard g(B->device);
+  for (auto st : B->streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  for (auto e : B->done) cudaEventDestroy(e);
+  cudaEventDestroy(B->fork);
+  delete B;
+}
+
+phiks_status phiks_batch_apply(phiks_batch_t B, int count, const phiks_plan_t* plans,
+                               const double* taus, const int* ps, const void* const* v,
+                               const int* nvs, const phiks_options* opts, void* const* outs,
+                               void* stream) {
+  g_err.clear();
+  if (!B || count < 0 || (count > 0 && (!plans || !taus || !ps || !v || !nvs || !outs)))
+    return fail(PHIKS_ERR_INVALID, "bad batch arguments");
+  if (count == 0) return PHIKS_OK;
+  DeviceGuard g(B->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  // longest-processing-time-first assignment of the instances to the streams,
+  // by the flops of one Tucker times the T# of the last call (20 if none yet)
+  std::vector<int> order(count);
+  std::vector<double> cost(count);
+  std::vector<size_t> voff(count);
+  size_t off = 0;
+  for (int k = 0; k < count; ++k) {
+    if (!plans[k]) return fail(PHIKS_ERR_INVALID, "plan %d is NULL", k);
+    order[k] = k;
+    double sn = 0;
+    for (int mu = 0; mu < plans[k]->d; ++mu) sn += (double)plans[k]->n[mu];
+    cost[k] = (double)plans[k]->N * sn * (plans[k]->last_tuckers > 0 ? plans[k]->last_tuckers : 20);
+    voff[k] = off;
+    off += (size_t)nvs[k];
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  const int W = (int)B->streams.size();
+  std::vector<double> load(W, 0.0);
+  std::vector<int> who(count);
+  for (int k : order) {
+    int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    who[k] = w;
+    load[w] += cost[k];
+  }
+  CK(cudaEventRecord(B->fork, st));
+  for (int w = 0; w < W; ++w) CK(cudaStreamWaitEvent(B->streams[w], B->fork, 0));
+  phiks_status first = PHIKS_OK;
+  std::string msg;
+  for (int k : order) {
+    phiks_status r = phiks_apply_ex(plans[k], taus[k], ps[k], v + voff[k], nvs[k],
+                                    opts ? &opts[k] : nullptr, outs[k], B->streams[who[k]]);
+    if (r != PHIKS_OK && first == PHIKS_OK) {
+      first = r;
+      msg = "instance " + std::to_string(k) + ": " + g_err;
+    }
+  }
+  for (int w = 0; w < W; ++w) {
+    CK(cudaEventRecord(B->done[w], B->streams[w]));
+    CK(cudaStreamWaitEvent(st, B->done[w], 0));
+  }
+  if (first != PHIKS_OK) return fail(first, "%s", msg.c_str());
+  return PHIKS_OK;
+}
+
+phiks_status phiks_batch_capture(phiks_batch_t B, int count, const phiks_plan_t* plans,
+                                 const double* taus, const int* ps, const void* const* v,
+                                 const int* nvs, const phiks_options* opts, void* const* outs,
+                                 void* stream, void** graph_exec) {
+  g_err.clear();
+  if (!stream || !graph_exec) return fail(PHIKS_ERR_INVALID, "capture needs a non-default stream");
+  *graph_exec = nullptr;
+  for (int k = 0; k < count; ++k)
+    if (!opts || !opts[k].vnorms)
+      return fail(PHIKS_ERR_INVALID, "capture needs caller norms (vnorms) for every instance");
+  DeviceGuard g(B->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  phiks_status r = phiks_batch_apply(B, count, plans, taus, ps, v, nvs, opts, outs, stream);
+  std::string msg = g_err;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &graph);
+  if (r != PHIKS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(r, "during capture: %s", msg.c_str());
+  }
+  if (e != cudaSuccess) return fail(PHIKS_ERR_CUDA, "capture failed: %s", cudaGetErrorString(e));
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(PHIKS_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
+  *graph_exec = exec;
+  return PHIKS_OK;
+}
+
+phiks_status phiks_graph_launch(void* graph_exec, void* stream) {
+  g_err.clear();
+  if (!graph_exec) return fail(PHIKS_ERR_INVALID, "NULL graph");
+  CK(cudaGraphLaunch((cudaGraphExec_t)graph_exec, (cudaStream_t)stream));
+  return PHIKS_OK;
+}
+
+void phiks_graph_destroy(void* graph_exec) {
+  if (graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)graph_exec);
 }
 
 void phiks_destroy(phiks_plan_t P) {

@@ -22,7 +22,10 @@
 #include <cmath>
 #include <complex>
 #include <limits>
+#include <map>
+#include <mutex>
 #include <thread>
+#include <tuple>
 
 namespace phiks {
 
@@ -368,18 +371,47 @@ int tucker_count(int kind, int s, int nscales, int q, int p) {
   return kind == 0 ? q + s * p + nscales : q * p + s * p + nscales;
 }
 
+namespace {
+
+// k_q(z(zeta_m)) on the ellipse of capacity r_grid()[ir], for the rule's q
+// nodes: independent of the operator, so computed once per process.
+struct KernelKey {
+  int rule, q, ir;
+  bool operator<(const KernelKey& o) const {
+    return std::tie(rule, q, ir) < std::tie(o.rule, o.q, o.ir);
+  }
+};
+std::mutex g_kernel_mu;
+std::map<KernelKey, std::vector<cd>> g_kernel_cache;
+
+const std::vector<cd>& cached_kernel(int rule, int q, int ir, const std::vector<cd>& z) {
+  {
+    std::lock_guard<std::mutex> lk(g_kernel_mu);
+    auto it = g_kernel_cache.find({rule, q, ir});
+    if (it != g_kernel_cache.end()) return it->second;
+  }
+  std::vector<double> xg, wg, nodes, wts;
+  gauss_legendre(kNT, xg, wg);
+  for (int j = 0; j < kNT; ++j) {
+    xg[j] = (xg[j] + 1.0) / 2.0;
+    wg[j] /= 2.0;
+  }
+  quad_rule(rule, q, nodes, wts);
+  std::vector<cd> k;
+  kernel_on_ellipse(nodes, z, xg, wg, k);
+  std::lock_guard<std::mutex> lk(g_kernel_mu);
+  return g_kernel_cache.emplace(KernelKey{rule, q, ir}, std::move(k)).first->second;
+}
+
+}  // namespace
+
 void remainder_bounds(const Rect& xi, int s, const std::vector<int>& qs, int p, int rule,
                       std::vector<double>& out) {
   const std::vector<double> rs = r_grid();
   std::vector<cd> w = rect_boundary(xi);
   const double scale = std::ldexp(1.0, -s);
   for (auto& x : w) x *= scale;
-  std::vector<double> xg, wg;
-  gauss_legendre(kNT, xg, wg);
-  for (int j = 0; j < kNT; ++j) {
-    xg[j] = (xg[j] + 1.0) / 2.0;
-    wg[j] /= 2.0;
-  }
+  const size_t nw = w.size();
   const double inf = std::numeric_limits<double>::infinity();
   const size_t nq = qs.size();
   std::vector<double> best_r(kNR * nq * p, inf);
@@ -392,25 +424,39 @@ void remainder_bounds(const Rect& xi, int s, const std::vector<int>& qs, int p, 
       z[m] = r * e + 0.5 + ei / (16.0 * r);
       dz[m] = r * e - ei / (16.0 * r);
     }
-    std::vector<cd> E(kNZeta * w.size());
-    for (size_t iw = 0; iw < w.size(); ++iw)
-      for (int m = 0; m < kNZeta; ++m) E[iw * kNZeta + m] = std::exp((1.0 - z[m]) * w[iw]);
-    std::vector<double> nodes, wts;
-    std::vector<cd> k, c(kNZeta);
+    // exp((1 - z_m) w) as separate real and imaginary arrays, [w][m]
+    std::vector<double> Er(nw * kNZeta), Ei(nw * kNZeta);
+    for (size_t iw = 0; iw < nw; ++iw)
+      for (int m = 0; m < kNZeta; ++m) {
+        cd e = std::exp((1.0 - z[m]) * w[iw]);
+        Er[iw * kNZeta + m] = e.real();
+        Ei[iw * kNZeta + m] = e.imag();
+      }
+    std::vector<double> cr(kNZeta), ci(kNZeta);
     for (size_t iq = 0; iq < nq; ++iq) {
-      quad_rule(rule, qs[iq], nodes, wts);
-      kernel_on_ellipse(nodes, z, xg, wg, k);
+      const std::vector<cd>& k = cached_kernel(rule, qs[iq], ir, z);
       for (int l = 1; l <= p; ++l) {
         const double fl = factorial(l - 1);
-        for (int m = 0; m < kNZeta; ++m) c[m] = k[m] * std::pow(z[m], l - 1) / fl * dz[m];
+        for (int m = 0; m < kNZeta; ++m) {
+          cd c = k[m] * std::pow(z[m], l - 1) / fl * dz[m];
+          cr[m] = c.real();
+          ci[m] = c.imag();
+        }
         double mx = 0;
         bool bad = false;
-        for (size_t iw = 0; iw < w.size(); ++iw) {
-          cd acc(0, 0);
-          const cd* Ew = &E[iw * kNZeta];
-          for (int m = 0; m < kNZeta; ++m) acc += c[m] * Ew[m];
-          double a = std::abs(acc);
-          if (!std::isfinite(a)) { bad = true; break; }
+        for (size_t iw = 0; iw < nw; ++iw) {
+          const double* er = &Er[iw * kNZeta];
+          const double* ei = &Ei[iw * kNZeta];
+          double sr = 0, si = 0;
+          for (int m = 0; m < kNZeta; ++m) {
+            sr += cr[m] * er[m] - ci[m] * ei[m];
+            si += cr[m] * ei[m] + ci[m] * er[m];
+          }
+          const double a = std::hypot(sr, si);
+          if (!std::isfinite(a)) {
+            bad = true;
+            break;
+          }
           mx = std::max(mx, a);
         }
         double val = mx * (1.0 + std::sqrt(2.0)) / kNZeta;

@@ -588,8 +588,18 @@ cudaError_t run_gemm(TcState* s, const CUtensorMap* mA, const CUtensorMap* mB, G
   P.stages = stages;
   const size_t smem = (size_t)stages * stage_bytes + extra;
   auto kern = tc_gemm_kernel<KIND, NP>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  // raise the kernel's dynamic shared-memory limit once per process (the
+  // attribute applies to every later launch on this device)
+  static int smem_set[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (smem_set[dev] < (int)smem) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         s->smem_optin);
+    if (e != cudaSuccess) return e;
+    smem_set[dev] = s->smem_optin;
+  }
   // With 512 TMEM columns the shared memory (>= 4 x 34 KiB) already keeps a
   // second CTA off the SM, so co-resident CTAs never oversubscribe TMEM.
   int grid = P.num_tiles < 152 ? P.num_tiles : 152;

@@ -209,3 +209,45 @@ def test_invalid_calls_report_errors():
         pk.phiks_apply(plan.handle, float("nan"), 3, [v], out)
     with pytest.raises(pk.PhiksError):
         pk.phiks_apply(plan.handle, 1e-3, 3, [None], out)
+
+
+def test_batch_apply_and_graph_match_single_calls():
+    """The batched form: uneven instances over worker streams, and the same
+    work captured in one CUDA graph, give the single-call results bit for bit."""
+    insts = wk.batched_instances(8)
+    insts = [w for w in insts if w.N <= 120000][:6] + [wk.small_same(20)]
+    rows = []
+    for w in insts:
+        plan = pk.Plan(w.A)
+        v = dev(w.vs[0])
+        p = w.p
+        per = p + (0 if w.skip_phi0 else 1)
+        o_single = torch.empty(per * w.N, device="cuda", dtype=torch.float64)
+        o_batch = torch.empty_like(o_single)
+        o_graph = torch.empty_like(o_single)
+        opts = pk.make_options(skip_phi0=int(w.skip_phi0), vnorms=[float(np.linalg.norm(w.vs[0]))])
+        rows.append((plan, w, v, o_single, o_batch, o_graph, opts))
+    for plan, w, v, o1, _, _, opts in rows:
+        pk.phiks_apply_ex(plan.handle, w.tau, w.p, [v], o1, opts=opts)
+    batch = pk.Batch(4)
+    stream = torch.cuda.Stream()
+    batch.apply([(r[0].handle, r[1].tau, r[1].p, [r[2]], r[4], r[6]) for r in rows], stream)
+    graph = batch.capture([(r[0].handle, r[1].tau, r[1].p, [r[2]], r[5], r[6]) for r in rows], stream)
+    batch.launch(graph, stream)
+    torch.cuda.synchronize()
+    for plan, w, v, o1, o2, o3, _ in rows:
+        assert torch.equal(o1, o2) and torch.equal(o1, o3)
+    # the graph replays: clear the outputs, launch again, same results
+    for r in rows:
+        r[5].zero_()
+    batch.launch(graph, stream)
+    torch.cuda.synchronize()
+    for r in rows:
+        assert torch.equal(r[3], r[5])
+    batch.destroy_graph(graph)
+    batch.close()
+    # one instance checked against the oracle
+    plan, w, v, o1, _, _, _ = rows[-1]
+    ex = dense.same(w.A, w.tau, w.vs[0], w.p)
+    for l in range(w.p + 1):
+        assert rel_inf(o1.cpu().numpy()[l * w.N:(l + 1) * w.N], ex[l]) < TOL_EXACT

@@ -94,3 +94,39 @@ def test_lincomb_split(dtype):
     errs = [rel_inf(out[L], ex[L]) for L in range(2)]
     print("lincomb dtype %d errs %s" % (dtype, ["%.2e" % e for e in errs]))
     assert max(errs) < 4 * TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [pk.PHIKS_BF16X3])
+def test_batch_graph_split(dtype):
+    """Split dtype, instances with n_mu above 256 (two N tiles), batched over
+    streams and replayed from a CUDA graph: same results as single calls and
+    within tolerance of the FP64 restatement."""
+    dims_list = [(288, 40), (512, 64), (40, 24, 16)]
+    rows = []
+    for k, dims in enumerate(dims_list):
+        A = [wk.fd_adr_dirichlet(m, 0.5, a) for m, a in zip(dims, (3.0, -5.0, 1.0))]
+        N = int(np.prod(dims))
+        v = wk.normal(50 + k, N).astype(np.float32).astype(np.float64)
+        plan = pk.Plan(A, dtype)
+        vt = dev(v, torch.float32)
+        o1 = torch.empty(3 * N, device="cuda", dtype=torch.float32)
+        o2 = torch.empty_like(o1)
+        opts = pk.make_options(skip_phi0=1, vnorms=[float(np.linalg.norm(v))], tol=1e-6 * float(np.linalg.norm(v)))
+        rows.append((plan, A, 2e-4, v, vt, o1, o2, opts))
+    for plan, A, tau, v, vt, o1, _, opts in rows:
+        pk.phiks_apply_ex(plan.handle, tau, 3, [vt], o1, opts=opts)
+    stream = torch.cuda.Stream()
+    batch = pk.Batch(3)
+    g = batch.capture([(r[0].handle, r[2], 3, [r[4]], r[6], r[7]) for r in rows], stream)
+    batch.launch(g, stream)
+    torch.cuda.synchronize()
+    for plan, A, tau, v, vt, o1, o2, opts in rows:
+        pk.phiks_device_status(plan.handle)
+        assert torch.equal(o1, o2)
+        s, q, _, _ = plan.last_params()
+        ref = phiks_ref.same(A, tau, v, 3, s, q, skip_phi0=True)
+        got = o1.double().cpu().numpy().reshape(3, -1)
+        for l in range(3):
+            assert rel_inf(got[l], ref[l]) < 4 * TOL[dtype]
+    batch.destroy_graph(g)
+    batch.close()
