@@ -229,9 +229,11 @@ def test_batch_apply_and_graph_match_single_calls():
         rows.append((plan, w, v, o_single, o_batch, o_graph, opts))
     for plan, w, v, o1, _, _, opts in rows:
         pk.phiks_apply_ex(plan.handle, w.tau, w.p, [v], o1, opts=opts)
+    torch.cuda.synchronize()   # the batch reuses each plan's workspace
     batch = pk.Batch(4)
     stream = torch.cuda.Stream()
     batch.apply([(r[0].handle, r[1].tau, r[1].p, [r[2]], r[4], r[6]) for r in rows], stream)
+    stream.synchronize()
     graph = batch.capture([(r[0].handle, r[1].tau, r[1].p, [r[2]], r[5], r[6]) for r in rows], stream)
     batch.launch(graph, stream)
     torch.cuda.synchronize()

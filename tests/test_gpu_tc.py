@@ -115,6 +115,9 @@ def test_batch_graph_split(dtype):
         rows.append((plan, A, 2e-4, v, vt, o1, o2, opts))
     for plan, A, tau, v, vt, o1, _, opts in rows:
         pk.phiks_apply_ex(plan.handle, tau, 3, [vt], o1, opts=opts)
+    # the single calls ran on the legacy stream and share each plan's
+    # workspace with the batch below: finish them first
+    torch.cuda.synchronize()
     stream = torch.cuda.Stream()
     batch = pk.Batch(3)
     g = batch.capture([(r[0].handle, r[2], 3, [r[4]], r[6], r[7]) for r in rows], stream)
