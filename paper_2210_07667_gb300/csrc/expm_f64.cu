@@ -27,7 +27,8 @@ __global__ void __launch_bounds__(GNT) gemm_batch_f64_kernel(GemmBatch gb) {
   const int tj = tid % GTHR, ti = tid / GTHR;
   const int i0 = bi * GT, j0 = bj * GT;
   double acc[GR][GR] = {{0.0, 0.0}, {0.0, 0.0}};
-  for (int k0 = 0; k0 < n; k0 += GK) {
+  const int kend = gb.alpha[k] != 0.0 ? n : 0;  // alpha = 0: addends only
+  for (int k0 = 0; k0 < kend; k0 += GK) {
     for (int e = tid; e < GT * GK; e += GNT) {
       int ii = e % GT, kk = e / GT;
       int i = i0 + ii, kc = k0 + kk;
@@ -53,7 +54,13 @@ __global__ void __launch_bounds__(GNT) gemm_batch_f64_kernel(GemmBatch gb) {
 #pragma unroll
     for (int c = 0; c < GR; ++c) {
       int i = i0 + ti + r * GTHR, j = j0 + tj + c * GTHR;
-      if (i < n && j < n) C[i + (int64_t)n * j] = alpha * acc[r][c] + (i == j ? beta : 0.0);
+      if (i < n && j < n) {
+        const int64_t e = i + (int64_t)n * j;
+        double v = alpha * acc[r][c] + (i == j ? beta : 0.0);
+        for (int a = 0; a < 3; ++a)
+          if (gb.addm[k][a]) v = fma(gb.addc[k][a], gb.addm[k][a][e], v);
+        C[e] = v;
+      }
     }
 }
 

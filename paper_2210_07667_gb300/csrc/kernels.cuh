@@ -74,9 +74,12 @@ struct GemmBatch {
   const double* B[kMaxBatch];
   double* C[kMaxBatch];
   double alpha[kMaxBatch];
-  double beta_I[kMaxBatch];  // C = alpha A B + beta_I I
+  double beta_I[kMaxBatch];          // coefficient of the identity
+  const double* addm[kMaxBatch][3];  // optional addends (may be null)
+  double addc[kMaxBatch][3];
 };
-// Batched C_k = alpha_k A_k B_k + beta_k I (column-major n_k x n_k).
+// Batched C_k = alpha_k A_k B_k + beta_k I + sum_j addc_kj addm_kj
+// (column-major n_k x n_k; alpha_k = 0 skips the product).
 cudaError_t launch_gemm_batch_f64(const GemmBatch& gb, int nmax, cudaStream_t st);
 
 struct ScaleBatch {

@@ -214,11 +214,13 @@ phiks_status select_cached(phiks_plan_s* P, double tau, int p, int kind, const d
 }
 
 // ---- small exponentials ----------------------------------------------------
-// E = e^{c sigma} T_14(X)^(2^t) with X = c (A - sigma I) / 2^t, ||X||_1 <= 1/2:
-// truncated Taylor series of degree 14 by Horner's rule (remainder below
-// 0.5^15/15! < 2.5e-17), then t squarings (scaling and squaring, Moler and
-// Van Loan's method 3).
-constexpr int kTaylorDeg = 14;
+// E = e^{c sigma} T_15(X)^(2^t) with X = c (A - sigma I) / 2^t, ||X||_1 <= 1/2:
+// the Taylor polynomial of degree 15 (remainder below 0.5^16/16! < 1e-18),
+// evaluated by Paterson and Stockmeyer's scheme with blocks of four terms
+// (X^2, X^3, X^4, then three products by X^4: six matrix products), followed
+// by t squarings (scaling and squaring, Moler and Van Loan's method 3).
+constexpr int kTaylorDeg = 15;
+constexpr int kScratchPerJob = 6;  // X, X^2, X^3, X^4, T0, T1
 
 struct ExpmJob {
   int n;
@@ -229,15 +231,21 @@ struct ExpmJob {
   double* out;           // device n x n
 };
 
+GemmBatch gemm_batch0() {
+  GemmBatch g;
+  std::memset(&g, 0, sizeof g);
+  return g;
+}
+
 phiks_status run_expm_jobs(phiks_plan_s* P, std::vector<ExpmJob>& jobs, double* scratch,
                            cudaStream_t st) {
-  // scratch: 3 buffers per job (X, T0, T1)
+  (void)P;
   std::vector<size_t> offs(jobs.size());
   size_t tot = 0;
   int nmax = 1;
   for (size_t k = 0; k < jobs.size(); ++k) {
     offs[k] = tot;
-    tot += 3 * (size_t)jobs[k].n * jobs[k].n;
+    tot += kScratchPerJob * (size_t)jobs[k].n * jobs[k].n;
     nmax = std::max(nmax, jobs[k].n);
   }
   std::vector<int> t(jobs.size());
@@ -247,70 +255,95 @@ phiks_status run_expm_jobs(phiks_plan_s* P, std::vector<ExpmJob>& jobs, double* 
     t[k] = nx > 0.5 ? (int)std::ceil(std::log2(nx / 0.5)) : 0;
     tmax = std::max(tmax, t[k]);
   }
-  for (size_t k0 = 0; k0 < jobs.size(); k0 += kMaxBatch) {
-    const size_t k1 = std::min(jobs.size(), k0 + kMaxBatch);
+  double cf[kTaylorDeg + 1];
+  cf[0] = 1.0;
+  for (int i = 1; i <= kTaylorDeg; ++i) cf[i] = cf[i - 1] / i;
+  const size_t per = kMaxBatch / 2;  // the X^3 / X^4 launch holds two entries per job
+  for (size_t k0 = 0; k0 < jobs.size(); k0 += per) {
+    const size_t k1 = std::min(jobs.size(), k0 + per);
     const int cnt = (int)(k1 - k0);
-    auto X = [&](size_t k) { return scratch + offs[k]; };
-    auto T = [&](size_t k, int i) { return scratch + offs[k] + (size_t)(1 + i) * jobs[k].n * jobs[k].n; };
-    // X = (c / 2^t) (A - sigma I);  T0 = X/14 + I
+    auto buf = [&](size_t k, int i) { return scratch + offs[k] + (size_t)i * jobs[k].n * jobs[k].n; };
+    enum { BX = 0, BX2 = 1, BX3 = 2, BX4 = 3, BT0 = 4, BT1 = 5 };
     ScaleBatch sb;
     sb.count = cnt;
     for (int i = 0; i < cnt; ++i) {
       size_t k = k0 + i;
       sb.n[i] = jobs[k].n;
       sb.X[i] = jobs[k].Ashift;
-      sb.Y[i] = X(k);
+      sb.Y[i] = buf(k, BX);
       sb.alpha[i] = std::ldexp(jobs[k].c, -t[k]);
       sb.shift[i] = 0.0;
     }
     CK(launch_scale_batch_f64(sb, nmax, st));
+    GemmBatch g = gemm_batch0();  // X^2
+    g.count = cnt;
     for (int i = 0; i < cnt; ++i) {
       size_t k = k0 + i;
-      sb.X[i] = X(k);
-      sb.Y[i] = T(k, 0);
-      sb.alpha[i] = 1.0 / kTaylorDeg;
-      sb.shift[i] = -(double)kTaylorDeg;
+      g.n[i] = jobs[k].n;
+      g.A[i] = buf(k, BX);
+      g.B[i] = buf(k, BX);
+      g.C[i] = buf(k, BX2);
+      g.alpha[i] = 1.0;
     }
-    CK(launch_scale_batch_f64(sb, nmax, st));
-    int cur = 0;
-    for (int m = kTaylorDeg - 1; m >= 1; --m) {  // T <- I + X T / m
-      GemmBatch gb;
-      gb.count = cnt;
+    CK(launch_gemm_batch_f64(g, nmax, st));
+    g = gemm_batch0();  // X^3 = X^2 X, X^4 = X^2 X^2
+    g.count = 2 * cnt;
+    for (int i = 0; i < cnt; ++i) {
+      size_t k = k0 + i;
+      for (int h = 0; h < 2; ++h) {
+        g.n[2 * i + h] = jobs[k].n;
+        g.A[2 * i + h] = buf(k, BX2);
+        g.B[2 * i + h] = buf(k, h ? BX2 : BX);
+        g.C[2 * i + h] = buf(k, h ? BX4 : BX3);
+        g.alpha[2 * i + h] = 1.0;
+      }
+    }
+    CK(launch_gemm_batch_f64(g, nmax, st));
+    // T = B_3 = c12 I + c13 X + c14 X^2 + c15 X^3, then T <- T X^4 + B_j, j = 2, 1, 0
+    int cur = BT0;
+    for (int j = 3; j >= 0; --j) {
+      g = gemm_batch0();
+      g.count = cnt;
       for (int i = 0; i < cnt; ++i) {
         size_t k = k0 + i;
-        gb.n[i] = jobs[k].n;
-        gb.A[i] = X(k);
-        gb.B[i] = T(k, cur);
-        gb.C[i] = T(k, 1 - cur);
-        gb.alpha[i] = 1.0 / m;
-        gb.beta_I[i] = 1.0;
+        g.n[i] = jobs[k].n;
+        g.alpha[i] = (j == 3) ? 0.0 : 1.0;
+        g.A[i] = buf(k, cur);
+        g.B[i] = buf(k, BX4);
+        g.C[i] = buf(k, (j == 3) ? BT0 : (cur == BT0 ? BT1 : BT0));
+        g.beta_I[i] = cf[4 * j];
+        g.addm[i][0] = buf(k, BX);
+        g.addm[i][1] = buf(k, BX2);
+        g.addm[i][2] = buf(k, BX3);
+        g.addc[i][0] = cf[4 * j + 1];
+        g.addc[i][1] = cf[4 * j + 2];
+        g.addc[i][2] = cf[4 * j + 3];
       }
-      CK(launch_gemm_batch_f64(gb, nmax, st));
-      cur = 1 - cur;
+      CK(launch_gemm_batch_f64(g, nmax, st));
+      if (j < 3) cur = (cur == BT0) ? BT1 : BT0;
     }
-    // squarings: job k squares t[k] times; its current buffer alternates
+    // squarings: job k squares t[k] times between T0 and T1
     std::vector<int> kcur(cnt, cur);
     for (int r = 0; r < tmax; ++r) {
-      GemmBatch gb;
-      gb.count = 0;
+      g = gemm_batch0();
       for (int i = 0; i < cnt; ++i) {
         size_t k = k0 + i;
         if (t[k] <= r) continue;
-        int j = gb.count++;
-        gb.n[j] = jobs[k].n;
-        gb.A[j] = T(k, kcur[i]);
-        gb.B[j] = T(k, kcur[i]);
-        gb.C[j] = T(k, 1 - kcur[i]);
-        gb.alpha[j] = 1.0;
-        gb.beta_I[j] = 0.0;
-        kcur[i] = 1 - kcur[i];
+        int jj = g.count++;
+        const int nxt = kcur[i] == BT0 ? BT1 : BT0;
+        g.n[jj] = jobs[k].n;
+        g.A[jj] = buf(k, kcur[i]);
+        g.B[jj] = buf(k, kcur[i]);
+        g.C[jj] = buf(k, nxt);
+        g.alpha[jj] = 1.0;
+        kcur[i] = nxt;
       }
-      if (gb.count) CK(launch_gemm_batch_f64(gb, nmax, st));
+      if (g.count) CK(launch_gemm_batch_f64(g, nmax, st));
     }
     for (int i = 0; i < cnt; ++i) {
       size_t k = k0 + i;
       sb.n[i] = jobs[k].n;
-      sb.X[i] = T(k, kcur[i]);
+      sb.X[i] = buf(k, kcur[i]);
       sb.Y[i] = jobs[k].out;
       sb.alpha[i] = jobs[k].esig;
       sb.shift[i] = 0.0;
@@ -387,7 +420,7 @@ phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool 
     }
     CK(cudaMalloc(&nb.dev, tot * 8));
   }
-  phiks_status es = ensure_expm_scratch(P, 3 * tot);
+  phiks_status es = ensure_expm_scratch(P, kScratchPerJob * tot);
   if (es != PHIKS_OK) {
     if (!hit) cudaFree(nb.dev);
     return es;
@@ -522,7 +555,7 @@ void bank_ptrs(const phiks_plan_s* P, const Bank* B, int b, Mats* M) {
 // Squaring chain: M <- M^2 for every mode (and the split planes of the result).
 phiks_status square_modes(Ctx& c, Mats& M, int& cur_buf) {
   phiks_plan_s* P = c.P;
-  GemmBatch gb;
+  GemmBatch gb = gemm_batch0();
   gb.count = P->d;
   size_t off = 0;
   for (int mu = 0; mu < P->d; ++mu) {
@@ -1286,7 +1319,7 @@ phiks_status phiks_expm(int batch, int n, const double* X, double* E, void* stre
     jobs[b].out = E + (size_t)b * n * n;
   }
   double* scratch = nullptr;
-  CK(cudaMallocAsync((void**)&scratch, 3 * h.size() * 8, st));
+  CK(cudaMallocAsync((void**)&scratch, kScratchPerJob * h.size() * 8, st));
   phiks_plan_s dummy;
   phiks_status r = run_expm_jobs(&dummy, jobs, scratch, st);
   cudaFreeAsync(scratch, st);

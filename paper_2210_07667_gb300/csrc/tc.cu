@@ -25,7 +25,9 @@
 
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
+#include <tuple>
 
 #include "tc.cuh"
 
@@ -496,7 +498,28 @@ struct TcState {
   int* status = nullptr;  // device
   uint8_t* ws = nullptr;
   int smem_optin = 0;
+  // encoded tensor maps by (address, inner extent, rows, box rows): encoding
+  // costs microseconds of host time, a lookup does not
+  std::map<std::tuple<const void*, uint64_t, uint64_t, uint32_t>, CUtensorMap> maps;
 };
+
+namespace {
+
+bool cached_map(TcState* s, CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows,
+                uint32_t box_rows) {
+  auto key = std::make_tuple(base, inner, rows, box_rows);
+  auto it = s->maps.find(key);
+  if (it != s->maps.end()) {
+    *m = it->second;
+    return true;
+  }
+  if (!make_map(m, s->dtype, base, inner, rows, box_rows)) return false;
+  if (s->maps.size() > 4096) s->maps.clear();
+  s->maps.emplace(key, *m);
+  return true;
+}
+
+}  // namespace
 
 size_t tc_workspace_bytes(int64_t N) {
   // two plane sets of up to 2 planes x 4 bytes, each rounded to 1 KiB
@@ -638,12 +661,12 @@ cudaError_t tc_tucker(TcState* s, const Combo& in, const void* const* Bp, const 
     std::memset(mB, 0, sizeof mB);
     const size_t bplane = ((size_t)np * np * elt + 1023) / 1024 * 1024;
     for (int p = 0; p < NP; ++p) {
-      if (!make_map(&mA[p], dtype, set[cur][p], (uint64_t)n, (uint64_t)M2, BM)) {
+      if (!cached_map(s, &mA[p], set[cur][p], (uint64_t)n, (uint64_t)M2, BM)) {
         g_tc_err = "tensor map for the A operand failed";
         return cudaErrorInvalidValue;
       }
-      if (!make_map(&mB[p], dtype, (const uint8_t*)Bp[mu] + p * bplane, (uint64_t)np, (uint64_t)np,
-                    (uint32_t)ntile)) {
+      if (!cached_map(s, &mB[p], (const uint8_t*)Bp[mu] + p * bplane, (uint64_t)np, (uint64_t)np,
+                      (uint32_t)ntile)) {
         g_tc_err = "tensor map for the B operand failed";
         return cudaErrorInvalidValue;
       }
