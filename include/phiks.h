@@ -26,8 +26,11 @@
  *     apply calls are asynchronous on that stream except where stated;
  *   - nothing throws: each call returns a phiks_status and records a message
  *     that phiks_last_error() returns (thread-local);
- *   - a plan is not safe for concurrent applies unless each apply passes its
- *     own workspace through phiks_options.
+ *   - everything an apply writes besides its outputs lives in its workspace,
+ *     so applies on one plan may overlap on the GPU (different streams) when
+ *     each passes its own workspace and its norms (phiks_options); the plan's
+ *     host-side state (parameter and exponential caches) is not thread-safe,
+ *     so issue the calls from one host thread.
  */
 #ifndef PHIKS_H
 #define PHIKS_H
@@ -227,6 +230,46 @@ phiks_status phiks_batch_capture(phiks_batch_t batch, int count, const phiks_pla
                                  void* stream, void** graph_exec);
 phiks_status phiks_graph_launch(void* graph_exec, void* stream);
 void phiks_graph_destroy(void* graph_exec);
+
+/* Served form: a trace of requests arriving over time (continuous batching).
+ * A request is one or two applies run in order (e.g. the two species of a
+ * Brusselator stage), each described as for phiks_apply_ex with its norms. */
+#define PHIKS_SERVE_MAX_APPLY 2
+typedef struct {
+  phiks_plan_t plan;
+  double tau;
+  int p, nv;              /* as in phiks_apply_ex */
+  const void* const* v;   /* host array of nv device pointers */
+  void* out;              /* device output */
+  int nscales, skip_phi0;
+  double tol;             /* 0: default 2^-53 */
+  const double* vnorms;   /* host, nv norms (required: serving never synchronises) */
+} phiks_apply_args;
+
+typedef struct {
+  int napply;
+  phiks_apply_args apply[PHIKS_SERVE_MAX_APPLY];
+} phiks_request;
+
+typedef struct {
+  int slots;              /* requests on the device at once (one stream each) */
+  size_t hbm_budget;      /* workspace bytes in flight at most; 0 = no limit */
+  int poll_us;            /* dispatcher pause when idle (0 = yield) */
+} phiks_serve_config;
+
+/* Run the trace in real time on the current device: request k becomes
+ * eligible arrival_s[k] seconds after the call starts (ascending), waits in a
+ * FIFO queue, and is dispatched to a free slot when its workspace fits in the
+ * budget; requests on different slots overlap on the GPU.  Workspaces come
+ * from a memory pool owned by the call.  Outputs: latency_ms[k] from arrival
+ * to completion of its kernels, queue_ms[k] (optional) from arrival to
+ * dispatch, *makespan_s (optional) from start to the last completion.  Plans
+ * must have run each (tau, p, norms) once before so that no parameter search
+ * or exponential is built while serving.  Returns after every request has
+ * finished. */
+phiks_status phiks_serve_trace(const phiks_serve_config* cfg, int count, const phiks_request* reqs,
+                               const double* arrival_s, double* latency_ms, double* queue_ms,
+                               double* makespan_s);
 
 /* Release the plan and its device memory (synchronises its device). */
 void phiks_destroy(phiks_plan_t plan);

@@ -20,7 +20,8 @@ __all__ = [
     "phiks_plan", "phiks_apply", "phiks_apply_ex", "phiks_workspace_size",
     "phiks_select_params", "phiks_choose_params", "phiks_last_params", "phiks_tucker", "phiks_expm",
     "phiks_profile_enable", "phiks_profile_read", "phiks_kernel_launches", "phiks_tucker_noalloc",
-    "phiks_device_status", "phiks_destroy", "phiks_last_error", "Plan", "Batch", "EXPORTED",
+    "phiks_device_status", "phiks_serve_trace", "phiks_destroy", "phiks_last_error", "Plan", "Batch",
+    "EXPORTED",
 ]
 
 PHIKS_FP64, PHIKS_TF32, PHIKS_TF32X3, PHIKS_BF16X3 = 0, 1, 2, 3
@@ -34,8 +35,8 @@ EXPORTED = [
     "phiks_select_params", "phiks_choose_params", "phiks_last_params", "phiks_tucker", "phiks_expm",
     "phiks_profile_enable", "phiks_profile_read", "phiks_kernel_launches", "phiks_tucker_noalloc",
     "phiks_device_status", "phiks_batch_create", "phiks_batch_destroy", "phiks_batch_apply",
-    "phiks_batch_capture", "phiks_graph_launch", "phiks_graph_destroy", "phiks_destroy",
-    "phiks_last_error",
+    "phiks_batch_capture", "phiks_graph_launch", "phiks_graph_destroy", "phiks_serve_trace",
+    "phiks_destroy", "phiks_last_error",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -61,6 +62,29 @@ class Options(ctypes.Structure):
         ("no_cache", ctypes.c_int),
         ("reserved", ctypes.c_int * 7),
     ]
+
+
+class ApplyArgs(ctypes.Structure):
+    _fields_ = [
+        ("plan", ctypes.c_void_p),
+        ("tau", ctypes.c_double),
+        ("p", ctypes.c_int),
+        ("nv", ctypes.c_int),
+        ("v", ctypes.POINTER(ctypes.c_void_p)),
+        ("out", ctypes.c_void_p),
+        ("nscales", ctypes.c_int),
+        ("skip_phi0", ctypes.c_int),
+        ("tol", ctypes.c_double),
+        ("vnorms", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("napply", ctypes.c_int), ("apply", ApplyArgs * 2)]
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("poll_us", ctypes.c_int)]
 
 
 class PhiksError(RuntimeError):
@@ -123,6 +147,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.phiks_graph_launch.restype = ctypes.c_int
     L.phiks_graph_destroy.argtypes = [vp]
     L.phiks_graph_destroy.restype = None
+    L.phiks_serve_trace.argtypes = [ctypes.POINTER(ServeConfig), i, ctypes.POINTER(Request),
+                                    ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
+                                    ctypes.POINTER(d)]
+    L.phiks_serve_trace.restype = ctypes.c_int
     L.phiks_device_status.argtypes = [vp, vp]
     L.phiks_device_status.restype = ctypes.c_int
     L.phiks_tucker_noalloc.argtypes = [i, ctypes.POINTER(ctypes.c_int64), vp, vp, ctypes.POINTER(vp), vp]
@@ -331,6 +359,33 @@ class Batch:
         if self.handle:
             load().phiks_batch_destroy(self.handle)
             self.handle = None
+
+
+def phiks_serve_trace(requests, arrivals, slots=8, hbm_budget=0, poll_us=0):
+    """requests: list of lists of applies, each apply a dict with keys plan
+    (handle), tau, p, v (list of tensors), out, vnorms, and optionally
+    nscales, skip_phi0, tol.  Returns (latency_ms, queue_ms, makespan_s)."""
+    n = len(requests)
+    keep = []
+    arr = (Request * n)()
+    for k, apps in enumerate(requests):
+        arr[k].napply = len(apps)
+        for a, x in enumerate(apps):
+            vp = (ctypes.c_void_p * len(x["v"]))(*[_ptr(t) for t in x["v"]])
+            vn = (ctypes.c_double * len(x["vnorms"]))(*[float(t) for t in x["vnorms"]])
+            keep += [vp, vn]
+            arr[k].apply[a] = ApplyArgs(x["plan"], float(x["tau"]), int(x["p"]), len(x["v"]),
+                                        ctypes.cast(vp, ctypes.POINTER(ctypes.c_void_p)), _ptr(x["out"]),
+                                        int(x.get("nscales", 1)), int(x.get("skip_phi0", 0)),
+                                        float(x.get("tol", 0.0)),
+                                        ctypes.cast(vn, ctypes.POINTER(ctypes.c_double)))
+    at = (ctypes.c_double * n)(*[float(t) for t in arrivals])
+    lat = (ctypes.c_double * n)()
+    qd = (ctypes.c_double * n)()
+    mk = ctypes.c_double()
+    cfg = ServeConfig(int(slots), int(hbm_budget), int(poll_us))
+    _check(load().phiks_serve_trace(ctypes.byref(cfg), n, arr, at, lat, qd, ctypes.byref(mk)))
+    return list(lat), list(qd), mk.value
 
 
 def phiks_destroy(plan: int):

@@ -110,8 +110,6 @@ struct phiks_plan_s {
   uint64_t clock = 0;
   double* expm_scratch = nullptr;  // 3 x (q + 1) x sum_n2 doubles
   size_t expm_scratch_elems = 0;
-  double* msq[2] = {nullptr, nullptr};  // squaring chain ping-pong, sum_n2 each
-  uint8_t* msq_tcb[2] = {nullptr, nullptr};  // split path: B planes of msq
   uint8_t* tucker_tcb = nullptr;             // split path: B planes for phiks_tucker
   size_t tcb_off[PHIKS_MAX_D] = {0};         // per-mode offsets inside one plane set
   size_t tcb_bytes = 0;
@@ -156,16 +154,44 @@ int64_t mode_b(const phiks_plan_s* P, int mu) {
 
 size_t elt_size(const phiks_plan_s* P) { return P->dtype == PHIKS_FP64 ? 8 : 4; }
 
-// Workspace: p accumulators and two Tucker temporaries of N elements (FP64
-// accumulators even for the split dtypes, whose Tucker temporaries are float),
-// plus the split-operand staging of the tensor-core path.
-size_t workspace_bytes(const phiks_plan_s* P, int p) {
-  size_t N = (size_t)P->N;
-  size_t acc = (size_t)std::max(p, 1) * N * 8;
-  size_t tmp = 2 * N * 8;
-  size_t tcx = P->dtype == PHIKS_FP64 ? 0 : tc_workspace_bytes(P->N) + 1024;
-  return acc + tmp + tcx + 256 * 4;
+// Workspace of one apply, everything an apply writes besides its outputs, so
+// that applies with distinct workspaces never share device state:
+//   p FP64 accumulators | two FP64 Tucker temporaries | the squaring chain
+//   (two sets of d small FP64 matrices) | split dtypes: their B-operand planes
+//   and the operand planes of the tensor-core passes.  Every region starts on
+//   a 1 KiB boundary.
+struct WsLayout {
+  size_t acc, tmp, msq0, msq1, tcb0, tcb1, planes, total;
+};
+
+size_t up1k(size_t x) { return (x + 1023) / 1024 * 1024; }
+
+WsLayout ws_layout(const phiks_plan_s* P, int p) {
+  const size_t N = (size_t)P->N;
+  WsLayout w;
+  size_t o = 0;
+  w.acc = o;
+  o += up1k((size_t)std::max(p, 1) * N * 8);
+  w.tmp = o;
+  o += up1k(2 * N * 8);
+  w.msq0 = o;
+  o += up1k(P->sum_n2 * 8);
+  w.msq1 = o;
+  o += up1k(P->sum_n2 * 8);
+  w.tcb0 = w.tcb1 = w.planes = o;
+  if (P->dtype != PHIKS_FP64) {
+    w.tcb0 = o;
+    o += up1k(P->tcb_bytes);
+    w.tcb1 = o;
+    o += up1k(P->tcb_bytes);
+    w.planes = o;
+    o += up1k(tc_workspace_bytes(P->N));
+  }
+  w.total = o + 1024;  // room to align the base
+  return w;
 }
+
+size_t workspace_bytes(const phiks_plan_s* P, int p) { return ws_layout(P, p).total; }
 
 Rect tau_rect(const phiks_plan_s* P, double tau) {
   Rect r;
@@ -470,7 +496,26 @@ struct Ctx {
   cudaStream_t st;
   double* tmp[2];
   int tuckers = 0;
+  double* msq[2] = {nullptr, nullptr};      // squaring chain ping-pong
+  uint8_t* msq_tcb[2] = {nullptr, nullptr}; // split path: their B planes
 };
+
+// Point the context (and the split path) at the regions of workspace `ws`.
+void carve(Ctx& c, int p, char* ws, double** acc) {
+  phiks_plan_s* P = c.P;
+  uintptr_t base = ((uintptr_t)ws + 1023) & ~(uintptr_t)1023;
+  WsLayout w = ws_layout(P, p);
+  for (int l = 0; l < std::max(p, 1); ++l) acc[l] = (double*)(base + w.acc) + (size_t)l * P->N;
+  c.tmp[0] = (double*)(base + w.tmp);
+  c.tmp[1] = c.tmp[0] + P->N;
+  c.msq[0] = (double*)(base + w.msq0);
+  c.msq[1] = (double*)(base + w.msq1);
+  if (P->dtype != PHIKS_FP64) {
+    c.msq_tcb[0] = (uint8_t*)(base + w.tcb0);
+    c.msq_tcb[1] = (uint8_t*)(base + w.tcb1);
+    tc_bind_workspace(P->tc, (void*)(base + w.planes));
+  }
+}
 
 // The d matrices of one Tucker operator: FP64 (FP64 path) and their
 // B-operand planes (split path).
@@ -562,7 +607,7 @@ phiks_status square_modes(Ctx& c, Mats& M, int& cur_buf) {
     gb.n[mu] = (int)P->n[mu];
     gb.A[mu] = M.L[mu];
     gb.B[mu] = M.L[mu];
-    gb.C[mu] = P->msq[cur_buf] + off;
+    gb.C[mu] = c.msq[cur_buf] + off;
     gb.alpha[mu] = 1.0;
     gb.beta_I[mu] = 0.0;
     off += (size_t)P->n[mu] * P->n[mu];
@@ -570,10 +615,10 @@ phiks_status square_modes(Ctx& c, Mats& M, int& cur_buf) {
   CK(launch_gemm_batch_f64(gb, P->nmax, c.st));
   off = 0;
   for (int mu = 0; mu < P->d; ++mu) {
-    M.L[mu] = P->msq[cur_buf] + off;
+    M.L[mu] = c.msq[cur_buf] + off;
     off += (size_t)P->n[mu] * P->n[mu];
     if (P->dtype != PHIKS_FP64) {
-      uint8_t* dst = P->msq_tcb[cur_buf] + P->tcb_off[mu];
+      uint8_t* dst = c.msq_tcb[cur_buf] + P->tcb_off[mu];
       CK(tc_prepare_b(P->dtype, M.L[mu], (int)P->n[mu], dst, c.st));
       M.B[mu] = dst;
     }
@@ -864,8 +909,6 @@ phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dty
     for (int64_t i = 0; i < m; ++i) sh[i + m * i] -= P->sigma[mu];
     CK(cudaMemcpy(P->dAs + P->offA[mu], sh.data(), m * m * 8, cudaMemcpyHostToDevice));
   }
-  CK(cudaMalloc(&P->msq[0], tot * 8));
-  CK(cudaMalloc(&P->msq[1], tot * 8));
   CK(cudaMalloc(&P->d_norms, (PHIKS_MAX_P + 1) * 8));
   CK(cudaMallocHost(&P->h_norms, (PHIKS_MAX_P + 1) * 8));
   if (dtype != PHIKS_FP64) {
@@ -877,8 +920,6 @@ phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dty
       tb += tc_bplanes_bytes(dtype, (int)n[mu]);
     }
     P->tcb_bytes = tb;
-    CK(cudaMalloc(&P->msq_tcb[0], tb));
-    CK(cudaMalloc(&P->msq_tcb[1], tb));
     CK(cudaMalloc(&P->tucker_tcb, tb));
   }
   *out = P.release();
@@ -1060,13 +1101,9 @@ void phiks_destroy(phiks_plan_t P) {
     cudaFree(b.dev);
     if (b.tcb) cudaFree(b.tcb);
   }
-  cudaFree(P->msq_tcb[0]);
-  cudaFree(P->msq_tcb[1]);
   cudaFree(P->tucker_tcb);
   cudaFree(P->dAs);
   cudaFree(P->expm_scratch);
-  cudaFree(P->msq[0]);
-  cudaFree(P->msq[1]);
   cudaFree(P->ws);
   cudaFree(P->d_norms);
   cudaFreeHost(P->h_norms);
@@ -1227,14 +1264,8 @@ phiks_status phiks_apply_ex(phiks_plan_t P, double tau, int p, const void* const
     ws = (char*)P->ws;
   }
   double* acc[PHIKS_MAX_P];
-  for (int l = 0; l < std::max(p, 1); ++l) acc[l] = (double*)(ws + (size_t)l * N * 8);
   Ctx c{P, st, {nullptr, nullptr}, 0};
-  c.tmp[0] = (double*)(ws + (size_t)std::max(p, 1) * N * 8);
-  c.tmp[1] = c.tmp[0] + N;
-  if (P->dtype != PHIKS_FP64) {
-    uintptr_t t = (uintptr_t)(ws + (size_t)(std::max(p, 1) + 2) * N * 8);
-    tc_bind_workspace(P->tc, (void*)((t + 1023) & ~(uintptr_t)1023));
-  }
+  carve(c, p, ws, acc);
 
   Bank* B = nullptr;
   TRY(get_bank(P, tau, s, q, o.rule, o.no_cache != 0, st, &B));
@@ -1271,10 +1302,9 @@ phiks_status phiks_tucker(phiks_plan_t P, const void* V, void* W, const double* 
     CK(cudaMalloc(&P->ws, need));
     P->ws_bytes = need;
   }
-  const int64_t N = P->N;
   Ctx c{P, (cudaStream_t)stream, {nullptr, nullptr}, 0};
-  c.tmp[0] = (double*)((char*)P->ws + (size_t)N * 8);
-  c.tmp[1] = c.tmp[0] + N;
+  double* acc[PHIKS_MAX_P];
+  carve(c, 1, (char*)P->ws, acc);
   const bool f32 = P->dtype != PHIKS_FP64;
   Mats M;
   for (int mu = 0; mu < P->d; ++mu) {
@@ -1282,8 +1312,6 @@ phiks_status phiks_tucker(phiks_plan_t P, const void* V, void* W, const double* 
     M.B[mu] = nullptr;
   }
   if (f32) {
-    uintptr_t t = (uintptr_t)((char*)P->ws + 3 * (size_t)N * 8);
-    tc_bind_workspace(P->tc, (void*)((t + 1023) & ~(uintptr_t)1023));
     for (int mu = 0; mu < P->d; ++mu) {
       uint8_t* dst = P->tucker_tcb + P->tcb_off[mu];
       CK(tc_prepare_b(P->dtype, L[mu], (int)P->n[mu], dst, c.st));
