@@ -55,6 +55,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms: float, world: int) -> float:
+    """Slowest rank's timed milliseconds (gloo all-reduce when world > 1)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
+def whole_job_rate(units_per_rank_step: int, steps: int, world: int, ms_total: float) -> float:
+    """Units per second of all ranks together (weak scaling: every rank runs
+    its own replica of the workload)."""
+    return world * units_per_rank_step * steps / (ms_total * 1e-3)
+
+
 def oracle_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -208,14 +225,9 @@ def run_phiks(args):
     launches = pk.phiks_kernel_launches() - launches0
     barrier()
     clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t[0])
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), ws)
     ms_step = ms / args.steps
-    value = ws * wl.nscales * args.steps / (ms * 1e-3)
+    value = whole_job_rate(wl.nscales, args.steps, ws, ms)
     gpu_out = out.cpu().numpy().copy()
 
     # ---- kernel-level pass: events around every mu-mode product launch
@@ -521,6 +533,122 @@ def run_batched(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+def build_served(pk, torch, arrivals, specs, dtype_name, tol_rel):
+    """Device-resident plans per (class, n, species), seeded inputs per
+    (class, n), one output per apply; returns (requests, plans, n_applies)."""
+    dt = pk.DTYPES[dtype_name]
+    tdt = torch.float64 if dtype_name == "fp64" else torch.float32
+    plans, inputs = {}, {}
+    requests = []
+    n_applies = 0
+    for k, (cls, n, p) in enumerate(specs):
+        if cls == "ac":
+            ops = [wk.ac_operator(n)]
+        elif cls == "adr":
+            ops = [[wk.fd_adr_dirichlet(n, 1.0, a, 2.0 / 3) for a in (10.0, -20.0, 5.0)]]
+        else:
+            ops = list(wk.brusselator_operators(n))
+        N = int(np.prod([a.shape[0] for a in ops[0]]))
+        key = (cls, n)
+        if key not in inputs:
+            seed = 1000000 + hash(key) % 100000
+            vs = [wk.normal(seed + l, N).astype(np.float32).astype(np.float64) for l in range(5)]
+            inputs[key] = ([torch.from_numpy(v).to(device="cuda", dtype=tdt) for v in vs],
+                           [float(np.linalg.norm(v)) for v in vs])
+        vdev, vn = inputs[key]
+        apps = []
+        for sp, A in enumerate(ops):
+            pkey = (cls, n, sp)
+            if pkey not in plans:
+                plans[pkey] = pk.Plan(A, dt)
+            out = torch.empty(N, device="cuda", dtype=tdt)
+            x = {"plan": plans[pkey].handle, "tau": wk.SERVED_CLASSES[cls]["tau"], "p": p,
+                 "v": vdev[: p + 1], "out": out, "vnorms": vn[: p + 1]}
+            if tol_rel is not None:
+                x["tol"] = tol_rel * max(vn[: p + 1])
+            apps.append(x)
+            n_applies += 1
+        requests.append(apps)
+    return requests, plans, n_applies
+
+
+def warm_served(pk, torch, requests):
+    """One apply per distinct (plan, p): parameter search and exponentials
+    happen here, not while serving."""
+    seen = set()
+    for apps in requests:
+        for x in apps:
+            key = (x["plan"], x["p"])
+            if key in seen:
+                continue
+            seen.add(key)
+            kw = dict(vnorms=x["vnorms"])
+            if "tol" in x:
+                kw["tol"] = x["tol"]
+            pk.phiks_apply_ex(x["plan"], x["tau"], x["p"], x["v"], x["out"], None, **kw)
+    torch.cuda.synchronize()
+
+
+def run_served(args):
+    """The served form: Poisson arrivals of Allen-Cahn, ADR and Brusselator
+    stage requests (linear combinations, p in {2,3,4}), continuous batching
+    over `slots` streams with HBM-budget admission, p50/p99 latency."""
+    import torch
+    import paper_2210_07667_gb300 as pk
+    pk.load(build_if_missing=True)
+    torch.cuda.set_device(0)
+    name = "bf16x3" if args.dtype == "all" else args.dtype
+    arrivals, specs = wk.served_trace(args.requests, args.rate, size_cap=args.size_cap)
+    t0 = time.perf_counter()
+    requests, plans, n_app = build_served(pk, torch, arrivals, specs, name, PRECISION_TOL[name])
+    warm_served(pk, torch, requests)
+    setup_s = time.perf_counter() - t0
+    res = {}
+    lat, qd, mk = pk.phiks_serve_trace(requests, arrivals, slots=args.slots,
+                                       hbm_budget=int(args.budget_gb * (1 << 30)))
+    lat = np.array(lat)
+    res[name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                 "mean_ms": float(lat.mean()), "queue_p50_ms": float(np.percentile(qd, 50)),
+                 "makespan_s": mk, "requests_per_s": len(requests) / mk, "phi_actions_per_s": n_app / mk,
+                 "slots": args.slots, "setup_s": setup_s}
+    # the same trace, all at once on one slot: the service rate without overlap
+    lat1, _, mk1 = pk.phiks_serve_trace(requests, np.zeros(len(requests)), slots=1)
+    res[name + "_one_slot"] = {"makespan_s": mk1, "phi_actions_per_s": n_app / mk1}
+    latb, _, mkb = pk.phiks_serve_trace(requests, np.zeros(len(requests)), slots=args.slots,
+                                        hbm_budget=int(args.budget_gb * (1 << 30)))
+    res[name + "_saturated"] = {"makespan_s": mkb, "phi_actions_per_s": n_app / mkb}
+    for p in plans.values():
+        p.close()
+    if not args.no_ref:
+        req64, plans64, _ = build_served(pk, torch, arrivals, specs, "fp64", None)
+        warm_served(pk, torch, req64)
+        _, _, mk64 = pk.phiks_serve_trace(req64, np.zeros(len(req64)), slots=1)
+        res["fp64_one_slot"] = {"makespan_s": mk64, "phi_actions_per_s": n_app / mk64}
+        res[name + "_saturated"]["speedup_vs_fp64"] = mk64 / mkb
+        errs = []
+        for a32, a64 in zip(requests, req64):
+            for x, y in zip(a32, a64):
+                o, r = x["out"].double().cpu().numpy(), y["out"].cpu().numpy()
+                errs.append(float(np.abs(o - r).max() / np.abs(r).max()))
+        res[name]["rel_err_vs_fp64_max"] = max(errs)
+        for p in plans64.values():
+            p.close()
+    h = res[name]
+    line = {"metric": METRIC, "value": h["phi_actions_per_s"], "unit": "phi-actions/s", "n_gpus": 1,
+            "steps": 1, "warmup": 1, "ms_per_step": 1e3 * h["makespan_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": name, "data": "synthetic",
+            "config": {"workload": "served_ac_adr_bru", "requests": len(requests), "applies": n_app,
+                       "offered_rate_per_s": args.rate, "p": "2..4", "mode": "lincomb",
+                       "sizes": {"ac": "128..%d" % min(1024, args.size_cap or 1024),
+                                 "adr": "32..%d" % min(192, args.size_cap or 192),
+                                 "bru": "128..%d" % min(512, args.size_cap or 512)},
+                       "slots": args.slots, "hbm_budget_gb": args.budget_gb},
+            "latency_ms": {"p50": h["p50_ms"], "p99": h["p99_ms"]}, "per_variant": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -528,7 +656,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="phiks", choices=["phiks", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="adr3d", choices=["adr3d", "precision", "batched"],
+    ap.add_argument("--config", default="adr3d", choices=["adr3d", "precision", "batched", "served"],
                     help="adr3d: the headline FP64 workload; precision: the split-dtype form")
     ap.add_argument("--dtype", default="all", choices=["all"] + PRECISION_DTYPES)
     ap.add_argument("--variant", default="cheb", choices=["cheb", "fd"])
@@ -536,6 +664,11 @@ def main():
     ap.add_argument("--no-ref", action="store_true", help="skip the FP64 reference path")
     ap.add_argument("--count", type=int, default=256, help="batched form: instances")
     ap.add_argument("--streams", type=int, default=16, help="batched form: worker streams")
+    ap.add_argument("--requests", type=int, default=2000, help="served form: trace length")
+    ap.add_argument("--rate", type=float, default=2000.0, help="served form: arrivals per second")
+    ap.add_argument("--slots", type=int, default=16, help="served form: concurrent requests")
+    ap.add_argument("--budget-gb", type=float, default=64.0, help="served form: workspace budget")
+    ap.add_argument("--size-cap", type=int, default=None, help="served form: largest n")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -543,6 +676,8 @@ def main():
         return run_precision(args)
     if args.config == "batched":
         return run_batched(args)
+    if args.config == "served":
+        return run_served(args)
     return run_phiks(args)
 
 

@@ -218,10 +218,9 @@ struct GemmParams {
   int num_tiles;  // ceil(M2 / 128) * n_ntiles
   int stages;
   int tmem_cols;
-  int last;       // 0: write planes for the next pass; 1: final epilogue
+  int last;       // 0: write planes for the next pass; 1: write FP32 results to out0
   void* out0;
   void* out1;
-  Epi epi;
   int* status;
 };
 
@@ -373,23 +372,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int i = r0 + c0 + j;
           if (i >= P.n) break;
           const int64_t idx = col + P.M2 * (int64_t)i;
-          if (!P.last) {
-            split_store_f<KIND, NP>(P.out0, P.out1, idx, v[j]);
-          } else {
-            const Epi& e = P.epi;
-            const double res = (double)v[j];
-            double sv[kMaxSrc];
-            for (int m = 0; m < e.nsrc; ++m)
-              sv[m] = ((e.src_f32mask >> m) & 1) ? (double)((const float*)e.src[m])[idx]
-                                                 : e.src[m][idx];
-            for (int tt = 0; tt < e.nout; ++tt) {
-              double o = e.b[tt] * res;
-              for (int m = 0; m < e.nsrc; ++m)
-                if (e.a[tt][m] != 0.0) o = fma(e.a[tt][m], sv[m], o);
-              if ((e.out_f32mask >> tt) & 1) ((float*)e.out[tt])[idx] = (float)o;
-              else e.out[tt][idx] = o;
-            }
-          }
+          if (!P.last) split_store_f<KIND, NP>(P.out0, P.out1, idx, v[j]);
+          else ((float*)P.out0)[idx] = v[j];
         }
       }
       tc_fence_before();
@@ -690,7 +674,6 @@ cudaError_t tc_tucker(TcState* s, const Combo& in, const void* const* Bp, const 
     P.last = (mu == s->d - 1);
     P.out0 = set[1 - cur][0];
     P.out1 = set[1 - cur][1];
-    P.epi = epi;
     P.status = s->status;
     cudaError_t e;
     if (dtype == PHIKS_BF16X3) e = run_gemm<0, 2>(s, mA, mB, P, st);
@@ -699,7 +682,16 @@ cudaError_t tc_tucker(TcState* s, const Combo& in, const void* const* Bp, const 
     if (e != cudaSuccess) return e;
     cur = 1 - cur;
   }
-  return cudaSuccess;
+  // FP64 epilogue over all N elements with the whole GPU: the result plane is
+  // one more (float) source whose coefficient in output t is epi.b[t]
+  Epi f = epi;
+  const int m = f.nsrc;
+  if (m >= kMaxSrc) return cudaErrorInvalidValue;
+  f.src[m] = (const double*)set[cur][0];
+  f.src_f32mask |= 1 << m;
+  for (int t = 0; t < f.nout; ++t) f.a[t][m] = epi.b[t];
+  f.nsrc = m + 1;
+  return launch_combine(f, N, st);
 }
 
 int tc_read_status(TcState* s, cudaStream_t st) {

@@ -38,14 +38,7 @@ __device__ __forceinline__ void store_epi(const Epi& epi, double* W, int64_t idx
     W[idx] = res;
     return;
   }
-  double sv[kMaxSrc];
-  for (int m = 0; m < epi.nsrc; ++m) sv[m] = epi.src[m][idx];
-  for (int t = 0; t < epi.nout; ++t) {
-    double o = epi.b[t] * res;
-    for (int m = 0; m < epi.nsrc; ++m)
-      if (epi.a[t][m] != 0.0) o = fma(epi.a[t][m], sv[m], o);
-    epi.out[t][idx] = o;
-  }
+  epi_apply(epi, idx, res);
 }
 
 // CTA tile: TI rows of L x TC columns c = x + a y; RI x RC outputs per thread
@@ -169,18 +162,8 @@ void launch_tiled(const Combo& pro, const double* L, ModeGeom g, double* W, cons
 
 __global__ void combine_kernel(Epi e, int64_t N) {
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    double sv[kMaxSrc];
-    for (int m = 0; m < e.nsrc; ++m)
-      sv[m] = ((e.src_f32mask >> m) & 1) ? (double)((const float*)e.src[m])[idx] : e.src[m][idx];
-    for (int t = 0; t < e.nout; ++t) {
-      double o = 0.0;
-      for (int m = 0; m < e.nsrc; ++m)
-        if (e.a[t][m] != 0.0) o = fma(e.a[t][m], sv[m], o);
-      if ((e.out_f32mask >> t) & 1) ((float*)e.out[t])[idx] = (float)o;
-      else e.out[t][idx] = o;
-    }
-  }
+       idx += (int64_t)gridDim.x * blockDim.x)
+    epi_apply(e, idx, 0.0);
 }
 
 struct PtrArray {
@@ -224,6 +207,7 @@ cudaError_t launch_mode_product_f64(const Combo& pro, const double* L, ModeGeom 
     e.nout = 0;
     e.nsrc = 0;
   }
+  epi_finalize(e);
   count_launch();
   // Large problems: 32 x 64 tiles (256 threads, 8 outputs each).  Otherwise
   // 16 x 16 tiles (64 threads, 4 outputs each), so that even N = 2^18 spreads
@@ -236,8 +220,12 @@ cudaError_t launch_mode_product_f64(const Combo& pro, const double* L, ModeGeom 
   return cudaGetLastError();
 }
 
-cudaError_t launch_combine(const Epi& e, int64_t N, cudaStream_t st) {
+cudaError_t launch_combine(const Epi& e0, int64_t N, cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
+  Epi e = e0;
+  e.nout = e0.nout;
+  for (int t = 0; t < kMaxOut; ++t) e.b[t] = 0.0;  // no product result here
+  epi_finalize(e);
   count_launch();
   combine_kernel<<<grid_for(N, 256), 256, 0, st>>>(e, N);
   return cudaGetLastError();

@@ -198,3 +198,48 @@ def batched_instances(count: int = 256, seed: int = 1000):
         N = int(np.prod(dims))
         out.append(Workload("inst%d" % k, A, tau, 3, "same", 1, [normal(s, N)], skip_phi0=True))
     return out
+
+
+# ----------------------------------------------------------------------------
+# Served form: a Poisson stream of exponential-integrator stage requests.
+# ----------------------------------------------------------------------------
+
+def ac_operator(n: int, eps: float = 0.01):
+    """2D Allen-Cahn linear part eps*Laplacian + I (homogeneous Neumann):
+    A_mu = eps*d_xx + I/2 per mode."""
+    A = fd_laplacian_neumann(n, eps, 0.5)
+    return [A, A.copy(order="F")]
+
+
+def brusselator_operators(n: int, d1: float = 0.002, d2: float = 0.001, b: float = 3.0):
+    """2D Brusselator, two species: K_1 = d1*Laplacian - (b+1) I,
+    K_2 = d2*Laplacian (homogeneous Neumann)."""
+    A1 = fd_laplacian_neumann(n, d1, -(b + 1.0) / 2.0)
+    A2 = fd_laplacian_neumann(n, d2, 0.0)
+    return [A1, A1.copy(order="F")], [A2, A2.copy(order="F")]
+
+
+SERVED_CLASSES = {
+    "ac": {"sizes": list(range(128, 1025, 32)), "tau": 1e-3},
+    "adr": {"sizes": list(range(32, 193, 16)), "tau": 5e-4},
+    "bru": {"sizes": list(range(128, 513, 32)), "tau": 1e-2},
+}
+
+
+def served_trace(count: int, rate: float, seed_arrivals: int = 7, seed_mix: int = 8,
+                 pmin: int = 2, pmax: int = 4, classes=("ac", "adr", "bru"), size_cap=None):
+    """Arrival times (Poisson, mean `rate` per second) and request specs:
+    (class, n, p).  Classes uniform; n uniform over the class sizes (at most
+    size_cap); p uniform in [pmin, pmax]."""
+    u = uniform(seed_arrivals, count, 0.0, 1.0)
+    gaps = -np.log1p(-u) / rate
+    arrivals = np.cumsum(gaps)
+    r = uniform(seed_mix, 3 * count, 0.0, 1.0).reshape(count, 3)
+    specs = []
+    for k in range(count):
+        cls = classes[min(int(r[k, 0] * len(classes)), len(classes) - 1)]
+        sizes = [s for s in SERVED_CLASSES[cls]["sizes"] if size_cap is None or s <= size_cap]
+        n = sizes[min(int(r[k, 1] * len(sizes)), len(sizes) - 1)]
+        p = pmin + min(int(r[k, 2] * (pmax - pmin + 1)), pmax - pmin)
+        specs.append((cls, n, p))
+    return arrivals, specs
