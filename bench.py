@@ -617,7 +617,18 @@ def run_served(args):
     res[name + "_one_slot"] = {"makespan_s": mk1, "phi_actions_per_s": n_app / mk1}
     latb, _, mkb = pk.phiks_serve_trace(requests, np.zeros(len(requests)), slots=args.slots,
                                         hbm_budget=int(args.budget_gb * (1 << 30)))
-    res[name + "_saturated"] = {"makespan_s": mkb, "phi_actions_per_s": n_app / mkb}
+    res[name + "_saturated"] = {"makespan_s": mkb, "phi_actions_per_s": n_app / mkb,
+                                "requests_per_s": len(requests) / mkb}
+    # the same requests offered at half the saturated rate: latency without
+    # an ever-growing queue
+    cap = len(requests) / mkb
+    half = arrivals * (args.rate / (0.5 * cap))
+    lath, qh, mkh = pk.phiks_serve_trace(requests, half, slots=args.slots,
+                                         hbm_budget=int(args.budget_gb * (1 << 30)))
+    lath = np.array(lath)
+    res[name + "_half_load"] = {"offered_rate_per_s": 0.5 * cap, "p50_ms": float(np.percentile(lath, 50)),
+                                "p99_ms": float(np.percentile(lath, 99)),
+                                "queue_p50_ms": float(np.percentile(qh, 50)), "makespan_s": mkh}
     for p in plans.values():
         p.close()
     if not args.no_ref:
@@ -644,8 +655,70 @@ def run_served(args):
                                  "adr": "32..%d" % min(192, args.size_cap or 192),
                                  "bru": "128..%d" % min(512, args.size_cap or 512)},
                        "slots": args.slots, "hbm_budget_gb": args.budget_gb},
-            "latency_ms": {"p50": h["p50_ms"], "p99": h["p99_ms"]}, "per_variant": res}
+            "latency_ms": {"p50": h["p50_ms"], "p99": h["p99_ms"],
+                           "p50_half_load": res[name + "_half_load"]["p50_ms"],
+                           "p99_half_load": res[name + "_half_load"]["p99_ms"]},
+            "per_variant": res}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_small(args):
+    """The latency case: d = 2, n = 32 (N = 1024), FD Laplacian + 0.5 d_x,
+    phi_0..phi_3 of one vector, FP64.  One call is captured in a CUDA graph
+    and replayed; reports calls/s and phi-actions/s (4 per call)."""
+    import torch
+    import paper_2210_07667_gb300 as pk
+    pk.load(build_if_missing=True)
+    torch.cuda.set_device(0)
+    wl = wk.small_same(32)
+    plan = pk.Plan(wl.A, pk.PHIKS_FP64)
+    v = torch.from_numpy(wl.vs[0]).cuda()
+    out = torch.empty(4 * wl.N, device="cuda", dtype=torch.float64)
+    opts = pk.make_options(vnorms=[float(np.linalg.norm(wl.vs[0]))])
+    stream = torch.cuda.Stream()
+    inst = [(plan.handle, wl.tau, 3, [v], out, opts)]
+    batch = pk.Batch(1)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            batch.apply(inst, stream)
+    torch.cuda.synchronize()
+    graph = batch.capture(inst, stream)
+    reps = args.reps
+    for _ in range(max(args.warmup, 3)):
+        batch.launch(graph, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(reps):
+            batch.launch(graph, stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    # direct calls (host issue included), for comparison
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(200):
+            pk.phiks_apply_ex(plan.handle, wl.tau, 3, [v], out, stream, opts=opts)
+    torch.cuda.synchronize()
+    ms_direct = (time.perf_counter() - t0) * 1e3 / 200
+    got = out.cpu().numpy().reshape(4, wl.N)
+    from oracle import dense
+    ref = dense.same(wl.A, wl.tau, wl.vs[0], 3)
+    err = max(float(np.abs(got[l] - ref[l]).max() / np.abs(ref[l]).max()) for l in range(4))
+    s_, q_, T_, tk = plan.last_params()
+    line = {"metric": METRIC, "value": 4 / (ms * 1e-3), "unit": "phi-actions/s", "n_gpus": 1,
+            "steps": reps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "d": 2, "n": [32, 32], "N": 1024, "p": 3, "mode": "same",
+                       "tau": wl.tau, "s": s_, "q": q_, "tuckers": tk, "replay": "CUDA graph"},
+            "calls_per_s": 1e3 / ms, "direct_call_ms": ms_direct, "rel_err_vs_oracle": err}
+    print(json.dumps(line), flush=True)
+    batch.destroy_graph(graph)
+    batch.close()
+    plan.close()
     return 0
 
 
@@ -656,7 +729,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="phiks", choices=["phiks", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="adr3d", choices=["adr3d", "precision", "batched", "served"],
+    ap.add_argument("--config", default="adr3d", choices=["adr3d", "small", "precision", "batched", "served"],
                     help="adr3d: the headline FP64 workload; precision: the split-dtype form")
     ap.add_argument("--dtype", default="all", choices=["all"] + PRECISION_DTYPES)
     ap.add_argument("--variant", default="cheb", choices=["cheb", "fd"])
@@ -665,6 +738,7 @@ def main():
     ap.add_argument("--count", type=int, default=256, help="batched form: instances")
     ap.add_argument("--streams", type=int, default=16, help="batched form: worker streams")
     ap.add_argument("--requests", type=int, default=2000, help="served form: trace length")
+    ap.add_argument("--reps", type=int, default=10000, help="small: graph replays")
     ap.add_argument("--rate", type=float, default=2000.0, help="served form: arrivals per second")
     ap.add_argument("--slots", type=int, default=16, help="served form: concurrent requests")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="served form: workspace budget")
@@ -678,6 +752,8 @@ def main():
         return run_batched(args)
     if args.config == "served":
         return run_served(args)
+    if args.config == "small":
+        return run_small(args)
     return run_phiks(args)
 
 
