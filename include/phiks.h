@@ -271,6 +271,27 @@ phiks_status phiks_serve_trace(const phiks_serve_config* cfg, int count, const p
                                const double* arrival_s, double* latency_ms, double* queue_ms,
                                double* makespan_s);
 
+/* Exponential integrators driving phiks (Sec. 2): exponential Euler
+ * (eq. expEullc) and ETD2RK (eq. ETD2RKlc), each stage one linear
+ * combination, with the nonlinear term g evaluated on the device. */
+typedef enum { PHIKS_EXP_EULER = 0, PHIKS_ETD2RK = 1 } phiks_scheme;
+typedef enum {
+  PHIKS_NL_ADR_EXACT = 0,   /* Sec. 4.2: g = 1/(1+u^2) + Psi(t,x), exact solution e^t u_0 on the
+                               Dirichlet grid of [0,1]^3 (d = 3) */
+  PHIKS_NL_ALLEN_CAHN = 1   /* Sec. 4.3: g = -u^3 / eps^2 */
+} phiks_nonlinearity;
+typedef struct {
+  int kind;                 /* phiks_nonlinearity */
+  double eps, alpha;        /* ADR: diffusion and advection coefficients; AC: eps */
+} phiks_nonlinear;
+
+/* Advance u (device, N doubles, FP64 plan of K) from t0 to t0 + T in `steps`
+ * equal steps.  n: host, d grid sizes (the plan's n_mu).  Each stage
+ * synchronises `stream` once (the norms for the parameter selection). */
+phiks_status phiks_integrate(phiks_plan_t plan, const int64_t* n, int d, int scheme,
+                             const phiks_nonlinear* g, double t0, double T, int steps, double* u,
+                             void* stream);
+
 /* Release the plan and its device memory (synchronises its device). */
 void phiks_destroy(phiks_plan_t plan);
 

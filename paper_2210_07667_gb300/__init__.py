@@ -20,7 +20,7 @@ __all__ = [
     "phiks_plan", "phiks_apply", "phiks_apply_ex", "phiks_workspace_size",
     "phiks_select_params", "phiks_choose_params", "phiks_last_params", "phiks_tucker", "phiks_expm",
     "phiks_profile_enable", "phiks_profile_read", "phiks_kernel_launches", "phiks_tucker_noalloc",
-    "phiks_device_status", "phiks_serve_trace", "phiks_destroy", "phiks_last_error", "Plan", "Batch",
+    "phiks_device_status", "phiks_serve_trace", "phiks_integrate", "phiks_destroy", "phiks_last_error", "Plan", "Batch",
     "EXPORTED",
 ]
 
@@ -36,7 +36,7 @@ EXPORTED = [
     "phiks_profile_enable", "phiks_profile_read", "phiks_kernel_launches", "phiks_tucker_noalloc",
     "phiks_device_status", "phiks_batch_create", "phiks_batch_destroy", "phiks_batch_apply",
     "phiks_batch_capture", "phiks_graph_launch", "phiks_graph_destroy", "phiks_serve_trace",
-    "phiks_destroy", "phiks_last_error",
+    "phiks_integrate", "phiks_destroy", "phiks_last_error",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -85,6 +85,14 @@ class Request(ctypes.Structure):
 
 class ServeConfig(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("poll_us", ctypes.c_int)]
+
+
+class Nonlinear(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("eps", ctypes.c_double), ("alpha", ctypes.c_double)]
+
+
+PHIKS_EXP_EULER, PHIKS_ETD2RK = 0, 1
+PHIKS_NL_ADR_EXACT, PHIKS_NL_ALLEN_CAHN = 0, 1
 
 
 class PhiksError(RuntimeError):
@@ -151,6 +159,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                                     ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
                                     ctypes.POINTER(d)]
     L.phiks_serve_trace.restype = ctypes.c_int
+    L.phiks_integrate.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), i, i, ctypes.POINTER(Nonlinear),
+                                  d, d, i, vp, vp]
+    L.phiks_integrate.restype = ctypes.c_int
     L.phiks_device_status.argtypes = [vp, vp]
     L.phiks_device_status.restype = ctypes.c_int
     L.phiks_tucker_noalloc.argtypes = [i, ctypes.POINTER(ctypes.c_int64), vp, vp, ctypes.POINTER(vp), vp]
@@ -386,6 +397,15 @@ def phiks_serve_trace(requests, arrivals, slots=8, hbm_budget=0, poll_us=0):
     cfg = ServeConfig(int(slots), int(hbm_budget), int(poll_us))
     _check(load().phiks_serve_trace(ctypes.byref(cfg), n, arr, at, lat, qd, ctypes.byref(mk)))
     return list(lat), list(qd), mk.value
+
+
+def phiks_integrate(plan: int, dims, scheme: int, kind: int, eps: float, alpha: float, t0: float,
+                    T: float, steps: int, u, stream=None):
+    """Advance u in place with exponential Euler or ETD2RK (see include/phiks.h)."""
+    n = (ctypes.c_int64 * len(dims))(*[int(m) for m in dims])
+    nl = Nonlinear(int(kind), float(eps), float(alpha))
+    _check(load().phiks_integrate(plan, n, len(dims), int(scheme), ctypes.byref(nl), float(t0), float(T),
+                                  int(steps), _ptr(u), _stream(stream)))
 
 
 def phiks_destroy(plan: int):
