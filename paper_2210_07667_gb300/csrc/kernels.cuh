@@ -40,45 +40,49 @@ struct Epi {
   const double* src[kMaxSrc];
   double b[kMaxOut];
   double a[kMaxOut][kMaxSrc];
-  // filled by epi_finalize (the launchers call it): bit m of nz[t] set when
-  // a[t][m] != 0, bit t of bnz set when b[t] != 0, so that device code tests
-  // integers instead of spending FP64-pipe cycles on comparisons
-  unsigned short nz[kMaxOut];
+  // filled by epi_finalize (the launchers call it): the nonzero a[t][m] as a
+  // flat list of terms, so that device code issues exactly one FP64 FMA per
+  // term (predicated-off FP64 instructions would still occupy the slow FP64
+  // pipe), and bit t of bnz set when b[t] != 0
+  int nterm;
+  unsigned char term_t[kMaxOut * kMaxSrc];
+  unsigned char term_m[kMaxOut * kMaxSrc];
+  double term_c[kMaxOut * kMaxSrc];
   unsigned char bnz;
 };
 
 inline void epi_finalize(Epi& e) {
   e.bnz = 0;
-  for (int t = 0; t < kMaxOut; ++t) {
-    e.nz[t] = 0;
-    if (t >= e.nout) continue;
+  e.nterm = 0;
+  for (int t = 0; t < e.nout && t < kMaxOut; ++t) {
     if (e.b[t] != 0.0) e.bnz |= (unsigned char)(1u << t);
     for (int m = 0; m < e.nsrc && m < kMaxSrc; ++m)
-      if (e.a[t][m] != 0.0) e.nz[t] |= (unsigned short)(1u << m);
+      if (e.a[t][m] != 0.0) {
+        e.term_t[e.nterm] = (unsigned char)t;
+        e.term_m[e.nterm] = (unsigned char)m;
+        e.term_c[e.nterm] = e.a[t][m];
+        e.nterm++;
+      }
   }
 }
 
 // out[t][idx] for every output of `e`, given the product result `res`
-// (device helper shared by the epilogues; sources loaded once, loops unrolled
-// over the fixed maxima so that everything stays in registers).
+// (device helper shared by the epilogues).
 #ifdef __CUDACC__
 __device__ __forceinline__ void epi_apply(const Epi& e, int64_t idx, double res) {
   double sv[kMaxSrc];
-#pragma unroll
-  for (int m = 0; m < kMaxSrc; ++m) {
-    sv[m] = 0.0;
-    if (m < e.nsrc)
-      sv[m] = ((e.src_f32mask >> m) & 1) ? (double)((const float*)e.src[m])[idx] : e.src[m][idx];
-  }
-#pragma unroll
-  for (int t = 0; t < kMaxOut; ++t) {
-    if (t >= e.nout) break;
-    double o = ((e.bnz >> t) & 1) ? e.b[t] * res : 0.0;
-#pragma unroll
-    for (int m = 0; m < kMaxSrc; ++m)
-      if ((e.nz[t] >> m) & 1) o = fma(e.a[t][m], sv[m], o);
-    if ((e.out_f32mask >> t) & 1) ((float*)e.out[t])[idx] = (float)o;
-    else e.out[t][idx] = o;
+  double o[kMaxOut];
+#pragma unroll 1
+  for (int m = 0; m < e.nsrc; ++m)
+    sv[m] = ((e.src_f32mask >> m) & 1) ? (double)((const float*)e.src[m])[idx] : e.src[m][idx];
+#pragma unroll 1
+  for (int t = 0; t < e.nout; ++t) o[t] = ((e.bnz >> t) & 1) ? e.b[t] * res : 0.0;
+#pragma unroll 1
+  for (int k = 0; k < e.nterm; ++k) o[e.term_t[k]] = fma(e.term_c[k], sv[e.term_m[k]], o[e.term_t[k]]);
+#pragma unroll 1
+  for (int t = 0; t < e.nout; ++t) {
+    if ((e.out_f32mask >> t) & 1) ((float*)e.out[t])[idx] = (float)o[t];
+    else e.out[t][idx] = o[t];
   }
 }
 #endif

@@ -33,12 +33,18 @@ __device__ __forceinline__ double load_combo(const Combo& pro, int64_t idx, bool
   return v;
 }
 
+// Kept out of line so that the local arrays of the epilogue do not affect the
+// register allocation of the contraction loop.
+__device__ __noinline__ void epi_apply_call(const Epi& epi, int64_t idx, double res) {
+  epi_apply(epi, idx, res);
+}
+
 __device__ __forceinline__ void store_epi(const Epi& epi, double* W, int64_t idx, double res) {
   if (epi.nout == 0) {
     W[idx] = res;
     return;
   }
-  epi_apply(epi, idx, res);
+  epi_apply_call(epi, idx, res);
 }
 
 // CTA tile: TI rows of L x TC columns c = x + a y; RI x RC outputs per thread
