@@ -58,12 +58,18 @@ typedef enum {
   PHIKS_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up */
 } phiks_status;
 
-/* Arithmetic of the mu-mode products.  FP64: vectors are double.  The split
- * types keep vectors in float and run the products on the tensor cores:
- * TF32 (one product), TF32X3 and BF16X3 (three-term compensated products,
- * hi*hi + hi*lo + lo*hi, FP32 accumulation).  Small exponentials, their
- * squaring and the doubling-formula combination stay FP64 in every type. */
-typedef enum { PHIKS_FP64 = 0, PHIKS_TF32 = 1, PHIKS_TF32X3 = 2, PHIKS_BF16X3 = 3 } phiks_dtype;
+/* Arithmetic of the mu-mode products.  FP64: vectors are double, products on
+ * the FP64 pipe.  The split types keep vectors in float and run the products
+ * on the tensor cores: TF32 (one product), TF32X3 and BF16X3 (three-term
+ * compensated products, hi*hi + hi*lo + lo*hi, FP32 accumulation).
+ * FP64_EMU: vectors double, products on the tensor cores as exact sums of
+ * bf16 digit products (seven base-256 digits per operand, FP32 accumulation
+ * that stays exact for n_mu <= 128), rounded once to FP64; needs every n_mu a
+ * multiple of 8 and at most 128.  Small exponentials, their squaring and the
+ * doubling-formula combination stay FP64 in every type. */
+typedef enum {
+  PHIKS_FP64 = 0, PHIKS_TF32 = 1, PHIKS_TF32X3 = 2, PHIKS_BF16X3 = 3, PHIKS_FP64_EMU = 4
+} phiks_dtype;
 
 /* Quadrature rule for the phi integral (Sec. 3.3): Gauss-Lobatto-Legendre
  * (default; theta_1 = 0 and theta_q = 1 save one Tucker operator each) or
@@ -112,7 +118,7 @@ phiks_status phiks_apply(phiks_plan_t plan, double tau, int p, const void* const
  *   tau      time step (any nonzero real)
  *   p        highest phi order, 0 <= p <= PHIKS_MAX_P
  *   v        host array of nv device pointers to N elements each (double for
- *            PHIKS_FP64, float otherwise); in the linear combination any v[l]
+ *            PHIKS_FP64 and PHIKS_FP64_EMU, float otherwise); in the linear combination any v[l]
  *            may be NULL (a zero vector; v[0] == NULL skips the exp Tuckers)
  *   nv       1: same vector;  p + 1: linear combination
  *   out      device, written (not accumulated):

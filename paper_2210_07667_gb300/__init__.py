@@ -15,7 +15,8 @@ from typing import Optional, Sequence
 import numpy as np
 
 __all__ = [
-    "PHIKS_FP64", "PHIKS_TF32", "PHIKS_TF32X3", "PHIKS_BF16X3", "PHIKS_RULE_GLL", "PHIKS_RULE_GL",
+    "PHIKS_FP64", "PHIKS_TF32", "PHIKS_TF32X3", "PHIKS_BF16X3", "PHIKS_FP64_EMU", "PHIKS_RULE_GLL",
+    "PHIKS_RULE_GL",
     "PhiksError", "Options", "lib", "library_path", "load",
     "phiks_plan", "phiks_apply", "phiks_apply_ex", "phiks_workspace_size",
     "phiks_select_params", "phiks_choose_params", "phiks_last_params", "phiks_tucker", "phiks_expm",
@@ -24,9 +25,10 @@ __all__ = [
     "EXPORTED",
 ]
 
-PHIKS_FP64, PHIKS_TF32, PHIKS_TF32X3, PHIKS_BF16X3 = 0, 1, 2, 3
+PHIKS_FP64, PHIKS_TF32, PHIKS_TF32X3, PHIKS_BF16X3, PHIKS_FP64_EMU = 0, 1, 2, 3, 4
 PHIKS_RULE_GLL, PHIKS_RULE_GL = 0, 1
-DTYPES = {"fp64": PHIKS_FP64, "tf32": PHIKS_TF32, "tf32x3": PHIKS_TF32X3, "bf16x3": PHIKS_BF16X3}
+DTYPES = {"fp64": PHIKS_FP64, "tf32": PHIKS_TF32, "tf32x3": PHIKS_TF32X3, "bf16x3": PHIKS_BF16X3,
+          "fp64emu": PHIKS_FP64_EMU}
 STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "UNSUPPORTED", 4: "NO_PARAMS", 5: "CUDA", 6: "TIMEOUT"}
 
 # every symbol include/phiks.h declares

@@ -1,0 +1,571 @@
+// FP64 mu-mode products emulated by exact bf16 digit products on tcgen05
+// (see oz.cuh for the arithmetic).
+//
+// A Tucker operator runs d passes; pass mu contracts the contiguous mode of
+// the current layout and writes its FP64 result with that mode moved to the
+// slowest position (so the next mode is contiguous and the natural layout is
+// back after d passes):
+//   1. split:  every fibre of X (n consecutive doubles) -> its exponent and
+//              seven bf16 digit planes (one warp per fibre);
+//   2. tcgen05: per tile of 128 fibres x NT rows of L, the 28 digit products
+//              accumulate into seven FP32 TMEM accumulators G_0..G_6 (exact);
+//              the epilogue rounds sum_k 2^(8(6-k)) G_k once to FP64.
+// The last pass writes natural-layout FP64 results that a full-GPU combine
+// pass turns into the Tucker operator's epilogue outputs.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+
+#include "oz.cuh"
+#include "tcgen05.cuh"
+
+namespace phiks {
+
+namespace {
+
+using namespace ptx;
+thread_local std::string g_oz_err;
+constexpr int NTH = 192;
+
+// Exponent and 7 balanced base-256 digits of a double relative to the fibre
+// exponent E (biased): x = 2^(E - 1029) sum_s c_s 2^(-8 s), |c_s| <= 128.
+__device__ __forceinline__ void oz_digits(double x, int E, int* c) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((bits >> 52) & 0x7FF);
+  long long Q = 0;
+  if (e > 0 && E > 0) {
+    const unsigned long long mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+    const int sh = E - e - 2;  // Q = mant * 2^(e - E + 2), |Q| < 2^55
+    if (sh <= 0) {
+      Q = (long long)(mant << (-sh));
+    } else if (sh < 60) {
+      Q = (long long)((mant + (1ull << (sh - 1))) >> sh);
+    }
+    if (bits >> 63) Q = -Q;
+  }
+#pragma unroll
+  for (int s = kOzSlices - 1; s >= 1; --s) {
+    int d = (int)(Q & 0xFF);
+    if (d >= 128) d -= 256;
+    Q = (Q - d) >> 8;
+    c[s] = d;
+  }
+  c[0] = (int)Q;
+}
+
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// One warp per fibre of n consecutive elements of X = (combination `in`).
+__global__ void oz_split_kernel(Combo in, int n, int64_t M2, __nv_bfloat16* planes, int64_t N,
+                                int* scale) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool plain = in.nsrc == 1 && in.coef[0] == 1.0;
+  for (int64_t m = warp; m < M2; m += nwarps) {
+    double xv[kOzMaxN / 32];
+    int E = 0;
+#pragma unroll
+    for (int r = 0; r < kOzMaxN / 32; ++r) {
+      const int j = lane + 32 * r;
+      double x = 0.0;
+      if (j < n) {
+        const int64_t idx = (int64_t)m * n + j;
+        if (plain) {
+          x = in.src[0][idx];
+        } else {
+          for (int k = 0; k < in.nsrc; ++k) x = fma(in.coef[k], in.src[k][idx], x);
+        }
+      }
+      xv[r] = x;
+      E = max(E, (int)((__double_as_longlong(x) >> 52) & 0x7FF));
+    }
+    E = warp_max(E);
+#pragma unroll
+    for (int r = 0; r < kOzMaxN / 32; ++r) {
+      const int j = lane + 32 * r;
+      if (j >= n) continue;
+      int c[kOzSlices];
+      oz_digits(xv[r], E, c);
+      const int64_t idx = (int64_t)m * n + j;
+#pragma unroll
+      for (int s = 0; s < kOzSlices; ++s) planes[s * N + idx] = __float2bfloat16_rn((float)c[s]);
+    }
+    if (lane == 0) scale[m] = E - 1029;
+  }
+}
+
+// B digits: row i of L (column-major n x n), row-major planes n_pad x n_pad.
+__global__ void oz_prep_b_kernel(const double* L, int n, int n_pad, __nv_bfloat16* planes,
+                                 int* scale) {
+  const int lane = threadIdx.x & 31;
+  const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (i >= n_pad) return;
+  const int64_t P = (int64_t)n_pad * n_pad;
+  int E = 0;
+  for (int k = lane; k < n; k += 32)
+    if (i < n) E = max(E, (int)((__double_as_longlong(L[i + (int64_t)n * k]) >> 52) & 0x7FF));
+  E = warp_max(E);
+  for (int k = lane; k < n_pad; k += 32) {
+    int c[kOzSlices];
+    const double x = (i < n && k < n) ? L[i + (int64_t)n * k] : 0.0;
+    oz_digits(x, E, c);
+#pragma unroll
+    for (int s = 0; s < kOzSlices; ++s)
+      planes[s * P + (int64_t)i * n_pad + k] = __float2bfloat16_rn((float)c[s]);
+  }
+  if (lane == 0) scale[i] = E - 1029;
+}
+
+// T * 2^e rounded once to double (T a signed 128-bit integer).
+__device__ __forceinline__ double i128_scaled(__int128 T, int e) {
+  if (T == 0) return 0.0;
+  unsigned long long sign = 0;
+  unsigned __int128 a;
+  if (T < 0) {
+    sign = 1ull << 63;
+    a = (unsigned __int128)(-T);
+  } else {
+    a = (unsigned __int128)T;
+  }
+  const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+  int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+  unsigned long long mant;
+  const int sh = msb - 52;
+  if (sh <= 0) {
+    mant = lo << (-sh);
+  } else {
+    const unsigned __int128 q = a >> sh;
+    const unsigned __int128 rem = a - (q << sh);
+    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+    mant = (unsigned long long)q;
+    if (rem > half || (rem == half && (mant & 1))) {
+      ++mant;
+      if (mant >> 53) {
+        mant >>= 1;
+        ++msb;
+      }
+    }
+  }
+  const int biased = msb + e + 1023;
+  if (biased <= 0) return __longlong_as_double((long long)sign);
+  if (biased >= 2047) return __longlong_as_double((long long)(sign | (0x7FFull << 52)));
+  return __longlong_as_double(
+      (long long)(sign | ((unsigned long long)biased << 52) | (mant & ((1ull << 52) - 1))));
+}
+
+struct OzParams {
+  int n;          // contraction length
+  int n_pad;      // rows of L padded to a multiple of NT
+  int64_t M2;     // fibres
+  int nk;         // 64-element K chunks
+  int n_ntiles;   // tiles of NT rows of L
+  int num_tiles;
+  int tmem_cols;
+  int nbuf;       // TMEM accumulator sets (1 or 2)
+  double* out;    // FP64 result, rotated layout: out[m + M2 * i]
+  const int* xscale;
+  const int* lscale;
+  int* status;
+};
+
+// Per tile: A = 7 digit planes of 128 fibres x 64 K (one 3D TMA box), B = 7
+// digit planes of NT rows x 64 K; 28 products x 4 K-steps per chunk into 7
+// accumulators; one shared-memory stage (the digits take 112 KiB per chunk).
+template <int NT>
+__global__ void __launch_bounds__(NTH, 1)
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   OzParams P) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr uint32_t A_SLICE = BM * 128;  // bytes of one digit plane of the A tile
+  constexpr uint32_t B_SLICE = NT * 128;
+  constexpr uint32_t STAGE = kOzSlices * (A_SLICE + B_SLICE);
+  uint64_t* full = (uint64_t*)(smem + STAGE);
+  uint64_t* empty = full + 1;
+  uint64_t* tfull = empty + 1;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(full, 1);
+    mbar_init(empty, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(P.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t ph = 0;
+      int issued = 0;
+      for (int t = blockIdx.x; t < P.num_tiles; t += gridDim.x) {
+        const int m0 = (t / P.n_ntiles) * BM;
+        const int r0 = (t % P.n_ntiles) * NT;
+        bool ok = true;
+        for (int kc = 0; kc < P.nk; ++kc) {
+          if (!mbar_wait(empty, ph ^ 1, P.status, 11)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(full, STAGE);
+          tma_load_3d(smem, &mapA, full, kc * 64, m0, 0);
+          tma_load_3d(smem + kOzSlices * A_SLICE, &mapB, full, kc * 64, r0, 0);
+          ph ^= 1;
+          ++issued;
+        }
+        if (!ok) break;
+      }
+      if (issued) (void)mbar_wait(full, ph ^ 1, P.status, 0);  // last copy landed
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_make(1, NT);
+      uint32_t ph = 0, aph = 0;
+      int buf = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < P.num_tiles && ok; t += gridDim.x) {
+        if (!mbar_wait(&tempty[buf], aph ^ 1, P.status, 12)) break;
+        tc_fence_after();
+        const uint32_t d0 = tmem_base + (uint32_t)(buf * kOzSlices * NT);
+        for (int kc = 0; kc < P.nk; ++kc) {
+          if (!mbar_wait(full, ph, P.status, 13)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(smem), b0 = a0 + kOzSlices * A_SLICE;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t off = kk * 32;
+#pragma unroll
+            for (int k = 0; k < kOzSlices; ++k) {
+#pragma unroll
+              for (int s = 0; s <= k; ++s) {  // digit s of L times digit k - s of X
+                const uint32_t first = (kc == 0 && kk == 0 && s == 0) ? 0u : 1u;
+                umma<0>(d0 + (uint32_t)(k * NT), sdesc_sw128(a0 + (k - s) * A_SLICE + off),
+                        sdesc_sw128(b0 + s * B_SLICE + off), idesc, first);
+              }
+            }
+          }
+          umma_commit(empty);
+          ph ^= 1;
+        }
+        if (!ok) break;
+        umma_commit(&tfull[buf]);
+        if (++buf == P.nbuf) {
+          buf = 0;
+          aph ^= 1;
+        }
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    int buf = 0;
+    uint32_t aph = 0;
+    for (int t = blockIdx.x; t < P.num_tiles; t += gridDim.x) {
+      if (!mbar_wait(&tfull[buf], aph, P.status, 14)) break;
+      tc_fence_after();
+      const int64_t m = (int64_t)(t / P.n_ntiles) * BM + row;
+      const int r0 = (t % P.n_ntiles) * NT;
+      const bool valid = m < P.M2;
+      const int sx = valid ? P.xscale[m] : 0;
+#pragma unroll 1
+      for (int c0 = 0; c0 < NT; c0 += 16) {
+        float G[kOzSlices][16];
+#pragma unroll
+        for (int k = 0; k < kOzSlices; ++k)
+          tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) +
+                        (uint32_t)(buf * kOzSlices * NT + k * NT + c0),
+                    G[k]);
+        if (!valid) continue;
+#pragma unroll 4
+        for (int j = 0; j < 16; ++j) {
+          const int i = r0 + c0 + j;
+          if (i >= P.n) break;
+          long long hi = __float2int_rn(G[0][j]);
+          hi = hi * 256 + __float2int_rn(G[1][j]);
+          hi = hi * 256 + __float2int_rn(G[2][j]);
+          hi = hi * 256 + __float2int_rn(G[3][j]);
+          long long lo = __float2int_rn(G[4][j]);
+          lo = lo * 256 + __float2int_rn(G[5][j]);
+          lo = lo * 256 + __float2int_rn(G[6][j]);
+          const __int128 T = (__int128)hi * ((__int128)1 << 24) + (__int128)lo;
+          P.out[m + P.M2 * (int64_t)i] = i128_scaled(T, sx + P.lscale[i] - 48);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[buf]);
+      if (++buf == P.nbuf) {
+        buf = 0;
+        aph ^= 1;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(P.tmem_cols)
+                 : "memory");
+  }
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                              CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                              CUtensorMapFloatOOBfill);
+EncodeFn g_enc = nullptr;
+
+bool get_enc() {
+  if (g_enc) return true;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+          cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return false;
+  g_enc = (EncodeFn)fn;
+  return true;
+}
+
+// 3D map over 7 planes of a row-major (rows x inner) bf16 array; box
+// {64, box_rows, 7} with the 128-byte swizzle.
+bool make_map3(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint32_t box_rows) {
+  cuuint64_t dims[3] = {inner, rows, (cuuint64_t)kOzSlices};
+  cuuint64_t strides[2] = {inner * 2, inner * rows * 2};
+  cuuint32_t box[3] = {64, box_rows, (cuuint32_t)kOzSlices};
+  cuuint32_t es[3] = {1, 1, 1};
+  return g_enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t up1k(size_t x) { return (x + 1023) / 1024 * 1024; }
+
+int ntile_for(int n, int64_t M2) {
+  // enough tiles to spread over the SMs, at most 64 rows (7 accumulators of
+  // NT columns must fit the 512 TMEM columns)
+  const int64_t mt = (M2 + BM - 1) / BM;
+  if (n <= 16) return 16;
+  if (mt * ((n + 31) / 32) >= 152 || n <= 32) return 32;
+  return mt * ((n + 15) / 16) >= 152 ? 32 : 16;
+}
+
+}  // namespace
+
+struct OzState {
+  int d = 0;
+  int64_t n[PHIKS_MAX_D] = {0};
+  int64_t N = 0;
+  int* status = nullptr;
+  uint8_t* ws = nullptr;
+  double* tmp[2] = {nullptr, nullptr};
+  int smem_optin = 0;
+  std::map<std::tuple<const void*, uint64_t, uint64_t, uint32_t>, CUtensorMap> maps;
+};
+
+size_t oz_workspace_bytes(int d, const int64_t* n, int64_t N) {
+  int64_t m2 = 0;
+  for (int mu = 0; mu < d; ++mu) m2 = std::max<int64_t>(m2, N / n[mu]);
+  return up1k((size_t)kOzSlices * N * 2) + up1k((size_t)m2 * 4) + 1024;
+}
+
+phiks_status oz_create(OzState** out, int d, const int64_t* n, int64_t N) {
+  *out = nullptr;
+  for (int mu = 0; mu < d; ++mu)
+    if (n[mu] > kOzMaxN || n[mu] % 8 != 0) {
+      g_oz_err = "FP64 emulation needs every n_mu to be a multiple of 8 and at most 128";
+      return PHIKS_ERR_UNSUPPORTED;
+    }
+  if (!get_enc()) {
+    g_oz_err = "cuTensorMapEncodeTiled is not available";
+    return PHIKS_ERR_UNSUPPORTED;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess || prop.major < 10) {
+    g_oz_err = "FP64 emulation needs an sm_100-class device";
+    return PHIKS_ERR_UNSUPPORTED;
+  }
+  OzState* s = new OzState;
+  s->d = d;
+  for (int mu = 0; mu < d; ++mu) s->n[mu] = n[mu];
+  s->N = N;
+  s->smem_optin = (int)prop.sharedMemPerBlockOptin;
+  if (cudaMalloc(&s->status, sizeof(int)) != cudaSuccess ||
+      cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess) {
+    delete s;
+    g_oz_err = "status word allocation failed";
+    return PHIKS_ERR_OOM;
+  }
+  *out = s;
+  return PHIKS_OK;
+}
+
+void oz_destroy(OzState* s) {
+  if (!s) return;
+  cudaFree(s->status);
+  delete s;
+}
+
+const char* oz_last_error() { return g_oz_err.c_str(); }
+
+void oz_bind_workspace(OzState* s, void* ws, double* tmp0, double* tmp1) {
+  s->ws = (uint8_t*)ws;
+  s->tmp[0] = tmp0;
+  s->tmp[1] = tmp1;
+}
+
+size_t oz_bplanes_bytes(int n) {
+  const size_t np = (size_t)(n + 63) / 64 * 64;
+  return up1k((size_t)kOzSlices * np * np * 2) + up1k(np * 4);
+}
+
+cudaError_t oz_prepare_b(const double* L, int n, void* dst, cudaStream_t st) {
+  const int np = (n + 63) / 64 * 64;
+  __nv_bfloat16* planes = (__nv_bfloat16*)dst;
+  int* scale = (int*)((uint8_t*)dst + up1k((size_t)kOzSlices * np * np * 2));
+  count_launch();
+  oz_prep_b_kernel<<<(np * 32 + 255) / 256, 256, 0, st>>>(L, n, np, planes, scale);
+  return cudaGetLastError();
+}
+
+namespace {
+
+template <int NT>
+cudaError_t run_oz_gemm(OzState* s, const CUtensorMap& mA, const CUtensorMap& mB, OzParams& P,
+                        cudaStream_t st) {
+  constexpr uint32_t STAGE = kOzSlices * (BM * 128 + NT * 128);
+  const size_t smem = STAGE + 1024 + 256;
+  if ((int)smem > s->smem_optin) return cudaErrorInvalidConfiguration;
+  auto kern = oz_gemm_kernel<NT>;
+  static int set[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, s->smem_optin);
+    if (e != cudaSuccess) return e;
+    set[dev] = 1;
+  }
+  const int grid = P.num_tiles < 152 ? P.num_tiles : 152;
+  count_launch();
+  kern<<<grid, NTH, smem, st>>>(mA, mB, P);
+  return cudaGetLastError();
+}
+
+bool cached(OzState* s, CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint32_t box) {
+  auto key = std::make_tuple(base, inner, rows, box);
+  auto it = s->maps.find(key);
+  if (it != s->maps.end()) {
+    *m = it->second;
+    return true;
+  }
+  if (!make_map3(m, base, inner, rows, box)) return false;
+  if (s->maps.size() > 4096) s->maps.clear();
+  s->maps.emplace(key, *m);
+  return true;
+}
+
+}  // namespace
+
+cudaError_t oz_tucker(OzState* s, const Combo& in, const void* const* Bp, const Epi& epi,
+                      cudaStream_t st) {
+  const int64_t N = s->N;
+  __nv_bfloat16* planes = (__nv_bfloat16*)s->ws;
+  int* xscale = (int*)(s->ws + up1k((size_t)kOzSlices * N * 2));
+  Combo cur = in;
+  double* dst = nullptr;
+  for (int mu = 0; mu < s->d; ++mu) {
+    const int n = (int)s->n[mu];
+    const int64_t M2 = N / n;
+    {  // split: one warp per fibre
+      int64_t blocks = (M2 * 32 + 255) / 256;
+      if (blocks > 152 * 16) blocks = 152 * 16;
+      count_launch();
+      oz_split_kernel<<<(int)blocks, 256, 0, st>>>(cur, n, M2, planes, N, xscale);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    const int np = (n + 63) / 64 * 64;
+    const int NT = ntile_for(n, M2);
+    const uint8_t* bpl = (const uint8_t*)Bp[mu];
+    const int* lscale = (const int*)(bpl + up1k((size_t)kOzSlices * np * np * 2));
+    CUtensorMap mA, mB;
+    if (!cached(s, &mA, planes, (uint64_t)n, (uint64_t)M2, BM) ||
+        !cached(s, &mB, bpl, (uint64_t)np, (uint64_t)np, (uint32_t)NT)) {
+      g_oz_err = "tensor map encoding failed";
+      return cudaErrorInvalidValue;
+    }
+    dst = s->tmp[mu & 1];
+    OzParams P;
+    std::memset(&P, 0, sizeof P);
+    P.n = n;
+    P.n_pad = np;
+    P.M2 = M2;
+    P.nk = (n + 63) / 64;
+    P.n_ntiles = (n + NT - 1) / NT;
+    P.num_tiles = (int)((M2 + BM - 1) / BM) * P.n_ntiles;
+    P.nbuf = (2 * kOzSlices * NT <= 512) ? 2 : 1;
+    int cols = 32;
+    while (cols < P.nbuf * kOzSlices * NT) cols <<= 1;
+    P.tmem_cols = cols;
+    P.out = dst;
+    P.xscale = xscale;
+    P.lscale = lscale;
+    P.status = s->status;
+    cudaError_t e = NT == 16 ? run_oz_gemm<16>(s, mA, mB, P, st)
+                             : (NT == 32 ? run_oz_gemm<32>(s, mA, mB, P, st)
+                                         : run_oz_gemm<64>(s, mA, mB, P, st));
+    if (e != cudaSuccess) return e;
+    std::memset(&cur, 0, sizeof cur);
+    cur.nsrc = 1;
+    cur.src[0] = dst;
+    cur.coef[0] = 1.0;
+  }
+  // the Tucker operator's epilogue over all N elements with the whole GPU
+  Epi f = epi;
+  const int m = f.nsrc;
+  if (m >= kMaxSrc) return cudaErrorInvalidValue;
+  f.src[m] = dst;
+  for (int t = 0; t < f.nout; ++t) f.a[t][m] = epi.b[t];
+  f.nsrc = m + 1;
+  return launch_combine(f, N, st);
+}
+
+int oz_read_status(OzState* s, cudaStream_t st) {
+  int h = 0;
+  if (cudaMemcpyAsync(&h, s->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return -1;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+  if (h) cudaMemsetAsync(s->status, 0, sizeof(int), st);
+  return h;
+}
+
+}  // namespace phiks

@@ -1,0 +1,49 @@
+// FP64 mu-mode products emulated on the tensor cores with exact integer
+// slice products (the PHIKS_FP64_EMU dtype).
+//
+// Every fibre of the operand X (the n values contracted together) and every
+// row of L is scaled by a power of two and written as seven balanced base-256
+// digits c_0 .. c_6 (|c_s| <= 128), each stored exactly as a bf16:
+//     x = 2^e_x sum_s c_s 2^(-8 s),     l = 2^e_l sum_s b_s 2^(-8 s).
+// Then sum_j l x = 2^(e_x + e_l) sum_k 2^(-8 k) G_k with
+// G_k = sum_{s + t = k} sum_j b_s c_t.  Each product of digits is below 2^14
+// and (k + 1) n 2^14 < 2^24 for n <= 128, so the tensor cores accumulate
+// every G_k (k = 0..6, 28 digit products) exactly in FP32; the epilogue
+// assembles sum_k 2^(8 (6 - k)) G_k as a 128-bit integer and rounds it once to
+// FP64.  Dropping the terms with s + t >= 7 leaves an error below about
+// 2^-53 of |l| |x| (the scale of an FP64 dot product's own rounding).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/phiks.h"
+#include "kernels.cuh"
+
+namespace phiks {
+
+struct OzState;
+
+constexpr int kOzSlices = 7;
+constexpr int kOzMaxN = 128;
+
+size_t oz_workspace_bytes(int d, const int64_t* n, int64_t N);
+phiks_status oz_create(OzState** out, int d, const int64_t* n, int64_t N);
+void oz_destroy(OzState* s);
+const char* oz_last_error();
+void oz_bind_workspace(OzState* s, void* ws, double* tmp0, double* tmp1);
+
+// Bytes of the B-operand slices of one n x n matrix (7 planes of n_pad x
+// n_pad bf16 and n_pad row exponents), and their preparation from an FP64
+// column-major matrix.
+size_t oz_bplanes_bytes(int n);
+cudaError_t oz_prepare_b(const double* L, int n, void* dst, cudaStream_t st);
+
+// (combination `in`) x_1 L_1 ... x_d L_d through `epi` (FP64), Bp[mu] made
+// by oz_prepare_b for L_mu.
+cudaError_t oz_tucker(OzState* s, const Combo& in, const void* const* Bp, const Epi& epi,
+                      cudaStream_t st);
+
+int oz_read_status(OzState* s, cudaStream_t st);
+
+}  // namespace phiks

@@ -18,6 +18,7 @@
 #include "../../include/phiks.h"
 #include "kernels.cuh"
 #include "planner.hpp"
+#include "oz.cuh"
 #include "tc.cuh"
 
 using namespace phiks;
@@ -121,6 +122,7 @@ struct phiks_plan_s {
       param_cache;
   int last_s = -1, last_q = -1, last_T = -1, last_tuckers = 0;
   TcState* tc = nullptr;
+  OzState* oz = nullptr;
   // profiling: event pairs around mu-mode products
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -152,7 +154,15 @@ int64_t mode_b(const phiks_plan_s* P, int mu) {
   return b;
 }
 
-size_t elt_size(const phiks_plan_s* P) { return P->dtype == PHIKS_FP64 ? 8 : 4; }
+// split dtypes: float vectors, products on the tensor cores in bf16/tf32;
+// FP64_EMU: double vectors, products by exact bf16 digit products
+bool split_dtype(const phiks_plan_s* P) {
+  return P->dtype == PHIKS_TF32 || P->dtype == PHIKS_TF32X3 || P->dtype == PHIKS_BF16X3;
+}
+bool emu_dtype(const phiks_plan_s* P) { return P->dtype == PHIKS_FP64_EMU; }
+bool double_vectors(const phiks_plan_s* P) { return !split_dtype(P); }
+
+size_t elt_size(const phiks_plan_s* P) { return double_vectors(P) ? 8 : 4; }
 
 // Workspace of one apply, everything an apply writes besides its outputs, so
 // that applies with distinct workspaces never share device state:
@@ -185,7 +195,7 @@ WsLayout ws_layout(const phiks_plan_s* P, int p) {
     w.tcb1 = o;
     o += up1k(P->tcb_bytes);
     w.planes = o;
-    o += up1k(tc_workspace_bytes(P->N));
+    o += up1k(emu_dtype(P) ? oz_workspace_bytes(P->d, P->n, P->N) : tc_workspace_bytes(P->N));
   }
   w.total = o + 1024;  // room to align the base
   return w;
@@ -476,7 +486,8 @@ phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool 
     for (int b = 0; b < nbk; ++b)
       for (int mu = 0; mu < P->d; ++mu) {
         nb.tcoff[b][mu] = (size_t)b * P->tcb_bytes + P->tcb_off[mu];
-        CK(tc_prepare_b(P->dtype, nb.dev + nb.off[b][mu], (int)P->n[mu], nb.tcb + nb.tcoff[b][mu], st));
+        if (emu_dtype(P)) CK(oz_prepare_b(nb.dev + nb.off[b][mu], (int)P->n[mu], nb.tcb + nb.tcoff[b][mu], st));
+        else CK(tc_prepare_b(P->dtype, nb.dev + nb.off[b][mu], (int)P->n[mu], nb.tcb + nb.tcoff[b][mu], st));
       }
   }
   nb.stamp = P->clock;
@@ -513,7 +524,8 @@ void carve(Ctx& c, int p, char* ws, double** acc) {
   if (P->dtype != PHIKS_FP64) {
     c.msq_tcb[0] = (uint8_t*)(base + w.tcb0);
     c.msq_tcb[1] = (uint8_t*)(base + w.tcb1);
-    tc_bind_workspace(P->tc, (void*)(base + w.planes));
+    if (emu_dtype(P)) oz_bind_workspace(P->oz, (void*)(base + w.planes), c.tmp[0], c.tmp[1]);
+    else tc_bind_workspace(P->tc, (void*)(base + w.planes));
   }
 }
 
@@ -554,9 +566,10 @@ phiks_status tucker(Ctx& c, const Combo& in, const Mats& M, const Epi* epi) {
   if (P->dtype != PHIKS_FP64) {
     cudaEvent_t e1;
     TRY(prof_begin(c, &e1));
-    cudaError_t e = tc_tucker(P->tc, in, M.B, *epi, c.st);
+    cudaError_t e = emu_dtype(P) ? oz_tucker(P->oz, in, M.B, *epi, c.st) : tc_tucker(P->tc, in, M.B, *epi, c.st);
     if (e != cudaSuccess)
-      return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), tc_last_error());
+      return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e),
+                  emu_dtype(P) ? oz_last_error() : tc_last_error());
     double fl = 0;
     for (int mu = 0; mu < P->d; ++mu) fl += 2.0 * (double)P->N * (double)P->n[mu];
     TRY(prof_end(c, e1, fl));
@@ -619,7 +632,8 @@ phiks_status square_modes(Ctx& c, Mats& M, int& cur_buf) {
     off += (size_t)P->n[mu] * P->n[mu];
     if (P->dtype != PHIKS_FP64) {
       uint8_t* dst = c.msq_tcb[cur_buf] + P->tcb_off[mu];
-      CK(tc_prepare_b(P->dtype, M.L[mu], (int)P->n[mu], dst, c.st));
+      if (emu_dtype(P)) CK(oz_prepare_b(M.L[mu], (int)P->n[mu], dst, c.st));
+      else CK(tc_prepare_b(P->dtype, M.L[mu], (int)P->n[mu], dst, c.st));
       M.B[mu] = dst;
     }
   }
@@ -639,7 +653,7 @@ phiks_status combine(Ctx& c, const Epi& e) {
 
 // dst (plan element type) <- acc (double)
 phiks_status store_acc(Ctx& c, void* dst, const double* acc) {
-  if (c.P->dtype == PHIKS_FP64) return copy_elems(c, dst, acc);
+  if (double_vectors(c.P)) return copy_elems(c, dst, acc);
   Epi e = make_epi();
   e.nout = 1;
   e.nsrc = 1;
@@ -657,7 +671,7 @@ phiks_status run_same(Ctx& c, const Bank* B, int s, int p, const void* v, const 
   phiks_plan_s* P = c.P;
   const int64_t N = P->N;
   const size_t es = elt_size(P);
-  const bool f32 = P->dtype != PHIKS_FP64;
+  const bool f32 = split_dtype(P);
   const int per = p + (o.skip_phi0 ? 0 : 1);
   const int q = (int)B->theta.size();
   for (int l = 0; l < p; ++l) CK(cudaMemsetAsync(acc[l], 0, N * 8, c.st));
@@ -732,7 +746,7 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
   phiks_plan_s* P = c.P;
   const int64_t N = P->N;
   const size_t es = elt_size(P);
-  const bool f32 = P->dtype != PHIKS_FP64;
+  const bool f32 = split_dtype(P);
   const int q = (int)B->theta.size();
   for (int l = 0; l < p; ++l) CK(cudaMemsetAsync(acc[l], 0, N * 8, c.st));
   for (int i = 0; i < q; ++i) {
@@ -870,7 +884,7 @@ phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dty
   *out = nullptr;
   if (d < 1 || d > PHIKS_MAX_D) return fail(PHIKS_ERR_INVALID, "d = %d out of [1, %d]", d, PHIKS_MAX_D);
   if (!n || !A) return fail(PHIKS_ERR_INVALID, "n or A is NULL");
-  if (dtype < PHIKS_FP64 || dtype > PHIKS_BF16X3) return fail(PHIKS_ERR_INVALID, "dtype %d", dtype);
+  if (dtype < PHIKS_FP64 || dtype > PHIKS_FP64_EMU) return fail(PHIKS_ERR_INVALID, "dtype %d", dtype);
   std::unique_ptr<phiks_plan_s> P(new phiks_plan_s);
   P->d = d;
   P->dtype = dtype;
@@ -912,12 +926,17 @@ phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dty
   CK(cudaMalloc(&P->d_norms, (PHIKS_MAX_P + 1) * 8));
   CK(cudaMallocHost(&P->h_norms, (PHIKS_MAX_P + 1) * 8));
   if (dtype != PHIKS_FP64) {
-    phiks_status st = tc_create(&P->tc, dtype, d, P->n, P->N);
-    if (st != PHIKS_OK) return fail(st, "%s", tc_last_error());
+    if (dtype == PHIKS_FP64_EMU) {
+      phiks_status st = oz_create(&P->oz, d, P->n, P->N);
+      if (st != PHIKS_OK) return fail(st, "%s", oz_last_error());
+    } else {
+      phiks_status st = tc_create(&P->tc, dtype, d, P->n, P->N);
+      if (st != PHIKS_OK) return fail(st, "%s", tc_last_error());
+    }
     size_t tb = 0;
     for (int mu = 0; mu < d; ++mu) {
       P->tcb_off[mu] = tb;
-      tb += tc_bplanes_bytes(dtype, (int)n[mu]);
+      tb += dtype == PHIKS_FP64_EMU ? oz_bplanes_bytes((int)n[mu]) : tc_bplanes_bytes(dtype, (int)n[mu]);
     }
     P->tcb_bytes = tb;
     CK(cudaMalloc(&P->tucker_tcb, tb));
@@ -956,11 +975,11 @@ phiks_status phiks_device_status(phiks_plan_t P, void* stream) {
   g_err.clear();
   if (!P) return fail(PHIKS_ERR_INVALID, "NULL plan");
   DeviceGuard g(P->device);
-  if (!P->tc) {
+  if (!P->tc && !P->oz) {
     CK(cudaStreamSynchronize((cudaStream_t)stream));
     return PHIKS_OK;
   }
-  int code = tc_read_status(P->tc, (cudaStream_t)stream);
+  int code = P->tc ? tc_read_status(P->tc, (cudaStream_t)stream) : oz_read_status(P->oz, (cudaStream_t)stream);
   if (code < 0) return fail(PHIKS_ERR_CUDA, "reading the device status failed");
   if (code > 0) return fail(PHIKS_ERR_TIMEOUT, "a bounded device-side wait gave up (site %d)", code);
   return PHIKS_OK;
@@ -1108,6 +1127,7 @@ void phiks_destroy(phiks_plan_t P) {
   cudaFree(P->d_norms);
   cudaFreeHost(P->h_norms);
   if (P->tc) tc_destroy(P->tc);
+  if (P->oz) oz_destroy(P->oz);
   delete P;
 }
 
@@ -1220,7 +1240,7 @@ phiks_status phiks_apply_ex(phiks_plan_t P, double tau, int p, const void* const
       }
     if (cnt) {
       CK(cudaMemsetAsync(P->d_norms, 0, cnt * 8, st));
-      CK(launch_sumsq(xs, cnt, N, P->dtype != PHIKS_FP64, P->d_norms, st));
+      CK(launch_sumsq(xs, cnt, N, split_dtype(P), P->d_norms, st));
       CK(cudaMemcpyAsync(P->h_norms, P->d_norms, cnt * 8, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       for (int k = 0; k < cnt; ++k) norms[idx[k]] = std::sqrt(P->h_norms[k]);
@@ -1305,16 +1325,17 @@ phiks_status phiks_tucker(phiks_plan_t P, const void* V, void* W, const double* 
   Ctx c{P, (cudaStream_t)stream, {nullptr, nullptr}, 0};
   double* acc[PHIKS_MAX_P];
   carve(c, 1, (char*)P->ws, acc);
-  const bool f32 = P->dtype != PHIKS_FP64;
+  const bool f32 = split_dtype(P);
   Mats M;
   for (int mu = 0; mu < P->d; ++mu) {
     M.L[mu] = L[mu];
     M.B[mu] = nullptr;
   }
-  if (f32) {
+  if (P->dtype != PHIKS_FP64) {
     for (int mu = 0; mu < P->d; ++mu) {
       uint8_t* dst = P->tucker_tcb + P->tcb_off[mu];
-      CK(tc_prepare_b(P->dtype, L[mu], (int)P->n[mu], dst, c.st));
+      if (emu_dtype(P)) CK(oz_prepare_b(L[mu], (int)P->n[mu], dst, c.st));
+      else CK(tc_prepare_b(P->dtype, L[mu], (int)P->n[mu], dst, c.st));
       M.B[mu] = dst;
     }
   }

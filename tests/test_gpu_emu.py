@@ -1,0 +1,61 @@
+"""FP64 emulated on the tensor cores (PHIKS_FP64_EMU): exact bf16 digit
+products, one rounding to FP64.  Checked against the FP64 oracle with the
+FP64 path's tolerances: 1e-14 for one Tucker operator (relative to the
+largest output), 1e-12 for whole phiks calls."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2210_07667_gb300 as pk  # noqa: E402
+import workloads as wk  # noqa: E402
+from oracle import dense, kron  # noqa: E402
+from oracle import taylor_action as ta  # noqa: E402
+
+from gpu_util import dev, rel_inf, run_workload  # noqa: E402
+
+EMU = pk.PHIKS_FP64_EMU
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pk.load(build_if_missing=True)
+
+
+@pytest.mark.parametrize("dims", [(32, 32), (64, 48, 40), (128, 16, 24), (8, 8, 8, 8), (64, 64, 64)])
+def test_tucker_emulated_fp64(dims):
+    rng = np.random.default_rng(sum(dims))
+    plan = pk.Plan([np.eye(m) for m in dims], EMU)
+    N = int(np.prod(dims))
+    V = rng.standard_normal(N) * np.exp(rng.uniform(-3, 3, N))   # wide dynamic range
+    Ls = [rng.standard_normal((m, m)) / np.sqrt(m) for m in dims]
+    W = torch.empty(N, device="cuda", dtype=torch.float64)
+    pk.phiks_tucker(plan.handle, dev(V), W, [dev(L.ravel(order="F")) for L in Ls])
+    pk.phiks_device_status(plan.handle)
+    ref = kron.vec(kron.tucker(kron.unvec(V, dims), Ls))
+    err = rel_inf(W.cpu().numpy(), ref)
+    print("emu tucker", dims, "%.2e" % err)
+    assert err < 1e-14
+    plan.close()
+
+
+def test_same_vector_emulated():
+    wl = wk.small_same(32)
+    out, plan = run_workload(wl, dtype=EMU)
+    pk.phiks_device_status(plan.handle)
+    for L in range(1):
+        ex = dense.same(wl.A, wl.tau, wl.vs[0], wl.p)
+        for k in range(wl.p + 1):
+            assert rel_inf(out[k], ex[k]) < 1e-12, k
+
+
+def test_lincomb_bench_workload_emulated():
+    wl = wk.adr3d_lincomb(64)
+    out, plan = run_workload(wl, dtype=EMU)
+    pk.phiks_device_status(plan.handle)
+    errs = [rel_inf(out[L], ta.lincomb(wl.A, wl.tau, wl.vs, 2.0 ** -L)) for L in range(3)]
+    print("emu lincomb errs", ["%.2e" % e for e in errs])
+    assert max(errs) < 1e-12
