@@ -13,7 +13,7 @@ def dev(x, dtype=torch.float64):
 def run_workload(wl, dtype=pk.PHIKS_FP64, **opts):
     """Apply the plan to the workload's vectors; returns (out as numpy float64
     array of shape (blocks, N), plan)."""
-    tdt = torch.float64 if dtype == pk.PHIKS_FP64 else torch.float32
+    tdt = torch.float64 if dtype in (pk.PHIKS_FP64, pk.PHIKS_FP64_EMU) else torch.float32
     plan = pk.Plan(wl.A, dtype)
     N = wl.N
     if wl.mode == "same":
