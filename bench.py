@@ -184,7 +184,8 @@ def run_phiks(args):
 
     wl = workload()
     N = wl.N
-    plan = pk.Plan(wl.A, pk.PHIKS_FP64)
+    main_dtype = pk.PHIKS_FP64_EMU if args.dtype == "fp64emu" else pk.PHIKS_FP64
+    plan = pk.Plan(wl.A, main_dtype)
     stream = torch.cuda.Stream()
     vs = [torch.from_numpy(v).cuda() for v in wl.vs]
     out = torch.empty(wl.nscales * N, device="cuda", dtype=torch.float64)
@@ -286,6 +287,8 @@ def run_phiks(args):
                                    "l2": "flushed before every timed step (256 MiB write, untimed)",
                                    "small_exponentials": "recomputed every step"}),
         "mu_mode_tflops": step_flops / (ms_step * 1e-3) / 1e12,
+        "mu_mode_products": "fp64 emulated by bf16 digit products on tcgen05" if main_dtype != pk.PHIKS_FP64
+        else "fp64 DFMA",
         "value_cached_exponentials": ws * wl.nscales * args.steps / (cms * 1e-3),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / PEAK_FP64_TFLOPS, "traffic": None,
@@ -301,6 +304,8 @@ def run_phiks(args):
     # the same workload with the mu-mode products emulated on the tensor cores
     # (exact bf16 digit products, one rounding to FP64)
     try:
+        if main_dtype != pk.PHIKS_FP64:
+            raise RuntimeError("headline already uses the emulated products")
         pe = pk.Plan(wl.A, pk.PHIKS_FP64_EMU)
         oute = torch.empty_like(out)
 
@@ -768,7 +773,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", default="adr3d", choices=["adr3d", "small", "precision", "batched", "served"],
                     help="adr3d: the headline FP64 workload; precision: the split-dtype form")
-    ap.add_argument("--dtype", default="all", choices=["all"] + PRECISION_DTYPES)
+    ap.add_argument("--dtype", default="all", choices=["all", "fp64emu"] + PRECISION_DTYPES,
+                    help="precision/batched/served: split dtype; adr3d: fp64 (default) or fp64emu")
     ap.add_argument("--variant", default="cheb", choices=["cheb", "fd"])
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--no-ref", action="store_true", help="skip the FP64 reference path")
