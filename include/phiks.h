@@ -92,7 +92,15 @@ typedef struct {
                             or NULL for the plan's own */
   size_t workspace_bytes;
   int no_cache;          /* recompute the small exponentials on every call */
-  int reserved[7];
+  int graph;             /* nonzero: the kernels of a call (everything after the
+                            norms and the (s, q) selection) are captured once
+                            into a CUDA graph per (tau, p, vectors, output,
+                            workspace, s, q, options, small-exponential storage)
+                            and later identical calls replay it with one
+                            launch.  Ignored while profiling, on the legacy
+                            default stream and when `stream` is already
+                            capturing. */
+  int reserved[6];
 } phiks_options;
 
 /* Fill `opt` with the defaults above. */

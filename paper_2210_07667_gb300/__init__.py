@@ -62,7 +62,8 @@ class Options(ctypes.Structure):
         ("workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_size_t),
         ("no_cache", ctypes.c_int),
-        ("reserved", ctypes.c_int * 7),
+        ("graph", ctypes.c_int),
+        ("reserved", ctypes.c_int * 6),
     ]
 
 

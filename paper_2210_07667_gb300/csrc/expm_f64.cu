@@ -8,11 +8,15 @@
 namespace phiks {
 namespace {
 
-constexpr int GT = 32, GK = 16, GNT = 256;
-constexpr int GR = 2;                  // 2 x 2 outputs per thread
-constexpr int GTHR = GT / GR;          // 16
+constexpr int GK = 16;
 
-__global__ void __launch_bounds__(GNT) gemm_batch_f64_kernel(GemmBatch gb) {
+// One CTA per GT x GT tile of one C_k, (GT / GR)^2 threads with GR x GR
+// outputs each.  The FP64 pipe bounds this kernel, so small matrices take
+// small tiles to spread over every SM.
+template <int GT, int GR>
+__global__ void __launch_bounds__((GT / GR) * (GT / GR)) gemm_batch_f64_kernel(GemmBatch gb) {
+  constexpr int GTHR = GT / GR;
+  constexpr int GNT = GTHR * GTHR;
   const int k = blockIdx.z;
   const int n = gb.n[k];
   const int tiles = (n + GT - 1) / GT;
@@ -26,7 +30,11 @@ __global__ void __launch_bounds__(GNT) gemm_batch_f64_kernel(GemmBatch gb) {
   const int tid = threadIdx.x;
   const int tj = tid % GTHR, ti = tid / GTHR;
   const int i0 = bi * GT, j0 = bj * GT;
-  double acc[GR][GR] = {{0.0, 0.0}, {0.0, 0.0}};
+  double acc[GR][GR];
+#pragma unroll
+  for (int r = 0; r < GR; ++r)
+#pragma unroll
+    for (int c = 0; c < GR; ++c) acc[r][c] = 0.0;
   const int kend = gb.alpha[k] != 0.0 ? n : 0;  // alpha = 0: addends only
   for (int k0 = 0; k0 < kend; k0 += GK) {
     for (int e = tid; e < GT * GK; e += GNT) {
@@ -39,12 +47,16 @@ __global__ void __launch_bounds__(GNT) gemm_batch_f64_kernel(GemmBatch gb) {
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      double a0 = sA[kk][ti], a1 = sA[kk][ti + GTHR];
-      double b0 = sB[kk][tj], b1 = sB[kk][tj + GTHR];
-      acc[0][0] = fma(a0, b0, acc[0][0]);
-      acc[0][1] = fma(a0, b1, acc[0][1]);
-      acc[1][0] = fma(a1, b0, acc[1][0]);
-      acc[1][1] = fma(a1, b1, acc[1][1]);
+      double a[GR], b[GR];
+#pragma unroll
+      for (int r = 0; r < GR; ++r) {
+        a[r] = sA[kk][ti + r * GTHR];
+        b[r] = sB[kk][tj + r * GTHR];
+      }
+#pragma unroll
+      for (int r = 0; r < GR; ++r)
+#pragma unroll
+        for (int c = 0; c < GR; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
     }
     __syncthreads();
   }
@@ -81,10 +93,19 @@ __global__ void scale_batch_f64_kernel(ScaleBatch sb) {
 cudaError_t launch_gemm_batch_f64(const GemmBatch& gb, int nmax, cudaStream_t st) {
   if (gb.count <= 0) return cudaSuccess;
   if (gb.count > kMaxBatch) return cudaErrorInvalidValue;
-  const int tiles = (nmax + GT - 1) / GT;
-  dim3 grid(tiles, tiles, gb.count);
+  // the largest tile that still gives every SM a few CTAs
+  auto ctas = [&](int gt) { return (int64_t)gb.count * ((nmax + gt - 1) / gt) * ((nmax + gt - 1) / gt); };
   count_launch();
-  gemm_batch_f64_kernel<<<grid, GNT, 0, st>>>(gb);
+  if (ctas(32) >= 4 * 152) {
+    const int t = (nmax + 31) / 32;
+    gemm_batch_f64_kernel<32, 2><<<dim3(t, t, gb.count), 256, 0, st>>>(gb);
+  } else if (ctas(16) >= 4 * 152) {
+    const int t = (nmax + 15) / 16;
+    gemm_batch_f64_kernel<16, 1><<<dim3(t, t, gb.count), 256, 0, st>>>(gb);
+  } else {
+    const int t = (nmax + 7) / 8;
+    gemm_batch_f64_kernel<8, 1><<<dim3(t, t, gb.count), 64, 0, st>>>(gb);
+  }
   return cudaGetLastError();
 }
 

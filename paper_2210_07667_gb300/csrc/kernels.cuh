@@ -11,7 +11,7 @@ void set_error_message(const char* msg);
 
 // Process-wide count of kernels launched by this library.
 uint64_t kernel_launch_count();
-void count_launch();
+void count_launch(uint64_t k = 1);
 
 constexpr int kMaxSrc = 10;  // tensors one combination may read
 constexpr int kMaxOut = 8;   // tensors one epilogue may write

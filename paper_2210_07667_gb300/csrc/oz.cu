@@ -6,10 +6,11 @@
 // slowest position (so the next mode is contiguous and the natural layout is
 // back after d passes):
 //   1. split:  every fibre of X (n consecutive doubles) -> its exponent and
-//              seven bf16 digit planes (one warp per fibre);
+//              seven bf16 digit planes (n / 8 threads per fibre);
 //   2. tcgen05: per tile of 128 fibres x NT rows of L, the 28 digit products
 //              accumulate into seven FP32 TMEM accumulators G_0..G_6 (exact);
-//              the epilogue rounds sum_k 2^(8(6-k)) G_k once to FP64.
+//              the epilogue assembles sum_k 2^(8(6-k)) G_k in 64-bit integers
+//              and rounds it to FP64.
 // The last pass writes natural-layout FP64 results that a full-GPU combine
 // pass turns into the Tucker operator's epilogue outputs.
 #include <cuda.h>
@@ -30,17 +31,17 @@ namespace {
 
 using namespace ptx;
 thread_local std::string g_oz_err;
-constexpr int NTH = 192;
 
-// Exponent and 7 balanced base-256 digits of a double relative to the fibre
-// exponent E (biased): x = 2^(E - 1029) sum_s c_s 2^(-8 s), |c_s| <= 128.
-__device__ __forceinline__ void oz_digits(double x, int E, int* c) {
+// Fixed-point value of a double relative to the fibre exponent E (biased):
+// x = Q 2^(E - 1077) up to rounding, |Q| < 2^55 (Q = 0 for zeros and
+// subnormals, and for elements more than 2^60 below the fibre maximum).
+__device__ __forceinline__ long long oz_fixed(double x, int E) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((bits >> 52) & 0x7FF);
   long long Q = 0;
   if (e > 0 && E > 0) {
     const unsigned long long mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
-    const int sh = E - e - 2;  // Q = mant * 2^(e - E + 2), |Q| < 2^55
+    const int sh = E - e - 2;  // Q = mant * 2^(e - E + 2)
     if (sh <= 0) {
       Q = (long long)(mant << (-sh));
     } else if (sh < 60) {
@@ -48,14 +49,27 @@ __device__ __forceinline__ void oz_digits(double x, int E, int* c) {
     }
     if (bits >> 63) Q = -Q;
   }
-#pragma unroll
-  for (int s = kOzSlices - 1; s >= 1; --s) {
-    int d = (int)(Q & 0xFF);
-    if (d >= 128) d -= 256;
-    Q = (Q - d) >> 8;
-    c[s] = d;
-  }
-  c[0] = (int)Q;
+  return Q;
+}
+
+// The 7 balanced base-256 digits c_0 (most significant) .. c_6 of Q, as
+// floats: Q = sum_s c_s 2^(8 (6 - s)), c_1..c_6 in [-128, 127], |c_0| <= 128.
+// Adding 128 to each of the six low digit positions turns the balanced digits
+// into plain bytes (c_s + 128); the top digit is what remains above them.
+__device__ __forceinline__ void oz_digits(long long Q, float* c) {
+  const long long Qp = Q + 0x0000808080808080ll;
+  const uint32_t lo = (uint32_t)Qp, hi = (uint32_t)((unsigned long long)Qp >> 32);
+  // byte b of a word as the float 2^23 + b, minus 2^23 + 128
+  auto byte_f = [](uint32_t w, uint32_t b) {
+    return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7440u | b)) - 8388736.0f;
+  };
+  c[6] = byte_f(lo, 0);
+  c[5] = byte_f(lo, 1);
+  c[4] = byte_f(lo, 2);
+  c[3] = byte_f(lo, 3);
+  c[2] = byte_f(hi, 0);
+  c[1] = byte_f(hi, 1);
+  c[0] = (float)((int)hi >> 16);
 }
 
 __device__ __forceinline__ int warp_max(int v) {
@@ -64,44 +78,78 @@ __device__ __forceinline__ int warp_max(int v) {
   return v;
 }
 
-// One warp per fibre of n consecutive elements of X = (combination `in`).
-__global__ void oz_split_kernel(Combo in, int n, int64_t M2, __nv_bfloat16* planes, int64_t N,
-                                int* scale) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const bool plain = in.nsrc == 1 && in.coef[0] == 1.0;
-  for (int64_t m = warp; m < M2; m += nwarps) {
-    double xv[kOzMaxN / 32];
-    int E = 0;
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ int biased_exp(double x) {
+  return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+constexpr int kSplitThreads = 128;
+
+// Each thread splits 8 consecutive elements of one fibre of X = (combination
+// `in`) and writes one 16-byte chunk of every digit plane; a block holds `fpb`
+// whole fibres (n / 8 threads each), whose exponents meet in shared memory.
+__global__ void __launch_bounds__(kSplitThreads) oz_split_kernel(Combo in, int n, int64_t M2, int fpb,
+                                                                 __nv_bfloat16* planes, int64_t N,
+                                                                 int* scale) {
+  __shared__ int emax[kSplitThreads];
+  const int cpf = n >> 3;
+  const int t = threadIdx.x;
+  const int fl = t / cpf;
+  const int64_t m = (int64_t)blockIdx.x * fpb + fl;
+  const bool active = fl < fpb && m < M2;
+  const int64_t base = m * n + (int64_t)(t - fl * cpf) * 8;
+  if (t < fpb) emax[t] = 0;
+  double x[8];
+  int E = 0;
+  if (active) {
+    if (in.nsrc == 1 && in.coef[0] == 1.0) {
+      const double* p = in.src[0] + base;
+      if (((uintptr_t)p & 15) == 0) {
 #pragma unroll
-    for (int r = 0; r < kOzMaxN / 32; ++r) {
-      const int j = lane + 32 * r;
-      double x = 0.0;
-      if (j < n) {
-        const int64_t idx = (int64_t)m * n + j;
-        if (plain) {
-          x = in.src[0][idx];
-        } else {
-          for (int k = 0; k < in.nsrc; ++k) x = fma(in.coef[k], in.src[k][idx], x);
+        for (int j = 0; j < 8; j += 2) {
+          const double2 v = __ldg(reinterpret_cast<const double2*>(p + j));
+          x[j] = v.x;
+          x[j + 1] = v.y;
         }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = p[j];
       }
-      xv[r] = x;
-      E = max(E, (int)((__double_as_longlong(x) >> 52) & 0x7FF));
-    }
-    E = warp_max(E);
+    } else {
 #pragma unroll
-    for (int r = 0; r < kOzMaxN / 32; ++r) {
-      const int j = lane + 32 * r;
-      if (j >= n) continue;
-      int c[kOzSlices];
-      oz_digits(xv[r], E, c);
-      const int64_t idx = (int64_t)m * n + j;
+      for (int j = 0; j < 8; ++j) x[j] = 0.0;
+      for (int k = 0; k < in.nsrc; ++k) {
+        const double* p = in.src[k] + base;
+        const double a = in.coef[k];
 #pragma unroll
-      for (int s = 0; s < kOzSlices; ++s) planes[s * N + idx] = __float2bfloat16_rn((float)c[s]);
+        for (int j = 0; j < 8; ++j) x[j] = fma(a, p[j], x[j]);
+      }
     }
-    if (lane == 0) scale[m] = E - 1029;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) E = max(E, biased_exp(x[j]));
   }
+  __syncthreads();
+  if (active) atomicMax(&emax[fl], E);
+  __syncthreads();
+  if (!active) return;
+  E = emax[fl];
+  uint32_t w[kOzSlices][4];
+#pragma unroll
+  for (int j = 0; j < 8; j += 2) {
+    float c0[kOzSlices], c1[kOzSlices];
+    oz_digits(oz_fixed(x[j], E), c0);
+    oz_digits(oz_fixed(x[j + 1], E), c1);
+#pragma unroll
+    for (int s = 0; s < kOzSlices; ++s) w[s][j >> 1] = pack_bf16x2(c0[s], c1[s]);
+  }
+#pragma unroll
+  for (int s = 0; s < kOzSlices; ++s)
+    *reinterpret_cast<uint4*>(planes + s * N + base) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+  if (t == fl * cpf) scale[m] = E - 1029;
 }
 
 // B digits: row i of L (column-major n x n), row-major planes n_pad x n_pad.
@@ -113,54 +161,44 @@ __global__ void oz_prep_b_kernel(const double* L, int n, int n_pad, __nv_bfloat1
   const int64_t P = (int64_t)n_pad * n_pad;
   int E = 0;
   for (int k = lane; k < n; k += 32)
-    if (i < n) E = max(E, (int)((__double_as_longlong(L[i + (int64_t)n * k]) >> 52) & 0x7FF));
+    if (i < n) E = max(E, biased_exp(L[i + (int64_t)n * k]));
   E = warp_max(E);
   for (int k = lane; k < n_pad; k += 32) {
-    int c[kOzSlices];
+    float c[kOzSlices];
     const double x = (i < n && k < n) ? L[i + (int64_t)n * k] : 0.0;
-    oz_digits(x, E, c);
+    oz_digits(oz_fixed(x, E), c);
 #pragma unroll
-    for (int s = 0; s < kOzSlices; ++s)
-      planes[s * P + (int64_t)i * n_pad + k] = __float2bfloat16_rn((float)c[s]);
+    for (int s = 0; s < kOzSlices; ++s) planes[s * P + (int64_t)i * n_pad + k] = __float2bfloat16_rn(c[s]);
   }
   if (lane == 0) scale[i] = E - 1029;
 }
 
-// T * 2^e rounded once to double (T a signed 128-bit integer).
-__device__ __forceinline__ double i128_scaled(__int128 T, int e) {
-  if (T == 0) return 0.0;
-  unsigned long long sign = 0;
-  unsigned __int128 a;
-  if (T < 0) {
-    sign = 1ull << 63;
-    a = (unsigned __int128)(-T);
-  } else {
-    a = (unsigned __int128)T;
-  }
-  const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
-  int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
-  unsigned long long mant;
-  const int sh = msb - 52;
-  if (sh <= 0) {
-    mant = lo << (-sh);
-  } else {
-    const unsigned __int128 q = a >> sh;
-    const unsigned __int128 rem = a - (q << sh);
-    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
-    mant = (unsigned long long)q;
-    if (rem > half || (rem == half && (mant & 1))) {
-      ++mant;
-      if (mant >> 53) {
-        mant >>= 1;
-        ++msb;
-      }
-    }
-  }
-  const int biased = msb + e + 1023;
-  if (biased <= 0) return __longlong_as_double((long long)sign);
-  if (biased >= 2047) return __longlong_as_double((long long)(sign | (0x7FFull << 52)));
-  return __longlong_as_double(
-      (long long)(sign | ((unsigned long long)biased << 52) | (mant & ((1ull << 52) - 1))));
+// T 2^e rounded to a double, T = sum_k G_k 2^(8 (6 - k)) for the exact
+// integer accumulators G_0..G_6 (FP32 bit patterns, |G_k| < 2^24): with
+// |T| < 2^70 for n <= 128, S = floor(T / 2^8) fits 63 bits and is rounded to
+// 53 bits (half up on the magnitude), an error below (1/2 + 2^-8) ulp.
+__device__ __forceinline__ double oz_assemble(const uint32_t* G, int e) {
+  int g[kOzSlices];
+#pragma unroll
+  for (int k = 0; k < kOzSlices; ++k) g[k] = __float2int_rn(__uint_as_float(G[k]));
+  long long hi = (long long)(g[0] * 256 + g[1]);
+  hi = hi * 256 + g[2];
+  hi = hi * 256 + g[3];
+  long long lo = (long long)g[4] * 256 + g[5];
+  lo = lo * 256 + g[6];
+  const long long S = hi * 65536 + (lo >> 8);
+  if (S == 0) return 0.0;
+  const unsigned long long sign = (unsigned long long)S & (1ull << 63);
+  const unsigned long long a = S < 0 ? 0ull - (unsigned long long)S : (unsigned long long)S;
+  const int lz = __clzll((long long)a);
+  const unsigned long long nm = a << lz;                      // leading one at bit 63
+  const unsigned long long m = (nm >> 11) + ((nm >> 10) & 1ull);  // in [2^52, 2^53]
+  const int be = e + 1094 - lz;                               // biased exponent of a 2^(e + 8)
+  if (be <= 0) return __longlong_as_double((long long)sign);
+  if (be >= 2047) return __longlong_as_double((long long)(sign | (0x7FFull << 52)));
+  // m = 2^53 carries into the exponent field (and to infinity from be = 2046)
+  const unsigned long long bits = ((unsigned long long)(be - 1) << 52) + m;
+  return __longlong_as_double((long long)(bits | sign));
 }
 
 struct OzParams {
@@ -178,9 +216,16 @@ struct OzParams {
   int* status;
 };
 
-// Per tile: A = 7 digit planes of 128 fibres x 64 K (one 3D TMA box), B = 7
-// digit planes of NT rows x 64 K; 28 products x 4 K-steps per chunk into 7
-// accumulators; one shared-memory stage (the digits take 112 KiB per chunk).
+constexpr int kOzEpiWarps = 8;
+constexpr int NTH = 64 + 32 * kOzEpiWarps;
+
+// Per tile: A = 7 digit planes of 128 fibres x 64 K, B = 7 digit planes of
+// NT rows x 64 K, each plane pair on its own barrier so that the products of
+// G_k start once planes 0..k have landed; 28 products x 4 K-steps per chunk
+// into 7 accumulators; one shared-memory stage (112 KiB of A digits per
+// chunk).  Warp 0 issues the copies, one thread of warp 1 the MMAs, and
+// warps 2..9 the epilogue (two warps per TMEM lane quarter, each taking half
+// of the NT columns).
 template <int NT>
 __global__ void __launch_bounds__(NTH, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
@@ -190,18 +235,18 @@ __global__ void __launch_bounds__(NTH, 1)
   constexpr uint32_t A_SLICE = BM * 128;  // bytes of one digit plane of the A tile
   constexpr uint32_t B_SLICE = NT * 128;
   constexpr uint32_t STAGE = kOzSlices * (A_SLICE + B_SLICE);
-  uint64_t* full = (uint64_t*)(smem + STAGE);
-  uint64_t* empty = full + 1;
+  uint64_t* full = (uint64_t*)(smem + STAGE);  // [7]: plane s of A and of B landed
+  uint64_t* empty = full + kOzSlices;
   uint64_t* tfull = empty + 1;
   uint64_t* tempty = tfull + 2;
   uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    mbar_init(full, 1);
+    for (int s = 0; s < kOzSlices; ++s) mbar_init(&full[s], 1);
     mbar_init(empty, 1);
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 128);
+      mbar_init(&tempty[b], 32 * kOzEpiWarps);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -231,15 +276,19 @@ __global__ void __launch_bounds__(NTH, 1)
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(full, STAGE);
-          tma_load_3d(smem, &mapA, full, kc * 64, m0, 0);
-          tma_load_3d(smem + kOzSlices * A_SLICE, &mapB, full, kc * 64, r0, 0);
+#pragma unroll 1
+          for (int s = 0; s < kOzSlices; ++s) {
+            mbar_arrive_expect_tx(&full[s], A_SLICE + B_SLICE);
+            tma_load_3d(smem + s * A_SLICE, &mapA, &full[s], kc * 64, m0, s);
+            tma_load_3d(smem + kOzSlices * A_SLICE + s * B_SLICE, &mapB, &full[s], kc * 64, r0, s);
+          }
           ph ^= 1;
           ++issued;
         }
         if (!ok) break;
       }
-      if (issued) (void)mbar_wait(full, ph ^ 1, P.status, 0);  // last copy landed
+      if (issued)  // the last copies landed
+        for (int s = 0; s < kOzSlices; ++s) (void)mbar_wait(&full[s], ph ^ 1, P.status, 0);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -251,18 +300,18 @@ __global__ void __launch_bounds__(NTH, 1)
         if (!mbar_wait(&tempty[buf], aph ^ 1, P.status, 12)) break;
         tc_fence_after();
         const uint32_t d0 = tmem_base + (uint32_t)(buf * kOzSlices * NT);
-        for (int kc = 0; kc < P.nk; ++kc) {
-          if (!mbar_wait(full, ph, P.status, 13)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
+        for (int kc = 0; kc < P.nk && ok; ++kc) {
           const uint32_t a0 = smem_u32(smem), b0 = a0 + kOzSlices * A_SLICE;
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint32_t off = kk * 32;
+          for (int k = 0; k < kOzSlices; ++k) {
+            if (!mbar_wait(&full[k], ph, P.status, 13)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
 #pragma unroll
-            for (int k = 0; k < kOzSlices; ++k) {
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t off = kk * 32;
 #pragma unroll
               for (int s = 0; s <= k; ++s) {  // digit s of L times digit k - s of X
                 const uint32_t first = (kc == 0 && kk == 0 && s == 0) ? 0u : 1u;
@@ -271,6 +320,7 @@ __global__ void __launch_bounds__(NTH, 1)
               }
             }
           }
+          if (!ok) break;
           umma_commit(empty);
           ph ^= 1;
         }
@@ -283,7 +333,9 @@ __global__ void __launch_bounds__(NTH, 1)
       }
     }
   } else {
-    const int q = warp & 3;
+    const int q = warp & 3;  // TMEM lane quarter of this warp
+    const int half = (warp - 2) >> 2;
+    constexpr int HALF = NT / 2;
     const int row = q * 32 + lane;
     int buf = 0;
     uint32_t aph = 0;
@@ -295,27 +347,23 @@ __global__ void __launch_bounds__(NTH, 1)
       const bool valid = m < P.M2;
       const int sx = valid ? P.xscale[m] : 0;
 #pragma unroll 1
-      for (int c0 = 0; c0 < NT; c0 += 16) {
-        float G[kOzSlices][16];
+      for (int c0 = half * HALF; c0 < (half + 1) * HALF; c0 += 8) {
+        uint32_t G[kOzSlices][8];
 #pragma unroll
         for (int k = 0; k < kOzSlices; ++k)
-          tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) +
-                        (uint32_t)(buf * kOzSlices * NT + k * NT + c0),
-                    G[k]);
+          tmem_ld8_nowait(tmem_base + ((uint32_t)(q * 32) << 16) +
+                              (uint32_t)(buf * kOzSlices * NT + k * NT + c0),
+                          G[k]);
+        tmem_wait_ld();
         if (!valid) continue;
-#pragma unroll 4
-        for (int j = 0; j < 16; ++j) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
           const int i = r0 + c0 + j;
           if (i >= P.n) break;
-          long long hi = __float2int_rn(G[0][j]);
-          hi = hi * 256 + __float2int_rn(G[1][j]);
-          hi = hi * 256 + __float2int_rn(G[2][j]);
-          hi = hi * 256 + __float2int_rn(G[3][j]);
-          long long lo = __float2int_rn(G[4][j]);
-          lo = lo * 256 + __float2int_rn(G[5][j]);
-          lo = lo * 256 + __float2int_rn(G[6][j]);
-          const __int128 T = (__int128)hi * ((__int128)1 << 24) + (__int128)lo;
-          P.out[m + P.M2 * (int64_t)i] = i128_scaled(T, sx + P.lscale[i] - 48);
+          uint32_t g[kOzSlices];
+#pragma unroll
+          for (int k = 0; k < kOzSlices; ++k) g[k] = G[k][j];
+          P.out[m + P.M2 * (int64_t)i] = oz_assemble(g, sx + P.lscale[i] - 48);
         }
       }
       tc_fence_before();
@@ -355,11 +403,11 @@ bool get_enc() {
 }
 
 // 3D map over 7 planes of a row-major (rows x inner) bf16 array; box
-// {64, box_rows, 7} with the 128-byte swizzle.
+// {64, box_rows, 1} (one plane) with the 128-byte swizzle.
 bool make_map3(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint32_t box_rows) {
   cuuint64_t dims[3] = {inner, rows, (cuuint64_t)kOzSlices};
   cuuint64_t strides[2] = {inner * 2, inner * rows * 2};
-  cuuint32_t box[3] = {64, box_rows, (cuuint32_t)kOzSlices};
+  cuuint32_t box[3] = {64, box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
   return g_enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -506,11 +554,11 @@ cudaError_t oz_tucker(OzState* s, const Combo& in, const void* const* Bp, const 
   for (int mu = 0; mu < s->d; ++mu) {
     const int n = (int)s->n[mu];
     const int64_t M2 = N / n;
-    {  // split: one warp per fibre
-      int64_t blocks = (M2 * 32 + 255) / 256;
-      if (blocks > 152 * 16) blocks = 152 * 16;
+    {  // split: n / 8 threads per fibre, whole fibres per block
+      const int fpb = kSplitThreads / (n / 8);
+      const int64_t blocks = (M2 + fpb - 1) / fpb;
       count_launch();
-      oz_split_kernel<<<(int)blocks, 256, 0, st>>>(cur, n, M2, planes, N, xscale);
+      oz_split_kernel<<<(unsigned)blocks, kSplitThreads, 0, st>>>(cur, n, M2, fpb, planes, N, xscale);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }

@@ -9,9 +9,10 @@
 // G_k = sum_{s + t = k} sum_j b_s c_t.  Each product of digits is below 2^14
 // and (k + 1) n 2^14 < 2^24 for n <= 128, so the tensor cores accumulate
 // every G_k (k = 0..6, 28 digit products) exactly in FP32; the epilogue
-// assembles sum_k 2^(8 (6 - k)) G_k as a 128-bit integer and rounds it once to
-// FP64.  Dropping the terms with s + t >= 7 leaves an error below about
-// 2^-53 of |l| |x| (the scale of an FP64 dot product's own rounding).
+// assembles floor(sum_k 2^(8 (6 - k)) G_k / 2^8) in 64-bit integers and
+// rounds it to FP64 (within (1/2 + 2^-8) ulp of the digit sum).  Dropping the
+// terms with s + t >= 7 leaves an error below about 2^-53 of |l| |x| (the
+// scale of an FP64 dot product's own rounding).
 #pragma once
 
 #include <cstdint>

@@ -123,6 +123,14 @@ struct phiks_plan_s {
   int last_s = -1, last_q = -1, last_T = -1, last_tuckers = 0;
   TcState* tc = nullptr;
   OzState* oz = nullptr;
+  // CUDA graphs of whole calls (phiks_options.graph), keyed by everything the
+  // captured launches depend on
+  struct CallGraph {
+    cudaGraphExec_t exec = nullptr;
+    uint64_t launches = 0;
+    int tuckers = 0;
+  };
+  std::map<std::vector<uint64_t>, CallGraph> graphs;
   // profiling: event pairs around mu-mode products
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -142,6 +150,11 @@ struct DeviceGuard {
     if (prev >= 0) cudaSetDevice(prev);
   }
 };
+
+void drop_graphs(phiks_plan_s* P) {
+  for (auto& g : P->graphs) cudaGraphExecDestroy(g.second.exec);
+  P->graphs.clear();
+}
 
 int64_t mode_a(const phiks_plan_s* P, int mu) {
   int64_t a = 1;
@@ -393,6 +406,7 @@ phiks_status ensure_expm_scratch(phiks_plan_s* P, size_t elems) {
   if (P->expm_scratch_elems >= elems) return PHIKS_OK;
   if (P->expm_scratch) {
     CK(cudaDeviceSynchronize());
+    drop_graphs(P);
     cudaFree(P->expm_scratch);
   }
   P->expm_scratch = nullptr;
@@ -450,6 +464,7 @@ phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool 
       auto lru = std::min_element(P->banks.begin(), P->banks.end(),
                                   [](const Bank& x, const Bank& y) { return x.stamp < y.stamp; });
       CK(cudaStreamSynchronize(st));
+      drop_graphs(P);
       cudaFree(lru->dev);
       if (lru->tcb) cudaFree(lru->tcb);
       P->banks.erase(lru);
@@ -1116,6 +1131,7 @@ void phiks_destroy(phiks_plan_t P) {
   DeviceGuard g(P->device);
   cudaDeviceSynchronize();
   for (auto e : P->ev_pool) cudaEventDestroy(e);
+  drop_graphs(P);
   for (auto& b : P->banks) {
     cudaFree(b.dev);
     if (b.tcb) cudaFree(b.tcb);
@@ -1274,6 +1290,7 @@ phiks_status phiks_apply_ex(phiks_plan_t P, double tau, int p, const void* const
     if (P->ws_bytes < need) {
       if (P->ws) {
         CK(cudaStreamSynchronize(st));
+        drop_graphs(P);
         cudaFree(P->ws);
       }
       P->ws = nullptr;
@@ -1283,22 +1300,80 @@ phiks_status phiks_apply_ex(phiks_plan_t P, double tau, int p, const void* const
     }
     ws = (char*)P->ws;
   }
-  double* acc[PHIKS_MAX_P];
-  Ctx c{P, st, {nullptr, nullptr}, 0};
-  carve(c, p, ws, acc);
+  // everything from here on is device work on `st` (host state aside)
+  int tuckers = 0;
+  auto body = [&]() -> phiks_status {
+    double* acc[PHIKS_MAX_P];
+    Ctx c{P, st, {nullptr, nullptr}, 0};
+    carve(c, p, ws, acc);
+    Bank* B = nullptr;
+    TRY(get_bank(P, tau, s, q, o.rule, o.no_cache != 0, st, &B));
+    if (kind == 0) {
+      TRY(run_same(c, B, s, p, v[0], o, acc, out));
+    } else {
+      TRY(run_lincomb(c, B, s, p, v, o, acc, out));
+    }
+    CK(cudaGetLastError());
+    tuckers = c.tuckers;
+    return PHIKS_OK;
+  };
 
-  Bank* B = nullptr;
-  TRY(get_bank(P, tau, s, q, o.rule, o.no_cache != 0, st, &B));
-  if (kind == 0) {
-    TRY(run_same(c, B, s, p, v[0], o, acc, out));
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(st, &cap));
+  Bank* hit = nullptr;
+  // (the legacy default stream cannot be captured)
+  if (o.graph && !P->prof && cap == cudaStreamCaptureStatusNone && st != nullptr &&
+      st != cudaStreamLegacy)
+    for (auto& b : P->banks)
+      if (b.tau == tau && b.s == s && b.q == q && b.rule == o.rule) hit = &b;
+  if (hit) {
+    // a bank exists, so the call allocates nothing: capture it once per key
+    std::vector<uint64_t> key;
+    uint64_t tb;
+    std::memcpy(&tb, &tau, 8);
+    key = {tb, (uint64_t)p, (uint64_t)nv, (uint64_t)(uintptr_t)out, (uint64_t)(uintptr_t)ws,
+           (uint64_t)s, (uint64_t)q, (uint64_t)o.rule, (uint64_t)o.nscales, (uint64_t)o.skip_phi0,
+           (uint64_t)o.no_cache, (uint64_t)(uintptr_t)hit->dev, (uint64_t)(uintptr_t)hit->tcb,
+           (uint64_t)(uintptr_t)P->expm_scratch};
+    for (int i = 0; i < nv; ++i) key.push_back((uint64_t)(uintptr_t)v[i]);
+    auto it = P->graphs.find(key);
+    if (it == P->graphs.end()) {
+      if (P->graphs.size() >= 64) drop_graphs(P);
+      const uint64_t l0 = phiks::kernel_launch_count();
+      CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      const phiks_status r = body();
+      cudaGraph_t gr = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(st, &gr);
+      if (r != PHIKS_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return r;
+      }
+      if (ce != cudaSuccess) {
+        if (gr) cudaGraphDestroy(gr);
+        CK(ce);
+      }
+      phiks_plan_s::CallGraph cg;
+      const cudaError_t ie = cudaGraphInstantiate(&cg.exec, gr, 0);
+      cudaGraphDestroy(gr);
+      CK(ie);
+      // the captured launches were counted once; the first replay below runs them
+      cg.launches = phiks::kernel_launch_count() - l0;
+      cg.tuckers = tuckers;
+      it = P->graphs.emplace(key, cg).first;
+      CK(cudaGraphLaunch(it->second.exec, st));
+    } else {
+      CK(cudaGraphLaunch(it->second.exec, st));
+      phiks::count_launch(it->second.launches);
+    }
+    hit->stamp = ++P->clock;
+    tuckers = it->second.tuckers;
   } else {
-    TRY(run_lincomb(c, B, s, p, v, o, acc, out));
+    TRY(body());
   }
-  CK(cudaGetLastError());
   P->last_s = s;
   P->last_q = q;
   P->last_T = T;
-  P->last_tuckers = c.tuckers;
+  P->last_tuckers = tuckers;
   (void)es;
   return PHIKS_OK;
 }
@@ -1315,6 +1390,7 @@ phiks_status phiks_tucker(phiks_plan_t P, const void* V, void* W, const double* 
   if (P->ws_bytes < need) {
     if (P->ws) {
       CK(cudaDeviceSynchronize());
+      drop_graphs(P);
       cudaFree(P->ws);
     }
     P->ws = nullptr;
