@@ -5,7 +5,10 @@ Workload: d = 3 advection-diffusion-reaction operator, n = 64 per mode
 phi_l(tau K) v_l with outputs at tau, tau/2, tau/4 (three phi-actions per
 step), tau = 5e-4, v_l ~ N(0, 1) seeded.  One step = one phiks_apply_ex call:
 norms, parameter selection, the small FP64 exponentials (recomputed every
-step), quadrature, squaring and the scale outputs.
+step), quadrature, squaring and the scale outputs.  The mu-mode products are
+FP64 emulated on the tensor cores (exact bf16 digit products) by default;
+`--dtype fp64` runs them on the FP64 pipe.  Both are timed, and both meet
+the 1e-12 FP64 tolerance against the oracle.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 (Taylor action of the augmented matrix) on the same workload instead.
@@ -171,6 +174,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one oz_gemm_kernel<16> launch on
+# this workload (ncu --set full capture, profiles/oz_gemm_fp64emu_adr3d_n64.md)
+OZ_GEMM_TRAFFIC_BYTES = 3.79392e6
+
+
 def run_phiks(args):
     import torch
 
@@ -184,79 +200,105 @@ def run_phiks(args):
 
     wl = workload()
     N = wl.N
-    main_dtype = pk.PHIKS_FP64_EMU if args.dtype == "fp64emu" else pk.PHIKS_FP64
-    plan = pk.Plan(wl.A, main_dtype)
+    # FP64-accurate arithmetic: the emulated products (default) or the DFMA path
+    main_dtype = pk.PHIKS_FP64 if args.dtype == "fp64" else pk.PHIKS_FP64_EMU
+    other_dtype = pk.PHIKS_FP64 if main_dtype == pk.PHIKS_FP64_EMU else pk.PHIKS_FP64_EMU
     stream = torch.cuda.Stream()
     vs = [torch.from_numpy(v).cuda() for v in wl.vs]
-    out = torch.empty(wl.nscales * N, device="cuda", dtype=torch.float64)
     flush = torch.empty(256 << 20, device="cuda", dtype=torch.uint8)   # 256 MiB > 129 MB L2
     # every call replays its kernels from a CUDA graph captured on the second
     # call (phiks_options.graph); norms and the (s, q) selection run each call
     opts = pk.make_options(nscales=wl.nscales, no_cache=1, graph=1)
     opts_plain = pk.make_options(nscales=wl.nscales, no_cache=1)
-
-    def step():
-        pk.phiks_apply_ex(plan.handle, wl.tau, wl.p, vs, out, stream, opts=opts)
+    # caller norms: no synchronisation inside the call (profiling pass only)
+    opts_plain_vn = pk.make_options(nscales=wl.nscales, no_cache=1,
+                                    vnorms=[float(np.linalg.norm(v)) for v in wl.vs])
 
     def barrier():
         if ws > 1:
             import torch.distributed as dist
             dist.barrier()
 
+    def timed_calls(plan, out, o, steps, ev_list=None):
+        """Summed ms of `steps` calls, L2 flushed (untimed) before each."""
+        tot = 0.0
+        for k in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+                e0.record(stream)
+                pk.phiks_apply_ex(plan.handle, wl.tau, wl.p, vs, out, stream, opts=o)
+                e1.record(stream)
+            if ev_list is not None:
+                ev_list.append((e0, e1))
+            else:
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+        return tot
+
+    def kernel_profile(plan, out):
+        """Per-launch ms and algorithmic flops of the mu-mode kernel (events
+        around every launch, a separate pass).  A 20 ms spin on the stream
+        before each call lets the host queue the whole call first, so that
+        the brackets time the kernels and not the host's launch rate."""
+        pk.phiks_profile_enable(plan.handle, True)
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(k & 0xFF)
+                torch.cuda._sleep(int(2.0e9 * 0.02))
+                pk.phiks_apply_ex(plan.handle, wl.tau, wl.p, vs, out, stream, opts=opts_plain_vn)
+        kms, kl, kfl = pk.phiks_profile_read(plan.handle)
+        pk.phiks_profile_enable(plan.handle, False)
+        return kms / max(kl, 1), kfl / max(kl, 1), kfl / args.steps
+
+    def roofline(dtype, per_launch_ms, flops_per_launch):
+        if dtype == pk.PHIKS_FP64:
+            achieved = flops_per_launch / (per_launch_ms * 1e-3) / 1e12
+            return {"bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / PEAK_FP64_TFLOPS, "traffic": None,
+                    "kernel": "mode_product_f64_kernel", "per_launch_ms": per_launch_ms,
+                    "flops_per_launch": flops_per_launch,
+                    "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)"}
+        peaks, src = measured_peaks()
+        nbytes = 16.0 * N    # algorithmic: N FP64 in + N FP64 out per mu-mode product
+        achieved = nbytes / (per_launch_ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": OZ_GEMM_TRAFFIC_BYTES,
+                "kernel": "oz_gemm_kernel<16>", "per_launch_ms": per_launch_ms,
+                "bytes_per_launch": nbytes, "peak_source": "hbm_gbs of %s peaks (copy)" % src,
+                "note": "latency bound at this size: 5.8% tensor-pipe activity (ncu)"}
+
+    # ---- headline path
+    plan = pk.Plan(wl.A, main_dtype)
+    out = torch.empty(wl.nscales * N, device="cuda", dtype=torch.float64)
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
-            step()
+            pk.phiks_apply_ex(plan.handle, wl.tau, wl.p, vs, out, stream, opts=opts)
     torch.cuda.synchronize()
     s_, q_, T_, tuckers = plan.last_params()
 
     # ---- timed region: K steps, L2 flushed before each (flush not timed)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+    ev = []
     clocks = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
     clocks.start()
     launches0 = pk.phiks_kernel_launches()
     t_wall = time.perf_counter()
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(k & 0xFF)
-            ev[k][0].record(stream)
-            step()
-            ev[k][1].record(stream)
+    timed_calls(plan, out, opts, args.steps, ev)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     launches = pk.phiks_kernel_launches() - launches0
     barrier()
     clk = clocks.stop()
+    pk.phiks_device_status(plan.handle, stream)
     ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), ws)
     ms_step = ms / args.steps
     value = whole_job_rate(wl.nscales, args.steps, ws, ms)
     gpu_out = out.cpu().numpy().copy()
 
-    # ---- kernel-level pass: events around every mu-mode product launch
-    pk.phiks_profile_enable(plan.handle, True)
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)
-            step()
-    kms, klaunch, kflops = pk.phiks_profile_read(plan.handle)
-    pk.phiks_profile_enable(plan.handle, False)
-    per_launch_ms = kms / max(klaunch, 1)
-    achieved = kflops / max(kms, 1e-9) / 1e9          # TFLOP/s (flops / ms / 1e9)
-    step_flops = kflops / args.steps
-
-    # ---- the same calls with one launch per kernel instead of the graph
-    pms = 0.0
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(k & 0xFF)
-            e0.record(stream)
-            pk.phiks_apply_ex(plan.handle, wl.tau, wl.p, vs, out, stream, opts=opts_plain)
-            e1.record(stream)
-        torch.cuda.synchronize()
-        pms += e0.elapsed_time(e1)
+    per_launch_ms, flops_per_launch, step_flops = kernel_profile(plan, out)
+    pms = timed_calls(plan, out, opts_plain, args.steps)
 
     # ---- cached small exponentials (steady state of a fixed-step integrator)
     opts_c = pk.make_options(nscales=wl.nscales, graph=1)
@@ -264,22 +306,15 @@ def run_phiks(args):
         for _ in range(2):
             pk.phiks_apply_ex(plan.handle, wl.tau, wl.p, vs, out, stream, opts=opts_c)
     torch.cuda.synchronize()
-    cms = 0.0
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(k & 0xFF)
-            e0.record(stream)
-            pk.phiks_apply_ex(plan.handle, wl.tau, wl.p, vs, out, stream, opts=opts_c)
-            e1.record(stream)
-        torch.cuda.synchronize()
-        cms += e0.elapsed_time(e1)
+    cms = timed_calls(plan, out, opts_c, args.steps)
 
     # ---- end to end through the C ABI with host buffers
     hv = [torch.from_numpy(v).pin_memory() for v in wl.vs]
     hout = torch.empty(wl.nscales * N, dtype=torch.float64).pin_memory()
     dv = [torch.empty(N, device="cuda", dtype=torch.float64) for _ in wl.vs]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_ms = 0.0
-    for k in range(args.steps):
+    for k in range(args.steps + 2):   # two untimed calls capture the graph for dv
         with torch.cuda.stream(stream):
             flush.fill_(k & 0xFF)
             e0.record(stream)
@@ -289,10 +324,12 @@ def run_phiks(args):
             hout.copy_(out, non_blocking=True)
             e1.record(stream)
         torch.cuda.synchronize()
-        e2e_ms += e0.elapsed_time(e1)
+        if k >= 2:
+            e2e_ms += e0.elapsed_time(e1)
     h2d = sum(v.nbytes for v in wl.vs)
     d2h = hout.numel() * 8
 
+    emu = main_dtype == pk.PHIKS_FP64_EMU
     line = {
         "metric": METRIC, "value": value, "unit": "phi-actions/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -303,72 +340,57 @@ def run_phiks(args):
                                    "small_exponentials": "recomputed every step",
                                    "submission": "CUDA graph of the call's kernels, replayed each "
                                                  "call after the norms and the (s, q) selection"}),
+        "mu_mode_products": ("FP64 emulated on tcgen05: exact bf16 digit products, FP32 "
+                             "accumulation, rounded to FP64" if emu else "FP64 DFMA"),
         "mu_mode_tflops": step_flops / (ms_step * 1e-3) / 1e12,
-        "mu_mode_products": "fp64 emulated by bf16 digit products on tcgen05" if main_dtype != pk.PHIKS_FP64
-        else "fp64 DFMA",
         "value_cached_exponentials": ws * wl.nscales * args.steps / (cms * 1e-3),
         "value_plain_launches": ws * wl.nscales * args.steps / (pms * 1e-3),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / PEAK_FP64_TFLOPS, "traffic": None,
-                     "kernel": "mode_product_f64_kernel", "per_launch_ms": per_launch_ms,
-                     "flops_per_launch": kflops / max(klaunch, 1),
-                     "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
+        "roofline": roofline(main_dtype, per_launch_ms, flops_per_launch),
         "e2e": {"value": ws * wl.nscales * args.steps / (e2e_ms * 1e-3), "unit": "phi-actions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clk,
         "wall_s_timed": t_wall,
     }
-    # the same workload with the mu-mode products emulated on the tensor cores
-    # (exact bf16 digit products, one rounding to FP64)
+    plan.close()
+
+    # ---- the other FP64-accurate path on the same workload
+    other_key = "fp64_dfma" if emu else "fp64_emulated"
+    other_out = None
     try:
-        if main_dtype != pk.PHIKS_FP64:
-            raise RuntimeError("headline already uses the emulated products")
-        pe = pk.Plan(wl.A, pk.PHIKS_FP64_EMU)
-        oute = torch.empty_like(out)
-
-        def step_e():
-            pk.phiks_apply_ex(pe.handle, wl.tau, wl.p, vs, oute, stream, opts=opts)
-
+        po = pk.Plan(wl.A, other_dtype)
+        oo = torch.empty_like(out)
         with torch.cuda.stream(stream):
             for _ in range(max(args.warmup, 3)):
-                step_e()
+                pk.phiks_apply_ex(po.handle, wl.tau, wl.p, vs, oo, stream, opts=opts)
         torch.cuda.synchronize()
-        pk.phiks_device_status(pe.handle, stream)
-        eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(k & 0xFF)
-                eev[k][0].record(stream)
-                step_e()
-                eev[k][1].record(stream)
+        oev = []
+        timed_calls(po, oo, opts, args.steps, oev)
         torch.cuda.synchronize()
-        pk.phiks_device_status(pe.handle, stream)
-        ems = max_over_ranks(sum(a.elapsed_time(b) for a, b in eev), ws)
-        emu_out = oute.cpu().numpy().copy()
-        line["fp64_emulated"] = {"value": whole_job_rate(wl.nscales, args.steps, ws, ems),
-                                 "ms_per_step": ems / args.steps, "speedup_vs_fp64": ms / ems,
-                                 "dtype": "f64 from exact bf16 digit products (tcgen05)"}
-        pe.close()
-    except Exception as ex:  # plan refused (shape) or device error: report, keep the FP64 line
-        emu_out = None
-        line["fp64_emulated"] = {"error": str(ex)[:200]}
+        pk.phiks_device_status(po.handle, stream)
+        oms = max_over_ranks(sum(a.elapsed_time(b) for a, b in oev), ws)
+        other_out = oo.cpu().numpy().copy()
+        opl, ofl, _ = kernel_profile(po, oo)
+        line[other_key] = {"value": whole_job_rate(wl.nscales, args.steps, ws, oms),
+                           "ms_per_step": oms / args.steps, "headline_speedup_over_it": oms / ms,
+                           "roofline": roofline(other_dtype, opl, ofl)}
+        po.close()
+    except Exception as ex:  # plan refused (shape) or device error: report, keep the headline
+        line[other_key] = {"error": str(ex)[:200]}
     if rank == 0 and not args.no_cpu_baseline:
         dt, outs = time_oracle_call(wl)
-        err = max(float(np.abs(gpu_out[L * N:(L + 1) * N] - outs[L]).max() / np.abs(outs[L]).max())
-                  for L in range(wl.nscales))
-        line["rel_err_vs_oracle"] = err
-        if emu_out is not None:
-            line["fp64_emulated"]["rel_err_vs_oracle"] = max(
-                float(np.abs(emu_out[L * N:(L + 1) * N] - outs[L]).max() / np.abs(outs[L]).max())
-                for L in range(wl.nscales))
+
+        def err_of(o):
+            return max(float(np.abs(o[L * N:(L + 1) * N] - outs[L]).max() / np.abs(outs[L]).max())
+                       for L in range(wl.nscales))
+        line["rel_err_vs_oracle"] = err_of(gpu_out)
+        if other_out is not None:
+            line[other_key]["rel_err_vs_oracle"] = err_of(other_out)
         line["cpu_baseline"] = {"value": wl.nscales / dt, "unit": "phi-actions/s",
                                 "cores": oracle_threads(), "kind": "oracle",
                                 "sample": "one full call (3 scale outputs), O3 Taylor action, %.1f s" % dt}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -792,7 +814,8 @@ def main():
     ap.add_argument("--config", default="adr3d", choices=["adr3d", "small", "precision", "batched", "served"],
                     help="adr3d: the headline FP64 workload; precision: the split-dtype form")
     ap.add_argument("--dtype", default="all", choices=["all", "fp64emu"] + PRECISION_DTYPES,
-                    help="precision/batched/served: split dtype; adr3d: fp64 (default) or fp64emu")
+                    help="precision/batched/served: split dtype; adr3d: FP64-accurate products, "
+                         "emulated on the tensor cores (default, or fp64emu) or fp64 (DFMA)")
     ap.add_argument("--variant", default="cheb", choices=["cheb", "fd"])
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--no-ref", action="store_true", help="skip the FP64 reference path")

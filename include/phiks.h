@@ -176,10 +176,12 @@ phiks_status phiks_tucker(phiks_plan_t plan, const void* V, void* W, const doubl
 phiks_status phiks_expm(int batch, int n, const double* X, double* E, void* stream);
 
 /* Kernel timing for measurement tools.  While enabled, every mu-mode product
- * the plan launches is bracketed by two CUDA events on its stream.
- * phiks_profile_read synchronises the plan's device, returns the summed
- * milliseconds of those launches, their count and their algorithmic flops
- * (2 N n_mu each), and resets the sums. */
+ * the plan launches is bracketed by two CUDA events on its stream: the FP64
+ * mode-product kernel, the tensor-core GEMM pass of FP64_EMU (its digit
+ * split excluded), or the whole tensor-core Tucker operator of the split
+ * dtypes.  phiks_profile_read synchronises the plan's device, returns the
+ * summed milliseconds of those brackets, their count and their algorithmic
+ * flops (2 N n_mu per mode), and resets the sums. */
 phiks_status phiks_profile_enable(phiks_plan_t plan, int enable);
 phiks_status phiks_profile_read(phiks_plan_t plan, double* ms, int64_t* launches, double* flops);
 

@@ -216,33 +216,43 @@ struct OzParams {
   int* status;
 };
 
-constexpr int kOzEpiWarps = 8;
+constexpr int kOzEpiWarps = 16;
 constexpr int NTH = 64 + 32 * kOzEpiWarps;
 
 // Per tile: A = 7 digit planes of 128 fibres x 64 K, B = 7 digit planes of
-// NT rows x 64 K, each plane pair on its own barrier so that the products of
-// G_k start once planes 0..k have landed; 28 products x 4 K-steps per chunk
-// into 7 accumulators; one shared-memory stage (112 KiB of A digits per
-// chunk).  Warp 0 issues the copies, one thread of warp 1 the MMAs, and
-// warps 2..9 the epilogue (two warps per TMEM lane quarter, each taking half
+// NT rows x 64 K stored back to back, so that one MMA multiplies A plane t by
+// B planes 0..6-t at once (N = (7 - t) NT) and writes block s of its result
+// to TMEM column block t + s: block k then accumulates
+//     G_k = sum_{s + t = k} B_s A_t^T,  k = 0..6,
+// with 7 MMAs per 16-wide K step instead of 28 (the first, t = 0, covers all
+// seven blocks and starts them).  A planes land on their own barriers, so
+// the MMAs of plane t start once it is in.  One shared-memory stage (112 KiB
+// of A digits per 64-wide K chunk).  Warp 0 issues the copies, one thread of
+// warp 1 the MMAs, and the kOzEpiWarps warps from 2 on the epilogue
+// (kOzEpiWarps / 4 warps per TMEM lane quarter, each taking an equal share
 // of the NT columns).
+
 template <int NT>
 __global__ void __launch_bounds__(NTH, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    OzParams P) {
+  static_assert(kOzSlices * NT <= 256 && (kOzSlices * NT) % 16 == 0, "MMA N out of range");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr uint32_t A_SLICE = BM * 128;  // bytes of one digit plane of the A tile
   constexpr uint32_t B_SLICE = NT * 128;
   constexpr uint32_t STAGE = kOzSlices * (A_SLICE + B_SLICE);
-  uint64_t* full = (uint64_t*)(smem + STAGE);  // [7]: plane s of A and of B landed
-  uint64_t* empty = full + kOzSlices;
+  constexpr uint32_t SET = kOzSlices * NT;  // TMEM columns of one accumulator set
+  uint64_t* fullA = (uint64_t*)(smem + STAGE);  // [7]: plane t of A landed
+  uint64_t* fullB = fullA + kOzSlices;          // all planes of B landed
+  uint64_t* empty = fullB + 1;
   uint64_t* tfull = empty + 1;
   uint64_t* tempty = tfull + 2;
   uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kOzSlices; ++s) mbar_init(&full[s], 1);
+    for (int t = 0; t < kOzSlices; ++t) mbar_init(&fullA[t], 1);
+    mbar_init(fullB, 1);
     mbar_init(empty, 1);
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -276,48 +286,52 @@ __global__ void __launch_bounds__(NTH, 1)
             ok = false;
             break;
           }
+          mbar_arrive_expect_tx(fullB, kOzSlices * B_SLICE);
+#pragma unroll 1
+          for (int s = 0; s < kOzSlices; ++s)
+            tma_load_3d(smem + kOzSlices * A_SLICE + s * B_SLICE, &mapB, fullB, kc * 64, r0, s);
 #pragma unroll 1
           for (int s = 0; s < kOzSlices; ++s) {
-            mbar_arrive_expect_tx(&full[s], A_SLICE + B_SLICE);
-            tma_load_3d(smem + s * A_SLICE, &mapA, &full[s], kc * 64, m0, s);
-            tma_load_3d(smem + kOzSlices * A_SLICE + s * B_SLICE, &mapB, &full[s], kc * 64, r0, s);
+            mbar_arrive_expect_tx(&fullA[s], A_SLICE);
+            tma_load_3d(smem + s * A_SLICE, &mapA, &fullA[s], kc * 64, m0, s);
           }
           ph ^= 1;
           ++issued;
         }
         if (!ok) break;
       }
-      if (issued)  // the last copies landed
-        for (int s = 0; s < kOzSlices; ++s) (void)mbar_wait(&full[s], ph ^ 1, P.status, 0);
+      if (issued) {  // the last copies landed
+        (void)mbar_wait(fullB, ph ^ 1, P.status, 0);
+        for (int s = 0; s < kOzSlices; ++s) (void)mbar_wait(&fullA[s], ph ^ 1, P.status, 0);
+      }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_make(1, NT);
       uint32_t ph = 0, aph = 0;
       int buf = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < P.num_tiles && ok; t += gridDim.x) {
         if (!mbar_wait(&tempty[buf], aph ^ 1, P.status, 12)) break;
         tc_fence_after();
-        const uint32_t d0 = tmem_base + (uint32_t)(buf * kOzSlices * NT);
+        const uint32_t d0 = tmem_base + (uint32_t)buf * SET;
         for (int kc = 0; kc < P.nk && ok; ++kc) {
           const uint32_t a0 = smem_u32(smem), b0 = a0 + kOzSlices * A_SLICE;
-#pragma unroll
-          for (int k = 0; k < kOzSlices; ++k) {
-            if (!mbar_wait(&full[k], ph, P.status, 13)) {
+          if (!mbar_wait(fullB, ph, P.status, 13)) {
+            ok = false;
+            break;
+          }
+#pragma unroll 1
+          for (int at = 0; at < kOzSlices; ++at) {  // digit plane at of X times every plane of L
+            if (!mbar_wait(&fullA[at], ph, P.status, 13)) {
               ok = false;
               break;
             }
             tc_fence_after();
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
-              const uint32_t off = kk * 32;
-#pragma unroll
-              for (int s = 0; s <= k; ++s) {  // digit s of L times digit k - s of X
-                const uint32_t first = (kc == 0 && kk == 0 && s == 0) ? 0u : 1u;
-                umma<0>(d0 + (uint32_t)(k * NT), sdesc_sw128(a0 + (k - s) * A_SLICE + off),
-                        sdesc_sw128(b0 + s * B_SLICE + off), idesc, first);
-              }
+              const uint32_t first = (kc == 0 && kk == 0 && at == 0) ? 0u : 1u;
+              umma<0>(d0 + (uint32_t)(at * NT), sdesc_sw128(a0 + at * A_SLICE + kk * 32),
+                      sdesc_sw128(b0 + kk * 32), idesc_make(1, (kOzSlices - at) * NT), first);
             }
           }
           if (!ok) break;
@@ -334,8 +348,11 @@ __global__ void __launch_bounds__(NTH, 1)
     }
   } else {
     const int q = warp & 3;  // TMEM lane quarter of this warp
-    const int half = (warp - 2) >> 2;
-    constexpr int HALF = NT / 2;
+    constexpr int GROUPS = kOzEpiWarps / 4;   // warps per lane quarter
+    constexpr int CW = NT / GROUPS;           // columns per warp
+    constexpr int CH = 4;                     // columns per TMEM load
+    static_assert(CW % CH == 0, "epilogue column split");
+    const int grp = (warp - 2) >> 2;
     const int row = q * 32 + lane;
     int buf = 0;
     uint32_t aph = 0;
@@ -347,24 +364,26 @@ __global__ void __launch_bounds__(NTH, 1)
       const bool valid = m < P.M2;
       const int sx = valid ? P.xscale[m] : 0;
 #pragma unroll 1
-      for (int c0 = half * HALF; c0 < (half + 1) * HALF; c0 += 8) {
-        uint32_t G[kOzSlices][8];
+      for (int c0 = grp * CW; c0 < (grp + 1) * CW; c0 += CH) {
+        const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * SET + (uint32_t)c0;
+        uint32_t G[kOzSlices][CH];
 #pragma unroll
-        for (int k = 0; k < kOzSlices; ++k)
-          tmem_ld8_nowait(tmem_base + ((uint32_t)(q * 32) << 16) +
-                              (uint32_t)(buf * kOzSlices * NT + k * NT + c0),
-                          G[k]);
+        for (int k = 0; k < kOzSlices; ++k) tmem_ld4_nowait(tb + (uint32_t)(k * NT), G[k]);
         tmem_wait_ld();
         if (!valid) continue;
+        // independent assemblies (lscale has n_pad >= every tile's columns
+        // entries), then the stores of the columns below n
+        double r[CH];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int i = r0 + c0 + j;
-          if (i >= P.n) break;
+        for (int j = 0; j < CH; ++j) {
           uint32_t g[kOzSlices];
 #pragma unroll
           for (int k = 0; k < kOzSlices; ++k) g[k] = G[k][j];
-          P.out[m + P.M2 * (int64_t)i] = oz_assemble(g, sx + P.lscale[i] - 48);
+          r[j] = oz_assemble(g, sx + P.lscale[r0 + c0 + j] - 48);
         }
+#pragma unroll
+        for (int j = 0; j < CH; ++j)
+          if (r0 + c0 + j < P.n) P.out[m + P.M2 * (int64_t)(r0 + c0 + j)] = r[j];
       }
       tc_fence_before();
       mbar_arrive(&tempty[buf]);
@@ -417,8 +436,8 @@ bool make_map3(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, 
 size_t up1k(size_t x) { return (x + 1023) / 1024 * 1024; }
 
 int ntile_for(int n, int64_t M2) {
-  // enough tiles to spread over the SMs, at most 64 rows (7 accumulators of
-  // NT columns must fit the 512 TMEM columns)
+  // enough tiles to spread over the SMs, at most 32 rows (one MMA covers the
+  // seven B planes: N = 7 NT <= 256)
   const int64_t mt = (M2 + BM - 1) / BM;
   if (n <= 16) return 16;
   if (mt * ((n + 31) / 32) >= 152 || n <= 32) return 32;
@@ -545,7 +564,7 @@ bool cached(OzState* s, CUtensorMap* m, const void* base, uint64_t inner, uint64
 }  // namespace
 
 cudaError_t oz_tucker(OzState* s, const Combo& in, const void* const* Bp, const Epi& epi,
-                      cudaStream_t st) {
+                      cudaStream_t st, const cudaEvent_t* ev) {
   const int64_t N = s->N;
   __nv_bfloat16* planes = (__nv_bfloat16*)s->ws;
   int* xscale = (int*)(s->ws + up1k((size_t)kOzSlices * N * 2));
@@ -589,10 +608,16 @@ cudaError_t oz_tucker(OzState* s, const Combo& in, const void* const* Bp, const 
     P.xscale = xscale;
     P.lscale = lscale;
     P.status = s->status;
-    cudaError_t e = NT == 16 ? run_oz_gemm<16>(s, mA, mB, P, st)
-                             : (NT == 32 ? run_oz_gemm<32>(s, mA, mB, P, st)
-                                         : run_oz_gemm<64>(s, mA, mB, P, st));
+    if (ev) {
+      cudaError_t e = cudaEventRecord(ev[2 * mu], st);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = NT == 16 ? run_oz_gemm<16>(s, mA, mB, P, st) : run_oz_gemm<32>(s, mA, mB, P, st);
     if (e != cudaSuccess) return e;
+    if (ev) {
+      e = cudaEventRecord(ev[2 * mu + 1], st);
+      if (e != cudaSuccess) return e;
+    }
     std::memset(&cur, 0, sizeof cur);
     cur.nsrc = 1;
     cur.src[0] = dst;

@@ -41,9 +41,10 @@ size_t oz_bplanes_bytes(int n);
 cudaError_t oz_prepare_b(const double* L, int n, void* dst, cudaStream_t st);
 
 // (combination `in`) x_1 L_1 ... x_d L_d through `epi` (FP64), Bp[mu] made
-// by oz_prepare_b for L_mu.
+// by oz_prepare_b for L_mu.  `ev` (2 d events, or null): ev[2 mu] and
+// ev[2 mu + 1] are recorded around the tensor-core pass of mode mu.
 cudaError_t oz_tucker(OzState* s, const Combo& in, const void* const* Bp, const Epi& epi,
-                      cudaStream_t st);
+                      cudaStream_t st, const cudaEvent_t* ev = nullptr);
 
 int oz_read_status(OzState* s, cudaStream_t st);
 

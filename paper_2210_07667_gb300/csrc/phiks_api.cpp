@@ -551,17 +551,24 @@ struct Mats {
   const void* B[PHIKS_MAX_D];
 };
 
-phiks_status prof_begin(Ctx& c, cudaEvent_t* e1) {
-  phiks_plan_s* P = c.P;
-  *e1 = nullptr;
-  if (!P->prof) return PHIKS_OK;
+// The next event pair of the profiling pool (read back in pairs).
+phiks_status prof_pair(phiks_plan_s* P, cudaEvent_t* e0, cudaEvent_t* e1) {
   while (P->ev_pool.size() < P->ev_used + 2) {
     cudaEvent_t e;
     CK(cudaEventCreate(&e));
     P->ev_pool.push_back(e);
   }
-  cudaEvent_t e0 = P->ev_pool[P->ev_used++];
+  *e0 = P->ev_pool[P->ev_used++];
   *e1 = P->ev_pool[P->ev_used++];
+  return PHIKS_OK;
+}
+
+phiks_status prof_begin(Ctx& c, cudaEvent_t* e1) {
+  phiks_plan_s* P = c.P;
+  *e1 = nullptr;
+  if (!P->prof) return PHIKS_OK;
+  cudaEvent_t e0;
+  TRY(prof_pair(P, &e0, e1));
   CK(cudaEventRecord(e0, c.st));
   return PHIKS_OK;
 }
@@ -574,17 +581,30 @@ phiks_status prof_end(Ctx& c, cudaEvent_t e1, double flops) {
 }
 
 // (input combination) x_1 L_1 ... x_d L_d, the last mode through `epi`.
-// FP64: one profiled launch per mode; split dtypes: one profiled tensor-core
-// Tucker (split pass + d GEMM passes).
+// FP64: one profiled launch per mode; FP64_EMU: one profiled tensor-core
+// pass per mode; split dtypes: one profiled tensor-core Tucker (split pass +
+// d GEMM passes).
 phiks_status tucker(Ctx& c, const Combo& in, const Mats& M, const Epi* epi) {
   phiks_plan_s* P = c.P;
+  if (emu_dtype(P)) {
+    cudaEvent_t ev[2 * PHIKS_MAX_D];
+    const bool prof = P->prof;
+    if (prof)
+      for (int mu = 0; mu < P->d; ++mu) TRY(prof_pair(P, &ev[2 * mu], &ev[2 * mu + 1]));
+    cudaError_t e = oz_tucker(P->oz, in, M.B, *epi, c.st, prof ? ev : nullptr);
+    if (e != cudaSuccess)
+      return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), oz_last_error());
+    if (prof)
+      for (int mu = 0; mu < P->d; ++mu) P->prof_flops += 2.0 * (double)P->N * (double)P->n[mu];
+    c.tuckers++;
+    return PHIKS_OK;
+  }
   if (P->dtype != PHIKS_FP64) {
     cudaEvent_t e1;
     TRY(prof_begin(c, &e1));
-    cudaError_t e = emu_dtype(P) ? oz_tucker(P->oz, in, M.B, *epi, c.st) : tc_tucker(P->tc, in, M.B, *epi, c.st);
+    cudaError_t e = tc_tucker(P->tc, in, M.B, *epi, c.st);
     if (e != cudaSuccess)
-      return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e),
-                  emu_dtype(P) ? oz_last_error() : tc_last_error());
+      return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), tc_last_error());
     double fl = 0;
     for (int mu = 0; mu < P->d; ++mu) fl += 2.0 * (double)P->N * (double)P->n[mu];
     TRY(prof_end(c, e1, fl));
