@@ -4,6 +4,7 @@
 // eq. Tuckerprod) and of the squaring chain exp(A_mu/2^(j-1)) =
 // exp(A_mu/2^j)^2 (eq. simul, eq. comb).
 #include "kernels.cuh"
+#include "pdl.cuh"
 
 namespace phiks {
 namespace {
@@ -15,6 +16,7 @@ constexpr int GK = 16;
 // small tiles to spread over every SM.
 template <int GT, int GR>
 __global__ void __launch_bounds__((GT / GR) * (GT / GR)) gemm_batch_f64_kernel(GemmBatch gb) {
+  pdl_wait();
   constexpr int GTHR = GT / GR;
   constexpr int GNT = GTHR * GTHR;
   const int k = blockIdx.z;
@@ -77,6 +79,7 @@ __global__ void __launch_bounds__((GT / GR) * (GT / GR)) gemm_batch_f64_kernel(G
 }
 
 __global__ void scale_batch_f64_kernel(ScaleBatch sb) {
+  pdl_wait();
   const int k = blockIdx.y;
   const int n = sb.n[k];
   const int64_t nn = (int64_t)n * n;
@@ -98,15 +101,14 @@ cudaError_t launch_gemm_batch_f64(const GemmBatch& gb, int nmax, cudaStream_t st
   count_launch();
   if (ctas(32) >= 4 * 152) {
     const int t = (nmax + 31) / 32;
-    gemm_batch_f64_kernel<32, 2><<<dim3(t, t, gb.count), 256, 0, st>>>(gb);
+    return launch_pdl(gemm_batch_f64_kernel<32, 2>, dim3(t, t, gb.count), dim3(256), 0, st, gb);
   } else if (ctas(16) >= 4 * 152) {
     const int t = (nmax + 15) / 16;
-    gemm_batch_f64_kernel<16, 1><<<dim3(t, t, gb.count), 256, 0, st>>>(gb);
+    return launch_pdl(gemm_batch_f64_kernel<16, 1>, dim3(t, t, gb.count), dim3(256), 0, st, gb);
   } else {
     const int t = (nmax + 7) / 8;
-    gemm_batch_f64_kernel<8, 1><<<dim3(t, t, gb.count), 64, 0, st>>>(gb);
+    return launch_pdl(gemm_batch_f64_kernel<8, 1>, dim3(t, t, gb.count), dim3(64), 0, st, gb);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_scale_batch_f64(const ScaleBatch& sb, int nmax, cudaStream_t st) {
@@ -117,8 +119,7 @@ cudaError_t launch_scale_batch_f64(const ScaleBatch& sb, int nmax, cudaStream_t 
   if (gx > 1024) gx = 1024;
   dim3 grid(gx, sb.count);
   count_launch();
-  scale_batch_f64_kernel<<<grid, 256, 0, st>>>(sb);
-  return cudaGetLastError();
+  return launch_pdl(scale_batch_f64_kernel, grid, dim3(256), 0, st, sb);
 }
 
 }  // namespace phiks

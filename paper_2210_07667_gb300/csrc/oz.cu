@@ -23,6 +23,7 @@
 #include <tuple>
 
 #include "oz.cuh"
+#include "pdl.cuh"
 #include "tcgen05.cuh"
 
 namespace phiks {
@@ -96,6 +97,7 @@ __global__ void __launch_bounds__(kSplitThreads) oz_split_kernel(Combo in, int n
                                                                  __nv_bfloat16* planes, int64_t N,
                                                                  int* scale) {
   __shared__ int emax[kSplitThreads];
+  pdl_wait();
   const int cpf = n >> 3;
   const int t = threadIdx.x;
   const int fl = t / cpf;
@@ -155,6 +157,7 @@ __global__ void __launch_bounds__(kSplitThreads) oz_split_kernel(Combo in, int n
 // B digits: row i of L (column-major n x n), row-major planes n_pad x n_pad.
 __global__ void oz_prep_b_kernel(const double* L, int n, int n_pad, __nv_bfloat16* planes,
                                  int* scale) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   if (i >= n_pad) return;
@@ -272,6 +275,7 @@ __global__ void __launch_bounds__(NTH, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  pdl_wait();  // the digit planes and scales come from the kernels before
 
   if (warp == 0) {
     if (lane == 0) {
@@ -520,8 +524,8 @@ cudaError_t oz_prepare_b(const double* L, int n, void* dst, cudaStream_t st) {
   __nv_bfloat16* planes = (__nv_bfloat16*)dst;
   int* scale = (int*)((uint8_t*)dst + up1k((size_t)kOzSlices * np * np * 2));
   count_launch();
-  oz_prep_b_kernel<<<(np * 32 + 255) / 256, 256, 0, st>>>(L, n, np, planes, scale);
-  return cudaGetLastError();
+  return launch_pdl(oz_prep_b_kernel, dim3((np * 32 + 255) / 256), dim3(256), 0, st, L, n, np, planes,
+                    scale);
 }
 
 namespace {
@@ -544,8 +548,7 @@ cudaError_t run_oz_gemm(OzState* s, const CUtensorMap& mA, const CUtensorMap& mB
   }
   const int grid = P.num_tiles < 152 ? P.num_tiles : 152;
   count_launch();
-  kern<<<grid, NTH, smem, st>>>(mA, mB, P);
-  return cudaGetLastError();
+  return launch_pdl(kern, dim3(grid), dim3(NTH), smem, st, mA, mB, P);
 }
 
 bool cached(OzState* s, CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint32_t box) {
@@ -577,8 +580,8 @@ cudaError_t oz_tucker(OzState* s, const Combo& in, const void* const* Bp, const 
       const int fpb = kSplitThreads / (n / 8);
       const int64_t blocks = (M2 + fpb - 1) / fpb;
       count_launch();
-      oz_split_kernel<<<(unsigned)blocks, kSplitThreads, 0, st>>>(cur, n, M2, fpb, planes, N, xscale);
-      cudaError_t e = cudaGetLastError();
+      cudaError_t e = launch_pdl(oz_split_kernel, dim3((unsigned)blocks), dim3(kSplitThreads), 0, st, cur, n,
+                                 M2, fpb, planes, N, xscale);
       if (e != cudaSuccess) return e;
     }
     const int np = (n + 63) / 64 * 64;

@@ -30,6 +30,7 @@
 #include <tuple>
 
 #include "tc.cuh"
+#include "pdl.cuh"
 #include "tcgen05.cuh"
 
 namespace phiks {
@@ -137,6 +138,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  pdl_wait();  // operand planes come from the kernels before
 
   if (warp == 0) {
     // ---------------- TMA producer
@@ -271,6 +273,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // at most 22 significant bits, FP32 holds 24).
 template <int KIND, int NP>
 __global__ void tc_split_kernel(Combo in, int64_t N, void* p0, void* p1) {
+  pdl_wait();
   const bool plain = in.nsrc == 1 && in.coef[0] == 1.0;
   const bool f32 = in.f32mask & 1;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
@@ -294,6 +297,7 @@ __global__ void tc_split_kernel(Combo in, int64_t N, void* p0, void* p1) {
 // B planes of an FP64 column-major n x n matrix: plane[i * n_pad + k] from L[i, k].
 template <int KIND, int NP>
 __global__ void tc_prep_b_kernel(const double* L, int n, int n_pad, void* p0, void* p1) {
+  pdl_wait();
   const int64_t tot = (int64_t)n_pad * n_pad;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -444,12 +448,12 @@ cudaError_t tc_prepare_b(int dtype, const double* L, int n, void* dst, cudaStrea
   const int64_t tot = (int64_t)np * np;
   const int grid = (int)std::min<int64_t>((tot + 255) / 256, 1024);
   count_launch();
+  void* none = nullptr;
   switch (dtype) {
-    case PHIKS_BF16X3: tc_prep_b_kernel<0, 2><<<grid, 256, 0, st>>>(L, n, np, p0, p1); break;
-    case PHIKS_TF32X3: tc_prep_b_kernel<1, 2><<<grid, 256, 0, st>>>(L, n, np, p0, p1); break;
-    default: tc_prep_b_kernel<1, 1><<<grid, 256, 0, st>>>(L, n, np, p0, nullptr); break;
+    case PHIKS_BF16X3: return launch_pdl(tc_prep_b_kernel<0, 2>, dim3(grid), dim3(256), 0, st, L, n, np, p0, p1);
+    case PHIKS_TF32X3: return launch_pdl(tc_prep_b_kernel<1, 2>, dim3(grid), dim3(256), 0, st, L, n, np, p0, p1);
+    default: return launch_pdl(tc_prep_b_kernel<1, 1>, dim3(grid), dim3(256), 0, st, L, n, np, p0, none);
   }
-  return cudaGetLastError();
 }
 
 namespace {
@@ -481,8 +485,7 @@ cudaError_t run_gemm(TcState* s, const CUtensorMap* mA, const CUtensorMap* mB, G
   // second CTA off the SM, so co-resident CTAs never oversubscribe TMEM.
   int grid = P.num_tiles < 152 ? P.num_tiles : 152;
   count_launch();
-  kern<<<grid, NTHREADS, smem, st>>>(mA[0], mA[1], mB[0], mB[1], P);
-  return cudaGetLastError();
+  return launch_pdl(kern, dim3(grid), dim3(NTHREADS), smem, st, mA[0], mA[1], mB[0], mB[1], P);
 }
 
 }  // namespace
@@ -498,10 +501,11 @@ cudaError_t tc_tucker(TcState* s, const Combo& in, const void* const* Bp, const 
   {
     const int grid = (int)std::min<int64_t>((N + 255) / 256, 152 * 8);
     count_launch();
-    if (dtype == PHIKS_BF16X3) tc_split_kernel<0, 2><<<grid, 256, 0, st>>>(in, N, set[0][0], set[0][1]);
-    else if (dtype == PHIKS_TF32X3) tc_split_kernel<1, 2><<<grid, 256, 0, st>>>(in, N, set[0][0], set[0][1]);
-    else tc_split_kernel<1, 1><<<grid, 256, 0, st>>>(in, N, set[0][0], nullptr);
-    cudaError_t e = cudaGetLastError();
+    void *q0 = set[0][0], *q1 = set[0][1], *none = nullptr;
+    cudaError_t e;
+    if (dtype == PHIKS_BF16X3) e = launch_pdl(tc_split_kernel<0, 2>, dim3(grid), dim3(256), 0, st, in, N, q0, q1);
+    else if (dtype == PHIKS_TF32X3) e = launch_pdl(tc_split_kernel<1, 2>, dim3(grid), dim3(256), 0, st, in, N, q0, q1);
+    else e = launch_pdl(tc_split_kernel<1, 1>, dim3(grid), dim3(256), 0, st, in, N, q0, none);
     if (e != cudaSuccess) return e;
   }
   int cur = 0;

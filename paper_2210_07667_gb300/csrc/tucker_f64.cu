@@ -15,6 +15,7 @@
 #include <atomic>
 
 #include "kernels.cuh"
+#include "pdl.cuh"
 
 namespace phiks {
 
@@ -54,6 +55,7 @@ __device__ __forceinline__ void store_epi(const Epi& epi, double* W, int64_t idx
 template <int TI, int TC, int RI, int RC, int KC, bool XFAST>
 __global__ void __launch_bounds__((TI / RI) * (TC / RC))
     mode_product_f64_kernel(Combo pro, const double* __restrict__ L, ModeGeom g, double* W, Epi epi) {
+  pdl_wait();
   constexpr int TROWS = TI / RI, TCOLS = TC / RC, NT = TROWS * TCOLS;
   constexpr int LPT = (TI * KC + NT - 1) / NT;
   constexpr int VPT = (TC * KC + NT - 1) / NT;
@@ -155,18 +157,20 @@ __global__ void __launch_bounds__((TI / RI) * (TC / RC))
 }
 
 template <int TI, int TC, int RI, int RC, int KC>
-void launch_tiled(const Combo& pro, const double* L, ModeGeom g, double* W, const Epi& e,
-                  cudaStream_t st) {
+cudaError_t launch_tiled(const Combo& pro, const double* L, ModeGeom g, double* W, const Epi& e,
+                         cudaStream_t st) {
   constexpr int NT = (TI / RI) * (TC / RC);
   const int64_t ncols = g.a * g.b;
   dim3 grid((unsigned)((ncols + TC - 1) / TC), (unsigned)((g.n + TI - 1) / TI));
   if (g.a >= TC)
-    mode_product_f64_kernel<TI, TC, RI, RC, KC, true><<<grid, NT, 0, st>>>(pro, L, g, W, e);
-  else
-    mode_product_f64_kernel<TI, TC, RI, RC, KC, false><<<grid, NT, 0, st>>>(pro, L, g, W, e);
+    return launch_pdl(mode_product_f64_kernel<TI, TC, RI, RC, KC, true>, grid, dim3(NT), 0, st, pro, L, g,
+                      W, e);
+  return launch_pdl(mode_product_f64_kernel<TI, TC, RI, RC, KC, false>, grid, dim3(NT), 0, st, pro, L, g,
+                    W, e);
 }
 
 __global__ void combine_kernel(Epi e, int64_t N) {
+  pdl_wait();
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
        idx += (int64_t)gridDim.x * blockDim.x)
     epi_apply(e, idx, 0.0);
@@ -177,6 +181,7 @@ struct PtrArray {
 };
 
 __global__ void sumsq_kernel_arr(PtrArray xs, int64_t N, int is_f32, double* out) {
+  pdl_wait();
   const int k = blockIdx.y;
   double s = 0.0;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
@@ -219,11 +224,8 @@ cudaError_t launch_mode_product_f64(const Combo& pro, const double* L, ModeGeom 
   // 16 x 16 tiles (64 threads, 4 outputs each), so that even N = 2^18 spreads
   // over ~1000 CTAs and the 152 SMs' FP64 pipes stay evenly loaded.
   const int64_t big_tiles = ((g.a * g.b + 63) / 64) * ((g.n + 31) / 32);
-  if (big_tiles >= 8 * 152)
-    launch_tiled<32, 64, 2, 4, 16>(pro, L, g, W, e, st);
-  else
-    launch_tiled<16, 16, 2, 2, 32>(pro, L, g, W, e, st);
-  return cudaGetLastError();
+  if (big_tiles >= 8 * 152) return launch_tiled<32, 64, 2, 4, 16>(pro, L, g, W, e, st);
+  return launch_tiled<16, 16, 2, 2, 32>(pro, L, g, W, e, st);
 }
 
 cudaError_t launch_combine(const Epi& e0, int64_t N, cudaStream_t st) {
@@ -233,8 +235,7 @@ cudaError_t launch_combine(const Epi& e0, int64_t N, cudaStream_t st) {
   for (int t = 0; t < kMaxOut; ++t) e.b[t] = 0.0;  // no product result here
   epi_finalize(e);
   count_launch();
-  combine_kernel<<<grid_for(N, 256), 256, 0, st>>>(e, N);
-  return cudaGetLastError();
+  return launch_pdl(combine_kernel, dim3(grid_for(N, 256)), dim3(256), 0, st, e, N);
 }
 
 cudaError_t launch_sumsq(const void* const* x, int count, int64_t N, int is_f32, double* out,
@@ -245,8 +246,7 @@ cudaError_t launch_sumsq(const void* const* x, int count, int64_t N, int is_f32,
   for (int k = 0; k < count; ++k) a.p[k] = x[k];
   dim3 grid(grid_for(N, 256) > 304 ? 304 : grid_for(N, 256), count);
   count_launch();
-  sumsq_kernel_arr<<<grid, 256, 0, st>>>(a, N, is_f32, out);
-  return cudaGetLastError();
+  return launch_pdl(sumsq_kernel_arr, grid, dim3(256), 0, st, a, N, is_f32, out);
 }
 
 }  // namespace phiks
