@@ -34,6 +34,63 @@ def test_orders_of_convergence():
     assert 3.8 < e[0] / e[1] < 4.2
 
 
+AC = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "ac_exprk3_errors.json")))
+
+
+@pytest.fixture(scope="module")
+def ac_problem():
+    A, u0 = wk.ac_paper(AC["n"], AC["eps"])
+    g = it.ac_g(AC["eps"])
+    ref = it.integrate_problem([A], g, u0, 0.0, AC["T"], AC["ref_steps"], "exprk4s6")
+    return A, u0, g, ref
+
+
+@pytest.mark.parametrize("steps,rtol", [(100, 1e-4), (200, 1e-4), (150, 1.5e-3)])
+def test_oracle_ac_exprk3_reproduces_printed_errors(ac_problem, steps, rtol):
+    """Sec. 4.3, Fig. ord3: expRK3 against the expRK4s6 reference; the printed
+    series agree with each other to 5e-4 at 125-175 steps, to 1e-5 at 100 and
+    200."""
+    A, u0, g, ref = ac_problem
+    u = it.integrate_problem([A], g, u0, 0.0, AC["T"], steps, "exprk3")
+    err = it.rel_inf(u, ref)
+    gold = AC["exprk3"][str(steps)]
+    assert abs(err - gold) <= rtol * gold, (err, gold)
+
+
+def test_orders_fourth_order_schemes_block_diagonal():
+    """Brusselator (block-diagonal K, Sec. 4.4) on a 6^3 grid to T = 1: the
+    error ratio on halving the step is 2^order."""
+    blocks, w0 = wk.brusselator3d(6)
+    g = it.bruss_g(1.0, 3.0)
+    ref = it.integrate_problem(blocks, g, w0, 0.0, 1.0, 160, "exprk4s6")
+    for sch, lo, hi in [("exprk4s5", 14.0, 18.0), ("exprk4s6", 14.0, 18.0), ("exprk3", 7.0, 9.5)]:
+        e = [it.rel_inf(it.integrate_problem(blocks, g, w0, 0.0, 1.0, s, sch), ref) for s in (10, 20)]
+        assert lo < e[0] / e[1] < hi, (sch, e)
+
+
+def test_block_diagonal_phi_actions_vs_dense():
+    """The block-by-block phi-actions equal the top rows of one dense
+    exponential of the augmented matrix of the whole block-diagonal K (Sec. 2
+    augmented-matrix statement; scipy's expm)."""
+    from scipy.linalg import expm
+    from oracle import kron
+    blocks, w0 = wk.brusselator3d(3)
+    K = np.zeros((54, 54))
+    K[:27, :27] = kron.kron_sum_dense(blocks[0])
+    K[27:, 27:] = kron.kron_sum_dense(blocks[1])
+    rng = np.random.default_rng(3)
+    v1, v2 = rng.standard_normal(54), rng.standard_normal(54)
+    tau = 0.3
+    B = np.zeros((56, 56))
+    B[:54, :54] = tau * K
+    B[:54, 54] = v2
+    B[:54, 55] = v1
+    B[54, 55] = 1.0
+    ref = (expm(B) @ np.concatenate([w0, [0.0, 1.0]]))[:54]
+    got = it.lc(blocks, tau, [w0, v1, v2])
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("scheme,steps", [("expeuler", 300), ("etd2rk", 200)])
 def test_gpu_integrator_matches_paper_and_oracle(scheme, steps):

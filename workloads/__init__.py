@@ -219,6 +219,35 @@ def brusselator_operators(n: int, d1: float = 0.002, d2: float = 0.001, b: float
     return [A1, A1.copy(order="F")], [A2, A2.copy(order="F")]
 
 
+def ac_paper(n: int = 21, eps: float = 0.05, beta: float = 7.0, alpha: float = 0.75):
+    """Allen-Cahn problem of Sec. 4.3 on [0,1]^2 (homogeneous Neumann, n
+    vertex-centred points per direction): A_mu = d_xx + I/(2 eps^2) (so that
+    K = Lap + I/eps^2) and the initial state
+    u_0 = tanh((1/4 + cos(beta atan2(y - 1/2, x - 1/2))/10 - r) / (sqrt(2) alpha)),
+    r the distance to (1/2, 1/2); u_0 column-major (x fastest)."""
+    A = fd_laplacian_neumann(n, 1.0, 0.5 / eps ** 2)
+    x = np.arange(n) / (n - 1.0)
+    X1, X2 = np.meshgrid(x, x, indexing="ij")
+    r = np.sqrt((X1 - 0.5) ** 2 + (X2 - 0.5) ** 2)
+    u0 = np.tanh((0.25 + 0.1 * np.cos(beta * np.arctan2(X2 - 0.5, X1 - 0.5)) - r) / (np.sqrt(2.0) * alpha))
+    return [A, A.copy(order="F")], np.reshape(u0, -1, order="F")
+
+
+def brusselator3d(n: int, d1: float = 0.02, d2: float = 0.02, a: float = 1.0, b: float = 3.0,
+                  c: float = 1.0):
+    """Brusselator problem of Sec. 4.4 on [0,1]^3 (homogeneous Neumann, n
+    vertex-centred points, second-order differences): blocks
+    K_1 = d1 Lap - (b + 1) I and K_2 = d2 Lap as Kronecker sums, and the state
+    [u_0; v_0], u_0 = 64^2 prod x^2 (1 - x)^2, v_0 = c."""
+    A1 = fd_laplacian_neumann(n, d1, -(b + 1.0) / 3.0)
+    A2 = fd_laplacian_neumann(n, d2, 0.0)
+    x = np.arange(n) / (n - 1.0)
+    X1, X2, X3 = np.meshgrid(x, x, x, indexing="ij")
+    u0 = 64.0 ** 2 * (X1 * (1 - X1) * X2 * (1 - X2) * X3 * (1 - X3)) ** 2
+    w0 = np.concatenate([np.reshape(u0, -1, order="F"), np.full(n ** 3, c)])
+    return [[A1, A1.copy(order="F"), A1.copy(order="F")], [A2, A2.copy(order="F"), A2.copy(order="F")]], w0
+
+
 SERVED_CLASSES = {
     "ac": {"sizes": list(range(128, 1025, 32)), "tau": 1e-3},
     "adr": {"sizes": list(range(32, 193, 16)), "tau": 5e-4},
