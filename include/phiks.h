@@ -287,23 +287,50 @@ phiks_status phiks_serve_trace(const phiks_serve_config* cfg, int count, const p
                                const double* arrival_s, double* latency_ms, double* queue_ms,
                                double* makespan_s);
 
-/* Exponential integrators driving phiks (Sec. 2): exponential Euler
- * (eq. expEullc) and ETD2RK (eq. ETD2RKlc), each stage one linear
- * combination, with the nonlinear term g evaluated on the device. */
-typedef enum { PHIKS_EXP_EULER = 0, PHIKS_ETD2RK = 1 } phiks_scheme;
+/* Exponential integrators driving phiks: the linear-combination form of the
+ * exponential Runge--Kutta methods of Sec. 2 (eq. RK) with the tableaux the
+ * paper uses, every stage assembled from phiks calls whose scale outputs
+ * (eq. comb, eq. scallincomb) give stages at halved times:
+ *   PHIKS_EXP_EULER  eq. (expEullc), 1 call per step
+ *   PHIKS_ETD2RK     eq. (ETD2RKlc), 2 calls
+ *   PHIKS_EXPRK3     eq. (expRK3s3), c_2 = 1/4, c_3 = 1/2, gamma = -4/5, 3 calls
+ *   PHIKS_EXPRK4S5   eq. (expRK4s5) assembled as in eq. (expRK4s5_smart), 5 calls
+ *   PHIKS_EXPRK4S6   eq. (expRK4s6), c_2 = c_3 = 1/3, c_4 = 2/3, c_5 = 1/2,
+ *                    c_6 = 1 (stages 3-4 and 5-6 from one call each), 4 calls
+ * with the nonlinear term g evaluated on the device. */
+typedef enum {
+  PHIKS_EXP_EULER = 0, PHIKS_ETD2RK = 1, PHIKS_EXPRK3 = 2, PHIKS_EXPRK4S5 = 3, PHIKS_EXPRK4S6 = 4
+} phiks_scheme;
 typedef enum {
   PHIKS_NL_ADR_EXACT = 0,   /* Sec. 4.2: g = 1/(1+u^2) + Psi(t,x), exact solution e^t u_0 on the
-                               Dirichlet grid of [0,1]^3 (d = 3) */
-  PHIKS_NL_ALLEN_CAHN = 1   /* Sec. 4.3: g = -u^3 / eps^2 */
+                               Dirichlet grid x_i = i/(n+1) of [0,1]^3 (one block, d = 3) */
+  PHIKS_NL_ALLEN_CAHN = 1,  /* Sec. 4.3: g = -u^3 / eps^2 (one block) */
+  PHIKS_NL_BRUSSELATOR = 2  /* Sec. 4.4: w = [u; v] over two blocks of equal size,
+                               g = [a + u^2 v; b u - u^2 v] */
 } phiks_nonlinearity;
 typedef struct {
   int kind;                 /* phiks_nonlinearity */
   double eps, alpha;        /* ADR: diffusion and advection coefficients; AC: eps */
+  double a, b;              /* Brusselator: the reaction constants */
 } phiks_nonlinear;
 
-/* Advance u (device, N doubles, FP64 plan of K) from t0 to t0 + T in `steps`
- * equal steps.  n: host, d grid sizes (the plan's n_mu).  Each stage
- * synchronises `stream` once (the norms for the parameter selection). */
+/* Grid of a plan: *d and n[0 .. d-1] (host; n has room for PHIKS_MAX_D). */
+phiks_status phiks_plan_shape(phiks_plan_t plan, int* d, int64_t* n);
+
+/* Advance w (device, FP64) from t0 to t0 + T in `steps` equal steps of
+ * `scheme` for w' = K w + g(t, w) with K = diag(K_1, ..., K_nblocks)
+ * block diagonal (eq. ODE2): block b is plans[b]'s Kronecker sum, acting on
+ * the N_b entries of w after those of blocks 0..b-1 (column-major each).
+ * plans: FP64 or FP64_EMU.  opt (may be NULL): tol and graph apply to every
+ * phiks call; nscales, skip_phi0, vnorms and workspace are set internally.
+ * Device scratch of about 24 N doubles comes from the stream-ordered
+ * allocator.  Each phiks call synchronises `stream` once (the norms). */
+phiks_status phiks_integrate_blocks(int nblocks, const phiks_plan_t* plans, int scheme,
+                                    const phiks_nonlinear* g, double t0, double T, int steps,
+                                    double* w, const phiks_options* opt, void* stream);
+
+/* One block: phiks_integrate_blocks(1, &plan, ...); n and d must match the
+ * plan's grid. */
 phiks_status phiks_integrate(phiks_plan_t plan, const int64_t* n, int d, int scheme,
                              const phiks_nonlinear* g, double t0, double T, int steps, double* u,
                              void* stream);

@@ -21,7 +21,8 @@ __all__ = [
     "phiks_plan", "phiks_apply", "phiks_apply_ex", "phiks_workspace_size",
     "phiks_select_params", "phiks_choose_params", "phiks_last_params", "phiks_tucker", "phiks_expm",
     "phiks_profile_enable", "phiks_profile_read", "phiks_kernel_launches", "phiks_tucker_noalloc",
-    "phiks_device_status", "phiks_serve_trace", "phiks_integrate", "phiks_destroy", "phiks_last_error", "Plan", "Batch",
+    "phiks_device_status", "phiks_serve_trace", "phiks_integrate", "phiks_integrate_blocks",
+    "phiks_plan_shape", "phiks_destroy", "phiks_last_error", "Plan", "Batch",
     "EXPORTED",
 ]
 
@@ -38,7 +39,7 @@ EXPORTED = [
     "phiks_profile_enable", "phiks_profile_read", "phiks_kernel_launches", "phiks_tucker_noalloc",
     "phiks_device_status", "phiks_batch_create", "phiks_batch_destroy", "phiks_batch_apply",
     "phiks_batch_capture", "phiks_graph_launch", "phiks_graph_destroy", "phiks_serve_trace",
-    "phiks_integrate", "phiks_destroy", "phiks_last_error",
+    "phiks_integrate", "phiks_integrate_blocks", "phiks_plan_shape", "phiks_destroy", "phiks_last_error",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -91,11 +92,14 @@ class ServeConfig(ctypes.Structure):
 
 
 class Nonlinear(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int), ("eps", ctypes.c_double), ("alpha", ctypes.c_double)]
+    _fields_ = [("kind", ctypes.c_int), ("eps", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("a", ctypes.c_double), ("b", ctypes.c_double)]
 
 
-PHIKS_EXP_EULER, PHIKS_ETD2RK = 0, 1
-PHIKS_NL_ADR_EXACT, PHIKS_NL_ALLEN_CAHN = 0, 1
+PHIKS_EXP_EULER, PHIKS_ETD2RK, PHIKS_EXPRK3, PHIKS_EXPRK4S5, PHIKS_EXPRK4S6 = 0, 1, 2, 3, 4
+PHIKS_NL_ADR_EXACT, PHIKS_NL_ALLEN_CAHN, PHIKS_NL_BRUSSELATOR = 0, 1, 2
+SCHEMES = {"expeuler": PHIKS_EXP_EULER, "etd2rk": PHIKS_ETD2RK, "exprk3": PHIKS_EXPRK3,
+           "exprk4s5": PHIKS_EXPRK4S5, "exprk4s6": PHIKS_EXPRK4S6}
 
 
 class PhiksError(RuntimeError):
@@ -165,6 +169,11 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.phiks_integrate.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), i, i, ctypes.POINTER(Nonlinear),
                                   d, d, i, vp, vp]
     L.phiks_integrate.restype = ctypes.c_int
+    L.phiks_integrate_blocks.argtypes = [i, ctypes.POINTER(vp), i, ctypes.POINTER(Nonlinear), d, d, i, vp,
+                                         ctypes.POINTER(Options), vp]
+    L.phiks_integrate_blocks.restype = ctypes.c_int
+    L.phiks_plan_shape.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_int64)]
+    L.phiks_plan_shape.restype = ctypes.c_int
     L.phiks_device_status.argtypes = [vp, vp]
     L.phiks_device_status.restype = ctypes.c_int
     L.phiks_tucker_noalloc.argtypes = [i, ctypes.POINTER(ctypes.c_int64), vp, vp, ctypes.POINTER(vp), vp]
@@ -404,11 +413,30 @@ def phiks_serve_trace(requests, arrivals, slots=8, hbm_budget=0, poll_us=0):
 
 def phiks_integrate(plan: int, dims, scheme: int, kind: int, eps: float, alpha: float, t0: float,
                     T: float, steps: int, u, stream=None):
-    """Advance u in place with exponential Euler or ETD2RK (see include/phiks.h)."""
+    """Advance u in place with an exponential Runge-Kutta scheme (see include/phiks.h)."""
     n = (ctypes.c_int64 * len(dims))(*[int(m) for m in dims])
-    nl = Nonlinear(int(kind), float(eps), float(alpha))
+    nl = Nonlinear(int(kind), float(eps), float(alpha), 0.0, 0.0)
     _check(load().phiks_integrate(plan, n, len(dims), int(scheme), ctypes.byref(nl), float(t0), float(T),
                                   int(steps), _ptr(u), _stream(stream)))
+
+
+def phiks_integrate_blocks(plans, scheme: int, kind: int, t0: float, T: float, steps: int, w,
+                           eps: float = 0.0, alpha: float = 0.0, a: float = 0.0, b: float = 0.0,
+                           stream=None, **opts):
+    """Advance w in place for a block-diagonal K = diag(plans) (see include/phiks.h)."""
+    arr = (ctypes.c_void_p * len(plans))(*[p.handle if hasattr(p, "handle") else p for p in plans])
+    nl = Nonlinear(int(kind), float(eps), float(alpha), float(a), float(b))
+    o = make_options(**opts) if opts else None
+    _check(load().phiks_integrate_blocks(len(plans), arr, int(scheme), ctypes.byref(nl), float(t0), float(T),
+                                         int(steps), _ptr(w), ctypes.byref(o) if o is not None else None,
+                                         _stream(stream)))
+
+
+def phiks_plan_shape(plan: int):
+    d = ctypes.c_int()
+    n = (ctypes.c_int64 * 8)()
+    _check(load().phiks_plan_shape(plan, ctypes.byref(d), n))
+    return tuple(int(n[k]) for k in range(d.value))
 
 
 def phiks_destroy(plan: int):

@@ -1,19 +1,24 @@
-// Exponential integrators driving phiks on the device: exponential Euler and
-// ETD2RK in their linear-combination forms (Sec. 2, eq. expEullc and
-// eq. ETD2RKlc), with the nonlinear term evaluated by a CUDA kernel.
+// Exponential Runge--Kutta integrators driving phiks on the device (Sec. 2,
+// eq. RK, linear-combination form):
+//   u_ni    = exp(c_i tau K) u_n + c_i tau phi_1(c_i tau K) g_n
+//             + tau sum_{j<i} a_ij(tau K) d_nj,
+//   u_{n+1} = exp(tau K) u_n + tau phi_1(tau K) g_n + tau sum_i b_i(tau K) d_ni,
+//   d_ni    = g(t_n + c_i tau, u_ni) - g_n,
+// for block-diagonal K = diag(K_1, ..., K_B) of Kronecker sums (eq. ODE2).
 //
-//   exponential Euler:  u_{n+1} = exp(tau K) u_n + tau phi_1(tau K) g(t_n, u_n)
-//   ETD2RK:             u_n2    = exp(tau K) u_n + tau phi_1(tau K) g_n
-//                       u_{n+1} = exp(tau K) u_n + tau phi_1(tau K) g_n
-//                                 + tau phi_2(tau K) (g(t_n + tau, u_n2) - g_n)
-// Every stage is one phiks_apply_ex call (a linear combination).
+// Every phi-action comes from a phiks call
+//   LC(tau', p, [v_0..v_p], S)[s] = exp(c tau' K) v_0 + sum_l c^l phi_l(c tau' K) v_l,
+//   c = 2^-s, s < S,
+// whose scale outputs (eq. comb, eq. scallincomb) supply stages at halved
+// times; the stages and the step are then elementwise combinations.  The
+// assemblies per scheme are derived in the comments of each step function.
 //
-// Nonlinear terms:
-//   PHIKS_NL_ADR_EXACT (Sec. 4.2): g = 1/(1 + u^2) + Psi(t, x) on the
-//     Dirichlet grid x_i = i/(n+1) of [0,1]^3, Psi making e^t u_0,
-//     u_0 = 64 prod x(1-x), the exact solution of u_t = eps Lap u +
-//     alpha (d_1 + d_2 + d_3) u + g.
-//   PHIKS_NL_ALLEN_CAHN (Sec. 4.3): g = -u^3 / eps^2 (K = Lap + I/eps^2).
+// Nonlinear terms (evaluated by CUDA kernels):
+//   ADR_EXACT (Sec. 4.2): g = 1/(1 + u^2) + Psi(t, x) on the Dirichlet grid
+//     x_i = i/(n+1) of [0,1]^3, Psi making e^t u_0, u_0 = 64 prod x(1-x), the
+//     exact solution of u_t = eps Lap u + alpha (d_1 + d_2 + d_3) u + g.
+//   ALLEN_CAHN (Sec. 4.3): g = -u^3 / eps^2 (K = Lap + I/eps^2).
+//   BRUSSELATOR (Sec. 4.4): g(u, v) = (a + u^2 v, b u - u^2 v).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -26,8 +31,10 @@
 
 namespace {
 
-__global__ void g_adr_kernel(const double* __restrict__ u, double t, int n1, int n2, int n3,
-                             double eps, double alpha, double scale, double* __restrict__ out) {
+// out = scale * g(t, x) - sub (sub may be null)
+__global__ void g_adr_kernel(const double* __restrict__ x, double t, int n1, int n2, int n3, double eps,
+                             double alpha, double scale, const double* __restrict__ sub,
+                             double* __restrict__ out) {
   const int64_t N = (int64_t)n1 * n2 * n3;
   const double et = exp(t);
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
@@ -43,25 +50,54 @@ __global__ void g_adr_kernel(const double* __restrict__ u, double t, int n1, int
     const double grad = 64.0 * ((1 - 2 * x1) * q2 * q3 + q1 * (1 - 2 * x2) * q3 + q1 * q2 * (1 - 2 * x3));
     const double w = et * u0;
     const double psi = et * (u0 - eps * lap - alpha * grad) - 1.0 / (1.0 + w * w);
-    const double v = u[idx];
-    out[idx] = scale * (1.0 / (1.0 + v * v) + psi);
+    const double v = x[idx];
+    const double r = scale * (1.0 / (1.0 + v * v) + psi);
+    out[idx] = sub ? r - sub[idx] : r;
   }
 }
 
-__global__ void g_ac_kernel(const double* __restrict__ u, int64_t N, double eps, double scale,
-                            double* __restrict__ out) {
+__global__ void g_ac_kernel(const double* __restrict__ x, int64_t N, double eps, double scale,
+                            const double* __restrict__ sub, double* __restrict__ out) {
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const double v = u[idx];
-    out[idx] = -scale * v * v * v / (eps * eps);
+    const double v = x[idx];
+    const double r = -scale * v * v * v / (eps * eps);
+    out[idx] = sub ? r - sub[idx] : r;
   }
 }
 
-__global__ void axpby_kernel(const double* x, const double* y, double a, double b, int64_t N,
-                             double* out) {
+// w = [u; v], each of M entries
+__global__ void g_bruss_kernel(const double* __restrict__ w, int64_t M, double a, double b, double scale,
+                               const double* __restrict__ sub, double* __restrict__ out) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < M;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const double u = w[idx], v = w[M + idx];
+    const double uuv = u * u * v;
+    double ru = scale * (a + uuv), rv = scale * (b * u - uuv);
+    if (sub) {
+      ru -= sub[idx];
+      rv -= sub[M + idx];
+    }
+    out[idx] = ru;
+    out[M + idx] = rv;
+  }
+}
+
+constexpr int kMaxTerms = 8;
+struct Terms {
+  int k;
+  double c[kMaxTerms];
+  const double* x[kMaxTerms];
+};
+
+// out = sum_k c_k x_k (out may alias an x_k: each element is read before written)
+__global__ void combo_kernel(Terms t, int64_t N, double* out) {
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
-       idx += (int64_t)gridDim.x * blockDim.x)
-    out[idx] = a * x[idx] + b * y[idx];
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    double r = 0.0;
+    for (int k = 0; k < t.k; ++k) r = fma(t.c[k], t.x[k][idx], r);
+    out[idx] = r;
+  }
 }
 
 int grid_of(int64_t N) {
@@ -69,72 +105,307 @@ int grid_of(int64_t N) {
   return (int)(g > 152 * 16 ? 152 * 16 : (g < 1 ? 1 : g));
 }
 
-struct Fail {
-  phiks_status st;
-  std::string msg;
+struct Engine {
+  int nb = 0;
+  phiks_plan_t plan[8];
+  int64_t off[8], size[8];
+  int64_t N = 0, Nmax = 0;
+  cudaStream_t st = nullptr;
+  phiks_options base;
+  const phiks_nonlinear* g = nullptr;
+  int gd = 0;
+  int64_t gn[PHIKS_MAX_D] = {0};
+  double* pool = nullptr;
+  double* scratch = nullptr;  // nscales x Nmax, block outputs before the scatter
+  std::string err;
+
+  phiks_status fail(phiks_status s, const std::string& m) {
+    if (err.empty()) err = m;
+    return s;
+  }
+
+  // out[s * N ...] = LC(tau, p, v, S)[s] over all blocks
+  phiks_status lc(double tau, int p, const double* const* v, int S, double* out) {
+    for (int b = 0; b < nb; ++b) {
+      const void* vb[PHIKS_MAX_P + 1];
+      for (int l = 0; l <= p; ++l) vb[l] = v[l] ? (const void*)(v[l] + off[b]) : nullptr;
+      phiks_options o = base;
+      o.nscales = S;
+      o.skip_phi0 = 0;
+      o.vnorms = nullptr;
+      o.workspace = nullptr;
+      o.workspace_bytes = 0;
+      double* dst = (nb == 1) ? out : scratch;
+      phiks_status r = phiks_apply_ex(plan[b], tau, p, vb, p + 1, &o, dst, st);
+      if (r != PHIKS_OK) return fail(r, std::string("phiks call: ") + phiks_last_error());
+      if (nb > 1)
+        for (int s = 0; s < S; ++s)
+          if (cudaMemcpyAsync(out + s * N + off[b], scratch + s * size[b], (size_t)size[b] * 8,
+                              cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return fail(PHIKS_ERR_CUDA, "block scatter");
+    }
+    return PHIKS_OK;
+  }
+
+  // out = scale g(t, x) - sub
+  phiks_status eval_g(double t, const double* x, double scale, const double* sub, double* out) {
+    phiks::count_launch();
+    if (g->kind == PHIKS_NL_ADR_EXACT)
+      g_adr_kernel<<<grid_of(N), 256, 0, st>>>(x, t, (int)gn[0], (int)gn[1], (int)gn[2], g->eps, g->alpha,
+                                               scale, sub, out);
+    else if (g->kind == PHIKS_NL_ALLEN_CAHN)
+      g_ac_kernel<<<grid_of(N), 256, 0, st>>>(x, N, g->eps, scale, sub, out);
+    else
+      g_bruss_kernel<<<grid_of(N / 2), 256, 0, st>>>(x, N / 2, g->a, g->b, scale, sub, out);
+    return cudaGetLastError() == cudaSuccess ? PHIKS_OK : fail(PHIKS_ERR_CUDA, "nonlinear term launch");
+  }
+
+  phiks_status combo(double* out, std::initializer_list<std::pair<double, const double*>> terms) {
+    Terms t;
+    t.k = 0;
+    for (auto& p : terms) {
+      if (t.k == kMaxTerms) return fail(PHIKS_ERR_INVALID, "too many terms");
+      t.c[t.k] = p.first;
+      t.x[t.k++] = p.second;
+    }
+    phiks::count_launch();
+    combo_kernel<<<grid_of(N), 256, 0, st>>>(t, N, out);
+    return cudaGetLastError() == cudaSuccess ? PHIKS_OK : fail(PHIKS_ERR_CUDA, "combination launch");
+  }
 };
+
+#define TRYE(x)                          \
+  do {                                   \
+    phiks_status s_ = (x);               \
+    if (s_ != PHIKS_OK) return s_;       \
+  } while (0)
+
+// Buffers: g0 = tau g_n, then per scheme (each N doubles, from B[k]).
+struct Bufs {
+  double* B[24];
+};
+
+// exponential Euler: u <- LC(tau, 1, [u, tau g_n], 1)
+phiks_status step_expeuler(Engine& E, Bufs& W, double t, double tau, double* u) {
+  double* tg = W.B[0];
+  TRYE(E.eval_g(t, u, tau, nullptr, tg));
+  const double* v[2] = {u, tg};
+  TRYE(E.lc(tau, 1, v, 1, W.B[1]));
+  return E.combo(u, {{1.0, W.B[1]}});
+}
+
+// ETD2RK: u_2 = LC(tau, 1, [u, tau g_n]); u <- LC(tau, 2, [u, tau g_n, tau d_2])
+phiks_status step_etd2rk(Engine& E, Bufs& W, double t, double tau, double* u) {
+  double *tg = W.B[0], *u2 = W.B[1], *td2 = W.B[2], *o = W.B[3];
+  TRYE(E.eval_g(t, u, tau, nullptr, tg));
+  const double* v1[2] = {u, tg};
+  TRYE(E.lc(tau, 1, v1, 1, u2));
+  TRYE(E.eval_g(t + tau, u2, tau, tg, td2));  // tau (g(t + tau, u_2) - g_n)
+  const double* v2[3] = {u, tg, td2};
+  TRYE(E.lc(tau, 2, v2, 1, o));
+  return E.combo(u, {{1.0, o}});
+}
+
+// expRK3 (eq. expRK3s3, c_2 = 1/4, c_3 = 1/2, gamma = -4/5):
+//   E = LC(tau, 1, [u, tau g_n], 3): E[s] = exp(tau K/2^s) u + 2^-s tau phi_1(.) g_n
+//   u_2 = E[2];  P = LC(tau, 2, [0, 0, tau d_2], 3): P[s] = 4^-s phi_2(tau K/2^s) tau d_2
+//   u_3 = E[1] + tau gamma c_2 phi_2(tau K/4) d_2 + tau (c_3^2/c_2) phi_2(tau K/2) d_2
+//       = E[1] + 16 gamma c_2 P[2] + 4 (c_3^2/c_2) P[1]
+//   u_{n+1} = E[0] + tau phi_2(tau K) (gamma d_2 + d_3) / (gamma c_2 + c_3)
+phiks_status step_exprk3(Engine& E, Bufs& W, double t, double tau, double* u) {
+  const double c2 = 0.25, c3 = 0.5, gam = (3 * c3 - 2) * c3 / ((2 - 3 * c2) * c2), den = gam * c2 + c3;
+  const int64_t N = E.N;
+  double *tg = W.B[0], *Ev = W.B[1] /* 3 N */, *td2 = W.B[4], *P = W.B[5] /* 3 N */, *u3 = W.B[8],
+         *td3 = W.B[9], *w = W.B[10], *o = W.B[11];
+  TRYE(E.eval_g(t, u, tau, nullptr, tg));
+  const double* v1[2] = {u, tg};
+  TRYE(E.lc(tau, 1, v1, 3, Ev));
+  TRYE(E.eval_g(t + c2 * tau, Ev + 2 * N, tau, tg, td2));
+  const double* v2[3] = {nullptr, nullptr, td2};
+  TRYE(E.lc(tau, 2, v2, 3, P));
+  TRYE(E.combo(u3, {{1.0, Ev + N}, {16.0 * gam * c2, P + 2 * N}, {4.0 * c3 * c3 / c2, P + N}}));
+  TRYE(E.eval_g(t + c3 * tau, u3, tau, tg, td3));
+  TRYE(E.combo(w, {{gam / den, td2}, {1.0 / den, td3}}));
+  const double* v3[3] = {nullptr, nullptr, w};
+  TRYE(E.lc(tau, 2, v3, 1, o));
+  return E.combo(u, {{1.0, Ev}, {1.0, o}});
+}
+
+// expRK4s5 (eq. expRK4s5, c = 1/2, 1/2, 1, 1/2) assembled as eq. (expRK4s5_smart):
+//   E  = LC(tau, 1, [u, tau g_n], 2);  u_2 = E[1]
+//   L2 = LC(tau, 2, [0, 0, tau d_2], 2), L3 likewise with d_3: Lk[s] = 4^-s phi_2(tau K/2^s) tau d_k
+//   u_3 = E[1] + 4 L2[1];   u_4 = E[0] + L2[0] + L3[0]
+//   L4 = LC(tau, 3, [0, 0, tau d_4, 4 tau (d_2 + d_3 - d_4)], 2)
+//   u_5 = E[1] + 2 (L2[1] + L3[1]) - L4[1] + (L2[0] + L3[0] - L4[0]) / 4
+//   u_{n+1} = E[0] + LC(tau, 3, [0, 0, tau (4 d_5 - d_4), tau (4 d_4 - 8 d_5)], 1)
+// (u_5 from a_52 = a_53 = phi_{2,5}/2 - phi_{3,4} + phi_{2,4}/4 - phi_{3,5}/2 and
+// a_54 = phi_{2,5}/4 - a_52 regrouped over d_2 + d_3 - d_4 and d_4.)
+phiks_status step_exprk4s5(Engine& E, Bufs& W, double t, double tau, double* u) {
+  const int64_t N = E.N;
+  double *tg = W.B[0], *Ev = W.B[1] /* 2 N */, *td2 = W.B[3], *L2 = W.B[4] /* 2 N */, *x = W.B[6],
+         *td3 = W.B[7], *L3 = W.B[8] /* 2 N */, *td4 = W.B[10], *q = W.B[11], *L4 = W.B[12] /* 2 N */,
+         *td5 = W.B[14], *r2 = W.B[15], *r3 = W.B[16], *o = W.B[17];
+  TRYE(E.eval_g(t, u, tau, nullptr, tg));
+  const double* v1[2] = {u, tg};
+  TRYE(E.lc(tau, 1, v1, 2, Ev));
+  TRYE(E.eval_g(t + 0.5 * tau, Ev + N, tau, tg, td2));
+  const double* v2[3] = {nullptr, nullptr, td2};
+  TRYE(E.lc(tau, 2, v2, 2, L2));
+  TRYE(E.combo(x, {{1.0, Ev + N}, {4.0, L2 + N}}));  // u_3
+  TRYE(E.eval_g(t + 0.5 * tau, x, tau, tg, td3));
+  const double* v3[3] = {nullptr, nullptr, td3};
+  TRYE(E.lc(tau, 2, v3, 2, L3));
+  TRYE(E.combo(x, {{1.0, Ev}, {1.0, L2}, {1.0, L3}}));  // u_4
+  TRYE(E.eval_g(t + tau, x, tau, tg, td4));
+  TRYE(E.combo(q, {{4.0, td2}, {4.0, td3}, {-4.0, td4}}));
+  const double* v4[4] = {nullptr, nullptr, td4, q};
+  TRYE(E.lc(tau, 3, v4, 2, L4));
+  TRYE(E.combo(x, {{1.0, Ev + N},
+                   {2.0, L2 + N},
+                   {2.0, L3 + N},
+                   {-1.0, L4 + N},
+                   {0.25, L2},
+                   {0.25, L3},
+                   {-0.25, L4}}));  // u_5
+  TRYE(E.eval_g(t + 0.5 * tau, x, tau, tg, td5));
+  TRYE(E.combo(r2, {{4.0, td5}, {-1.0, td4}}));
+  TRYE(E.combo(r3, {{4.0, td4}, {-8.0, td5}}));
+  const double* v5[4] = {nullptr, nullptr, r2, r3};
+  TRYE(E.lc(tau, 3, v5, 1, o));
+  return E.combo(u, {{1.0, Ev}, {1.0, o}});
+}
+
+// expRK4s6 (eq. expRK4s6, c_2 = c_3 = 1/3, c_4 = 2/3, c_5 = 1/2, c_6 = 1):
+//   u_2 = LC(c_2 tau, 1, [u, c_2 tau g_n], 1)
+//   [u_4, u_3] = LC(c_4 tau, 2, [u, c_4 tau g_n, (c_4^2/c_2) tau d_2], 2)     (c_3 = c_4 / 2)
+//   [u_6, u_5] = LC(tau, 3, [u, tau g_n, tau (al3 d_3 + al4 d_4), tau (be3 d_3 + be4 d_4)], 2)
+//                with a_i3 = al3 c_i^2 phi_{2,i} + be3 c_i^3 phi_{3,i}, a_i4 likewise (c_6 = 1)
+//   u_{n+1} = LC(tau, 3, [u, tau g_n, tau (b52 d_5 + b62 d_6), tau (b53 d_5 + b63 d_6)], 1)
+phiks_status step_exprk4s6(Engine& E, Bufs& W, double t, double tau, double* u) {
+  const double c2 = 1.0 / 3, c3 = 1.0 / 3, c4 = 2.0 / 3, c5 = 0.5;
+  const double c6 = (4 * c5 - 3) / (6 * c5 - 4);
+  const double al3 = c4 / (c3 * (c4 - c3)), be3 = 2.0 / (c3 * (c3 - c4));
+  const double al4 = c3 / (c4 * (c3 - c4)), be4 = 2.0 / (c4 * (c4 - c3));
+  const double b52 = c6 / (c5 * (c6 - c5)), b53 = 2.0 / (c5 * (c5 - c6));
+  const double b62 = c5 / (c6 * (c5 - c6)), b63 = 2.0 / (c6 * (c6 - c5));
+  const int64_t N = E.N;
+  double *tg = W.B[0], *sg = W.B[1], *u2 = W.B[2], *td2 = W.B[3], *s2 = W.B[4], *U34 = W.B[5] /* 2 N */,
+         *td3 = W.B[7], *td4 = W.B[8], *w2 = W.B[9], *w3 = W.B[10], *U56 = W.B[11] /* 2 N */,
+         *td5 = W.B[13], *td6 = W.B[14];
+  TRYE(E.eval_g(t, u, tau, nullptr, tg));
+  TRYE(E.combo(sg, {{c2, tg}}));
+  const double* v1[2] = {u, sg};
+  TRYE(E.lc(c2 * tau, 1, v1, 1, u2));
+  TRYE(E.eval_g(t + c2 * tau, u2, tau, tg, td2));
+  TRYE(E.combo(sg, {{c4, tg}}));
+  TRYE(E.combo(s2, {{c4 * c4 / c2, td2}}));
+  const double* v2[3] = {u, sg, s2};
+  TRYE(E.lc(c4 * tau, 2, v2, 2, U34));  // U34[0] = u_4, U34[1] = u_3
+  TRYE(E.eval_g(t + c3 * tau, U34 + N, tau, tg, td3));
+  TRYE(E.eval_g(t + c4 * tau, U34, tau, tg, td4));
+  TRYE(E.combo(w2, {{al3, td3}, {al4, td4}}));
+  TRYE(E.combo(w3, {{be3, td3}, {be4, td4}}));
+  const double* v3[4] = {u, tg, w2, w3};
+  TRYE(E.lc(c6 * tau, 3, v3, 2, U56));  // U56[0] = u_6, U56[1] = u_5
+  TRYE(E.eval_g(t + c5 * tau, U56 + N, tau, tg, td5));
+  TRYE(E.eval_g(t + c6 * tau, U56, tau, tg, td6));
+  TRYE(E.combo(w2, {{b52, td5}, {b62, td6}}));
+  TRYE(E.combo(w3, {{b53, td5}, {b63, td6}}));
+  const double* v4[4] = {u, tg, w2, w3};
+  TRYE(E.lc(tau, 3, v4, 1, W.B[15]));
+  return E.combo(u, {{1.0, W.B[15]}});
+}
 
 }  // namespace
 
-extern "C" phiks_status phiks_integrate(phiks_plan_t plan, const int64_t* n, int d, int scheme,
-                                        const phiks_nonlinear* g, double t0, double T, int steps,
-                                        double* u, void* stream) {
+extern "C" phiks_status phiks_integrate_blocks(int nblocks, const phiks_plan_t* plans, int scheme,
+                                               const phiks_nonlinear* g, double t0, double T, int steps,
+                                               double* w, const phiks_options* opt, void* stream) {
   phiks::set_error_message("");
-  auto fail = [](phiks_status s, const char* m) {
-    phiks::set_error_message((std::string("phiks_integrate: ") + m).c_str());
+  auto fail = [](phiks_status s, const std::string& m) {
+    phiks::set_error_message(("phiks_integrate: " + m).c_str());
     return s;
   };
-  if (!plan || !n || !g || !u || steps < 1 || !(T > 0) || d < 1 || d > PHIKS_MAX_D)
+  if (nblocks < 1 || nblocks > 8 || !plans || !g || !w || steps < 1 || !(T > 0) || !std::isfinite(t0))
     return fail(PHIKS_ERR_INVALID, "bad arguments");
-  if (scheme != PHIKS_EXP_EULER && scheme != PHIKS_ETD2RK) return fail(PHIKS_ERR_INVALID, "scheme");
-  if (g->kind == PHIKS_NL_ADR_EXACT && d != 3) return fail(PHIKS_ERR_INVALID, "ADR needs d = 3");
-  if (g->kind != PHIKS_NL_ADR_EXACT && g->kind != PHIKS_NL_ALLEN_CAHN)
-    return fail(PHIKS_ERR_INVALID, "nonlinearity kind");
-  int64_t N = 1;
-  for (int mu = 0; mu < d; ++mu) N *= n[mu];
-  cudaStream_t st = (cudaStream_t)stream;
-  double* buf = nullptr;
-  if (cudaMallocAsync((void**)&buf, 4 * (size_t)N * sizeof(double), st) != cudaSuccess)
-    return fail(PHIKS_ERR_OOM, "workspace");
-  double *g1 = buf, *g2 = buf + N, *u2 = buf + 2 * N, *un = buf + 3 * N;
+  if (scheme < PHIKS_EXP_EULER || scheme > PHIKS_EXPRK4S6) return fail(PHIKS_ERR_INVALID, "scheme");
+  Engine E;
+  E.nb = nblocks;
+  E.g = g;
+  E.st = (cudaStream_t)stream;
+  if (opt) E.base = *opt;
+  else phiks_options_init(&E.base);
+  for (int b = 0; b < nblocks; ++b) {
+    if (!plans[b]) return fail(PHIKS_ERR_INVALID, "NULL plan");
+    int d = 0;
+    int64_t n[PHIKS_MAX_D];
+    phiks_status r = phiks_plan_shape(plans[b], &d, n);
+    if (r != PHIKS_OK) return fail(r, "plan shape");
+    int64_t Nb = 1;
+    for (int mu = 0; mu < d; ++mu) Nb *= n[mu];
+    E.plan[b] = plans[b];
+    E.off[b] = E.N;
+    E.size[b] = Nb;
+    E.N += Nb;
+    E.Nmax = std::max(E.Nmax, Nb);
+    if (b == 0) {
+      E.gd = d;
+      for (int mu = 0; mu < d; ++mu) E.gn[mu] = n[mu];
+    }
+  }
+  switch (g->kind) {
+    case PHIKS_NL_ADR_EXACT:
+      if (nblocks != 1 || E.gd != 3) return fail(PHIKS_ERR_INVALID, "ADR needs one block with d = 3");
+      break;
+    case PHIKS_NL_ALLEN_CAHN:
+      if (nblocks != 1) return fail(PHIKS_ERR_INVALID, "Allen-Cahn needs one block");
+      break;
+    case PHIKS_NL_BRUSSELATOR:
+      if (nblocks != 2 || E.size[0] != E.size[1])
+        return fail(PHIKS_ERR_INVALID, "Brusselator needs two blocks of equal size");
+      break;
+    default:
+      return fail(PHIKS_ERR_INVALID, "nonlinearity kind");
+  }
+  Bufs W;
+  const size_t nbuf = 24;
+  if (cudaMallocAsync((void**)&E.pool, (nbuf * E.N + 3 * E.Nmax) * sizeof(double), E.st) != cudaSuccess)
+    return fail(PHIKS_ERR_OOM, "scratch");
+  for (size_t k = 0; k < nbuf; ++k) W.B[k] = E.pool + k * E.N;
+  E.scratch = E.pool + nbuf * E.N;
   const double tau = T / steps;
   phiks_status res = PHIKS_OK;
-  auto eval_g = [&](const double* x, double t, double* out) -> bool {
-    phiks::count_launch();
-    if (g->kind == PHIKS_NL_ADR_EXACT)
-      g_adr_kernel<<<grid_of(N), 256, 0, st>>>(x, t, (int)n[0], (int)n[1], (int)n[2], g->eps,
-                                               g->alpha, tau, out);
-    else
-      g_ac_kernel<<<grid_of(N), 256, 0, st>>>(x, N, g->eps, tau, out);
-    return cudaGetLastError() == cudaSuccess;
-  };
-  double t = t0;
   for (int k = 0; k < steps && res == PHIKS_OK; ++k) {
-    if (!eval_g(u, t, g1)) {
-      res = fail(PHIKS_ERR_CUDA, "nonlinear term launch");
-      break;
+    const double t = t0 + k * tau;
+    switch (scheme) {
+      case PHIKS_EXP_EULER: res = step_expeuler(E, W, t, tau, w); break;
+      case PHIKS_ETD2RK: res = step_etd2rk(E, W, t, tau, w); break;
+      case PHIKS_EXPRK3: res = step_exprk3(E, W, t, tau, w); break;
+      case PHIKS_EXPRK4S5: res = step_exprk4s5(E, W, t, tau, w); break;
+      default: res = step_exprk4s6(E, W, t, tau, w); break;
     }
-    if (scheme == PHIKS_EXP_EULER) {
-      const void* v[2] = {u, g1};
-      res = phiks_apply(plan, tau, 1, v, 2, un, stream);
-    } else {
-      const void* v1[2] = {u, g1};
-      res = phiks_apply(plan, tau, 1, v1, 2, u2, stream);
-      if (res != PHIKS_OK) break;
-      if (!eval_g(u2, t + tau, g2)) {
-        res = fail(PHIKS_ERR_CUDA, "nonlinear term launch");
-        break;
-      }
-      phiks::count_launch();
-      axpby_kernel<<<grid_of(N), 256, 0, st>>>(g2, g1, 1.0, -1.0, N, g2);
-      const void* v2[3] = {u, g1, g2};
-      res = phiks_apply(plan, tau, 2, v2, 3, un, stream);
-    }
-    if (res != PHIKS_OK) break;
-    if (cudaMemcpyAsync(u, un, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-      res = fail(PHIKS_ERR_CUDA, "copy");
-    t = t0 + (k + 1) * tau;
   }
-  cudaFreeAsync(buf, st);
-  return res;
+  cudaFreeAsync(E.pool, E.st);
+  if (res != PHIKS_OK) return fail(res, E.err);
+  return PHIKS_OK;
+}
+
+extern "C" phiks_status phiks_integrate(phiks_plan_t plan, const int64_t* n, int d, int scheme,
+                                        const phiks_nonlinear* g, double t0, double T, int steps, double* u,
+                                        void* stream) {
+  if (!plan || !n) {
+    phiks::set_error_message("phiks_integrate: bad arguments");
+    return PHIKS_ERR_INVALID;
+  }
+  int pd = 0;
+  int64_t pn[PHIKS_MAX_D];
+  phiks_status r = phiks_plan_shape(plan, &pd, pn);
+  if (r != PHIKS_OK) return r;
+  bool same = pd == d;
+  for (int mu = 0; same && mu < d; ++mu) same = pn[mu] == n[mu];
+  if (!same) {
+    phiks::set_error_message("phiks_integrate: n and d do not match the plan");
+    return PHIKS_ERR_INVALID;
+  }
+  return phiks_integrate_blocks(1, &plan, scheme, g, t0, T, steps, u, nullptr, stream);
 }

@@ -1228,6 +1228,13 @@ phiks_status phiks_choose_params(int d, const int64_t* n, const double* const* A
   return PHIKS_OK;
 }
 
+phiks_status phiks_plan_shape(phiks_plan_t P, int* d, int64_t* n) {
+  if (!P || !d || !n) return fail(PHIKS_ERR_INVALID, "NULL argument");
+  *d = P->d;
+  for (int mu = 0; mu < P->d; ++mu) n[mu] = P->n[mu];
+  return PHIKS_OK;
+}
+
 phiks_status phiks_last_params(phiks_plan_t P, int* s, int* q, int* tcount, int* tuckers) {
   if (!P) return fail(PHIKS_ERR_INVALID, "NULL plan");
   if (s) *s = P->last_s;

@@ -112,3 +112,91 @@ def test_gpu_integrator_matches_paper_and_oracle(scheme, steps):
     orc = it.integrate(A, N, EPS, ALPHA, T, steps, scheme)
     assert float(np.abs(got - orc).max() / np.abs(orc).max()) < 1e-12
     plan.close()
+
+
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2210_07667_gb300 as pk
+    pk.load(build_if_missing=True)
+    return torch, pk
+
+
+@pytest.mark.gpu
+def test_gpu_ac_exprk3_matches_paper_and_oracle(ac_problem):
+    """Sec. 4.3 on the device: expRK3 at 100 steps gives the printed error
+    against the oracle's expRK4s6 reference, and the oracle's expRK3 state."""
+    torch, pk = _gpu()
+    A, u0, g, ref = ac_problem
+    plan = pk.Plan(A)
+    u = torch.from_numpy(u0.copy()).cuda()
+    pk.phiks_integrate_blocks([plan], pk.PHIKS_EXPRK3, pk.PHIKS_NL_ALLEN_CAHN, 0.0, AC["T"], 100, u,
+                              eps=AC["eps"])
+    torch.cuda.synchronize()
+    got = u.cpu().numpy()
+    err = it.rel_inf(got, ref)
+    assert abs(err - AC["exprk3"]["100"]) <= 1e-4 * AC["exprk3"]["100"], err
+    orc = it.integrate_problem([A], g, u0, 0.0, AC["T"], 100, "exprk3")
+    assert it.rel_inf(got, orc) < 1e-12
+    plan.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("scheme,steps", [("exprk4s6", 40), ("exprk4s5", 30), ("etd2rk", 40),
+                                          ("expeuler", 40)])
+def test_gpu_ac_schemes_match_oracle(ac_problem, scheme, steps):
+    torch, pk = _gpu()
+    A, u0, g, _ = ac_problem
+    plan = pk.Plan(A)
+    u = torch.from_numpy(u0.copy()).cuda()
+    pk.phiks_integrate_blocks([plan], pk.SCHEMES[scheme], pk.PHIKS_NL_ALLEN_CAHN, 0.0, AC["T"], steps, u,
+                              eps=AC["eps"])
+    torch.cuda.synchronize()
+    orc = it.integrate_problem([A], g, u0, 0.0, AC["T"], steps, scheme)
+    assert it.rel_inf(u.cpu().numpy(), orc) < 1e-12
+    plan.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("scheme", ["exprk4s5", "exprk4s6", "exprk3"])
+@pytest.mark.parametrize("dtype_name", ["fp64", "fp64emu"])
+def test_gpu_brusselator_block_diagonal(scheme, dtype_name):
+    """Block-diagonal K = diag(K_1, K_2) (Sec. 4.4, eq. ODE2) on an 8^3 grid,
+    two plans, 10 steps to T = 1, against the oracle."""
+    torch, pk = _gpu()
+    blocks, w0 = wk.brusselator3d(8)
+    dt = pk.DTYPES[dtype_name]
+    plans = [pk.Plan(blocks[0], dt), pk.Plan(blocks[1], dt)]
+    w = torch.from_numpy(w0.copy()).cuda()
+    pk.phiks_integrate_blocks(plans, pk.SCHEMES[scheme], pk.PHIKS_NL_BRUSSELATOR, 0.0, 1.0, 10, w,
+                              a=1.0, b=3.0)
+    torch.cuda.synchronize()
+    for p in plans:
+        pk.phiks_device_status(p.handle)
+    orc = it.integrate_problem(blocks, it.bruss_g(1.0, 3.0), w0, 0.0, 1.0, 10, scheme)
+    err = it.rel_inf(w.cpu().numpy(), orc)
+    print(scheme, dtype_name, "%.2e" % err)
+    assert err < 1e-12
+    for p in plans:
+        p.close()
+
+
+@pytest.mark.gpu
+def test_gpu_integrator_graph_replay_same_result(ac_problem):
+    """phiks_options.graph inside the integrator: every stage call replays a
+    captured graph from the second step on; the state equals plain calls'."""
+    torch, pk = _gpu()
+    A, u0, _, _ = ac_problem
+    plan = pk.Plan(A)
+    st = torch.cuda.Stream()
+    outs = []
+    for graph in (0, 1):
+        u = torch.from_numpy(u0.copy()).cuda()
+        torch.cuda.synchronize()
+        pk.phiks_integrate_blocks([plan], pk.PHIKS_EXPRK4S6, pk.PHIKS_NL_ALLEN_CAHN, 0.0, AC["T"], 12, u,
+                                  eps=AC["eps"], stream=st, graph=graph)
+        torch.cuda.synchronize()
+        outs.append(u.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    plan.close()
