@@ -15,7 +15,8 @@
  *
  * Layout (Lemma 1 of Sec. 2): a vector of length N = n_1 * ... * n_d is the
  * column-major vec of an n_1 x ... x n_d tensor (mode 1 fastest).  Matrices
- * A_mu are n_mu x n_mu, column-major, real.
+ * A_mu are n_mu x n_mu, column-major, real (complex for PHIKS_C128 plans:
+ * interleaved real and imaginary parts, as are those plans' vectors).
  *
  * Conventions for every entry point:
  *   - pointers named "host" are CPU memory, all other buffers are device
@@ -65,10 +66,15 @@ typedef enum {
  * FP64_EMU: vectors double, products on the tensor cores as exact sums of
  * bf16 digit products (seven base-256 digits per operand, FP32 accumulation
  * that stays exact for n_mu <= 128), rounded once to FP64; needs every n_mu a
- * multiple of 8 and at most 128.  Small exponentials, their squaring and the
- * doubling-formula combination stay FP64 in every type. */
+ * multiple of 8 and at most 128.  C128: complex A_mu and vectors (the
+ * validation operator of Sec. 4.1), complex FP64 products on the FP64 pipe;
+ * vectors are N complex numbers stored as 2 N doubles (real, imaginary).
+ * Small exponentials, their squaring and the doubling-formula combination
+ * stay FP64 in every type (complex plans hold each small matrix as its real
+ * representation [[Re, -Im], [Im, Re]]). */
 typedef enum {
-  PHIKS_FP64 = 0, PHIKS_TF32 = 1, PHIKS_TF32X3 = 2, PHIKS_BF16X3 = 3, PHIKS_FP64_EMU = 4
+  PHIKS_FP64 = 0, PHIKS_TF32 = 1, PHIKS_TF32X3 = 2, PHIKS_BF16X3 = 3, PHIKS_FP64_EMU = 4,
+  PHIKS_C128 = 5
 } phiks_dtype;
 
 /* Quadrature rule for the phi integral (Sec. 3.3): Gauss-Lobatto-Legendre
@@ -109,11 +115,14 @@ void phiks_options_init(phiks_options* opt);
 /* Build a plan for K = A_d (+) ... (+) A_1 (Sec. 1, eq. kronsum).
  *   d        tensor order, 1 <= d <= PHIKS_MAX_D
  *   n        host, d entries, n_mu >= 1
- *   A        host, d pointers to column-major n_mu x n_mu doubles (copied)
+ *   A        host, d pointers to column-major n_mu x n_mu doubles (copied);
+ *            PHIKS_C128: 2 n_mu^2 doubles, entry (i, j) at 2 (i + n_mu j)
+ *            (real part) and 2 (i + n_mu j) + 1 (imaginary part)
  *   dtype    arithmetic of the mu-mode products (phiks_dtype)
  *   out      receives the plan; NULL on failure
- * Computes on the host the shifts sigma_mu = tr(A_mu)/n_mu (Remark of Sec. 3.1)
- * and the numerical-range rectangles Xi_mu (Sec. 3.3), and uploads A_mu. */
+ * Computes on the host the shifts sigma_mu = tr(A_mu)/n_mu (Remark of Sec. 3.1;
+ * the real part for complex A_mu) and the numerical-range rectangles Xi_mu
+ * (Sec. 3.3), and uploads A_mu. */
 phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dtype,
                         phiks_plan_t* out);
 
@@ -165,7 +174,9 @@ phiks_status phiks_last_params(phiks_plan_t plan, int* s, int* q, int* tcount, i
 /* Tucker operator W = V x_1 L_1 x_2 ... x_d L_d (Sec. 2) in the plan's dtype.
  *   V, W     device, N elements each (may not alias)
  *   L        host array of d device pointers to column-major n_mu x n_mu
- *            doubles (converted on the fly for the split dtypes) */
+ *            doubles (converted on the fly for the split dtypes); PHIKS_C128
+ *            plans: the 2 n_mu x 2 n_mu real representation
+ *            [[Re L, -Im L], [Im L, Re L]] of the complex L_mu */
 phiks_status phiks_tucker(phiks_plan_t plan, const void* V, void* W, const double* const* L,
                           void* stream);
 
@@ -321,7 +332,7 @@ phiks_status phiks_plan_shape(phiks_plan_t plan, int* d, int64_t* n);
  * `scheme` for w' = K w + g(t, w) with K = diag(K_1, ..., K_nblocks)
  * block diagonal (eq. ODE2): block b is plans[b]'s Kronecker sum, acting on
  * the N_b entries of w after those of blocks 0..b-1 (column-major each).
- * plans: FP64 or FP64_EMU.  opt (may be NULL): tol and graph apply to every
+ * plans: FP64 or FP64_EMU (real).  opt (may be NULL): tol and graph apply to every
  * phiks call; nscales, skip_phi0, vnorms and workspace are set internally.
  * Device scratch of about 24 N doubles comes from the stream-ordered
  * allocator.  Each phiks call synchronises `stream` once (the norms). */

@@ -96,3 +96,51 @@ def lincomb(A, tau, vs, c: float = 1.0):
             continue
         acc = acc + np.longdouble(c) ** l * phi_actions(A, tau, v, [l], c)[l]
     return acc
+
+
+def scaled_phi_actions(zeta: complex, T: Sequence[np.ndarray], tau: float, v: np.ndarray,
+                       ells: Sequence[int], c: float = 1.0):
+    """{l: phi_l(c tau K) v} for K = zeta (T_d (+) ... (+) T_1), every T_mu real
+    symmetric tridiagonal Toeplitz (sub = super): with the orthonormal sine
+    eigenvectors S_mu and eigenvalues lambda_mu, phi_l(c tau K) v =
+    (x_mu S_mu) [phi_l(c tau zeta sum_mu lambda) o (x_mu S_mu^T) v].  The bases
+    are orthogonal, so complex128 arithmetic keeps the result at double
+    precision (the complex validation operator (1+i)/100 Laplacian of Sec. 4.1)."""
+    n = [t.shape[0] for t in T]
+    fac = []
+    for t in T:
+        a, b, cc = toeplitz_coeffs(t)
+        if a != cc:
+            raise ValueError("symmetric Toeplitz only")
+        m = t.shape[0]
+        k = np.arange(1, m + 1)
+        S = np.sqrt(2.0 / (m + 1)) * np.sin(np.outer(k, k) * np.pi / (m + 1))
+        lam = b + 2 * a * np.cos(k * np.pi / (m + 1))
+        fac.append((lam, S))
+    V = np.reshape(np.asarray(v, dtype=np.complex128), tuple(n), order="F")
+    for mu, (lam, S) in enumerate(fac):
+        V = _mode(V, S.T, mu)
+    Z = np.zeros(tuple(n))
+    for mu, (lam, S) in enumerate(fac):
+        shape = [1] * len(n)
+        shape[mu] = n[mu]
+        Z = Z + np.reshape(lam, shape)
+    Z = complex(c) * tau * complex(zeta) * Z
+    out = {}
+    for l in ells:
+        W = phi(l, Z) * V
+        for mu, (lam, S) in enumerate(fac):
+            W = _mode(W, S, mu)
+        out[l] = np.reshape(W, (-1,), order="F")
+    return out
+
+
+def scaled_lincomb(zeta: complex, T, tau, vs, c: float = 1.0):
+    """exp(c tau K) v_0 + sum_l c^l phi_l(c tau K) v_l for K as in scaled_phi_actions."""
+    N = int(np.prod([t.shape[0] for t in T]))
+    acc = np.zeros(N, dtype=np.complex128)
+    for l, v in enumerate(vs):
+        if v is None:
+            continue
+        acc = acc + c ** l * scaled_phi_actions(zeta, T, tau, v, [l], c)[l]
+    return acc

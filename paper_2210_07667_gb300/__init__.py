@@ -15,7 +15,8 @@ from typing import Optional, Sequence
 import numpy as np
 
 __all__ = [
-    "PHIKS_FP64", "PHIKS_TF32", "PHIKS_TF32X3", "PHIKS_BF16X3", "PHIKS_FP64_EMU", "PHIKS_RULE_GLL",
+    "PHIKS_FP64", "PHIKS_TF32", "PHIKS_TF32X3", "PHIKS_BF16X3", "PHIKS_FP64_EMU", "PHIKS_C128",
+    "PHIKS_RULE_GLL",
     "PHIKS_RULE_GL",
     "PhiksError", "Options", "lib", "library_path", "load",
     "phiks_plan", "phiks_apply", "phiks_apply_ex", "phiks_workspace_size",
@@ -26,10 +27,10 @@ __all__ = [
     "EXPORTED",
 ]
 
-PHIKS_FP64, PHIKS_TF32, PHIKS_TF32X3, PHIKS_BF16X3, PHIKS_FP64_EMU = 0, 1, 2, 3, 4
+PHIKS_FP64, PHIKS_TF32, PHIKS_TF32X3, PHIKS_BF16X3, PHIKS_FP64_EMU, PHIKS_C128 = 0, 1, 2, 3, 4, 5
 PHIKS_RULE_GLL, PHIKS_RULE_GL = 0, 1
 DTYPES = {"fp64": PHIKS_FP64, "tf32": PHIKS_TF32, "tf32x3": PHIKS_TF32X3, "bf16x3": PHIKS_BF16X3,
-          "fp64emu": PHIKS_FP64_EMU}
+          "fp64emu": PHIKS_FP64_EMU, "c128": PHIKS_C128}
 STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "UNSUPPORTED", 4: "NO_PARAMS", 5: "CUDA", 6: "TIMEOUT"}
 
 # every symbol include/phiks.h declares
@@ -236,7 +237,8 @@ def phiks_plan(A: Sequence[np.ndarray], dtype: int = PHIKS_FP64) -> int:
     """Plan for K = A_d (+) ... (+) A_1; A_mu host arrays (any order, copied
     to column-major doubles)."""
     d = len(A)
-    mats = [np.asfortranarray(np.asarray(a, dtype=np.float64)) for a in A]
+    edt = np.complex128 if int(dtype) == PHIKS_C128 else np.float64
+    mats = [np.asfortranarray(np.asarray(a, dtype=edt)) for a in A]
     n = (ctypes.c_int64 * d)(*[m.shape[0] for m in mats])
     ptrs = (ctypes.c_void_p * d)(*[m.ctypes.data for m in mats])
     out = ctypes.c_void_p()
@@ -276,7 +278,7 @@ def phiks_select_params(plan: int, tau: float, p: int, vnorms: Sequence[float], 
 
 
 def phiks_choose_params(A: Sequence[np.ndarray], tau: float, p: int, vnorms: Sequence[float], **kw):
-    """(s, q, T#) of Sec. 3.3 on the host, without a plan or a GPU."""
+    """(s, q, T#) of Sec. 3.3 on the host, without a plan or a GPU (real A)."""
     d = len(A)
     mats = [np.asfortranarray(np.asarray(a, dtype=np.float64)) for a in A]
     n = (ctypes.c_int64 * d)(*[m.shape[0] for m in mats])

@@ -337,6 +337,9 @@ extern "C" phiks_status phiks_integrate_blocks(int nblocks, const phiks_plan_t* 
   else phiks_options_init(&E.base);
   for (int b = 0; b < nblocks; ++b) {
     if (!plans[b]) return fail(PHIKS_ERR_INVALID, "NULL plan");
+    const int dt = phiks::plan_dtype(plans[b]);
+    if (dt != PHIKS_FP64 && dt != PHIKS_FP64_EMU)
+      return fail(PHIKS_ERR_UNSUPPORTED, "integrators take real FP64 or FP64_EMU plans");
     int d = 0;
     int64_t n[PHIKS_MAX_D];
     phiks_status r = phiks_plan_shape(plans[b], &d, n);

@@ -11,6 +11,8 @@ void set_error_message(const char* msg);
 
 // Process-wide count of kernels launched by this library.
 uint64_t kernel_launch_count();
+// dtype of a plan (phiks_dtype), -1 for NULL
+int plan_dtype(const void* plan);
 void count_launch(uint64_t k = 1);
 
 constexpr int kMaxSrc = 10;  // tensors one combination may read
@@ -98,6 +100,10 @@ struct ModeGeom {
 // W = V x_mu L (FP64).  V given by `pro` (a combination), L column-major
 // n x n.  With epi == nullptr or epi->nout == 0 the result goes to W.
 cudaError_t launch_mode_product_f64(const Combo& pro, const double* L, ModeGeom g, double* W,
+                                    const Epi* epi, cudaStream_t st);
+// The same for complex V, W (interleaved) and L given as its 2n x 2n real
+// representation (PHIKS_C128 plans).
+cudaError_t launch_mode_product_c128(const Combo& pro, const double* L, ModeGeom g, double* W,
                                     const Epi* epi, cudaStream_t st);
 
 // out[t][i] = sum_m a[t][m] src[m][i] over N elements (Epi with b ignored),

@@ -99,6 +99,12 @@ struct phiks_plan_s {
   int64_t n[PHIKS_MAX_D] = {0};
   int64_t N = 0;
   int dtype = PHIKS_FP64;
+  // complex plans (PHIKS_C128): vectors are N interleaved complex numbers (NR =
+  // 2 N doubles) and every small matrix is held as the 2n x 2n real
+  // representation [[Re, -Im], [Im, Re]] (m = 2 n); real plans: NR = N, m = n.
+  bool cplx = false;
+  int64_t NR = 0;
+  int64_t m[PHIKS_MAX_D] = {0};
   std::vector<std::vector<double>> A;
   double sigma[PHIKS_MAX_D] = {0};
   double norm1_shifted[PHIKS_MAX_D] = {0};
@@ -138,6 +144,10 @@ struct phiks_plan_s {
   double prof_flops = 0;
 };
 
+namespace phiks {
+int plan_dtype(const void* plan) { return plan ? ((const phiks_plan_s*)plan)->dtype : -1; }
+}  // namespace phiks
+
 namespace {
 
 struct DeviceGuard {
@@ -174,8 +184,11 @@ bool split_dtype(const phiks_plan_s* P) {
 }
 bool emu_dtype(const phiks_plan_s* P) { return P->dtype == PHIKS_FP64_EMU; }
 bool double_vectors(const phiks_plan_s* P) { return !split_dtype(P); }
+// the products run on the tensor cores (split dtypes and FP64_EMU)
+bool tc_path(const phiks_plan_s* P) { return split_dtype(P) || emu_dtype(P); }
 
-size_t elt_size(const phiks_plan_s* P) { return double_vectors(P) ? 8 : 4; }
+// bytes per vector element (a complex element is two doubles)
+size_t elt_size(const phiks_plan_s* P) { return P->cplx ? 16 : (double_vectors(P) ? 8 : 4); }
 
 // Workspace of one apply, everything an apply writes besides its outputs, so
 // that applies with distinct workspaces never share device state:
@@ -190,7 +203,7 @@ struct WsLayout {
 size_t up1k(size_t x) { return (x + 1023) / 1024 * 1024; }
 
 WsLayout ws_layout(const phiks_plan_s* P, int p) {
-  const size_t N = (size_t)P->N;
+  const size_t N = (size_t)P->NR;  // doubles per FP64 vector
   WsLayout w;
   size_t o = 0;
   w.acc = o;
@@ -202,7 +215,7 @@ WsLayout ws_layout(const phiks_plan_s* P, int p) {
   w.msq1 = o;
   o += up1k(P->sum_n2 * 8);
   w.tcb0 = w.tcb1 = w.planes = o;
-  if (P->dtype != PHIKS_FP64) {
+  if (tc_path(P)) {
     w.tcb0 = o;
     o += up1k(P->tcb_bytes);
     w.tcb1 = o;
@@ -455,7 +468,7 @@ phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool 
   for (int b = 0; b < nbk; ++b)
     for (int mu = 0; mu < P->d; ++mu) {
       nb.off[b][mu] = tot;
-      tot += (size_t)P->n[mu] * P->n[mu];
+      tot += (size_t)P->m[mu] * P->m[mu];
     }
   if (hit) {
     nb.dev = hit->dev;  // recompute in place (same layout: same q and rule)
@@ -481,7 +494,7 @@ phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool 
   for (int b = 0; b < nbk; ++b)
     for (int mu = 0; mu < P->d; ++mu) {
       ExpmJob j;
-      j.n = (int)P->n[mu];
+      j.n = (int)P->m[mu];
       j.Ashift = P->dAs + P->offA[mu];
       j.c = (1.0 - bank_theta[b]) * scale;
       j.norm1 = P->norm1_shifted[mu];
@@ -494,7 +507,7 @@ phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool 
     if (!hit) cudaFree(nb.dev);
     return stt;
   }
-  if (P->dtype != PHIKS_FP64) {  // B-operand planes of every small exponential
+  if (tc_path(P)) {  // B-operand planes of every small exponential
     nb.tcoff.assign(nbk, std::vector<size_t>(P->d));
     if (hit) nb.tcb = hit->tcb;
     else CK(cudaMalloc(&nb.tcb, (size_t)nbk * P->tcb_bytes));
@@ -531,12 +544,12 @@ void carve(Ctx& c, int p, char* ws, double** acc) {
   phiks_plan_s* P = c.P;
   uintptr_t base = ((uintptr_t)ws + 1023) & ~(uintptr_t)1023;
   WsLayout w = ws_layout(P, p);
-  for (int l = 0; l < std::max(p, 1); ++l) acc[l] = (double*)(base + w.acc) + (size_t)l * P->N;
+  for (int l = 0; l < std::max(p, 1); ++l) acc[l] = (double*)(base + w.acc) + (size_t)l * P->NR;
   c.tmp[0] = (double*)(base + w.tmp);
-  c.tmp[1] = c.tmp[0] + P->N;
+  c.tmp[1] = c.tmp[0] + P->NR;
   c.msq[0] = (double*)(base + w.msq0);
   c.msq[1] = (double*)(base + w.msq1);
-  if (P->dtype != PHIKS_FP64) {
+  if (tc_path(P)) {
     c.msq_tcb[0] = (uint8_t*)(base + w.tcb0);
     c.msq_tcb[1] = (uint8_t*)(base + w.tcb1);
     if (emu_dtype(P)) oz_bind_workspace(P->oz, (void*)(base + w.planes), c.tmp[0], c.tmp[1]);
@@ -599,7 +612,7 @@ phiks_status tucker(Ctx& c, const Combo& in, const Mats& M, const Epi* epi) {
     c.tuckers++;
     return PHIKS_OK;
   }
-  if (P->dtype != PHIKS_FP64) {
+  if (tc_path(P)) {
     cudaEvent_t e1;
     TRY(prof_begin(c, &e1));
     cudaError_t e = tc_tucker(P->tc, in, M.B, *epi, c.st);
@@ -618,8 +631,9 @@ phiks_status tucker(Ctx& c, const Combo& in, const Mats& M, const Epi* epi) {
     ModeGeom g{mode_a(P, mu), (int)P->n[mu], mode_b(P, mu)};
     cudaEvent_t e1;
     TRY(prof_begin(c, &e1));
-    CK(launch_mode_product_f64(cur, M.L[mu], g, out, last ? epi : nullptr, c.st));
-    TRY(prof_end(c, e1, 2.0 * (double)P->N * (double)P->n[mu]));
+    if (P->cplx) CK(launch_mode_product_c128(cur, M.L[mu], g, out, last ? epi : nullptr, c.st));
+    else CK(launch_mode_product_f64(cur, M.L[mu], g, out, last ? epi : nullptr, c.st));
+    TRY(prof_end(c, e1, (P->cplx ? 8.0 : 2.0) * (double)P->N * (double)P->n[mu]));
     cur = make_combo();
     cur.nsrc = 1;
     cur.src[0] = out;
@@ -652,20 +666,20 @@ phiks_status square_modes(Ctx& c, Mats& M, int& cur_buf) {
   gb.count = P->d;
   size_t off = 0;
   for (int mu = 0; mu < P->d; ++mu) {
-    gb.n[mu] = (int)P->n[mu];
+    gb.n[mu] = (int)P->m[mu];
     gb.A[mu] = M.L[mu];
     gb.B[mu] = M.L[mu];
     gb.C[mu] = c.msq[cur_buf] + off;
     gb.alpha[mu] = 1.0;
     gb.beta_I[mu] = 0.0;
-    off += (size_t)P->n[mu] * P->n[mu];
+    off += (size_t)P->m[mu] * P->m[mu];
   }
   CK(launch_gemm_batch_f64(gb, P->nmax, c.st));
   off = 0;
   for (int mu = 0; mu < P->d; ++mu) {
     M.L[mu] = c.msq[cur_buf] + off;
-    off += (size_t)P->n[mu] * P->n[mu];
-    if (P->dtype != PHIKS_FP64) {
+    off += (size_t)P->m[mu] * P->m[mu];
+    if (tc_path(P)) {
       uint8_t* dst = c.msq_tcb[cur_buf] + P->tcb_off[mu];
       if (emu_dtype(P)) CK(oz_prepare_b(M.L[mu], (int)P->n[mu], dst, c.st));
       else CK(tc_prepare_b(P->dtype, M.L[mu], (int)P->n[mu], dst, c.st));
@@ -682,7 +696,7 @@ phiks_status copy_elems(Ctx& c, void* dst, const void* src) {
 }
 
 phiks_status combine(Ctx& c, const Epi& e) {
-  CK(launch_combine(e, c.P->N, c.st));
+  CK(launch_combine(e, c.P->NR, c.st));
   return PHIKS_OK;
 }
 
@@ -709,7 +723,7 @@ phiks_status run_same(Ctx& c, const Bank* B, int s, int p, const void* v, const 
   const bool f32 = split_dtype(P);
   const int per = p + (o.skip_phi0 ? 0 : 1);
   const int q = (int)B->theta.size();
-  for (int l = 0; l < p; ++l) CK(cudaMemsetAsync(acc[l], 0, N * 8, c.st));
+  for (int l = 0; l < p; ++l) CK(cudaMemsetAsync(acc[l], 0, P->NR * 8, c.st));
   // quadrature at K/2^s: phi_l += w_i theta_i^(l-1)/(l-1)! exp((1-theta_i)K/2^s) v
   for (int i = 0; i < q && p > 0; ++i) {
     const double th = B->theta[i], w = B->w[i];
@@ -783,7 +797,7 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
   const size_t es = elt_size(P);
   const bool f32 = split_dtype(P);
   const int q = (int)B->theta.size();
-  for (int l = 0; l < p; ++l) CK(cudaMemsetAsync(acc[l], 0, N * 8, c.st));
+  for (int l = 0; l < p; ++l) CK(cudaMemsetAsync(acc[l], 0, P->NR * 8, c.st));
   for (int i = 0; i < q; ++i) {
     const double th = B->theta[i], w = B->w[i];
     for (int l = 1; l <= p; ++l) {
@@ -919,30 +933,51 @@ phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dty
   *out = nullptr;
   if (d < 1 || d > PHIKS_MAX_D) return fail(PHIKS_ERR_INVALID, "d = %d out of [1, %d]", d, PHIKS_MAX_D);
   if (!n || !A) return fail(PHIKS_ERR_INVALID, "n or A is NULL");
-  if (dtype < PHIKS_FP64 || dtype > PHIKS_FP64_EMU) return fail(PHIKS_ERR_INVALID, "dtype %d", dtype);
+  if (dtype < PHIKS_FP64 || dtype > PHIKS_C128) return fail(PHIKS_ERR_INVALID, "dtype %d", dtype);
   std::unique_ptr<phiks_plan_s> P(new phiks_plan_s);
   P->d = d;
   P->dtype = dtype;
+  P->cplx = dtype == PHIKS_C128;
   P->N = 1;
   for (int mu = 0; mu < d; ++mu) {
     if (n[mu] < 1 || n[mu] > 65536) return fail(PHIKS_ERR_INVALID, "n[%d] = %lld", mu, (long long)n[mu]);
     if (!A[mu]) return fail(PHIKS_ERR_INVALID, "A[%d] is NULL", mu);
     P->n[mu] = n[mu];
+    P->m[mu] = P->cplx ? 2 * n[mu] : n[mu];
     if (P->N > (int64_t(1) << 40) / n[mu]) return fail(PHIKS_ERR_INVALID, "N too large");
     P->N *= n[mu];
-    P->nmax = std::max<int>(P->nmax, (int)n[mu]);
+    P->nmax = std::max<int>(P->nmax, (int)P->m[mu]);
   }
+  P->NR = P->cplx ? 2 * P->N : P->N;
   CK(cudaGetDevice(&P->device));
   size_t tot = 0;
   for (int mu = 0; mu < d; ++mu) {
-    const int64_t m = n[mu];
-    std::vector<double> a(A[mu], A[mu] + m * m);
-    for (double x : a)
-      if (!std::isfinite(x)) return fail(PHIKS_ERR_INVALID, "A[%d] has a non-finite entry", mu);
+    const int64_t nn = n[mu], m = P->m[mu];
+    const int64_t nin = P->cplx ? 2 * nn * nn : nn * nn;  // doubles given
+    for (int64_t k = 0; k < nin; ++k)
+      if (!std::isfinite(A[mu][k])) return fail(PHIKS_ERR_INVALID, "A[%d] has a non-finite entry", mu);
+    std::vector<double> a(m * m);
     double tr = 0;
-    for (int64_t i = 0; i < m; ++i) tr += a[i + m * i];
-    P->sigma[mu] = tr / m;  // Remark of Sec. 3.1: sigma_mu = tr(A_mu)/n_mu
-    P->rect[mu] = numerical_range_rect(a.data(), m);
+    if (P->cplx) {
+      // real representation of the complex (interleaved, column-major) A_mu
+      for (int64_t j = 0; j < nn; ++j)
+        for (int64_t i = 0; i < nn; ++i) {
+          const double re = A[mu][2 * (i + nn * j)], im = A[mu][2 * (i + nn * j) + 1];
+          a[i + m * j] = re;
+          a[nn + i + m * j] = im;
+          a[i + m * (nn + j)] = -im;
+          a[nn + i + m * (nn + j)] = re;
+        }
+      for (int64_t i = 0; i < nn; ++i) tr += A[mu][2 * (i + nn * i)];
+      // shift by the real part of the mean eigenvalue: e^{c sigma} stays real
+      P->sigma[mu] = tr / nn;
+      P->rect[mu] = numerical_range_rect_complex(A[mu], nn);
+    } else {
+      std::copy(A[mu], A[mu] + m * m, a.begin());
+      for (int64_t i = 0; i < m; ++i) tr += a[i + m * i];
+      P->sigma[mu] = tr / m;  // Remark of Sec. 3.1: sigma_mu = tr(A_mu)/n_mu
+      P->rect[mu] = numerical_range_rect(a.data(), m);
+    }
     std::vector<double> sh(a);
     for (int64_t i = 0; i < m; ++i) sh[i + m * i] -= P->sigma[mu];
     P->norm1_shifted[mu] = norm1(sh.data(), m);
@@ -953,14 +988,14 @@ phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dty
   P->sum_n2 = tot;
   CK(cudaMalloc(&P->dAs, tot * 8));
   for (int mu = 0; mu < d; ++mu) {
-    const int64_t m = n[mu];
+    const int64_t m = P->m[mu];
     std::vector<double> sh(P->A[mu]);
     for (int64_t i = 0; i < m; ++i) sh[i + m * i] -= P->sigma[mu];
     CK(cudaMemcpy(P->dAs + P->offA[mu], sh.data(), m * m * 8, cudaMemcpyHostToDevice));
   }
   CK(cudaMalloc(&P->d_norms, (PHIKS_MAX_P + 1) * 8));
   CK(cudaMallocHost(&P->h_norms, (PHIKS_MAX_P + 1) * 8));
-  if (dtype != PHIKS_FP64) {
+  if (tc_path(P.get())) {
     if (dtype == PHIKS_FP64_EMU) {
       phiks_status st = oz_create(&P->oz, d, P->n, P->N);
       if (st != PHIKS_OK) return fail(st, "%s", oz_last_error());
@@ -1283,7 +1318,7 @@ phiks_status phiks_apply_ex(phiks_plan_t P, double tau, int p, const void* const
       }
     if (cnt) {
       CK(cudaMemsetAsync(P->d_norms, 0, cnt * 8, st));
-      CK(launch_sumsq(xs, cnt, N, split_dtype(P), P->d_norms, st));
+      CK(launch_sumsq(xs, cnt, P->NR, split_dtype(P), P->d_norms, st));
       CK(cudaMemcpyAsync(P->h_norms, P->d_norms, cnt * 8, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       for (int k = 0; k < cnt; ++k) norms[idx[k]] = std::sqrt(P->h_norms[k]);
@@ -1434,7 +1469,7 @@ phiks_status phiks_tucker(phiks_plan_t P, const void* V, void* W, const double* 
     M.L[mu] = L[mu];
     M.B[mu] = nullptr;
   }
-  if (P->dtype != PHIKS_FP64) {
+  if (tc_path(P)) {
     for (int mu = 0; mu < P->d; ++mu) {
       uint8_t* dst = P->tucker_tcb + P->tcb_off[mu];
       if (emu_dtype(P)) CK(oz_prepare_b(L[mu], (int)P->n[mu], dst, c.st));

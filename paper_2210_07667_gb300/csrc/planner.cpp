@@ -324,6 +324,29 @@ double norm1(const double* A, int64_t n) {
   return m;
 }
 
+Rect numerical_range_rect_complex(const double* A, int64_t n) {
+  const int64_t m = 2 * n;
+  std::vector<double> RH(m * m), RS(m * m);
+  auto re = [&](int64_t i, int64_t j) { return A[2 * (i + n * j)]; };
+  auto im = [&](int64_t i, int64_t j) { return A[2 * (i + n * j) + 1]; };
+  auto put = [&](std::vector<double>& R, int64_t i, int64_t j, double xr, double xi) {
+    R[i + m * j] = xr;
+    R[n + i + m * j] = xi;
+    R[i + m * (n + j)] = -xi;
+    R[n + i + m * (n + j)] = xr;
+  };
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < n; ++i) {
+      // H_ij = (A_ij + conj(A_ji)) / 2;  S_ij = (A_ij - conj(A_ji)) / (2i)
+      put(RH, i, j, 0.5 * (re(i, j) + re(j, i)), 0.5 * (im(i, j) - im(j, i)));
+      put(RS, i, j, 0.5 * (im(i, j) + im(j, i)), -0.5 * (re(i, j) - re(j, i)));
+    }
+  Rect r;
+  sym_extremes(RH, m, &r.xlo, &r.xhi);
+  sym_extremes(RS, m, &r.ylo, &r.yhi);
+  return r;
+}
+
 Rect numerical_range_rect(const double* A, int64_t n) {
   std::vector<double> H(n * n), S2(n * n);
   for (int64_t j = 0; j < n; ++j)

@@ -19,6 +19,13 @@ void quad_rule(int rule, int q, std::vector<double>& theta, std::vector<double>&
 // in [-||S||_2, ||S||_2], S = (A - A^T)/2.
 Rect numerical_range_rect(const double* A, int64_t n);
 
+// Rectangle enclosing the numerical range of a complex n x n A (interleaved
+// real and imaginary parts, column-major): real part in the eigenvalue range
+// of H = (A + A^*)/2, imaginary part in that of S = (A - A^*)/(2i), both
+// Hermitian, taken from their real representations [[Re, -Im], [Im, Re]]
+// (real symmetric, the same eigenvalues each twice).
+Rect numerical_range_rect_complex(const double* A, int64_t n);
+
 // ||A||_1 (max column sum), column-major.
 double norm1(const double* A, int64_t n);
 

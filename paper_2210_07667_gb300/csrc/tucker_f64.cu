@@ -156,6 +156,141 @@ __global__ void __launch_bounds__((TI / RI) * (TC / RC))
   }
 }
 
+// Complex variant (PHIKS_C128): elements of V and W are interleaved complex
+// numbers (element e at doubles 2e, 2e+1); L is the 2n x 2n real
+// representation [[Re, -Im], [Im, Re]] of the complex n x n L, so Re L(i, k)
+// = L[i + 2n k] and Im L(i, k) = L[n + i + 2n k].  The prologue combination
+// and the epilogue take real coefficients and act on both parts.
+template <int TI, int TC, int RI, int RC, int KC, bool XFAST>
+__global__ void __launch_bounds__((TI / RI) * (TC / RC))
+    mode_product_c128_kernel(Combo pro, const double* __restrict__ L, ModeGeom g, double* W, Epi epi) {
+  pdl_wait();
+  constexpr int TROWS = TI / RI, TCOLS = TC / RC, NT = TROWS * TCOLS;
+  constexpr int LPT = (TI * KC + NT - 1) / NT;
+  constexpr int VPT = (TC * KC + NT - 1) / NT;
+  __shared__ double2 sL[KC][TI + 1];
+  __shared__ double2 sV[KC][TC + 1];
+  const int tid = threadIdx.x;
+  const int tc = tid % TCOLS;
+  const int ti = tid / TCOLS;
+  const int i0 = blockIdx.y * TI;
+  const int64_t c0 = (int64_t)blockIdx.x * TC;
+  const int64_t ncols = g.a * g.b;
+  const int n = g.n;
+  const int64_t m = 2 * (int64_t)n;
+  const int64_t an = g.a * (int64_t)n;
+  const bool plain = (pro.nsrc == 1 && pro.coef[0] == 1.0);
+
+  double2 rl[LPT], rv[VPT];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int e = 0; e < LPT; ++e) {
+      const int idx = tid + e * NT;
+      const int ii = idx % TI, kk = idx / TI;
+      const int i = i0 + ii, k = k0 + kk;
+      double2 v = make_double2(0.0, 0.0);
+      if (idx < TI * KC && i < n && k < n) {
+        v.x = __ldg(L + i + m * k);
+        v.y = __ldg(L + n + i + m * k);
+      }
+      rl[e] = v;
+    }
+#pragma unroll
+    for (int e = 0; e < VPT; ++e) {
+      const int idx = tid + e * NT;
+      int cc, kk;
+      if (XFAST) {
+        cc = idx % TC;
+        kk = idx / TC;
+      } else {
+        kk = idx % KC;
+        cc = idx / KC;
+      }
+      const int64_t c = c0 + cc;
+      const int k = k0 + kk;
+      double2 val = make_double2(0.0, 0.0);
+      if (idx < TC * KC && c < ncols && k < n) {
+        const int64_t x = c % g.a, y = c / g.a;
+        const int64_t el = x + g.a * k + an * y;
+        val.x = load_combo(pro, 2 * el, plain);
+        val.y = load_combo(pro, 2 * el + 1, plain);
+      }
+      rv[e] = val;
+    }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int e = 0; e < LPT; ++e) {
+      const int idx = tid + e * NT;
+      if (idx < TI * KC) sL[idx / TI][idx % TI] = rl[e];
+    }
+#pragma unroll
+    for (int e = 0; e < VPT; ++e) {
+      const int idx = tid + e * NT;
+      if (idx < TC * KC) {
+        if (XFAST) sV[idx / TC][idx % TC] = rv[e];
+        else sV[idx % KC][idx / KC] = rv[e];
+      }
+    }
+  };
+
+  double2 acc[RI][RC];
+#pragma unroll
+  for (int r = 0; r < RI; ++r)
+#pragma unroll
+    for (int c = 0; c < RC; ++c) acc[r][c] = make_double2(0.0, 0.0);
+
+  fetch(0);
+  for (int k0 = 0; k0 < n; k0 += KC) {
+    stash();
+    __syncthreads();
+    if (k0 + KC < n) fetch(k0 + KC);
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      double2 lv[RI], vv[RC];
+#pragma unroll
+      for (int r = 0; r < RI; ++r) lv[r] = sL[kk][ti + r * TROWS];
+#pragma unroll
+      for (int c = 0; c < RC; ++c) vv[c] = sV[kk][tc + c * TCOLS];
+#pragma unroll
+      for (int r = 0; r < RI; ++r)
+#pragma unroll
+        for (int c = 0; c < RC; ++c) {
+          acc[r][c].x = fma(lv[r].x, vv[c].x, fma(-lv[r].y, vv[c].y, acc[r][c].x));
+          acc[r][c].y = fma(lv[r].x, vv[c].y, fma(lv[r].y, vv[c].x, acc[r][c].y));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < RI; ++r) {
+    const int i = i0 + ti + r * TROWS;
+    if (i >= n) continue;
+#pragma unroll
+    for (int c = 0; c < RC; ++c) {
+      const int64_t col = c0 + tc + c * TCOLS;
+      if (col >= ncols) continue;
+      const int64_t x = col % g.a, y = col / g.a;
+      const int64_t el = x + g.a * i + an * y;
+      store_epi(epi, W, 2 * el, acc[r][c].x);
+      store_epi(epi, W, 2 * el + 1, acc[r][c].y);
+    }
+  }
+}
+
+template <int TI, int TC, int RI, int RC, int KC>
+cudaError_t launch_tiled_c128(const Combo& pro, const double* L, ModeGeom g, double* W, const Epi& e,
+                              cudaStream_t st) {
+  constexpr int NT = (TI / RI) * (TC / RC);
+  const int64_t ncols = g.a * g.b;
+  dim3 grid((unsigned)((ncols + TC - 1) / TC), (unsigned)((g.n + TI - 1) / TI));
+  if (g.a >= TC)
+    return launch_pdl(mode_product_c128_kernel<TI, TC, RI, RC, KC, true>, grid, dim3(NT), 0, st, pro, L,
+                      g, W, e);
+  return launch_pdl(mode_product_c128_kernel<TI, TC, RI, RC, KC, false>, grid, dim3(NT), 0, st, pro, L, g,
+                    W, e);
+}
+
 template <int TI, int TC, int RI, int RC, int KC>
 cudaError_t launch_tiled(const Combo& pro, const double* L, ModeGeom g, double* W, const Epi& e,
                          cudaStream_t st) {
@@ -226,6 +361,24 @@ cudaError_t launch_mode_product_f64(const Combo& pro, const double* L, ModeGeom 
   const int64_t big_tiles = ((g.a * g.b + 63) / 64) * ((g.n + 31) / 32);
   if (big_tiles >= 8 * 152) return launch_tiled<32, 64, 2, 4, 16>(pro, L, g, W, e, st);
   return launch_tiled<16, 16, 2, 2, 32>(pro, L, g, W, e, st);
+}
+
+cudaError_t launch_mode_product_c128(const Combo& pro, const double* L, ModeGeom g, double* W,
+                                     const Epi* epi, cudaStream_t st) {
+  Epi e;
+  if (epi) {
+    e = *epi;
+  } else {
+    e.nout = 0;
+    e.nsrc = 0;
+  }
+  epi_finalize(e);
+  count_launch();
+  // four DFMA per complex product: the small tiles already give ~1000 CTAs
+  // at N = 2^18, the large ones when there are eight per SM
+  const int64_t big_tiles = ((g.a * g.b + 63) / 64) * ((g.n + 31) / 32);
+  if (big_tiles >= 8 * 152) return launch_tiled_c128<32, 64, 2, 4, 16>(pro, L, g, W, e, st);
+  return launch_tiled_c128<16, 16, 2, 2, 32>(pro, L, g, W, e, st);
 }
 
 cudaError_t launch_combine(const Epi& e0, int64_t N, cudaStream_t st) {

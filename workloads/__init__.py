@@ -219,6 +219,21 @@ def brusselator_operators(n: int, d1: float = 0.002, d2: float = 0.001, b: float
     return [A1, A1.copy(order="F")], [A2, A2.copy(order="F")]
 
 
+def validation_complex(n: int, d: int):
+    """Code-validation inputs of Sec. 4.1: A_mu = zeta T with zeta = (1+i)/100
+    and T the second-order Dirichlet Laplacian (h = 1/(n+1)); the vector
+    4096 (1+i) prod_mu x_mu (1 - x_mu) (column-major vec).  Returns
+    (zeta, [T] * d, v)."""
+    T = fd_adr_dirichlet(n, 1.0, 0.0)
+    x = np.arange(1, n + 1) / (n + 1.0)
+    f = x * (1 - x)
+    t = f
+    for _ in range(d - 1):
+        t = np.multiply.outer(t, f)
+    v = 4096 * (1 + 1j) * np.reshape(t, -1, order="F")
+    return (1 + 1j) / 100, [T.copy() for _ in range(d)], v
+
+
 def ac_paper(n: int = 21, eps: float = 0.05, beta: float = 7.0, alpha: float = 0.75):
     """Allen-Cahn problem of Sec. 4.3 on [0,1]^2 (homogeneous Neumann, n
     vertex-centred points per direction): A_mu = d_xx + I/(2 eps^2) (so that
