@@ -182,9 +182,10 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one oz_gemm_kernel<16> launch on
-# this workload (ncu --set full capture, profiles/oz_gemm_fp64emu_adr3d_n64.md)
-OZ_GEMM_TRAFFIC_BYTES = 3.79392e6
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the batched
+# oz_gemm_kernel on this workload (ncu capture, profiles/oz_gemm_fp64emu_adr3d_n64.md);
+# None until taken for the current kernel
+OZ_GEMM_TRAFFIC_BYTES = None
 
 
 def run_phiks(args):
@@ -260,13 +261,17 @@ def run_phiks(args):
                     "flops_per_launch": flops_per_launch,
                     "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)"}
         peaks, src = measured_peaks()
-        nbytes = 16.0 * N    # algorithmic: N FP64 in + N FP64 out per mu-mode product
+        # algorithmic: N FP64 in + N FP64 out per mu-mode product; one launch
+        # runs the products of up to four Tucker operators together
+        products = flops_per_launch / (2.0 * N * WORKLOAD["n"])
+        nbytes = 16.0 * N * products
         achieved = nbytes / (per_launch_ms * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": OZ_GEMM_TRAFFIC_BYTES,
-                "kernel": "oz_gemm_kernel<16>", "per_launch_ms": per_launch_ms,
+                "kernel": "oz_gemm_kernel<32>", "per_launch_ms": per_launch_ms,
+                "products_per_launch": products,
                 "bytes_per_launch": nbytes, "peak_source": "hbm_gbs of %s peaks (copy)" % src,
-                "note": "latency bound at this size: 5.8% tensor-pipe activity (ncu)"}
+                "note": "latency bound at this size (tensor pipe mostly idle, ncu)"}
 
     # ---- headline path
     plan = pk.Plan(wl.A, main_dtype)

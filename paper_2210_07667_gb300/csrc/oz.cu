@@ -90,14 +90,23 @@ __device__ __forceinline__ int biased_exp(double x) {
 
 constexpr int kSplitThreads = 128;
 
-// Each thread splits 8 consecutive elements of one fibre of X = (combination
-// `in`) and writes one 16-byte chunk of every digit plane; a block holds `fpb`
-// whole fibres (n / 8 threads each), whose exponents meet in shared memory.
-__global__ void __launch_bounds__(kSplitThreads) oz_split_kernel(Combo in, int n, int64_t M2, int fpb,
+struct ComboBatch {
+  Combo c[kOzMaxBatch];
+};
+
+// Each thread splits 8 consecutive elements of one fibre of X_b = (combination
+// in.c[b], b = blockIdx.y) and writes one 16-byte chunk of every digit plane;
+// a block holds `fpb` whole fibres (n / 8 threads each), whose exponents meet
+// in shared memory.  Plane s of tensor b starts at planes + s * PS + b * N;
+// the fibre exponents of tensor b at scale + b * M2.
+__global__ void __launch_bounds__(kSplitThreads) oz_split_kernel(ComboBatch inb, int n, int64_t M2, int fpb,
                                                                  __nv_bfloat16* planes, int64_t N,
-                                                                 int* scale) {
+                                                                 int64_t PS, int* scale) {
   __shared__ int emax[kSplitThreads];
   pdl_wait();
+  const Combo& in = inb.c[blockIdx.y];
+  planes += (int64_t)blockIdx.y * N;
+  scale += (int64_t)blockIdx.y * M2;
   const int cpf = n >> 3;
   const int t = threadIdx.x;
   const int fl = t / cpf;
@@ -150,7 +159,7 @@ __global__ void __launch_bounds__(kSplitThreads) oz_split_kernel(Combo in, int n
   }
 #pragma unroll
   for (int s = 0; s < kOzSlices; ++s)
-    *reinterpret_cast<uint4*>(planes + s * N + base) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+    *reinterpret_cast<uint4*>(planes + s * PS + base) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
   if (t == fl * cpf) scale[m] = E - 1029;
 }
 
@@ -207,13 +216,15 @@ __device__ __forceinline__ double oz_assemble(const uint32_t* G, int e) {
 struct OzParams {
   int n;          // contraction length
   int n_pad;      // rows of L padded to a multiple of NT
-  int64_t M2;     // fibres
+  int64_t M2;     // fibres of one tensor
+  int64_t rows;   // fibres of the batch (tensor b owns rows b M2 .. b M2 + M2 - 1)
+  int64_t N;      // elements of one tensor (the output stride between tensors)
   int nk;         // 64-element K chunks
   int n_ntiles;   // tiles of NT rows of L
   int num_tiles;
   int tmem_cols;
   int nbuf;       // TMEM accumulator sets (1 or 2)
-  double* out;    // FP64 result, rotated layout: out[m + M2 * i]
+  double* out;    // FP64 result of tensor b, rotated layout: out[b N + m + M2 i]
   const int* xscale;
   const int* lscale;
   int* status;
@@ -363,10 +374,13 @@ __global__ void __launch_bounds__(NTH, 1)
     for (int t = blockIdx.x; t < P.num_tiles; t += gridDim.x) {
       if (!mbar_wait(&tfull[buf], aph, P.status, 14)) break;
       tc_fence_after();
-      const int64_t m = (int64_t)(t / P.n_ntiles) * BM + row;
+      const int64_t rg = (int64_t)(t / P.n_ntiles) * BM + row;  // fibre of the batch
       const int r0 = (t % P.n_ntiles) * NT;
-      const bool valid = m < P.M2;
-      const int sx = valid ? P.xscale[m] : 0;
+      const bool valid = rg < P.rows;
+      const int sx = valid ? P.xscale[rg] : 0;
+      const int64_t bt = valid ? rg / P.M2 : 0;
+      double* const outb = P.out + bt * P.N;
+      const int64_t m = rg - bt * P.M2;
 #pragma unroll 1
       for (int c0 = grp * CW; c0 < (grp + 1) * CW; c0 += CH) {
         const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * SET + (uint32_t)c0;
@@ -387,7 +401,7 @@ __global__ void __launch_bounds__(NTH, 1)
         }
 #pragma unroll
         for (int j = 0; j < CH; ++j)
-          if (r0 + c0 + j < P.n) P.out[m + P.M2 * (int64_t)(r0 + c0 + j)] = r[j];
+          if (r0 + c0 + j < P.n) outb[m + P.M2 * (int64_t)(r0 + c0 + j)] = r[j];
       }
       tc_fence_before();
       mbar_arrive(&tempty[buf]);
@@ -425,11 +439,12 @@ bool get_enc() {
   return true;
 }
 
-// 3D map over 7 planes of a row-major (rows x inner) bf16 array; box
-// {64, box_rows, 1} (one plane) with the 128-byte swizzle.
-bool make_map3(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint32_t box_rows) {
+// 3D map over 7 planes of row-major (rows x inner) bf16 arrays, plane_elems
+// elements apart; box {64, box_rows, 1} (one plane) with the 128-byte swizzle.
+bool make_map3(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint32_t box_rows,
+               uint64_t plane_elems) {
   cuuint64_t dims[3] = {inner, rows, (cuuint64_t)kOzSlices};
-  cuuint64_t strides[2] = {inner * 2, inner * rows * 2};
+  cuuint64_t strides[2] = {inner * 2, plane_elems * 2};
   cuuint32_t box[3] = {64, box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
   return g_enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
@@ -458,13 +473,13 @@ struct OzState {
   uint8_t* ws = nullptr;
   double* tmp[2] = {nullptr, nullptr};
   int smem_optin = 0;
-  std::map<std::tuple<const void*, uint64_t, uint64_t, uint32_t>, CUtensorMap> maps;
+  std::map<std::tuple<const void*, uint64_t, uint64_t, uint32_t, uint64_t>, CUtensorMap> maps;
 };
 
 size_t oz_workspace_bytes(int d, const int64_t* n, int64_t N) {
   int64_t m2 = 0;
   for (int mu = 0; mu < d; ++mu) m2 = std::max<int64_t>(m2, N / n[mu]);
-  return up1k((size_t)kOzSlices * N * 2) + up1k((size_t)m2 * 4) + 1024;
+  return up1k((size_t)kOzSlices * kOzMaxBatch * N * 2) + up1k((size_t)kOzMaxBatch * m2 * 4) + 1024;
 }
 
 phiks_status oz_create(OzState** out, int d, const int64_t* n, int64_t N) {
@@ -551,14 +566,15 @@ cudaError_t run_oz_gemm(OzState* s, const CUtensorMap& mA, const CUtensorMap& mB
   return launch_pdl(kern, dim3(grid), dim3(NTH), smem, st, mA, mB, P);
 }
 
-bool cached(OzState* s, CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint32_t box) {
-  auto key = std::make_tuple(base, inner, rows, box);
+bool cached(OzState* s, CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint32_t box,
+            uint64_t plane_elems) {
+  auto key = std::make_tuple(base, inner, rows, box, plane_elems);
   auto it = s->maps.find(key);
   if (it != s->maps.end()) {
     *m = it->second;
     return true;
   }
-  if (!make_map3(m, base, inner, rows, box)) return false;
+  if (!make_map3(m, base, inner, rows, box, plane_elems)) return false;
   if (s->maps.size() > 4096) s->maps.clear();
   s->maps.emplace(key, *m);
   return true;
@@ -566,31 +582,36 @@ bool cached(OzState* s, CUtensorMap* m, const void* base, uint64_t inner, uint64
 
 }  // namespace
 
-cudaError_t oz_tucker(OzState* s, const Combo& in, const void* const* Bp, const Epi& epi,
+cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const void* const* Bp, const Epi* epi,
                       cudaStream_t st, const cudaEvent_t* ev) {
+  if (B < 1 || B > kOzMaxBatch) return cudaErrorInvalidValue;
   const int64_t N = s->N;
+  const int64_t PS = (int64_t)kOzMaxBatch * N;  // elements between digit planes
   __nv_bfloat16* planes = (__nv_bfloat16*)s->ws;
-  int* xscale = (int*)(s->ws + up1k((size_t)kOzSlices * N * 2));
-  Combo cur = in;
+  int* xscale = (int*)(s->ws + up1k((size_t)kOzSlices * PS * 2));
+  ComboBatch cur;
+  std::memset(&cur, 0, sizeof cur);
+  for (int b = 0; b < B; ++b) cur.c[b] = in[b];
   double* dst = nullptr;
   for (int mu = 0; mu < s->d; ++mu) {
     const int n = (int)s->n[mu];
     const int64_t M2 = N / n;
-    {  // split: n / 8 threads per fibre, whole fibres per block
+    const int64_t rows = (int64_t)B * M2;
+    {  // split: n / 8 threads per fibre, whole fibres per block, one grid row per tensor
       const int fpb = kSplitThreads / (n / 8);
       const int64_t blocks = (M2 + fpb - 1) / fpb;
       count_launch();
-      cudaError_t e = launch_pdl(oz_split_kernel, dim3((unsigned)blocks), dim3(kSplitThreads), 0, st, cur, n,
-                                 M2, fpb, planes, N, xscale);
+      cudaError_t e = launch_pdl(oz_split_kernel, dim3((unsigned)blocks, (unsigned)B), dim3(kSplitThreads), 0,
+                                 st, cur, n, M2, fpb, planes, N, PS, xscale);
       if (e != cudaSuccess) return e;
     }
     const int np = (n + 63) / 64 * 64;
-    const int NT = ntile_for(n, M2);
+    const int NT = ntile_for(n, rows);
     const uint8_t* bpl = (const uint8_t*)Bp[mu];
     const int* lscale = (const int*)(bpl + up1k((size_t)kOzSlices * np * np * 2));
     CUtensorMap mA, mB;
-    if (!cached(s, &mA, planes, (uint64_t)n, (uint64_t)M2, BM) ||
-        !cached(s, &mB, bpl, (uint64_t)np, (uint64_t)np, (uint32_t)NT)) {
+    if (!cached(s, &mA, planes, (uint64_t)n, (uint64_t)rows, BM, (uint64_t)PS) ||
+        !cached(s, &mB, bpl, (uint64_t)np, (uint64_t)np, (uint32_t)NT, (uint64_t)np * np)) {
       g_oz_err = "tensor map encoding failed";
       return cudaErrorInvalidValue;
     }
@@ -600,9 +621,11 @@ cudaError_t oz_tucker(OzState* s, const Combo& in, const void* const* Bp, const 
     P.n = n;
     P.n_pad = np;
     P.M2 = M2;
+    P.rows = rows;
+    P.N = N;
     P.nk = (n + 63) / 64;
     P.n_ntiles = (n + NT - 1) / NT;
-    P.num_tiles = (int)((M2 + BM - 1) / BM) * P.n_ntiles;
+    P.num_tiles = (int)((rows + BM - 1) / BM) * P.n_ntiles;
     P.nbuf = (2 * kOzSlices * NT <= 512) ? 2 : 1;
     int cols = 32;
     while (cols < P.nbuf * kOzSlices * NT) cols <<= 1;
@@ -622,18 +645,24 @@ cudaError_t oz_tucker(OzState* s, const Combo& in, const void* const* Bp, const 
       if (e != cudaSuccess) return e;
     }
     std::memset(&cur, 0, sizeof cur);
-    cur.nsrc = 1;
-    cur.src[0] = dst;
-    cur.coef[0] = 1.0;
+    for (int b = 0; b < B; ++b) {
+      cur.c[b].nsrc = 1;
+      cur.c[b].src[0] = dst + (int64_t)b * N;
+      cur.c[b].coef[0] = 1.0;
+    }
   }
-  // the Tucker operator's epilogue over all N elements with the whole GPU
-  Epi f = epi;
-  const int m = f.nsrc;
-  if (m >= kMaxSrc) return cudaErrorInvalidValue;
-  f.src[m] = dst;
-  for (int t = 0; t < f.nout; ++t) f.a[t][m] = epi.b[t];
-  f.nsrc = m + 1;
-  return launch_combine(f, N, st);
+  // each Tucker operator's epilogue over its N elements with the whole GPU
+  for (int b = 0; b < B; ++b) {
+    Epi f = epi[b];
+    const int m = f.nsrc;
+    if (m >= kMaxSrc) return cudaErrorInvalidValue;
+    f.src[m] = dst + (int64_t)b * N;
+    for (int t = 0; t < f.nout; ++t) f.a[t][m] = epi[b].b[t];
+    f.nsrc = m + 1;
+    cudaError_t e = launch_combine(f, N, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 int oz_read_status(OzState* s, cudaStream_t st) {

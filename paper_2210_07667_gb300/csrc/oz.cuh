@@ -27,6 +27,7 @@ struct OzState;
 
 constexpr int kOzSlices = 7;
 constexpr int kOzMaxN = 128;
+constexpr int kOzMaxBatch = 4;  // Tucker operators one oz_tucker call runs together
 
 size_t oz_workspace_bytes(int d, const int64_t* n, int64_t N);
 phiks_status oz_create(OzState** out, int d, const int64_t* n, int64_t N);
@@ -40,10 +41,14 @@ void oz_bind_workspace(OzState* s, void* ws, double* tmp0, double* tmp1);
 size_t oz_bplanes_bytes(int n);
 cudaError_t oz_prepare_b(const double* L, int n, void* dst, cudaStream_t st);
 
-// (combination `in`) x_1 L_1 ... x_d L_d through `epi` (FP64), Bp[mu] made
-// by oz_prepare_b for L_mu.  `ev` (2 d events, or null): ev[2 mu] and
-// ev[2 mu + 1] are recorded around the tensor-core pass of mode mu.
-cudaError_t oz_tucker(OzState* s, const Combo& in, const void* const* Bp, const Epi& epi,
+// B <= kOzMaxBatch Tucker operators with the same matrices, run together:
+// (combination in[b]) x_1 L_1 ... x_d L_d through epi[b] (FP64), Bp[mu] made
+// by oz_prepare_b for L_mu.  Every pass treats the B tensors as one tensor
+// with B times the fibres.  The workspace bound by oz_bind_workspace holds the
+// digit planes of kOzMaxBatch tensors, and tmp0 / tmp1 kOzMaxBatch N doubles
+// each.  `ev` (2 d events, or null): ev[2 mu] and ev[2 mu + 1] are recorded
+// around the tensor-core pass of mode mu.
+cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const void* const* Bp, const Epi* epi,
                       cudaStream_t st, const cudaEvent_t* ev = nullptr);
 
 int oz_read_status(OzState* s, cudaStream_t st);

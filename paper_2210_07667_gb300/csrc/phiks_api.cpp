@@ -197,8 +197,12 @@ size_t elt_size(const phiks_plan_s* P) { return P->cplx ? 16 : (double_vectors(P
 //   and the operand planes of the tensor-core passes.  Every region starts on
 //   a 1 KiB boundary.
 struct WsLayout {
-  size_t acc, tmp, msq0, msq1, tcb0, tcb1, planes, total;
+  size_t acc, acc2, tmp, msq0, msq1, tcb0, tcb1, planes, total;
 };
+
+// Tucker operators the FP64_EMU path runs together (one for the others); its
+// Tucker temporaries and second set of accumulators are sized for them.
+int tucker_batch_max(const phiks_plan_s* P) { return emu_dtype(P) ? kOzMaxBatch : 1; }
 
 size_t up1k(size_t x) { return (x + 1023) / 1024 * 1024; }
 
@@ -208,8 +212,10 @@ WsLayout ws_layout(const phiks_plan_s* P, int p) {
   size_t o = 0;
   w.acc = o;
   o += up1k((size_t)std::max(p, 1) * N * 8);
+  w.acc2 = o;  // new accumulators of a batched squaring step
+  if (emu_dtype(P)) o += up1k((size_t)std::max(p, 1) * N * 8);
   w.tmp = o;
-  o += up1k(2 * N * 8);
+  o += up1k(2 * (size_t)tucker_batch_max(P) * N * 8);
   w.msq0 = o;
   o += up1k(P->sum_n2 * 8);
   w.msq1 = o;
@@ -535,6 +541,7 @@ struct Ctx {
   cudaStream_t st;
   double* tmp[2];
   int tuckers = 0;
+  double* acc2[PHIKS_MAX_P] = {nullptr};  // FP64_EMU: accumulators of batched squaring
   double* msq[2] = {nullptr, nullptr};      // squaring chain ping-pong
   uint8_t* msq_tcb[2] = {nullptr, nullptr}; // split path: their B planes
 };
@@ -545,8 +552,10 @@ void carve(Ctx& c, int p, char* ws, double** acc) {
   uintptr_t base = ((uintptr_t)ws + 1023) & ~(uintptr_t)1023;
   WsLayout w = ws_layout(P, p);
   for (int l = 0; l < std::max(p, 1); ++l) acc[l] = (double*)(base + w.acc) + (size_t)l * P->NR;
+  if (emu_dtype(P))
+    for (int l = 0; l < std::max(p, 1); ++l) c.acc2[l] = (double*)(base + w.acc2) + (size_t)l * P->NR;
   c.tmp[0] = (double*)(base + w.tmp);
-  c.tmp[1] = c.tmp[0] + P->NR;
+  c.tmp[1] = c.tmp[0] + (size_t)tucker_batch_max(P) * P->NR;
   c.msq[0] = (double*)(base + w.msq0);
   c.msq[1] = (double*)(base + w.msq1);
   if (tc_path(P)) {
@@ -604,7 +613,7 @@ phiks_status tucker(Ctx& c, const Combo& in, const Mats& M, const Epi* epi) {
     const bool prof = P->prof;
     if (prof)
       for (int mu = 0; mu < P->d; ++mu) TRY(prof_pair(P, &ev[2 * mu], &ev[2 * mu + 1]));
-    cudaError_t e = oz_tucker(P->oz, in, M.B, *epi, c.st, prof ? ev : nullptr);
+    cudaError_t e = oz_tucker(P->oz, 1, &in, M.B, epi, c.st, prof ? ev : nullptr);
     if (e != cudaSuccess)
       return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), oz_last_error());
     if (prof)
@@ -640,6 +649,32 @@ phiks_status tucker(Ctx& c, const Combo& in, const Mats& M, const Epi* epi) {
     cur.coef[0] = 1.0;
   }
   c.tuckers++;
+  return PHIKS_OK;
+}
+
+// B Tucker operators sharing the matrices M (their inputs and epilogues
+// independent: no epilogue writes what another one reads): one batched run
+// on the FP64_EMU path (in groups of kOzMaxBatch), one after the other
+// otherwise.
+phiks_status tucker_batch(Ctx& c, int B, const Combo* in, const Mats& M, const Epi* epi) {
+  phiks_plan_s* P = c.P;
+  if (!emu_dtype(P)) {
+    for (int b = 0; b < B; ++b) TRY(tucker(c, in[b], M, &epi[b]));
+    return PHIKS_OK;
+  }
+  for (int b0 = 0; b0 < B; b0 += kOzMaxBatch) {
+    const int nb = std::min(kOzMaxBatch, B - b0);
+    cudaEvent_t ev[2 * PHIKS_MAX_D];
+    const bool prof = P->prof;
+    if (prof)
+      for (int mu = 0; mu < P->d; ++mu) TRY(prof_pair(P, &ev[2 * mu], &ev[2 * mu + 1]));
+    cudaError_t e = oz_tucker(P->oz, nb, in + b0, M.B, epi + b0, c.st, prof ? ev : nullptr);
+    if (e != cudaSuccess)
+      return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), oz_last_error());
+    if (prof)
+      for (int mu = 0; mu < P->d; ++mu) P->prof_flops += 2.0 * nb * (double)P->N * (double)P->n[mu];
+    c.tuckers += nb;
+  }
   return PHIKS_OK;
 }
 
@@ -768,19 +803,33 @@ phiks_status run_same(Ctx& c, const Bank* B, int s, int p, const void* v, const 
     return PHIKS_OK;
   };
   if (s < o.nscales) TRY(emit(s));
+  const bool batched = c.acc2[0] != nullptr;  // FP64_EMU: the p Tuckers of a level together
   for (int j = s; j >= 1; --j) {
     // eq. (simul): phi_l(K/2^(j-1)) v = 2^-l (exp(K/2^j) phi_l + sum_k phi_k/(l-k)!), l = p..1
+    // (in place from l = p down; batched: every l reads the old values and
+    // writes the second set of accumulators, which then become the first)
+    Combo ins[PHIKS_MAX_P];
+    Epi es[PHIKS_MAX_P];
     for (int l = p; l >= 1; --l) {
       Epi e = make_epi();
       e.nout = 1;
       e.nsrc = l;
-      e.out[0] = acc[l - 1];
+      e.out[0] = batched ? c.acc2[l - 1] : acc[l - 1];
       e.b[0] = std::ldexp(1.0, -l);
       for (int k = 1; k <= l; ++k) {
         e.src[k - 1] = acc[k - 1];
         e.a[0][k - 1] = std::ldexp(1.0, -l) / factorial(l - k);
       }
-      TRY(tucker(c, plain(acc[l - 1], false), M, &e));
+      if (batched) {
+        ins[p - l] = plain(acc[l - 1], false);
+        es[p - l] = e;
+      } else {
+        TRY(tucker(c, plain(acc[l - 1], false), M, &e));
+      }
+    }
+    if (batched) {
+      TRY(tucker_batch(c, p, ins, M, es));
+      for (int l = 0; l < p; ++l) std::swap(acc[l], c.acc2[l]);
     }
     TRY(square_modes(c, M, mbuf));
     if (j - 1 < o.nscales) TRY(emit(j - 1));
@@ -800,6 +849,9 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
   for (int l = 0; l < p; ++l) CK(cudaMemsetAsync(acc[l], 0, P->NR * 8, c.st));
   for (int i = 0; i < q; ++i) {
     const double th = B->theta[i], w = B->w[i];
+    Combo ins[PHIKS_MAX_P];
+    Epi es[PHIKS_MAX_P];
+    int nb = 0;
     for (int l = 1; l <= p; ++l) {
       // input: sum_{k=1}^{l} theta^(l-k)/(l-k)! v_{p+1-k} / 2^((l-k+1) s)
       Combo in = make_combo();
@@ -834,9 +886,13 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
       e.src[0] = acc[l - 1];
       e.a[0][0] = 1.0;
       e.b[0] = w;
+      ins[nb] = in;
+      es[nb++] = e;
+    }
+    if (nb) {  // the node's Tucker operators share its matrices
       Mats L;
       bank_ptrs(P, B, B->node_bank[i], &L);
-      TRY(tucker(c, in, L, &e));
+      TRY(tucker_batch(c, nb, ins, L, es));
     }
   }
   Mats M;
@@ -864,19 +920,32 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
     return PHIKS_OK;
   };
   if (s < o.nscales) TRY(emit(s));
+  const bool batched = c.acc2[0] != nullptr;  // FP64_EMU: the p Tuckers of a level together
   for (int j = s; j >= 1; --j) {
-    // eq. (comb), l = p..1
+    // eq. (comb), l = p..1 in place; batched: from the old values into the
+    // second set of accumulators, which then become the first
+    Combo ins[PHIKS_MAX_P];
+    Epi es[PHIKS_MAX_P];
     for (int l = p; l >= 1; --l) {
       Epi e = make_epi();
       e.nout = 1;
       e.nsrc = l;
-      e.out[0] = acc[l - 1];
+      e.out[0] = batched ? c.acc2[l - 1] : acc[l - 1];
       e.b[0] = 1.0;
       for (int k = 1; k <= l; ++k) {
         e.src[k - 1] = acc[k - 1];
         e.a[0][k - 1] = 1.0 / (factorial(l - k) * std::ldexp(1.0, (l - k) * j));
       }
-      TRY(tucker(c, plain(acc[l - 1], false), M, &e));
+      if (batched) {
+        ins[p - l] = plain(acc[l - 1], false);
+        es[p - l] = e;
+      } else {
+        TRY(tucker(c, plain(acc[l - 1], false), M, &e));
+      }
+    }
+    if (batched) {
+      TRY(tucker_batch(c, p, ins, M, es));
+      for (int l = 0; l < p; ++l) std::swap(acc[l], c.acc2[l]);
     }
     TRY(square_modes(c, M, mbuf));
     if (j - 1 < o.nscales) TRY(emit(j - 1));
