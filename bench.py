@@ -182,10 +182,10 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the batched
-# oz_gemm_kernel on this workload (ncu capture, profiles/oz_gemm_fp64emu_adr3d_n64.md);
-# None until taken for the current kernel
-OZ_GEMM_TRAFFIC_BYTES = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one oz_gemm_kernel<32> launch
+# running four mu-mode products (ncu capture, profiles/oz_gemm_fp64emu_adr3d_n64.md),
+# per product; None once the kernel has changed since the capture
+OZ_GEMM_TRAFFIC_PER_PRODUCT = 14.8298e6 / 4
 
 
 def run_phiks(args):
@@ -267,7 +267,8 @@ def run_phiks(args):
         nbytes = 16.0 * N * products
         achieved = nbytes / (per_launch_ms * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": OZ_GEMM_TRAFFIC_BYTES,
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": None if OZ_GEMM_TRAFFIC_PER_PRODUCT is None else OZ_GEMM_TRAFFIC_PER_PRODUCT * products,
                 "kernel": "oz_gemm_kernel<32>", "per_launch_ms": per_launch_ms,
                 "products_per_launch": products,
                 "bytes_per_launch": nbytes, "peak_source": "hbm_gbs of %s peaks (copy)" % src,

@@ -163,10 +163,22 @@ __global__ void __launch_bounds__(kSplitThreads) oz_split_kernel(ComboBatch inb,
   if (t == fl * cpf) scale[m] = E - 1029;
 }
 
-// B digits: row i of L (column-major n x n), row-major planes n_pad x n_pad.
-__global__ void oz_prep_b_kernel(const double* L, int n, int n_pad, __nv_bfloat16* planes,
-                                 int* scale) {
+// B digits: row i of L (column-major n x n), row-major planes n_pad x n_pad;
+// one warp per row, one grid row (blockIdx.y) per matrix of the batch.
+constexpr int kPrepBatch = 32;
+struct PrepBatch {
+  const double* L[kPrepBatch];
+  int n[kPrepBatch];
+  __nv_bfloat16* planes[kPrepBatch];
+};
+
+__global__ void oz_prep_b_kernel(PrepBatch pb) {
   pdl_wait();
+  const double* L = pb.L[blockIdx.y];
+  const int n = pb.n[blockIdx.y];
+  const int n_pad = (n + 63) / 64 * 64;
+  __nv_bfloat16* planes = pb.planes[blockIdx.y];
+  int* scale = (int*)((uint8_t*)planes + (((size_t)kOzSlices * n_pad * n_pad * 2 + 1023) / 1024 * 1024));
   const int lane = threadIdx.x & 31;
   const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   if (i >= n_pad) return;
@@ -476,6 +488,7 @@ struct OzState {
   std::map<std::tuple<const void*, uint64_t, uint64_t, uint32_t, uint64_t>, CUtensorMap> maps;
 };
 
+// Digit planes and fibre exponents of kOzMaxBatch tensors.
 size_t oz_workspace_bytes(int d, const int64_t* n, int64_t N) {
   int64_t m2 = 0;
   for (int mu = 0; mu < d; ++mu) m2 = std::max<int64_t>(m2, N / n[mu]);
@@ -534,13 +547,24 @@ size_t oz_bplanes_bytes(int n) {
   return up1k((size_t)kOzSlices * np * np * 2) + up1k(np * 4);
 }
 
-cudaError_t oz_prepare_b(const double* L, int n, void* dst, cudaStream_t st) {
-  const int np = (n + 63) / 64 * 64;
-  __nv_bfloat16* planes = (__nv_bfloat16*)dst;
-  int* scale = (int*)((uint8_t*)dst + up1k((size_t)kOzSlices * np * np * 2));
-  count_launch();
-  return launch_pdl(oz_prep_b_kernel, dim3((np * 32 + 255) / 256), dim3(256), 0, st, L, n, np, planes,
-                    scale);
+cudaError_t oz_prepare_b(int count, const double* const* L, const int* n, void* const* dst,
+                         cudaStream_t st) {
+  for (int k0 = 0; k0 < count; k0 += kPrepBatch) {
+    PrepBatch pb;
+    std::memset(&pb, 0, sizeof pb);
+    const int cnt = std::min(kPrepBatch, count - k0);
+    int npmax = 64;
+    for (int k = 0; k < cnt; ++k) {
+      pb.L[k] = L[k0 + k];
+      pb.n[k] = n[k0 + k];
+      pb.planes[k] = (__nv_bfloat16*)dst[k0 + k];
+      npmax = std::max(npmax, (n[k0 + k] + 63) / 64 * 64);
+    }
+    count_launch();
+    cudaError_t e = launch_pdl(oz_prep_b_kernel, dim3((npmax * 32 + 255) / 256, cnt), dim3(256), 0, st, pb);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 namespace {
@@ -549,7 +573,7 @@ template <int NT>
 cudaError_t run_oz_gemm(OzState* s, const CUtensorMap& mA, const CUtensorMap& mB, OzParams& P,
                         cudaStream_t st) {
   constexpr uint32_t STAGE = kOzSlices * (BM * 128 + NT * 128);
-  const size_t smem = STAGE + 1024 + 256;
+  const size_t smem = STAGE + 1024 + 256;  // alignment slack, barriers
   if ((int)smem > s->smem_optin) return cudaErrorInvalidConfiguration;
   auto kern = oz_gemm_kernel<NT>;
   static int set[64] = {0};
@@ -651,18 +675,17 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const void* const* Bp,
       cur.c[b].coef[0] = 1.0;
     }
   }
-  // each Tucker operator's epilogue over its N elements with the whole GPU
+  // the Tucker operators' epilogues over their N elements with the whole GPU
+  Epi f[kOzMaxBatch];
   for (int b = 0; b < B; ++b) {
-    Epi f = epi[b];
-    const int m = f.nsrc;
+    f[b] = epi[b];
+    const int m = f[b].nsrc;
     if (m >= kMaxSrc) return cudaErrorInvalidValue;
-    f.src[m] = dst + (int64_t)b * N;
-    for (int t = 0; t < f.nout; ++t) f.a[t][m] = epi[b].b[t];
-    f.nsrc = m + 1;
-    cudaError_t e = launch_combine(f, N, st);
-    if (e != cudaSuccess) return e;
+    f[b].src[m] = dst + (int64_t)b * N;
+    for (int t = 0; t < f[b].nout; ++t) f[b].a[t][m] = epi[b].b[t];
+    f[b].nsrc = m + 1;
   }
-  return cudaSuccess;
+  return launch_combine_batch(f, B, N, st);
 }
 
 int oz_read_status(OzState* s, cudaStream_t st) {

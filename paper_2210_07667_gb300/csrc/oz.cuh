@@ -36,10 +36,11 @@ const char* oz_last_error();
 void oz_bind_workspace(OzState* s, void* ws, double* tmp0, double* tmp1);
 
 // Bytes of the B-operand slices of one n x n matrix (7 planes of n_pad x
-// n_pad bf16 and n_pad row exponents), and their preparation from an FP64
-// column-major matrix.
+// n_pad bf16 and n_pad row exponents), and their preparation from FP64
+// column-major matrices: L[k] (n[k] x n[k]) into dst[k], k < count.
 size_t oz_bplanes_bytes(int n);
-cudaError_t oz_prepare_b(const double* L, int n, void* dst, cudaStream_t st);
+cudaError_t oz_prepare_b(int count, const double* const* L, const int* n, void* const* dst,
+                         cudaStream_t st);
 
 // B <= kOzMaxBatch Tucker operators with the same matrices, run together:
 // (combination in[b]) x_1 L_1 ... x_d L_d through epi[b] (FP64), Bp[mu] made

@@ -517,12 +517,21 @@ phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool 
     nb.tcoff.assign(nbk, std::vector<size_t>(P->d));
     if (hit) nb.tcb = hit->tcb;
     else CK(cudaMalloc(&nb.tcb, (size_t)nbk * P->tcb_bytes));
+    std::vector<const double*> srcs;
+    std::vector<int> ns;
+    std::vector<void*> dsts;
     for (int b = 0; b < nbk; ++b)
       for (int mu = 0; mu < P->d; ++mu) {
         nb.tcoff[b][mu] = (size_t)b * P->tcb_bytes + P->tcb_off[mu];
-        if (emu_dtype(P)) CK(oz_prepare_b(nb.dev + nb.off[b][mu], (int)P->n[mu], nb.tcb + nb.tcoff[b][mu], st));
-        else CK(tc_prepare_b(P->dtype, nb.dev + nb.off[b][mu], (int)P->n[mu], nb.tcb + nb.tcoff[b][mu], st));
+        if (emu_dtype(P)) {
+          srcs.push_back(nb.dev + nb.off[b][mu]);
+          ns.push_back((int)P->n[mu]);
+          dsts.push_back(nb.tcb + nb.tcoff[b][mu]);
+        } else {
+          CK(tc_prepare_b(P->dtype, nb.dev + nb.off[b][mu], (int)P->n[mu], nb.tcb + nb.tcoff[b][mu], st));
+        }
       }
+    if (!srcs.empty()) CK(oz_prepare_b((int)srcs.size(), srcs.data(), ns.data(), dsts.data(), st));
   }
   nb.stamp = P->clock;
   if (hit) {
@@ -711,16 +720,22 @@ phiks_status square_modes(Ctx& c, Mats& M, int& cur_buf) {
   }
   CK(launch_gemm_batch_f64(gb, P->nmax, c.st));
   off = 0;
+  const double* srcs[PHIKS_MAX_D];
+  int ns[PHIKS_MAX_D];
+  void* dsts[PHIKS_MAX_D];
   for (int mu = 0; mu < P->d; ++mu) {
     M.L[mu] = c.msq[cur_buf] + off;
     off += (size_t)P->m[mu] * P->m[mu];
     if (tc_path(P)) {
       uint8_t* dst = c.msq_tcb[cur_buf] + P->tcb_off[mu];
-      if (emu_dtype(P)) CK(oz_prepare_b(M.L[mu], (int)P->n[mu], dst, c.st));
-      else CK(tc_prepare_b(P->dtype, M.L[mu], (int)P->n[mu], dst, c.st));
+      srcs[mu] = M.L[mu];
+      ns[mu] = (int)P->n[mu];
+      dsts[mu] = dst;
+      if (!emu_dtype(P)) CK(tc_prepare_b(P->dtype, M.L[mu], (int)P->n[mu], dst, c.st));
       M.B[mu] = dst;
     }
   }
+  if (emu_dtype(P)) CK(oz_prepare_b(P->d, srcs, ns, dsts, c.st));
   cur_buf = 1 - cur_buf;
   return PHIKS_OK;
 }
@@ -1539,12 +1554,18 @@ phiks_status phiks_tucker(phiks_plan_t P, const void* V, void* W, const double* 
     M.B[mu] = nullptr;
   }
   if (tc_path(P)) {
+    const double* srcs[PHIKS_MAX_D];
+    int ns[PHIKS_MAX_D];
+    void* dsts[PHIKS_MAX_D];
     for (int mu = 0; mu < P->d; ++mu) {
       uint8_t* dst = P->tucker_tcb + P->tcb_off[mu];
-      if (emu_dtype(P)) CK(oz_prepare_b(L[mu], (int)P->n[mu], dst, c.st));
-      else CK(tc_prepare_b(P->dtype, L[mu], (int)P->n[mu], dst, c.st));
+      srcs[mu] = L[mu];
+      ns[mu] = (int)P->n[mu];
+      dsts[mu] = dst;
+      if (!emu_dtype(P)) CK(tc_prepare_b(P->dtype, L[mu], (int)P->n[mu], dst, c.st));
       M.B[mu] = dst;
     }
+    if (emu_dtype(P)) CK(oz_prepare_b(P->d, srcs, ns, dsts, c.st));
   }
   Epi e = make_epi();
   e.nout = 1;

@@ -304,6 +304,20 @@ cudaError_t launch_tiled(const Combo& pro, const double* L, ModeGeom g, double* 
                     W, e);
 }
 
+constexpr int kMaxEpiBatch = 4;
+struct EpiBatch {
+  Epi e[kMaxEpiBatch];
+};
+
+// One combination per grid row (blockIdx.y), each over N elements.
+__global__ void combine_batch_kernel(EpiBatch eb, int64_t N) {
+  pdl_wait();
+  const Epi& e = eb.e[blockIdx.y];
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (int64_t)gridDim.x * blockDim.x)
+    epi_apply(e, idx, 0.0);
+}
+
 __global__ void combine_kernel(Epi e, int64_t N) {
   pdl_wait();
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
@@ -379,6 +393,21 @@ cudaError_t launch_mode_product_c128(const Combo& pro, const double* L, ModeGeom
   const int64_t big_tiles = ((g.a * g.b + 63) / 64) * ((g.n + 31) / 32);
   if (big_tiles >= 8 * 152) return launch_tiled_c128<32, 64, 2, 4, 16>(pro, L, g, W, e, st);
   return launch_tiled_c128<16, 16, 2, 2, 32>(pro, L, g, W, e, st);
+}
+
+cudaError_t launch_combine_batch(const Epi* e0, int B, int64_t N, cudaStream_t st) {
+  if (N <= 0 || B <= 0) return cudaSuccess;
+  if (B > kMaxEpiBatch) return cudaErrorInvalidValue;
+  EpiBatch eb;
+  for (int b = 0; b < B; ++b) {
+    eb.e[b] = e0[b];
+    for (int t = 0; t < kMaxOut; ++t) eb.e[b].b[t] = 0.0;  // no product result here
+    epi_finalize(eb.e[b]);
+  }
+  count_launch();
+  int gx = grid_for(N, 256) / B;
+  if (gx < 1) gx = 1;
+  return launch_pdl(combine_batch_kernel, dim3(gx, B), dim3(256), 0, st, eb, N);
 }
 
 cudaError_t launch_combine(const Epi& e0, int64_t N, cudaStream_t st) {

@@ -25,7 +25,8 @@ def _cuda():
     pk.load(build_if_missing=True)
 
 
-@pytest.mark.parametrize("dims", [(32, 32), (64, 48, 40), (128, 16, 24), (8, 8, 8, 8), (64, 64, 64)])
+@pytest.mark.parametrize("dims", [(32, 32), (64, 48, 40), (128, 16, 24), (8, 8, 8, 8), (64, 64, 64),
+                                  (16, 128, 24), (24, 64, 32)])
 def test_tucker_emulated_fp64(dims):
     rng = np.random.default_rng(sum(dims))
     plan = pk.Plan([np.eye(m) for m in dims], EMU)
