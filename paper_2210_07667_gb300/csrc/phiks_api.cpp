@@ -200,9 +200,12 @@ struct WsLayout {
   size_t acc, acc2, tmp, msq0, msq1, tcb0, tcb1, planes, total;
 };
 
-// Tucker operators the FP64_EMU path runs together (one for the others); its
-// Tucker temporaries and second set of accumulators are sized for them.
-int tucker_batch_max(const phiks_plan_s* P) { return emu_dtype(P) ? kOzMaxBatch : 1; }
+// Tucker operators the tensor-core paths run together (one for the FP64
+// pipe); their Tucker temporaries and second set of accumulators are sized
+// for them.
+int tucker_batch_max(const phiks_plan_s* P) {
+  return emu_dtype(P) ? kOzMaxBatch : (split_dtype(P) ? kTcMaxBatch : 1);
+}
 
 size_t up1k(size_t x) { return (x + 1023) / 1024 * 1024; }
 
@@ -213,7 +216,7 @@ WsLayout ws_layout(const phiks_plan_s* P, int p) {
   w.acc = o;
   o += up1k((size_t)std::max(p, 1) * N * 8);
   w.acc2 = o;  // new accumulators of a batched squaring step
-  if (emu_dtype(P)) o += up1k((size_t)std::max(p, 1) * N * 8);
+  if (tc_path(P)) o += up1k((size_t)std::max(p, 1) * N * 8);
   w.tmp = o;
   o += up1k(2 * (size_t)tucker_batch_max(P) * N * 8);
   w.msq0 = o;
@@ -561,7 +564,7 @@ void carve(Ctx& c, int p, char* ws, double** acc) {
   uintptr_t base = ((uintptr_t)ws + 1023) & ~(uintptr_t)1023;
   WsLayout w = ws_layout(P, p);
   for (int l = 0; l < std::max(p, 1); ++l) acc[l] = (double*)(base + w.acc) + (size_t)l * P->NR;
-  if (emu_dtype(P))
+  if (tc_path(P))
     for (int l = 0; l < std::max(p, 1); ++l) c.acc2[l] = (double*)(base + w.acc2) + (size_t)l * P->NR;
   c.tmp[0] = (double*)(base + w.tmp);
   c.tmp[1] = c.tmp[0] + (size_t)tucker_batch_max(P) * P->NR;
@@ -633,7 +636,7 @@ phiks_status tucker(Ctx& c, const Combo& in, const Mats& M, const Epi* epi) {
   if (tc_path(P)) {
     cudaEvent_t e1;
     TRY(prof_begin(c, &e1));
-    cudaError_t e = tc_tucker(P->tc, in, M.B, *epi, c.st);
+    cudaError_t e = tc_tucker(P->tc, 1, &in, M.B, epi, c.st);
     if (e != cudaSuccess)
       return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), tc_last_error());
     double fl = 0;
@@ -667,21 +670,32 @@ phiks_status tucker(Ctx& c, const Combo& in, const Mats& M, const Epi* epi) {
 // otherwise.
 phiks_status tucker_batch(Ctx& c, int B, const Combo* in, const Mats& M, const Epi* epi) {
   phiks_plan_s* P = c.P;
-  if (!emu_dtype(P)) {
+  if (!tc_path(P)) {
     for (int b = 0; b < B; ++b) TRY(tucker(c, in[b], M, &epi[b]));
     return PHIKS_OK;
   }
-  for (int b0 = 0; b0 < B; b0 += kOzMaxBatch) {
-    const int nb = std::min(kOzMaxBatch, B - b0);
-    cudaEvent_t ev[2 * PHIKS_MAX_D];
+  const int bmax = tucker_batch_max(P);
+  double fl = 0;
+  for (int mu = 0; mu < P->d; ++mu) fl += 2.0 * (double)P->N * (double)P->n[mu];
+  for (int b0 = 0; b0 < B; b0 += bmax) {
+    const int nb = std::min(bmax, B - b0);
     const bool prof = P->prof;
-    if (prof)
-      for (int mu = 0; mu < P->d; ++mu) TRY(prof_pair(P, &ev[2 * mu], &ev[2 * mu + 1]));
-    cudaError_t e = oz_tucker(P->oz, nb, in + b0, M.B, epi + b0, c.st, prof ? ev : nullptr);
+    cudaError_t e;
+    if (emu_dtype(P)) {  // events around every tensor-core pass
+      cudaEvent_t ev[2 * PHIKS_MAX_D];
+      if (prof)
+        for (int mu = 0; mu < P->d; ++mu) TRY(prof_pair(P, &ev[2 * mu], &ev[2 * mu + 1]));
+      e = oz_tucker(P->oz, nb, in + b0, M.B, epi + b0, c.st, prof ? ev : nullptr);
+      if (prof) P->prof_flops += nb * fl;
+    } else {  // events around the whole batch
+      cudaEvent_t e1;
+      TRY(prof_begin(c, &e1));
+      e = tc_tucker(P->tc, nb, in + b0, M.B, epi + b0, c.st);
+      if (e == cudaSuccess) TRY(prof_end(c, e1, nb * fl));
+    }
     if (e != cudaSuccess)
-      return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), oz_last_error());
-    if (prof)
-      for (int mu = 0; mu < P->d; ++mu) P->prof_flops += 2.0 * nb * (double)P->N * (double)P->n[mu];
+      return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e),
+                  emu_dtype(P) ? oz_last_error() : tc_last_error());
     c.tuckers += nb;
   }
   return PHIKS_OK;
@@ -818,7 +832,7 @@ phiks_status run_same(Ctx& c, const Bank* B, int s, int p, const void* v, const 
     return PHIKS_OK;
   };
   if (s < o.nscales) TRY(emit(s));
-  const bool batched = c.acc2[0] != nullptr;  // FP64_EMU: the p Tuckers of a level together
+  const bool batched = c.acc2[0] != nullptr;  // tensor-core paths: the p Tuckers of a level together
   for (int j = s; j >= 1; --j) {
     // eq. (simul): phi_l(K/2^(j-1)) v = 2^-l (exp(K/2^j) phi_l + sum_k phi_k/(l-k)!), l = p..1
     // (in place from l = p down; batched: every l reads the old values and
@@ -935,7 +949,7 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
     return PHIKS_OK;
   };
   if (s < o.nscales) TRY(emit(s));
-  const bool batched = c.acc2[0] != nullptr;  // FP64_EMU: the p Tuckers of a level together
+  const bool batched = c.acc2[0] != nullptr;  // tensor-core paths: the p Tuckers of a level together
   for (int j = s; j >= 1; --j) {
     // eq. (comb), l = p..1 in place; batched: from the old values into the
     // second set of accumulators, which then become the first

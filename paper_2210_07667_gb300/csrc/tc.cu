@@ -84,9 +84,11 @@ struct GemmParams {
   int n_pad;      // n rounded up to 16
   int ntile;      // MMA N: rows of L per tile (multiple of 16, <= 256)
   int n_ntiles;   // N tiles per row block
-  int64_t M2;     // N / n
+  int64_t M2;     // N / n: fibres of one tensor
+  int64_t rows;   // fibres of the batch (tensor b owns rows b M2 .. b M2 + M2 - 1)
+  int64_t N;      // elements of one tensor
   int nk;         // 128-byte K chunks
-  int num_tiles;  // ceil(M2 / 128) * n_ntiles
+  int num_tiles;  // ceil(rows / 128) * n_ntiles
   int stages;
   int tmem_cols;
   int last;       // 0: write planes for the next pass; 1: write FP32 results to out0
@@ -231,9 +233,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int t = blockIdx.x; t < P.num_tiles; t += gridDim.x) {
       if (!mbar_wait(&tfull[buf], aph, P.status, 4)) break;
       tc_fence_after();
-      const int64_t col = (int64_t)(t / P.n_ntiles) * BM + row;
+      const int64_t colb = (int64_t)(t / P.n_ntiles) * BM + row;  // fibre of the batch
       const int r0 = (t % P.n_ntiles) * P.ntile;
-      const bool valid = col < P.M2;
+      const bool valid = colb < P.rows;
+      const int64_t bt = valid ? colb / P.M2 : 0;
+      const int64_t col = colb - bt * P.M2 + bt * P.N;  // tensor b's elements start at b N
       const int cend = P.n - r0 < P.ntile ? P.n - r0 : P.ntile;
       for (int c0 = 0; c0 < cend; c0 += 16) {
         float v[16];
@@ -271,9 +275,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // combination is formed in FP64 only when it has more than one term or a
 // coefficient other than one; the split itself runs in FP32 (the planes carry
 // at most 22 significant bits, FP32 holds 24).
+struct ComboBatch {
+  Combo c[kTcMaxBatch];
+};
+
 template <int KIND, int NP>
-__global__ void tc_split_kernel(Combo in, int64_t N, void* p0, void* p1) {
+__global__ void tc_split_kernel(ComboBatch inb, int64_t N, void* p0, void* p1) {
   pdl_wait();
+  const Combo& in = inb.c[blockIdx.y];
+  const int64_t off = (int64_t)blockIdx.y * N;  // tensor b's elements in the planes
   const bool plain = in.nsrc == 1 && in.coef[0] == 1.0;
   const bool f32 = in.f32mask & 1;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
@@ -290,7 +300,7 @@ __global__ void tc_split_kernel(Combo in, int64_t N, void* p0, void* p1) {
       }
       xf = (float)x;
     }
-    split_store_f<KIND, NP>(p0, p1, idx, xf);
+    split_store_f<KIND, NP>(p0, p1, off + idx, xf);
   }
 }
 
@@ -380,8 +390,9 @@ bool cached_map(TcState* s, CUtensorMap* m, const void* base, uint64_t inner, ui
 }  // namespace
 
 size_t tc_workspace_bytes(int64_t N) {
-  // two plane sets of up to 2 planes x 4 bytes, each rounded to 1 KiB
-  const size_t plane = ((size_t)N * 4 + 1023) / 1024 * 1024;
+  // two plane sets of up to 2 planes x 4 bytes for kTcMaxBatch tensors, each
+  // rounded to 1 KiB
+  const size_t plane = ((size_t)kTcMaxBatch * N * 4 + 1023) / 1024 * 1024;
   return 4 * plane + 1024;
 }
 
@@ -490,28 +501,35 @@ cudaError_t run_gemm(TcState* s, const CUtensorMap* mA, const CUtensorMap* mB, G
 
 }  // namespace
 
-cudaError_t tc_tucker(TcState* s, const Combo& in, const void* const* Bp, const Epi& epi,
+cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const void* const* Bp, const Epi* epi,
                       cudaStream_t st) {
+  if (B < 1 || B > kTcMaxBatch) return cudaErrorInvalidValue;
   const int dtype = s->dtype;
   const int NP = planes_of(dtype), elt = elt_of(dtype);
   const int64_t N = s->N;
-  const size_t plane = ((size_t)N * 4 + 1023) / 1024 * 1024;
+  const size_t plane = ((size_t)kTcMaxBatch * N * 4 + 1023) / 1024 * 1024;
   uint8_t* set[2][2] = {{s->ws, s->ws + plane}, {s->ws + 2 * plane, s->ws + 3 * plane}};
-  // split the (combined) input into planes: natural layout, mode 1 contiguous
+  // split the (combined) inputs into planes: natural layout, mode 1
+  // contiguous, tensor b at element b N of every plane
   {
-    const int grid = (int)std::min<int64_t>((N + 255) / 256, 152 * 8);
+    ComboBatch cb;
+    std::memset(&cb, 0, sizeof cb);
+    for (int b = 0; b < B; ++b) cb.c[b] = in[b];
+    const int grid = (int)std::min<int64_t>((N + 255) / 256, 152 * 8 / B);
     count_launch();
     void *q0 = set[0][0], *q1 = set[0][1], *none = nullptr;
+    const dim3 g(grid, B);
     cudaError_t e;
-    if (dtype == PHIKS_BF16X3) e = launch_pdl(tc_split_kernel<0, 2>, dim3(grid), dim3(256), 0, st, in, N, q0, q1);
-    else if (dtype == PHIKS_TF32X3) e = launch_pdl(tc_split_kernel<1, 2>, dim3(grid), dim3(256), 0, st, in, N, q0, q1);
-    else e = launch_pdl(tc_split_kernel<1, 1>, dim3(grid), dim3(256), 0, st, in, N, q0, none);
+    if (dtype == PHIKS_BF16X3) e = launch_pdl(tc_split_kernel<0, 2>, g, dim3(256), 0, st, cb, N, q0, q1);
+    else if (dtype == PHIKS_TF32X3) e = launch_pdl(tc_split_kernel<1, 2>, g, dim3(256), 0, st, cb, N, q0, q1);
+    else e = launch_pdl(tc_split_kernel<1, 1>, g, dim3(256), 0, st, cb, N, q0, none);
     if (e != cudaSuccess) return e;
   }
   int cur = 0;
   for (int mu = 0; mu < s->d; ++mu) {
     const int n = (int)s->n[mu], np = pad16(n);
     const int64_t M2 = N / n;
+    const int64_t rows = (int64_t)B * M2;
     const int nnt = (np + 255) / 256;          // N tiles of at most 256 rows
     const int ntile = pad16((np + nnt - 1) / nnt);
     CUtensorMap mA[2], mB[2];
@@ -519,7 +537,7 @@ cudaError_t tc_tucker(TcState* s, const Combo& in, const void* const* Bp, const 
     std::memset(mB, 0, sizeof mB);
     const size_t bplane = ((size_t)np * np * elt + 1023) / 1024 * 1024;
     for (int p = 0; p < NP; ++p) {
-      if (!cached_map(s, &mA[p], set[cur][p], (uint64_t)n, (uint64_t)M2, BM)) {
+      if (!cached_map(s, &mA[p], set[cur][p], (uint64_t)n, (uint64_t)rows, BM)) {
         g_tc_err = "tensor map for the A operand failed";
         return cudaErrorInvalidValue;
       }
@@ -540,8 +558,10 @@ cudaError_t tc_tucker(TcState* s, const Combo& in, const void* const* Bp, const 
     P.ntile = ntile;
     P.n_ntiles = nnt;
     P.M2 = M2;
+    P.rows = rows;
+    P.N = N;
     P.nk = (n * elt + 127) / 128;
-    P.num_tiles = (int)((M2 + BM - 1) / BM) * nnt;
+    P.num_tiles = (int)((rows + BM - 1) / BM) * nnt;
     int cols = 32;
     while (cols < 2 * ntile) cols <<= 1;
     P.tmem_cols = cols;
@@ -556,16 +576,20 @@ cudaError_t tc_tucker(TcState* s, const Combo& in, const void* const* Bp, const 
     if (e != cudaSuccess) return e;
     cur = 1 - cur;
   }
-  // FP64 epilogue over all N elements with the whole GPU: the result plane is
-  // one more (float) source whose coefficient in output t is epi.b[t]
-  Epi f = epi;
-  const int m = f.nsrc;
-  if (m >= kMaxSrc) return cudaErrorInvalidValue;
-  f.src[m] = (const double*)set[cur][0];
-  f.src_f32mask |= 1 << m;
-  for (int t = 0; t < f.nout; ++t) f.a[t][m] = epi.b[t];
-  f.nsrc = m + 1;
-  return launch_combine(f, N, st);
+  // FP64 epilogues over all N elements of each tensor with the whole GPU: the
+  // result plane is one more (float) source whose coefficient in output t is
+  // epi.b[t]
+  Epi f[kTcMaxBatch];
+  for (int b = 0; b < B; ++b) {
+    f[b] = epi[b];
+    const int m = f[b].nsrc;
+    if (m >= kMaxSrc) return cudaErrorInvalidValue;
+    f[b].src[m] = (const double*)((const float*)set[cur][0] + (int64_t)b * N);
+    f[b].src_f32mask |= 1 << m;
+    for (int t = 0; t < f[b].nout; ++t) f[b].a[t][m] = epi[b].b[t];
+    f[b].nsrc = m + 1;
+  }
+  return launch_combine_batch(f, B, N, st);
 }
 
 int tc_read_status(TcState* s, cudaStream_t st) {

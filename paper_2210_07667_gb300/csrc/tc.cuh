@@ -19,7 +19,10 @@ namespace phiks {
 
 struct TcState;
 
-// Bytes of workspace the split path needs for tensors of N elements.
+// Tucker operators one tc_tucker call runs together.
+constexpr int kTcMaxBatch = 4;
+
+// Bytes of workspace the split path needs for kTcMaxBatch tensors of N elements.
 size_t tc_workspace_bytes(int64_t N);
 
 phiks_status tc_create(TcState** out, int dtype, int d, const int64_t* n, int64_t N);
@@ -33,10 +36,12 @@ void tc_bind_workspace(TcState* s, void* ws);
 size_t tc_bplanes_bytes(int dtype, int n);
 cudaError_t tc_prepare_b(int dtype, const double* L, int n, void* dst, cudaStream_t st);
 
-// W = (combination `in`) x_1 L_1 ... x_d L_d through `epi` (FP64 arithmetic in
-// the epilogue; outputs double or float as its masks say).  Bp[mu] are B planes
-// made by tc_prepare_b for L_mu.
-cudaError_t tc_tucker(TcState* s, const Combo& in, const void* const* Bp, const Epi& epi,
+// B <= kTcMaxBatch Tucker operators with the same matrices, run together:
+// W_b = (combination in[b]) x_1 L_1 ... x_d L_d through epi[b] (FP64
+// arithmetic in the epilogue; outputs double or float as its masks say).
+// Every pass treats the B tensors as one tensor with B times the fibres.
+// Bp[mu] are B planes made by tc_prepare_b for L_mu.
+cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const void* const* Bp, const Epi* epi,
                       cudaStream_t st);
 
 // Device-side status: 0, or the code of a bounded wait that gave up (the
