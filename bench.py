@@ -395,6 +395,15 @@ def run_phiks(args):
         line["cpu_baseline"] = {"value": wl.nscales / dt, "unit": "phi-actions/s",
                                 "cores": oracle_threads(), "kind": "oracle",
                                 "sample": "one full call (3 scale outputs), O3 Taylor action, %.1f s" % dt}
+        # context only: the paper's method itself (the oracle's step-by-step
+        # restatement, numpy BLAS mode products) on the host cores, same (s, q)
+        from oracle import phiks_ref
+        t0 = time.perf_counter()
+        phiks_ref.lincomb(wl.A, wl.tau, wl.vs, s_, q_, nscales=wl.nscales)
+        dtp = time.perf_counter() - t0
+        line["cpu_phiks_context"] = {"value": wl.nscales / dtp, "unit": "phi-actions/s",
+                                     "cores": oracle_threads(), "s": s_, "q": q_,
+                                     "note": "phiks restated step by step in numpy (FP64), one call"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
