@@ -413,9 +413,9 @@ def run_phiks(args):
 
 
 # ---------------------------------------------------------------------------
-PRECISION_DTYPES = ["fp64", "tf32", "tf32x3", "bf16x3"]
+PRECISION_DTYPES = ["fp64", "fp64emu", "tf32", "tf32x3", "bf16x3"]
 # relative accuracy asked of the selection per dtype (tol = rel * ||v||)
-PRECISION_TOL = {"fp64": None, "tf32": 1e-4, "tf32x3": 1e-7, "bf16x3": 1e-6}
+PRECISION_TOL = {"fp64": None, "fp64emu": None, "tf32": 1e-4, "tf32x3": 1e-7, "bf16x3": 1e-6}
 
 
 def run_precision(args):
@@ -439,11 +439,11 @@ def run_precision(args):
         dtypes = [d for d in dtypes if d != "fp64"]
     for name in dtypes:
         dt = pk.DTYPES[name]
-        tdt = torch.float64 if name == "fp64" else torch.float32
+        tdt = torch.float64 if name in ("fp64", "fp64emu") else torch.float32
         plan = pk.Plan(wl.A, dt)
         vs = [torch.from_numpy(v).to(device="cuda", dtype=tdt) for v in wl.vs]
         outs = [torch.empty(p * N, device="cuda", dtype=tdt) for _ in vs]
-        norms = [float(np.linalg.norm(v.astype(np.float32) if name != "fp64" else v)) for v in wl.vs]
+        norms = [float(np.linalg.norm(v.astype(np.float32) if tdt == torch.float32 else v)) for v in wl.vs]
         kw = dict(skip_phi0=1)
         if PRECISION_TOL[name] is not None:
             kw["tol"] = PRECISION_TOL[name] * max(norms)
@@ -503,7 +503,7 @@ def run_precision(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": h["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"bf16x3": "bf16x3 (fp32 accumulate)", "tf32": "tf32", "tf32x3": "tf32x3",
-                      "fp64": "f64"}[head],
+                      "fp64": "f64", "fp64emu": "f64 (emulated on tcgen05)"}[head],
             "data": "synthetic",
             "config": {"workload": wl.name, "d": 3, "n": [args.n] * 3, "N": N, "p": 3, "mode": "same",
                        "skip_phi0": True, "nrhs": 8, "tau": tau, "variant": args.variant,
@@ -828,7 +828,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", default="adr3d", choices=["adr3d", "small", "precision", "batched", "served"],
                     help="adr3d: the headline FP64 workload; precision: the split-dtype form")
-    ap.add_argument("--dtype", default="all", choices=["all", "fp64emu"] + PRECISION_DTYPES,
+    ap.add_argument("--dtype", default="all", choices=["all"] + PRECISION_DTYPES,
                     help="precision/batched/served: split dtype; adr3d: FP64-accurate products, "
                          "emulated on the tensor cores (default, or fp64emu) or fp64 (DFMA)")
     ap.add_argument("--variant", default="cheb", choices=["cheb", "fd"])

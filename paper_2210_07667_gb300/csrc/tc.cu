@@ -40,7 +40,8 @@ namespace {
 thread_local std::string g_tc_err;
 
 using namespace ptx;
-constexpr int NTHREADS = 192;
+constexpr int kTcEpiWarps = 16;  // four per TMEM lane quarter, each a quarter of the columns
+constexpr int NTHREADS = 64 + 32 * kTcEpiWarps;
 
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4 * 32);
+      mbar_init(&tempty[b], kTcEpiWarps * 32);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -225,8 +226,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
   } else {
-    // ---------------- epilogue: warps 2..5
+    // ---------------- epilogue: warps 2 .. 2 + kTcEpiWarps - 1; the four
+    // warps of a lane quarter take interleaved 16-column chunks
     const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int grp = (warp - 2) >> 2;
+    constexpr int GROUPS = kTcEpiWarps / 4;
     const int row = q * 32 + lane;
     int buf = 0;
     uint32_t aph = 0;
@@ -239,7 +243,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int64_t bt = valid ? colb / P.M2 : 0;
       const int64_t col = colb - bt * P.M2 + bt * P.N;  // tensor b's elements start at b N
       const int cend = P.n - r0 < P.ntile ? P.n - r0 : P.ntile;
-      for (int c0 = 0; c0 < cend; c0 += 16) {
+      for (int c0 = 16 * grp; c0 < cend; c0 += 16 * GROUPS) {
         float v[16];
         tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * P.ntile + c0), v);
         if (!valid) continue;
