@@ -533,7 +533,7 @@ def run_batched(args):
 
     def setup(dname):
         dt = pk.DTYPES[dname]
-        tdt = torch.float64 if dname == "fp64" else torch.float32
+        tdt = torch.float64 if dname in ("fp64", "fp64emu") else torch.float32
         rows = []
         for w in insts:
             plan = pk.Plan(w.A, dt)
@@ -635,7 +635,7 @@ def build_served(pk, torch, arrivals, specs, dtype_name, tol_rel):
     """Device-resident plans per (class, n, species), seeded inputs per
     (class, n), one output per apply; returns (requests, plans, n_applies)."""
     dt = pk.DTYPES[dtype_name]
-    tdt = torch.float64 if dtype_name == "fp64" else torch.float32
+    tdt = torch.float64 if dtype_name in ("fp64", "fp64emu") else torch.float32
     plans, inputs = {}, {}
     requests = []
     n_applies = 0
