@@ -60,3 +60,14 @@ def test_lincomb_bench_workload_emulated():
     errs = [rel_inf(out[L], ta.lincomb(wl.A, wl.tau, wl.vs, 2.0 ** -L)) for L in range(3)]
     print("emu lincomb errs", ["%.2e" % e for e in errs])
     assert max(errs) < 1e-12
+
+
+def test_lincomb_emulated_ragged_batches():
+    """Batched emulated passes whose 128-fibre tiles straddle the tensors of a
+    batch (960, 640 and 1600 fibres per tensor for the three modes)."""
+    wl = wk.adr3d_lincomb(p=3, dims=(40, 24, 16), nscales=2)
+    out, plan = run_workload(wl, dtype=EMU)
+    pk.phiks_device_status(plan.handle)
+    errs = [rel_inf(out[L], ta.lincomb(wl.A, wl.tau, wl.vs, 2.0 ** -L)) for L in range(2)]
+    print("emu ragged lincomb errs", ["%.2e" % e for e in errs])
+    assert max(errs) < 1e-12

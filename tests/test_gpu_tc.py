@@ -57,7 +57,8 @@ def test_tucker_single_tile(dtype):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("dims", [(64, 48, 40), (128, 16, 24), (96, 200), (16, 16, 16, 8), (256, 136)])
+@pytest.mark.parametrize("dims", [(64, 48, 40), (128, 16, 24), (96, 200), (16, 16, 16, 8), (256, 136),
+                                  (600, 24), (1024, 8)])
 def test_tucker_shapes(dtype, dims):
     if dtype == pk.PHIKS_BF16X3 and any(m % 8 for m in dims):
         pytest.skip("bf16 planes need n_mu % 8 == 0")
