@@ -137,6 +137,14 @@ struct phiks_plan_s {
     int tuckers = 0;
   };
   std::map<std::vector<uint64_t>, CallGraph> graphs;
+  // squaring of the small matrices for the next level, overlapped with the
+  // current level's Tucker operators: one auxiliary stream per caller stream
+  struct Aux {
+    cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+  };
+  std::map<cudaStream_t, Aux> aux;
+  std::mutex aux_mu;
   // profiling: event pairs around mu-mode products
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -719,6 +727,7 @@ void bank_ptrs(const phiks_plan_s* P, const Bank* B, int b, Mats* M) {
 
 // Squaring chain: M <- M^2 for every mode (and the split planes of the result).
 phiks_status square_modes(Ctx& c, Mats& M, int& cur_buf) {
+  // (the launches below go to c.st)
   phiks_plan_s* P = c.P;
   GemmBatch gb = gemm_batch0();
   gb.count = P->d;
@@ -751,6 +760,52 @@ phiks_status square_modes(Ctx& c, Mats& M, int& cur_buf) {
   }
   if (emu_dtype(P)) CK(oz_prepare_b(P->d, srcs, ns, dsts, c.st));
   cur_buf = 1 - cur_buf;
+  return PHIKS_OK;
+}
+
+// Starts Mn = M^2 (the next level's matrices) on the plan's auxiliary stream
+// after everything queued on c.st so far: the buffer it overwrites was last
+// read by the previous level's Tucker operators.  finish_square makes c.st
+// wait for it.  The squaring reads only M and writes only its own buffers,
+// so it runs beside the current level's Tucker operators.  A stream being
+// captured by the caller that has no auxiliary stream yet squares in line
+// (*aside = false): creating a stream could break the caller's capture.
+phiks_status begin_square(Ctx& c, Mats& Mn, int& mbuf, bool* aside) {
+  phiks_plan_s* P = c.P;
+  phiks_plan_s::Aux x;
+  *aside = false;
+  {
+    std::lock_guard<std::mutex> lk(P->aux_mu);
+    auto it = P->aux.find(c.st);
+    if (it == P->aux.end()) {
+      cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+      CK(cudaStreamIsCapturing(c.st, &cap));
+      if (cap != cudaStreamCaptureStatusNone) return square_modes(c, Mn, mbuf);
+      CK(cudaStreamCreateWithFlags(&x.st, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming));
+      it = P->aux.emplace(c.st, x).first;
+    }
+    x = it->second;
+  }
+  CK(cudaEventRecord(x.fork, c.st));
+  CK(cudaStreamWaitEvent(x.st, x.fork, 0));
+  Ctx a = c;
+  a.st = x.st;
+  TRY(square_modes(a, Mn, mbuf));
+  CK(cudaEventRecord(x.join, x.st));
+  *aside = true;
+  return PHIKS_OK;
+}
+
+phiks_status finish_square(Ctx& c, bool aside) {
+  if (!aside) return PHIKS_OK;
+  phiks_plan_s::Aux x;
+  {
+    std::lock_guard<std::mutex> lk(c.P->aux_mu);
+    x = c.P->aux.at(c.st);
+  }
+  CK(cudaStreamWaitEvent(c.st, x.join, 0));
   return PHIKS_OK;
 }
 
@@ -834,6 +889,9 @@ phiks_status run_same(Ctx& c, const Bank* B, int s, int p, const void* v, const 
   if (s < o.nscales) TRY(emit(s));
   const bool batched = c.acc2[0] != nullptr;  // tensor-core paths: the p Tuckers of a level together
   for (int j = s; j >= 1; --j) {
+    Mats Mn = M;  // exp(K/2^(j-1)), squared beside this level's Tuckers
+    bool aside = false;
+    TRY(begin_square(c, Mn, mbuf, &aside));
     // eq. (simul): phi_l(K/2^(j-1)) v = 2^-l (exp(K/2^j) phi_l + sum_k phi_k/(l-k)!), l = p..1
     // (in place from l = p down; batched: every l reads the old values and
     // writes the second set of accumulators, which then become the first)
@@ -860,7 +918,8 @@ phiks_status run_same(Ctx& c, const Bank* B, int s, int p, const void* v, const 
       TRY(tucker_batch(c, p, ins, M, es));
       for (int l = 0; l < p; ++l) std::swap(acc[l], c.acc2[l]);
     }
-    TRY(square_modes(c, M, mbuf));
+    TRY(finish_square(c, aside));
+    M = Mn;
     if (j - 1 < o.nscales) TRY(emit(j - 1));
   }
   return PHIKS_OK;
@@ -951,6 +1010,9 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
   if (s < o.nscales) TRY(emit(s));
   const bool batched = c.acc2[0] != nullptr;  // tensor-core paths: the p Tuckers of a level together
   for (int j = s; j >= 1; --j) {
+    Mats Mn = M;  // exp(K/2^(j-1)), squared beside this level's Tuckers
+    bool aside = false;
+    TRY(begin_square(c, Mn, mbuf, &aside));
     // eq. (comb), l = p..1 in place; batched: from the old values into the
     // second set of accumulators, which then become the first
     Combo ins[PHIKS_MAX_P];
@@ -976,7 +1038,8 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
       TRY(tucker_batch(c, p, ins, M, es));
       for (int l = 0; l < p; ++l) std::swap(acc[l], c.acc2[l]);
     }
-    TRY(square_modes(c, M, mbuf));
+    TRY(finish_square(c, aside));
+    M = Mn;
     if (j - 1 < o.nscales) TRY(emit(j - 1));
   }
   return PHIKS_OK;
@@ -1285,6 +1348,11 @@ void phiks_destroy(phiks_plan_t P) {
   cudaDeviceSynchronize();
   for (auto e : P->ev_pool) cudaEventDestroy(e);
   drop_graphs(P);
+  for (auto& a : P->aux) {
+    cudaStreamDestroy(a.second.st);
+    cudaEventDestroy(a.second.fork);
+    cudaEventDestroy(a.second.join);
+  }
   for (auto& b : P->banks) {
     cudaFree(b.dev);
     if (b.tcb) cudaFree(b.tcb);
