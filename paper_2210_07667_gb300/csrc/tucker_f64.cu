@@ -318,6 +318,48 @@ __global__ void combine_batch_kernel(EpiBatch eb, int64_t N) {
     epi_apply(e, idx, 0.0);
 }
 
+// The common case of one FP64 output from FP64 sources: out = sum_k c_k src_k,
+// two elements per thread with 16-byte loads, no local arrays.
+struct Lin1 {
+  int nterm;
+  const double* src[kMaxSrc];
+  double c[kMaxSrc];
+  double* out;
+};
+struct Lin1Batch {
+  Lin1 l[kMaxEpiBatch];
+};
+
+__global__ void lincomb1_kernel(Lin1Batch lb, int64_t N2) {
+  pdl_wait();
+  const Lin1& L = lb.l[blockIdx.y];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N2;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double ox = 0.0, oy = 0.0;
+    for (int k = 0; k < L.nterm; ++k) {
+      const double2 x = __ldg(reinterpret_cast<const double2*>(L.src[k]) + i);
+      ox = fma(L.c[k], x.x, ox);
+      oy = fma(L.c[k], x.y, oy);
+    }
+    reinterpret_cast<double2*>(L.out)[i] = make_double2(ox, oy);
+  }
+}
+
+// One combination as a Lin1 when it has a single FP64 output, FP64 sources,
+// no product term and 16-byte aligned pointers (N even).
+bool as_lin1(const Epi& e, int64_t N, Lin1* l) {
+  if (e.nout != 1 || e.bnz || e.out_f32mask || e.src_f32mask || (N & 1)) return false;
+  if (((uintptr_t)e.out[0] & 15) != 0) return false;
+  l->nterm = e.nterm;
+  l->out = e.out[0];
+  for (int k = 0; k < e.nterm; ++k) {
+    l->src[k] = e.src[e.term_m[k]];
+    l->c[k] = e.term_c[k];
+    if (((uintptr_t)l->src[k] & 15) != 0) return false;
+  }
+  return true;
+}
+
 __global__ void combine_kernel(Epi e, int64_t N) {
   pdl_wait();
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
@@ -399,12 +441,20 @@ cudaError_t launch_combine_batch(const Epi* e0, int B, int64_t N, cudaStream_t s
   if (N <= 0 || B <= 0) return cudaSuccess;
   if (B > kMaxEpiBatch) return cudaErrorInvalidValue;
   EpiBatch eb;
+  Lin1Batch lb;
+  bool lin = true;
   for (int b = 0; b < B; ++b) {
     eb.e[b] = e0[b];
     for (int t = 0; t < kMaxOut; ++t) eb.e[b].b[t] = 0.0;  // no product result here
     epi_finalize(eb.e[b]);
+    lin = lin && as_lin1(eb.e[b], N, &lb.l[b]);
   }
   count_launch();
+  if (lin) {
+    int gx = grid_for(N / 2, 256) / B;
+    if (gx < 1) gx = 1;
+    return launch_pdl(lincomb1_kernel, dim3(gx, B), dim3(256), 0, st, lb, N / 2);
+  }
   int gx = grid_for(N, 256) / B;
   if (gx < 1) gx = 1;
   return launch_pdl(combine_batch_kernel, dim3(gx, B), dim3(256), 0, st, eb, N);
@@ -416,6 +466,11 @@ cudaError_t launch_combine(const Epi& e0, int64_t N, cudaStream_t st) {
   e.nout = e0.nout;
   for (int t = 0; t < kMaxOut; ++t) e.b[t] = 0.0;  // no product result here
   epi_finalize(e);
+  Lin1Batch lb;
+  if (as_lin1(e, N, &lb.l[0])) {
+    count_launch();
+    return launch_pdl(lincomb1_kernel, dim3(grid_for(N / 2, 256)), dim3(256), 0, st, lb, N / 2);
+  }
   count_launch();
   return launch_pdl(combine_kernel, dim3(grid_for(N, 256)), dim3(256), 0, st, e, N);
 }
