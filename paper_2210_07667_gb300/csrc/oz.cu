@@ -484,15 +484,16 @@ struct OzState {
   int* status = nullptr;
   uint8_t* ws = nullptr;
   double* tmp[2] = {nullptr, nullptr};
+  int batch = 0;  // tensors the bound workspace holds
   int smem_optin = 0;
   std::map<std::tuple<const void*, uint64_t, uint64_t, uint32_t, uint64_t>, CUtensorMap> maps;
 };
 
-// Digit planes and fibre exponents of kOzMaxBatch tensors.
-size_t oz_workspace_bytes(int d, const int64_t* n, int64_t N) {
+// Digit planes and fibre exponents of `batch` tensors.
+size_t oz_workspace_bytes(int d, const int64_t* n, int64_t N, int batch) {
   int64_t m2 = 0;
   for (int mu = 0; mu < d; ++mu) m2 = std::max<int64_t>(m2, N / n[mu]);
-  return up1k((size_t)kOzSlices * kOzMaxBatch * N * 2) + up1k((size_t)kOzMaxBatch * m2 * 4) + 1024;
+  return up1k((size_t)kOzSlices * batch * N * 2) + up1k((size_t)batch * m2 * 4) + 1024;
 }
 
 phiks_status oz_create(OzState** out, int d, const int64_t* n, int64_t N) {
@@ -536,8 +537,9 @@ void oz_destroy(OzState* s) {
 
 const char* oz_last_error() { return g_oz_err.c_str(); }
 
-void oz_bind_workspace(OzState* s, void* ws, double* tmp0, double* tmp1) {
+void oz_bind_workspace(OzState* s, void* ws, double* tmp0, double* tmp1, int batch) {
   s->ws = (uint8_t*)ws;
+  s->batch = batch;
   s->tmp[0] = tmp0;
   s->tmp[1] = tmp1;
 }
@@ -608,9 +610,9 @@ bool cached(OzState* s, CUtensorMap* m, const void* base, uint64_t inner, uint64
 
 cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const void* const* Bp, const Epi* epi,
                       cudaStream_t st, const cudaEvent_t* ev) {
-  if (B < 1 || B > kOzMaxBatch) return cudaErrorInvalidValue;
+  if (B < 1 || B > s->batch || s->batch > kOzMaxBatch) return cudaErrorInvalidValue;
   const int64_t N = s->N;
-  const int64_t PS = (int64_t)kOzMaxBatch * N;  // elements between digit planes
+  const int64_t PS = (int64_t)s->batch * N;  // elements between digit planes
   __nv_bfloat16* planes = (__nv_bfloat16*)s->ws;
   int* xscale = (int*)(s->ws + up1k((size_t)kOzSlices * PS * 2));
   ComboBatch cur;

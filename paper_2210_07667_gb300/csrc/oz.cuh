@@ -27,13 +27,14 @@ struct OzState;
 
 constexpr int kOzSlices = 7;
 constexpr int kOzMaxN = 128;
-constexpr int kOzMaxBatch = 4;  // Tucker operators one oz_tucker call runs together
+constexpr int kOzMaxBatch = 8;  // Tucker operators one oz_tucker call can run together
 
-size_t oz_workspace_bytes(int d, const int64_t* n, int64_t N);
+// Workspace of oz_tucker for batches of up to `batch` (<= kOzMaxBatch) tensors.
+size_t oz_workspace_bytes(int d, const int64_t* n, int64_t N, int batch);
 phiks_status oz_create(OzState** out, int d, const int64_t* n, int64_t N);
 void oz_destroy(OzState* s);
 const char* oz_last_error();
-void oz_bind_workspace(OzState* s, void* ws, double* tmp0, double* tmp1);
+void oz_bind_workspace(OzState* s, void* ws, double* tmp0, double* tmp1, int batch);
 
 // Bytes of the B-operand slices of one n x n matrix (7 planes of n_pad x
 // n_pad bf16 and n_pad row exponents), and their preparation from FP64
@@ -42,12 +43,12 @@ size_t oz_bplanes_bytes(int n);
 cudaError_t oz_prepare_b(int count, const double* const* L, const int* n, void* const* dst,
                          cudaStream_t st);
 
-// B <= kOzMaxBatch Tucker operators with the same matrices, run together:
-// (combination in[b]) x_1 L_1 ... x_d L_d through epi[b] (FP64), Bp[mu] made
-// by oz_prepare_b for L_mu.  Every pass treats the B tensors as one tensor
-// with B times the fibres.  The workspace bound by oz_bind_workspace holds the
-// digit planes of kOzMaxBatch tensors, and tmp0 / tmp1 kOzMaxBatch N doubles
-// each.  `ev` (2 d events, or null): ev[2 mu] and ev[2 mu + 1] are recorded
+// B Tucker operators with the same matrices, run together (B at most the
+// `batch` given to oz_bind_workspace): (combination in[b]) x_1 L_1 ... x_d L_d
+// through epi[b] (FP64), Bp[mu] made by oz_prepare_b for L_mu.  Every pass
+// treats the B tensors as one tensor with B times the fibres.  The bound
+// workspace holds the digit planes of `batch` tensors, and tmp0 / tmp1
+// batch N doubles each.  `ev` (2 d events, or null): ev[2 mu] and ev[2 mu + 1] are recorded
 // around the tensor-core pass of mode mu.
 cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const void* const* Bp, const Epi* epi,
                       cudaStream_t st, const cudaEvent_t* ev = nullptr);

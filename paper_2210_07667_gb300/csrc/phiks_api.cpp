@@ -209,10 +209,12 @@ struct WsLayout {
 };
 
 // Tucker operators the tensor-core paths run together (one for the FP64
-// pipe); their Tucker temporaries and second set of accumulators are sized
-// for them.
-int tucker_batch_max(const phiks_plan_s* P) {
-  return emu_dtype(P) ? kOzMaxBatch : (split_dtype(P) ? kTcMaxBatch : 1);
+// pipe) in an apply with p accumulators; the Tucker temporaries are sized for
+// them.  FP64_EMU: the p operators of a squaring level and the output
+// operator of that level's scale.
+int tucker_batch_max(const phiks_plan_s* P, int p) {
+  if (emu_dtype(P)) return std::min(kOzMaxBatch, std::max(p, 1) + 1);
+  return split_dtype(P) ? kTcMaxBatch : 1;
 }
 
 size_t up1k(size_t x) { return (x + 1023) / 1024 * 1024; }
@@ -226,7 +228,7 @@ WsLayout ws_layout(const phiks_plan_s* P, int p) {
   w.acc2 = o;  // new accumulators of a batched squaring step
   if (tc_path(P)) o += up1k((size_t)std::max(p, 1) * N * 8);
   w.tmp = o;
-  o += up1k(2 * (size_t)tucker_batch_max(P) * N * 8);
+  o += up1k(2 * (size_t)tucker_batch_max(P, p) * N * 8);
   w.msq0 = o;
   o += up1k(P->sum_n2 * 8);
   w.msq1 = o;
@@ -238,7 +240,8 @@ WsLayout ws_layout(const phiks_plan_s* P, int p) {
     w.tcb1 = o;
     o += up1k(P->tcb_bytes);
     w.planes = o;
-    o += up1k(emu_dtype(P) ? oz_workspace_bytes(P->d, P->n, P->N) : tc_workspace_bytes(P->N));
+    o += up1k(emu_dtype(P) ? oz_workspace_bytes(P->d, P->n, P->N, tucker_batch_max(P, p))
+                           : tc_workspace_bytes(P->N));
   }
   w.total = o + 1024;  // room to align the base
   return w;
@@ -561,6 +564,7 @@ struct Ctx {
   cudaStream_t st;
   double* tmp[2];
   int tuckers = 0;
+  int bmax = 1;  // Tucker operators one tensor-core batch may hold
   double* acc2[PHIKS_MAX_P] = {nullptr};  // FP64_EMU: accumulators of batched squaring
   double* msq[2] = {nullptr, nullptr};      // squaring chain ping-pong
   uint8_t* msq_tcb[2] = {nullptr, nullptr}; // split path: their B planes
@@ -575,13 +579,14 @@ void carve(Ctx& c, int p, char* ws, double** acc) {
   if (tc_path(P))
     for (int l = 0; l < std::max(p, 1); ++l) c.acc2[l] = (double*)(base + w.acc2) + (size_t)l * P->NR;
   c.tmp[0] = (double*)(base + w.tmp);
-  c.tmp[1] = c.tmp[0] + (size_t)tucker_batch_max(P) * P->NR;
+  c.bmax = tucker_batch_max(P, p);
+  c.tmp[1] = c.tmp[0] + (size_t)c.bmax * P->NR;
   c.msq[0] = (double*)(base + w.msq0);
   c.msq[1] = (double*)(base + w.msq1);
   if (tc_path(P)) {
     c.msq_tcb[0] = (uint8_t*)(base + w.tcb0);
     c.msq_tcb[1] = (uint8_t*)(base + w.tcb1);
-    if (emu_dtype(P)) oz_bind_workspace(P->oz, (void*)(base + w.planes), c.tmp[0], c.tmp[1]);
+    if (emu_dtype(P)) oz_bind_workspace(P->oz, (void*)(base + w.planes), c.tmp[0], c.tmp[1], c.bmax);
     else tc_bind_workspace(P->tc, (void*)(base + w.planes));
   }
 }
@@ -682,7 +687,7 @@ phiks_status tucker_batch(Ctx& c, int B, const Combo* in, const Mats& M, const E
     for (int b = 0; b < B; ++b) TRY(tucker(c, in[b], M, &epi[b]));
     return PHIKS_OK;
   }
-  const int bmax = tucker_batch_max(P);
+  const int bmax = c.bmax;
   double fl = 0;
   for (int mu = 0; mu < P->d; ++mu) fl += 2.0 * (double)P->N * (double)P->n[mu];
   for (int b0 = 0; b0 < B; b0 += bmax) {
@@ -871,23 +876,32 @@ phiks_status run_same(Ctx& c, const Bank* B, int s, int p, const void* v, const 
   Mats M;
   bank_ptrs(P, B, B->b0, &M);
   int mbuf = 0;
+  auto phi0_epi = [&](int Lv) {  // phi_0 = exp(K/2^Lv) v into the block of scale Lv
+    Epi e = make_epi();
+    e.nout = 1;
+    e.out[0] = (double*)((char*)out + (size_t)Lv * per * N * es);
+    e.out_f32mask = f32 ? 1 : 0;
+    e.b[0] = 1.0;
+    return e;
+  };
+  const bool batched = c.acc2[0] != nullptr;  // tensor-core paths: the p Tuckers of a level together
+  // the phi_0 operator of scale Lv >= 1 runs in the batch of squaring level
+  // Lv, whose matrices it shares
+  const bool join = batched && !o.skip_phi0 && p + 1 <= c.bmax;
   auto emit = [&](int Lv) -> phiks_status {
     char* blk = (char*)out + (size_t)Lv * per * N * es;
     int slot = 0;
     if (!o.skip_phi0) {
-      Epi e = make_epi();  // phi_0 = exp(K/2^Lv) v
-      e.nout = 1;
-      e.out[0] = (double*)blk;
-      e.out_f32mask = f32 ? 1 : 0;
-      e.b[0] = 1.0;
-      TRY(tucker(c, plain(v, f32), M, &e));
+      if (!(join && Lv >= 1)) {  // else in the batch of level Lv
+        Epi e = phi0_epi(Lv);
+        TRY(tucker(c, plain(v, f32), M, &e));
+      }
       slot = 1;
     }
     for (int l = 0; l < p; ++l) TRY(store_acc(c, blk + (size_t)(slot + l) * N * es, acc[l]));
     return PHIKS_OK;
   };
   if (s < o.nscales) TRY(emit(s));
-  const bool batched = c.acc2[0] != nullptr;  // tensor-core paths: the p Tuckers of a level together
   for (int j = s; j >= 1; --j) {
     Mats Mn = M;  // exp(K/2^(j-1)), squared beside this level's Tuckers
     bool aside = false;
@@ -895,8 +909,8 @@ phiks_status run_same(Ctx& c, const Bank* B, int s, int p, const void* v, const 
     // eq. (simul): phi_l(K/2^(j-1)) v = 2^-l (exp(K/2^j) phi_l + sum_k phi_k/(l-k)!), l = p..1
     // (in place from l = p down; batched: every l reads the old values and
     // writes the second set of accumulators, which then become the first)
-    Combo ins[PHIKS_MAX_P];
-    Epi es[PHIKS_MAX_P];
+    Combo ins[PHIKS_MAX_P + 1];
+    Epi es[PHIKS_MAX_P + 1];
     for (int l = p; l >= 1; --l) {
       Epi e = make_epi();
       e.nout = 1;
@@ -915,7 +929,12 @@ phiks_status run_same(Ctx& c, const Bank* B, int s, int p, const void* v, const 
       }
     }
     if (batched) {
-      TRY(tucker_batch(c, p, ins, M, es));
+      int nb = p;
+      if (join && j < o.nscales) {
+        ins[nb] = plain(v, f32);
+        es[nb++] = phi0_epi(j);
+      }
+      TRY(tucker_batch(c, nb, ins, M, es));
       for (int l = 0; l < p; ++l) std::swap(acc[l], c.acc2[l]);
     }
     TRY(finish_square(c, aside));
@@ -986,20 +1005,31 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
   Mats M;
   bank_ptrs(P, B, B->b0, &M);
   int mbuf = 0;
+  auto out_epi = [&](int Lv) {  // exp(K/2^Lv) v_0 + Phi_Lv v_{1..p} into the block of scale Lv
+    Epi e = make_epi();
+    e.nout = 1;
+    e.out[0] = (double*)((char*)out + (size_t)Lv * N * es);
+    e.out_f32mask = f32 ? 1 : 0;
+    e.b[0] = 1.0;
+    if (p > 0) {
+      e.nsrc = 1;
+      e.src[0] = acc[p - 1];
+      e.a[0][0] = 1.0;
+    }
+    return e;
+  };
+  const bool batched = c.acc2[0] != nullptr;  // tensor-core paths: the p Tuckers of a level together
+  // the output operator of scale Lv >= 1 runs in the batch of squaring level
+  // Lv: it shares that level's matrices and reads acc[p-1] before the level's
+  // results replace it
+  const bool join = batched && v[0] && p + 1 <= c.bmax;
   auto emit = [&](int Lv) -> phiks_status {
     char* blk = (char*)out + (size_t)Lv * N * es;
-    if (v[0]) {  // exp(K/2^Lv) v_0 + Phi_Lv v_{1..p}
-      Epi e = make_epi();
-      e.nout = 1;
-      e.out[0] = (double*)blk;
-      e.out_f32mask = f32 ? 1 : 0;
-      e.b[0] = 1.0;
-      if (p > 0) {
-        e.nsrc = 1;
-        e.src[0] = acc[p - 1];
-        e.a[0][0] = 1.0;
+    if (v[0]) {
+      if (!(join && Lv >= 1)) {  // else in the batch of level Lv
+        Epi e = out_epi(Lv);
+        TRY(tucker(c, plain(v[0], f32), M, &e));
       }
-      TRY(tucker(c, plain(v[0], f32), M, &e));
     } else if (p > 0) {
       TRY(store_acc(c, blk, acc[p - 1]));
     } else {
@@ -1008,15 +1038,14 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
     return PHIKS_OK;
   };
   if (s < o.nscales) TRY(emit(s));
-  const bool batched = c.acc2[0] != nullptr;  // tensor-core paths: the p Tuckers of a level together
   for (int j = s; j >= 1; --j) {
     Mats Mn = M;  // exp(K/2^(j-1)), squared beside this level's Tuckers
     bool aside = false;
     TRY(begin_square(c, Mn, mbuf, &aside));
     // eq. (comb), l = p..1 in place; batched: from the old values into the
     // second set of accumulators, which then become the first
-    Combo ins[PHIKS_MAX_P];
-    Epi es[PHIKS_MAX_P];
+    Combo ins[PHIKS_MAX_P + 1];
+    Epi es[PHIKS_MAX_P + 1];
     for (int l = p; l >= 1; --l) {
       Epi e = make_epi();
       e.nout = 1;
@@ -1035,7 +1064,12 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
       }
     }
     if (batched) {
-      TRY(tucker_batch(c, p, ins, M, es));
+      int nb = p;
+      if (join && j < o.nscales) {
+        ins[nb] = plain(v[0], f32);
+        es[nb++] = out_epi(j);
+      }
+      TRY(tucker_batch(c, nb, ins, M, es));
       for (int l = 0; l < p; ++l) std::swap(acc[l], c.acc2[l]);
     }
     TRY(finish_square(c, aside));
