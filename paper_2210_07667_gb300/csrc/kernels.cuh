@@ -109,7 +109,8 @@ cudaError_t launch_mode_product_c128(const Combo& pro, const double* L, ModeGeom
 // out[t][i] = sum_m a[t][m] src[m][i] over N elements (Epi with b ignored),
 // FP64 arithmetic; sources and outputs double or float as the masks say.
 cudaError_t launch_combine(const Epi& e, int64_t N, cudaStream_t st);
-// B <= 8 independent combinations over N elements each, in one launch.
+// B <= kMaxEpiBatch independent combinations over N elements each, in one launch.
+constexpr int kMaxEpiBatch = 8;
 cudaError_t launch_combine_batch(const Epi* e, int B, int64_t N, cudaStream_t st);
 
 // out[k] = ||x_k||_2^2 accumulated (out must be zeroed), k < count; x_k double

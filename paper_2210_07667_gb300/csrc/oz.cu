@@ -99,7 +99,8 @@ struct ComboBatch {
 // a block holds `fpb` whole fibres (n / 8 threads each), whose exponents meet
 // in shared memory.  Plane s of tensor b starts at planes + s * PS + b * N;
 // the fibre exponents of tensor b at scale + b * M2.
-__global__ void __launch_bounds__(kSplitThreads) oz_split_kernel(ComboBatch inb, int n, int64_t M2, int fpb,
+__global__ void __launch_bounds__(kSplitThreads) oz_split_kernel(const __grid_constant__ ComboBatch inb, int n,
+                                                                 int64_t M2, int fpb,
                                                                  __nv_bfloat16* planes, int64_t N,
                                                                  int64_t PS, int* scale) {
   __shared__ int emax[kSplitThreads];
@@ -238,8 +239,14 @@ struct OzParams {
   int nbuf;       // TMEM accumulator sets (1 or 2)
   double* out;    // FP64 result of tensor b, rotated layout: out[b N + m + M2 i]
   const int* xscale;
-  const int* lscale;
+  int mixed;      // tensors with their own matrices (every tile within one tensor)
+  const int* lscale[kOzMaxBatch];  // row exponents of tensor b's matrix (entry 0 unless mixed)
   int* status;
+};
+
+// TMA maps of the B digit planes: of tensor b's matrix (entry 0 unless mixed).
+struct OzMaps {
+  CUtensorMap b[kOzMaxBatch];
 };
 
 constexpr int kOzEpiWarps = 16;
@@ -260,8 +267,8 @@ constexpr int NTH = 64 + 32 * kOzEpiWarps;
 
 template <int NT>
 __global__ void __launch_bounds__(NTH, 1)
-    oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                   OzParams P) {
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ OzMaps mapsB,
+                   const __grid_constant__ OzParams P) {
   static_assert(kOzSlices * NT <= 256 && (kOzSlices * NT) % 16 == 0, "MMA N out of range");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -307,6 +314,7 @@ __global__ void __launch_bounds__(NTH, 1)
       for (int t = blockIdx.x; t < P.num_tiles; t += gridDim.x) {
         const int m0 = (t / P.n_ntiles) * BM;
         const int r0 = (t % P.n_ntiles) * NT;
+        const CUtensorMap* mapB = &mapsB.b[P.mixed ? (int)(m0 / P.M2) : 0];
         bool ok = true;
         for (int kc = 0; kc < P.nk; ++kc) {
           if (!mbar_wait(empty, ph ^ 1, P.status, 11)) {
@@ -316,7 +324,7 @@ __global__ void __launch_bounds__(NTH, 1)
           mbar_arrive_expect_tx(fullB, kOzSlices * B_SLICE);
 #pragma unroll 1
           for (int s = 0; s < kOzSlices; ++s)
-            tma_load_3d(smem + kOzSlices * A_SLICE + s * B_SLICE, &mapB, fullB, kc * 64, r0, s);
+            tma_load_3d(smem + kOzSlices * A_SLICE + s * B_SLICE, mapB, fullB, kc * 64, r0, s);
 #pragma unroll 1
           for (int s = 0; s < kOzSlices; ++s) {
             mbar_arrive_expect_tx(&fullA[s], A_SLICE);
@@ -393,6 +401,7 @@ __global__ void __launch_bounds__(NTH, 1)
       const int64_t bt = valid ? rg / P.M2 : 0;
       double* const outb = P.out + bt * P.N;
       const int64_t m = rg - bt * P.M2;
+      const int* const lscale = P.lscale[P.mixed ? bt : 0];
 #pragma unroll 1
       for (int c0 = grp * CW; c0 < (grp + 1) * CW; c0 += CH) {
         const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * SET + (uint32_t)c0;
@@ -409,7 +418,7 @@ __global__ void __launch_bounds__(NTH, 1)
           uint32_t g[kOzSlices];
 #pragma unroll
           for (int k = 0; k < kOzSlices; ++k) g[k] = G[k][j];
-          r[j] = oz_assemble(g, sx + P.lscale[r0 + c0 + j] - 48);
+          r[j] = oz_assemble(g, sx + lscale[r0 + c0 + j] - 48);
         }
 #pragma unroll
         for (int j = 0; j < CH; ++j)
@@ -572,7 +581,7 @@ cudaError_t oz_prepare_b(int count, const double* const* L, const int* n, void* 
 namespace {
 
 template <int NT>
-cudaError_t run_oz_gemm(OzState* s, const CUtensorMap& mA, const CUtensorMap& mB, OzParams& P,
+cudaError_t run_oz_gemm(OzState* s, const CUtensorMap& mA, const OzMaps& mB, const OzParams& P,
                         cudaStream_t st) {
   constexpr uint32_t STAGE = kOzSlices * (BM * 128 + NT * 128);
   const size_t smem = STAGE + 1024 + 256;  // alignment slack, barriers
@@ -608,9 +617,20 @@ bool cached(OzState* s, CUtensorMap* m, const void* base, uint64_t inner, uint64
 
 }  // namespace
 
-cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const void* const* Bp, const Epi* epi,
-                      cudaStream_t st, const cudaEvent_t* ev) {
+bool oz_mixed_ok(const OzState* s) {
+  for (int mu = 0; mu < s->d; ++mu)
+    if ((s->N / s->n[mu]) % BM != 0) return false;
+  return true;
+}
+
+cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, const Epi* epi,
+                      cudaStream_t st, const cudaEvent_t* ev, const double** res) {
   if (B < 1 || B > s->batch || s->batch > kOzMaxBatch) return cudaErrorInvalidValue;
+  bool mixed = false;
+  for (int b = 1; b < B; ++b)
+    for (int mu = 0; mu < s->d; ++mu) mixed = mixed || mats[b].B[mu] != mats[0].B[mu];
+  if (mixed && !oz_mixed_ok(s)) return cudaErrorInvalidValue;
+  const int nmat = mixed ? B : 1;
   const int64_t N = s->N;
   const int64_t PS = (int64_t)s->batch * N;  // elements between digit planes
   __nv_bfloat16* planes = (__nv_bfloat16*)s->ws;
@@ -633,17 +653,23 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const void* const* Bp,
     }
     const int np = (n + 63) / 64 * 64;
     const int NT = ntile_for(n, rows);
-    const uint8_t* bpl = (const uint8_t*)Bp[mu];
-    const int* lscale = (const int*)(bpl + up1k((size_t)kOzSlices * np * np * 2));
-    CUtensorMap mA, mB;
-    if (!cached(s, &mA, planes, (uint64_t)n, (uint64_t)rows, BM, (uint64_t)PS) ||
-        !cached(s, &mB, bpl, (uint64_t)np, (uint64_t)np, (uint32_t)NT, (uint64_t)np * np)) {
+    OzParams P;
+    std::memset(&P, 0, sizeof P);
+    OzMaps mB;
+    CUtensorMap mA;
+    if (!cached(s, &mA, planes, (uint64_t)n, (uint64_t)rows, BM, (uint64_t)PS)) {
       g_oz_err = "tensor map encoding failed";
       return cudaErrorInvalidValue;
     }
+    for (int b = 0; b < nmat; ++b) {
+      const uint8_t* bpl = (const uint8_t*)mats[b].B[mu];
+      P.lscale[b] = (const int*)(bpl + up1k((size_t)kOzSlices * np * np * 2));
+      if (!cached(s, &mB.b[b], bpl, (uint64_t)np, (uint64_t)np, (uint32_t)NT, (uint64_t)np * np)) {
+        g_oz_err = "tensor map encoding failed";
+        return cudaErrorInvalidValue;
+      }
+    }
     dst = s->tmp[mu & 1];
-    OzParams P;
-    std::memset(&P, 0, sizeof P);
     P.n = n;
     P.n_pad = np;
     P.M2 = M2;
@@ -658,7 +684,7 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const void* const* Bp,
     P.tmem_cols = cols;
     P.out = dst;
     P.xscale = xscale;
-    P.lscale = lscale;
+    P.mixed = mixed ? 1 : 0;
     P.status = s->status;
     if (ev) {
       cudaError_t e = cudaEventRecord(ev[2 * mu], st);
@@ -677,6 +703,8 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const void* const* Bp,
       cur.c[b].coef[0] = 1.0;
     }
   }
+  if (res) *res = dst;
+  if (!epi) return cudaSuccess;
   // the Tucker operators' epilogues over their N elements with the whole GPU
   Epi f[kOzMaxBatch];
   for (int b = 0; b < B; ++b) {
@@ -687,7 +715,11 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const void* const* Bp,
     for (int t = 0; t < f[b].nout; ++t) f[b].a[t][m] = epi[b].b[t];
     f[b].nsrc = m + 1;
   }
-  return launch_combine_batch(f, B, N, st);
+  for (int b0 = 0; b0 < B; b0 += kMaxEpiBatch) {
+    cudaError_t e = launch_combine_batch(f + b0, std::min(kMaxEpiBatch, B - b0), N, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 int oz_read_status(OzState* s, cudaStream_t st) {

@@ -27,7 +27,7 @@ struct OzState;
 
 constexpr int kOzSlices = 7;
 constexpr int kOzMaxN = 128;
-constexpr int kOzMaxBatch = 8;  // Tucker operators one oz_tucker call can run together
+constexpr int kOzMaxBatch = 16;  // Tucker operators one oz_tucker call can run together
 
 // Workspace of oz_tucker for batches of up to `batch` (<= kOzMaxBatch) tensors.
 size_t oz_workspace_bytes(int d, const int64_t* n, int64_t N, int batch);
@@ -43,15 +43,28 @@ size_t oz_bplanes_bytes(int n);
 cudaError_t oz_prepare_b(int count, const double* const* L, const int* n, void* const* dst,
                          cudaStream_t st);
 
-// B Tucker operators with the same matrices, run together (B at most the
-// `batch` given to oz_bind_workspace): (combination in[b]) x_1 L_1 ... x_d L_d
-// through epi[b] (FP64), Bp[mu] made by oz_prepare_b for L_mu.  Every pass
-// treats the B tensors as one tensor with B times the fibres.  The bound
-// workspace holds the digit planes of `batch` tensors, and tmp0 / tmp1
-// batch N doubles each.  `ev` (2 d events, or null): ev[2 mu] and ev[2 mu + 1] are recorded
-// around the tensor-core pass of mode mu.
-cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const void* const* Bp, const Epi* epi,
-                      cudaStream_t st, const cudaEvent_t* ev = nullptr);
+// The B-operand planes (made by oz_prepare_b) of the d matrices of one Tucker
+// operator.
+struct OzMats {
+  const void* B[PHIKS_MAX_D];
+};
+
+// Whether the tensors of one oz_tucker call may have different matrices:
+// every mode's fibre count N / n_mu a multiple of 128 (no tile spans two
+// tensors).
+bool oz_mixed_ok(const OzState* s);
+
+// B Tucker operators run together (B at most the `batch` given to
+// oz_bind_workspace): (combination in[b]) x_1 L_1 ... x_d L_d with the
+// matrices mats[b] (the same for every b, or oz_mixed_ok), then through
+// epi[b] (FP64).  Every pass treats the B tensors as one tensor with B times
+// the fibres.  The bound workspace holds the digit planes of `batch` tensors,
+// and tmp0 / tmp1 batch N doubles each.  With epi == nullptr no epilogue
+// runs and *res receives the B results (tensor b at *res + b N, valid until
+// the next call).  `ev` (2 d events, or null): ev[2 mu] and ev[2 mu + 1] are
+// recorded around the tensor-core pass of mode mu.
+cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, const Epi* epi,
+                      cudaStream_t st, const cudaEvent_t* ev = nullptr, const double** res = nullptr);
 
 int oz_read_status(OzState* s, cudaStream_t st);
 

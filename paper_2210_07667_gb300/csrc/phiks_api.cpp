@@ -210,10 +210,16 @@ struct WsLayout {
 
 // Tucker operators the tensor-core paths run together (one for the FP64
 // pipe) in an apply with p accumulators; the Tucker temporaries are sized for
-// them.  FP64_EMU: the p operators of a squaring level and the output
-// operator of that level's scale.
+// them.  FP64_EMU: up to kOzMaxBatch (the operators of several quadrature
+// nodes) while their digit planes and temporaries (about 38 bytes per element
+// and operator) stay within 2 GiB, and never fewer than the p operators of a
+// squaring level and the output operator of that level's scale.
 int tucker_batch_max(const phiks_plan_s* P, int p) {
-  if (emu_dtype(P)) return std::min(kOzMaxBatch, std::max(p, 1) + 1);
+  if (emu_dtype(P)) {
+    const int64_t by_mem = ((int64_t)2 << 30) / (38 * std::max<int64_t>(P->N, 1));
+    const int64_t floor_p = std::min(kOzMaxBatch, std::max(p, 1) + 1);
+    return (int)std::max<int64_t>(floor_p, std::min<int64_t>(kOzMaxBatch, by_mem));
+  }
   return split_dtype(P) ? kTcMaxBatch : 1;
 }
 
@@ -638,7 +644,9 @@ phiks_status tucker(Ctx& c, const Combo& in, const Mats& M, const Epi* epi) {
     const bool prof = P->prof;
     if (prof)
       for (int mu = 0; mu < P->d; ++mu) TRY(prof_pair(P, &ev[2 * mu], &ev[2 * mu + 1]));
-    cudaError_t e = oz_tucker(P->oz, 1, &in, M.B, epi, c.st, prof ? ev : nullptr);
+    OzMats om;
+    for (int mu = 0; mu < P->d; ++mu) om.B[mu] = M.B[mu];
+    cudaError_t e = oz_tucker(P->oz, 1, &in, &om, epi, c.st, prof ? ev : nullptr);
     if (e != cudaSuccess)
       return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), oz_last_error());
     if (prof)
@@ -698,7 +706,10 @@ phiks_status tucker_batch(Ctx& c, int B, const Combo* in, const Mats& M, const E
       cudaEvent_t ev[2 * PHIKS_MAX_D];
       if (prof)
         for (int mu = 0; mu < P->d; ++mu) TRY(prof_pair(P, &ev[2 * mu], &ev[2 * mu + 1]));
-      e = oz_tucker(P->oz, nb, in + b0, M.B, epi + b0, c.st, prof ? ev : nullptr);
+      OzMats om[kOzMaxBatch];
+      for (int b = 0; b < nb; ++b)
+        for (int mu = 0; mu < P->d; ++mu) om[b].B[mu] = M.B[mu];
+      e = oz_tucker(P->oz, nb, in + b0, om, epi + b0, c.st, prof ? ev : nullptr);
       if (prof) P->prof_flops += nb * fl;
     } else {  // events around the whole batch
       cudaEvent_t e1;
@@ -711,6 +722,35 @@ phiks_status tucker_batch(Ctx& c, int B, const Combo* in, const Mats& M, const E
                   emu_dtype(P) ? oz_last_error() : tc_last_error());
     c.tuckers += nb;
   }
+  return PHIKS_OK;
+}
+
+// FP64_EMU with oz_mixed_ok: B <= c.bmax Tucker operators with their own
+// matrices M[b] in one batch, no epilogue; *res receives the results (tensor
+// b at *res + b N) for the caller's combination.
+phiks_status tucker_mixed(Ctx& c, int B, const Combo* in, const Mats* M, const double** res) {
+  phiks_plan_s* P = c.P;
+  if (B < 1 || B > c.bmax) return fail(PHIKS_ERR_INVALID, "mixed batch of %d", B);
+  OzMats om[kOzMaxBatch];
+  for (int b = 0; b < B; ++b)
+    for (int mu = 0; mu < P->d; ++mu) om[b].B[mu] = M[b].B[mu];
+  const bool prof = P->prof;
+  cudaEvent_t ev[2 * PHIKS_MAX_D];
+  if (prof)
+    for (int mu = 0; mu < P->d; ++mu) TRY(prof_pair(P, &ev[2 * mu], &ev[2 * mu + 1]));
+  cudaError_t e = oz_tucker(P->oz, B, in, om, nullptr, c.st, prof ? ev : nullptr, res);
+  if (e != cudaSuccess)
+    return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), oz_last_error());
+  if (prof)
+    for (int mu = 0; mu < P->d; ++mu) P->prof_flops += 2.0 * B * (double)P->N * (double)P->n[mu];
+  c.tuckers += B;
+  return PHIKS_OK;
+}
+
+// Combinations over N elements, kMaxEpiBatch per launch.
+phiks_status combine_many(Ctx& c, const Epi* e, int count) {
+  for (int k0 = 0; k0 < count; k0 += kMaxEpiBatch)
+    CK(launch_combine_batch(e + k0, std::min(kMaxEpiBatch, count - k0), c.P->NR, c.st));
   return PHIKS_OK;
 }
 
@@ -849,8 +889,45 @@ phiks_status run_same(Ctx& c, const Bank* B, int s, int p, const void* v, const 
   const int q = (int)B->theta.size();
   for (int l = 0; l < p; ++l) CK(cudaMemsetAsync(acc[l], 0, P->NR * 8, c.st));
   // quadrature at K/2^s: phi_l += w_i theta_i^(l-1)/(l-1)! exp((1-theta_i)K/2^s) v
+  // FP64_EMU: the nodes' Tucker operators in batches (each with its node's
+  // matrices), their weighted results summed into the p accumulators
+  const bool mix = emu_dtype(P) && oz_mixed_ok(P->oz) && p > 0;
+  if (mix) {
+    const int per_batch = std::min(c.bmax, kMaxSrc - 1);
+    std::vector<int> nodes;
+    for (int i = 0; i < q; ++i)
+      if (B->node_bank[i] >= 0) nodes.push_back(i);
+    for (size_t k0 = 0; k0 < nodes.size(); k0 += per_batch) {
+      const int nb = (int)std::min<size_t>(per_batch, nodes.size() - k0);
+      Combo ins[kOzMaxBatch];
+      Mats Ls[kOzMaxBatch];
+      for (int k = 0; k < nb; ++k) {
+        ins[k] = plain(v, f32);
+        bank_ptrs(P, B, B->node_bank[nodes[k0 + k]], &Ls[k]);
+      }
+      const double* R = nullptr;
+      TRY(tucker_mixed(c, nb, ins, Ls, &R));
+      Epi es[PHIKS_MAX_P];
+      for (int t = 0; t < p; ++t) {
+        Epi e = make_epi();
+        e.nout = 1;
+        e.nsrc = nb + 1;
+        e.out[0] = acc[t];
+        e.src[0] = acc[t];
+        e.a[0][0] = 1.0;
+        for (int k = 0; k < nb; ++k) {
+          const double th = B->theta[nodes[k0 + k]];
+          e.src[k + 1] = R + (size_t)k * P->NR;
+          e.a[0][k + 1] = B->w[nodes[k0 + k]] * std::pow(th, t) / factorial(t);
+        }
+        es[t] = e;
+      }
+      TRY(combine_many(c, es, p));
+    }
+  }
   for (int i = 0; i < q && p > 0; ++i) {
     const double th = B->theta[i], w = B->w[i];
+    if (mix && B->node_bank[i] >= 0) continue;  // done above
     Epi e = make_epi();
     e.nout = p;
     e.nsrc = p;
@@ -954,10 +1031,17 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
   const bool f32 = split_dtype(P);
   const int q = (int)B->theta.size();
   for (int l = 0; l < p; ++l) CK(cudaMemsetAsync(acc[l], 0, P->NR * 8, c.st));
+  // FP64_EMU: the Tucker operators of several nodes in one batch (each with
+  // its node's matrices), their weighted results summed into the accumulators
+  const bool mix = emu_dtype(P) && oz_mixed_ok(P->oz) && p > 0;
+  std::vector<int> mnodes;
+  std::vector<Combo> mins;
+  std::vector<int> mls;
   for (int i = 0; i < q; ++i) {
     const double th = B->theta[i], w = B->w[i];
     Combo ins[PHIKS_MAX_P];
     Epi es[PHIKS_MAX_P];
+    int ls[PHIKS_MAX_P];
     int nb = 0;
     for (int l = 1; l <= p; ++l) {
       // input: sum_{k=1}^{l} theta^(l-k)/(l-k)! v_{p+1-k} / 2^((l-k+1) s)
@@ -994,13 +1078,57 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
       e.a[0][0] = 1.0;
       e.b[0] = w;
       ins[nb] = in;
+      ls[nb] = l;
       es[nb++] = e;
     }
-    if (nb) {  // the node's Tucker operators share its matrices
+    if (nb && mix) {
+      for (int k = 0; k < nb; ++k) {
+        mnodes.push_back(i);
+        mins.push_back(ins[k]);
+        mls.push_back(ls[k]);
+      }
+    } else if (nb) {  // the node's Tucker operators share its matrices
       Mats L;
       bank_ptrs(P, B, B->node_bank[i], &L);
       TRY(tucker_batch(c, nb, ins, L, es));
     }
+  }
+  // batches of whole nodes (at most kMaxSrc - 1 nodes, so that every
+  // accumulator's combination reads it and the nodes' results)
+  for (size_t k0 = 0; k0 < mins.size();) {
+    size_t k1 = k0;
+    int nn = 0;
+    while (k1 < mins.size()) {
+      size_t k2 = k1;
+      while (k2 < mins.size() && mnodes[k2] == mnodes[k1]) ++k2;
+      if ((int)(k2 - k0) > c.bmax || nn + 1 > kMaxSrc - 1) break;
+      k1 = k2;
+      ++nn;
+    }
+    if (k1 == k0) return fail(PHIKS_ERR_INVALID, "node batch exceeds %d operators", c.bmax);
+    const int nb = (int)(k1 - k0);
+    Mats Ls[kOzMaxBatch];
+    for (int k = 0; k < nb; ++k) bank_ptrs(P, B, B->node_bank[mnodes[k0 + k]], &Ls[k]);
+    const double* R = nullptr;
+    TRY(tucker_mixed(c, nb, mins.data() + k0, Ls, &R));
+    Epi es[PHIKS_MAX_P];
+    int ne = 0;
+    for (int l = 1; l <= p; ++l) {
+      Epi e = make_epi();
+      e.nout = 1;
+      e.nsrc = 1;
+      e.out[0] = acc[l - 1];
+      e.src[0] = acc[l - 1];
+      e.a[0][0] = 1.0;
+      for (int k = 0; k < nb; ++k)
+        if (mls[k0 + k] == l) {
+          e.src[e.nsrc] = R + (size_t)k * P->NR;
+          e.a[0][e.nsrc++] = B->w[mnodes[k0 + k]];
+        }
+      if (e.nsrc > 1) es[ne++] = e;
+    }
+    TRY(combine_many(c, es, ne));
+    k0 = k1;
   }
   Mats M;
   bank_ptrs(P, B, B->b0, &M);

@@ -304,7 +304,6 @@ cudaError_t launch_tiled(const Combo& pro, const double* L, ModeGeom g, double* 
                     W, e);
 }
 
-constexpr int kMaxEpiBatch = 8;
 struct EpiBatch {
   Epi e[kMaxEpiBatch];
 };

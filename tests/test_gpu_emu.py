@@ -71,3 +71,36 @@ def test_lincomb_emulated_ragged_batches():
     errs = [rel_inf(out[L], ta.lincomb(wl.A, wl.tau, wl.vs, 2.0 ** -L)) for L in range(2)]
     print("emu ragged lincomb errs", ["%.2e" % e for e in errs])
     assert max(errs) < 1e-12
+
+
+def test_same_vector_emulated_node_batches():
+    """SAME mode whose quadrature nodes run as one batch of Tucker operators
+    with their own matrices (every mode's fibre count a multiple of 128)."""
+    dims = (64, 32, 64)
+    A = [wk.fd_adr_dirichlet(m, 1.0, a, 0.5) for m, a in zip(dims, (4.0, -2.0, 1.0))]
+    N = int(np.prod(dims))
+    wl = wk.Workload("adr3d_same_%dx%dx%d" % dims, A, 5e-4, 3, "same", 2, [wk.uniform(21, N)])
+    out, plan = run_workload(wl, dtype=EMU)
+    pk.phiks_device_status(plan.handle)
+    per = wl.p + 1
+    worst = 0.0
+    for L in range(2):
+        ex = ta.same(wl.A, wl.tau, wl.vs[0], wl.p, c=2.0 ** -L)
+        for k in range(per):
+            e = rel_inf(out[L * per + k], ex[k])
+            worst = max(worst, e)
+            assert e < 1e-12, (L, k, e)
+    print("emu same node batches: max rel err %.2e" % worst)
+
+
+def test_lincomb_emulated_many_nodes():
+    """Linear combination with (s, q) = (6, 12): eleven quadrature nodes with
+    Tucker operators, in batches of whole nodes (four operators each)."""
+    wl = wk.adr3d_lincomb(p=4, dims=(64, 32, 64), nscales=2)
+    out, plan = run_workload(wl, dtype=EMU, force_s=6, force_q=12)
+    pk.phiks_device_status(plan.handle)
+    s, q, _, _ = plan.last_params()
+    assert (s, q) == (6, 12)
+    errs = [rel_inf(out[L], ta.lincomb(wl.A, wl.tau, wl.vs, 2.0 ** -L)) for L in range(2)]
+    print("emu lincomb q=12 errs", ["%.2e" % e for e in errs])
+    assert max(errs) < 1e-12
