@@ -887,16 +887,21 @@ phiks_status run_same(Ctx& c, const Bank* B, int s, int p, const void* v, const 
   const bool f32 = split_dtype(P);
   const int per = p + (o.skip_phi0 ? 0 : 1);
   const int q = (int)B->theta.size();
-  for (int l = 0; l < p; ++l) CK(cudaMemsetAsync(acc[l], 0, P->NR * 8, c.st));
   // quadrature at K/2^s: phi_l += w_i theta_i^(l-1)/(l-1)! exp((1-theta_i)K/2^s) v
   // FP64_EMU: the nodes' Tucker operators in batches (each with its node's
-  // matrices), their weighted results summed into the p accumulators
-  const bool mix = emu_dtype(P) && oz_mixed_ok(P->oz) && p > 0;
+  // matrices), their weighted results summed into the p accumulators; the
+  // first batch's sums (with the theta = 1 node's term) set them
+  std::vector<int> nodes;
+  int one = -1;  // the theta = 1 node
+  for (int i = 0; i < q; ++i) {
+    if (B->node_bank[i] >= 0) nodes.push_back(i);
+    else one = i;
+  }
+  const bool mix = emu_dtype(P) && oz_mixed_ok(P->oz) && p > 0 && !nodes.empty();
+  if (!mix)
+    for (int l = 0; l < p; ++l) CK(cudaMemsetAsync(acc[l], 0, P->NR * 8, c.st));
   if (mix) {
     const int per_batch = std::min(c.bmax, kMaxSrc - 1);
-    std::vector<int> nodes;
-    for (int i = 0; i < q; ++i)
-      if (B->node_bank[i] >= 0) nodes.push_back(i);
     for (size_t k0 = 0; k0 < nodes.size(); k0 += per_batch) {
       const int nb = (int)std::min<size_t>(per_batch, nodes.size() - k0);
       Combo ins[kOzMaxBatch];
@@ -911,23 +916,29 @@ phiks_status run_same(Ctx& c, const Bank* B, int s, int p, const void* v, const 
       for (int t = 0; t < p; ++t) {
         Epi e = make_epi();
         e.nout = 1;
-        e.nsrc = nb + 1;
         e.out[0] = acc[t];
-        e.src[0] = acc[t];
-        e.a[0][0] = 1.0;
+        if (k0 > 0) {  // add to the sums so far
+          e.src[0] = acc[t];
+          e.a[0][0] = 1.0;
+          e.nsrc = 1;
+        } else if (one >= 0) {  // theta = 1: exp(0) = I
+          e.src[0] = (const double*)v;
+          e.src_f32mask = f32 ? 1 : 0;
+          e.a[0][0] = B->w[one] / factorial(t);
+          e.nsrc = 1;
+        }
         for (int k = 0; k < nb; ++k) {
           const double th = B->theta[nodes[k0 + k]];
-          e.src[k + 1] = R + (size_t)k * P->NR;
-          e.a[0][k + 1] = B->w[nodes[k0 + k]] * std::pow(th, t) / factorial(t);
+          e.src[e.nsrc] = R + (size_t)k * P->NR;
+          e.a[0][e.nsrc++] = B->w[nodes[k0 + k]] * std::pow(th, t) / factorial(t);
         }
         es[t] = e;
       }
       TRY(combine_many(c, es, p));
     }
   }
-  for (int i = 0; i < q && p > 0; ++i) {
+  for (int i = 0; i < q && p > 0 && !mix; ++i) {
     const double th = B->theta[i], w = B->w[i];
-    if (mix && B->node_bank[i] >= 0) continue;  // done above
     Epi e = make_epi();
     e.nout = p;
     e.nsrc = p;
@@ -1030,13 +1041,17 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
   const size_t es = elt_size(P);
   const bool f32 = split_dtype(P);
   const int q = (int)B->theta.size();
-  for (int l = 0; l < p; ++l) CK(cudaMemsetAsync(acc[l], 0, P->NR * 8, c.st));
   // FP64_EMU: the Tucker operators of several nodes in one batch (each with
-  // its node's matrices), their weighted results summed into the accumulators
+  // its node's matrices), their weighted results summed into the accumulators;
+  // the first sums into an accumulator (with the theta = 1 node's term) set it
   const bool mix = emu_dtype(P) && oz_mixed_ok(P->oz) && p > 0;
+  if (!mix)
+    for (int l = 0; l < p; ++l) CK(cudaMemsetAsync(acc[l], 0, P->NR * 8, c.st));
   std::vector<int> mnodes;
   std::vector<Combo> mins;
   std::vector<int> mls;
+  Combo one[PHIKS_MAX_P];  // theta = 1 terms of accumulator l - 1 (weights applied)
+  for (int l = 0; l < p; ++l) one[l] = make_combo(), one[l].nsrc = 0;
   for (int i = 0; i < q; ++i) {
     const double th = B->theta[i], w = B->w[i];
     Combo ins[PHIKS_MAX_P];
@@ -1055,6 +1070,11 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
         in.nsrc++;
       }
       if (in.nsrc == 0) continue;
+      if (B->node_bank[i] < 0 && mix) {  // theta = 1: w * input, added below
+        one[l - 1] = in;
+        for (int m = 0; m < in.nsrc; ++m) one[l - 1].coef[m] *= w;
+        continue;
+      }
       if (B->node_bank[i] < 0) {  // theta = 1: acc_l += w * input
         Epi f = make_epi();
         f.nout = 1;
@@ -1093,15 +1113,19 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
       TRY(tucker_batch(c, nb, ins, L, es));
     }
   }
-  // batches of whole nodes (at most kMaxSrc - 1 nodes, so that every
-  // accumulator's combination reads it and the nodes' results)
+  // batches of whole nodes, few enough that every accumulator's combination
+  // (its sum so far or its theta = 1 terms, and the nodes' results) has at
+  // most kMaxSrc sources
+  bool set[PHIKS_MAX_P] = {false};
   for (size_t k0 = 0; k0 < mins.size();) {
+    int lead = 1;  // sources besides the nodes' results
+    for (int l = 0; l < p; ++l) lead = std::max(lead, set[l] ? 1 : one[l].nsrc);
     size_t k1 = k0;
     int nn = 0;
     while (k1 < mins.size()) {
       size_t k2 = k1;
       while (k2 < mins.size() && mnodes[k2] == mnodes[k1]) ++k2;
-      if ((int)(k2 - k0) > c.bmax || nn + 1 > kMaxSrc - 1) break;
+      if ((int)(k2 - k0) > c.bmax || lead + nn + 1 > kMaxSrc) break;
       k1 = k2;
       ++nn;
     }
@@ -1116,20 +1140,51 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
     for (int l = 1; l <= p; ++l) {
       Epi e = make_epi();
       e.nout = 1;
-      e.nsrc = 1;
       e.out[0] = acc[l - 1];
-      e.src[0] = acc[l - 1];
-      e.a[0][0] = 1.0;
+      if (set[l - 1]) {
+        e.nsrc = 1;
+        e.src[0] = acc[l - 1];
+        e.a[0][0] = 1.0;
+      } else {
+        e.nsrc = one[l - 1].nsrc;
+        e.src_f32mask = one[l - 1].f32mask;
+        for (int m = 0; m < e.nsrc; ++m) {
+          e.src[m] = one[l - 1].src[m];
+          e.a[0][m] = one[l - 1].coef[m];
+        }
+      }
+      const int lead_l = e.nsrc;
       for (int k = 0; k < nb; ++k)
         if (mls[k0 + k] == l) {
           e.src[e.nsrc] = R + (size_t)k * P->NR;
           e.a[0][e.nsrc++] = B->w[mnodes[k0 + k]];
         }
-      if (e.nsrc > 1) es[ne++] = e;
+      if (e.nsrc > lead_l) {
+        es[ne++] = e;
+        set[l - 1] = true;
+      }
     }
     TRY(combine_many(c, es, ne));
     k0 = k1;
   }
+  if (mix)  // accumulators without node operators
+    for (int l = 0; l < p; ++l) {
+      if (set[l]) continue;
+      if (one[l].nsrc == 0) {
+        CK(cudaMemsetAsync(acc[l], 0, P->NR * 8, c.st));
+        continue;
+      }
+      Epi e = make_epi();
+      e.nout = 1;
+      e.out[0] = acc[l];
+      e.nsrc = one[l].nsrc;
+      e.src_f32mask = one[l].f32mask;
+      for (int m = 0; m < e.nsrc; ++m) {
+        e.src[m] = one[l].src[m];
+        e.a[0][m] = one[l].coef[m];
+      }
+      TRY(combine(c, e));
+    }
   Mats M;
   bank_ptrs(P, B, B->b0, &M);
   int mbuf = 0;
@@ -1151,6 +1206,10 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
   // Lv: it shares that level's matrices and reads acc[p-1] before the level's
   // results replace it
   const bool join = batched && v[0] && p + 1 <= c.bmax;
+  // FP64_EMU: the output operator of scale 0 runs in the batch of level 1
+  // (with its own matrices), together with the p operators of that level and
+  // the output operator of scale 1
+  const bool join0 = join && p > 0 && emu_dtype(P) && oz_mixed_ok(P->oz) && p + 2 <= c.bmax;
   auto emit = [&](int Lv) -> phiks_status {
     char* blk = (char*)out + (size_t)Lv * N * es;
     if (v[0]) {
@@ -1172,8 +1231,8 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
     TRY(begin_square(c, Mn, mbuf, &aside));
     // eq. (comb), l = p..1 in place; batched: from the old values into the
     // second set of accumulators, which then become the first
-    Combo ins[PHIKS_MAX_P + 1];
-    Epi es[PHIKS_MAX_P + 1];
+    Combo ins[PHIKS_MAX_P + 2];
+    Epi es[PHIKS_MAX_P + 2];
     for (int l = p; l >= 1; --l) {
       Epi e = make_epi();
       e.nout = 1;
@@ -1191,18 +1250,47 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
         TRY(tucker(c, plain(acc[l - 1], false), M, &e));
       }
     }
+    const bool last0 = join0 && j == 1;
     if (batched) {
       int nb = p;
       if (join && j < o.nscales) {
         ins[nb] = plain(v[0], f32);
         es[nb++] = out_epi(j);
       }
-      TRY(tucker_batch(c, nb, ins, M, es));
+      if (last0) {
+        // with the output operator of scale 0 (matrices exp(K), squared
+        // first), whose epilogue adds the new Phi_0 v_{1..p} = this level's
+        // l = p result through that operator's own combination
+        TRY(finish_square(c, aside));
+        aside = false;
+        Mats Ls[PHIKS_MAX_P + 2];
+        for (int k = 0; k < nb; ++k) Ls[k] = M;
+        Ls[nb] = Mn;
+        ins[nb] = plain(v[0], f32);
+        const double* R = nullptr;
+        TRY(tucker_mixed(c, nb + 1, ins, Ls, &R));
+        Epi fs[PHIKS_MAX_P + 2];
+        for (int k = 0; k < nb; ++k) {
+          fs[k] = es[k];
+          fs[k].src[fs[k].nsrc] = R + (size_t)k * P->NR;
+          fs[k].a[0][fs[k].nsrc++] = es[k].b[0];
+          fs[k].b[0] = 0.0;
+        }
+        Epi e0 = fs[0];  // es[0]: l = p
+        e0.out[0] = (double*)out;
+        e0.out_f32mask = f32 ? 1 : 0;
+        e0.src[e0.nsrc] = R + (size_t)nb * P->NR;
+        e0.a[0][e0.nsrc++] = 1.0;
+        fs[nb] = e0;
+        TRY(combine_many(c, fs, nb + 1));
+      } else {
+        TRY(tucker_batch(c, nb, ins, M, es));
+      }
       for (int l = 0; l < p; ++l) std::swap(acc[l], c.acc2[l]);
     }
     TRY(finish_square(c, aside));
     M = Mn;
-    if (j - 1 < o.nscales) TRY(emit(j - 1));
+    if (j - 1 < o.nscales && !(last0 && j - 1 == 0)) TRY(emit(j - 1));
   }
   return PHIKS_OK;
 }
