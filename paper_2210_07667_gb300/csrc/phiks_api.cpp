@@ -111,6 +111,10 @@ struct phiks_plan_s {
   Rect rect[PHIKS_MAX_D];
   double* dAs = nullptr;  // device: A_mu - sigma_mu I, concatenated
   size_t offA[PHIKS_MAX_D] = {0};
+  // device: (g_mu (A_mu - sigma_mu I))^i for i = 2, 3, 4 (i - 2 blocks of
+  // sum_n2 doubles, each laid out as dAs), g_mu a power of two
+  double* dApow = nullptr;
+  double apow_g[PHIKS_MAX_D] = {0};
   size_t sum_n2 = 0;
   int nmax = 0;
   std::vector<Bank> banks;
@@ -302,13 +306,20 @@ phiks_status select_cached(phiks_plan_s* P, double tau, int p, int kind, const d
 }
 
 // ---- small exponentials ----------------------------------------------------
-// E = e^{c sigma} T_15(X)^(2^t) with X = c (A - sigma I) / 2^t, ||X||_1 <= 1/2:
-// the Taylor polynomial of degree 15 (remainder below 0.5^16/16! < 1e-18),
-// evaluated by Paterson and Stockmeyer's scheme with blocks of four terms
-// (X^2, X^3, X^4, then three products by X^4: six matrix products), followed
-// by t squarings (scaling and squaring, Moler and Van Loan's method 3).
-constexpr int kTaylorDeg = 15;
-constexpr int kScratchPerJob = 6;  // X, X^2, X^3, X^4, T0, T1
+// E = e^{c sigma} T_m(X)^(2^t) with X = c (A - sigma I) / 2^t, ||X||_1 <= 1/2,
+// T_m the Taylor polynomial of degree m = 4J - 1 (J = 1..4, the smallest with
+// a remainder below 2^-54 for this ||X||_1; m = 15 leaves 0.5^16/16! < 1e-18),
+// evaluated by Paterson and Stockmeyer's scheme with blocks of four terms:
+// T = B_{J-1}, then T <- T X^4 + B_j for j = J-2 .. 0, B_j = sum_{i<4}
+// c_{4j+i} X^i, followed by t squarings (scaling and squaring, Moler and Van
+// Loan's method 3).  The powers 2..4 of g (A - sigma I), g a power of two
+// near 1 / ||A - sigma I||_1, come from the plan (computed once) or are
+// formed first; X^i = (c 2^-t / g)^i (g (A - sigma I))^i enters through the
+// coefficients, and e^{c sigma} (its 2^-t-th power when t > 0) through the
+// last polynomial step, which writes E directly when t = 0.
+constexpr int kTaylorBlocks = 4;
+constexpr int kTaylorDeg = 4 * kTaylorBlocks - 1;
+constexpr int kScratchPerJob = 6;  // (gA)^2, (gA)^3, (gA)^4, T0, T1, spare
 
 struct ExpmJob {
   int n;
@@ -317,6 +328,8 @@ struct ExpmJob {
   double norm1;          // ||A - sigma I||_1
   double esig;           // e^{c sigma}
   double* out;           // device n x n
+  const double* pw[3] = {nullptr, nullptr, nullptr};  // (g Ashift)^2..4, or null
+  double g = 1.0;                                      // that power of two
 };
 
 GemmBatch gemm_batch0() {
@@ -325,118 +338,158 @@ GemmBatch gemm_batch0() {
   return g;
 }
 
+// The power of two near 1 / ||M||_1 (1 for a zero matrix).
+double pow2_scale(double norm1) {
+  if (!(norm1 > 0) || !std::isfinite(norm1)) return 1.0;
+  return std::ldexp(1.0, -std::ilogb(norm1));
+}
+
+// (g A_k)^2 into P2[k], (g A_k)^3 into P3[k], (g A_k)^4 into P4[k]: two
+// batched launches.
+phiks_status matrix_powers(int count, const int* n, const double* const* A, const double* g,
+                           double* const* P2, double* const* P3, double* const* P4, cudaStream_t st) {
+  for (int k0 = 0; k0 < count; k0 += kMaxBatch / 2) {
+    const int cnt = std::min(kMaxBatch / 2, count - k0);
+    int nmax = 1;
+    GemmBatch gb = gemm_batch0();
+    gb.count = cnt;
+    for (int i = 0; i < cnt; ++i) {
+      const int k = k0 + i;
+      nmax = std::max(nmax, n[k]);
+      gb.n[i] = n[k];
+      gb.A[i] = A[k];
+      gb.B[i] = A[k];
+      gb.C[i] = P2[k];
+      gb.alpha[i] = g[k] * g[k];
+    }
+    CK(launch_gemm_batch_f64(gb, nmax, st));
+    gb = gemm_batch0();
+    gb.count = 2 * cnt;
+    for (int i = 0; i < cnt; ++i) {
+      const int k = k0 + i;
+      gb.n[2 * i] = gb.n[2 * i + 1] = n[k];
+      gb.A[2 * i] = P2[k];  // (gA)^3 = (gA)^2 A g
+      gb.B[2 * i] = A[k];
+      gb.C[2 * i] = P3[k];
+      gb.alpha[2 * i] = g[k];
+      gb.A[2 * i + 1] = P2[k];  // (gA)^4 = (gA)^2 (gA)^2
+      gb.B[2 * i + 1] = P2[k];
+      gb.C[2 * i + 1] = P4[k];
+      gb.alpha[2 * i + 1] = 1.0;
+    }
+    CK(launch_gemm_batch_f64(gb, nmax, st));
+  }
+  return PHIKS_OK;
+}
+
 phiks_status run_expm_jobs(phiks_plan_s* P, std::vector<ExpmJob>& jobs, double* scratch,
                            cudaStream_t st) {
   (void)P;
-  std::vector<size_t> offs(jobs.size());
+  const int nj = (int)jobs.size();
+  std::vector<size_t> offs(nj);
   size_t tot = 0;
   int nmax = 1;
-  for (size_t k = 0; k < jobs.size(); ++k) {
+  for (int k = 0; k < nj; ++k) {
     offs[k] = tot;
     tot += kScratchPerJob * (size_t)jobs[k].n * jobs[k].n;
     nmax = std::max(nmax, jobs[k].n);
   }
-  std::vector<int> t(jobs.size());
-  int tmax = 0;
-  for (size_t k = 0; k < jobs.size(); ++k) {
-    double nx = std::fabs(jobs[k].c) * jobs[k].norm1;
-    t[k] = nx > 0.5 ? (int)std::ceil(std::log2(nx / 0.5)) : 0;
-    tmax = std::max(tmax, t[k]);
+  auto buf = [&](int k, int i) { return scratch + offs[k] + (size_t)i * jobs[k].n * jobs[k].n; };
+  // powers the plan does not hold
+  {
+    std::vector<int> n;
+    std::vector<const double*> A;
+    std::vector<double> g;
+    std::vector<double*> p2, p3, p4;
+    for (int k = 0; k < nj; ++k) {
+      if (jobs[k].pw[0]) continue;
+      jobs[k].g = pow2_scale(jobs[k].norm1);
+      jobs[k].pw[0] = buf(k, 0);
+      jobs[k].pw[1] = buf(k, 1);
+      jobs[k].pw[2] = buf(k, 2);
+      n.push_back(jobs[k].n);
+      A.push_back(jobs[k].Ashift);
+      g.push_back(jobs[k].g);
+      p2.push_back(buf(k, 0));
+      p3.push_back(buf(k, 1));
+      p4.push_back(buf(k, 2));
+    }
+    if (!n.empty())
+      TRY(matrix_powers((int)n.size(), n.data(), A.data(), g.data(), p2.data(), p3.data(), p4.data(), st));
   }
   double cf[kTaylorDeg + 1];
   cf[0] = 1.0;
   for (int i = 1; i <= kTaylorDeg; ++i) cf[i] = cf[i - 1] / i;
-  const size_t per = kMaxBatch / 2;  // the X^3 / X^4 launch holds two entries per job
-  for (size_t k0 = 0; k0 < jobs.size(); k0 += per) {
-    const size_t k1 = std::min(jobs.size(), k0 + per);
-    const int cnt = (int)(k1 - k0);
-    auto buf = [&](size_t k, int i) { return scratch + offs[k] + (size_t)i * jobs[k].n * jobs[k].n; };
-    enum { BX = 0, BX2 = 1, BX3 = 2, BX4 = 3, BT0 = 4, BT1 = 5 };
-    ScaleBatch sb;
-    sb.count = cnt;
-    for (int i = 0; i < cnt; ++i) {
-      size_t k = k0 + i;
-      sb.n[i] = jobs[k].n;
-      sb.X[i] = jobs[k].Ashift;
-      sb.Y[i] = buf(k, BX);
-      sb.alpha[i] = std::ldexp(jobs[k].c, -t[k]);
-      sb.shift[i] = 0.0;
-    }
-    CK(launch_scale_batch_f64(sb, nmax, st));
-    GemmBatch g = gemm_batch0();  // X^2
-    g.count = cnt;
-    for (int i = 0; i < cnt; ++i) {
-      size_t k = k0 + i;
-      g.n[i] = jobs[k].n;
-      g.A[i] = buf(k, BX);
-      g.B[i] = buf(k, BX);
-      g.C[i] = buf(k, BX2);
-      g.alpha[i] = 1.0;
-    }
-    CK(launch_gemm_batch_f64(g, nmax, st));
-    g = gemm_batch0();  // X^3 = X^2 X, X^4 = X^2 X^2
-    g.count = 2 * cnt;
-    for (int i = 0; i < cnt; ++i) {
-      size_t k = k0 + i;
-      for (int h = 0; h < 2; ++h) {
-        g.n[2 * i + h] = jobs[k].n;
-        g.A[2 * i + h] = buf(k, BX2);
-        g.B[2 * i + h] = buf(k, h ? BX2 : BX);
-        g.C[2 * i + h] = buf(k, h ? BX4 : BX3);
-        g.alpha[2 * i + h] = 1.0;
+  std::vector<int> t(nj), J(nj);
+  std::vector<double> h(nj), fin(nj);
+  int tmax = 0, Jmax = 1;
+  for (int k = 0; k < nj; ++k) {
+    const double nx0 = std::fabs(jobs[k].c) * jobs[k].norm1;
+    t[k] = nx0 > 0.5 ? (int)std::ceil(std::log2(nx0 / 0.5)) : 0;
+    const double cs = std::ldexp(jobs[k].c, -t[k]);  // X = cs (A - sigma I)
+    const double nx = std::fabs(cs) * jobs[k].norm1;
+    // remainder of T_{4J-1}: at most nx^(4J) / (4J)! / (1 - nx / (4J + 1))
+    J[k] = kTaylorBlocks;
+    for (int b = 1; b < kTaylorBlocks; ++b) {
+      double term = 1.0;
+      for (int i = 1; i <= 4 * b; ++i) term *= nx / i;
+      if (term / (1.0 - nx / (4 * b + 1)) <= std::ldexp(1.0, -54)) {
+        J[k] = b;
+        break;
       }
     }
-    CK(launch_gemm_batch_f64(g, nmax, st));
-    // T = B_3 = c12 I + c13 X + c14 X^2 + c15 X^3, then T <- T X^4 + B_j, j = 2, 1, 0
-    int cur = BT0;
-    for (int j = 3; j >= 0; --j) {
-      g = gemm_batch0();
-      g.count = cnt;
-      for (int i = 0; i < cnt; ++i) {
-        size_t k = k0 + i;
+    h[k] = cs / jobs[k].g;  // X^i = h^i (g (A - sigma I))^i
+    fin[k] = t[k] ? std::pow(jobs[k].esig, std::ldexp(1.0, -t[k])) : jobs[k].esig;
+    tmax = std::max(tmax, t[k]);
+    Jmax = std::max(Jmax, J[k]);
+  }
+  // polynomial: step j runs the jobs with J > j; the first step of a job
+  // (j = J - 1) sets T = B_j, later ones T <- T X^4 + B_j; step 0 carries the
+  // final factor and writes E when the job has no squarings
+  std::vector<int> cur(nj, 3);  // T0 = slot 3, T1 = slot 4
+  for (int k0 = 0; k0 < nj; k0 += kMaxBatch) {
+    const int k1 = std::min(nj, k0 + kMaxBatch);
+    for (int j = Jmax - 1; j >= 0; --j) {
+      GemmBatch g = gemm_batch0();
+      for (int k = k0; k < k1; ++k) {
+        if (J[k] <= j) continue;
+        const int i = g.count++;
+        const bool first = j == J[k] - 1;
+        const double f = j == 0 ? fin[k] : 1.0;
+        const double hk = h[k];
         g.n[i] = jobs[k].n;
-        g.alpha[i] = (j == 3) ? 0.0 : 1.0;
-        g.A[i] = buf(k, cur);
-        g.B[i] = buf(k, BX4);
-        g.C[i] = buf(k, (j == 3) ? BT0 : (cur == BT0 ? BT1 : BT0));
-        g.beta_I[i] = cf[4 * j];
-        g.addm[i][0] = buf(k, BX);
-        g.addm[i][1] = buf(k, BX2);
-        g.addm[i][2] = buf(k, BX3);
-        g.addc[i][0] = cf[4 * j + 1];
-        g.addc[i][1] = cf[4 * j + 2];
-        g.addc[i][2] = cf[4 * j + 3];
-      }
-      CK(launch_gemm_batch_f64(g, nmax, st));
-      if (j < 3) cur = (cur == BT0) ? BT1 : BT0;
-    }
-    // squarings: job k squares t[k] times between T0 and T1
-    std::vector<int> kcur(cnt, cur);
-    for (int r = 0; r < tmax; ++r) {
-      g = gemm_batch0();
-      for (int i = 0; i < cnt; ++i) {
-        size_t k = k0 + i;
-        if (t[k] <= r) continue;
-        int jj = g.count++;
-        const int nxt = kcur[i] == BT0 ? BT1 : BT0;
-        g.n[jj] = jobs[k].n;
-        g.A[jj] = buf(k, kcur[i]);
-        g.B[jj] = buf(k, kcur[i]);
-        g.C[jj] = buf(k, nxt);
-        g.alpha[jj] = 1.0;
-        kcur[i] = nxt;
+        g.alpha[i] = first ? 0.0 : f * hk * hk * hk * hk;
+        g.A[i] = buf(k, cur[k]);
+        g.B[i] = jobs[k].pw[2];
+        const int nxt = first ? 3 : (cur[k] == 3 ? 4 : 3);
+        g.C[i] = (j == 0 && t[k] == 0) ? jobs[k].out : buf(k, nxt);
+        g.beta_I[i] = f * cf[4 * j];
+        g.addm[i][0] = jobs[k].Ashift;  // X = cs (A - sigma I) = hk g (A - sigma I)
+        g.addc[i][0] = f * cf[4 * j + 1] * hk * jobs[k].g;
+        g.addm[i][1] = jobs[k].pw[0];
+        g.addc[i][1] = f * cf[4 * j + 2] * hk * hk;
+        g.addm[i][2] = jobs[k].pw[1];
+        g.addc[i][2] = f * cf[4 * j + 3] * hk * hk * hk;
+        cur[k] = nxt;
       }
       if (g.count) CK(launch_gemm_batch_f64(g, nmax, st));
     }
-    for (int i = 0; i < cnt; ++i) {
-      size_t k = k0 + i;
-      sb.n[i] = jobs[k].n;
-      sb.X[i] = buf(k, kcur[i]);
-      sb.Y[i] = jobs[k].out;
-      sb.alpha[i] = jobs[k].esig;
-      sb.shift[i] = 0.0;
+    // squarings: job k squares t[k] times, the last into E
+    for (int r = 0; r < tmax; ++r) {
+      GemmBatch g = gemm_batch0();
+      for (int k = k0; k < k1; ++k) {
+        if (t[k] <= r) continue;
+        const int i = g.count++;
+        const int nxt = cur[k] == 3 ? 4 : 3;
+        g.n[i] = jobs[k].n;
+        g.A[i] = buf(k, cur[k]);
+        g.B[i] = buf(k, cur[k]);
+        g.C[i] = r == t[k] - 1 ? jobs[k].out : buf(k, nxt);
+        g.alpha[i] = 1.0;
+        cur[k] = nxt;
+      }
+      if (g.count) CK(launch_gemm_batch_f64(g, nmax, st));
     }
-    CK(launch_scale_batch_f64(sb, nmax, st));
   }
   return PHIKS_OK;
 }
@@ -524,6 +577,8 @@ phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool 
       j.Ashift = P->dAs + P->offA[mu];
       j.c = (1.0 - bank_theta[b]) * scale;
       j.norm1 = P->norm1_shifted[mu];
+      j.g = P->apow_g[mu];
+      for (int i = 0; i < 3; ++i) j.pw[i] = P->dApow + (size_t)i * P->sum_n2 + P->offA[mu];
       j.esig = std::exp(j.c * P->sigma[mu]);
       j.out = nb.dev + nb.off[b][mu];
       jobs.push_back(j);
@@ -1404,6 +1459,25 @@ phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dty
     for (int64_t i = 0; i < m; ++i) sh[i + m * i] -= P->sigma[mu];
     CK(cudaMemcpy(P->dAs + P->offA[mu], sh.data(), m * m * 8, cudaMemcpyHostToDevice));
   }
+  {  // powers 2..4 of the scaled shifted matrices, for every small exponential
+    CK(cudaMalloc(&P->dApow, 3 * tot * 8));
+    int nn[PHIKS_MAX_D];
+    const double* As[PHIKS_MAX_D];
+    double* pw[3][PHIKS_MAX_D];
+    for (int mu = 0; mu < d; ++mu) {
+      nn[mu] = (int)P->m[mu];
+      As[mu] = P->dAs + P->offA[mu];
+      P->apow_g[mu] = pow2_scale(P->norm1_shifted[mu]);
+      for (int i = 0; i < 3; ++i) pw[i][mu] = P->dApow + (size_t)i * tot + P->offA[mu];
+    }
+    cudaStream_t s0;
+    CK(cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking));
+    phiks_status ps = matrix_powers(d, nn, As, P->apow_g, pw[0], pw[1], pw[2], s0);
+    const cudaError_t se = cudaStreamSynchronize(s0);
+    cudaStreamDestroy(s0);
+    if (ps != PHIKS_OK) return ps;
+    CK(se);
+  }
   CK(cudaMalloc(&P->d_norms, (PHIKS_MAX_P + 1) * 8));
   CK(cudaMallocHost(&P->h_norms, (PHIKS_MAX_P + 1) * 8));
   if (tc_path(P.get())) {
@@ -1609,6 +1683,7 @@ void phiks_destroy(phiks_plan_t P) {
   }
   cudaFree(P->tucker_tcb);
   cudaFree(P->dAs);
+  cudaFree(P->dApow);
   cudaFree(P->expm_scratch);
   cudaFree(P->ws);
   cudaFree(P->d_norms);
