@@ -90,24 +90,32 @@ __device__ __forceinline__ int biased_exp(double x) {
 
 constexpr int kSplitThreads = 128;
 
-struct ComboBatch {
-  Combo c[kOzMaxBatch];
+// Grid rows of a split launch: rows below ntensor are the batch's tensors
+// X_b = (combination c[b]), split into digit planes; the rest evaluate their
+// combination only.  store[y] (or null): where row y's FP64 values are also
+// written.
+struct SplitJobs {
+  Combo c[kOzMaxBatch + kOzMaxSide];
+  double* store[kOzMaxBatch + kOzMaxSide];
+  int ntensor;
 };
 
 // Each thread splits 8 consecutive elements of one fibre of X_b = (combination
-// in.c[b], b = blockIdx.y) and writes one 16-byte chunk of every digit plane;
+// jb.c[b], b = blockIdx.y) and writes one 16-byte chunk of every digit plane;
 // a block holds `fpb` whole fibres (n / 8 threads each), whose exponents meet
 // in shared memory.  Plane s of tensor b starts at planes + s * PS + b * N;
 // the fibre exponents of tensor b at scale + b * M2.
-__global__ void __launch_bounds__(kSplitThreads) oz_split_kernel(const __grid_constant__ ComboBatch inb, int n,
+__global__ void __launch_bounds__(kSplitThreads) oz_split_kernel(const __grid_constant__ SplitJobs jb, int n,
                                                                  int64_t M2, int fpb,
                                                                  __nv_bfloat16* planes, int64_t N,
                                                                  int64_t PS, int* scale) {
   __shared__ int emax[kSplitThreads];
   pdl_wait();
-  const Combo& in = inb.c[blockIdx.y];
-  planes += (int64_t)blockIdx.y * N;
-  scale += (int64_t)blockIdx.y * M2;
+  const int y = blockIdx.y;
+  const Combo& in = jb.c[y];
+  double* const xout = jb.store[y];
+  planes += (int64_t)y * N;
+  scale += (int64_t)y * M2;
   const int cpf = n >> 3;
   const int t = threadIdx.x;
   const int fl = t / cpf;
@@ -143,7 +151,18 @@ __global__ void __launch_bounds__(kSplitThreads) oz_split_kernel(const __grid_co
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) E = max(E, biased_exp(x[j]));
+    if (xout) {
+      double* q = xout + base;
+      if (((uintptr_t)q & 15) == 0) {
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) *reinterpret_cast<double2*>(q + j) = make_double2(x[j], x[j + 1]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) q[j] = x[j];
+      }
+    }
   }
+  if (y >= jb.ntensor) return;  // a combination only (uniform over the block)
   __syncthreads();
   if (active) atomicMax(&emax[fl], E);
   __syncthreads();
@@ -624,8 +643,9 @@ bool oz_mixed_ok(const OzState* s) {
 }
 
 cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, const Epi* epi,
-                      cudaStream_t st, const cudaEvent_t* ev, const double** res) {
+                      cudaStream_t st, const cudaEvent_t* ev, const double** res, const OzPrologue* pro) {
   if (B < 1 || B > s->batch || s->batch > kOzMaxBatch) return cudaErrorInvalidValue;
+  if (pro && (pro->nside < 0 || pro->nside > kOzMaxSide)) return cudaErrorInvalidValue;
   bool mixed = false;
   for (int b = 1; b < B; ++b)
     for (int mu = 0; mu < s->d; ++mu) mixed = mixed || mats[b].B[mu] != mats[0].B[mu];
@@ -635,9 +655,19 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, co
   const int64_t PS = (int64_t)s->batch * N;  // elements between digit planes
   __nv_bfloat16* planes = (__nv_bfloat16*)s->ws;
   int* xscale = (int*)(s->ws + up1k((size_t)kOzSlices * PS * 2));
-  ComboBatch cur;
+  SplitJobs cur;
   std::memset(&cur, 0, sizeof cur);
-  for (int b = 0; b < B; ++b) cur.c[b] = in[b];
+  for (int b = 0; b < B; ++b) {
+    cur.c[b] = in[b];
+    cur.store[b] = pro ? pro->store[b] : nullptr;
+  }
+  cur.ntensor = B;
+  int rows0 = B;  // grid rows of the first split
+  if (pro)
+    for (int k = 0; k < pro->nside; ++k, ++rows0) {
+      cur.c[rows0] = pro->side[k];
+      cur.store[rows0] = pro->side_out[k];
+    }
   double* dst = nullptr;
   for (int mu = 0; mu < s->d; ++mu) {
     const int n = (int)s->n[mu];
@@ -647,7 +677,8 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, co
       const int fpb = kSplitThreads / (n / 8);
       const int64_t blocks = (M2 + fpb - 1) / fpb;
       count_launch();
-      cudaError_t e = launch_pdl(oz_split_kernel, dim3((unsigned)blocks, (unsigned)B), dim3(kSplitThreads), 0,
+      cudaError_t e = launch_pdl(oz_split_kernel, dim3((unsigned)blocks, (unsigned)(mu == 0 ? rows0 : B)),
+                                 dim3(kSplitThreads), 0,
                                  st, cur, n, M2, fpb, planes, N, PS, xscale);
       if (e != cudaSuccess) return e;
     }
@@ -702,6 +733,7 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, co
       cur.c[b].src[0] = dst + (int64_t)b * N;
       cur.c[b].coef[0] = 1.0;
     }
+    cur.ntensor = B;
   }
   if (res) *res = dst;
   if (!epi) return cudaSuccess;

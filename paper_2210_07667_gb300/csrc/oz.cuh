@@ -28,6 +28,7 @@ struct OzState;
 constexpr int kOzSlices = 7;
 constexpr int kOzMaxN = 128;
 constexpr int kOzMaxBatch = 16;  // Tucker operators one oz_tucker call can run together
+constexpr int kOzMaxSide = 8;    // extra combinations of its first split pass
 
 // Workspace of oz_tucker for batches of up to `batch` (<= kOzMaxBatch) tensors.
 size_t oz_workspace_bytes(int d, const int64_t* n, int64_t N, int batch);
@@ -63,8 +64,19 @@ bool oz_mixed_ok(const OzState* s);
 // runs and *res receives the B results (tensor b at *res + b N, valid until
 // the next call).  `ev` (2 d events, or null): ev[2 mu] and ev[2 mu + 1] are
 // recorded around the tensor-core pass of mode mu.
+// `pro` (or null) extends the first split pass: tensor b's input values are
+// also stored to pro->store[b] (when not null), and pro->nside further
+// combinations (FP64, as the inputs) are evaluated into pro->side_out[k] in
+// the same launch; they may read the results of the previous call (its *res).
+struct OzPrologue {
+  double* store[kOzMaxBatch];
+  int nside;
+  Combo side[kOzMaxSide];
+  double* side_out[kOzMaxSide];
+};
 cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, const Epi* epi,
-                      cudaStream_t st, const cudaEvent_t* ev = nullptr, const double** res = nullptr);
+                      cudaStream_t st, const cudaEvent_t* ev = nullptr, const double** res = nullptr,
+                      const OzPrologue* pro = nullptr);
 
 int oz_read_status(OzState* s, cudaStream_t st);
 

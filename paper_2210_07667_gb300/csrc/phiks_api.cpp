@@ -783,7 +783,8 @@ phiks_status tucker_batch(Ctx& c, int B, const Combo* in, const Mats& M, const E
 // FP64_EMU with oz_mixed_ok: B <= c.bmax Tucker operators with their own
 // matrices M[b] in one batch, no epilogue; *res receives the results (tensor
 // b at *res + b N) for the caller's combination.
-phiks_status tucker_mixed(Ctx& c, int B, const Combo* in, const Mats* M, const double** res) {
+phiks_status tucker_mixed(Ctx& c, int B, const Combo* in, const Mats* M, const double** res,
+                          const OzPrologue* pro = nullptr) {
   phiks_plan_s* P = c.P;
   if (B < 1 || B > c.bmax) return fail(PHIKS_ERR_INVALID, "mixed batch of %d", B);
   OzMats om[kOzMaxBatch];
@@ -793,7 +794,7 @@ phiks_status tucker_mixed(Ctx& c, int B, const Combo* in, const Mats* M, const d
   cudaEvent_t ev[2 * PHIKS_MAX_D];
   if (prof)
     for (int mu = 0; mu < P->d; ++mu) TRY(prof_pair(P, &ev[2 * mu], &ev[2 * mu + 1]));
-  cudaError_t e = oz_tucker(P->oz, B, in, om, nullptr, c.st, prof ? ev : nullptr, res);
+  cudaError_t e = oz_tucker(P->oz, B, in, om, nullptr, c.st, prof ? ev : nullptr, res, pro);
   if (e != cudaSuccess)
     return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), oz_last_error());
   if (prof)
@@ -1350,6 +1351,168 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
   return PHIKS_OK;
 }
 
+// FP64_EMU when a batch may mix matrices (oz_mixed_ok) and hold p + 2
+// operators, s >= 1: the operators and combinations of run_lincomb, but every
+// batch's FP64 combinations (quadrature sums, eq. (comb), the outputs) are
+// evaluated by the next batch's first split pass, which stores them and
+// splits those that are its Tucker inputs, so that no combination pass runs
+// between batches; the last batch's outputs take one combination pass.
+phiks_status run_lincomb_emu(Ctx& c, const Bank* B, int s, int p, const void* const* v,
+                             const phiks_options& o, double** acc, void* out) {
+  phiks_plan_s* P = c.P;
+  const int64_t NR = P->NR;
+  const int q = (int)B->theta.size();
+  auto add = [](Combo& x, const double* src, double coef) -> phiks_status {
+    if (x.nsrc >= kMaxSrc) return fail(PHIKS_ERR_INVALID, "combination of more than %d terms", kMaxSrc);
+    x.src[x.nsrc] = src;
+    x.coef[x.nsrc++] = coef;
+    return PHIKS_OK;
+  };
+  auto blk = [&](int Lv) { return (double*)((char*)out + (size_t)Lv * P->N * 8); };
+  Combo pend[PHIKS_MAX_P];  // the accumulators' values, not yet evaluated
+  for (int l = 0; l < p; ++l) pend[l] = make_combo();
+  std::vector<std::pair<Combo, double*>> pout;  // combinations due before the next batch's products
+  // quadrature: the theta = 1 node's terms, the others' Tucker operators
+  std::vector<int> mnodes, mls;
+  std::vector<Combo> mins;
+  for (int i = 0; i < q; ++i) {
+    const double th = B->theta[i], w = B->w[i];
+    for (int l = 1; l <= p; ++l) {
+      Combo in = make_combo();  // as in run_lincomb
+      for (int k = 1; k <= l; ++k) {
+        const void* vk = v[p + 1 - k];
+        if (!vk) continue;
+        in.src[in.nsrc] = (const double*)vk;
+        in.coef[in.nsrc++] = std::pow(th, l - k) / factorial(l - k) * std::ldexp(1.0, -(l - k + 1) * s);
+      }
+      if (in.nsrc == 0) continue;
+      if (B->node_bank[i] < 0) {
+        for (int m = 0; m < in.nsrc; ++m) TRY(add(pend[l - 1], in.src[m], w * in.coef[m]));
+        continue;
+      }
+      mnodes.push_back(i);
+      mins.push_back(in);
+      mls.push_back(l);
+    }
+  }
+  for (size_t k0 = 0; k0 < mins.size();) {
+    // a later batch first evaluates the sums so far into acc
+    OzPrologue pro;
+    std::memset(&pro, 0, sizeof pro);
+    if (k0 > 0) {
+      for (int l = 0; l < p; ++l) {
+        pro.side[pro.nside] = pend[l];
+        pro.side_out[pro.nside++] = acc[l];
+        pend[l] = make_combo();
+        TRY(add(pend[l], acc[l], 1.0));
+      }
+    }
+    int lead = 1;
+    for (int l = 0; l < p; ++l) lead = std::max(lead, pend[l].nsrc);
+    size_t k1 = k0;
+    int nn = 0;
+    while (k1 < mins.size()) {
+      size_t k2 = k1;
+      while (k2 < mins.size() && mnodes[k2] == mnodes[k1]) ++k2;
+      if ((int)(k2 - k0) > c.bmax || lead + nn + 1 > kMaxSrc) break;
+      k1 = k2;
+      ++nn;
+    }
+    if (k1 == k0) return fail(PHIKS_ERR_INVALID, "node batch exceeds %d operators", c.bmax);
+    const int nb = (int)(k1 - k0);
+    Mats Ls[kOzMaxBatch];
+    for (int k = 0; k < nb; ++k) bank_ptrs(P, B, B->node_bank[mnodes[k0 + k]], &Ls[k]);
+    const double* R = nullptr;
+    TRY(tucker_mixed(c, nb, mins.data() + k0, Ls, &R, &pro));
+    for (int k = 0; k < nb; ++k) TRY(add(pend[mls[k0 + k] - 1], R + (size_t)k * NR, B->w[mnodes[k0 + k]]));
+    k0 = k1;
+  }
+  // squaring, eq. (comb): level j evaluates its accumulators (stored to A)
+  // and splits them; its results and A make the next level's combinations
+  Mats M;
+  bank_ptrs(P, B, B->b0, &M);
+  int mbuf = 0;
+  double* A[PHIKS_MAX_P];
+  double* Anext[PHIKS_MAX_P];
+  for (int l = 0; l < p; ++l) {
+    A[l] = c.acc2[l];  // pend may read acc
+    Anext[l] = acc[l];
+  }
+  const double* v0 = (const double*)v[0];
+  if (!v0 && s < o.nscales) pout.push_back({pend[p - 1], blk(s)});
+  for (int j = s; j >= 1; --j) {
+    Mats Mn = M;  // exp(K/2^(j-1)), squared beside this level's Tuckers
+    bool aside = false;
+    TRY(begin_square(c, Mn, mbuf, &aside));
+    Combo ins[PHIKS_MAX_P + 2];
+    Mats Ls[PHIKS_MAX_P + 2];
+    OzPrologue pro;
+    std::memset(&pro, 0, sizeof pro);
+    int nb = 0;
+    for (int l = p; l >= 1; --l) {  // operator l at index p - l
+      ins[nb] = pend[l - 1];
+      pro.store[nb] = A[l - 1];
+      Ls[nb++] = M;
+    }
+    int ie = -1, ie0 = -1;
+    if (v0 && j < o.nscales) {  // exp(K/2^j) v_0 for the output of scale j
+      ie = nb;
+      ins[nb] = plain(v0, false);
+      Ls[nb++] = M;
+    }
+    if (v0 && j == 1) {  // exp(K) v_0 for the output of scale 0, with its own matrices
+      TRY(finish_square(c, aside));
+      aside = false;
+      ie0 = nb;
+      ins[nb] = plain(v0, false);
+      Ls[nb++] = Mn;
+    }
+    if (pout.size() > (size_t)kOzMaxSide) return fail(PHIKS_ERR_INVALID, "too many pending outputs");
+    for (auto& x : pout) {
+      pro.side[pro.nside] = x.first;
+      pro.side_out[pro.nside++] = x.second;
+    }
+    pout.clear();
+    const double* R = nullptr;
+    TRY(tucker_mixed(c, nb, ins, Ls, &R, &pro));
+    for (int l = p; l >= 1; --l) {
+      Combo x = make_combo();
+      TRY(add(x, R + (size_t)(p - l) * NR, 1.0));
+      for (int k = 1; k <= l; ++k) TRY(add(x, A[k - 1], 1.0 / (factorial(l - k) * std::ldexp(1.0, (l - k) * j))));
+      pend[l - 1] = x;
+    }
+    if (ie >= 0) {
+      Combo x = make_combo();
+      TRY(add(x, R + (size_t)ie * NR, 1.0));
+      TRY(add(x, A[p - 1], 1.0));
+      pout.push_back({x, blk(j)});
+    }
+    if (ie0 >= 0) {
+      Combo x = pend[p - 1];
+      TRY(add(x, R + (size_t)ie0 * NR, 1.0));
+      pout.push_back({x, blk(0)});
+    } else if (!v0 && j - 1 < o.nscales) {
+      pout.push_back({pend[p - 1], blk(j - 1)});
+    }
+    for (int l = 0; l < p; ++l) std::swap(A[l], Anext[l]);
+    TRY(finish_square(c, aside));
+    M = Mn;
+  }
+  std::vector<Epi> es;
+  for (auto& x : pout) {
+    Epi e = make_epi();
+    e.nout = 1;
+    e.out[0] = x.second;
+    e.nsrc = x.first.nsrc;
+    for (int m = 0; m < e.nsrc; ++m) {
+      e.src[m] = x.first.src[m];
+      e.a[0][m] = x.first.coef[m];
+    }
+    es.push_back(e);
+  }
+  return combine_many(c, es.data(), (int)es.size());
+}
+
 phiks_status check_opts(const phiks_options& o) {
   if (o.nscales < 1 || o.nscales > 64) return fail(PHIKS_ERR_INVALID, "nscales %d", o.nscales);
   if (o.rule != PHIKS_RULE_GLL && o.rule != PHIKS_RULE_GL)
@@ -1864,7 +2027,10 @@ phiks_status phiks_apply_ex(phiks_plan_t P, double tau, int p, const void* const
     if (kind == 0) {
       TRY(run_same(c, B, s, p, v[0], o, acc, out));
     } else {
-      TRY(run_lincomb(c, B, s, p, v, o, acc, out));
+      if (emu_dtype(P) && oz_mixed_ok(P->oz) && p >= 1 && s >= 1 && c.bmax >= p + 2)
+        TRY(run_lincomb_emu(c, B, s, p, v, o, acc, out));
+      else
+        TRY(run_lincomb(c, B, s, p, v, o, acc, out));
     }
     CK(cudaGetLastError());
     tuckers = c.tuckers;

@@ -104,3 +104,16 @@ def test_lincomb_emulated_many_nodes():
     errs = [rel_inf(out[L], ta.lincomb(wl.A, wl.tau, wl.vs, 2.0 ** -L)) for L in range(2)]
     print("emu lincomb q=12 errs", ["%.2e" % e for e in errs])
     assert max(errs) < 1e-12
+
+
+def test_lincomb_emulated_missing_vectors():
+    """Linear combination without v_0 and v_2: outputs that are the
+    accumulators alone, and quadrature inputs with fewer terms."""
+    wl = wk.adr3d_lincomb(p=4, dims=(64, 32, 64), nscales=3)
+    wl.vs[0] = None
+    wl.vs[2] = None
+    out, plan = run_workload(wl, dtype=EMU)
+    pk.phiks_device_status(plan.handle)
+    errs = [rel_inf(out[L], ta.lincomb(wl.A, wl.tau, wl.vs, 2.0 ** -L)) for L in range(3)]
+    print("emu lincomb without v0, v2 errs", ["%.2e" % e for e in errs])
+    assert max(errs) < 1e-12
