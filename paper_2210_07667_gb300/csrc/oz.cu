@@ -219,8 +219,9 @@ __global__ void oz_prep_b_kernel(PrepBatch pb) {
 
 // T 2^e rounded to a double, T = sum_k G_k 2^(8 (6 - k)) for the exact
 // integer accumulators G_0..G_6 (FP32 bit patterns, |G_k| < 2^24): with
-// |T| < 2^70 for n <= 128, S = floor(T / 2^8) fits 63 bits and is rounded to
-// 53 bits (half up on the magnitude), an error below (1/2 + 2^-8) ulp.
+// |T| < 2^70 for n <= 128, S = floor(T / 2^8) fits 63 bits; its conversion
+// to double rounds to nearest (an error below (1/2 + 2^-8) ulp of T 2^e in
+// all), and 2^(e + 8) enters the exponent field.
 __device__ __forceinline__ double oz_assemble(const uint32_t* G, int e) {
   int g[kOzSlices];
 #pragma unroll
@@ -232,17 +233,11 @@ __device__ __forceinline__ double oz_assemble(const uint32_t* G, int e) {
   lo = lo * 256 + g[6];
   const long long S = hi * 65536 + (lo >> 8);
   if (S == 0) return 0.0;
-  const unsigned long long sign = (unsigned long long)S & (1ull << 63);
-  const unsigned long long a = S < 0 ? 0ull - (unsigned long long)S : (unsigned long long)S;
-  const int lz = __clzll((long long)a);
-  const unsigned long long nm = a << lz;                      // leading one at bit 63
-  const unsigned long long m = (nm >> 11) + ((nm >> 10) & 1ull);  // in [2^52, 2^53]
-  const int be = e + 1094 - lz;                               // biased exponent of a 2^(e + 8)
-  if (be <= 0) return __longlong_as_double((long long)sign);
-  if (be >= 2047) return __longlong_as_double((long long)(sign | (0x7FFull << 52)));
-  // m = 2^53 carries into the exponent field (and to infinity from be = 2046)
-  const unsigned long long bits = ((unsigned long long)(be - 1) << 52) + m;
-  return __longlong_as_double((long long)(bits | sign));
+  const long long d = __double_as_longlong(__ll2double_rn(S));
+  const int be = (int)((d >> 52) & 0x7FF) + e + 8;  // biased exponent of the result
+  if (be <= 0) return __longlong_as_double(d & (1ll << 63));  // below the normal range: signed zero
+  if (be >= 2047) return __longlong_as_double((d & (1ll << 63)) | (0x7FFll << 52));
+  return __longlong_as_double(d + ((long long)(e + 8) << 52));
 }
 
 struct OzParams {
@@ -404,7 +399,7 @@ __global__ void __launch_bounds__(NTH, 1)
     const int q = warp & 3;  // TMEM lane quarter of this warp
     constexpr int GROUPS = kOzEpiWarps / 4;   // warps per lane quarter
     constexpr int CW = NT / GROUPS;           // columns per warp
-    constexpr int CH = 4;                     // columns per TMEM load
+    constexpr int CH = CW >= 8 ? 8 : 4;       // columns per TMEM load
     static_assert(CW % CH == 0, "epilogue column split");
     const int grp = (warp - 2) >> 2;
     const int row = q * 32 + lane;
@@ -425,8 +420,13 @@ __global__ void __launch_bounds__(NTH, 1)
       for (int c0 = grp * CW; c0 < (grp + 1) * CW; c0 += CH) {
         const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * SET + (uint32_t)c0;
         uint32_t G[kOzSlices][CH];
+        if constexpr (CH == 8) {
 #pragma unroll
-        for (int k = 0; k < kOzSlices; ++k) tmem_ld4_nowait(tb + (uint32_t)(k * NT), G[k]);
+          for (int k = 0; k < kOzSlices; ++k) tmem_ld8_nowait(tb + (uint32_t)(k * NT), G[k]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < kOzSlices; ++k) tmem_ld4_nowait(tb + (uint32_t)(k * NT), G[k]);
+        }
         tmem_wait_ld();
         if (!valid) continue;
         // independent assemblies (lscale has n_pad >= every tile's columns
