@@ -183,9 +183,10 @@ def measured_peaks():
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one oz_gemm_kernel<32> launch
-# running four mu-mode products (ncu capture, profiles/oz_gemm_fp64emu_adr3d_n64.md),
-# per product; None once the kernel has changed since the capture
-OZ_GEMM_TRAFFIC_PER_PRODUCT = 14.8298e6 / 4
+# running four mu-mode products (ncu capture of the current kernel,
+# profiles/oz_gemm_fp64emu_adr3d_n64.md), per product; None once the kernel has
+# changed since the capture
+OZ_GEMM_TRAFFIC_PER_PRODUCT = 14.8331e6 / 4
 
 
 def run_phiks(args):
