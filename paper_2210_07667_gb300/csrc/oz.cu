@@ -163,11 +163,15 @@ __global__ void __launch_bounds__(kSplitThreads) oz_split_kernel(const __grid_co
     }
   }
   if (y >= jb.ntensor) return;  // a combination only (uniform over the block)
-  __syncthreads();
-  if (active) atomicMax(&emax[fl], E);
-  __syncthreads();
+  if ((cpf & (cpf - 1)) == 0) {  // (uniform) a fibre's threads are cpf <= 32 consecutive lanes
+    for (int o = 1; o < cpf; o <<= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+  } else {
+    __syncthreads();
+    if (active) atomicMax(&emax[fl], E);
+    __syncthreads();
+    E = emax[fl];
+  }
   if (!active) return;
-  E = emax[fl];
   uint32_t w[kOzSlices][4];
 #pragma unroll
   for (int j = 0; j < 8; j += 2) {
