@@ -1351,6 +1351,149 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
   return PHIKS_OK;
 }
 
+// SAME form on the FP64_EMU path under the conditions of run_lincomb_emu
+// (and p <= 7): the operators and combinations of run_same, every batch's
+// FP64 combinations (quadrature sums, eq. (simul), copies of the outputs)
+// evaluated by the next batch's first split pass.
+phiks_status run_same_emu(Ctx& c, const Bank* B, int s, int p, const void* v, const phiks_options& o,
+                          double** acc, void* out) {
+  phiks_plan_s* P = c.P;
+  const int64_t NR = P->NR;
+  const int q = (int)B->theta.size();
+  const int per = p + (o.skip_phi0 ? 0 : 1);
+  const int s0 = o.skip_phi0 ? 0 : 1;  // slot of phi_1 in an output block
+  auto add = [](Combo& x, const double* src, double coef) -> phiks_status {
+    if (x.nsrc >= kMaxSrc) return fail(PHIKS_ERR_INVALID, "combination of more than %d terms", kMaxSrc);
+    x.src[x.nsrc] = src;
+    x.coef[x.nsrc++] = coef;
+    return PHIKS_OK;
+  };
+  auto slot = [&](int Lv, int k) { return (double*)((char*)out + ((size_t)Lv * per + k) * P->N * 8); };
+  Combo pend[PHIKS_MAX_P];  // phi_1..phi_p at the current scale, not yet evaluated
+  for (int l = 0; l < p; ++l) pend[l] = make_combo();
+  std::vector<std::pair<Combo, double*>> pout;
+  // quadrature: phi_l += w_i theta_i^(l-1)/(l-1)! exp((1-theta_i)K/2^s) v
+  std::vector<int> nodes;
+  for (int i = 0; i < q; ++i) {
+    if (B->node_bank[i] >= 0) {
+      nodes.push_back(i);
+    } else {  // theta = 1: exp(0) = I
+      for (int t = 0; t < p; ++t) TRY(add(pend[t], (const double*)v, B->w[i] / factorial(t)));
+    }
+  }
+  for (size_t k0 = 0; k0 < nodes.size();) {
+    OzPrologue pro;
+    std::memset(&pro, 0, sizeof pro);
+    if (k0 > 0) {  // the sums so far into acc
+      for (int t = 0; t < p; ++t) {
+        pro.side[pro.nside] = pend[t];
+        pro.side_out[pro.nside++] = acc[t];
+        pend[t] = make_combo();
+        TRY(add(pend[t], acc[t], 1.0));
+      }
+    }
+    int lead = 0;
+    for (int t = 0; t < p; ++t) lead = std::max(lead, pend[t].nsrc);
+    const int nb = (int)std::min<size_t>({nodes.size() - k0, (size_t)c.bmax, (size_t)(kMaxSrc - lead)});
+    if (nb < 1) return fail(PHIKS_ERR_INVALID, "node batch of %d operators", nb);
+    Combo ins[kOzMaxBatch];
+    Mats Ls[kOzMaxBatch];
+    for (int k = 0; k < nb; ++k) {
+      ins[k] = plain(v, false);
+      bank_ptrs(P, B, B->node_bank[nodes[k0 + k]], &Ls[k]);
+    }
+    const double* R = nullptr;
+    TRY(tucker_mixed(c, nb, ins, Ls, &R, &pro));
+    for (int k = 0; k < nb; ++k) {
+      const double th = B->theta[nodes[k0 + k]], w = B->w[nodes[k0 + k]];
+      for (int t = 0; t < p; ++t) TRY(add(pend[t], R + (size_t)k * NR, w * std::pow(th, t) / factorial(t)));
+    }
+    k0 += nb;
+  }
+  // squaring, eq. (simul)
+  Mats M;
+  bank_ptrs(P, B, B->b0, &M);
+  int mbuf = 0;
+  double* A[PHIKS_MAX_P];
+  double* Anext[PHIKS_MAX_P];
+  for (int l = 0; l < p; ++l) {
+    A[l] = c.acc2[l];  // pend may read acc
+    Anext[l] = acc[l];
+  }
+  if (s < o.nscales)
+    for (int t = 0; t < p; ++t) pout.push_back({pend[t], slot(s, s0 + t)});
+  for (int j = s; j >= 1; --j) {
+    Mats Mn = M;  // exp(K/2^(j-1)), squared beside this level's Tuckers
+    bool aside = false;
+    TRY(begin_square(c, Mn, mbuf, &aside));
+    Combo ins[PHIKS_MAX_P + 2];
+    Mats Ls[PHIKS_MAX_P + 2];
+    OzPrologue pro;
+    std::memset(&pro, 0, sizeof pro);
+    int nb = 0;
+    for (int l = p; l >= 1; --l) {  // operator l at index p - l
+      ins[nb] = pend[l - 1];
+      pro.store[nb] = A[l - 1];
+      Ls[nb++] = M;
+    }
+    int ie = -1, ie0 = -1;
+    if (!o.skip_phi0 && j < o.nscales) {  // phi_0 = exp(K/2^j) v of scale j
+      ie = nb;
+      ins[nb] = plain(v, false);
+      Ls[nb++] = M;
+    }
+    if (!o.skip_phi0 && j == 1) {  // phi_0 of scale 0, with its own matrices exp(K)
+      TRY(finish_square(c, aside));
+      aside = false;
+      ie0 = nb;
+      ins[nb] = plain(v, false);
+      Ls[nb++] = Mn;
+    }
+    if (pout.size() > (size_t)kOzMaxSide) return fail(PHIKS_ERR_INVALID, "too many pending outputs");
+    for (auto& x : pout) {
+      pro.side[pro.nside] = x.first;
+      pro.side_out[pro.nside++] = x.second;
+    }
+    pout.clear();
+    const double* R = nullptr;
+    TRY(tucker_mixed(c, nb, ins, Ls, &R, &pro));
+    for (int l = p; l >= 1; --l) {
+      Combo x = make_combo();
+      TRY(add(x, R + (size_t)(p - l) * NR, std::ldexp(1.0, -l)));
+      for (int k = 1; k <= l; ++k) TRY(add(x, A[k - 1], std::ldexp(1.0, -l) / factorial(l - k)));
+      pend[l - 1] = x;
+    }
+    if (ie >= 0) {
+      Combo x = make_combo();
+      TRY(add(x, R + (size_t)ie * NR, 1.0));
+      pout.push_back({x, slot(j, 0)});
+    }
+    if (ie0 >= 0) {
+      Combo x = make_combo();
+      TRY(add(x, R + (size_t)ie0 * NR, 1.0));
+      pout.push_back({x, slot(0, 0)});
+    }
+    if (j - 1 < o.nscales)
+      for (int t = 0; t < p; ++t) pout.push_back({pend[t], slot(j - 1, s0 + t)});
+    for (int l = 0; l < p; ++l) std::swap(A[l], Anext[l]);
+    TRY(finish_square(c, aside));
+    M = Mn;
+  }
+  std::vector<Epi> es;
+  for (auto& x : pout) {
+    Epi e = make_epi();
+    e.nout = 1;
+    e.out[0] = x.second;
+    e.nsrc = x.first.nsrc;
+    for (int m = 0; m < e.nsrc; ++m) {
+      e.src[m] = x.first.src[m];
+      e.a[0][m] = x.first.coef[m];
+    }
+    es.push_back(e);
+  }
+  return combine_many(c, es.data(), (int)es.size());
+}
+
 // FP64_EMU when a batch may mix matrices (oz_mixed_ok) and hold p + 2
 // operators, s >= 1: the operators and combinations of run_lincomb, but every
 // batch's FP64 combinations (quadrature sums, eq. (comb), the outputs) are
@@ -2025,7 +2168,10 @@ phiks_status phiks_apply_ex(phiks_plan_t P, double tau, int p, const void* const
     Bank* B = nullptr;
     TRY(get_bank(P, tau, s, q, o.rule, o.no_cache != 0, st, &B));
     if (kind == 0) {
-      TRY(run_same(c, B, s, p, v[0], o, acc, out));
+      if (emu_dtype(P) && oz_mixed_ok(P->oz) && p >= 1 && p <= 7 && s >= 1 && c.bmax >= p + 2)
+        TRY(run_same_emu(c, B, s, p, v[0], o, acc, out));
+      else
+        TRY(run_same(c, B, s, p, v[0], o, acc, out));
     } else {
       if (emu_dtype(P) && oz_mixed_ok(P->oz) && p >= 1 && s >= 1 && c.bmax >= p + 2)
         TRY(run_lincomb_emu(c, B, s, p, v, o, acc, out));

@@ -117,3 +117,21 @@ def test_lincomb_emulated_missing_vectors():
     errs = [rel_inf(out[L], ta.lincomb(wl.A, wl.tau, wl.vs, 2.0 ** -L)) for L in range(3)]
     print("emu lincomb without v0, v2 errs", ["%.2e" % e for e in errs])
     assert max(errs) < 1e-12
+
+
+@pytest.mark.parametrize("skip_phi0,nscales,p", [(True, 3, 3), (False, 1, 5)])
+def test_same_vector_emulated_scales(skip_phi0, nscales, p):
+    """SAME mode on the emulated path with phi_0 skipped or kept, several
+    scale outputs: every output against the oracle."""
+    dims = (64, 32, 64)
+    A = [wk.fd_adr_dirichlet(m, 1.0, a, 0.5) for m, a in zip(dims, (4.0, -2.0, 1.0))]
+    N = int(np.prod(dims))
+    wl = wk.Workload("adr3d_same", A, 8e-4, p, "same", nscales, [wk.uniform(23, N)], skip_phi0=skip_phi0)
+    out, plan = run_workload(wl, dtype=EMU)
+    pk.phiks_device_status(plan.handle)
+    ells = list(range(1 if skip_phi0 else 0, p + 1))
+    for L in range(nscales):
+        ex = ta.same(wl.A, wl.tau, wl.vs[0], p, c=2.0 ** -L, ells=ells)
+        for k in range(len(ells)):
+            e = rel_inf(out[L * len(ells) + k], ex[k])
+            assert e < 1e-12, (L, ells[k], e)
