@@ -93,7 +93,8 @@ typedef struct {
                             selection of Sec. 3.3 (both or neither) */
   const double* vnorms;  /* host, nv entries ||v_l||_2 (0 for NULL vectors), or
                             NULL: the norms are computed on the device and the
-                            call synchronises `stream` once to read them */
+                            call waits once for them to reach the host (see
+                            phiks_apply_ex) */
   void* workspace;       /* device workspace of >= phiks_workspace_size bytes,
                             or NULL for the plan's own */
   size_t workspace_bytes;
@@ -147,7 +148,12 @@ phiks_status phiks_apply(phiks_plan_t plan, double tau, int p, const void* const
  *              (the c^l convention of eq. scallincomb).
  * The first call for a given (tau, s, q) builds the small exponentials
  * exp((1 - theta_i) tau A_mu / 2^s) on the device and caches them in the plan.
- * Without opt->vnorms the call synchronises `stream` once (norms of v). */
+ * Without opt->vnorms the call waits once for the device norms of v to reach
+ * the host.  When an earlier call with the same tau, p, nv, NULL pattern of v
+ * and selection options selected (s, q), the call first enqueues its work with
+ * that (s, q) and waits for the norms while the device runs it; if the norms
+ * select another (s, q), it enqueues the work again with those (the results
+ * in `out` are the latter's once the stream has run). */
 phiks_status phiks_apply_ex(phiks_plan_t plan, double tau, int p, const void* const* v, int nv,
                             const phiks_options* opt, void* out, void* stream);
 

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -127,6 +128,10 @@ struct phiks_plan_s {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   double* d_norms = nullptr;
+  cudaEvent_t norms_ready = nullptr;  // the device norms are in h_norms
+  cudaEvent_t norms_done = nullptr;   // the device norms are in d_norms
+  cudaStream_t norm_stream = nullptr; // their copy to the host
+  std::map<std::vector<uint64_t>, std::array<int, 3>> spec;  // last (s, q, T#) per call shape
   double* h_norms = nullptr;  // pinned
   std::map<std::tuple<double, int, int, int, int, double, int, int, std::vector<int>>, Selection>
       param_cache;
@@ -1993,6 +1998,9 @@ void phiks_destroy(phiks_plan_t P) {
   cudaFree(P->expm_scratch);
   cudaFree(P->ws);
   cudaFree(P->d_norms);
+  if (P->norms_ready) cudaEventDestroy(P->norms_ready);
+  if (P->norms_done) cudaEventDestroy(P->norms_done);
+  if (P->norm_stream) cudaStreamDestroy(P->norm_stream);
   cudaFreeHost(P->h_norms);
   if (P->tc) tc_destroy(P->tc);
   if (P->oz) oz_destroy(P->oz);
@@ -2101,29 +2109,49 @@ phiks_status phiks_apply_ex(phiks_plan_t P, double tau, int p, const void* const
   const int64_t N = P->N;
   const size_t es = elt_size(P);
 
-  // vector norms (Sec. 3.3 uses ||v_l||_2)
+  // vector norms (Sec. 3.3 uses ||v_l||_2): given, or computed on the device
+  // and read back once the event `norms_ready` has passed
   double norms[PHIKS_MAX_P + 1] = {0};
+  int nidx[PHIKS_MAX_P + 1], ncnt = 0;
   if (o.vnorms) {
     for (int i = 0; i < nv; ++i) norms[i] = o.vnorms[i];
-  } else {
+  } else if (p > 0 && o.force_s < 0) {  // (only the selection reads them)
     const void* xs[PHIKS_MAX_P + 1];
-    int idx[PHIKS_MAX_P + 1], cnt = 0;
     for (int i = 0; i < nv; ++i)
       if (v[i]) {
-        idx[cnt] = i;
-        xs[cnt++] = v[i];
+        nidx[ncnt] = i;
+        xs[ncnt++] = v[i];
       }
-    if (cnt) {
-      CK(cudaMemsetAsync(P->d_norms, 0, cnt * 8, st));
-      CK(launch_sumsq(xs, cnt, P->NR, split_dtype(P), P->d_norms, st));
-      CK(cudaMemcpyAsync(P->h_norms, P->d_norms, cnt * 8, cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      for (int k = 0; k < cnt; ++k) norms[idx[k]] = std::sqrt(P->h_norms[k]);
+    if (ncnt) {
+      // the copy to the host runs on a stream of its own, so that the work
+      // enqueued after it on `st` does not wait for the copy
+      if (!P->norms_ready) {
+        CK(cudaEventCreateWithFlags(&P->norms_ready, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&P->norms_done, cudaEventDisableTiming));
+        CK(cudaStreamCreateWithFlags(&P->norm_stream, cudaStreamNonBlocking));
+      }
+      CK(cudaMemsetAsync(P->d_norms, 0, ncnt * 8, st));
+      CK(launch_sumsq(xs, ncnt, P->NR, split_dtype(P), P->d_norms, st));
+      CK(cudaEventRecord(P->norms_done, st));
+      CK(cudaStreamWaitEvent(P->norm_stream, P->norms_done, 0));
+      CK(cudaMemcpyAsync(P->h_norms, P->d_norms, ncnt * 8, cudaMemcpyDeviceToHost, P->norm_stream));
+      CK(cudaEventRecord(P->norms_ready, P->norm_stream));
     }
   }
+  auto read_norms = [&]() -> phiks_status {
+    if (!ncnt) return PHIKS_OK;
+    CK(cudaEventSynchronize(P->norms_ready));
+    for (int k = 0; k < ncnt; ++k) norms[nidx[k]] = std::sqrt(P->h_norms[k]);
+    return PHIKS_OK;
+  };
 
-  // (s, q) of Sec. 3.3
+  // (s, q) of Sec. 3.3.  When the norms come from the device and an earlier
+  // call with the same tau, p and options selected (s, q), the call runs with
+  // that selection while the norms are read back, and runs again if the norms
+  // select differently: the device does not wait for the host's selection.
   int s, q, T;
+  bool spec = false;
+  std::vector<uint64_t> skey;
   if (p == 0) {
     s = o.nscales - 1;  // exponential only: no quadrature
     q = (o.rule == PHIKS_RULE_GLL) ? 2 : 1;
@@ -2133,11 +2161,28 @@ phiks_status phiks_apply_ex(phiks_plan_t P, double tau, int p, const void* const
     q = o.force_q;
     T = tucker_count(kind, s, o.nscales, q, p);
   } else {
-    Selection sel;
-    TRY(select_cached(P, tau, p, kind, norms, nv, o, &sel));
-    s = sel.s;
-    q = sel.q;
-    T = sel.tcount;
+    uint64_t tb, tolb;
+    std::memcpy(&tb, &tau, 8);
+    std::memcpy(&tolb, &o.tol, 8);
+    skey = {tb, (uint64_t)p, (uint64_t)nv, (uint64_t)o.nscales, (uint64_t)o.rule, (uint64_t)o.qmin,
+            (uint64_t)o.qmax, tolb};
+    for (int i = 0; i < nv; ++i) skey.push_back(v[i] ? 1u : 0u);
+    auto it = P->spec.find(skey);
+    if (ncnt && !P->prof && it != P->spec.end()) {
+      s = it->second[0];
+      q = it->second[1];
+      T = it->second[2];
+      spec = true;
+    } else {
+      TRY(read_norms());
+      Selection sel;
+      TRY(select_cached(P, tau, p, kind, norms, nv, o, &sel));
+      s = sel.s;
+      q = sel.q;
+      T = sel.tcount;
+      if (P->spec.size() > 256) P->spec.clear();
+      P->spec[skey] = {s, q, T};
+    }
   }
   // workspace
   const size_t need = workspace_bytes(P, p);
@@ -2159,81 +2204,97 @@ phiks_status phiks_apply_ex(phiks_plan_t P, double tau, int p, const void* const
     }
     ws = (char*)P->ws;
   }
-  // everything from here on is device work on `st` (host state aside)
   int tuckers = 0;
-  auto body = [&]() -> phiks_status {
-    double* acc[PHIKS_MAX_P];
-    Ctx c{P, st, {nullptr, nullptr}, 0};
-    carve(c, p, ws, acc);
-    Bank* B = nullptr;
-    TRY(get_bank(P, tau, s, q, o.rule, o.no_cache != 0, st, &B));
-    if (kind == 0) {
-      if (emu_dtype(P) && oz_mixed_ok(P->oz) && p >= 1 && p <= 7 && s >= 1 && c.bmax >= p + 2)
-        TRY(run_same_emu(c, B, s, p, v[0], o, acc, out));
-      else
-        TRY(run_same(c, B, s, p, v[0], o, acc, out));
+  auto run_with = [&](int s, int q) -> phiks_status {
+    // everything from here on is device work on `st` (host state aside)
+    auto body = [&]() -> phiks_status {
+      double* acc[PHIKS_MAX_P];
+      Ctx c{P, st, {nullptr, nullptr}, 0};
+      carve(c, p, ws, acc);
+      Bank* B = nullptr;
+      TRY(get_bank(P, tau, s, q, o.rule, o.no_cache != 0, st, &B));
+      if (kind == 0) {
+        if (emu_dtype(P) && oz_mixed_ok(P->oz) && p >= 1 && p <= 7 && s >= 1 && c.bmax >= p + 2)
+          TRY(run_same_emu(c, B, s, p, v[0], o, acc, out));
+        else
+          TRY(run_same(c, B, s, p, v[0], o, acc, out));
+      } else {
+        if (emu_dtype(P) && oz_mixed_ok(P->oz) && p >= 1 && s >= 1 && c.bmax >= p + 2)
+          TRY(run_lincomb_emu(c, B, s, p, v, o, acc, out));
+        else
+          TRY(run_lincomb(c, B, s, p, v, o, acc, out));
+      }
+      CK(cudaGetLastError());
+      tuckers = c.tuckers;
+      return PHIKS_OK;
+    };
+
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cap));
+    Bank* hit = nullptr;
+    // (the legacy default stream cannot be captured)
+    if (o.graph && !P->prof && cap == cudaStreamCaptureStatusNone && st != nullptr &&
+        st != cudaStreamLegacy)
+      for (auto& b : P->banks)
+        if (b.tau == tau && b.s == s && b.q == q && b.rule == o.rule) hit = &b;
+    if (hit) {
+      // a bank exists, so the call allocates nothing: capture it once per key
+      std::vector<uint64_t> key;
+      uint64_t tb;
+      std::memcpy(&tb, &tau, 8);
+      key = {tb, (uint64_t)p, (uint64_t)nv, (uint64_t)(uintptr_t)out, (uint64_t)(uintptr_t)ws,
+             (uint64_t)s, (uint64_t)q, (uint64_t)o.rule, (uint64_t)o.nscales, (uint64_t)o.skip_phi0,
+             (uint64_t)o.no_cache, (uint64_t)(uintptr_t)hit->dev, (uint64_t)(uintptr_t)hit->tcb,
+             (uint64_t)(uintptr_t)P->expm_scratch};
+      for (int i = 0; i < nv; ++i) key.push_back((uint64_t)(uintptr_t)v[i]);
+      auto it = P->graphs.find(key);
+      if (it == P->graphs.end()) {
+        if (P->graphs.size() >= 64) drop_graphs(P);
+        const uint64_t l0 = phiks::kernel_launch_count();
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        const phiks_status r = body();
+        cudaGraph_t gr = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(st, &gr);
+        if (r != PHIKS_OK) {
+          if (gr) cudaGraphDestroy(gr);
+          return r;
+        }
+        if (ce != cudaSuccess) {
+          if (gr) cudaGraphDestroy(gr);
+          CK(ce);
+        }
+        phiks_plan_s::CallGraph cg;
+        const cudaError_t ie = cudaGraphInstantiate(&cg.exec, gr, 0);
+        cudaGraphDestroy(gr);
+        CK(ie);
+        // the captured launches were counted once; the first replay below runs them
+        cg.launches = phiks::kernel_launch_count() - l0;
+        cg.tuckers = tuckers;
+        it = P->graphs.emplace(key, cg).first;
+        CK(cudaGraphLaunch(it->second.exec, st));
+      } else {
+        CK(cudaGraphLaunch(it->second.exec, st));
+        phiks::count_launch(it->second.launches);
+      }
+      hit->stamp = ++P->clock;
+      tuckers = it->second.tuckers;
     } else {
-      if (emu_dtype(P) && oz_mixed_ok(P->oz) && p >= 1 && s >= 1 && c.bmax >= p + 2)
-        TRY(run_lincomb_emu(c, B, s, p, v, o, acc, out));
-      else
-        TRY(run_lincomb(c, B, s, p, v, o, acc, out));
+      TRY(body());
     }
-    CK(cudaGetLastError());
-    tuckers = c.tuckers;
     return PHIKS_OK;
   };
-
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  CK(cudaStreamIsCapturing(st, &cap));
-  Bank* hit = nullptr;
-  // (the legacy default stream cannot be captured)
-  if (o.graph && !P->prof && cap == cudaStreamCaptureStatusNone && st != nullptr &&
-      st != cudaStreamLegacy)
-    for (auto& b : P->banks)
-      if (b.tau == tau && b.s == s && b.q == q && b.rule == o.rule) hit = &b;
-  if (hit) {
-    // a bank exists, so the call allocates nothing: capture it once per key
-    std::vector<uint64_t> key;
-    uint64_t tb;
-    std::memcpy(&tb, &tau, 8);
-    key = {tb, (uint64_t)p, (uint64_t)nv, (uint64_t)(uintptr_t)out, (uint64_t)(uintptr_t)ws,
-           (uint64_t)s, (uint64_t)q, (uint64_t)o.rule, (uint64_t)o.nscales, (uint64_t)o.skip_phi0,
-           (uint64_t)o.no_cache, (uint64_t)(uintptr_t)hit->dev, (uint64_t)(uintptr_t)hit->tcb,
-           (uint64_t)(uintptr_t)P->expm_scratch};
-    for (int i = 0; i < nv; ++i) key.push_back((uint64_t)(uintptr_t)v[i]);
-    auto it = P->graphs.find(key);
-    if (it == P->graphs.end()) {
-      if (P->graphs.size() >= 64) drop_graphs(P);
-      const uint64_t l0 = phiks::kernel_launch_count();
-      CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-      const phiks_status r = body();
-      cudaGraph_t gr = nullptr;
-      const cudaError_t ce = cudaStreamEndCapture(st, &gr);
-      if (r != PHIKS_OK) {
-        if (gr) cudaGraphDestroy(gr);
-        return r;
-      }
-      if (ce != cudaSuccess) {
-        if (gr) cudaGraphDestroy(gr);
-        CK(ce);
-      }
-      phiks_plan_s::CallGraph cg;
-      const cudaError_t ie = cudaGraphInstantiate(&cg.exec, gr, 0);
-      cudaGraphDestroy(gr);
-      CK(ie);
-      // the captured launches were counted once; the first replay below runs them
-      cg.launches = phiks::kernel_launch_count() - l0;
-      cg.tuckers = tuckers;
-      it = P->graphs.emplace(key, cg).first;
-      CK(cudaGraphLaunch(it->second.exec, st));
-    } else {
-      CK(cudaGraphLaunch(it->second.exec, st));
-      phiks::count_launch(it->second.launches);
+  TRY(run_with(s, q));
+  if (spec) {  // the norms of this call, while the device runs
+    TRY(read_norms());
+    Selection sel;
+    TRY(select_cached(P, tau, p, kind, norms, nv, o, &sel));
+    if (sel.s != s || sel.q != q) {
+      s = sel.s;
+      q = sel.q;
+      T = sel.tcount;
+      P->spec[skey] = {s, q, T};
+      TRY(run_with(s, q));
     }
-    hit->stamp = ++P->clock;
-    tuckers = it->second.tuckers;
-  } else {
-    TRY(body());
   }
   P->last_s = s;
   P->last_q = q;

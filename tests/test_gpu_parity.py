@@ -163,6 +163,42 @@ def test_caller_norms_skip_the_sync_and_agree():
     assert torch.equal(o1, o2)
 
 
+@pytest.mark.parametrize("dtype", [pk.PHIKS_FP64, pk.PHIKS_FP64_EMU])
+def test_norms_that_change_the_selection(dtype):
+    """Repeated calls with the same tau and p run first with the previous
+    selection while the device norms are read back; a vector 1e8 times larger
+    selects another (s, q) and must still give the result of its own
+    selection."""
+    wl = wk.small_same(32) if dtype == pk.PHIKS_FP64 else wk.adr3d_lincomb(p=4, dims=(64, 32, 64), nscales=1)
+    plan = pk.Plan(wl.A, dtype)
+    if wl.mode == "same":
+        vs_small = [dev(wl.vs[0])]
+        out = torch.empty((wl.p + 1) * wl.N, device="cuda", dtype=torch.float64)
+    else:
+        vs_small = [dev(v) for v in wl.vs]
+        out = torch.empty(wl.N, device="cuda", dtype=torch.float64)
+    vs_big = [x * 1e8 for x in vs_small]
+    sel = []
+    for vs in (vs_small, vs_small, vs_big, vs_big, vs_small):
+        plan.apply(wl.tau, wl.p, vs, out, nscales=1)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().reshape(-1, wl.N)
+        scale = 1e8 if vs is vs_big else 1.0
+        if wl.mode == "same":
+            ex = _exact_same(wl) * scale
+        else:
+            ex = np.stack([ta.lincomb(wl.A, wl.tau, wl.vs, 1.0)]) * scale
+        for k in range(got.shape[0]):
+            assert rel_inf(got[k], ex[k]) < 1e-12, k
+        s, q, T, _ = plan.last_params()
+        norms = [float(np.linalg.norm(x.cpu().numpy())) for x in vs]
+        ref = plan.select_params(wl.tau, wl.p, norms)
+        assert (s, q) == (ref[0], ref[1])
+        sel.append((s, q))
+    assert sel[0] != sel[2], sel  # the large vectors do select differently
+    plan.close()
+
+
 @pytest.mark.parametrize("dims", [(5,), (70, 3), (33, 8, 17), (4, 3, 2, 5)])
 def test_tucker_entry_point(dims):
     rng = np.random.default_rng(3)
