@@ -739,8 +739,13 @@ def run_served(args):
         for a32, a64 in zip(requests, req64):
             for x, y in zip(a32, a64):
                 o, r = x["out"].double().cpu().numpy(), y["out"].cpu().numpy()
-                errs.append(float(np.abs(o - r).max() / np.abs(r).max()))
-        res[name]["rel_err_vs_fp64_max"] = max(errs)
+                den = np.abs(r).max()
+                errs.append(float(np.abs(o - r).max() / den) if den > 0 else float("nan"))
+        errs = np.array(errs)
+        res[name]["rel_err_vs_fp64_max"] = float(np.nanmax(errs)) if np.isfinite(errs).any() else None
+        res[name]["rel_err_vs_fp64_median"] = float(np.nanmedian(errs)) if np.isfinite(errs).any() else None
+        res[name]["outputs_compared"] = int(np.isfinite(errs).sum())
+        res[name]["outputs_not_finite_or_zero_ref"] = int((~np.isfinite(errs)).sum())
         for p in plans64.values():
             p.close()
     h = res[name]

@@ -229,7 +229,12 @@ int tucker_batch_max(const phiks_plan_s* P, int p) {
     const int64_t floor_p = std::min(kOzMaxBatch, std::max(p, 1) + 1);
     return (int)std::max<int64_t>(floor_p, std::min<int64_t>(kOzMaxBatch, by_mem));
   }
-  return split_dtype(P) ? kTcMaxBatch : 1;
+  if (split_dtype(P)) {  // operand planes and temporaries: about 32 bytes per element and operator
+    const int64_t by_mem = ((int64_t)2 << 30) / (32 * std::max<int64_t>(P->N, 1));
+    const int64_t floor_p = std::min(kTcMaxBatch, std::max(p, 1) + 1);
+    return (int)std::max<int64_t>(floor_p, std::min<int64_t>(kTcMaxBatch, by_mem));
+  }
+  return 1;
 }
 
 size_t up1k(size_t x) { return (x + 1023) / 1024 * 1024; }
@@ -256,7 +261,7 @@ WsLayout ws_layout(const phiks_plan_s* P, int p) {
     o += up1k(P->tcb_bytes);
     w.planes = o;
     o += up1k(emu_dtype(P) ? oz_workspace_bytes(P->d, P->n, P->N, tucker_batch_max(P, p))
-                           : tc_workspace_bytes(P->N));
+                           : tc_workspace_bytes(P->N, tucker_batch_max(P, p)));
   }
   w.total = o + 1024;  // room to align the base
   return w;
@@ -603,15 +608,14 @@ phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool 
     for (int b = 0; b < nbk; ++b)
       for (int mu = 0; mu < P->d; ++mu) {
         nb.tcoff[b][mu] = (size_t)b * P->tcb_bytes + P->tcb_off[mu];
-        if (emu_dtype(P)) {
-          srcs.push_back(nb.dev + nb.off[b][mu]);
-          ns.push_back((int)P->n[mu]);
-          dsts.push_back(nb.tcb + nb.tcoff[b][mu]);
-        } else {
-          CK(tc_prepare_b(P->dtype, nb.dev + nb.off[b][mu], (int)P->n[mu], nb.tcb + nb.tcoff[b][mu], st));
-        }
+        srcs.push_back(nb.dev + nb.off[b][mu]);
+        ns.push_back((int)P->n[mu]);
+        dsts.push_back(nb.tcb + nb.tcoff[b][mu]);
       }
-    if (!srcs.empty()) CK(oz_prepare_b((int)srcs.size(), srcs.data(), ns.data(), dsts.data(), st));
+    if (!srcs.empty()) {
+      if (emu_dtype(P)) CK(oz_prepare_b((int)srcs.size(), srcs.data(), ns.data(), dsts.data(), st));
+      else CK(tc_prepare_b_many(P->dtype, (int)srcs.size(), srcs.data(), ns.data(), dsts.data(), st));
+    }
   }
   nb.stamp = P->clock;
   if (hit) {
@@ -653,7 +657,7 @@ void carve(Ctx& c, int p, char* ws, double** acc) {
     c.msq_tcb[0] = (uint8_t*)(base + w.tcb0);
     c.msq_tcb[1] = (uint8_t*)(base + w.tcb1);
     if (emu_dtype(P)) oz_bind_workspace(P->oz, (void*)(base + w.planes), c.tmp[0], c.tmp[1], c.bmax);
-    else tc_bind_workspace(P->tc, (void*)(base + w.planes));
+    else tc_bind_workspace(P->tc, (void*)(base + w.planes), c.bmax);
   }
 }
 
@@ -717,7 +721,9 @@ phiks_status tucker(Ctx& c, const Combo& in, const Mats& M, const Epi* epi) {
   if (tc_path(P)) {
     cudaEvent_t e1;
     TRY(prof_begin(c, &e1));
-    cudaError_t e = tc_tucker(P->tc, 1, &in, M.B, epi, c.st);
+    TcMats tm;
+    for (int mu = 0; mu < P->d; ++mu) tm.B[mu] = M.B[mu];
+    cudaError_t e = tc_tucker(P->tc, 1, &in, &tm, epi, c.st);
     if (e != cudaSuccess)
       return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), tc_last_error());
     double fl = 0;
@@ -774,7 +780,10 @@ phiks_status tucker_batch(Ctx& c, int B, const Combo* in, const Mats& M, const E
     } else {  // events around the whole batch
       cudaEvent_t e1;
       TRY(prof_begin(c, &e1));
-      e = tc_tucker(P->tc, nb, in + b0, M.B, epi + b0, c.st);
+      TcMats tm[kTcMaxBatch];
+      for (int b = 0; b < nb; ++b)
+        for (int mu = 0; mu < P->d; ++mu) tm[b].B[mu] = M.B[mu];
+      e = tc_tucker(P->tc, nb, in + b0, tm, epi + b0, c.st);
       if (e == cudaSuccess) TRY(prof_end(c, e1, nb * fl));
     }
     if (e != cudaSuccess)
@@ -785,25 +794,89 @@ phiks_status tucker_batch(Ctx& c, int B, const Combo* in, const Mats& M, const E
   return PHIKS_OK;
 }
 
-// FP64_EMU with oz_mixed_ok: B <= c.bmax Tucker operators with their own
-// matrices M[b] in one batch, no epilogue; *res receives the results (tensor
-// b at *res + b N) for the caller's combination.
-phiks_status tucker_mixed(Ctx& c, int B, const Combo* in, const Mats* M, const double** res,
-                          const OzPrologue* pro = nullptr) {
+// Extensions of a batch's first split pass (the oz / tc prologues): the
+// tensors' input values also stored to store[b] (FP64, or null), and nside
+// further combinations evaluated into side_out[k] (float where bit k of
+// side_f32 is set; split dtypes only).
+struct BatchPro {
+  double* store[kOzMaxBatch > kTcMaxBatch ? kOzMaxBatch : kTcMaxBatch];
+  int nside;
+  unsigned side_f32;
+  Combo side[kOzMaxSide > kTcMaxSide ? kOzMaxSide : kTcMaxSide];
+  void* side_out[kOzMaxSide > kTcMaxSide ? kOzMaxSide : kTcMaxSide];
+};
+
+// Whether a tensor-core batch may mix matrices (every mode's fibre count a
+// multiple of 128).
+bool mixed_ok(const phiks_plan_s* P) {
+  if (emu_dtype(P)) return oz_mixed_ok(P->oz);
+  return split_dtype(P) && tc_mixed_ok(P->tc);
+}
+
+// Tensor-core paths with mixed_ok: B <= c.bmax Tucker operators with their
+// own matrices M[b] in one batch, no epilogue; *res receives the results
+// (tensor b at element b NR; float when *r32, the split dtypes, else double)
+// for the caller's combinations.
+phiks_status tucker_mixed(Ctx& c, int B, const Combo* in, const Mats* M, const void** res, bool* r32,
+                          const BatchPro* pro = nullptr) {
   phiks_plan_s* P = c.P;
   if (B < 1 || B > c.bmax) return fail(PHIKS_ERR_INVALID, "mixed batch of %d", B);
-  OzMats om[kOzMaxBatch];
-  for (int b = 0; b < B; ++b)
-    for (int mu = 0; mu < P->d; ++mu) om[b].B[mu] = M[b].B[mu];
   const bool prof = P->prof;
-  cudaEvent_t ev[2 * PHIKS_MAX_D];
-  if (prof)
-    for (int mu = 0; mu < P->d; ++mu) TRY(prof_pair(P, &ev[2 * mu], &ev[2 * mu + 1]));
-  cudaError_t e = oz_tucker(P->oz, B, in, om, nullptr, c.st, prof ? ev : nullptr, res, pro);
-  if (e != cudaSuccess)
-    return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), oz_last_error());
-  if (prof)
-    for (int mu = 0; mu < P->d; ++mu) P->prof_flops += 2.0 * B * (double)P->N * (double)P->n[mu];
+  cudaError_t e;
+  if (emu_dtype(P)) {
+    OzMats om[kOzMaxBatch];
+    for (int b = 0; b < B; ++b)
+      for (int mu = 0; mu < P->d; ++mu) om[b].B[mu] = M[b].B[mu];
+    OzPrologue op;
+    std::memset(&op, 0, sizeof op);
+    if (pro) {
+      if (pro->side_f32 || pro->nside > kOzMaxSide) return fail(PHIKS_ERR_INVALID, "prologue");
+      for (int b = 0; b < B; ++b) op.store[b] = pro->store[b];
+      op.nside = pro->nside;
+      for (int k = 0; k < pro->nside; ++k) {
+        op.side[k] = pro->side[k];
+        op.side_out[k] = (double*)pro->side_out[k];
+      }
+    }
+    cudaEvent_t ev[2 * PHIKS_MAX_D];
+    if (prof)
+      for (int mu = 0; mu < P->d; ++mu) TRY(prof_pair(P, &ev[2 * mu], &ev[2 * mu + 1]));
+    const double* R = nullptr;
+    e = oz_tucker(P->oz, B, in, om, nullptr, c.st, prof ? ev : nullptr, &R, pro ? &op : nullptr);
+    *res = R;
+    *r32 = false;
+    if (e != cudaSuccess)
+      return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), oz_last_error());
+    if (prof)
+      for (int mu = 0; mu < P->d; ++mu) P->prof_flops += 2.0 * B * (double)P->N * (double)P->n[mu];
+  } else {
+    TcMats tm[kTcMaxBatch];
+    for (int b = 0; b < B; ++b)
+      for (int mu = 0; mu < P->d; ++mu) tm[b].B[mu] = M[b].B[mu];
+    TcPrologue tp;
+    std::memset(&tp, 0, sizeof tp);
+    if (pro) {
+      if (pro->nside > kTcMaxSide) return fail(PHIKS_ERR_INVALID, "prologue");
+      for (int b = 0; b < B; ++b) tp.store[b] = pro->store[b];
+      tp.nside = pro->nside;
+      tp.side_f32 = pro->side_f32;
+      for (int k = 0; k < pro->nside; ++k) {
+        tp.side[k] = pro->side[k];
+        tp.side_out[k] = pro->side_out[k];
+      }
+    }
+    double fl = 0;
+    for (int mu = 0; mu < P->d; ++mu) fl += 2.0 * B * (double)P->N * (double)P->n[mu];
+    cudaEvent_t e1;
+    TRY(prof_begin(c, &e1));
+    const float* R = nullptr;
+    e = tc_tucker(P->tc, B, in, tm, nullptr, c.st, &R, pro ? &tp : nullptr);
+    *res = R;
+    *r32 = true;
+    if (e != cudaSuccess)
+      return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), tc_last_error());
+    TRY(prof_end(c, e1, fl));
+  }
   c.tuckers += B;
   return PHIKS_OK;
 }
@@ -860,11 +933,11 @@ phiks_status square_modes(Ctx& c, Mats& M, int& cur_buf) {
       srcs[mu] = M.L[mu];
       ns[mu] = (int)P->n[mu];
       dsts[mu] = dst;
-      if (!emu_dtype(P)) CK(tc_prepare_b(P->dtype, M.L[mu], (int)P->n[mu], dst, c.st));
       M.B[mu] = dst;
     }
   }
   if (emu_dtype(P)) CK(oz_prepare_b(P->d, srcs, ns, dsts, c.st));
+  else if (tc_path(P)) CK(tc_prepare_b_many(P->dtype, P->d, srcs, ns, dsts, c.st));
   cur_buf = 1 - cur_buf;
   return PHIKS_OK;
 }
@@ -971,8 +1044,10 @@ phiks_status run_same(Ctx& c, const Bank* B, int s, int p, const void* v, const 
         ins[k] = plain(v, f32);
         bank_ptrs(P, B, B->node_bank[nodes[k0 + k]], &Ls[k]);
       }
-      const double* R = nullptr;
-      TRY(tucker_mixed(c, nb, ins, Ls, &R));
+      const void* Rv = nullptr;
+      bool r32 = false;
+      TRY(tucker_mixed(c, nb, ins, Ls, &Rv, &r32));
+      const double* R = (const double*)Rv;  // (FP64_EMU: double results)
       Epi es[PHIKS_MAX_P];
       for (int t = 0; t < p; ++t) {
         Epi e = make_epi();
@@ -1194,8 +1269,10 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
     const int nb = (int)(k1 - k0);
     Mats Ls[kOzMaxBatch];
     for (int k = 0; k < nb; ++k) bank_ptrs(P, B, B->node_bank[mnodes[k0 + k]], &Ls[k]);
-    const double* R = nullptr;
-    TRY(tucker_mixed(c, nb, mins.data() + k0, Ls, &R));
+    const void* Rv = nullptr;
+    bool r32 = false;
+    TRY(tucker_mixed(c, nb, mins.data() + k0, Ls, &Rv, &r32));
+    const double* R = (const double*)Rv;  // (FP64_EMU: double results)
     Epi es[PHIKS_MAX_P];
     int ne = 0;
     for (int l = 1; l <= p; ++l) {
@@ -1328,8 +1405,10 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
         for (int k = 0; k < nb; ++k) Ls[k] = M;
         Ls[nb] = Mn;
         ins[nb] = plain(v[0], f32);
-        const double* R = nullptr;
-        TRY(tucker_mixed(c, nb + 1, ins, Ls, &R));
+        const void* Rv = nullptr;
+        bool r32 = false;
+        TRY(tucker_mixed(c, nb + 1, ins, Ls, &Rv, &r32));
+        const double* R = (const double*)Rv;  // (FP64_EMU: double results)
         Epi fs[PHIKS_MAX_P + 2];
         for (int k = 0; k < nb; ++k) {
           fs[k] = es[k];
@@ -1356,62 +1435,109 @@ phiks_status run_lincomb(Ctx& c, const Bank* B, int s, int p, const void* const*
   return PHIKS_OK;
 }
 
-// SAME form on the FP64_EMU path under the conditions of run_lincomb_emu
-// (and p <= 7): the operators and combinations of run_same, every batch's
-// FP64 combinations (quadrature sums, eq. (simul), copies of the outputs)
-// evaluated by the next batch's first split pass.
-phiks_status run_same_emu(Ctx& c, const Bank* B, int s, int p, const void* v, const phiks_options& o,
-                          double** acc, void* out) {
+// Combinations the batched forms carry from one batch to the next: sources
+// typed per term (bit m of f32mask: float).
+phiks_status add_term(Combo& x, const void* src, double coef, bool f32) {
+  if (x.nsrc >= kMaxSrc) return fail(PHIKS_ERR_INVALID, "combination of more than %d terms", kMaxSrc);
+  x.src[x.nsrc] = (const double*)src;
+  if (f32) x.f32mask |= 1 << x.nsrc;
+  x.coef[x.nsrc++] = coef;
+  return PHIKS_OK;
+}
+
+// An output combination due before the next batch's products.
+struct Pending {
+  Combo x;
+  void* out;
+};
+
+// The last batch's pending outputs: one combination pass (outputs float for
+// the split dtypes).
+phiks_status flush_pending(Ctx& c, const std::vector<Pending>& pout) {
+  std::vector<Epi> es;
+  for (auto& x : pout) {
+    Epi e = make_epi();
+    e.nout = 1;
+    e.out[0] = (double*)x.out;
+    e.out_f32mask = split_dtype(c.P) ? 1 : 0;
+    e.nsrc = x.x.nsrc;
+    e.src_f32mask = x.x.f32mask;
+    for (int m = 0; m < e.nsrc; ++m) {
+      e.src[m] = x.x.src[m];
+      e.a[0][m] = x.x.coef[m];
+    }
+    es.push_back(e);
+  }
+  return combine_many(c, es.data(), (int)es.size());
+}
+
+// Pending outputs as extra rows of a batch's first split pass.
+phiks_status pending_to_side(const Ctx& c, std::vector<Pending>& pout, BatchPro& pro) {
+  const int cap = emu_dtype(c.P) ? kOzMaxSide : kTcMaxSide;
+  if ((int)pout.size() + pro.nside > cap) return fail(PHIKS_ERR_INVALID, "too many pending outputs");
+  for (auto& x : pout) {
+    if (split_dtype(c.P)) pro.side_f32 |= 1u << pro.nside;
+    pro.side[pro.nside] = x.x;
+    pro.side_out[pro.nside++] = x.out;
+  }
+  pout.clear();
+  return PHIKS_OK;
+}
+
+// SAME form on the tensor-core paths when batches may mix matrices
+// (mixed_ok) and hold p + 2 operators, p <= 7: the operators and
+// combinations of run_same, every batch's FP64 combinations (quadrature sums,
+// eq. (simul), copies of the outputs) evaluated by the next batch's first
+// split pass.
+phiks_status run_same_batched(Ctx& c, const Bank* B, int s, int p, const void* v, const phiks_options& o,
+                              double** acc, void* out) {
   phiks_plan_s* P = c.P;
   const int64_t NR = P->NR;
+  const bool f32 = split_dtype(P);  // input and outputs float
   const int q = (int)B->theta.size();
   const int per = p + (o.skip_phi0 ? 0 : 1);
   const int s0 = o.skip_phi0 ? 0 : 1;  // slot of phi_1 in an output block
-  auto add = [](Combo& x, const double* src, double coef) -> phiks_status {
-    if (x.nsrc >= kMaxSrc) return fail(PHIKS_ERR_INVALID, "combination of more than %d terms", kMaxSrc);
-    x.src[x.nsrc] = src;
-    x.coef[x.nsrc++] = coef;
-    return PHIKS_OK;
-  };
-  auto slot = [&](int Lv, int k) { return (double*)((char*)out + ((size_t)Lv * per + k) * P->N * 8); };
+  auto slot = [&](int Lv, int k) { return (void*)((char*)out + ((size_t)Lv * per + k) * P->N * elt_size(P)); };
+  const void* R = nullptr;
+  bool r32 = false;
+  auto res = [&](int k) { return r32 ? (const void*)((const float*)R + (size_t)k * NR) : (const void*)((const double*)R + (size_t)k * NR); };
   Combo pend[PHIKS_MAX_P];  // phi_1..phi_p at the current scale, not yet evaluated
   for (int l = 0; l < p; ++l) pend[l] = make_combo();
-  std::vector<std::pair<Combo, double*>> pout;
+  std::vector<Pending> pout;
   // quadrature: phi_l += w_i theta_i^(l-1)/(l-1)! exp((1-theta_i)K/2^s) v
   std::vector<int> nodes;
   for (int i = 0; i < q; ++i) {
     if (B->node_bank[i] >= 0) {
       nodes.push_back(i);
     } else {  // theta = 1: exp(0) = I
-      for (int t = 0; t < p; ++t) TRY(add(pend[t], (const double*)v, B->w[i] / factorial(t)));
+      for (int t = 0; t < p; ++t) TRY(add_term(pend[t], v, B->w[i] / factorial(t), f32));
     }
   }
   for (size_t k0 = 0; k0 < nodes.size();) {
-    OzPrologue pro;
+    BatchPro pro;
     std::memset(&pro, 0, sizeof pro);
     if (k0 > 0) {  // the sums so far into acc
       for (int t = 0; t < p; ++t) {
         pro.side[pro.nside] = pend[t];
         pro.side_out[pro.nside++] = acc[t];
         pend[t] = make_combo();
-        TRY(add(pend[t], acc[t], 1.0));
+        TRY(add_term(pend[t], acc[t], 1.0, false));
       }
     }
     int lead = 0;
     for (int t = 0; t < p; ++t) lead = std::max(lead, pend[t].nsrc);
     const int nb = (int)std::min<size_t>({nodes.size() - k0, (size_t)c.bmax, (size_t)(kMaxSrc - lead)});
     if (nb < 1) return fail(PHIKS_ERR_INVALID, "node batch of %d operators", nb);
-    Combo ins[kOzMaxBatch];
-    Mats Ls[kOzMaxBatch];
+    Combo ins[kOzMaxBatch > kTcMaxBatch ? kOzMaxBatch : kTcMaxBatch];
+    Mats Ls[kOzMaxBatch > kTcMaxBatch ? kOzMaxBatch : kTcMaxBatch];
     for (int k = 0; k < nb; ++k) {
-      ins[k] = plain(v, false);
+      ins[k] = plain(v, f32);
       bank_ptrs(P, B, B->node_bank[nodes[k0 + k]], &Ls[k]);
     }
-    const double* R = nullptr;
-    TRY(tucker_mixed(c, nb, ins, Ls, &R, &pro));
+    TRY(tucker_mixed(c, nb, ins, Ls, &R, &r32, &pro));
     for (int k = 0; k < nb; ++k) {
       const double th = B->theta[nodes[k0 + k]], w = B->w[nodes[k0 + k]];
-      for (int t = 0; t < p; ++t) TRY(add(pend[t], R + (size_t)k * NR, w * std::pow(th, t) / factorial(t)));
+      for (int t = 0; t < p; ++t) TRY(add_term(pend[t], res(k), w * std::pow(th, t) / factorial(t), r32));
     }
     k0 += nb;
   }
@@ -1433,7 +1559,7 @@ phiks_status run_same_emu(Ctx& c, const Bank* B, int s, int p, const void* v, co
     TRY(begin_square(c, Mn, mbuf, &aside));
     Combo ins[PHIKS_MAX_P + 2];
     Mats Ls[PHIKS_MAX_P + 2];
-    OzPrologue pro;
+    BatchPro pro;
     std::memset(&pro, 0, sizeof pro);
     int nb = 0;
     for (int l = p; l >= 1; --l) {  // operator l at index p - l
@@ -1444,38 +1570,32 @@ phiks_status run_same_emu(Ctx& c, const Bank* B, int s, int p, const void* v, co
     int ie = -1, ie0 = -1;
     if (!o.skip_phi0 && j < o.nscales) {  // phi_0 = exp(K/2^j) v of scale j
       ie = nb;
-      ins[nb] = plain(v, false);
+      ins[nb] = plain(v, f32);
       Ls[nb++] = M;
     }
     if (!o.skip_phi0 && j == 1) {  // phi_0 of scale 0, with its own matrices exp(K)
       TRY(finish_square(c, aside));
       aside = false;
       ie0 = nb;
-      ins[nb] = plain(v, false);
+      ins[nb] = plain(v, f32);
       Ls[nb++] = Mn;
     }
-    if (pout.size() > (size_t)kOzMaxSide) return fail(PHIKS_ERR_INVALID, "too many pending outputs");
-    for (auto& x : pout) {
-      pro.side[pro.nside] = x.first;
-      pro.side_out[pro.nside++] = x.second;
-    }
-    pout.clear();
-    const double* R = nullptr;
-    TRY(tucker_mixed(c, nb, ins, Ls, &R, &pro));
+    TRY(pending_to_side(c, pout, pro));
+    TRY(tucker_mixed(c, nb, ins, Ls, &R, &r32, &pro));
     for (int l = p; l >= 1; --l) {
       Combo x = make_combo();
-      TRY(add(x, R + (size_t)(p - l) * NR, std::ldexp(1.0, -l)));
-      for (int k = 1; k <= l; ++k) TRY(add(x, A[k - 1], std::ldexp(1.0, -l) / factorial(l - k)));
+      TRY(add_term(x, res(p - l), std::ldexp(1.0, -l), r32));
+      for (int k = 1; k <= l; ++k) TRY(add_term(x, A[k - 1], std::ldexp(1.0, -l) / factorial(l - k), false));
       pend[l - 1] = x;
     }
     if (ie >= 0) {
       Combo x = make_combo();
-      TRY(add(x, R + (size_t)ie * NR, 1.0));
+      TRY(add_term(x, res(ie), 1.0, r32));
       pout.push_back({x, slot(j, 0)});
     }
     if (ie0 >= 0) {
       Combo x = make_combo();
-      TRY(add(x, R + (size_t)ie0 * NR, 1.0));
+      TRY(add_term(x, res(ie0), 1.0, r32));
       pout.push_back({x, slot(0, 0)});
     }
     if (j - 1 < o.nscales)
@@ -1484,42 +1604,39 @@ phiks_status run_same_emu(Ctx& c, const Bank* B, int s, int p, const void* v, co
     TRY(finish_square(c, aside));
     M = Mn;
   }
-  std::vector<Epi> es;
-  for (auto& x : pout) {
-    Epi e = make_epi();
-    e.nout = 1;
-    e.out[0] = x.second;
-    e.nsrc = x.first.nsrc;
-    for (int m = 0; m < e.nsrc; ++m) {
-      e.src[m] = x.first.src[m];
-      e.a[0][m] = x.first.coef[m];
-    }
-    es.push_back(e);
+  if (s == 0 && !o.skip_phi0) {  // no squaring: phi_0 = exp(K) v in a batch of its own
+    BatchPro pro;
+    std::memset(&pro, 0, sizeof pro);
+    TRY(pending_to_side(c, pout, pro));
+    Combo in = plain(v, f32);
+    TRY(tucker_mixed(c, 1, &in, &M, &R, &r32, &pro));
+    Combo x = make_combo();
+    TRY(add_term(x, res(0), 1.0, r32));
+    pout.push_back({x, slot(0, 0)});
   }
-  return combine_many(c, es.data(), (int)es.size());
+  return flush_pending(c, pout);
 }
 
-// FP64_EMU when a batch may mix matrices (oz_mixed_ok) and hold p + 2
-// operators, s >= 1: the operators and combinations of run_lincomb, but every
-// batch's FP64 combinations (quadrature sums, eq. (comb), the outputs) are
-// evaluated by the next batch's first split pass, which stores them and
-// splits those that are its Tucker inputs, so that no combination pass runs
-// between batches; the last batch's outputs take one combination pass.
-phiks_status run_lincomb_emu(Ctx& c, const Bank* B, int s, int p, const void* const* v,
-                             const phiks_options& o, double** acc, void* out) {
+// Linear-combination form on the tensor-core paths when batches may mix
+// matrices (mixed_ok) and hold p + 2 operators: the operators and
+// combinations of run_lincomb, but every batch's FP64 combinations
+// (quadrature sums, eq. (comb), the outputs) are evaluated by the next
+// batch's first split pass, which stores them and splits those that are its
+// Tucker inputs, so that no combination pass runs between batches; the last
+// batch's outputs take one combination pass.
+phiks_status run_lincomb_batched(Ctx& c, const Bank* B, int s, int p, const void* const* v,
+                                 const phiks_options& o, double** acc, void* out) {
   phiks_plan_s* P = c.P;
   const int64_t NR = P->NR;
+  const bool f32 = split_dtype(P);  // inputs and outputs float
   const int q = (int)B->theta.size();
-  auto add = [](Combo& x, const double* src, double coef) -> phiks_status {
-    if (x.nsrc >= kMaxSrc) return fail(PHIKS_ERR_INVALID, "combination of more than %d terms", kMaxSrc);
-    x.src[x.nsrc] = src;
-    x.coef[x.nsrc++] = coef;
-    return PHIKS_OK;
-  };
-  auto blk = [&](int Lv) { return (double*)((char*)out + (size_t)Lv * P->N * 8); };
+  auto blk = [&](int Lv) { return (void*)((char*)out + (size_t)Lv * P->N * elt_size(P)); };
+  const void* R = nullptr;
+  bool r32 = false;
+  auto res = [&](int k) { return r32 ? (const void*)((const float*)R + (size_t)k * NR) : (const void*)((const double*)R + (size_t)k * NR); };
   Combo pend[PHIKS_MAX_P];  // the accumulators' values, not yet evaluated
   for (int l = 0; l < p; ++l) pend[l] = make_combo();
-  std::vector<std::pair<Combo, double*>> pout;  // combinations due before the next batch's products
+  std::vector<Pending> pout;
   // quadrature: the theta = 1 node's terms, the others' Tucker operators
   std::vector<int> mnodes, mls;
   std::vector<Combo> mins;
@@ -1530,12 +1647,11 @@ phiks_status run_lincomb_emu(Ctx& c, const Bank* B, int s, int p, const void* co
       for (int k = 1; k <= l; ++k) {
         const void* vk = v[p + 1 - k];
         if (!vk) continue;
-        in.src[in.nsrc] = (const double*)vk;
-        in.coef[in.nsrc++] = std::pow(th, l - k) / factorial(l - k) * std::ldexp(1.0, -(l - k + 1) * s);
+        TRY(add_term(in, vk, std::pow(th, l - k) / factorial(l - k) * std::ldexp(1.0, -(l - k + 1) * s), f32));
       }
       if (in.nsrc == 0) continue;
       if (B->node_bank[i] < 0) {
-        for (int m = 0; m < in.nsrc; ++m) TRY(add(pend[l - 1], in.src[m], w * in.coef[m]));
+        for (int m = 0; m < in.nsrc; ++m) TRY(add_term(pend[l - 1], in.src[m], w * in.coef[m], f32));
         continue;
       }
       mnodes.push_back(i);
@@ -1545,14 +1661,14 @@ phiks_status run_lincomb_emu(Ctx& c, const Bank* B, int s, int p, const void* co
   }
   for (size_t k0 = 0; k0 < mins.size();) {
     // a later batch first evaluates the sums so far into acc
-    OzPrologue pro;
+    BatchPro pro;
     std::memset(&pro, 0, sizeof pro);
     if (k0 > 0) {
       for (int l = 0; l < p; ++l) {
         pro.side[pro.nside] = pend[l];
         pro.side_out[pro.nside++] = acc[l];
         pend[l] = make_combo();
-        TRY(add(pend[l], acc[l], 1.0));
+        TRY(add_term(pend[l], acc[l], 1.0, false));
       }
     }
     int lead = 1;
@@ -1568,11 +1684,10 @@ phiks_status run_lincomb_emu(Ctx& c, const Bank* B, int s, int p, const void* co
     }
     if (k1 == k0) return fail(PHIKS_ERR_INVALID, "node batch exceeds %d operators", c.bmax);
     const int nb = (int)(k1 - k0);
-    Mats Ls[kOzMaxBatch];
+    Mats Ls[kOzMaxBatch > kTcMaxBatch ? kOzMaxBatch : kTcMaxBatch];
     for (int k = 0; k < nb; ++k) bank_ptrs(P, B, B->node_bank[mnodes[k0 + k]], &Ls[k]);
-    const double* R = nullptr;
-    TRY(tucker_mixed(c, nb, mins.data() + k0, Ls, &R, &pro));
-    for (int k = 0; k < nb; ++k) TRY(add(pend[mls[k0 + k] - 1], R + (size_t)k * NR, B->w[mnodes[k0 + k]]));
+    TRY(tucker_mixed(c, nb, mins.data() + k0, Ls, &R, &r32, &pro));
+    for (int k = 0; k < nb; ++k) TRY(add_term(pend[mls[k0 + k] - 1], res(k), B->w[mnodes[k0 + k]], r32));
     k0 = k1;
   }
   // squaring, eq. (comb): level j evaluates its accumulators (stored to A)
@@ -1586,7 +1701,7 @@ phiks_status run_lincomb_emu(Ctx& c, const Bank* B, int s, int p, const void* co
     A[l] = c.acc2[l];  // pend may read acc
     Anext[l] = acc[l];
   }
-  const double* v0 = (const double*)v[0];
+  const void* v0 = v[0];
   if (!v0 && s < o.nscales) pout.push_back({pend[p - 1], blk(s)});
   for (int j = s; j >= 1; --j) {
     Mats Mn = M;  // exp(K/2^(j-1)), squared beside this level's Tuckers
@@ -1594,7 +1709,7 @@ phiks_status run_lincomb_emu(Ctx& c, const Bank* B, int s, int p, const void* co
     TRY(begin_square(c, Mn, mbuf, &aside));
     Combo ins[PHIKS_MAX_P + 2];
     Mats Ls[PHIKS_MAX_P + 2];
-    OzPrologue pro;
+    BatchPro pro;
     std::memset(&pro, 0, sizeof pro);
     int nb = 0;
     for (int l = p; l >= 1; --l) {  // operator l at index p - l
@@ -1605,39 +1720,34 @@ phiks_status run_lincomb_emu(Ctx& c, const Bank* B, int s, int p, const void* co
     int ie = -1, ie0 = -1;
     if (v0 && j < o.nscales) {  // exp(K/2^j) v_0 for the output of scale j
       ie = nb;
-      ins[nb] = plain(v0, false);
+      ins[nb] = plain(v0, f32);
       Ls[nb++] = M;
     }
     if (v0 && j == 1) {  // exp(K) v_0 for the output of scale 0, with its own matrices
       TRY(finish_square(c, aside));
       aside = false;
       ie0 = nb;
-      ins[nb] = plain(v0, false);
+      ins[nb] = plain(v0, f32);
       Ls[nb++] = Mn;
     }
-    if (pout.size() > (size_t)kOzMaxSide) return fail(PHIKS_ERR_INVALID, "too many pending outputs");
-    for (auto& x : pout) {
-      pro.side[pro.nside] = x.first;
-      pro.side_out[pro.nside++] = x.second;
-    }
-    pout.clear();
-    const double* R = nullptr;
-    TRY(tucker_mixed(c, nb, ins, Ls, &R, &pro));
+    TRY(pending_to_side(c, pout, pro));
+    TRY(tucker_mixed(c, nb, ins, Ls, &R, &r32, &pro));
     for (int l = p; l >= 1; --l) {
       Combo x = make_combo();
-      TRY(add(x, R + (size_t)(p - l) * NR, 1.0));
-      for (int k = 1; k <= l; ++k) TRY(add(x, A[k - 1], 1.0 / (factorial(l - k) * std::ldexp(1.0, (l - k) * j))));
+      TRY(add_term(x, res(p - l), 1.0, r32));
+      for (int k = 1; k <= l; ++k)
+        TRY(add_term(x, A[k - 1], 1.0 / (factorial(l - k) * std::ldexp(1.0, (l - k) * j)), false));
       pend[l - 1] = x;
     }
     if (ie >= 0) {
       Combo x = make_combo();
-      TRY(add(x, R + (size_t)ie * NR, 1.0));
-      TRY(add(x, A[p - 1], 1.0));
+      TRY(add_term(x, res(ie), 1.0, r32));
+      TRY(add_term(x, A[p - 1], 1.0, false));
       pout.push_back({x, blk(j)});
     }
     if (ie0 >= 0) {
       Combo x = pend[p - 1];
-      TRY(add(x, R + (size_t)ie0 * NR, 1.0));
+      TRY(add_term(x, res(ie0), 1.0, r32));
       pout.push_back({x, blk(0)});
     } else if (!v0 && j - 1 < o.nscales) {
       pout.push_back({pend[p - 1], blk(j - 1)});
@@ -1646,19 +1756,17 @@ phiks_status run_lincomb_emu(Ctx& c, const Bank* B, int s, int p, const void* co
     TRY(finish_square(c, aside));
     M = Mn;
   }
-  std::vector<Epi> es;
-  for (auto& x : pout) {
-    Epi e = make_epi();
-    e.nout = 1;
-    e.out[0] = x.second;
-    e.nsrc = x.first.nsrc;
-    for (int m = 0; m < e.nsrc; ++m) {
-      e.src[m] = x.first.src[m];
-      e.a[0][m] = x.first.coef[m];
-    }
-    es.push_back(e);
+  if (s == 0 && v0) {  // no squaring: exp(K) v_0 in a batch of its own
+    BatchPro pro;
+    std::memset(&pro, 0, sizeof pro);
+    TRY(pending_to_side(c, pout, pro));
+    Combo in = plain(v0, f32);
+    TRY(tucker_mixed(c, 1, &in, &M, &R, &r32, &pro));
+    Combo x = pend[p - 1];
+    TRY(add_term(x, res(0), 1.0, r32));
+    pout.push_back({x, blk(0)});
   }
-  return combine_many(c, es.data(), (int)es.size());
+  return flush_pending(c, pout);
 }
 
 phiks_status check_opts(const phiks_options& o) {
@@ -2214,13 +2322,13 @@ phiks_status phiks_apply_ex(phiks_plan_t P, double tau, int p, const void* const
       Bank* B = nullptr;
       TRY(get_bank(P, tau, s, q, o.rule, o.no_cache != 0, st, &B));
       if (kind == 0) {
-        if (emu_dtype(P) && oz_mixed_ok(P->oz) && p >= 1 && p <= 7 && s >= 1 && c.bmax >= p + 2)
-          TRY(run_same_emu(c, B, s, p, v[0], o, acc, out));
+        if (tc_path(P) && mixed_ok(P) && p >= 1 && p <= 7 && c.bmax >= p + 2)
+          TRY(run_same_batched(c, B, s, p, v[0], o, acc, out));
         else
           TRY(run_same(c, B, s, p, v[0], o, acc, out));
       } else {
-        if (emu_dtype(P) && oz_mixed_ok(P->oz) && p >= 1 && s >= 1 && c.bmax >= p + 2)
-          TRY(run_lincomb_emu(c, B, s, p, v, o, acc, out));
+        if (tc_path(P) && mixed_ok(P) && p >= 1 && c.bmax >= p + 2)
+          TRY(run_lincomb_batched(c, B, s, p, v, o, acc, out));
         else
           TRY(run_lincomb(c, B, s, p, v, o, acc, out));
       }

@@ -93,16 +93,21 @@ struct GemmParams {
   int stages;
   int tmem_cols;
   int last;       // 0: write planes for the next pass; 1: write FP32 results to out0
+  int mixed;      // tensors with their own matrices (every tile within one tensor)
   void* out0;
   void* out1;
   int* status;
 };
 
+// TMA maps of the B planes (hi, lo) of tensor b's matrix (entry 0 unless mixed).
+struct TcMapsB {
+  CUtensorMap b[kTcMaxBatch][2];
+};
+
 template <int KIND, int NP>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
-                   const __grid_constant__ CUtensorMap mapB0, const __grid_constant__ CUtensorMap mapB1,
-                   GemmParams P) {
+                   const __grid_constant__ TcMapsB mapsB, const __grid_constant__ GemmParams P) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int S = P.stages;
@@ -152,6 +157,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int t = blockIdx.x; t < P.num_tiles && ok; t += gridDim.x) {
         const int m0 = (t / P.n_ntiles) * BM;
         const int r0 = (t % P.n_ntiles) * P.ntile;
+        const int mi = P.mixed ? (int)(m0 / P.M2) : 0;
+        const CUtensorMap* mapB0 = &mapsB.b[mi][0];
+        const CUtensorMap* mapB1 = &mapsB.b[mi][1];
         for (int kc = 0; kc < P.nk && ok; ++kc) {
           if (!mbar_wait(&empty[s], ph ^ 1, P.status, 1)) {
             ok = false;
@@ -162,8 +170,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int x = kc * (128 / (KIND == 0 ? 2 : 4));
           tma_load_2d(st, &mapA0, &full[s], x, m0);
           if (NP == 2) tma_load_2d(st + a_plane, &mapA1, &full[s], x, m0);
-          tma_load_2d(st + NP * a_plane, &mapB0, &full[s], x, r0);
-          if (NP == 2) tma_load_2d(st + NP * a_plane + b_plane, &mapB1, &full[s], x, r0);
+          tma_load_2d(st + NP * a_plane, mapB0, &full[s], x, r0);
+          if (NP == 2) tma_load_2d(st + NP * a_plane + b_plane, mapB1, &full[s], x, r0);
           if (++s == S) {
             s = 0;
             ph ^= 1;
@@ -279,16 +287,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // combination is formed in FP64 only when it has more than one term or a
 // coefficient other than one; the split itself runs in FP32 (the planes carry
 // at most 22 significant bits, FP32 holds 24).
-struct ComboBatch {
-  Combo c[kTcMaxBatch];
+// Grid rows of a split launch: rows below ntensor are the batch's tensors
+// (split into planes, and their FP64 values also stored where store[y] is not
+// null); the rest evaluate their combination into store[y] only (float when
+// bit y of store_f32 is set).
+struct TcSplitJobs {
+  Combo c[kTcMaxBatch + kTcMaxSide];
+  void* store[kTcMaxBatch + kTcMaxSide];
+  unsigned store_f32;
+  int ntensor;
 };
 
 template <int KIND, int NP>
-__global__ void tc_split_kernel(ComboBatch inb, int64_t N, void* p0, void* p1) {
+__global__ void tc_split_kernel(const __grid_constant__ TcSplitJobs jb, int64_t N, void* p0, void* p1) {
   pdl_wait();
-  const Combo& in = inb.c[blockIdx.y];
-  const int64_t off = (int64_t)blockIdx.y * N;  // tensor b's elements in the planes
-  const bool plain = in.nsrc == 1 && in.coef[0] == 1.0;
+  const int y = blockIdx.y;
+  const Combo& in = jb.c[y];
+  void* const xout = jb.store[y];
+  const bool out32 = (jb.store_f32 >> y) & 1;
+  const bool split = y < jb.ntensor;
+  const int64_t off = (int64_t)y * N;  // tensor b's elements in the planes
+  const bool plain = in.nsrc == 1 && in.coef[0] == 1.0 && !xout;
   const bool f32 = in.f32mask & 1;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -302,9 +321,13 @@ __global__ void tc_split_kernel(ComboBatch inb, int64_t N, void* p0, void* p1) {
             ((in.f32mask >> m) & 1) ? (double)((const float*)in.src[m])[idx] : in.src[m][idx];
         x = fma(in.coef[m], v, x);
       }
+      if (xout) {
+        if (out32) ((float*)xout)[idx] = (float)x;
+        else ((double*)xout)[idx] = x;
+      }
       xf = (float)x;
     }
-    split_store_f<KIND, NP>(p0, p1, off + idx, xf);
+    if (split) split_store_f<KIND, NP>(p0, p1, off + idx, xf);
   }
 }
 
@@ -318,6 +341,31 @@ __global__ void tc_prep_b_kernel(const double* L, int n, int n_pad, void* p0, vo
     const int i = (int)(e / n_pad), k = (int)(e % n_pad);
     const double x = (i < n && k < n) ? L[i + (int64_t)n * k] : 0.0;
     split_store<KIND, NP>(p0, p1, e, x);
+  }
+}
+
+// The same for up to kPrepBatch matrices, one per grid row.
+constexpr int kPrepBatch = 32;
+struct TcPrepBatch {
+  const double* L[kPrepBatch];
+  int n[kPrepBatch];
+  void* p0[kPrepBatch];
+  void* p1[kPrepBatch];
+};
+
+template <int KIND, int NP>
+__global__ void tc_prep_b_batch_kernel(const __grid_constant__ TcPrepBatch pb) {
+  pdl_wait();
+  const int y = blockIdx.y;
+  const double* L = pb.L[y];
+  const int n = pb.n[y];
+  const int n_pad = (n + 15) / 16 * 16;
+  const int64_t tot = (int64_t)n_pad * n_pad;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n_pad), k = (int)(e % n_pad);
+    const double x = (i < n && k < n) ? L[i + (int64_t)n * k] : 0.0;
+    split_store<KIND, NP>(pb.p0[y], pb.p1[y], e, x);
   }
 }
 
@@ -369,6 +417,8 @@ struct TcState {
   int64_t N = 0;
   int* status = nullptr;  // device
   uint8_t* ws = nullptr;
+  int batch = 0;     // tensors the bound workspace holds
+  int last_res = 1;  // plane set holding the last call's results
   int smem_optin = 0;
   // encoded tensor maps by (address, inner extent, rows, box rows): encoding
   // costs microseconds of host time, a lookup does not
@@ -393,11 +443,17 @@ bool cached_map(TcState* s, CUtensorMap* m, const void* base, uint64_t inner, ui
 
 }  // namespace
 
-size_t tc_workspace_bytes(int64_t N) {
-  // two plane sets of up to 2 planes x 4 bytes for kTcMaxBatch tensors, each
+size_t tc_workspace_bytes(int64_t N, int batch) {
+  // two plane sets of up to 2 planes x 4 bytes for `batch` tensors, each
   // rounded to 1 KiB
-  const size_t plane = ((size_t)kTcMaxBatch * N * 4 + 1023) / 1024 * 1024;
+  const size_t plane = ((size_t)batch * N * 4 + 1023) / 1024 * 1024;
   return 4 * plane + 1024;
+}
+
+bool tc_mixed_ok(const TcState* s) {
+  for (int mu = 0; mu < s->d; ++mu)
+    if ((s->N / s->n[mu]) % BM != 0) return false;
+  return true;
 }
 
 phiks_status tc_create(TcState** out, int dtype, int d, const int64_t* n, int64_t N) {
@@ -448,7 +504,10 @@ void tc_destroy(TcState* s) {
 
 const char* tc_last_error() { return g_tc_err.c_str(); }
 
-void tc_bind_workspace(TcState* s, void* ws) { s->ws = (uint8_t*)ws; }
+void tc_bind_workspace(TcState* s, void* ws, int batch) {
+  s->ws = (uint8_t*)ws;
+  s->batch = batch;
+}
 
 size_t tc_bplanes_bytes(int dtype, int n) {
   const size_t p = (size_t)pad16(n) * pad16(n) * elt_of(dtype);
@@ -471,10 +530,39 @@ cudaError_t tc_prepare_b(int dtype, const double* L, int n, void* dst, cudaStrea
   }
 }
 
+cudaError_t tc_prepare_b_many(int dtype, int count, const double* const* L, const int* n, void* const* dst,
+                              cudaStream_t st) {
+  for (int k0 = 0; k0 < count; k0 += kPrepBatch) {
+    TcPrepBatch pb;
+    std::memset(&pb, 0, sizeof pb);
+    const int cnt = std::min(kPrepBatch, count - k0);
+    int64_t tot = 0;
+    for (int k = 0; k < cnt; ++k) {
+      const int np = pad16(n[k0 + k]);
+      const size_t p = ((size_t)np * np * elt_of(dtype) + 1023) / 1024 * 1024;
+      pb.L[k] = L[k0 + k];
+      pb.n[k] = n[k0 + k];
+      pb.p0[k] = dst[k0 + k];
+      pb.p1[k] = (uint8_t*)dst[k0 + k] + p;
+      tot = std::max<int64_t>(tot, (int64_t)np * np);
+    }
+    const int gx = (int)std::min<int64_t>((tot + 255) / 256, 1024);
+    count_launch();
+    cudaError_t e;
+    switch (dtype) {
+      case PHIKS_BF16X3: e = launch_pdl(tc_prep_b_batch_kernel<0, 2>, dim3(gx, cnt), dim3(256), 0, st, pb); break;
+      case PHIKS_TF32X3: e = launch_pdl(tc_prep_b_batch_kernel<1, 2>, dim3(gx, cnt), dim3(256), 0, st, pb); break;
+      default: e = launch_pdl(tc_prep_b_batch_kernel<1, 1>, dim3(gx, cnt), dim3(256), 0, st, pb); break;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 namespace {
 
 template <int KIND, int NP>
-cudaError_t run_gemm(TcState* s, const CUtensorMap* mA, const CUtensorMap* mB, GemmParams& P,
+cudaError_t run_gemm(TcState* s, const CUtensorMap* mA, const TcMapsB& mB, GemmParams& P,
                      cudaStream_t st) {
   const uint32_t stage_bytes = NP * (BM * 128 + (uint32_t)P.ntile * 128);
   const size_t extra = 1024 + 64 * 8 + 64;
@@ -500,60 +588,80 @@ cudaError_t run_gemm(TcState* s, const CUtensorMap* mA, const CUtensorMap* mB, G
   // second CTA off the SM, so co-resident CTAs never oversubscribe TMEM.
   int grid = P.num_tiles < 152 ? P.num_tiles : 152;
   count_launch();
-  return launch_pdl(kern, dim3(grid), dim3(NTHREADS), smem, st, mA[0], mA[1], mB[0], mB[1], P);
+  return launch_pdl(kern, dim3(grid), dim3(NTHREADS), smem, st, mA[0], mA[1], mB, P);
 }
 
 }  // namespace
 
-cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const void* const* Bp, const Epi* epi,
-                      cudaStream_t st) {
-  if (B < 1 || B > kTcMaxBatch) return cudaErrorInvalidValue;
+cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const TcMats* mats, const Epi* epi,
+                      cudaStream_t st, const float** res, const TcPrologue* pro) {
+  if (B < 1 || B > s->batch || s->batch > kTcMaxBatch) return cudaErrorInvalidValue;
+  if (pro && (pro->nside < 0 || pro->nside > kTcMaxSide)) return cudaErrorInvalidValue;
+  bool mixed = false;
+  for (int b = 1; b < B; ++b)
+    for (int mu = 0; mu < s->d; ++mu) mixed = mixed || mats[b].B[mu] != mats[0].B[mu];
+  if (mixed && !tc_mixed_ok(s)) return cudaErrorInvalidValue;
+  const int nmat = mixed ? B : 1;
   const int dtype = s->dtype;
   const int NP = planes_of(dtype), elt = elt_of(dtype);
   const int64_t N = s->N;
-  const size_t plane = ((size_t)kTcMaxBatch * N * 4 + 1023) / 1024 * 1024;
+  const size_t plane = ((size_t)s->batch * N * 4 + 1023) / 1024 * 1024;
   uint8_t* set[2][2] = {{s->ws, s->ws + plane}, {s->ws + 2 * plane, s->ws + 3 * plane}};
   // split the (combined) inputs into planes: natural layout, mode 1
-  // contiguous, tensor b at element b N of every plane
+  // contiguous, tensor b at element b N of every plane; into the set that
+  // does not hold the last call's results, which the inputs may read
+  int cur = 1 - s->last_res;
   {
-    ComboBatch cb;
-    std::memset(&cb, 0, sizeof cb);
-    for (int b = 0; b < B; ++b) cb.c[b] = in[b];
-    const int grid = (int)std::min<int64_t>((N + 255) / 256, 152 * 8 / B);
+    TcSplitJobs jb;
+    std::memset(&jb, 0, sizeof jb);
+    for (int b = 0; b < B; ++b) {
+      jb.c[b] = in[b];
+      jb.store[b] = pro ? pro->store[b] : nullptr;
+    }
+    jb.ntensor = B;
+    int rows = B;
+    if (pro)
+      for (int k = 0; k < pro->nside; ++k, ++rows) {
+        jb.c[rows] = pro->side[k];
+        jb.store[rows] = pro->side_out[k];
+        if ((pro->side_f32 >> k) & 1) jb.store_f32 |= 1u << rows;
+      }
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 152 * 8 / rows));
     count_launch();
-    void *q0 = set[0][0], *q1 = set[0][1], *none = nullptr;
-    const dim3 g(grid, B);
+    void *q0 = set[cur][0], *q1 = set[cur][1], *none = nullptr;
+    const dim3 g(grid, rows);
     cudaError_t e;
-    if (dtype == PHIKS_BF16X3) e = launch_pdl(tc_split_kernel<0, 2>, g, dim3(256), 0, st, cb, N, q0, q1);
-    else if (dtype == PHIKS_TF32X3) e = launch_pdl(tc_split_kernel<1, 2>, g, dim3(256), 0, st, cb, N, q0, q1);
-    else e = launch_pdl(tc_split_kernel<1, 1>, g, dim3(256), 0, st, cb, N, q0, none);
+    if (dtype == PHIKS_BF16X3) e = launch_pdl(tc_split_kernel<0, 2>, g, dim3(256), 0, st, jb, N, q0, q1);
+    else if (dtype == PHIKS_TF32X3) e = launch_pdl(tc_split_kernel<1, 2>, g, dim3(256), 0, st, jb, N, q0, q1);
+    else e = launch_pdl(tc_split_kernel<1, 1>, g, dim3(256), 0, st, jb, N, q0, none);
     if (e != cudaSuccess) return e;
   }
-  int cur = 0;
   for (int mu = 0; mu < s->d; ++mu) {
     const int n = (int)s->n[mu], np = pad16(n);
     const int64_t M2 = N / n;
     const int64_t rows = (int64_t)B * M2;
     const int nnt = (np + 255) / 256;          // N tiles of at most 256 rows
     const int ntile = pad16((np + nnt - 1) / nnt);
-    CUtensorMap mA[2], mB[2];
+    CUtensorMap mA[2];
+    TcMapsB mB;
     std::memset(mA, 0, sizeof mA);
-    std::memset(mB, 0, sizeof mB);
+    std::memset(&mB, 0, sizeof mB);
     const size_t bplane = ((size_t)np * np * elt + 1023) / 1024 * 1024;
     for (int p = 0; p < NP; ++p) {
       if (!cached_map(s, &mA[p], set[cur][p], (uint64_t)n, (uint64_t)rows, BM)) {
         g_tc_err = "tensor map for the A operand failed";
         return cudaErrorInvalidValue;
       }
-      if (!cached_map(s, &mB[p], (const uint8_t*)Bp[mu] + p * bplane, (uint64_t)np, (uint64_t)np,
-                      (uint32_t)ntile)) {
-        g_tc_err = "tensor map for the B operand failed";
-        return cudaErrorInvalidValue;
-      }
+      for (int b = 0; b < nmat; ++b)
+        if (!cached_map(s, &mB.b[b][p], (const uint8_t*)mats[b].B[mu] + p * bplane, (uint64_t)np,
+                        (uint64_t)np, (uint32_t)ntile)) {
+          g_tc_err = "tensor map for the B operand failed";
+          return cudaErrorInvalidValue;
+        }
     }
     if (NP == 1) {
       mA[1] = mA[0];
-      mB[1] = mB[0];
+      for (int b = 0; b < nmat; ++b) mB.b[b][1] = mB.b[b][0];
     }
     GemmParams P;
     std::memset(&P, 0, sizeof P);
@@ -570,6 +678,7 @@ cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const void* const* Bp,
     while (cols < 2 * ntile) cols <<= 1;
     P.tmem_cols = cols;
     P.last = (mu == s->d - 1);
+    P.mixed = mixed ? 1 : 0;
     P.out0 = set[1 - cur][0];
     P.out1 = set[1 - cur][1];
     P.status = s->status;
@@ -580,6 +689,9 @@ cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const void* const* Bp,
     if (e != cudaSuccess) return e;
     cur = 1 - cur;
   }
+  s->last_res = cur;
+  if (res) *res = (const float*)set[cur][0];
+  if (!epi) return cudaSuccess;
   // FP64 epilogues over all N elements of each tensor with the whole GPU: the
   // result plane is one more (float) source whose coefficient in output t is
   // epi.b[t]
@@ -593,7 +705,11 @@ cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const void* const* Bp,
     for (int t = 0; t < f[b].nout; ++t) f[b].a[t][m] = epi[b].b[t];
     f[b].nsrc = m + 1;
   }
-  return launch_combine_batch(f, B, N, st);
+  for (int b0 = 0; b0 < B; b0 += kMaxEpiBatch) {
+    cudaError_t e = launch_combine_batch(f + b0, std::min(kMaxEpiBatch, B - b0), N, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 int tc_read_status(TcState* s, cudaStream_t st) {

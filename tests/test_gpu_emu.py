@@ -11,6 +11,7 @@ pytestmark = pytest.mark.gpu
 import paper_2210_07667_gb300 as pk  # noqa: E402
 import workloads as wk  # noqa: E402
 from oracle import dense, kron  # noqa: E402
+from oracle import phiks_ref  # noqa: E402
 from oracle import taylor_action as ta  # noqa: E402
 
 from gpu_util import dev, rel_inf, run_workload  # noqa: E402
@@ -135,3 +136,27 @@ def test_same_vector_emulated_scales(skip_phi0, nscales, p):
         for k in range(len(ells)):
             e = rel_inf(out[L * len(ells) + k], ex[k])
             assert e < 1e-12, (L, ells[k], e)
+
+
+@pytest.mark.parametrize("mode", ["same", "lincomb"])
+def test_emulated_no_squaring(mode):
+    """(s, q) = (0, 12): the quadrature batch, then the phi_0 / exp(K) v_0
+    operator in a batch of its own; against the oracle's restatement of the
+    method with the same (s, q)."""
+    dims = (64, 32, 64)
+    A = [wk.fd_adr_dirichlet(m, 1.0, a, 0.5) for m, a in zip(dims, (4.0, -2.0, 1.0))]
+    N = int(np.prod(dims))
+    tau = 1e-4
+    if mode == "same":
+        wl = wk.Workload("t", A, tau, 3, "same", 1, [wk.uniform(31, N)])
+    else:
+        wl = wk.Workload("t", A, tau, 4, "lincomb", 1, [wk.normal(50 + l, N) for l in range(5)])
+    out, plan = run_workload(wl, dtype=EMU, force_s=0, force_q=12)
+    pk.phiks_device_status(plan.handle)
+    assert plan.last_params()[:2] == (0, 12)
+    if mode == "same":
+        ref = phiks_ref.same(A, tau, wl.vs[0], 3, 0, 12, nscales=1)
+    else:
+        ref = phiks_ref.lincomb(A, tau, wl.vs, 0, 12, nscales=1)
+    for k in range(out.shape[0]):
+        assert rel_inf(out[k], ref[k]) < 1e-12, k

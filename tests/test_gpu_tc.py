@@ -97,6 +97,44 @@ def test_lincomb_split(dtype):
     assert max(errs) < 4 * TOL[dtype]
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dims", [(64, 32, 64), (128, 256)])
+def test_lincomb_split_node_batches(dtype, dims):
+    """Linear combination whose quadrature nodes run as one batch with their
+    own matrices, each batch's combinations in the next batch's split pass
+    (d = 3 and d = 2: an even number of passes per operator)."""
+    wl = wk.adr3d_lincomb(p=4, dims=dims, nscales=3) if len(dims) == 3 else None
+    if wl is None:
+        A = [wk.fd_adr_dirichlet(m, 1.0, a, 0.5) for m, a in zip(dims, (6.0, -4.0))]
+        N = int(np.prod(dims))
+        wl = wk.Workload("t", A, 2e-4, 4, "lincomb", 3, [wk.normal(40 + l, N) for l in range(5)])
+    vs = [v.astype(np.float32).astype(np.float64) for v in wl.vs]
+    w2 = wk.Workload("t", wl.A, wl.tau, wl.p, "lincomb", wl.nscales, vs)
+    out, plan = run_workload(w2, dtype=dtype)
+    pk.phiks_device_status(plan.handle)
+    s, q, _, _ = plan.last_params()
+    ex = [ta.lincomb(wl.A, wl.tau, vs, 2.0 ** -L) for L in range(wl.nscales)]
+    errs = [rel_inf(out[L], ex[L]) for L in range(wl.nscales)]
+    print("lincomb batched %s dtype %d (s,q)=(%d,%d) errs %s" % (dims, dtype, s, q, ["%.2e" % e for e in errs]))
+    assert s >= 1
+    assert max(errs) < 4 * TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_same_vector_split_d2_batches(dtype):
+    A = [wk.fd_adr_dirichlet(m, 1.0, a, 0.3) for m, a in zip((256, 128), (2.0, -3.0))]
+    N = 256 * 128
+    v = wk.normal(5, N).astype(np.float32).astype(np.float64)
+    wl = wk.Workload("t", A, 3e-4, 3, "same", 2, [v])
+    out, plan = run_workload(wl, dtype=dtype)
+    pk.phiks_device_status(plan.handle)
+    s, q, T, _ = plan.last_params()
+    ref = phiks_ref.same(A, 3e-4, v, 3, s, q, nscales=2)
+    errs = [rel_inf(out[k], ref[k]) for k in range(out.shape[0])]
+    print("same d2 dtype %d (s,q)=(%d,%d) errs %s" % (dtype, s, q, ["%.2e" % e for e in errs]))
+    assert max(errs) < 4 * TOL[dtype]
+
+
 @pytest.mark.parametrize("dtype", [pk.PHIKS_BF16X3])
 def test_batch_graph_split(dtype):
     """Split dtype, instances with n_mu above 256 (two N tiles), batched over
@@ -134,3 +172,18 @@ def test_batch_graph_split(dtype):
             assert rel_inf(got[l], ref[l]) < 4 * TOL[dtype]
     batch.destroy_graph(g)
     batch.close()
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_same_vector_split_no_squaring(dtype):
+    """(s, q) = (0, 10), phi_0 skipped: the node batch alone, its sums into
+    the outputs by the last combination pass."""
+    A = [wk.fd_adr_dirichlet(m, 1.0, a, 0.3) for m, a in zip((48, 40, 32), (2.0, -3.0, 1.0))]
+    N = 48 * 40 * 32
+    v = wk.normal(8, N).astype(np.float32).astype(np.float64)
+    wl = wk.Workload("t", A, 1e-4, 3, "same", 1, [v], skip_phi0=True)
+    out, plan = run_workload(wl, dtype=dtype, force_s=0, force_q=10)
+    pk.phiks_device_status(plan.handle)
+    ref = phiks_ref.same(A, 1e-4, v, 3, 0, 10, nscales=1)[1:]
+    errs = [rel_inf(out[k], ref[k]) for k in range(out.shape[0])]
+    assert max(errs) < 4 * TOL[dtype], errs
