@@ -101,6 +101,15 @@ struct ModeGeom {
 // n x n.  With epi == nullptr or epi->nout == 0 the result goes to W.
 cudaError_t launch_mode_product_f64(const Combo& pro, const double* L, ModeGeom g, double* W,
                                     const Epi* epi, cudaStream_t st);
+// B <= kMaxModeBatch independent mode products of the same geometry in one
+// launch: W[b] = (combination pro[b]) x_mu L[b], stored plainly.
+constexpr int kMaxModeBatch = 16;
+struct ModeBatch {
+  Combo pro[kMaxModeBatch];
+  const double* L[kMaxModeBatch];
+  double* W[kMaxModeBatch];
+};
+cudaError_t launch_mode_product_f64_batch(const ModeBatch& mb, int B, ModeGeom g, cudaStream_t st);
 // The same for complex V, W (interleaved) and L given as its 2n x 2n real
 // representation (PHIKS_C128 plans).
 cudaError_t launch_mode_product_c128(const Combo& pro, const double* L, ModeGeom g, double* W,

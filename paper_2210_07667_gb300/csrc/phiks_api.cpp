@@ -203,6 +203,11 @@ bool emu_dtype(const phiks_plan_s* P) { return P->dtype == PHIKS_FP64_EMU; }
 bool double_vectors(const phiks_plan_s* P) { return !split_dtype(P); }
 // the products run on the tensor cores (split dtypes and FP64_EMU)
 bool tc_path(const phiks_plan_s* P) { return split_dtype(P) || emu_dtype(P); }
+// the paths whose Tucker operators run in batches (the tensor-core paths, and
+// the real FP64 path through its batched mode products)
+bool batched_path(const phiks_plan_s* P) {
+  return tc_path(P) || (P->dtype == PHIKS_FP64 && !P->cplx);
+}
 
 // bytes per vector element (a complex element is two doubles)
 size_t elt_size(const phiks_plan_s* P) { return P->cplx ? 16 : (double_vectors(P) ? 8 : 4); }
@@ -234,6 +239,11 @@ int tucker_batch_max(const phiks_plan_s* P, int p) {
     const int64_t floor_p = std::min(kTcMaxBatch, std::max(p, 1) + 1);
     return (int)std::max<int64_t>(floor_p, std::min<int64_t>(kTcMaxBatch, by_mem));
   }
+  if (batched_path(P)) {  // real FP64: the two temporaries, 16 bytes per element and operator
+    const int64_t by_mem = ((int64_t)2 << 30) / (16 * std::max<int64_t>(P->N, 1));
+    const int64_t floor_p = std::min(kMaxModeBatch, std::max(p, 1) + 1);
+    return (int)std::max<int64_t>(floor_p, std::min<int64_t>(kMaxModeBatch, by_mem));
+  }
   return 1;
 }
 
@@ -246,7 +256,7 @@ WsLayout ws_layout(const phiks_plan_s* P, int p) {
   w.acc = o;
   o += up1k((size_t)std::max(p, 1) * N * 8);
   w.acc2 = o;  // new accumulators of a batched squaring step
-  if (tc_path(P)) o += up1k((size_t)std::max(p, 1) * N * 8);
+  if (batched_path(P)) o += up1k((size_t)std::max(p, 1) * N * 8);
   w.tmp = o;
   o += up1k(2 * (size_t)tucker_batch_max(P, p) * N * 8);
   w.msq0 = o;
@@ -646,7 +656,7 @@ void carve(Ctx& c, int p, char* ws, double** acc) {
   uintptr_t base = ((uintptr_t)ws + 1023) & ~(uintptr_t)1023;
   WsLayout w = ws_layout(P, p);
   for (int l = 0; l < std::max(p, 1); ++l) acc[l] = (double*)(base + w.acc) + (size_t)l * P->NR;
-  if (tc_path(P))
+  if (batched_path(P))
     for (int l = 0; l < std::max(p, 1); ++l) c.acc2[l] = (double*)(base + w.acc2) + (size_t)l * P->NR;
   c.tmp[0] = (double*)(base + w.tmp);
   c.bmax = tucker_batch_max(P, p);
@@ -806,17 +816,22 @@ struct BatchPro {
   void* side_out[kOzMaxSide > kTcMaxSide ? kOzMaxSide : kTcMaxSide];
 };
 
-// Whether a tensor-core batch may mix matrices (every mode's fibre count a
-// multiple of 128).
+Combo plain(const void* x, bool f32);
+phiks_status combine_many(Ctx& c, const Epi* e, int count);
+
+// Whether a batch may mix matrices: the tensor-core paths when every mode's
+// fibre count is a multiple of 128 (no tile spans two tensors); the real FP64
+// path always (one grid layer per tensor).
 bool mixed_ok(const phiks_plan_s* P) {
   if (emu_dtype(P)) return oz_mixed_ok(P->oz);
-  return split_dtype(P) && tc_mixed_ok(P->tc);
+  if (split_dtype(P)) return tc_mixed_ok(P->tc);
+  return batched_path(P);  // real FP64: one grid layer per tensor
 }
 
-// Tensor-core paths with mixed_ok: B <= c.bmax Tucker operators with their
-// own matrices M[b] in one batch, no epilogue; *res receives the results
-// (tensor b at element b NR; float when *r32, the split dtypes, else double)
-// for the caller's combinations.
+// Batched paths with mixed_ok: B <= c.bmax Tucker operators with their own
+// matrices M[b] in one batch, no epilogue; *res receives the results (tensor
+// b at element b NR; float when *r32, the split dtypes, else double) for the
+// caller's combinations.
 phiks_status tucker_mixed(Ctx& c, int B, const Combo* in, const Mats* M, const void** res, bool* r32,
                           const BatchPro* pro = nullptr) {
   phiks_plan_s* P = c.P;
@@ -849,6 +864,58 @@ phiks_status tucker_mixed(Ctx& c, int B, const Combo* in, const Mats* M, const v
       return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), oz_last_error());
     if (prof)
       for (int mu = 0; mu < P->d; ++mu) P->prof_flops += 2.0 * B * (double)P->N * (double)P->n[mu];
+  } else if (!tc_path(P)) {
+    // real FP64: the prologue's stores and extra combinations first (one
+    // combination pass), then d batched mode products through the two
+    // temporaries
+    Combo ins[kMaxModeBatch];
+    for (int b = 0; b < B; ++b) ins[b] = in[b];
+    if (pro) {
+      if (pro->side_f32) return fail(PHIKS_ERR_INVALID, "prologue");
+      std::vector<Epi> es;
+      auto as_epi = [&](const Combo& x, void* dst) {
+        Epi e = make_epi();
+        e.nout = 1;
+        e.out[0] = (double*)dst;
+        e.nsrc = x.nsrc;
+        for (int m = 0; m < x.nsrc; ++m) {
+          e.src[m] = x.src[m];
+          e.a[0][m] = x.coef[m];
+        }
+        return e;
+      };
+      for (int b = 0; b < B; ++b)
+        if (pro->store[b]) {
+          es.push_back(as_epi(in[b], pro->store[b]));
+          ins[b] = plain(pro->store[b], false);
+        }
+      for (int k = 0; k < pro->nside; ++k) es.push_back(as_epi(pro->side[k], pro->side_out[k]));
+      TRY(combine_many(c, es.data(), (int)es.size()));
+    }
+    cudaEvent_t e1;
+    double fl = 0;
+    for (int mu = 0; mu < P->d; ++mu) fl += 2.0 * B * (double)P->N * (double)P->n[mu];
+    TRY(prof_begin(c, &e1));
+    int64_t a = 1;
+    for (int mu = 0; mu < P->d; ++mu) {
+      ModeBatch mb;
+      std::memset(&mb, 0, sizeof mb);
+      double* outp = c.tmp[mu & 1];
+      for (int b = 0; b < B; ++b) {
+        mb.pro[b] = mu == 0 ? ins[b] : plain(c.tmp[(mu - 1) & 1] + (size_t)b * P->NR, false);
+        mb.L[b] = M[b].L[mu];
+        mb.W[b] = outp + (size_t)b * P->NR;
+      }
+      ModeGeom g;
+      g.a = a;
+      g.n = (int)P->n[mu];
+      g.b = P->N / (a * P->n[mu]);
+      CK(launch_mode_product_f64_batch(mb, B, g, c.st));
+      a *= P->n[mu];
+    }
+    TRY(prof_end(c, e1, fl));
+    *res = c.tmp[(P->d - 1) & 1];
+    *r32 = false;
   } else {
     TcMats tm[kTcMaxBatch];
     for (int b = 0; b < B; ++b)
@@ -1484,7 +1551,7 @@ phiks_status pending_to_side(const Ctx& c, std::vector<Pending>& pout, BatchPro&
   return PHIKS_OK;
 }
 
-// SAME form on the tensor-core paths when batches may mix matrices
+// SAME form on the batched paths when batches may mix matrices
 // (mixed_ok) and hold p + 2 operators, p <= 7: the operators and
 // combinations of run_same, every batch's FP64 combinations (quadrature sums,
 // eq. (simul), copies of the outputs) evaluated by the next batch's first
@@ -1617,7 +1684,7 @@ phiks_status run_same_batched(Ctx& c, const Bank* B, int s, int p, const void* v
   return flush_pending(c, pout);
 }
 
-// Linear-combination form on the tensor-core paths when batches may mix
+// Linear-combination form on the batched paths when batches may mix
 // matrices (mixed_ok) and hold p + 2 operators: the operators and
 // combinations of run_lincomb, but every batch's FP64 combinations
 // (quadrature sums, eq. (comb), the outputs) are evaluated by the next
@@ -1760,9 +1827,14 @@ phiks_status run_lincomb_batched(Ctx& c, const Bank* B, int s, int p, const void
     BatchPro pro;
     std::memset(&pro, 0, sizeof pro);
     TRY(pending_to_side(c, pout, pro));
+    // Phi_0 v_{1..p} evaluated (into A) by this batch's split pass, before
+    // its products overwrite the quadrature's results it reads
+    pro.side[pro.nside] = pend[p - 1];
+    pro.side_out[pro.nside++] = A[p - 1];
     Combo in = plain(v0, f32);
     TRY(tucker_mixed(c, 1, &in, &M, &R, &r32, &pro));
-    Combo x = pend[p - 1];
+    Combo x = make_combo();
+    TRY(add_term(x, A[p - 1], 1.0, false));
     TRY(add_term(x, res(0), 1.0, r32));
     pout.push_back({x, blk(0)});
   }
@@ -2322,12 +2394,12 @@ phiks_status phiks_apply_ex(phiks_plan_t P, double tau, int p, const void* const
       Bank* B = nullptr;
       TRY(get_bank(P, tau, s, q, o.rule, o.no_cache != 0, st, &B));
       if (kind == 0) {
-        if (tc_path(P) && mixed_ok(P) && p >= 1 && p <= 7 && c.bmax >= p + 2)
+        if (batched_path(P) && mixed_ok(P) && p >= 1 && p <= 7 && c.bmax >= p + 2)
           TRY(run_same_batched(c, B, s, p, v[0], o, acc, out));
         else
           TRY(run_same(c, B, s, p, v[0], o, acc, out));
       } else {
-        if (tc_path(P) && mixed_ok(P) && p >= 1 && c.bmax >= p + 2)
+        if (batched_path(P) && mixed_ok(P) && p >= 1 && c.bmax >= p + 2)
           TRY(run_lincomb_batched(c, B, s, p, v, o, acc, out));
         else
           TRY(run_lincomb(c, B, s, p, v, o, acc, out));

@@ -52,10 +52,9 @@ __device__ __forceinline__ void store_epi(const Epi& epi, double* W, int64_t idx
 // (rows ti + r * TI/RI, columns tc + c * TC/RC, so a warp reads consecutive
 // shared-memory words); KC-deep slices of L and of the fibres, the next slice
 // fetched into registers while the current one is consumed.
-template <int TI, int TC, int RI, int RC, int KC, bool XFAST>
-__global__ void __launch_bounds__((TI / RI) * (TC / RC))
-    mode_product_f64_kernel(Combo pro, const double* __restrict__ L, ModeGeom g, double* W, Epi epi) {
-  pdl_wait();
+template <int TI, int TC, int RI, int RC, int KC, bool XFAST, bool EPI>
+__device__ __forceinline__ void mode_product_tile(const Combo& pro, const double* __restrict__ L, ModeGeom g,
+                                                  double* W, const Epi* epi) {
   constexpr int TROWS = TI / RI, TCOLS = TC / RC, NT = TROWS * TCOLS;
   constexpr int LPT = (TI * KC + NT - 1) / NT;
   constexpr int VPT = (TC * KC + NT - 1) / NT;
@@ -151,9 +150,27 @@ __global__ void __launch_bounds__((TI / RI) * (TC / RC))
       const int64_t col = c0 + tc + c * TCOLS;
       if (col >= ncols) continue;
       const int64_t x = col % g.a, y = col / g.a;
-      store_epi(epi, W, x + g.a * i + an * y, acc[r][c]);
+      if (EPI) store_epi(*epi, W, x + g.a * i + an * y, acc[r][c]);
+      else W[x + g.a * i + an * y] = acc[r][c];
     }
   }
+}
+
+template <int TI, int TC, int RI, int RC, int KC, bool XFAST>
+__global__ void __launch_bounds__((TI / RI) * (TC / RC))
+    mode_product_f64_kernel(Combo pro, const double* __restrict__ L, ModeGeom g, double* W, Epi epi) {
+  pdl_wait();
+  mode_product_tile<TI, TC, RI, RC, KC, XFAST, true>(pro, L, g, W, &epi);
+}
+
+// Independent mode products of the same geometry, one per grid layer
+// (blockIdx.z), results stored plainly.
+template <int TI, int TC, int RI, int RC, int KC, bool XFAST>
+__global__ void __launch_bounds__((TI / RI) * (TC / RC))
+    mode_product_f64_batch_kernel(const __grid_constant__ ModeBatch mb, ModeGeom g) {
+  pdl_wait();
+  const int z = blockIdx.z;
+  mode_product_tile<TI, TC, RI, RC, KC, XFAST, false>(mb.pro[z], mb.L[z], g, mb.W[z], nullptr);
 }
 
 // Complex variant (PHIKS_C128): elements of V and W are interleaved complex
@@ -292,6 +309,16 @@ cudaError_t launch_tiled_c128(const Combo& pro, const double* L, ModeGeom g, dou
 }
 
 template <int TI, int TC, int RI, int RC, int KC>
+cudaError_t launch_tiled_batch(const ModeBatch& mb, int B, ModeGeom g, cudaStream_t st) {
+  constexpr int NT = (TI / RI) * (TC / RC);
+  const int64_t ncols = g.a * g.b;
+  dim3 grid((unsigned)((ncols + TC - 1) / TC), (unsigned)((g.n + TI - 1) / TI), (unsigned)B);
+  if (g.a >= TC)
+    return launch_pdl(mode_product_f64_batch_kernel<TI, TC, RI, RC, KC, true>, grid, dim3(NT), 0, st, mb, g);
+  return launch_pdl(mode_product_f64_batch_kernel<TI, TC, RI, RC, KC, false>, grid, dim3(NT), 0, st, mb, g);
+}
+
+template <int TI, int TC, int RI, int RC, int KC>
 cudaError_t launch_tiled(const Combo& pro, const double* L, ModeGeom g, double* W, const Epi& e,
                          cudaStream_t st) {
   constexpr int NT = (TI / RI) * (TC / RC);
@@ -416,6 +443,14 @@ cudaError_t launch_mode_product_f64(const Combo& pro, const double* L, ModeGeom 
   const int64_t big_tiles = ((g.a * g.b + 63) / 64) * ((g.n + 31) / 32);
   if (big_tiles >= 8 * 152) return launch_tiled<32, 64, 2, 4, 16>(pro, L, g, W, e, st);
   return launch_tiled<16, 16, 2, 2, 32>(pro, L, g, W, e, st);
+}
+
+cudaError_t launch_mode_product_f64_batch(const ModeBatch& mb, int B, ModeGeom g, cudaStream_t st) {
+  if (B < 1 || B > kMaxModeBatch) return cudaErrorInvalidValue;
+  count_launch();
+  const int64_t big_tiles = B * ((g.a * g.b + 63) / 64) * ((g.n + 31) / 32);
+  if (big_tiles >= 8 * 152) return launch_tiled_batch<32, 64, 2, 4, 16>(mb, B, g, st);
+  return launch_tiled_batch<16, 16, 2, 2, 32>(mb, B, g, st);
 }
 
 cudaError_t launch_mode_product_c128(const Combo& pro, const double* L, ModeGeom g, double* W,

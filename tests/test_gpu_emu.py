@@ -138,8 +138,8 @@ def test_same_vector_emulated_scales(skip_phi0, nscales, p):
             assert e < 1e-12, (L, ells[k], e)
 
 
-@pytest.mark.parametrize("mode", ["same", "lincomb"])
-def test_emulated_no_squaring(mode):
+@pytest.mark.parametrize("mode,p", [("same", 3), ("lincomb", 4), ("lincomb", 1)])
+def test_emulated_no_squaring(mode, p):
     """(s, q) = (0, 12): the quadrature batch, then the phi_0 / exp(K) v_0
     operator in a batch of its own; against the oracle's restatement of the
     method with the same (s, q)."""
@@ -148,14 +148,14 @@ def test_emulated_no_squaring(mode):
     N = int(np.prod(dims))
     tau = 1e-4
     if mode == "same":
-        wl = wk.Workload("t", A, tau, 3, "same", 1, [wk.uniform(31, N)])
+        wl = wk.Workload("t", A, tau, p, "same", 1, [wk.uniform(31, N)])
     else:
-        wl = wk.Workload("t", A, tau, 4, "lincomb", 1, [wk.normal(50 + l, N) for l in range(5)])
+        wl = wk.Workload("t", A, tau, p, "lincomb", 1, [wk.normal(50 + l, N) for l in range(p + 1)])
     out, plan = run_workload(wl, dtype=EMU, force_s=0, force_q=12)
     pk.phiks_device_status(plan.handle)
     assert plan.last_params()[:2] == (0, 12)
     if mode == "same":
-        ref = phiks_ref.same(A, tau, wl.vs[0], 3, 0, 12, nscales=1)
+        ref = phiks_ref.same(A, tau, wl.vs[0], p, 0, 12, nscales=1)
     else:
         ref = phiks_ref.lincomb(A, tau, wl.vs, 0, 12, nscales=1)
     for k in range(out.shape[0]):

@@ -163,6 +163,22 @@ def test_caller_norms_skip_the_sync_and_agree():
     assert torch.equal(o1, o2)
 
 
+@pytest.mark.parametrize("p,s", [(1, 0), (1, 2), (3, 0)])
+def test_fp64_batched_lincomb_forced(p, s):
+    """The FP64 path's batched form (all node operators in one batch, the
+    combinations deferred), with and without squaring, against the oracle's
+    restatement of the method with the same (s, q)."""
+    dims = (12, 10, 8)
+    A = [wk.fd_adr_dirichlet(m, 1.0, a, 0.5) for m, a in zip(dims, (4.0, -2.0, 1.0))]
+    N = int(np.prod(dims))
+    vs = [wk.normal(60 + l, N) for l in range(p + 1)]
+    wl = wk.Workload("t", A, 2e-3, p, "lincomb", 1, vs)
+    out, plan = run_workload(wl, force_s=s, force_q=9)
+    ref = phiks_ref.lincomb(A, 2e-3, vs, s, 9, nscales=1)
+    assert rel_inf(out[0], ref[0]) < 1e-12
+    plan.close()
+
+
 @pytest.mark.parametrize("dtype", [pk.PHIKS_FP64, pk.PHIKS_FP64_EMU])
 def test_norms_that_change_the_selection(dtype):
     """Repeated calls with the same tau and p run first with the previous
