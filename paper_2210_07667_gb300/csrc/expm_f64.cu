@@ -78,6 +78,25 @@ __global__ void __launch_bounds__((GT / GR) * (GT / GR)) gemm_batch_f64_kernel(G
     }
 }
 
+__global__ void poly_batch_f64_kernel(const __grid_constant__ PolyBatch pb) {
+  pdl_wait();
+  const int k = blockIdx.y;
+  const int n = pb.n[k], m = pb.m[k];
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double x[kPolyMax];  // all loads issued before the sum
+#pragma unroll
+    for (int i = 0; i < kPolyMax; ++i) x[i] = i < m ? __ldg(pb.P[k][i] + e) : 0.0;
+    double v = 0.0;
+#pragma unroll
+    for (int i = kPolyMax; i >= 1; --i)
+      if (i <= m) v = fma(pb.c[k][i], x[i - 1], v);
+    if (e % n == e / n) v += pb.c[k][0];
+    pb.Y[k][e] = v;
+  }
+}
+
 __global__ void scale_batch_f64_kernel(ScaleBatch sb) {
   pdl_wait();
   const int k = blockIdx.y;
@@ -92,6 +111,15 @@ __global__ void scale_batch_f64_kernel(ScaleBatch sb) {
 }
 
 }  // namespace
+
+cudaError_t launch_poly_batch_f64(const PolyBatch& pb, int nmax, cudaStream_t st) {
+  if (pb.count <= 0) return cudaSuccess;
+  if (pb.count > kPolyBatch) return cudaErrorInvalidValue;
+  const int64_t nn = (int64_t)nmax * nmax;
+  const int gx = (int)std::min<int64_t>((nn + 255) / 256, 64);
+  count_launch();
+  return launch_pdl(poly_batch_f64_kernel, dim3(gx, pb.count), dim3(256), 0, st, pb);
+}
 
 cudaError_t launch_gemm_batch_f64(const GemmBatch& gb, int nmax, cudaStream_t st) {
   if (gb.count <= 0) return cudaSuccess;

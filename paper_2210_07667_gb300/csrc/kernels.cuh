@@ -145,6 +145,21 @@ struct GemmBatch {
 // (column-major n_k x n_k; alpha_k = 0 skips the product).
 cudaError_t launch_gemm_batch_f64(const GemmBatch& gb, int nmax, cudaStream_t st);
 
+// Batched matrix polynomials from stored powers:
+//   Y_k = c_k0 I + sum_{i=1}^{m_k} c_ki P_ki   (column-major n_k x n_k),
+// summed from the highest power down.
+constexpr int kPolyBatch = 32;
+constexpr int kPolyMax = 15;
+struct PolyBatch {
+  int count;
+  int n[kPolyBatch];
+  int m[kPolyBatch];
+  double* Y[kPolyBatch];
+  const double* P[kPolyBatch][kPolyMax];  // P[k][i - 1] = the i-th power
+  double c[kPolyBatch][kPolyMax + 1];
+};
+cudaError_t launch_poly_batch_f64(const PolyBatch& pb, int nmax, cudaStream_t st);
+
 struct ScaleBatch {
   int count;
   int n[kMaxBatch];

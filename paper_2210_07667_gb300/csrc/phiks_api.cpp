@@ -114,7 +114,8 @@ struct phiks_plan_s {
   size_t offA[PHIKS_MAX_D] = {0};
   // device: (g_mu (A_mu - sigma_mu I))^i for i = 2, 3, 4 (i - 2 blocks of
   // sum_n2 doubles, each laid out as dAs), g_mu a power of two
-  double* dApow = nullptr;
+  double* dApow = nullptr;              // powers 2..apow_n of g (A - sigma I), blocks of sum_n2
+  int apow_n = 4;
   double apow_g[PHIKS_MAX_D] = {0};
   size_t sum_n2 = 0;
   int nmax = 0;
@@ -336,7 +337,9 @@ phiks_status select_cached(phiks_plan_s* P, double tau, int p, int kind, const d
 // near 1 / ||A - sigma I||_1, come from the plan (computed once) or are
 // formed first; X^i = (c 2^-t / g)^i (g (A - sigma I))^i enters through the
 // coefficients, and e^{c sigma} (its 2^-t-th power when t > 0) through the
-// last polynomial step, which writes E directly when t = 0.
+// last polynomial step, which writes E directly when t = 0.  When the plan holds
+// the powers up to 15 (small matrices), T is instead one elementwise sum of the
+// stored powers, c_0 I + sum_i c_i h^i (g (A - sigma I))^i.
 constexpr int kTaylorBlocks = 4;
 constexpr int kTaylorDeg = 4 * kTaylorBlocks - 1;
 constexpr int kScratchPerJob = 6;  // (gA)^2, (gA)^3, (gA)^4, T0, T1, spare
@@ -348,8 +351,9 @@ struct ExpmJob {
   double norm1;          // ||A - sigma I||_1
   double esig;           // e^{c sigma}
   double* out;           // device n x n
-  const double* pw[3] = {nullptr, nullptr, nullptr};  // (g Ashift)^2..4, or null
-  double g = 1.0;                                      // that power of two
+  const double* pw[kPolyMax - 1] = {};  // (g Ashift)^2..npow, or null
+  int npow = 4;
+  double g = 1.0;  // that power of two
 };
 
 GemmBatch gemm_batch0() {
@@ -398,6 +402,36 @@ phiks_status matrix_powers(int count, const int* n, const double* const* A, cons
       gb.alpha[2 * i + 1] = 1.0;
     }
     CK(launch_gemm_batch_f64(gb, nmax, st));
+  }
+  return PHIKS_OK;
+}
+
+// (g A_k)^5 .. (g A_k)^15 from the powers 2..4 (pw[k][i] = (g A_k)^(i + 2)):
+// two batched launches, (gA)^(4 + i) = (gA)^4 (gA)^i for i = 1..4 and
+// (gA)^(8 + i) = (gA)^8 (gA)^i for i = 1..7.
+phiks_status matrix_powers_high(int count, const int* n, const double* const* A, const double* g,
+                                double* const (*pw)[kPolyMax - 1], cudaStream_t st) {
+  const int per[2] = {4, 7};
+  const int base[2] = {4, 8};
+  for (int r = 0; r < 2; ++r) {
+    const int step = kMaxBatch / per[r];
+    for (int k0 = 0; k0 < count; k0 += step) {
+      const int cnt = std::min(step, count - k0);
+      int nmax = 1;
+      GemmBatch gb = gemm_batch0();
+      for (int kk = k0; kk < k0 + cnt; ++kk) {
+        nmax = std::max(nmax, n[kk]);
+        for (int i = 1; i <= per[r]; ++i) {
+          const int j = gb.count++;
+          gb.n[j] = n[kk];
+          gb.A[j] = pw[kk][base[r] - 2];
+          gb.B[j] = i == 1 ? A[kk] : pw[kk][i - 2];
+          gb.alpha[j] = i == 1 ? g[kk] : 1.0;
+          gb.C[j] = pw[kk][base[r] + i - 2];
+        }
+      }
+      CK(launch_gemm_batch_f64(gb, nmax, st));
+    }
   }
   return PHIKS_OK;
 }
@@ -467,12 +501,43 @@ phiks_status run_expm_jobs(phiks_plan_s* P, std::vector<ExpmJob>& jobs, double* 
   // (j = J - 1) sets T = B_j, later ones T <- T X^4 + B_j; step 0 carries the
   // final factor and writes E when the job has no squarings
   std::vector<int> cur(nj, 3);  // T0 = slot 3, T1 = slot 4
+  std::vector<char> direct(nj);
+  for (int k = 0; k < nj; ++k) direct[k] = jobs[k].npow >= 4 * J[k] - 1;
   for (int k0 = 0; k0 < nj; k0 += kMaxBatch) {
     const int k1 = std::min(nj, k0 + kMaxBatch);
+    {  // jobs whose powers are all stored: one elementwise sum each
+      PolyBatch pb;
+      pb.count = 0;
+      int pmax = 1;
+      for (int k = k0; k <= k1; ++k) {
+        if (pb.count == kPolyBatch || (k == k1 && pb.count)) {
+          CK(launch_poly_batch_f64(pb, pmax, st));
+          pb.count = 0;
+          pmax = 1;
+        }
+        if (k == k1 || !direct[k]) continue;
+        const int i = pb.count++;
+        const int m = 4 * J[k] - 1;
+        const double f = fin[k];
+        pb.n[i] = jobs[k].n;
+        pb.m[i] = m;
+        pb.Y[i] = t[k] == 0 ? jobs[k].out : buf(k, 3);
+        pb.c[i][0] = f * cf[0];
+        pb.c[i][1] = f * cf[1] * h[k] * jobs[k].g;  // the first power is A - sigma I itself
+        pb.P[i][0] = jobs[k].Ashift;
+        double hp = h[k];
+        for (int e = 2; e <= m; ++e) {
+          hp *= h[k];
+          pb.c[i][e] = f * cf[e] * hp;
+          pb.P[i][e - 1] = jobs[k].pw[e - 2];
+        }
+        pmax = std::max(pmax, jobs[k].n);
+      }
+    }
     for (int j = Jmax - 1; j >= 0; --j) {
       GemmBatch g = gemm_batch0();
       for (int k = k0; k < k1; ++k) {
-        if (J[k] <= j) continue;
+        if (J[k] <= j || direct[k]) continue;
         const int i = g.count++;
         const bool first = j == J[k] - 1;
         const double f = j == 0 ? fin[k] : 1.0;
@@ -598,7 +663,8 @@ phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool 
       j.c = (1.0 - bank_theta[b]) * scale;
       j.norm1 = P->norm1_shifted[mu];
       j.g = P->apow_g[mu];
-      for (int i = 0; i < 3; ++i) j.pw[i] = P->dApow + (size_t)i * P->sum_n2 + P->offA[mu];
+      j.npow = P->apow_n;
+      for (int i = 0; i + 2 <= P->apow_n; ++i) j.pw[i] = P->dApow + (size_t)i * P->sum_n2 + P->offA[mu];
       j.esig = std::exp(j.c * P->sigma[mu]);
       j.out = nb.dev + nb.off[b][mu];
       jobs.push_back(j);
@@ -1950,20 +2016,29 @@ phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dty
     for (int64_t i = 0; i < m; ++i) sh[i + m * i] -= P->sigma[mu];
     CK(cudaMemcpy(P->dAs + P->offA[mu], sh.data(), m * m * 8, cudaMemcpyHostToDevice));
   }
-  {  // powers 2..4 of the scaled shifted matrices, for every small exponential
-    CK(cudaMalloc(&P->dApow, 3 * tot * 8));
+  {  // powers of the scaled shifted matrices for every small exponential:
+     // 2..15 when they take at most 256 MiB, else 2..4
+    P->apow_n = (kPolyMax - 1) * tot * 8 <= (size_t(256) << 20) ? kPolyMax : 4;
+    CK(cudaMalloc(&P->dApow, (size_t)(P->apow_n - 1) * tot * 8));
     int nn[PHIKS_MAX_D];
     const double* As[PHIKS_MAX_D];
-    double* pw[3][PHIKS_MAX_D];
+    double* pw[PHIKS_MAX_D][kPolyMax - 1];
+    double* p2[PHIKS_MAX_D];
+    double* p3[PHIKS_MAX_D];
+    double* p4[PHIKS_MAX_D];
     for (int mu = 0; mu < d; ++mu) {
       nn[mu] = (int)P->m[mu];
       As[mu] = P->dAs + P->offA[mu];
       P->apow_g[mu] = pow2_scale(P->norm1_shifted[mu]);
-      for (int i = 0; i < 3; ++i) pw[i][mu] = P->dApow + (size_t)i * tot + P->offA[mu];
+      for (int i = 0; i + 2 <= P->apow_n; ++i) pw[mu][i] = P->dApow + (size_t)i * tot + P->offA[mu];
+      p2[mu] = pw[mu][0];
+      p3[mu] = pw[mu][1];
+      p4[mu] = pw[mu][2];
     }
     cudaStream_t s0;
     CK(cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking));
-    phiks_status ps = matrix_powers(d, nn, As, P->apow_g, pw[0], pw[1], pw[2], s0);
+    phiks_status ps = matrix_powers(d, nn, As, P->apow_g, p2, p3, p4, s0);
+    if (ps == PHIKS_OK && P->apow_n == kPolyMax) ps = matrix_powers_high(d, nn, As, P->apow_g, pw, s0);
     const cudaError_t se = cudaStreamSynchronize(s0);
     cudaStreamDestroy(s0);
     if (ps != PHIKS_OK) return ps;
