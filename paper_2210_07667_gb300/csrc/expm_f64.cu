@@ -97,19 +97,6 @@ __global__ void poly_batch_f64_kernel(const __grid_constant__ PolyBatch pb) {
   }
 }
 
-__global__ void scale_batch_f64_kernel(ScaleBatch sb) {
-  pdl_wait();
-  const int k = blockIdx.y;
-  const int n = sb.n[k];
-  const int64_t nn = (int64_t)n * n;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = e % n, j = e / n;
-    double x = sb.X[k][e] - (i == j ? sb.shift[k] : 0.0);
-    sb.Y[k][e] = sb.alpha[k] * x;
-  }
-}
-
 }  // namespace
 
 cudaError_t launch_poly_batch_f64(const PolyBatch& pb, int nmax, cudaStream_t st) {
@@ -137,17 +124,6 @@ cudaError_t launch_gemm_batch_f64(const GemmBatch& gb, int nmax, cudaStream_t st
     const int t = (nmax + 7) / 8;
     return launch_pdl(gemm_batch_f64_kernel<8, 1>, dim3(t, t, gb.count), dim3(64), 0, st, gb);
   }
-}
-
-cudaError_t launch_scale_batch_f64(const ScaleBatch& sb, int nmax, cudaStream_t st) {
-  if (sb.count <= 0) return cudaSuccess;
-  if (sb.count > kMaxBatch) return cudaErrorInvalidValue;
-  int64_t nn = (int64_t)nmax * nmax;
-  int gx = (int)((nn + 255) / 256);
-  if (gx > 1024) gx = 1024;
-  dim3 grid(gx, sb.count);
-  count_launch();
-  return launch_pdl(scale_batch_f64_kernel, grid, dim3(256), 0, st, sb);
 }
 
 }  // namespace phiks

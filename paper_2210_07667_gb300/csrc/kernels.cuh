@@ -160,14 +160,4 @@ struct PolyBatch {
 };
 cudaError_t launch_poly_batch_f64(const PolyBatch& pb, int nmax, cudaStream_t st);
 
-struct ScaleBatch {
-  int count;
-  int n[kMaxBatch];
-  const double* X[kMaxBatch];
-  double* Y[kMaxBatch];
-  double alpha[kMaxBatch];
-  double shift[kMaxBatch];  // Y = alpha (X - shift I)
-};
-cudaError_t launch_scale_batch_f64(const ScaleBatch& sb, int nmax, cudaStream_t st);
-
 }  // namespace phiks

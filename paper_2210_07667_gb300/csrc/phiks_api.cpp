@@ -2361,7 +2361,6 @@ phiks_status phiks_apply_ex(phiks_plan_t P, double tau, int p, const void* const
   if (kind == 0 && p == 0 && o.skip_phi0) return fail(PHIKS_ERR_INVALID, "nothing to compute");
   DeviceGuard g(P->device);
   cudaStream_t st = (cudaStream_t)stream;
-  const int64_t N = P->N;
   const size_t es = elt_size(P);
 
   // vector norms (Sec. 3.3 uses ||v_l||_2): given, or computed on the device
