@@ -649,8 +649,8 @@ def build_served(pk, torch, arrivals, specs, dtype_name, tol_rel):
             ops = list(wk.brusselator_operators(n))
         N = int(np.prod([a.shape[0] for a in ops[0]]))
         key = (cls, n)
-        if key not in inputs:
-            seed = 1000000 + hash(key) % 100000
+        if key not in inputs:  # one seeded input set per (class, n), shared by its requests
+            seed = 1000000 + 10000 * ("ac", "adr", "bru").index(cls) + 5 * n
             vs = [wk.normal(seed + l, N).astype(np.float32).astype(np.float64) for l in range(5)]
             inputs[key] = ([torch.from_numpy(v).to(device="cuda", dtype=tdt) for v in vs],
                            [float(np.linalg.norm(v)) for v in vs])
