@@ -22,7 +22,9 @@
  *   - pointers named "host" are CPU memory, all other buffers are device
  *     memory on the device that was current when the plan was made;
  *   - the caller owns every buffer it passes; the plan owns its device copies
- *     of A_mu, the cached small exponentials and its default workspace;
+ *     of A_mu (with powers 2..15 of a scaled A_mu - sigma_mu I, or 2..4 when
+ *     those would pass 256 MiB), the cached small exponentials and its
+ *     default workspace;
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream);
  *     apply calls are asynchronous on that stream except where stated;
  *   - nothing throws: each call returns a phiks_status and records a message
