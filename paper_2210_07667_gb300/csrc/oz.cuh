@@ -10,9 +10,12 @@
 // and (k + 1) n 2^14 < 2^24 for n <= 128, so the tensor cores accumulate
 // every G_k (k = 0..6, 28 digit products) exactly in FP32; the epilogue
 // assembles floor(sum_k 2^(8 (6 - k)) G_k / 2^8) in 64-bit integers and
-// rounds it to FP64 (within (1/2 + 2^-8) ulp of the digit sum).  Dropping the
-// terms with s + t >= 7 leaves an error below about 2^-53 of |l| |x| (the
-// scale of an FP64 dot product's own rounding).
+// rounds it to FP64 (within (1/2 + 2^-8) ulp of the digit sum).  Per dot
+// product of length n the error is at most
+//   (7.03 n 2^-54 + 2^-52) max|x| max|l| + 2^-53 |result|:
+// rounding x and l to the fibre's fixed point costs 2^-54 max|x| max|l| per
+// term, the dropped digit products with s + t >= 7 at most 6.03 2^-54 per
+// term (only when the low digit products all share a sign), the floor 2^-52.
 #pragma once
 
 #include <cstdint>

@@ -1,0 +1,180 @@
+"""The arithmetic of the FP64-emulated mu-mode products (PHIKS_FP64_EMU),
+modelled on the host with exact integers.
+
+The scheme is Ozaki-style splitting (Ozaki, Ogita, Oishi and Rump, 2012) with
+balanced base-256 digits: each fibre x of the tensor (the n values contracted
+together) and each row l of the matrix is written as x_j = Q_j 2^k with
+|Q_j| < 2^55 (k from the largest element; smaller elements rounded to the
+nearest integer Q_j) and Q_j = sum_s c_s 2^(8 (6 - s)), seven digits with
+c_1..c_6 in [-128, 127] and |c_0| <= 128.  The dot product keeps the 28 digit
+products with s + t <= 6: G_k = sum_j sum_{s+t=k} b_s c_t, accumulated in FP32
+on the tensor cores, then T = sum_k 2^(8 (6 - k)) G_k, S = floor(T / 2^8) and
+the result RN(S) 2^(k_x + k_l + 56).
+
+These tests pin the two facts the GPU path relies on, independently of its
+kernels: every G_k is an integer below 2^24 for n <= 128 (so FP32 sums it
+exactly in any order), and the error per dot product is at most
+    (n (1 + 6.03) 2^-54 + 2^-52) max|x| max|l| + 2^-53 |result|
+(input rounding 2^-54 per term, the dropped products s + t >= 7 at most
+6.03 2^-54 per term, the floor 2^-52, the final rounding).
+"""
+import math
+import random
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+DIGITS = 7
+
+
+def fixed_point(x):
+    """Q_j and k with x_j = Q_j 2^k up to rounding, |Q_j| < 2^55."""
+    m = max(abs(v) for v in x)
+    if m == 0:
+        return [0] * len(x), 0
+    k = math.frexp(m)[1] - 55  # m in [2^(k + 54), 2^(k + 55))
+    scale = Fraction(2) ** k
+    return [round(Fraction(v) / scale) for v in x], k
+
+
+def balanced_digits(Q):
+    """c_0 (most significant) .. c_6 with Q = sum_s c_s 256^(6 - s)."""
+    low = []
+    for _ in range(DIGITS - 1):
+        r = (Q + 128) % 256 - 128
+        low.append(r)
+        Q = (Q - r) // 256
+    return [Q] + low[::-1]
+
+
+def slice_sums(cx, cl):
+    """G_k = sum_j sum_{s+t=k} b_s c_t for k = 0..6 (exact integers)."""
+    G = [0] * DIGITS
+    for c, b in zip(cx, cl):
+        for s in range(DIGITS):
+            for t in range(DIGITS - s):
+                G[s + t] += b[s] * c[t]
+    return G
+
+
+def emulated_dot(x, l):
+    Qx, kx = fixed_point(x)
+    Ql, kl = fixed_point(l)
+    G = slice_sums([balanced_digits(q) for q in Qx], [balanced_digits(q) for q in Ql])
+    T = sum(g << (8 * (DIGITS - 1 - k)) for k, g in enumerate(G))
+    S = T >> 8  # floor
+    return math.ldexp(float(S), kx + kl + 56), G
+
+
+def bound(x, l, result):
+    n = len(x)
+    M = max(abs(v) for v in x) * max(abs(v) for v in l)
+    return (n * 7.03 * 2.0 ** -54 + 2.0 ** -52) * M + 2.0 ** -53 * abs(result)
+
+
+def exact_dot(x, l):
+    return sum(Fraction(a) * Fraction(b) for a, b in zip(x, l))
+
+
+def test_digits_reconstruct_and_stay_balanced():
+    rng = random.Random(3)
+    for _ in range(2000):
+        Q = rng.randrange(-(2 ** 55) + 1, 2 ** 55)
+        c = balanced_digits(Q)
+        assert sum(v * 256 ** (DIGITS - 1 - s) for s, v in enumerate(c)) == Q
+        assert abs(c[0]) <= 128
+        assert all(-128 <= v <= 127 for v in c[1:])
+    for Q in (2 ** 55 - 1, -(2 ** 55) + 1, 0, 128, -128, 127 * 2 ** 40):
+        c = balanced_digits(Q)
+        assert abs(c[0]) <= 128 and sum(v * 256 ** (DIGITS - 1 - s) for s, v in enumerate(c)) == Q
+
+
+def test_fixed_point_rounding_is_half_a_unit():
+    rng = np.random.default_rng(4)
+    x = list(rng.standard_normal(64) * np.exp2(rng.integers(-70, 3, 64)))
+    Q, k = fixed_point(x)
+    m = max(abs(v) for v in x)
+    assert max(abs(q) for q in Q) < 2 ** 55
+    for v, q in zip(x, Q):
+        assert abs(Fraction(v) - q * Fraction(2) ** k) <= Fraction(2) ** (k - 1)
+        assert abs(Fraction(v) - q * Fraction(2) ** k) <= Fraction(m) * Fraction(2) ** -55
+
+
+@pytest.mark.parametrize("n", [8, 128])
+def test_slice_sums_are_exact_in_fp32_at_the_worst_digits(n):
+    # every digit at its largest magnitude with equal signs: the largest |G_k|
+    worst = [-128] * DIGITS
+    G = slice_sums([worst] * n, [worst] * n)
+    assert all(abs(g) < 2 ** 24 for g in G)
+    assert G[DIGITS - 1] == DIGITS * n * 128 * 128
+    # FP32 accumulation in a random order reproduces each G_k exactly
+    rng = np.random.default_rng(n)
+    for k in range(DIGITS):
+        terms = np.full((k + 1) * n, 128.0 * 128.0, dtype=np.float32)
+        terms[rng.random(terms.size) < 0.5] *= -1
+        exact = int(terms.astype(np.int64).sum())
+        acc = np.float32(0)
+        for v in terms[rng.permutation(terms.size)]:
+            acc = np.float32(acc + v)
+        assert int(acc) == exact
+
+
+def test_longest_exact_contraction_covers_the_supported_n():
+    # (k + 1) n 2^14 < 2^24 for k = 6 needs n <= 146; the kernels accept n <= 128
+    assert max(n for n in range(1, 400) if DIGITS * n * 2 ** 14 < 2 ** 24) == 146
+
+
+@pytest.mark.parametrize("n,seed", [(8, 1), (64, 2), (128, 3)])
+def test_error_bound_on_random_fibres(n, seed):
+    rng = np.random.default_rng(seed)
+    for trial in range(20):
+        if trial % 2:
+            x = rng.standard_normal(n)
+            l = rng.standard_normal(n)
+        else:  # wide dynamic range, including elements far below the largest
+            x = rng.standard_normal(n) * np.exp2(rng.integers(-80, 4, n))
+            l = rng.standard_normal(n) * np.exp2(rng.integers(-30, 4, n))
+        x, l = [float(v) for v in x], [float(v) for v in l]
+        got, G = emulated_dot(x, l)
+        assert all(abs(g) < 2 ** 24 for g in G)
+        err = abs(Fraction(got) - exact_dot(x, l))
+        assert err <= Fraction(bound(x, l, got))
+
+
+def _from_digits(c, shift):
+    return math.ldexp(float(sum(v * 256 ** (DIGITS - 1 - s) for s, v in enumerate(c))), shift)
+
+
+def test_error_bound_on_adversarial_digits():
+    # digits near +-128 everywhere make the dropped products s + t >= 7 as
+    # large as they can be; the bound must still hold
+    n = 128
+    x = [_from_digits([96] + [127 if (j + s) % 2 else -128 for s in range(1, DIGITS)], -48)
+         for j in range(n)]
+    l = [_from_digits([96] + [127 if s % 2 else -128 for s in range(1, DIGITS)], -48)] * n
+    got, _ = emulated_dot(x, l)
+    assert abs(Fraction(got) - exact_dot(x, l)) <= Fraction(bound(x, l, got))
+    # equal signs in every low digit: the dropped products add up, past
+    # n 2^-53 max|x| max|l|, so the truncation term of the bound is needed
+    x = [_from_digits([96] + [-128] * (DIGITS - 1), -48)] * n
+    got, _ = emulated_dot(x, x)
+    err = abs(Fraction(got) - exact_dot(x, x))
+    M = Fraction(max(abs(v) for v in x)) ** 2
+    assert err <= Fraction(bound(x, x, got))
+    assert err > n * Fraction(2) ** -53 * M
+
+
+def test_a_dropped_term_breaks_the_bound():
+    # the bound is tight enough to catch a slip: losing one slice sum (G_5,
+    # weight 2^8 in T) exceeds it on ordinary inputs
+    rng = np.random.default_rng(9)
+    x = [float(v) for v in rng.standard_normal(64)]
+    l = [float(v) for v in rng.standard_normal(64)]
+    Qx, kx = fixed_point(x)
+    Ql, kl = fixed_point(l)
+    G = slice_sums([balanced_digits(q) for q in Qx], [balanced_digits(q) for q in Ql])
+    G[DIGITS - 2] = 0
+    T = sum(g << (8 * (DIGITS - 1 - k)) for k, g in enumerate(G))
+    wrong = math.ldexp(float(T >> 8), kx + kl + 56)
+    assert abs(Fraction(wrong) - exact_dot(x, l)) > Fraction(bound(x, l, wrong))
