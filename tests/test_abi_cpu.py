@@ -80,3 +80,32 @@ def test_invalid_arguments_are_reported(pk):
     with pytest.raises(pk.PhiksError) as e:
         pk.phiks_choose_params(A, 1.0, 2, [1.0], force_s=2)    # force_s without force_q
     assert "force" in str(e.value)
+
+
+def test_plan_arguments_are_checked_before_any_device_call(pk):
+    import ctypes
+    lib = pk.load()
+    a = np.asfortranarray(np.eye(4))
+    out = ctypes.c_void_p()
+
+    def plan(d, ns, mats, dtype=pk.PHIKS_FP64, use_out=True):
+        n = (ctypes.c_int64 * max(d, 1))(*ns) if ns is not None else None
+        A = (ctypes.c_void_p * max(d, 1))(*mats) if mats is not None else None
+        return lib.phiks_plan(d, n, A, dtype, ctypes.byref(out) if use_out else None)
+
+    good = a.ctypes.data
+    cases = [
+        (dict(d=0, ns=[4], mats=[good]), "d = 0"),
+        (dict(d=9, ns=[4] * 9, mats=[good] * 9), "d = 9"),
+        (dict(d=1, ns=None, mats=[good]), "NULL"),
+        (dict(d=1, ns=[4], mats=None), "NULL"),
+        (dict(d=1, ns=[4], mats=[good], dtype=99), "dtype"),
+        (dict(d=1, ns=[0], mats=[good]), "n[0]"),
+        (dict(d=2, ns=[4, 4], mats=[good, None]), "A[1]"),
+        (dict(d=4, ns=[65536] * 4, mats=[good] * 4), "N too large"),
+        (dict(d=1, ns=[4], mats=[good], use_out=False), "out"),
+    ]
+    for kw, words in cases:
+        st = plan(**kw)
+        assert st == 1, (kw, st)                       # PHIKS_ERR_INVALID, no CUDA error
+        assert words in pk.phiks_last_error(), (kw, pk.phiks_last_error())
