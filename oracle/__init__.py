@@ -20,8 +20,12 @@ Modules
   quadrature    Gauss-Lobatto-Legendre and Gauss-Legendre rules on [0, 1]
   params        choice of s and q (Sec. 3.3)
   phiks_ref     the phiks algorithm (Sec. 3.1, 3.2) restated step by step
+  integrators   exponential Runge-Kutta schemes of Sec. 4 (exp. Euler, ETD2RK,
+                expRK3, expRK4s5, expRK4s6) with every phi term its own Taylor
+                action, and the ADR, Allen-Cahn and Brusselator nonlinear terms
 
-Parity status: every function has pins in tests/test_oracle_*.py except the
-soft reproduction of the parameter table (Table 1), which depends on readings
-of unstated constants; see the `params` module header.
+Parity status: every function has pins (tests/test_oracle_pins.py,
+tests/test_integrators.py, tests/test_complex_oracle.py); the parameter table
+(Table 1) is reproduced softly, since it depends on readings of unstated
+constants (see the `params` module header).
 """
