@@ -1971,14 +1971,16 @@ phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dty
     P->N *= n[mu];
     P->nmax = std::max<int>(P->nmax, (int)P->m[mu]);
   }
+  for (int mu = 0; mu < d; ++mu) {
+    const int64_t nin = P->cplx ? 2 * n[mu] * n[mu] : n[mu] * n[mu];  // doubles given
+    for (int64_t k = 0; k < nin; ++k)
+      if (!std::isfinite(A[mu][k])) return fail(PHIKS_ERR_INVALID, "A[%d] has a non-finite entry", mu);
+  }
   P->NR = P->cplx ? 2 * P->N : P->N;
   CK(cudaGetDevice(&P->device));
   size_t tot = 0;
   for (int mu = 0; mu < d; ++mu) {
     const int64_t nn = n[mu], m = P->m[mu];
-    const int64_t nin = P->cplx ? 2 * nn * nn : nn * nn;  // doubles given
-    for (int64_t k = 0; k < nin; ++k)
-      if (!std::isfinite(A[mu][k])) return fail(PHIKS_ERR_INVALID, "A[%d] has a non-finite entry", mu);
     std::vector<double> a(m * m);
     double tr = 0;
     if (P->cplx) {

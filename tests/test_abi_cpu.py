@@ -94,6 +94,8 @@ def test_plan_arguments_are_checked_before_any_device_call(pk):
         return lib.phiks_plan(d, n, A, dtype, ctypes.byref(out) if use_out else None)
 
     good = a.ctypes.data
+    bad = np.asfortranarray(np.eye(4))
+    bad[2, 1] = np.nan
     cases = [
         (dict(d=0, ns=[4], mats=[good]), "d = 0"),
         (dict(d=9, ns=[4] * 9, mats=[good] * 9), "d = 9"),
@@ -104,6 +106,7 @@ def test_plan_arguments_are_checked_before_any_device_call(pk):
         (dict(d=2, ns=[4, 4], mats=[good, None]), "A[1]"),
         (dict(d=4, ns=[65536] * 4, mats=[good] * 4), "N too large"),
         (dict(d=1, ns=[4], mats=[good], use_out=False), "out"),
+        (dict(d=2, ns=[4, 4], mats=[good, bad.ctypes.data]), "non-finite"),
     ]
     for kw, words in cases:
         st = plan(**kw)
