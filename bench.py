@@ -182,11 +182,14 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one oz_gemm_kernel<32> launch
-# running four mu-mode products (ncu capture of the current kernel,
-# profiles/oz_gemm_fp64emu_adr3d_n64.md), per product; None once the kernel has
-# changed since the capture
-OZ_GEMM_TRAFFIC_PER_PRODUCT = 14.8331e6 / 4
+# dram__bytes_read.sum + dram__bytes_write.sum per mu-mode product of
+# oz_gemm_kernel<32> from an ncu capture of the kernel as it stands (the
+# profile summary under profiles/ names the command); None while no capture of
+# the current kernel exists
+OZ_GEMM_TRAFFIC_PER_PRODUCT = None
+# bf16 digit products the emulated pass executes per FP64 product (digit
+# planes s + t <= 6 of seven per operand)
+OZ_DIGIT_PRODUCTS = 28
 
 
 def run_phiks(args):
@@ -262,18 +265,27 @@ def run_phiks(args):
                     "flops_per_launch": flops_per_launch,
                     "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)"}
         peaks, src = measured_peaks()
-        # algorithmic: N FP64 in + N FP64 out per mu-mode product; one launch
-        # runs the products of up to four Tucker operators together
+        # The emulated pass is a dense contraction on the tensor pipe: it
+        # executes 28 bf16 digit products (2 N n_mu flop each) per FP64
+        # mu-mode product, against the bf16 dense peak (burst: the kernel is
+        # timed launch by launch).  Its operands stay in L2 (about 0 DRAM
+        # writes, ncu), so HBM is reported beside it only as context: N
+        # doubles in and N out per product.
         products = flops_per_launch / (2.0 * N * WORKLOAD["n"])
+        executed = OZ_DIGIT_PRODUCTS * flops_per_launch
+        achieved = executed / (per_launch_ms * 1e-3) / 1e12
+        peak = peaks["bf16_tflops"]
         nbytes = 16.0 * N * products
-        achieved = nbytes / (per_launch_ms * 1e-3) / 1e9
-        return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"],
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
                 "traffic": None if OZ_GEMM_TRAFFIC_PER_PRODUCT is None else OZ_GEMM_TRAFFIC_PER_PRODUCT * products,
                 "kernel": "oz_gemm_kernel<32>", "per_launch_ms": per_launch_ms,
-                "products_per_launch": products,
-                "bytes_per_launch": nbytes, "peak_source": "hbm_gbs of %s peaks (copy)" % src,
-                "note": "latency bound at this size (tensor pipe mostly idle, ncu)"}
+                "products_per_launch": products, "fp64_flops_per_launch": flops_per_launch,
+                "bf16_flops_per_launch": executed,
+                "peak_source": "bf16_tflops (burst) of %s peaks" % src,
+                "hbm_context": {"bytes_per_launch": nbytes,
+                                "achieved_gbs": nbytes / (per_launch_ms * 1e-3) / 1e9,
+                                "peak_gbs": peaks["hbm_gbs"]}}
 
     # ---- headline path
     plan = pk.Plan(wl.A, main_dtype)
@@ -340,7 +352,8 @@ def run_phiks(args):
     line = {
         "metric": METRIC, "value": value, "unit": "phi-actions/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 (bf16-digit products emulated on tcgen05)" if main_dtype == pk.PHIKS_FP64_EMU else "f64",
         "data": "synthetic",
         "config": config_dict(wl, {"s": s_, "q": q_, "T#": T_, "tuckers_per_step": tuckers,
                                    "l2": "flushed before every timed step (256 MiB write, untimed)",
@@ -434,6 +447,7 @@ def run_precision(args):
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, device="cuda", dtype=torch.uint8)
     results = {}
+    oracle_rows = {}
     ref_out = None
     dtypes = PRECISION_DTYPES if args.dtype == "all" else ["fp64", args.dtype]
     if args.no_ref:
@@ -481,6 +495,7 @@ def run_precision(args):
         kms, kl, kfl = pk.phiks_profile_read(plan.handle)
         pk.phiks_profile_enable(plan.handle, False)
         out = torch.stack(outs).double().cpu().numpy()
+        oracle_rows[name] = out[0][:N].copy()      # phi_1 of vector 0
         if name == "fp64":
             ref_out = out
             err = 0.0
@@ -498,6 +513,21 @@ def run_precision(args):
         base = results["fp64"]["ms_per_step"]
         for r in results.values():
             r["speedup_vs_fp64"] = base / r["ms_per_step"]
+    # every dtype against the oracle on one output: phi_1(tau K) v_0 (O3;
+    # the inputs as each dtype saw them)
+    if not args.no_oracle:
+        from oracle import taylor_action as ta
+        t0 = time.perf_counter()
+        for key, v0 in (("f64", wl.vs[0]), ("f32", wl.vs[0].astype(np.float32).astype(np.float64))):
+            ex = ta.lincomb(wl.A, wl.tau, [None, v0])
+            for name, r in results.items():
+                if ("f64" if name in ("fp64", "fp64emu") else "f32") != key:
+                    continue
+                got = oracle_rows[name]
+                r["rel_err_vs_oracle"] = float(np.abs(got - ex).max() / np.abs(ex).max())
+        oracle_s = time.perf_counter() - t0
+    else:
+        oracle_s = None
     head = args.dtype if args.dtype != "all" else "bf16x3"
     h = results[head]
     line = {"metric": METRIC, "value": h["phi_actions_per_s"], "unit": "phi-actions/s", "n_gpus": 1,
@@ -509,7 +539,10 @@ def run_precision(args):
             "config": {"workload": wl.name, "d": 3, "n": [args.n] * 3, "N": N, "p": 3, "mode": "same",
                        "skip_phi0": True, "nrhs": 8, "tau": tau, "variant": args.variant,
                        "l2": "flushed before every timed step (256 MiB write, untimed)"},
-            "rel_err_vs_fp64": h["rel_err_vs_fp64"], "per_dtype": results}
+            "rel_err_vs_fp64": h["rel_err_vs_fp64"], "rel_err_vs_oracle": h.get("rel_err_vs_oracle"),
+            "oracle_check": {"output": "phi_1(tau K) v_0 (one of 24 per step)", "oracle": "O3 Taylor action",
+                             "seconds": oracle_s},
+            "per_dtype": results}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -618,10 +651,12 @@ def run_batched(args):
         for r in rows64:
             r[0].close()
     h = res[name + "_graph"]
+    if not args.no_oracle:
+        h["oracle_check"] = oracle_check_instances(insts, out_split, name)
     line = {"metric": METRIC, "value": h["phi_actions_per_s"], "unit": "phi-actions/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": h["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": name,
-            "data": "synthetic",
+            "data": "synthetic", "rel_err_vs_oracle": h.get("oracle_check", {}).get("max_rel_err"),
             "config": {"workload": "batched_adr_%d_instances" % len(insts), "instances": len(insts),
                        "d2_n": "64..512 step 32", "d3_n": "16..96 step 8", "p": 3, "skip_phi0": True,
                        "small_exponentials": "cached per instance",
@@ -629,6 +664,64 @@ def run_batched(args):
             "per_variant": res}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def o3_cost(A, tau, N):
+    """Rough cost of the O3 oracle: N sum(n) flops per matvec, ~20 terms per
+    unit of tau ||K||_1."""
+    return N * sum(a.shape[0] for a in A) * max(1.0, abs(tau) * sum(float(np.abs(a).sum(0).max()) for a in A))
+
+
+def oracle_check_instances(insts, outs, dname):
+    """phi_1..phi_3 of the cheapest d = 2 and d = 3 instances against the O3
+    oracle (the inputs rounded as the dtype saw them)."""
+    from oracle import taylor_action as ta
+    t0 = time.perf_counter()
+    picked = []
+    for d in (2, 3):
+        cand = [(o3_cost(w.A, w.tau, w.N), k) for k, w in enumerate(insts) if len(w.A) == d]
+        if cand:
+            picked.append(min(cand)[1])
+    errs = {}
+    for k in picked:
+        w = insts[k]
+        v = w.vs[0] if dname in ("fp64", "fp64emu") else w.vs[0].astype(np.float32).astype(np.float64)
+        ex = ta.same(w.A, w.tau, v, 3, ells=[1, 2, 3])
+        got = outs[k].reshape(3, w.N)
+        errs[w.name] = max(float(np.abs(got[l] - ex[l]).max() / np.abs(ex[l]).max()) for l in range(3))
+    return {"instances": errs, "max_rel_err": max(errs.values()) if errs else None,
+            "outputs": "phi_1..phi_3 of the cheapest d=2 and d=3 instance (O3)",
+            "seconds": time.perf_counter() - t0}
+
+
+def served_operators(cls, n):
+    if cls == "ac":
+        return [wk.ac_operator(n)]
+    if cls == "adr":
+        return [[wk.fd_adr_dirichlet(n, 1.0, a, 2.0 / 3) for a in (10.0, -20.0, 5.0)]]
+    return list(wk.brusselator_operators(n))
+
+
+def oracle_check_served(specs, requests):
+    """The smallest request of each class (its first apply) against the O3
+    oracle."""
+    from oracle import taylor_action as ta
+    t0 = time.perf_counter()
+    errs = {}
+    for cls in ("ac", "adr", "bru"):
+        ks = [k for k, sp in enumerate(specs) if sp[0] == cls]
+        if not ks:
+            continue
+        k = min(ks, key=lambda j: specs[j][1])
+        x = requests[k][0]
+        A = served_operators(cls, specs[k][1])[0]
+        vs = [v.double().cpu().numpy() for v in x["v"]]
+        ex = ta.lincomb(A, x["tau"], vs)
+        got = x["out"].double().cpu().numpy()
+        errs["%s_n%d" % (cls, specs[k][1])] = float(np.abs(got - ex).max() / np.abs(ex).max())
+    return {"requests": errs, "max_rel_err": max(errs.values()) if errs else None,
+            "outputs": "the smallest request of each class, first apply (O3)",
+            "seconds": time.perf_counter() - t0}
 
 
 # ---------------------------------------------------------------------------
@@ -641,12 +734,7 @@ def build_served(pk, torch, arrivals, specs, dtype_name, tol_rel):
     requests = []
     n_applies = 0
     for k, (cls, n, p) in enumerate(specs):
-        if cls == "ac":
-            ops = [wk.ac_operator(n)]
-        elif cls == "adr":
-            ops = [[wk.fd_adr_dirichlet(n, 1.0, a, 2.0 / 3) for a in (10.0, -20.0, 5.0)]]
-        else:
-            ops = list(wk.brusselator_operators(n))
+        ops = served_operators(cls, n)
         N = int(np.prod([a.shape[0] for a in ops[0]]))
         key = (cls, n)
         if key not in inputs:  # one seeded input set per (class, n), shared by its requests
@@ -727,6 +815,8 @@ def run_served(args):
     res[name + "_half_load"] = {"offered_rate_per_s": 0.5 * cap, "p50_ms": float(np.percentile(lath, 50)),
                                 "p99_ms": float(np.percentile(lath, 99)),
                                 "queue_p50_ms": float(np.percentile(qh, 50)), "makespan_s": mkh}
+    if not args.no_oracle:
+        res[name]["oracle_check"] = oracle_check_served(specs, requests)
     for p in plans.values():
         p.close()
     if not args.no_ref:
@@ -758,6 +848,7 @@ def run_served(args):
                                  "adr": "32..%d" % min(192, args.size_cap or 192),
                                  "bru": "128..%d" % min(512, args.size_cap or 512)},
                        "slots": args.slots, "hbm_budget_gb": args.budget_gb},
+            "rel_err_vs_oracle": h.get("oracle_check", {}).get("max_rel_err"),
             "latency_ms": {"p50": h["p50_ms"], "p99": h["p99_ms"],
                            "p50_half_load": res[name + "_half_load"]["p50_ms"],
                            "p99_half_load": res[name + "_half_load"]["p99_ms"]},
@@ -840,6 +931,8 @@ def main():
     ap.add_argument("--variant", default="cheb", choices=["cheb", "fd"])
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--no-ref", action="store_true", help="skip the FP64 reference path")
+    ap.add_argument("--no-oracle", action="store_true",
+                    help="precision/batched/served: skip the oracle check of sampled outputs")
     ap.add_argument("--count", type=int, default=256, help="batched form: instances")
     ap.add_argument("--streams", type=int, default=16, help="batched form: worker streams")
     ap.add_argument("--requests", type=int, default=2000, help="served form: trace length")

@@ -29,11 +29,19 @@
  *     apply calls are asynchronous on that stream except where stated;
  *   - nothing throws: each call returns a phiks_status and records a message
  *     that phiks_last_error() returns (thread-local);
- *   - everything an apply writes besides its outputs lives in its workspace,
- *     so applies on one plan may overlap on the GPU (different streams) when
- *     each passes its own workspace and its norms (phiks_options); the plan's
- *     host-side state (parameter and exponential caches) is not thread-safe,
- *     so issue the calls from one host thread.
+ *   - everything an apply writes besides its outputs lives in its workspace
+ *     or in the plan's cached small exponentials, so applies on one plan may
+ *     overlap on the GPU (different streams) when each passes its own
+ *     workspace and its norms (phiks_options).  The cached exponentials are
+ *     ordered across streams by events: a call waits (on the device, not the
+ *     host) for a cache entry another stream is still building, and a
+ *     rebuild (no_cache) or an eviction waits for every earlier use on other
+ *     streams.  The plan's host-side state (parameter and exponential
+ *     caches) is not thread-safe, so issue the calls from one host thread;
+ *   - an apply never synchronises with the host except where stated (the
+ *     device norms, below); its allocations (the plan's own workspace, new
+ *     cache entries, freed ones) are stream-ordered (cudaMallocAsync /
+ *     cudaFreeAsync on the call's stream).
  */
 #ifndef PHIKS_H
 #define PHIKS_H
@@ -149,7 +157,12 @@ phiks_status phiks_apply(phiks_plan_t plan, double tau, int p, const void* const
  *              exp(c tau K) v_0 + sum_l c^l phi_l(c tau K) v_l, c = 2^-j
  *              (the c^l convention of eq. scallincomb).
  * The first call for a given (tau, s, q) builds the small exponentials
- * exp((1 - theta_i) tau A_mu / 2^s) on the device and caches them in the plan.
+ * exp((1 - theta_i) tau A_mu / 2^s) on the device and caches them in the plan
+ * (at most 8 entries; the least recently used is evicted).  Inside a stream
+ * capture of the caller's the entry must exist already (PHIKS_ERR_INVALID
+ * otherwise), as must a plan-owned workspace of the needed size; with
+ * no_cache a captured call rebuilds the entry inside the graph, on `stream`,
+ * without waiting for other streams' uses.
  * Without opt->vnorms the call waits once for the device norms of v to reach
  * the host.  When an earlier call with the same tau, p, nv, NULL pattern of v
  * and selection options selected (s, q), the call first enqueues its work with
@@ -222,7 +235,8 @@ uint64_t phiks_kernel_launches(void);
  *   d        1 <= d <= PHIKS_MAX_D
  *   n        host, d sizes; N = n_1 ... n_d must not exceed 1,048,576
  *            (larger N returns PHIKS_ERR_INVALID)
- *   V, W     device, N doubles each, column-major tensors, may not alias
+ *   V, W     device, N doubles each, column-major tensors; the two ranges
+ *            may not overlap (PHIKS_ERR_INVALID, checked before any device call)
  *   L        host array of d device pointers to column-major n_mu x n_mu doubles
  * No plan is needed.  The intermediate tensors live in a fixed 16 MiB
  * __device__ array inside the library (two halves of 1,048,576 doubles) that
@@ -298,10 +312,11 @@ typedef struct {
  * budget; requests on different slots overlap on the GPU.  Workspaces come
  * from a memory pool owned by the call.  Outputs: latency_ms[k] from arrival
  * to completion of its kernels, queue_ms[k] (optional) from arrival to
- * dispatch, *makespan_s (optional) from start to the last completion.  Plans
- * must have run each (tau, p, norms) once before so that no parameter search
- * or exponential is built while serving.  Returns after every request has
- * finished. */
+ * dispatch, *makespan_s (optional) from start to the last completion.  A
+ * request whose (tau, s, q) has no cached exponentials yet builds them on its
+ * slot (requests of the same entry on other slots wait for it on the
+ * device); warming the plans first keeps the parameter search and those
+ * builds out of the latencies.  Returns after every request has finished. */
 phiks_status phiks_serve_trace(const phiks_serve_config* cfg, int count, const phiks_request* reqs,
                                const double* arrival_s, double* latency_ms, double* queue_ms,
                                double* makespan_s);
@@ -353,6 +368,27 @@ phiks_status phiks_integrate_blocks(int nblocks, const phiks_plan_t* plans, int 
 phiks_status phiks_integrate(phiks_plan_t plan, const int64_t* n, int d, int scheme,
                              const phiks_nonlinear* g, double t0, double T, int steps, double* u,
                              void* stream);
+
+/* Fault injection for tests of the out-of-memory paths (not for production
+ * use).  phiks_debug_fail_alloc(k): the library's device allocations (plans,
+ * workspaces, cached exponentials, scratch; in every thread) let k more
+ * succeed, then the next one fails as if the device were out of memory, and
+ * later ones succeed again; k < 0 cancels a pending failure.  The failing
+ * call returns PHIKS_ERR_OOM and releases what it had allocated.
+ * phiks_debug_live_allocations(): device allocations the library holds now
+ * (all plans together), to check that failed calls leak nothing. */
+void phiks_debug_fail_alloc(int after);
+int64_t phiks_debug_live_allocations(void);
+
+/* A check of the bounded-wait failure path of the tensor-core kernels (not
+ * for production use): launches on `stream` one CTA that allocates TMEM,
+ * waits on an mbarrier nothing arrives at until limit_ms (0 < limit_ms <=
+ * 2000) has passed, records the failure in the plan's device status word as
+ * the plan's kernels do, frees the TMEM and returns.  Afterwards
+ * phiks_device_status reports PHIKS_ERR_TIMEOUT (and clears it), the
+ * plan's kernels queued before that read skip their work, and later calls
+ * run normally.  Tensor-core plans only (PHIKS_ERR_UNSUPPORTED otherwise). */
+phiks_status phiks_debug_wait_timeout(phiks_plan_t plan, double limit_ms, void* stream);
 
 /* Release the plan and its device memory (synchronises its device). */
 void phiks_destroy(phiks_plan_t plan);

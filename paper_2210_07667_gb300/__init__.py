@@ -24,6 +24,7 @@ __all__ = [
     "phiks_profile_enable", "phiks_profile_read", "phiks_kernel_launches", "phiks_tucker_noalloc",
     "phiks_device_status", "phiks_serve_trace", "phiks_integrate", "phiks_integrate_blocks",
     "phiks_plan_shape", "phiks_destroy", "phiks_last_error", "Plan", "Batch",
+    "phiks_debug_fail_alloc", "phiks_debug_live_allocations", "phiks_debug_wait_timeout",
     "EXPORTED",
 ]
 
@@ -41,6 +42,7 @@ EXPORTED = [
     "phiks_device_status", "phiks_batch_create", "phiks_batch_destroy", "phiks_batch_apply",
     "phiks_batch_capture", "phiks_graph_launch", "phiks_graph_destroy", "phiks_serve_trace",
     "phiks_integrate", "phiks_integrate_blocks", "phiks_plan_shape", "phiks_destroy", "phiks_last_error",
+    "phiks_debug_fail_alloc", "phiks_debug_live_allocations", "phiks_debug_wait_timeout",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -181,6 +183,12 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.phiks_tucker_noalloc.restype = ctypes.c_int
     L.phiks_destroy.argtypes = [vp]
     L.phiks_destroy.restype = None
+    L.phiks_debug_fail_alloc.argtypes = [i]
+    L.phiks_debug_fail_alloc.restype = None
+    L.phiks_debug_live_allocations.argtypes = []
+    L.phiks_debug_live_allocations.restype = ctypes.c_int64
+    L.phiks_debug_wait_timeout.argtypes = [vp, d, vp]
+    L.phiks_debug_wait_timeout.restype = ctypes.c_int
     L.phiks_last_error.argtypes = []
     L.phiks_last_error.restype = ctypes.c_char_p
     for name in ["phiks_plan", "phiks_apply", "phiks_apply_ex", "phiks_workspace_size",
@@ -439,6 +447,22 @@ def phiks_plan_shape(plan: int):
     n = (ctypes.c_int64 * 8)()
     _check(load().phiks_plan_shape(plan, ctypes.byref(d), n))
     return tuple(int(n[k]) for k in range(d.value))
+
+
+def phiks_debug_fail_alloc(after: int):
+    """Make the library's device allocation after `after` more successes
+    fail as out of memory (once); a negative value cancels it."""
+    load().phiks_debug_fail_alloc(int(after))
+
+
+def phiks_debug_live_allocations() -> int:
+    """Device allocations the library holds now (all plans)."""
+    return int(load().phiks_debug_live_allocations())
+
+
+def phiks_debug_wait_timeout(plan: int, limit_ms: float, stream=None):
+    """Launch the bounded-wait check (a wait nothing ends, limit_ms)."""
+    _check(load().phiks_debug_wait_timeout(plan, float(limit_ms), _stream(stream)))
 
 
 def phiks_destroy(plan: int):

@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "../../include/phiks.h"
+#include "devmem.hpp"
 #include "kernels.cuh"
 
 namespace {
@@ -372,7 +373,7 @@ extern "C" phiks_status phiks_integrate_blocks(int nblocks, const phiks_plan_t* 
   }
   Bufs W;
   const size_t nbuf = 24;
-  if (cudaMallocAsync((void**)&E.pool, (nbuf * E.N + 3 * E.Nmax) * sizeof(double), E.st) != cudaSuccess)
+  if (phiks::dev_malloc_async((void**)&E.pool, (nbuf * E.N + 3 * E.Nmax) * sizeof(double), E.st) != cudaSuccess)
     return fail(PHIKS_ERR_OOM, "scratch");
   for (size_t k = 0; k < nbuf; ++k) W.B[k] = E.pool + k * E.N;
   E.scratch = E.pool + nbuf * E.N;
@@ -388,7 +389,7 @@ extern "C" phiks_status phiks_integrate_blocks(int nblocks, const phiks_plan_t* 
       default: res = step_exprk4s6(E, W, t, tau, w); break;
     }
   }
-  cudaFreeAsync(E.pool, E.st);
+  phiks::dev_free_async(E.pool, E.st);
   if (res != PHIKS_OK) return fail(res, E.err);
   return PHIKS_OK;
 }

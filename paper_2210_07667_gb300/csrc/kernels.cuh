@@ -127,6 +127,11 @@ cudaError_t launch_combine_batch(const Epi* e, int B, int64_t N, cudaStream_t st
 cudaError_t launch_sumsq(const void* const* x, int count, int64_t N, int is_f32, double* out,
                          cudaStream_t st);
 
+// One CTA of a tcgen05 kernel whose mbarrier wait has nothing to arrive at:
+// the wait gives up after limit_ns and records its failure in *status (the
+// status word of a tensor-core plan); waitcheck.cu.
+cudaError_t launch_wait_check(int* status, uint64_t limit_ns, cudaStream_t st);
+
 // ---- small dense FP64 matrices (the exponentials of Sec. 3) ---------------
 constexpr int kMaxBatch = 64;
 

@@ -22,6 +22,7 @@
 #include <string>
 #include <tuple>
 
+#include "devmem.hpp"
 #include "oz.cuh"
 #include "pdl.cuh"
 #include "tcgen05.cuh"
@@ -299,12 +300,14 @@ __global__ void __launch_bounds__(NTH, 1)
   uint64_t* empty = fullB + 1;
   uint64_t* tfull = empty + 1;
   uint64_t* tempty = tfull + 2;
-  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+  uint64_t* mdone = tempty + 2;  // the MMA warp's issued MMAs finished (failure path)
+  uint32_t* tmem_slot = (uint32_t*)(mdone + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int t = 0; t < kOzSlices; ++t) mbar_init(&fullA[t], 1);
     mbar_init(fullB, 1);
     mbar_init(empty, 1);
+    mbar_init(mdone, 1);
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], 32 * kOzEpiWarps);
@@ -353,18 +356,21 @@ __global__ void __launch_bounds__(NTH, 1)
         }
         if (!ok) break;
       }
-      if (issued) {  // the last copies landed
-        (void)mbar_wait(fullB, ph ^ 1, P.status, 0);
-        for (int s = 0; s < kOzSlices; ++s) (void)mbar_wait(&fullA[s], ph ^ 1, P.status, 0);
+      if (issued) {  // the last copies landed (also after another role gave up)
+        (void)mbar_drain(fullB, ph ^ 1);
+        for (int s = 0; s < kOzSlices; ++s) (void)mbar_drain(&fullA[s], ph ^ 1);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       uint32_t ph = 0, aph = 0;
       int buf = 0;
-      bool ok = true;
+      bool ok = true, any = false;
       for (int t = blockIdx.x; t < P.num_tiles && ok; t += gridDim.x) {
-        if (!mbar_wait(&tempty[buf], aph ^ 1, P.status, 12)) break;
+        if (!mbar_wait(&tempty[buf], aph ^ 1, P.status, 12)) {
+          ok = false;
+          break;
+        }
         tc_fence_after();
         const uint32_t d0 = tmem_base + (uint32_t)buf * SET;
         for (int kc = 0; kc < P.nk && ok; ++kc) {
@@ -386,6 +392,7 @@ __global__ void __launch_bounds__(NTH, 1)
               umma<0>(d0 + (uint32_t)(at * NT), sdesc_sw128(a0 + at * A_SLICE + kk * 32),
                       sdesc_sw128(b0 + kk * 32), idesc_make(1, (kOzSlices - at) * NT), first);
             }
+            any = true;
           }
           if (!ok) break;
           umma_commit(empty);
@@ -397,6 +404,10 @@ __global__ void __launch_bounds__(NTH, 1)
           buf = 0;
           aph ^= 1;
         }
+      }
+      if (!ok && any) {  // given up: the MMAs already issued finish before TMEM is freed
+        umma_commit(mdone);
+        (void)mbar_drain(mdone, 0);
       }
     }
   } else {
@@ -551,8 +562,9 @@ phiks_status oz_create(OzState** out, int d, const int64_t* n, int64_t N) {
   for (int mu = 0; mu < d; ++mu) s->n[mu] = n[mu];
   s->N = N;
   s->smem_optin = (int)prop.sharedMemPerBlockOptin;
-  if (cudaMalloc(&s->status, sizeof(int)) != cudaSuccess ||
+  if (dev_malloc((void**)&s->status, sizeof(int)) != cudaSuccess ||
       cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess) {
+    dev_free(s->status);
     delete s;
     g_oz_err = "status word allocation failed";
     return PHIKS_ERR_OOM;
@@ -563,7 +575,7 @@ phiks_status oz_create(OzState** out, int d, const int64_t* n, int64_t N) {
 
 void oz_destroy(OzState* s) {
   if (!s) return;
-  cudaFree(s->status);
+  dev_free(s->status);
   delete s;
 }
 
@@ -757,6 +769,8 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, co
   }
   return cudaSuccess;
 }
+
+int* oz_status_word(OzState* s) { return s->status; }
 
 int oz_read_status(OzState* s, cudaStream_t st) {
   int h = 0;

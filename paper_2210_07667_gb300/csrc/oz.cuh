@@ -82,5 +82,7 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, co
                       const OzPrologue* pro = nullptr);
 
 int oz_read_status(OzState* s, cudaStream_t st);
+// The device status word the kernels record a failed wait in.
+int* oz_status_word(OzState* s);
 
 }  // namespace phiks

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -21,8 +22,63 @@
 #include "planner.hpp"
 #include "oz.cuh"
 #include "tc.cuh"
+#include "devmem.hpp"
 
 using namespace phiks;
+
+// ---- device memory (devmem.hpp) ---------------------------------------------
+namespace phiks {
+namespace {
+std::atomic<int64_t> g_alloc_fail_after{-1};  // allocations to let pass before one fails (-1: none)
+std::atomic<int64_t> g_live_allocs{0};
+
+// True for the allocation that is due to fail (then the countdown stops).
+bool injected_failure() {
+  int64_t k = g_alloc_fail_after.load();
+  while (k >= 0)
+    if (g_alloc_fail_after.compare_exchange_weak(k, k - 1)) return k == 0;
+  return false;
+}
+}  // namespace
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();  // a failed allocation is reported here, not by a later call
+    return e;
+  }
+  g_live_allocs++;
+  return e;
+}
+
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaMallocAsync(p, bytes, st);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return e;
+  }
+  g_live_allocs++;
+  return e;
+}
+
+void dev_free(void* p) {
+  if (!p) return;
+  cudaFree(p);
+  g_live_allocs--;
+}
+
+void dev_free_async(void* p, cudaStream_t st) {
+  if (!p) return;
+  cudaFreeAsync(p, st);
+  g_live_allocs--;
+}
+}  // namespace phiks
 
 namespace {
 
@@ -90,6 +146,14 @@ struct Bank {
   uint64_t stamp = 0;
   uint8_t* tcb = nullptr;                  // split path: B planes of every entry
   std::vector<std::vector<size_t>> tcoff;  // tcoff[b][mu], bytes
+  // Ordering across streams, so that applies on one plan may run on several
+  // streams: `ready` is recorded on the stream that last (re)built the bank,
+  // after that call's work; uses[k] is recorded on stream k after each call
+  // that read the bank.  A call on another stream waits for `ready` before
+  // reading, and a rebuild, an eviction or a free waits for every use.
+  cudaEvent_t ready = nullptr;
+  cudaStream_t built_on = nullptr;
+  std::vector<std::pair<cudaStream_t, cudaEvent_t>> uses;
 };
 
 }  // namespace
@@ -123,6 +187,12 @@ struct phiks_plan_s {
   uint64_t clock = 0;
   double* expm_scratch = nullptr;  // 3 x (q + 1) x sum_n2 doubles
   size_t expm_scratch_elems = 0;
+  // the stream that last used expm_scratch and an event after that use: a
+  // bank built on another stream waits for it
+  cudaEvent_t scratch_ev = nullptr;
+  cudaStream_t scratch_st = nullptr;
+  bool built_this_call = false;  // get_bank (re)built a bank in the current apply
+  bool device_touched = false;   // phiks_plan reached its first CUDA call
   uint8_t* tucker_tcb = nullptr;             // split path: B planes for phiks_tucker
   size_t tcb_off[PHIKS_MAX_D] = {0};         // per-mode offsets inside one plane set
   size_t tcb_bytes = 0;
@@ -180,8 +250,32 @@ struct DeviceGuard {
 };
 
 void drop_graphs(phiks_plan_s* P) {
+  // (an executable graph still running is released when it completes)
   for (auto& g : P->graphs) cudaGraphExecDestroy(g.second.exec);
   P->graphs.clear();
+}
+
+// Drop the call graphs whose launches read or write `ptr` (about to be freed).
+void drop_graphs_using(phiks_plan_s* P, const void* ptr) {
+  if (!ptr) return;
+  const uint64_t key = (uint64_t)(uintptr_t)ptr;
+  for (auto it = P->graphs.begin(); it != P->graphs.end();) {
+    if (std::find(it->first.begin(), it->first.end(), key) != it->first.end()) {
+      cudaGraphExecDestroy(it->second.exec);
+      it = P->graphs.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cap != cudaStreamCaptureStatusNone;
 }
 
 int64_t mode_a(const phiks_plan_s* P, int mu) {
@@ -579,18 +673,49 @@ phiks_status run_expm_jobs(phiks_plan_s* P, std::vector<ExpmJob>& jobs, double* 
   return PHIKS_OK;
 }
 
-phiks_status ensure_expm_scratch(phiks_plan_s* P, size_t elems) {
+// The stream st waits for the last use of the exponential scratch on another
+// stream (stream-ordered; nothing waits on the host).
+phiks_status wait_scratch(phiks_plan_s* P, cudaStream_t st) {
+  if (P->scratch_ev && P->scratch_st != st) CK(cudaStreamWaitEvent(st, P->scratch_ev, 0));
+  return PHIKS_OK;
+}
+
+// Grow the exponential scratch in stream order on st: the old buffer is
+// released after its last use (which st waits for), the new one allocated.
+phiks_status ensure_expm_scratch(phiks_plan_s* P, size_t elems, cudaStream_t st) {
   if (P->expm_scratch_elems >= elems) return PHIKS_OK;
-  if (P->expm_scratch) {
-    CK(cudaDeviceSynchronize());
-    drop_graphs(P);
-    cudaFree(P->expm_scratch);
-  }
+  if (capturing(st))
+    return fail(PHIKS_ERR_INVALID, "the exponential scratch must grow outside stream capture");
+  TRY(wait_scratch(P, st));
+  drop_graphs_using(P, P->expm_scratch);
+  dev_free_async(P->expm_scratch, st);
   P->expm_scratch = nullptr;
   P->expm_scratch_elems = 0;
-  CK(cudaMalloc(&P->expm_scratch, elems * 8));
+  CK(dev_malloc_async((void**)&P->expm_scratch, elems * 8, st));
   P->expm_scratch_elems = elems;
   return PHIKS_OK;
+}
+
+// st waits until the bank's last build (on another stream) has run.
+phiks_status wait_bank_ready(const Bank* b, cudaStream_t st) {
+  if (b->ready && b->built_on != st) CK(cudaStreamWaitEvent(st, b->ready, 0));
+  return PHIKS_OK;
+}
+
+// st waits until the bank's last build and every use of it on another stream
+// have run: before it is rebuilt in place or freed.
+phiks_status wait_bank_idle(const Bank* b, cudaStream_t st) {
+  TRY(wait_bank_ready(b, st));
+  for (auto& u : b->uses)
+    if (u.first != st) CK(cudaStreamWaitEvent(st, u.second, 0));
+  return PHIKS_OK;
+}
+
+void destroy_bank_events(Bank& b) {
+  if (b.ready) cudaEventDestroy(b.ready);
+  for (auto& u : b.uses) cudaEventDestroy(u.second);
+  b.ready = nullptr;
+  b.uses.clear();
 }
 
 constexpr size_t kMaxBanks = 8;
@@ -598,14 +723,21 @@ constexpr size_t kMaxBanks = 8;
 phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool no_cache,
                       cudaStream_t st, Bank** out) {
   P->clock++;
+  const bool cap = capturing(st);
   Bank* hit = nullptr;
   for (auto& b : P->banks)
     if (b.tau == tau && b.s == s && b.q == q && b.rule == rule) hit = &b;
   if (hit && !no_cache) {
     hit->stamp = P->clock;
+    if (!cap) TRY(wait_bank_ready(hit, st));
     *out = hit;
     return PHIKS_OK;
   }
+  if (cap && !hit)
+    return fail(PHIKS_ERR_INVALID,
+                "the small exponentials of (tau, s, q) = (%g, %d, %d) must be built before stream capture "
+                "(run the call once first)", tau, s, q);
+  P->built_this_call = true;
   Bank nb;
   nb.tau = tau;
   nb.s = s;
@@ -635,22 +767,31 @@ phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool 
       tot += (size_t)P->m[mu] * P->m[mu];
     }
   if (hit) {
-    nb.dev = hit->dev;  // recompute in place (same layout: same q and rule)
+    // recompute in place (same layout: same q and rule) once every use of
+    // the old contents on other streams has run (inside a capture the
+    // rebuild is part of the captured call on st)
+    nb.dev = hit->dev;
+    if (!cap) TRY(wait_bank_idle(hit, st));
   } else {
-    if (P->banks.size() >= kMaxBanks) {  // evict the least recently used bank
+    if (P->banks.size() >= kMaxBanks) {
+      // evict the least recently used bank: freed in stream order on st once
+      // its last build and uses have run
       auto lru = std::min_element(P->banks.begin(), P->banks.end(),
                                   [](const Bank& x, const Bank& y) { return x.stamp < y.stamp; });
-      CK(cudaStreamSynchronize(st));
-      drop_graphs(P);
-      cudaFree(lru->dev);
-      if (lru->tcb) cudaFree(lru->tcb);
+      TRY(wait_bank_idle(&*lru, st));
+      drop_graphs_using(P, lru->dev);
+      drop_graphs_using(P, lru->tcb);
+      dev_free_async(lru->dev, st);
+      dev_free_async(lru->tcb, st);
+      destroy_bank_events(*lru);
       P->banks.erase(lru);
     }
-    CK(cudaMalloc(&nb.dev, tot * 8));
+    CK(dev_malloc_async((void**)&nb.dev, tot * 8, st));
   }
-  phiks_status es = ensure_expm_scratch(P, kScratchPerJob * tot);
+  phiks_status es = ensure_expm_scratch(P, kScratchPerJob * tot, st);
+  if (es == PHIKS_OK && !cap) es = wait_scratch(P, st);
   if (es != PHIKS_OK) {
-    if (!hit) cudaFree(nb.dev);
+    if (!hit) dev_free_async(nb.dev, st);
     return es;
   }
   std::vector<ExpmJob> jobs;
@@ -671,13 +812,20 @@ phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool 
     }
   phiks_status stt = run_expm_jobs(P, jobs, P->expm_scratch, st);
   if (stt != PHIKS_OK) {
-    if (!hit) cudaFree(nb.dev);
+    if (!hit) dev_free_async(nb.dev, st);
     return stt;
   }
   if (tc_path(P)) {  // B-operand planes of every small exponential
     nb.tcoff.assign(nbk, std::vector<size_t>(P->d));
-    if (hit) nb.tcb = hit->tcb;
-    else CK(cudaMalloc(&nb.tcb, (size_t)nbk * P->tcb_bytes));
+    if (hit) {
+      nb.tcb = hit->tcb;
+    } else {
+      const cudaError_t ae = dev_malloc_async((void**)&nb.tcb, (size_t)nbk * P->tcb_bytes, st);
+      if (ae != cudaSuccess) {
+        dev_free_async(nb.dev, st);
+        return fail(PHIKS_ERR_OOM, "B-operand planes of the small exponentials: %s", cudaGetErrorString(ae));
+      }
+    }
     std::vector<const double*> srcs;
     std::vector<int> ns;
     std::vector<void*> dsts;
@@ -695,6 +843,9 @@ phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool 
   }
   nb.stamp = P->clock;
   if (hit) {
+    nb.ready = hit->ready;  // the events stay with the bank
+    nb.built_on = hit->built_on;
+    nb.uses = std::move(hit->uses);
     *hit = nb;
     *out = hit;
   } else {
@@ -1907,6 +2058,50 @@ phiks_status run_lincomb_batched(Ctx& c, const Bank* B, int s, int p, const void
   return flush_pending(c, pout);
 }
 
+// After a call's work on st (outside any capture): mark the bank of (tau, s,
+// q, rule) as used on st, and as rebuilt on st when this call built it, and
+// the exponential scratch as last used on st.
+phiks_status record_bank_use(phiks_plan_s* P, double tau, int s, int q, int rule, bool rebuilt,
+                             cudaStream_t st) {
+  for (auto& b : P->banks) {
+    if (!(b.tau == tau && b.s == s && b.q == q && b.rule == rule)) continue;
+    cudaEvent_t ev = nullptr;
+    for (auto& u : b.uses)
+      if (u.first == st) ev = u.second;
+    if (!ev) {
+      CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      b.uses.emplace_back(st, ev);
+    }
+    CK(cudaEventRecord(ev, st));
+    if (rebuilt) {
+      if (!b.ready) CK(cudaEventCreateWithFlags(&b.ready, cudaEventDisableTiming));
+      CK(cudaEventRecord(b.ready, st));
+      b.built_on = st;
+      if (!P->scratch_ev) CK(cudaEventCreateWithFlags(&P->scratch_ev, cudaEventDisableTiming));
+      CK(cudaEventRecord(P->scratch_ev, st));
+      P->scratch_st = st;
+    }
+  }
+  return PHIKS_OK;
+}
+
+// Grow a plan-owned workspace in stream order on st (the old buffer is freed
+// after the work already queued on st; calls on the plan's own workspace
+// are ordered by the caller, see include/phiks.h).
+phiks_status grow_plan_workspace(phiks_plan_s* P, size_t need, cudaStream_t st) {
+  if (P->ws_bytes >= need) return PHIKS_OK;
+  if (capturing(st))
+    return fail(PHIKS_ERR_INVALID, "the plan's workspace must grow outside stream capture "
+                                   "(run the call once first, or pass a workspace)");
+  drop_graphs_using(P, P->ws);
+  dev_free_async(P->ws, st);
+  P->ws = nullptr;
+  P->ws_bytes = 0;
+  CK(dev_malloc_async(&P->ws, need, st));
+  P->ws_bytes = need;
+  return PHIKS_OK;
+}
+
 phiks_status check_opts(const phiks_options& o) {
   if (o.nscales < 1 || o.nscales > 64) return fail(PHIKS_ERR_INVALID, "nscales %d", o.nscales);
   if (o.rule != PHIKS_RULE_GLL && o.rule != PHIKS_RULE_GL)
@@ -1932,8 +2127,63 @@ struct phiks_batch_s {
   cudaEvent_t fork = nullptr;
 };
 
+namespace {
+
+// Every resource a plan holds (also a partly built one); the caller has made
+// sure no work on them is pending.  Stream-ordered allocations (workspace,
+// banks, exponential scratch) are released on the legacy stream.
+void release_plan(phiks_plan_s* P) {
+  for (auto e : P->ev_pool) cudaEventDestroy(e);
+  drop_graphs(P);
+  for (auto& a : P->aux) {
+    cudaStreamDestroy(a.second.st);
+    cudaEventDestroy(a.second.fork);
+    cudaEventDestroy(a.second.join);
+  }
+  for (auto& b : P->banks) {
+    dev_free_async(b.dev, nullptr);
+    dev_free_async(b.tcb, nullptr);
+    destroy_bank_events(b);
+  }
+  P->banks.clear();
+  dev_free_async(P->expm_scratch, nullptr);
+  dev_free_async(P->ws, nullptr);
+  cudaStreamSynchronize(nullptr);
+  dev_free(P->tucker_tcb);
+  dev_free(P->dAs);
+  dev_free(P->dApow);
+  dev_free(P->d_norms);
+  if (P->scratch_ev) cudaEventDestroy(P->scratch_ev);
+  if (P->norms_ready) cudaEventDestroy(P->norms_ready);
+  if (P->norms_done) cudaEventDestroy(P->norms_done);
+  if (P->norm_stream) cudaStreamDestroy(P->norm_stream);
+  if (P->h_norms) cudaFreeHost(P->h_norms);
+  if (P->tc) tc_destroy(P->tc);
+  if (P->oz) oz_destroy(P->oz);
+}
+
+// Releases a plan that phiks_plan did not hand out (an error part-way).
+struct PlanGuard {
+  phiks_plan_s* P;
+  ~PlanGuard() {
+    if (!P) return;
+    if (P->device_touched) {
+      cudaDeviceSynchronize();
+      cudaGetLastError();
+      release_plan(P);
+    }
+    delete P;
+  }
+};
+
+}  // namespace
+
 // ============================================================================
 extern "C" {
+
+void phiks_debug_fail_alloc(int after) { phiks::g_alloc_fail_after.store(after < 0 ? -1 : after); }
+
+int64_t phiks_debug_live_allocations(void) { return phiks::g_live_allocs.load(); }
 
 void phiks_options_init(phiks_options* opt) {
   if (!opt) return;
@@ -1957,7 +2207,8 @@ phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dty
   if (d < 1 || d > PHIKS_MAX_D) return fail(PHIKS_ERR_INVALID, "d = %d out of [1, %d]", d, PHIKS_MAX_D);
   if (!n || !A) return fail(PHIKS_ERR_INVALID, "n or A is NULL");
   if (dtype < PHIKS_FP64 || dtype > PHIKS_C128) return fail(PHIKS_ERR_INVALID, "dtype %d", dtype);
-  std::unique_ptr<phiks_plan_s> P(new phiks_plan_s);
+  PlanGuard guard{new phiks_plan_s};
+  phiks_plan_s* const P = guard.P;
   P->d = d;
   P->dtype = dtype;
   P->cplx = dtype == PHIKS_C128;
@@ -1977,6 +2228,7 @@ phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dty
       if (!std::isfinite(A[mu][k])) return fail(PHIKS_ERR_INVALID, "A[%d] has a non-finite entry", mu);
   }
   P->NR = P->cplx ? 2 * P->N : P->N;
+  P->device_touched = true;
   CK(cudaGetDevice(&P->device));
   size_t tot = 0;
   for (int mu = 0; mu < d; ++mu) {
@@ -2011,7 +2263,7 @@ phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dty
     tot += (size_t)m * m;
   }
   P->sum_n2 = tot;
-  CK(cudaMalloc(&P->dAs, tot * 8));
+  CK(dev_malloc((void**)&P->dAs, tot * 8));
   for (int mu = 0; mu < d; ++mu) {
     const int64_t m = P->m[mu];
     std::vector<double> sh(P->A[mu]);
@@ -2021,7 +2273,7 @@ phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dty
   {  // powers of the scaled shifted matrices for every small exponential:
      // 2..15 when they take at most 256 MiB, else 2..4
     P->apow_n = (kPolyMax - 1) * tot * 8 <= (size_t(256) << 20) ? kPolyMax : 4;
-    CK(cudaMalloc(&P->dApow, (size_t)(P->apow_n - 1) * tot * 8));
+    CK(dev_malloc((void**)&P->dApow, (size_t)(P->apow_n - 1) * tot * 8));
     int nn[PHIKS_MAX_D];
     const double* As[PHIKS_MAX_D];
     double* pw[PHIKS_MAX_D][kPolyMax - 1];
@@ -2046,9 +2298,9 @@ phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dty
     if (ps != PHIKS_OK) return ps;
     CK(se);
   }
-  CK(cudaMalloc(&P->d_norms, (PHIKS_MAX_P + 1) * 8));
+  CK(dev_malloc((void**)&P->d_norms, (PHIKS_MAX_P + 1) * 8));
   CK(cudaMallocHost(&P->h_norms, (PHIKS_MAX_P + 1) * 8));
-  if (tc_path(P.get())) {
+  if (tc_path(P)) {
     if (dtype == PHIKS_FP64_EMU) {
       phiks_status st = oz_create(&P->oz, d, P->n, P->N);
       if (st != PHIKS_OK) return fail(st, "%s", oz_last_error());
@@ -2062,9 +2314,10 @@ phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dty
       tb += dtype == PHIKS_FP64_EMU ? oz_bplanes_bytes((int)n[mu]) : tc_bplanes_bytes(dtype, (int)n[mu]);
     }
     P->tcb_bytes = tb;
-    CK(cudaMalloc(&P->tucker_tcb, tb));
+    CK(dev_malloc((void**)&P->tucker_tcb, tb));
   }
-  *out = P.release();
+  *out = P;
+  guard.P = nullptr;
   return PHIKS_OK;
 }
 
@@ -2093,6 +2346,17 @@ phiks_status phiks_profile_read(phiks_plan_t P, double* ms, int64_t* launches, d
 }
 
 uint64_t phiks_kernel_launches(void) { return phiks::kernel_launch_count(); }
+
+phiks_status phiks_debug_wait_timeout(phiks_plan_t P, double limit_ms, void* stream) {
+  g_err.clear();
+  if (!P) return fail(PHIKS_ERR_INVALID, "NULL plan");
+  if (!(limit_ms > 0) || limit_ms > 2000) return fail(PHIKS_ERR_INVALID, "limit %g ms out of (0, 2000]", limit_ms);
+  if (!P->tc && !P->oz) return fail(PHIKS_ERR_UNSUPPORTED, "the plan runs no tensor-core kernel");
+  DeviceGuard g(P->device);
+  int* status = P->tc ? tc_status_word(P->tc) : oz_status_word(P->oz);
+  CK(launch_wait_check(status, (uint64_t)(limit_ms * 1e6), (cudaStream_t)stream));
+  return PHIKS_OK;
+}
 
 phiks_status phiks_device_status(phiks_plan_t P, void* stream) {
   g_err.clear();
@@ -2238,29 +2502,7 @@ void phiks_destroy(phiks_plan_t P) {
   if (!P) return;
   DeviceGuard g(P->device);
   cudaDeviceSynchronize();
-  for (auto e : P->ev_pool) cudaEventDestroy(e);
-  drop_graphs(P);
-  for (auto& a : P->aux) {
-    cudaStreamDestroy(a.second.st);
-    cudaEventDestroy(a.second.fork);
-    cudaEventDestroy(a.second.join);
-  }
-  for (auto& b : P->banks) {
-    cudaFree(b.dev);
-    if (b.tcb) cudaFree(b.tcb);
-  }
-  cudaFree(P->tucker_tcb);
-  cudaFree(P->dAs);
-  cudaFree(P->dApow);
-  cudaFree(P->expm_scratch);
-  cudaFree(P->ws);
-  cudaFree(P->d_norms);
-  if (P->norms_ready) cudaEventDestroy(P->norms_ready);
-  if (P->norms_done) cudaEventDestroy(P->norms_done);
-  if (P->norm_stream) cudaStreamDestroy(P->norm_stream);
-  cudaFreeHost(P->h_norms);
-  if (P->tc) tc_destroy(P->tc);
-  if (P->oz) oz_destroy(P->oz);
+  release_plan(P);
   delete P;
 }
 
@@ -2447,19 +2689,10 @@ phiks_status phiks_apply_ex(phiks_plan_t P, double tau, int p, const void* const
     if (o.workspace_bytes < need)
       return fail(PHIKS_ERR_INVALID, "workspace of %zu bytes, need %zu", o.workspace_bytes, need);
   } else {
-    if (P->ws_bytes < need) {
-      if (P->ws) {
-        CK(cudaStreamSynchronize(st));
-        drop_graphs(P);
-        cudaFree(P->ws);
-      }
-      P->ws = nullptr;
-      P->ws_bytes = 0;
-      CK(cudaMalloc(&P->ws, need));
-      P->ws_bytes = need;
-    }
+    TRY(grow_plan_workspace(P, need, st));
     ws = (char*)P->ws;
   }
+  P->built_this_call = false;
   int tuckers = 0;
   auto run_with = [&](int s, int q) -> phiks_status {
     // everything from here on is device work on `st` (host state aside)
@@ -2494,7 +2727,14 @@ phiks_status phiks_apply_ex(phiks_plan_t P, double tau, int p, const void* const
       for (auto& b : P->banks)
         if (b.tau == tau && b.s == s && b.q == q && b.rule == o.rule) hit = &b;
     if (hit) {
-      // a bank exists, so the call allocates nothing: capture it once per key
+      // a bank exists, so the call allocates nothing: capture it once per key.
+      // The waits on other streams' builds and uses go before the capture or
+      // replay (they are not part of the graph).
+      TRY(wait_bank_ready(hit, st));
+      if (o.no_cache) {
+        TRY(wait_bank_idle(hit, st));
+        TRY(wait_scratch(P, st));
+      }
       std::vector<uint64_t> key;
       uint64_t tb;
       std::memcpy(&tb, &tau, 8);
@@ -2534,8 +2774,13 @@ phiks_status phiks_apply_ex(phiks_plan_t P, double tau, int p, const void* const
       }
       hit->stamp = ++P->clock;
       tuckers = it->second.tuckers;
+      if (o.no_cache) P->built_this_call = true;  // the graph rebuilt the bank on st
     } else {
       TRY(body());
+    }
+    if (cap == cudaStreamCaptureStatusNone) {
+      TRY(record_bank_use(P, tau, s, q, o.rule, P->built_this_call, st));
+      P->built_this_call = false;
     }
     return PHIKS_OK;
   };
@@ -2569,17 +2814,7 @@ phiks_status phiks_tucker(phiks_plan_t P, const void* V, void* W, const double* 
     if (!L[mu]) return fail(PHIKS_ERR_INVALID, "L[%d] is NULL", mu);
   DeviceGuard g(P->device);
   const size_t need = workspace_bytes(P, 1);
-  if (P->ws_bytes < need) {
-    if (P->ws) {
-      CK(cudaDeviceSynchronize());
-      drop_graphs(P);
-      cudaFree(P->ws);
-    }
-    P->ws = nullptr;
-    P->ws_bytes = 0;
-    CK(cudaMalloc(&P->ws, need));
-    P->ws_bytes = need;
-  }
+  TRY(grow_plan_workspace(P, need, (cudaStream_t)stream));
   Ctx c{P, (cudaStream_t)stream, {nullptr, nullptr}, 0};
   double* acc[PHIKS_MAX_P];
   carve(c, 1, (char*)P->ws, acc);
@@ -2632,10 +2867,10 @@ phiks_status phiks_expm(int batch, int n, const double* X, double* E, void* stre
     jobs[b].out = E + (size_t)b * n * n;
   }
   double* scratch = nullptr;
-  CK(cudaMallocAsync((void**)&scratch, kScratchPerJob * h.size() * 8, st));
+  CK(dev_malloc_async((void**)&scratch, kScratchPerJob * h.size() * 8, st));
   phiks_plan_s dummy;
   phiks_status r = run_expm_jobs(&dummy, jobs, scratch, st);
-  cudaFreeAsync(scratch, st);
+  dev_free_async(scratch, st);
   return r;
 }
 

@@ -29,6 +29,7 @@
 #include <string>
 #include <tuple>
 
+#include "devmem.hpp"
 #include "tc.cuh"
 #include "pdl.cuh"
 #include "tcgen05.cuh"
@@ -118,7 +119,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* empty = full + S;
   uint64_t* tfull = empty + S;
   uint64_t* tempty = tfull + 2;
-  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+  uint64_t* mdone = tempty + 2;  // the MMA warp's issued MMAs finished (failure path)
+  uint32_t* tmem_slot = (uint32_t*)(mdone + 1);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -132,6 +134,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], kTcEpiWarps * 32);
     }
+    mbar_init(mdone, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -178,13 +181,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
       }
-      // let the copies already issued land before the CTA may leave
+      // let the copies already issued land before the CTA may leave (also
+      // after another role gave up)
       for (int k = 0; k < S; ++k) {
         if (--s < 0) {
           s = S - 1;
           ph ^= 1;
         }
-        (void)mbar_wait(&full[s], ph, P.status, 0);
+        (void)mbar_drain(&full[s], ph);
       }
     }
   } else if (warp == 1) {
@@ -195,9 +199,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t ph = 0;
       int buf = 0;
       uint32_t aph = 0;
-      bool ok = true;
+      bool ok = true, any = false;
       for (int t = blockIdx.x; t < P.num_tiles && ok; t += gridDim.x) {
-        if (!mbar_wait(&tempty[buf], aph ^ 1, P.status, 2)) break;
+        if (!mbar_wait(&tempty[buf], aph ^ 1, P.status, 2)) {
+          ok = false;
+          break;
+        }
         tc_fence_after();
         const uint32_t dtm = tmem_base + (uint32_t)(buf * P.ntile);
         for (int kc = 0; kc < P.nk; ++kc) {
@@ -219,6 +226,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               umma<KIND>(dtm, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, 1);
             }
           }
+          any = true;
           umma_commit(&empty[s]);
           if (++s == S) {
             s = 0;
@@ -231,6 +239,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           buf = 0;
           aph ^= 1;
         }
+      }
+      if (!ok && any) {  // given up: the MMAs already issued finish before TMEM is freed
+        umma_commit(mdone);
+        (void)mbar_drain(mdone, 0);
       }
     }
   } else {
@@ -486,8 +498,9 @@ phiks_status tc_create(TcState** out, int dtype, int d, const int64_t* n, int64_
   for (int mu = 0; mu < d; ++mu) s->n[mu] = n[mu];
   s->N = N;
   s->smem_optin = (int)prop.sharedMemPerBlockOptin;
-  if (cudaMalloc(&s->status, sizeof(int)) != cudaSuccess ||
+  if (dev_malloc((void**)&s->status, sizeof(int)) != cudaSuccess ||
       cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess) {
+    dev_free(s->status);
     delete s;
     g_tc_err = "status word allocation failed";
     return PHIKS_ERR_OOM;
@@ -498,7 +511,7 @@ phiks_status tc_create(TcState** out, int dtype, int d, const int64_t* n, int64_
 
 void tc_destroy(TcState* s) {
   if (!s) return;
-  cudaFree(s->status);
+  dev_free(s->status);
   delete s;
 }
 
@@ -711,6 +724,8 @@ cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const TcMats* mats, co
   }
   return cudaSuccess;
 }
+
+int* tc_status_word(TcState* s) { return s->status; }
 
 int tc_read_status(TcState* s, cudaStream_t st) {
   int h = 0;

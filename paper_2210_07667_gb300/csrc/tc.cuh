@@ -77,6 +77,8 @@ cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const TcMats* mats, co
 // Device-side status: 0, or the code of a bounded wait that gave up (the
 // flag is cleared by the read).  Synchronises the stream.
 int tc_read_status(TcState* s, cudaStream_t st);
+// The device status word the kernels record a failed wait in.
+int* tc_status_word(TcState* s);
 
 // Largest n_mu the tensor-core path handles (N tiles of <= 256 rows beyond 256).
 constexpr int kTcMaxN = 1024;

@@ -52,19 +52,38 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait for the phase of `parity`; false (and *status set to `code`)
-// after about a second or as soon as another role has failed.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, int code) {
+// after limit_ns or as soon as another role has failed.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, int* status, int code,
+                                              uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 63) == 0) {
       if (*(volatile int*)status != 0) return false;
-      if (globaltimer() - t0 > kWaitNs) {
+      if (globaltimer() - t0 > limit_ns) {
         atomicCAS(status, 0, code);
         return false;
       }
     }
+  }
+}
+
+// The waits of the tensor-core kernels: limited to about a second.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, int code) {
+  return mbar_wait_for(bar, parity, status, code, kWaitNs);
+}
+
+// Bounded wait that ignores the shared failure status: a role that has
+// given up still lets its own asynchronous work (TMA copies into this CTA's
+// shared memory, MMAs writing its TMEM) finish before the CTA releases shared
+// memory and TMEM.  False after about a second.
+__device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63) == 0 && globaltimer() - t0 > kWaitNs) return false;
   }
 }
 

@@ -71,7 +71,6 @@ extern "C" phiks_status phiks_tucker_noalloc(int d, const int64_t* n, const doub
   set_error_message("");
   if (d < 1 || d > PHIKS_MAX_D) return noalloc_fail(PHIKS_ERR_INVALID, "d out of [1, PHIKS_MAX_D]");
   if (!n || !V || !W || !L) return noalloc_fail(PHIKS_ERR_INVALID, "NULL argument");
-  if (V == W) return noalloc_fail(PHIKS_ERR_INVALID, "V and W alias");
   int64_t N = 1;
   for (int mu = 0; mu < d; ++mu) {
     if (n[mu] < 1 || n[mu] > 65536) return noalloc_fail(PHIKS_ERR_INVALID, "n_mu out of [1, 65536]");
@@ -79,6 +78,11 @@ extern "C" phiks_status phiks_tucker_noalloc(int d, const int64_t* n, const doub
     if (N > kMaxElems / n[mu])
       return noalloc_fail(PHIKS_ERR_INVALID, "N = n_1 ... n_d exceeds the 1,048,576-element scratch");
     N *= n[mu];
+  }
+  {  // V and W may not share any element: with d == 1 the single mode
+     // product would read V while it writes W
+    const uintptr_t v0 = (uintptr_t)V, w0 = (uintptr_t)W, bytes = (uintptr_t)N * sizeof(double);
+    if (v0 < w0 + bytes && w0 < v0 + bytes) return noalloc_fail(PHIKS_ERR_INVALID, "V and W overlap");
   }
   double* scratch = nullptr;
   phiks_status st = scratch_address(&scratch);

@@ -160,3 +160,52 @@ def test_emulated_no_squaring(mode, p):
         ref = phiks_ref.lincomb(A, tau, wl.vs, 0, 12, nscales=1)
     for k in range(out.shape[0]):
         assert rel_inf(out[k], ref[k]) < 1e-12, k
+
+
+def _emu_bound(x_fibre_max, l_row_max, n, result):
+    """Per-output bound of one emulated dot product (x fibre, l row):
+    (7.03 n 2^-54 + 2^-52) max|x| max|l| + 2^-53 |result| (the truncated
+    digit products s + t >= 7, the fixed-point fibre representation and the
+    final rounding to FP64)."""
+    return (7.03 * n * 2.0 ** -54 + 2.0 ** -52) * x_fibre_max * l_row_max + 2.0 ** -53 * np.abs(result)
+
+
+def test_tucker_emulated_twelve_decades_within_fibres():
+    """V with magnitudes log-uniform over 1e-12 .. 1 inside every fibre
+    (d = 2, 64 x 64).  The emulation's accuracy is relative to each fibre's
+    largest element, not to sum |x_j l_j|: the exact result (rational
+    arithmetic) must lie within the composed two-mode bound of every
+    output element, and tiny elements may lose their own relative accuracy."""
+    from fractions import Fraction
+    n1 = n2 = 64
+    rng = np.random.default_rng(77)
+    X = rng.standard_normal((n1, n2)) * 10.0 ** rng.uniform(-12, 0, (n1, n2))
+    L1 = rng.standard_normal((n1, n1)) / 8
+    L2 = rng.standard_normal((n2, n2)) / 8
+    plan = pk.Plan([np.eye(n1), np.eye(n2)], EMU)
+    W = torch.empty(n1 * n2, device="cuda", dtype=torch.float64)
+    pk.phiks_tucker(plan.handle, dev(X.ravel(order="F")), W, [dev(L1.ravel(order="F")), dev(L2.ravel(order="F"))])
+    pk.phiks_device_status(plan.handle)
+    got = W.cpu().numpy().reshape((n1, n2), order="F")
+    plan.close()
+    # exact Y = L1 X L2^T in rationals
+    Xf = [[Fraction(float(X[i, j])) for j in range(n2)] for i in range(n1)]
+    L1f = [[Fraction(float(L1[i, k])) for k in range(n1)] for i in range(n1)]
+    L2f = [[Fraction(float(L2[j, k])) for k in range(n2)] for j in range(n2)]
+    Y1 = [[sum(L1f[i][k] * Xf[k][j] for k in range(n1)) for j in range(n2)] for i in range(n1)]
+    Z = np.array([[float(sum(Y1[i][k] * L2f[j][k] for k in range(n2))) for j in range(n2)]
+                  for i in range(n1)])
+    Y1d = np.array([[float(y) for y in row] for row in Y1])
+    # mode 1 (fibres = columns of X), then mode 2 on the rounded result
+    b1 = _emu_bound(np.abs(X).max(axis=0)[None, :], np.abs(L1).max(axis=1)[:, None], n1, Y1d)
+    Y1max = (np.abs(Y1d) + b1).max(axis=1)[:, None]      # fibres of mode 2 = rows of Y1
+    b2 = _emu_bound(Y1max, np.abs(L2).max(axis=1)[None, :], n2, Z)
+    bound = b1 @ np.abs(L2).T + b2
+    err = np.abs(got - Z)
+    ratio = float((err / bound).max())
+    rel = float(err.max() / np.abs(Z).max())
+    elem_rel = float(np.median(err / np.abs(Z)))
+    print("emu 12-decade fibres: max err/bound %.3f, rel inf-norm %.2e, median element rel %.2e"
+          % (ratio, rel, elem_rel))
+    assert ratio <= 1.0
+    assert rel < 1e-14
