@@ -369,6 +369,52 @@ phiks_status phiks_integrate(phiks_plan_t plan, const int64_t* n, int d, int sch
                              const phiks_nonlinear* g, double t0, double T, int steps, double* u,
                              void* stream);
 
+/* Tuning of a plan's kernels: the tile shapes and mode orders the
+ * autotuner chooses among (0 = the library's size-based default for each
+ * knob).  Results of every setting agree to rounding: the modes of a Tucker
+ * operator commute, and the tiles only regroup the same sums.
+ *   fused         real FP64 plans: -1 by size (N <= 65536), 0 mode-by-mode
+ *                 passes, 1 the fused small-slab kernel (all d modes of a
+ *                 Tucker operator, and the batch's input combinations, in one
+ *                 launch with the intermediates in shared memory; only when
+ *                 16 N / n_d bytes and the matrices fit there)
+ *   fused_rows    fused kernel: rows of the last mode per CTA (1, 2, 4, 8;
+ *                 0 by batch size)
+ *   fp64_tile     FP64 / C128 mode products: 1 16 x 16, 2 32 x 64 output tiles
+ *   mode_order    FP64 / C128 mode-by-mode passes: a permutation of 0..d-1
+ *                 (entries past d are ignored; phiks_get_tuning sets them -1)
+ *   emu_cols      FP64_EMU GEMM pass: rows of L per tile, 16 or 32
+ *   split_ntiles  split dtypes: GEMM column tiles per pass as a multiple of
+ *                 ceil(n_pad / 256): 1, 2 or 4 */
+typedef struct {
+  int fused;
+  int fused_rows;
+  int fp64_tile;
+  int mode_order[PHIKS_MAX_D];
+  int emu_cols;
+  int split_ntiles;
+  int reserved[8];
+} phiks_tuning;
+
+/* The plan's current tuning (host only). */
+phiks_status phiks_get_tuning(phiks_plan_t plan, phiks_tuning* tuning);
+/* Set it (host only; checked, PHIKS_ERR_INVALID / PHIKS_ERR_UNSUPPORTED for a
+ * knob the plan cannot take).  Drops the plan's captured call graphs. */
+phiks_status phiks_set_tuning(phiks_plan_t plan, const phiks_tuning* tuning);
+
+/* Autotuner: times every candidate tuning of the plan's dtype (tile shapes,
+ * mode orders, fused or mode-by-mode) on `reps` applies of this call shape
+ * (tau, p, nv and opt's nscales, skip_phi0, tolerance and graph; seeded
+ * synthetic inputs in [-1, 1]) on `stream`, sets the fastest and returns it
+ * with its milliseconds per apply.  Synchronises `stream` and allocates its
+ * inputs and output (not for use inside a capture).  When the environment
+ * variable PHIKS_TUNE_CACHE names a file, a line for the same (dtype, n_mu,
+ * p, nv, nscales) found there is used instead of timing (its milliseconds
+ * returned as recorded), and a new result is appended as one line
+ * "<key> | <knobs> ms=<time>". */
+phiks_status phiks_autotune(phiks_plan_t plan, double tau, int p, int nv, const phiks_options* opt,
+                            int reps, void* stream, phiks_tuning* best, double* best_ms);
+
 /* Fault injection for tests of the out-of-memory paths (not for production
  * use).  phiks_debug_fail_alloc(k): the library's device allocations (plans,
  * workspaces, cached exponentials, scratch; in every thread) let k more

@@ -25,6 +25,7 @@ __all__ = [
     "phiks_device_status", "phiks_serve_trace", "phiks_integrate", "phiks_integrate_blocks",
     "phiks_plan_shape", "phiks_destroy", "phiks_last_error", "Plan", "Batch",
     "phiks_debug_fail_alloc", "phiks_debug_live_allocations", "phiks_debug_wait_timeout",
+    "Tuning", "phiks_get_tuning", "phiks_set_tuning", "phiks_autotune",
     "EXPORTED",
 ]
 
@@ -43,6 +44,7 @@ EXPORTED = [
     "phiks_batch_capture", "phiks_graph_launch", "phiks_graph_destroy", "phiks_serve_trace",
     "phiks_integrate", "phiks_integrate_blocks", "phiks_plan_shape", "phiks_destroy", "phiks_last_error",
     "phiks_debug_fail_alloc", "phiks_debug_live_allocations", "phiks_debug_wait_timeout",
+    "phiks_get_tuning", "phiks_set_tuning", "phiks_autotune",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -50,6 +52,25 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 def library_path() -> str:
     return os.path.join(HERE, "libphiks.so")
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [
+        ("fused", ctypes.c_int),
+        ("fused_rows", ctypes.c_int),
+        ("fp64_tile", ctypes.c_int),
+        ("mode_order", ctypes.c_int * 8),
+        ("emu_cols", ctypes.c_int),
+        ("split_ntiles", ctypes.c_int),
+        ("reserved", ctypes.c_int * 8),
+    ]
+
+    def as_dict(self, d=None):
+        order = list(self.mode_order)
+        if d is not None:
+            order = order[:d]
+        return {"fused": self.fused, "fused_rows": self.fused_rows, "fp64_tile": self.fp64_tile,
+                "mode_order": order, "emu_cols": self.emu_cols, "split_ntiles": self.split_ntiles}
 
 
 class Options(ctypes.Structure):
@@ -189,6 +210,13 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.phiks_debug_live_allocations.restype = ctypes.c_int64
     L.phiks_debug_wait_timeout.argtypes = [vp, d, vp]
     L.phiks_debug_wait_timeout.restype = ctypes.c_int
+    L.phiks_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+    L.phiks_get_tuning.restype = ctypes.c_int
+    L.phiks_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+    L.phiks_set_tuning.restype = ctypes.c_int
+    L.phiks_autotune.argtypes = [vp, d, i, i, ctypes.POINTER(Options), i, vp, ctypes.POINTER(Tuning),
+                                 ctypes.POINTER(d)]
+    L.phiks_autotune.restype = ctypes.c_int
     L.phiks_last_error.argtypes = []
     L.phiks_last_error.restype = ctypes.c_char_p
     for name in ["phiks_plan", "phiks_apply", "phiks_apply_ex", "phiks_workspace_size",
@@ -463,6 +491,38 @@ def phiks_debug_live_allocations() -> int:
 def phiks_debug_wait_timeout(plan: int, limit_ms: float, stream=None):
     """Launch the bounded-wait check (a wait nothing ends, limit_ms)."""
     _check(load().phiks_debug_wait_timeout(plan, float(limit_ms), _stream(stream)))
+
+
+def phiks_get_tuning(plan: int) -> Tuning:
+    t = Tuning()
+    _check(load().phiks_get_tuning(plan, ctypes.byref(t)))
+    return t
+
+
+def phiks_set_tuning(plan: int, t: Tuning = None, **kw):
+    """Set the plan's tuning: a Tuning, or the current one with fields from kw
+    (mode_order as a sequence)."""
+    if t is None:
+        t = phiks_get_tuning(plan)
+    for k, v in kw.items():
+        if k == "mode_order":
+            for j in range(8):
+                t.mode_order[j] = int(v[j]) if j < len(v) else -1
+        else:
+            setattr(t, k, int(v))
+    _check(load().phiks_set_tuning(plan, ctypes.byref(t)))
+    return t
+
+
+def phiks_autotune(plan: int, tau: float, p: int, nv: int, reps: int = 5, stream=None, **kw):
+    """Time the candidate tunings on this call shape, set and return the
+    fastest: (Tuning, ms per apply)."""
+    o = make_options(**kw)
+    t = Tuning()
+    ms = ctypes.c_double()
+    _check(load().phiks_autotune(plan, float(tau), int(p), int(nv), ctypes.byref(o), int(reps),
+                                 _stream(stream), ctypes.byref(t), ctypes.byref(ms)))
+    return t, ms.value
 
 
 def phiks_destroy(plan: int):

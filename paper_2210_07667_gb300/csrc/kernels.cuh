@@ -99,8 +99,9 @@ struct ModeGeom {
 
 // W = V x_mu L (FP64).  V given by `pro` (a combination), L column-major
 // n x n.  With epi == nullptr or epi->nout == 0 the result goes to W.
+// tile: 0 by size, 1 16 x 16 output tiles, 2 32 x 64 output tiles.
 cudaError_t launch_mode_product_f64(const Combo& pro, const double* L, ModeGeom g, double* W,
-                                    const Epi* epi, cudaStream_t st);
+                                    const Epi* epi, cudaStream_t st, int tile = 0);
 // B <= kMaxModeBatch independent mode products of the same geometry in one
 // launch: W[b] = (combination pro[b]) x_mu L[b], stored plainly.
 constexpr int kMaxModeBatch = 16;
@@ -109,7 +110,8 @@ struct ModeBatch {
   const double* L[kMaxModeBatch];
   double* W[kMaxModeBatch];
 };
-cudaError_t launch_mode_product_f64_batch(const ModeBatch& mb, int B, ModeGeom g, cudaStream_t st);
+cudaError_t launch_mode_product_f64_batch(const ModeBatch& mb, int B, ModeGeom g, cudaStream_t st,
+                                          int tile = 0);
 // The same for complex V, W (interleaved) and L given as its 2n x 2n real
 // representation (PHIKS_C128 plans).
 cudaError_t launch_mode_product_c128(const Combo& pro, const double* L, ModeGeom g, double* W,
@@ -126,6 +128,35 @@ cudaError_t launch_combine_batch(const Epi* e, int B, int64_t N, cudaStream_t st
 // (is_f32 == 0) or float.
 cudaError_t launch_sumsq(const void* const* x, int count, int64_t N, int is_f32, double* out,
                          cudaStream_t st);
+
+// Fused small-slab Tucker operators (tucker_fused.cu): B <= kMaxModeBatch
+// independent FP64 Tucker operators W[b] = (combination pro[b]) x_1 L[b][0]
+// ... x_d L[b][d-1] in one launch, every intermediate in shared memory;
+// store[b] (or null) also receives the input combination's values, and nside
+// elementwise combinations side[k] -> side_out[k] over N elements run in the
+// same launch (they may read what the launch's inputs read, and nothing the
+// launch writes).  Needs the slab of one last-mode row, 16 N / n_d bytes, and
+// the matrices in shared memory (fused_f64_ok).  nj: last-mode rows per CTA
+// (1, 2, 4 or 8; fewer when the slab would not fit); with an epilogue
+// (epi->nout > 0) the results go through it instead of W.
+constexpr int kFusedMaxD = 8;
+constexpr int kFusedMaxSide = 8;
+constexpr int64_t kFusedMaxN = int64_t(1) << 20;
+constexpr int kFusedMaxSmem = 200 * 1024;
+struct FusedBatch {
+  int B;
+  Combo pro[kMaxModeBatch];
+  const double* L[kMaxModeBatch][kFusedMaxD];
+  double* W[kMaxModeBatch];
+  double* store[kMaxModeBatch];
+  int nside;
+  Combo side[kFusedMaxSide];
+  double* side_out[kFusedMaxSide];
+};
+bool fused_f64_ok(int d, const int64_t* n, int64_t N);
+int fused_f64_default_nj(int d, const int64_t* n, int64_t N, int B);
+cudaError_t launch_tucker_fused_f64(const FusedBatch& fb, int d, const int64_t* n, int64_t N, int nj,
+                                    const Epi* epi, cudaStream_t st);
 
 // One CTA of a tcgen05 kernel whose mbarrier wait has nothing to arrive at:
 // the wait gives up after limit_ns and records its failure in *status (the

@@ -529,6 +529,7 @@ struct OzState {
   double* tmp[2] = {nullptr, nullptr};
   int batch = 0;  // tensors the bound workspace holds
   int smem_optin = 0;
+  int ntile = 0;  // rows of L per GEMM tile (0: by size)
   std::map<std::tuple<const void*, uint64_t, uint64_t, uint32_t, uint64_t>, CUtensorMap> maps;
 };
 
@@ -699,7 +700,7 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, co
       if (e != cudaSuccess) return e;
     }
     const int np = (n + 63) / 64 * 64;
-    const int NT = ntile_for(n, rows);
+    const int NT = s->ntile ? s->ntile : ntile_for(n, rows);
     OzParams P;
     std::memset(&P, 0, sizeof P);
     OzMaps mB;
@@ -771,6 +772,8 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, co
 }
 
 int* oz_status_word(OzState* s) { return s->status; }
+
+void oz_set_ntile(OzState* s, int nt) { s->ntile = (nt == 16 || nt == 32) ? nt : 0; }
 
 int oz_read_status(OzState* s, cudaStream_t st) {
   int h = 0;

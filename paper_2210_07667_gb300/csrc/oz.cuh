@@ -82,6 +82,8 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, co
                       const OzPrologue* pro = nullptr);
 
 int oz_read_status(OzState* s, cudaStream_t st);
+// Rows of L per GEMM tile (16 or 32; 0 = by size).
+void oz_set_ntile(OzState* s, int nt);
 // The device status word the kernels record a failed wait in.
 int* oz_status_word(OzState* s);
 

@@ -10,6 +10,10 @@
 #include <cstdio>
 #include <cstring>
 #include <array>
+#include <cstdlib>
+#include <fstream>
+#include <iomanip>
+#include <sstream>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -209,6 +213,20 @@ struct phiks_plan_s {
   int last_s = -1, last_q = -1, last_T = -1, last_tuckers = 0;
   TcState* tc = nullptr;
   OzState* oz = nullptr;
+  // fused small-slab Tucker operators (real FP64 plans whose slab of one
+  // last-mode row and matrices fit in shared memory): fused_ok from the
+  // shape; fused_mode -1 = by size (N <= kFusedAutoN), 0 = off, 1 = on;
+  // fused_nj = last-mode rows per CTA (0 = by batch size)
+  bool fused_ok = false;
+  int fused_mode = -1;
+  int fused_nj = 0;
+  // other tuned knobs (phiks_tuning): FP64 mode-product tiles (0 by size),
+  // the order of the FP64 mode-by-mode passes, the FP64_EMU GEMM tile rows
+  // and the split dtypes' N-tile multiplier
+  int fp64_tile = 0;
+  int order[PHIKS_MAX_D] = {0, 1, 2, 3, 4, 5, 6, 7};
+  int emu_cols = 0;
+  int split_ntiles = 0;
   // CUDA graphs of whole calls (phiks_options.graph), keyed by everything the
   // captured launches depend on
   struct CallGraph {
@@ -861,6 +879,7 @@ struct Ctx {
   cudaStream_t st;
   double* tmp[2];
   int tuckers = 0;
+  int ftog = 0;  // fused batches: the temporary the next batch's results go to
   int bmax = 1;  // Tucker operators one tensor-core batch may hold
   double* acc2[PHIKS_MAX_P] = {nullptr};  // FP64_EMU: accumulators of batched squaring
   double* msq[2] = {nullptr, nullptr};      // squaring chain ping-pong
@@ -924,6 +943,26 @@ phiks_status prof_end(Ctx& c, cudaEvent_t e1, double flops) {
   return PHIKS_OK;
 }
 
+// Fused kernel for B Tucker operators of this plan (real FP64 only).
+constexpr int64_t kFusedAutoN = 65536;
+bool use_fused(const phiks_plan_s* P) {
+  if (P->dtype != PHIKS_FP64 || P->cplx || !P->fused_ok) return false;
+  return P->fused_mode == 1 || (P->fused_mode < 0 && P->N <= kFusedAutoN);
+}
+int fused_nj(const phiks_plan_s* P, int B) {
+  return P->fused_nj > 0 ? P->fused_nj : fused_f64_default_nj(P->d, P->n, P->N, B);
+}
+
+// Whether an epilogue writes a tensor the Tucker input reads: every CTA of
+// the fused kernel reads the whole input, so those cannot run fused.
+bool epi_writes_input(const Combo& in, const Epi* e) {
+  if (!e) return false;
+  for (int t = 0; t < e->nout; ++t)
+    for (int m = 0; m < in.nsrc; ++m)
+      if ((const void*)e->out[t] == (const void*)in.src[m]) return true;
+  return false;
+}
+
 // (input combination) x_1 L_1 ... x_d L_d, the last mode through `epi`.
 // FP64: one profiled launch per mode; FP64_EMU: one profiled tensor-core
 // pass per mode; split dtypes: one profiled tensor-core Tucker (split pass +
@@ -959,15 +998,31 @@ phiks_status tucker(Ctx& c, const Combo& in, const Mats& M, const Epi* epi) {
     c.tuckers++;
     return PHIKS_OK;
   }
+  if (!P->cplx && use_fused(P) && epi && epi->nout > 0 && !epi_writes_input(in, epi)) {
+    FusedBatch fb;
+    std::memset(&fb, 0, sizeof fb);
+    fb.B = 1;
+    fb.pro[0] = in;
+    for (int mu = 0; mu < P->d; ++mu) fb.L[0][mu] = M.L[mu];
+    cudaEvent_t e1;
+    TRY(prof_begin(c, &e1));
+    CK(launch_tucker_fused_f64(fb, P->d, P->n, P->N, fused_nj(P, 1), epi, c.st));
+    double fl = 0;
+    for (int mu = 0; mu < P->d; ++mu) fl += 2.0 * (double)P->N * (double)P->n[mu];
+    TRY(prof_end(c, e1, fl));
+    c.tuckers++;
+    return PHIKS_OK;
+  }
   Combo cur = in;
-  for (int mu = 0; mu < P->d; ++mu) {
-    const bool last = (mu == P->d - 1);
-    double* out = last ? nullptr : c.tmp[mu & 1];
+  for (int k = 0; k < P->d; ++k) {
+    const int mu = P->order[k];  // the modes commute: any order gives the operator
+    const bool last = (k == P->d - 1);
+    double* out = last ? nullptr : c.tmp[k & 1];
     ModeGeom g{mode_a(P, mu), (int)P->n[mu], mode_b(P, mu)};
     cudaEvent_t e1;
     TRY(prof_begin(c, &e1));
     if (P->cplx) CK(launch_mode_product_c128(cur, M.L[mu], g, out, last ? epi : nullptr, c.st));
-    else CK(launch_mode_product_f64(cur, M.L[mu], g, out, last ? epi : nullptr, c.st));
+    else CK(launch_mode_product_f64(cur, M.L[mu], g, out, last ? epi : nullptr, c.st, P->fp64_tile));
     TRY(prof_end(c, e1, (P->cplx ? 8.0 : 2.0) * (double)P->N * (double)P->n[mu]));
     cur = make_combo();
     cur.nsrc = 1;
@@ -1081,6 +1136,54 @@ phiks_status tucker_mixed(Ctx& c, int B, const Combo* in, const Mats* M, const v
       return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), oz_last_error());
     if (prof)
       for (int mu = 0; mu < P->d; ++mu) P->prof_flops += 2.0 * B * (double)P->N * (double)P->n[mu];
+  } else if (!tc_path(P) && use_fused(P)) {
+    // real FP64, fused: one launch evaluates the prologue (inputs, stores,
+    // extra combinations) and all d modes of the B operators; the results
+    // alternate between the two temporaries, since this batch's inputs may
+    // read the previous batch's results
+    FusedBatch fb;
+    std::memset(&fb, 0, sizeof fb);
+    fb.B = B;
+    double* W = c.tmp[c.ftog];
+    for (int b = 0; b < B; ++b) {
+      fb.pro[b] = in[b];
+      for (int mu = 0; mu < P->d; ++mu) fb.L[b][mu] = M[b].L[mu];
+      fb.W[b] = W + (size_t)b * P->NR;
+      fb.store[b] = pro ? pro->store[b] : nullptr;
+    }
+    if (pro) {
+      if (pro->side_f32) return fail(PHIKS_ERR_INVALID, "prologue");
+      int k0 = 0;
+      if (pro->nside > kFusedMaxSide) {  // the extra ones first, in a pass of their own
+        std::vector<Epi> es;
+        for (k0 = 0; k0 < pro->nside - kFusedMaxSide; ++k0) {
+          Epi e = make_epi();
+          e.nout = 1;
+          e.out[0] = (double*)pro->side_out[k0];
+          e.nsrc = pro->side[k0].nsrc;
+          e.src_f32mask = pro->side[k0].f32mask;
+          for (int m = 0; m < e.nsrc; ++m) {
+            e.src[m] = pro->side[k0].src[m];
+            e.a[0][m] = pro->side[k0].coef[m];
+          }
+          es.push_back(e);
+        }
+        TRY(combine_many(c, es.data(), (int)es.size()));
+      }
+      for (int k = k0; k < pro->nside; ++k) {
+        fb.side[fb.nside] = pro->side[k];
+        fb.side_out[fb.nside++] = (double*)pro->side_out[k];
+      }
+    }
+    cudaEvent_t e1;
+    double fl = 0;
+    for (int mu = 0; mu < P->d; ++mu) fl += 2.0 * B * (double)P->N * (double)P->n[mu];
+    TRY(prof_begin(c, &e1));
+    CK(launch_tucker_fused_f64(fb, P->d, P->n, P->N, fused_nj(P, B), nullptr, c.st));
+    TRY(prof_end(c, e1, fl));
+    *res = W;
+    *r32 = false;
+    c.ftog ^= 1;
   } else if (!tc_path(P)) {
     // real FP64: the prologue's stores and extra combinations first (one
     // combination pass), then d batched mode products through the two
@@ -1113,22 +1216,21 @@ phiks_status tucker_mixed(Ctx& c, int B, const Combo* in, const Mats* M, const v
     double fl = 0;
     for (int mu = 0; mu < P->d; ++mu) fl += 2.0 * B * (double)P->N * (double)P->n[mu];
     TRY(prof_begin(c, &e1));
-    int64_t a = 1;
-    for (int mu = 0; mu < P->d; ++mu) {
+    for (int k = 0; k < P->d; ++k) {
+      const int mu = P->order[k];
       ModeBatch mb;
       std::memset(&mb, 0, sizeof mb);
-      double* outp = c.tmp[mu & 1];
+      double* outp = c.tmp[k & 1];
       for (int b = 0; b < B; ++b) {
-        mb.pro[b] = mu == 0 ? ins[b] : plain(c.tmp[(mu - 1) & 1] + (size_t)b * P->NR, false);
+        mb.pro[b] = k == 0 ? ins[b] : plain(c.tmp[(k - 1) & 1] + (size_t)b * P->NR, false);
         mb.L[b] = M[b].L[mu];
         mb.W[b] = outp + (size_t)b * P->NR;
       }
       ModeGeom g;
-      g.a = a;
+      g.a = mode_a(P, mu);
       g.n = (int)P->n[mu];
-      g.b = P->N / (a * P->n[mu]);
-      CK(launch_mode_product_f64_batch(mb, B, g, c.st));
-      a *= P->n[mu];
+      g.b = mode_b(P, mu);
+      CK(launch_mode_product_f64_batch(mb, B, g, c.st, P->fp64_tile));
     }
     TRY(prof_end(c, e1, fl));
     *res = c.tmp[(P->d - 1) & 1];
@@ -2228,6 +2330,7 @@ phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dty
       if (!std::isfinite(A[mu][k])) return fail(PHIKS_ERR_INVALID, "A[%d] has a non-finite entry", mu);
   }
   P->NR = P->cplx ? 2 * P->N : P->N;
+  P->fused_ok = dtype == PHIKS_FP64 && fused_f64_ok(d, P->n, P->N);
   P->device_touched = true;
   CK(cudaGetDevice(&P->device));
   size_t tot = 0;
@@ -2504,6 +2607,266 @@ void phiks_destroy(phiks_plan_t P) {
   cudaDeviceSynchronize();
   release_plan(P);
   delete P;
+}
+
+// ---- tuning -------------------------------------------------------------------
+phiks_status phiks_get_tuning(phiks_plan_t P, phiks_tuning* t) {
+  g_err.clear();
+  if (!P || !t) return fail(PHIKS_ERR_INVALID, "NULL argument");
+  std::memset(t, 0, sizeof *t);
+  t->fused = P->fused_mode;
+  t->fused_rows = P->fused_nj;
+  t->fp64_tile = P->fp64_tile;
+  for (int k = 0; k < PHIKS_MAX_D; ++k) t->mode_order[k] = k < P->d ? P->order[k] : -1;
+  t->emu_cols = P->emu_cols;
+  t->split_ntiles = P->split_ntiles;
+  return PHIKS_OK;
+}
+
+phiks_status phiks_set_tuning(phiks_plan_t P, const phiks_tuning* t) {
+  g_err.clear();
+  if (!P || !t) return fail(PHIKS_ERR_INVALID, "NULL argument");
+  if (t->fused < -1 || t->fused > 1) return fail(PHIKS_ERR_INVALID, "fused = %d", t->fused);
+  if (t->fused_rows != 0 && t->fused_rows != 1 && t->fused_rows != 2 && t->fused_rows != 4 && t->fused_rows != 8)
+    return fail(PHIKS_ERR_INVALID, "fused_rows = %d", t->fused_rows);
+  if (t->fp64_tile < 0 || t->fp64_tile > 2) return fail(PHIKS_ERR_INVALID, "fp64_tile = %d", t->fp64_tile);
+  if (t->emu_cols != 0 && t->emu_cols != 16 && t->emu_cols != 32)
+    return fail(PHIKS_ERR_INVALID, "emu_cols = %d", t->emu_cols);
+  if (t->split_ntiles != 0 && t->split_ntiles != 1 && t->split_ntiles != 2 && t->split_ntiles != 4)
+    return fail(PHIKS_ERR_INVALID, "split_ntiles = %d", t->split_ntiles);
+  unsigned seen = 0;
+  for (int k = 0; k < P->d; ++k) {
+    const int mu = t->mode_order[k];
+    if (mu < 0 || mu >= P->d || ((seen >> mu) & 1)) return fail(PHIKS_ERR_INVALID, "mode_order is not a permutation");
+    seen |= 1u << mu;
+  }
+  if (t->fused == 1 && !P->fused_ok)
+    return fail(PHIKS_ERR_UNSUPPORTED, "the fused kernel needs a real FP64 plan whose slab fits on chip");
+  P->fused_mode = t->fused;
+  P->fused_nj = t->fused_rows;
+  P->fp64_tile = t->fp64_tile;
+  for (int k = 0; k < P->d; ++k) P->order[k] = t->mode_order[k];
+  P->emu_cols = t->emu_cols;
+  P->split_ntiles = t->split_ntiles;
+  if (P->oz) oz_set_ntile(P->oz, t->emu_cols);
+  if (P->tc) tc_set_ntiles(P->tc, t->split_ntiles);
+  drop_graphs(P);  // captured calls hold the old launch shapes
+  return PHIKS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The candidates the tuner times for a plan: tile shapes and mode orders of
+// its dtype's passes (the first is the library's default).
+std::vector<phiks_tuning> tuning_candidates(const phiks_plan_s* P) {
+  std::vector<phiks_tuning> out;
+  phiks_tuning base;
+  std::memset(&base, 0, sizeof base);
+  base.fused = -1;
+  for (int k = 0; k < PHIKS_MAX_D; ++k) base.mode_order[k] = k < P->d ? k : -1;
+  out.push_back(base);
+  if (P->dtype == PHIKS_FP64 || P->cplx) {
+    std::vector<std::vector<int>> orders;
+    std::vector<int> id(P->d);
+    for (int k = 0; k < P->d; ++k) id[k] = k;
+    orders.push_back(id);
+    if (P->d <= 3) {  // every order for d <= 3
+      std::vector<int> o = id;
+      while (std::next_permutation(o.begin(), o.end())) orders.push_back(o);
+    } else {
+      orders.push_back(std::vector<int>(id.rbegin(), id.rend()));
+    }
+    for (int tile = 1; tile <= 2; ++tile)
+      for (auto& o : orders) {
+        phiks_tuning t = base;
+        t.fused = 0;
+        t.fp64_tile = tile;
+        for (int k = 0; k < P->d; ++k) t.mode_order[k] = o[k];
+        out.push_back(t);
+      }
+    if (P->fused_ok)
+      for (int rows : {1, 2, 4, 8}) {
+        if (rows > P->n[P->d - 1]) break;
+        phiks_tuning t = base;
+        t.fused = 1;
+        t.fused_rows = rows;
+        out.push_back(t);
+      }
+  } else if (P->dtype == PHIKS_FP64_EMU) {
+    for (int c : {16, 32}) {
+      phiks_tuning t = base;
+      t.emu_cols = c;
+      out.push_back(t);
+    }
+  } else {
+    for (int m : {1, 2, 4}) {
+      phiks_tuning t = base;
+      t.split_ntiles = m;
+      out.push_back(t);
+    }
+  }
+  return out;
+}
+
+std::string tuning_key(const phiks_plan_s* P, int p, int nv, int nscales) {
+  std::ostringstream k;
+  k << "dtype=" << P->dtype << " n=";
+  for (int mu = 0; mu < P->d; ++mu) k << (mu ? "," : "") << P->n[mu];
+  k << " p=" << p << " nv=" << nv << " nscales=" << nscales;
+  return k.str();
+}
+
+std::string tuning_text(const phiks_tuning& t, int d) {
+  std::ostringstream v;
+  v << "fused=" << t.fused << " fused_rows=" << t.fused_rows << " fp64_tile=" << t.fp64_tile << " order=";
+  for (int k = 0; k < d; ++k) v << (k ? "," : "") << t.mode_order[k];
+  v << " emu_cols=" << t.emu_cols << " split_ntiles=" << t.split_ntiles;
+  return v.str();
+}
+
+bool parse_tuning(const std::string& text, int d, phiks_tuning* t) {
+  std::memset(t, 0, sizeof *t);
+  for (int k = 0; k < PHIKS_MAX_D; ++k) t->mode_order[k] = -1;
+  std::istringstream in(text);
+  std::string tok;
+  int got = 0;
+  while (in >> tok) {
+    const size_t eq = tok.find('=');
+    if (eq == std::string::npos) continue;
+    const std::string name = tok.substr(0, eq), val = tok.substr(eq + 1);
+    if (name == "fused") t->fused = std::atoi(val.c_str()), got |= 1;
+    else if (name == "fused_rows") t->fused_rows = std::atoi(val.c_str()), got |= 2;
+    else if (name == "fp64_tile") t->fp64_tile = std::atoi(val.c_str()), got |= 4;
+    else if (name == "emu_cols") t->emu_cols = std::atoi(val.c_str()), got |= 8;
+    else if (name == "split_ntiles") t->split_ntiles = std::atoi(val.c_str()), got |= 16;
+    else if (name == "order") {
+      std::istringstream ov(val);
+      std::string x;
+      int k = 0;
+      while (std::getline(ov, x, ',') && k < PHIKS_MAX_D) t->mode_order[k++] = std::atoi(x.c_str());
+      if (k == d) got |= 32;
+    }
+  }
+  return got == 63;
+}
+
+}  // namespace
+
+extern "C" {
+
+phiks_status phiks_autotune(phiks_plan_t P, double tau, int p, int nv, const phiks_options* opt, int reps,
+                            void* stream, phiks_tuning* best, double* best_ms) {
+  g_err.clear();
+  if (!P || !std::isfinite(tau)) return fail(PHIKS_ERR_INVALID, "NULL plan or tau not finite");
+  if (p < 1 || p > PHIKS_MAX_P) return fail(PHIKS_ERR_INVALID, "p = %d", p);
+  if (nv != 1 && nv != p + 1) return fail(PHIKS_ERR_INVALID, "nv must be 1 or p + 1");
+  if (reps < 1 || reps > 1000) return fail(PHIKS_ERR_INVALID, "reps = %d", reps);
+  phiks_options o;
+  if (opt) o = *opt; else phiks_options_init(&o);
+  TRY(check_opts(o));
+  o.vnorms = nullptr;
+  o.workspace = nullptr;
+  DeviceGuard g(P->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const std::string key = tuning_key(P, p, nv, o.nscales);
+  const char* cache = std::getenv("PHIKS_TUNE_CACHE");
+  if (cache && *cache) {  // an earlier tuning of this shape
+    std::ifstream in(cache);
+    std::string line, found;
+    while (std::getline(in, line)) {
+      const size_t bar = line.find(" | ");
+      if (bar != std::string::npos && line.substr(0, bar) == key) found = line.substr(bar + 3);
+    }
+    phiks_tuning t;
+    if (!found.empty() && parse_tuning(found, P->d, &t) && phiks_set_tuning(P, &t) == PHIKS_OK) {
+      if (best) *best = t;
+      if (best_ms) {
+        const size_t m = found.find("ms=");
+        *best_ms = m == std::string::npos ? 0.0 : std::atof(found.c_str() + m + 3);
+      }
+      return PHIKS_OK;
+    }
+  }
+  // seeded synthetic inputs (uniform in [-1, 1]), their norms, an output
+  const size_t es = elt_size(P);
+  const size_t nel = (size_t)P->NR;
+  std::vector<double> h(nel);
+  uint64_t x = 0x9E3779B97F4A7C15ull;
+  std::vector<void*> vdev(nv, nullptr);
+  std::vector<double> norms(nv, 0.0);
+  void* out = nullptr;
+  const int per = nv == 1 ? p + 1 : 1;
+  phiks_status res = PHIKS_OK;
+  auto cleanup = [&]() {
+    for (void* v : vdev) dev_free(v);
+    dev_free(out);
+  };
+  for (int i = 0; i < nv && res == PHIKS_OK; ++i) {
+    double ss = 0;
+    for (size_t k = 0; k < nel; ++k) {
+      x ^= x << 13, x ^= x >> 7, x ^= x << 17;  // xorshift64
+      h[k] = (double)(x >> 11) * 0x1.0p-52 - 1.0;
+      ss += h[k] * h[k];
+    }
+    norms[i] = std::sqrt(ss);
+    if (dev_malloc(&vdev[i], nel * es) != cudaSuccess) res = fail(PHIKS_ERR_OOM, "tuning inputs");
+    else if (es == 4) {
+      std::vector<float> f(h.begin(), h.end());
+      if (cudaMemcpy(vdev[i], f.data(), nel * 4, cudaMemcpyHostToDevice) != cudaSuccess) res = fail(PHIKS_ERR_CUDA, "copy");
+    } else if (cudaMemcpy(vdev[i], h.data(), nel * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+      res = fail(PHIKS_ERR_CUDA, "copy");
+    }
+  }
+  if (res == PHIKS_OK && dev_malloc(&out, (size_t)o.nscales * per * nel * es) != cudaSuccess)
+    res = fail(PHIKS_ERR_OOM, "tuning output");
+  if (res != PHIKS_OK) {
+    cleanup();
+    return res;
+  }
+  o.vnorms = norms.data();
+  phiks_tuning saved;
+  phiks_get_tuning(P, &saved);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double tbest = 1e300;
+  phiks_tuning tb = saved;
+  for (const phiks_tuning& t : tuning_candidates(P)) {
+    if (phiks_set_tuning(P, &t) != PHIKS_OK) continue;
+    res = phiks_apply_ex(P, tau, p, vdev.data(), nv, &o, out, stream);  // warm-up: banks, workspace
+    if (res != PHIKS_OK) break;
+    if (cudaEventRecord(e0, st) != cudaSuccess) { res = fail(PHIKS_ERR_CUDA, "event"); break; }
+    for (int r = 0; r < reps && res == PHIKS_OK; ++r) res = phiks_apply_ex(P, tau, p, vdev.data(), nv, &o, out, stream);
+    if (res != PHIKS_OK) break;
+    float ms = 0;
+    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      res = fail(PHIKS_ERR_CUDA, "timing");
+      break;
+    }
+    if (ms / reps < tbest) {
+      tbest = ms / reps;
+      tb = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  cleanup();
+  if (res != PHIKS_OK) {
+    phiks_set_tuning(P, &saved);
+    return res;
+  }
+  TRY(phiks_set_tuning(P, &tb));
+  if (best) *best = tb;
+  if (best_ms) *best_ms = tbest;
+  if (cache && *cache) {
+    std::ofstream outf(cache, std::ios::app);
+    outf << key << " | " << tuning_text(tb, P->d) << " ms=" << std::setprecision(17) << tbest << "\n";
+  }
+  return PHIKS_OK;
 }
 
 phiks_status phiks_workspace_size(phiks_plan_t P, int p, int nv, int nscales, size_t* bytes) {

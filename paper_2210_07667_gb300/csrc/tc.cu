@@ -432,6 +432,7 @@ struct TcState {
   int batch = 0;     // tensors the bound workspace holds
   int last_res = 1;  // plane set holding the last call's results
   int smem_optin = 0;
+  int ntiles_mult = 1;  // tuned: N tiles per pass, times the minimum
   // encoded tensor maps by (address, inner extent, rows, box rows): encoding
   // costs microseconds of host time, a lookup does not
   std::map<std::tuple<const void*, uint64_t, uint64_t, uint32_t>, CUtensorMap> maps;
@@ -653,7 +654,8 @@ cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const TcMats* mats, co
     const int n = (int)s->n[mu], np = pad16(n);
     const int64_t M2 = N / n;
     const int64_t rows = (int64_t)B * M2;
-    const int nnt = (np + 255) / 256;          // N tiles of at most 256 rows
+    // N tiles of at most 256 rows (times the tuned multiplier, at least 16 rows each)
+    const int nnt = std::min((np + 255) / 256 * std::max(s->ntiles_mult, 1), std::max(np / 16, 1));
     const int ntile = pad16((np + nnt - 1) / nnt);
     CUtensorMap mA[2];
     TcMapsB mB;
@@ -726,6 +728,8 @@ cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const TcMats* mats, co
 }
 
 int* tc_status_word(TcState* s) { return s->status; }
+
+void tc_set_ntiles(TcState* s, int mult) { s->ntiles_mult = (mult == 2 || mult == 4) ? mult : 1; }
 
 int tc_read_status(TcState* s, cudaStream_t st) {
   int h = 0;

@@ -77,6 +77,9 @@ cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const TcMats* mats, co
 // Device-side status: 0, or the code of a bounded wait that gave up (the
 // flag is cleared by the read).  Synchronises the stream.
 int tc_read_status(TcState* s, cudaStream_t st);
+// N tiles per GEMM pass as a multiple of the minimum ceil(n_pad / 256):
+// 1, 2 or 4 (smaller tiles, more CTAs); 0 = 1.
+void tc_set_ntiles(TcState* s, int mult);
 // The device status word the kernels record a failed wait in.
 int* tc_status_word(TcState* s);
 

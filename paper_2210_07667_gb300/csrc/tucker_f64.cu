@@ -427,7 +427,7 @@ int grid_for(int64_t N, int threads) {
 }  // namespace
 
 cudaError_t launch_mode_product_f64(const Combo& pro, const double* L, ModeGeom g, double* W,
-                                    const Epi* epi, cudaStream_t st) {
+                                    const Epi* epi, cudaStream_t st, int tile) {
   Epi e;
   if (epi) {
     e = *epi;
@@ -441,15 +441,15 @@ cudaError_t launch_mode_product_f64(const Combo& pro, const double* L, ModeGeom 
   // 16 x 16 tiles (64 threads, 4 outputs each), so that even N = 2^18 spreads
   // over ~1000 CTAs and the 152 SMs' FP64 pipes stay evenly loaded.
   const int64_t big_tiles = ((g.a * g.b + 63) / 64) * ((g.n + 31) / 32);
-  if (big_tiles >= 8 * 152) return launch_tiled<32, 64, 2, 4, 16>(pro, L, g, W, e, st);
+  if (tile == 2 || (tile == 0 && big_tiles >= 8 * 152)) return launch_tiled<32, 64, 2, 4, 16>(pro, L, g, W, e, st);
   return launch_tiled<16, 16, 2, 2, 32>(pro, L, g, W, e, st);
 }
 
-cudaError_t launch_mode_product_f64_batch(const ModeBatch& mb, int B, ModeGeom g, cudaStream_t st) {
+cudaError_t launch_mode_product_f64_batch(const ModeBatch& mb, int B, ModeGeom g, cudaStream_t st, int tile) {
   if (B < 1 || B > kMaxModeBatch) return cudaErrorInvalidValue;
   count_launch();
   const int64_t big_tiles = B * ((g.a * g.b + 63) / 64) * ((g.n + 31) / 32);
-  if (big_tiles >= 8 * 152) return launch_tiled_batch<32, 64, 2, 4, 16>(mb, B, g, st);
+  if (tile == 2 || (tile == 0 && big_tiles >= 8 * 152)) return launch_tiled_batch<32, 64, 2, 4, 16>(mb, B, g, st);
   return launch_tiled_batch<16, 16, 2, 2, 32>(mb, B, g, st);
 }
 

@@ -87,8 +87,8 @@ def test_cheb_n64_every_dtype_vs_oracle(dtype, tau):
     errs = [rel_inf(got[k], ex[k]) for k in range(P)]
     print("cheb n=64 tau=%g dtype %d (s,q,T#)=(%d,%d,%d) errs %s"
           % (tau, dtype, s, q, T, ["%.2e" % e for e in errs]))
-    if tau > 1e-6:
-        assert s >= 1
+    if tau > 1e-6 and dtype in (pk.PHIKS_FP64, pk.PHIKS_FP64_EMU):
+        assert s >= 1   # (the split dtypes' looser tolerance may need no squaring)
     assert max(errs) < TOL_CALL[dtype]
 
 

@@ -100,18 +100,26 @@ def test_injected_allocation_failures(dtype):
     vs = [dev(wl.vs[0], tdt)]
     out = torch.empty(4 * wl.N, device="cuda", dtype=tdt)
     vn = [float(np.linalg.norm(wl.vs[0]))]
-    # the first apply allocates the workspace, the exponential scratch and a bank
-    for j in range(3):
+    # the first apply allocates the plan's workspace, a bank of exponentials,
+    # the exponential scratch (and for FP64_EMU the bank's B planes): let j
+    # of them pass and the next fail, j = 0, 1, ..., until the call goes
+    # through (what a failed call allocated before the failure either stays
+    # with the plan, the workspace and scratch, or is released, the bank)
+    fails = 0
+    for j in range(8):
         pk.phiks_debug_fail_alloc(j)
-        with pytest.raises(pk.PhiksError) as e:
+        try:
             plan.apply(wl.tau, 3, vs, out, vnorms=vn)
-        assert e.value.status == 2
-        torch.cuda.synchronize()
-        # whatever this call allocated before the failure stays with the plan
-        # (workspace, scratch) or was released (the bank)
-        assert pk.phiks_debug_live_allocations() <= held + j
+        except pk.PhiksError as e:
+            assert e.status == 2, str(e)
+            torch.cuda.synchronize()
+            assert pk.phiks_debug_live_allocations() <= held + 2
+            fails += 1
+            continue
+        pk.phiks_debug_fail_alloc(-1)
+        break
     pk.phiks_debug_fail_alloc(-1)
-    plan.apply(wl.tau, 3, vs, out, vnorms=vn)
+    assert fails >= 2
     torch.cuda.synchronize()
     got = out.cpu().numpy().reshape(4, wl.N)
     for i in range(4):
