@@ -15,7 +15,7 @@ uint64_t kernel_launch_count();
 int plan_dtype(const void* plan);
 void count_launch(uint64_t k = 1);
 
-constexpr int kMaxSrc = 10;  // tensors one combination may read
+constexpr int kMaxSrc = 12;  // tensors one combination may read (all nodes of q <= 12 and one more)
 constexpr int kMaxOut = 8;   // tensors one epilogue may write
 
 // Input of a mu-mode product as a linear combination of tensors:
@@ -74,9 +74,11 @@ inline void epi_finalize(Epi& e) {
 __device__ __forceinline__ void epi_apply(const Epi& e, int64_t idx, double res) {
   double sv[kMaxSrc];
   double o[kMaxOut];
-#pragma unroll 1
-  for (int m = 0; m < e.nsrc; ++m)
-    sv[m] = ((e.src_f32mask >> m) & 1) ? (double)((const float*)e.src[m])[idx] : e.src[m][idx];
+  // every source load issued before the first is used (static indices)
+#pragma unroll
+  for (int m = 0; m < kMaxSrc; ++m)
+    if (m < e.nsrc)
+      sv[m] = ((e.src_f32mask >> m) & 1) ? (double)((const float*)e.src[m])[idx] : e.src[m][idx];
 #pragma unroll 1
   for (int t = 0; t < e.nout; ++t) o[t] = ((e.bnz >> t) & 1) ? e.b[t] * res : 0.0;
 #pragma unroll 1
