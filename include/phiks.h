@@ -209,11 +209,11 @@ phiks_status phiks_expm(int batch, int n, const double* X, double* E, void* stre
 
 /* Kernel timing for measurement tools.  While enabled, every mu-mode product
  * the plan launches is bracketed by two CUDA events on its stream: the FP64
- * mode-product kernel, the tensor-core GEMM pass of FP64_EMU (its digit
- * split excluded), or the whole tensor-core Tucker operator of the split
- * dtypes.  phiks_profile_read synchronises the plan's device, returns the
- * summed milliseconds of those brackets, their count and their algorithmic
- * flops (2 N n_mu per mode), and resets the sums. */
+ * mode-product kernel (the fused small-slab kernel: one bracket for all d
+ * modes), or the tensor-core GEMM pass of FP64_EMU and of the split dtypes
+ * (their operand split excluded).  phiks_profile_read synchronises the plan's
+ * device, returns the summed milliseconds of those brackets, their count and
+ * their algorithmic flops (2 N n_mu per mode), and resets the sums. */
 phiks_status phiks_profile_enable(phiks_plan_t plan, int enable);
 phiks_status phiks_profile_read(phiks_plan_t plan, double* ms, int64_t* launches, double* flops);
 
@@ -304,6 +304,13 @@ typedef struct {
   int slots;              /* requests on the device at once (one stream each) */
   size_t hbm_budget;      /* workspace bytes in flight at most; 0 = no limit */
   int poll_us;            /* dispatcher pause when idle (0 = yield) */
+  int graphs;             /* nonzero: every slot owns a workspace and staging
+                             buffers (allocated once, sized for the largest
+                             request); a request's inputs are copied in, its
+                             applies replay CUDA graphs captured once per
+                             (plan, tau, p, slot), its outputs are copied out.
+                             0: a workspace per request from the pool and
+                             direct kernel launches */
 } phiks_serve_config;
 
 /* Run the trace in real time on the current device: request k becomes
@@ -373,7 +380,7 @@ phiks_status phiks_integrate(phiks_plan_t plan, const int64_t* n, int d, int sch
  * autotuner chooses among (0 = the library's size-based default for each
  * knob).  Results of every setting agree to rounding: the modes of a Tucker
  * operator commute, and the tiles only regroup the same sums.
- *   fused         real FP64 plans: -1 by size (N <= 65536), 0 mode-by-mode
+ *   fused         real FP64 plans: -1 by size (N <= 8192), 0 mode-by-mode
  *                 passes, 1 the fused small-slab kernel (all d modes of a
  *                 Tucker operator, and the batch's input combinations, in one
  *                 launch with the intermediates in shared memory; only when

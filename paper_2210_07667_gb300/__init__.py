@@ -112,7 +112,8 @@ class Request(ctypes.Structure):
 
 
 class ServeConfig(ctypes.Structure):
-    _fields_ = [("slots", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("poll_us", ctypes.c_int)]
+    _fields_ = [("slots", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("poll_us", ctypes.c_int),
+                ("graphs", ctypes.c_int)]
 
 
 class Nonlinear(ctypes.Structure):
@@ -422,7 +423,7 @@ class Batch:
             self.handle = None
 
 
-def phiks_serve_trace(requests, arrivals, slots=8, hbm_budget=0, poll_us=0):
+def phiks_serve_trace(requests, arrivals, slots=8, hbm_budget=0, poll_us=0, graphs=1):
     """requests: list of lists of applies, each apply a dict with keys plan
     (handle), tau, p, v (list of tensors), out, vnorms, and optionally
     nscales, skip_phi0, tol.  Returns (latency_ms, queue_ms, makespan_s)."""
@@ -444,7 +445,7 @@ def phiks_serve_trace(requests, arrivals, slots=8, hbm_budget=0, poll_us=0):
     lat = (ctypes.c_double * n)()
     qd = (ctypes.c_double * n)()
     mk = ctypes.c_double()
-    cfg = ServeConfig(int(slots), int(hbm_budget), int(poll_us))
+    cfg = ServeConfig(int(slots), int(hbm_budget), int(poll_us), int(graphs))
     _check(load().phiks_serve_trace(ctypes.byref(cfg), n, arr, at, lat, qd, ctypes.byref(mk)))
     return list(lat), list(qd), mk.value
 

@@ -74,11 +74,9 @@ inline void epi_finalize(Epi& e) {
 __device__ __forceinline__ void epi_apply(const Epi& e, int64_t idx, double res) {
   double sv[kMaxSrc];
   double o[kMaxOut];
-  // every source load issued before the first is used (static indices)
-#pragma unroll
-  for (int m = 0; m < kMaxSrc; ++m)
-    if (m < e.nsrc)
-      sv[m] = ((e.src_f32mask >> m) & 1) ? (double)((const float*)e.src[m])[idx] : e.src[m][idx];
+#pragma unroll 1
+  for (int m = 0; m < e.nsrc; ++m)
+    sv[m] = ((e.src_f32mask >> m) & 1) ? (double)((const float*)e.src[m])[idx] : e.src[m][idx];
 #pragma unroll 1
   for (int t = 0; t < e.nout; ++t) o[t] = ((e.bnz >> t) & 1) ? e.b[t] * res : 0.0;
 #pragma unroll 1

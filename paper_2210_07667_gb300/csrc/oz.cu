@@ -258,7 +258,8 @@ struct OzParams {
   int nbuf;       // TMEM accumulator sets (1 or 2)
   double* out;    // FP64 result of tensor b, rotated layout: out[b N + m + M2 i]
   const int* xscale;
-  int mixed;      // tensors with their own matrices (every tile within one tensor)
+  int mixed;      // tensors with their own matrices: every tile within one tensor
+  int64_t tpt;    // mixed: row tiles per tensor, ceil(M2 / 128) (the last one partial)
   const int* lscale[kOzMaxBatch];  // row exponents of tensor b's matrix (entry 0 unless mixed)
   int* status;
 };
@@ -267,6 +268,21 @@ struct OzParams {
 struct OzMaps {
   CUtensorMap b[kOzMaxBatch];
 };
+
+// First fibre (row of the batch) of row tile rt, and its tensor.  Mixed
+// batches tile every tensor on its own (a tensor's last tile may be partial:
+// its rows past the tensor read the next tensor's fibres, or the copy's zero
+// fill past the batch, and are not stored), so that a tile never needs two
+// matrices; otherwise the rows of all tensors are tiled together.
+__device__ __forceinline__ int64_t oz_tile_row0(const OzParams& P, int64_t rt, int* b) {
+  if (P.mixed) {
+    const int64_t bb = rt / P.tpt;
+    *b = (int)bb;
+    return bb * P.M2 + (rt - bb * P.tpt) * BM;
+  }
+  *b = 0;
+  return rt * BM;
+}
 
 constexpr int kOzEpiWarps = 16;
 constexpr int NTH = 64 + 32 * kOzEpiWarps;
@@ -333,9 +349,10 @@ __global__ void __launch_bounds__(NTH, 1)
       uint32_t ph = 0;
       int issued = 0;
       for (int t = blockIdx.x; t < P.num_tiles; t += gridDim.x) {
-        const int m0 = (t / P.n_ntiles) * BM;
+        int tb = 0;
+        const int m0 = (int)oz_tile_row0(P, t / P.n_ntiles, &tb);
         const int r0 = (t % P.n_ntiles) * NT;
-        const CUtensorMap* mapB = &mapsB.b[P.mixed ? (int)(m0 / P.M2) : 0];
+        const CUtensorMap* mapB = &mapsB.b[tb];
         bool ok = true;
         for (int kc = 0; kc < P.nk; ++kc) {
           if (!mbar_wait(empty, ph ^ 1, P.status, 11)) {
@@ -423,14 +440,16 @@ __global__ void __launch_bounds__(NTH, 1)
     for (int t = blockIdx.x; t < P.num_tiles; t += gridDim.x) {
       if (!mbar_wait(&tfull[buf], aph, P.status, 14)) break;
       tc_fence_after();
-      const int64_t rg = (int64_t)(t / P.n_ntiles) * BM + row;  // fibre of the batch
+      int tb = 0;
+      const int64_t m0t = oz_tile_row0(P, t / P.n_ntiles, &tb);
+      const int64_t rg = m0t + row;  // fibre of the batch
       const int r0 = (t % P.n_ntiles) * NT;
-      const bool valid = rg < P.rows;
+      const bool valid = P.mixed ? (rg - (int64_t)tb * P.M2 < P.M2) : (rg < P.rows);
       const int sx = valid ? P.xscale[rg] : 0;
-      const int64_t bt = valid ? rg / P.M2 : 0;
+      const int64_t bt = valid ? (P.mixed ? tb : rg / P.M2) : 0;
       double* const outb = P.out + bt * P.N;
       const int64_t m = rg - bt * P.M2;
-      const int* const lscale = P.lscale[P.mixed ? bt : 0];
+      const int* const lscale = P.lscale[P.mixed ? tb : 0];
 #pragma unroll 1
       for (int c0 = grp * CW; c0 < (grp + 1) * CW; c0 += CH) {
         const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * SET + (uint32_t)c0;
@@ -654,8 +673,7 @@ bool cached(OzState* s, CUtensorMap* m, const void* base, uint64_t inner, uint64
 }  // namespace
 
 bool oz_mixed_ok(const OzState* s) {
-  for (int mu = 0; mu < s->d; ++mu)
-    if ((s->N / s->n[mu]) % BM != 0) return false;
+  (void)s;  // every shape: mixed batches tile each tensor on its own
   return true;
 }
 
@@ -725,7 +743,8 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, co
     P.N = N;
     P.nk = (n + 63) / 64;
     P.n_ntiles = (n + NT - 1) / NT;
-    P.num_tiles = (int)((rows + BM - 1) / BM) * P.n_ntiles;
+    P.tpt = (M2 + BM - 1) / BM;
+    P.num_tiles = (int)((mixed ? B * P.tpt : (rows + BM - 1) / BM) * P.n_ntiles);
     P.nbuf = (2 * kOzSlices * NT <= 512) ? 2 : 1;
     int cols = 32;
     while (cols < P.nbuf * kOzSlices * NT) cols <<= 1;

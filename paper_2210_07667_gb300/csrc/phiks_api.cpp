@@ -943,8 +943,12 @@ phiks_status prof_end(Ctx& c, cudaEvent_t e1, double flops) {
   return PHIKS_OK;
 }
 
-// Fused kernel for B Tucker operators of this plan (real FP64 only).
-constexpr int64_t kFusedAutoN = 65536;
+// Fused kernel for B Tucker operators of this plan (real FP64 only).  By
+// size only for inputs small enough to stage whole in shared memory (there a
+// combined input is formed once per cluster); larger ones re-form a combined
+// input in every CTA of a tensor on the FP64 pipe, so they stay mode by mode
+// unless tuned otherwise.
+constexpr int64_t kFusedAutoN = 8192;
 bool use_fused(const phiks_plan_s* P) {
   if (P->dtype != PHIKS_FP64 || P->cplx || !P->fused_ok) return false;
   return P->fused_mode == 1 || (P->fused_mode < 0 && P->N <= kFusedAutoN);
@@ -984,17 +988,18 @@ phiks_status tucker(Ctx& c, const Combo& in, const Mats& M, const Epi* epi) {
     c.tuckers++;
     return PHIKS_OK;
   }
-  if (tc_path(P)) {
-    cudaEvent_t e1;
-    TRY(prof_begin(c, &e1));
+  if (tc_path(P)) {  // events around every GEMM pass
+    cudaEvent_t ev[2 * PHIKS_MAX_D];
+    const bool prof = P->prof;
+    if (prof)
+      for (int mu = 0; mu < P->d; ++mu) TRY(prof_pair(P, &ev[2 * mu], &ev[2 * mu + 1]));
     TcMats tm;
     for (int mu = 0; mu < P->d; ++mu) tm.B[mu] = M.B[mu];
-    cudaError_t e = tc_tucker(P->tc, 1, &in, &tm, epi, c.st);
+    cudaError_t e = tc_tucker(P->tc, 1, &in, &tm, epi, c.st, nullptr, nullptr, prof ? ev : nullptr);
     if (e != cudaSuccess)
       return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), tc_last_error());
-    double fl = 0;
-    for (int mu = 0; mu < P->d; ++mu) fl += 2.0 * (double)P->N * (double)P->n[mu];
-    TRY(prof_end(c, e1, fl));
+    if (prof)
+      for (int mu = 0; mu < P->d; ++mu) P->prof_flops += 2.0 * (double)P->N * (double)P->n[mu];
     c.tuckers++;
     return PHIKS_OK;
   }
@@ -1059,14 +1064,15 @@ phiks_status tucker_batch(Ctx& c, int B, const Combo* in, const Mats& M, const E
         for (int mu = 0; mu < P->d; ++mu) om[b].B[mu] = M.B[mu];
       e = oz_tucker(P->oz, nb, in + b0, om, epi + b0, c.st, prof ? ev : nullptr);
       if (prof) P->prof_flops += nb * fl;
-    } else {  // events around the whole batch
-      cudaEvent_t e1;
-      TRY(prof_begin(c, &e1));
+    } else {  // events around every GEMM pass
+      cudaEvent_t ev[2 * PHIKS_MAX_D];
+      if (prof)
+        for (int mu = 0; mu < P->d; ++mu) TRY(prof_pair(P, &ev[2 * mu], &ev[2 * mu + 1]));
       TcMats tm[kTcMaxBatch];
       for (int b = 0; b < nb; ++b)
         for (int mu = 0; mu < P->d; ++mu) tm[b].B[mu] = M.B[mu];
-      e = tc_tucker(P->tc, nb, in + b0, tm, epi + b0, c.st);
-      if (e == cudaSuccess) TRY(prof_end(c, e1, nb * fl));
+      e = tc_tucker(P->tc, nb, in + b0, tm, epi + b0, c.st, nullptr, nullptr, prof ? ev : nullptr);
+      if (e == cudaSuccess && prof) P->prof_flops += nb * fl;
     }
     if (e != cudaSuccess)
       return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e),
@@ -1251,17 +1257,17 @@ phiks_status tucker_mixed(Ctx& c, int B, const Combo* in, const Mats* M, const v
         tp.side_out[k] = pro->side_out[k];
       }
     }
-    double fl = 0;
-    for (int mu = 0; mu < P->d; ++mu) fl += 2.0 * B * (double)P->N * (double)P->n[mu];
-    cudaEvent_t e1;
-    TRY(prof_begin(c, &e1));
+    cudaEvent_t ev[2 * PHIKS_MAX_D];
+    if (prof)
+      for (int mu = 0; mu < P->d; ++mu) TRY(prof_pair(P, &ev[2 * mu], &ev[2 * mu + 1]));
     const float* R = nullptr;
-    e = tc_tucker(P->tc, B, in, tm, nullptr, c.st, &R, pro ? &tp : nullptr);
+    e = tc_tucker(P->tc, B, in, tm, nullptr, c.st, &R, pro ? &tp : nullptr, prof ? ev : nullptr);
     *res = R;
     *r32 = true;
     if (e != cudaSuccess)
       return fail(PHIKS_ERR_CUDA, "tensor-core Tucker: %s %s", cudaGetErrorString(e), tc_last_error());
-    TRY(prof_end(c, e1, fl));
+    if (prof)
+      for (int mu = 0; mu < P->d; ++mu) P->prof_flops += 2.0 * B * (double)P->N * (double)P->n[mu];
   }
   c.tuckers += B;
   return PHIKS_OK;

@@ -7,10 +7,18 @@
 // time has passed into a FIFO queue, hands the queue head to a free slot when
 // the workspace bytes in flight stay within the budget (a request that alone
 // exceeds the budget runs when nothing else is in flight), and retires slots
-// whose work has finished.  Each request's workspace comes from a memory pool
-// owned by this call (stream-ordered cudaMallocAsync / cudaFreeAsync, so no
-// device-wide synchronisation); completion times are stamped by a host
-// function enqueued behind the request's kernels.
+// whose work has finished.  Completion times are stamped by a host function
+// enqueued behind the request's kernels.
+//
+// Submission (cfg->graphs): the dispatcher is one host thread, and a request
+// is hundreds of short kernels, so issuing them one by one would make the
+// host the bound.  Each slot therefore owns a workspace, input staging
+// vectors and an output staging buffer (from a memory pool of this call,
+// allocated once); a request's inputs are copied into the slot's staging
+// vectors, its applies replay CUDA graphs captured once per (plan, tau, p,
+// slot) (phiks_options.graph: the graph key holds only slot-owned pointers),
+// and the outputs are copied to the request's buffers.  Without graphs each
+// request takes a workspace from the pool and launches its kernels directly.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -47,7 +55,25 @@ struct Slot {
   int req = -1;
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  // graph submission: slot-owned buffers
+  void* ws_fixed = nullptr;
+  void* stage_v[PHIKS_MAX_P + 1] = {nullptr};
+  void* stage_out = nullptr;
 };
+
+// Bytes of one vector and of the output of one apply.
+void apply_bytes(const phiks_apply_args& x, size_t* vec, size_t* out) {
+  int d = 0;
+  int64_t n[PHIKS_MAX_D];
+  phiks_plan_shape(x.plan, &d, n);
+  int64_t N = 1;
+  for (int mu = 0; mu < d; ++mu) N *= n[mu];
+  const int dt = phiks::plan_dtype(x.plan);
+  const size_t elt = dt == PHIKS_C128 ? 16 : (dt == PHIKS_FP64 || dt == PHIKS_FP64_EMU) ? 8 : 4;
+  *vec = (size_t)N * elt;
+  const int per = x.nv == 1 ? x.p + 1 - (x.skip_phi0 ? 1 : 0) : 1;
+  *out = (size_t)std::max(1, x.nscales) * per * N * elt;
+}
 
 phiks_status sfail(phiks_status st, const std::string& m) {
   phiks::set_error_message(("phiks_serve_trace: " + m).c_str());
@@ -109,6 +135,35 @@ extern "C" phiks_status phiks_serve_trace(const phiks_serve_config* cfg, int cou
       result = PHIKS_ERR_CUDA;
       msg = "stream creation";
     }
+  const bool graphs = cfg->graphs != 0;
+  if (graphs && result == PHIKS_OK) {
+    // every slot's buffers, sized for the largest request
+    size_t ws_max = 0, vec_max = 0, out_max = 0;
+    int nv_max = 1;
+    for (int k = 0; k < count; ++k) {
+      ws_max = std::max(ws_max, need[k]);
+      for (int a = 0; a < reqs[k].napply; ++a) {
+        size_t vb = 0, ob = 0;
+        apply_bytes(reqs[k].apply[a], &vb, &ob);
+        vec_max = std::max(vec_max, vb);
+        out_max = std::max(out_max, ob);
+        nv_max = std::max(nv_max, reqs[k].apply[a].nv);
+      }
+    }
+    for (auto& s : slots) {
+      bool ok = cudaMallocFromPoolAsync(&s.ws_fixed, ws_max, pool, s.st) == cudaSuccess &&
+                cudaMallocFromPoolAsync(&s.stage_out, out_max, pool, s.st) == cudaSuccess;
+      for (int l = 0; l < nv_max && ok; ++l)
+        ok = cudaMallocFromPoolAsync(&s.stage_v[l], vec_max, pool, s.st) == cudaSuccess;
+      if (!ok) {
+        result = PHIKS_ERR_OOM;
+        msg = "slot buffers";
+        break;
+      }
+      s.ws_bytes = 0;
+    }
+    for (auto& s : slots) cudaStreamSynchronize(s.st);  // (before the clock starts)
+  }
 
   std::vector<Done> done(count);
   std::vector<double> t_dispatch(count, 0.0);
@@ -143,7 +198,7 @@ extern "C" phiks_status phiks_serve_trace(const phiks_serve_config* cfg, int cou
       if (budget && inflight > 0 && inflight_bytes + need[k] > budget) break;
       queue.pop_front();
       Slot& s = *free_slot;
-      if (cudaMallocFromPoolAsync(&s.ws, need[k], pool, s.st) != cudaSuccess) {
+      if (!graphs && cudaMallocFromPoolAsync(&s.ws, need[k], pool, s.st) != cudaSuccess) {
         result = PHIKS_ERR_OOM;
         msg = "workspace allocation for request " + std::to_string(k);
         break;
@@ -161,12 +216,32 @@ extern "C" phiks_status phiks_serve_trace(const phiks_serve_config* cfg, int cou
         o.skip_phi0 = x.skip_phi0;
         if (x.tol > 0) o.tol = x.tol;
         o.vnorms = x.vnorms;
-        o.workspace = s.ws;
-        o.workspace_bytes = need[k];
-        phiks_status r = phiks_apply_ex(x.plan, x.tau, x.p, x.v, x.nv, &o, x.out, s.st);
-        if (r != PHIKS_OK) {
+        phiks_status r;
+        if (graphs) {
+          size_t vb = 0, ob = 0;
+          apply_bytes(x, &vb, &ob);
+          const void* sv[PHIKS_MAX_P + 1];
+          for (int l = 0; l < x.nv; ++l) {
+            sv[l] = x.v[l] ? s.stage_v[l] : nullptr;
+            if (x.v[l] && cudaMemcpyAsync(s.stage_v[l], x.v[l], vb, cudaMemcpyDeviceToDevice, s.st) != cudaSuccess)
+              result = PHIKS_ERR_CUDA;
+          }
+          o.workspace = s.ws_fixed;
+          o.workspace_bytes = need[k];
+          o.graph = 1;
+          r = phiks_apply_ex(x.plan, x.tau, x.p, sv, x.nv, &o, s.stage_out, s.st);
+          if (r == PHIKS_OK && cudaMemcpyAsync(x.out, s.stage_out, ob, cudaMemcpyDeviceToDevice, s.st) != cudaSuccess)
+            r = PHIKS_ERR_CUDA;
+        } else {
+          o.workspace = s.ws;
+          o.workspace_bytes = need[k];
+          r = phiks_apply_ex(x.plan, x.tau, x.p, x.v, x.nv, &o, x.out, s.st);
+        }
+        if (r != PHIKS_OK && result == PHIKS_OK) {
           result = r;
           msg = "request " + std::to_string(k) + ": " + phiks_last_error();
+        } else if (result != PHIKS_OK && msg.empty()) {
+          msg = "request " + std::to_string(k) + ": staging copy";
         }
       }
       if (result != PHIKS_OK) break;
@@ -187,6 +262,10 @@ extern "C" phiks_status phiks_serve_trace(const phiks_serve_config* cfg, int cou
     if (!s.st) continue;
     cudaStreamSynchronize(s.st);
     if (s.ws) cudaFreeAsync(s.ws, s.st);
+    if (s.ws_fixed) cudaFreeAsync(s.ws_fixed, s.st);
+    if (s.stage_out) cudaFreeAsync(s.stage_out, s.st);
+    for (void* v : s.stage_v)
+      if (v) cudaFreeAsync(v, s.st);
     cudaStreamSynchronize(s.st);
     cudaStreamDestroy(s.st);
   }

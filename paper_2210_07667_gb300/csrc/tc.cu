@@ -94,7 +94,8 @@ struct GemmParams {
   int stages;
   int tmem_cols;
   int last;       // 0: write planes for the next pass; 1: write FP32 results to out0
-  int mixed;      // tensors with their own matrices (every tile within one tensor)
+  int mixed;      // tensors with their own matrices: every tile within one tensor
+  int64_t tpt;    // mixed: row tiles per tensor, ceil(M2 / 128) (the last one partial)
   void* out0;
   void* out1;
   int* status;
@@ -104,6 +105,19 @@ struct GemmParams {
 struct TcMapsB {
   CUtensorMap b[kTcMaxBatch][2];
 };
+
+// First fibre (row of the batch) of row tile rt, and its tensor: mixed
+// batches tile every tensor on its own (rows of a partial last tile past the
+// tensor are computed from whatever the copy brings and not stored).
+__device__ __forceinline__ int64_t tc_tile_row0(const GemmParams& P, int64_t rt, int* b) {
+  if (P.mixed) {
+    const int64_t bb = rt / P.tpt;
+    *b = (int)bb;
+    return bb * P.M2 + (rt - bb * P.tpt) * BM;
+  }
+  *b = 0;
+  return rt * BM;
+}
 
 template <int KIND, int NP>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -158,9 +172,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t ph = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < P.num_tiles && ok; t += gridDim.x) {
-        const int m0 = (t / P.n_ntiles) * BM;
+        int mi = 0;
+        const int m0 = (int)tc_tile_row0(P, t / P.n_ntiles, &mi);
         const int r0 = (t % P.n_ntiles) * P.ntile;
-        const int mi = P.mixed ? (int)(m0 / P.M2) : 0;
         const CUtensorMap* mapB0 = &mapsB.b[mi][0];
         const CUtensorMap* mapB1 = &mapsB.b[mi][1];
         for (int kc = 0; kc < P.nk && ok; ++kc) {
@@ -257,10 +271,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int t = blockIdx.x; t < P.num_tiles; t += gridDim.x) {
       if (!mbar_wait(&tfull[buf], aph, P.status, 4)) break;
       tc_fence_after();
-      const int64_t colb = (int64_t)(t / P.n_ntiles) * BM + row;  // fibre of the batch
+      int tb = 0;
+      const int64_t colb = tc_tile_row0(P, t / P.n_ntiles, &tb) + row;  // fibre of the batch
       const int r0 = (t % P.n_ntiles) * P.ntile;
-      const bool valid = colb < P.rows;
-      const int64_t bt = valid ? colb / P.M2 : 0;
+      const bool valid = P.mixed ? (colb - (int64_t)tb * P.M2 < P.M2) : (colb < P.rows);
+      const int64_t bt = valid ? (P.mixed ? tb : colb / P.M2) : 0;
       const int64_t col = colb - bt * P.M2 + bt * P.N;  // tensor b's elements start at b N
       const int cend = P.n - r0 < P.ntile ? P.n - r0 : P.ntile;
       for (int c0 = 16 * grp; c0 < cend; c0 += 16 * GROUPS) {
@@ -464,8 +479,7 @@ size_t tc_workspace_bytes(int64_t N, int batch) {
 }
 
 bool tc_mixed_ok(const TcState* s) {
-  for (int mu = 0; mu < s->d; ++mu)
-    if ((s->N / s->n[mu]) % BM != 0) return false;
+  (void)s;  // every shape: mixed batches tile each tensor on its own
   return true;
 }
 
@@ -608,7 +622,7 @@ cudaError_t run_gemm(TcState* s, const CUtensorMap* mA, const TcMapsB& mB, GemmP
 }  // namespace
 
 cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const TcMats* mats, const Epi* epi,
-                      cudaStream_t st, const float** res, const TcPrologue* pro) {
+                      cudaStream_t st, const float** res, const TcPrologue* pro, const cudaEvent_t* ev) {
   if (B < 1 || B > s->batch || s->batch > kTcMaxBatch) return cudaErrorInvalidValue;
   if (pro && (pro->nside < 0 || pro->nside > kTcMaxSide)) return cudaErrorInvalidValue;
   bool mixed = false;
@@ -688,7 +702,8 @@ cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const TcMats* mats, co
     P.rows = rows;
     P.N = N;
     P.nk = (n * elt + 127) / 128;
-    P.num_tiles = (int)((rows + BM - 1) / BM) * nnt;
+    P.tpt = (M2 + BM - 1) / BM;
+    P.num_tiles = (int)((mixed ? B * P.tpt : (rows + BM - 1) / BM) * nnt);
     int cols = 32;
     while (cols < 2 * ntile) cols <<= 1;
     P.tmem_cols = cols;
@@ -698,10 +713,12 @@ cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const TcMats* mats, co
     P.out1 = set[1 - cur][1];
     P.status = s->status;
     cudaError_t e;
+    if (ev && (e = cudaEventRecord(ev[2 * mu], st)) != cudaSuccess) return e;
     if (dtype == PHIKS_BF16X3) e = run_gemm<0, 2>(s, mA, mB, P, st);
     else if (dtype == PHIKS_TF32X3) e = run_gemm<1, 2>(s, mA, mB, P, st);
     else e = run_gemm<1, 1>(s, mA, mB, P, st);
     if (e != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[2 * mu + 1], st)) != cudaSuccess) return e;
     cur = 1 - cur;
   }
   s->last_res = cur;

@@ -70,9 +70,12 @@ struct TcPrologue {
 // double or float as its masks say).  Every pass treats the B tensors as one
 // tensor with B times the fibres.  With epi == nullptr no epilogue runs and
 // *res receives the B results as float (tensor b at *res + b N, valid until
-// the next call).  `pro` (or null) extends the split pass.
+// the next call).  `pro` (or null) extends the split pass.  `ev` (2 d
+// events, or null): ev[2 mu] and ev[2 mu + 1] are recorded around the GEMM
+// pass of mode mu.
 cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const TcMats* mats, const Epi* epi,
-                      cudaStream_t st, const float** res = nullptr, const TcPrologue* pro = nullptr);
+                      cudaStream_t st, const float** res = nullptr, const TcPrologue* pro = nullptr,
+                      const cudaEvent_t* ev = nullptr);
 
 // Device-side status: 0, or the code of a bounded wait that gave up (the
 // flag is cleared by the read).  Synchronises the stream.

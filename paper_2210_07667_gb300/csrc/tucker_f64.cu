@@ -362,16 +362,13 @@ __global__ void lincomb1_kernel(Lin1Batch lb, int64_t N2) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N2;
        i += (int64_t)gridDim.x * blockDim.x) {
     double ox = 0.0, oy = 0.0;
-    double2 x[kMaxSrc];  // every load issued before the first multiply-add
-#pragma unroll
-    for (int k = 0; k < kMaxSrc; ++k)
-      if (k < L.nterm) x[k] = __ldg(reinterpret_cast<const double2*>(L.src[k]) + i);
-#pragma unroll
-    for (int k = 0; k < kMaxSrc; ++k)
-      if (k < L.nterm) {
-        ox = fma(L.c[k], x[k].x, ox);
-        oy = fma(L.c[k], x[k].y, oy);
-      }
+    // unrolled by four: four independent loads in flight ahead of their FMAs
+#pragma unroll 4
+    for (int k = 0; k < L.nterm; ++k) {
+      const double2 x = __ldg(reinterpret_cast<const double2*>(L.src[k]) + i);
+      ox = fma(L.c[k], x.x, ox);
+      oy = fma(L.c[k], x.y, oy);
+    }
     reinterpret_cast<double2*>(L.out)[i] = make_double2(ox, oy);
   }
 }

@@ -209,3 +209,25 @@ def test_tucker_emulated_twelve_decades_within_fibres():
           % (ratio, rel, elem_rel))
     assert ratio <= 1.0
     assert rel < 1e-14
+
+
+@pytest.mark.parametrize("dims", [(56, 40, 24), (96, 120), (8, 8, 8, 8)])
+def test_mixed_batches_with_ragged_fibre_counts(dims):
+    """Batches that mix matrices (all quadrature nodes together, a squaring
+    level with the output operators) on shapes whose fibre counts N / n_mu
+    are not multiples of 128: every tensor is tiled on its own, its last tile
+    partial.  Against the oracle's Taylor action at 1e-12."""
+    alpha = (4.0, -6.0, 2.0, 1.0)[: len(dims)]
+    A = [wk.fd_adr_dirichlet(m, 1.0, a, 0.5) for m, a in zip(dims, alpha)]
+    N = int(np.prod(dims))
+    assert any((N // m) % 128 for m in dims) or len(dims) == 4
+    vs = [wk.normal(90 + l, N) for l in range(4)]
+    wl = wk.Workload("t", A, 3e-4, 3, "lincomb", 2, vs)
+    out, plan = run_workload(wl, dtype=EMU)
+    pk.phiks_device_status(plan.handle)
+    s, q, _, tk = plan.last_params()
+    for L in range(2):
+        ex = ta.lincomb(A, 3e-4, vs, 2.0 ** -L)
+        assert rel_inf(out[L], ex) < 1e-12, L
+    assert s >= 1
+    plan.close()

@@ -23,14 +23,15 @@ def _cuda():
     pk.load(build_if_missing=True)
 
 
+@pytest.mark.parametrize("graphs", [1, 0])
 @pytest.mark.parametrize("dtype", ["fp64", "bf16x3"])
-def test_served_results_equal_alone_and_in_the_mix(dtype):
+def test_served_results_equal_alone_and_in_the_mix(dtype, graphs):
     arrivals, specs = wk.served_trace(24, 20000.0, size_cap=160, classes=("ac", "adr", "bru"))
     specs = [(c, min(n, 48) if c == "adr" else n, p) for c, n, p in specs]
     tol = bench.PRECISION_TOL[dtype]
     reqs, plans, n_app = bench.build_served(pk, torch, arrivals, specs, dtype, tol)
     bench.warm_served(pk, torch, reqs)
-    lat, qd, mk = pk.phiks_serve_trace(reqs, arrivals, slots=6, hbm_budget=1 << 30)
+    lat, qd, mk = pk.phiks_serve_trace(reqs, arrivals, slots=6, hbm_budget=1 << 30, graphs=graphs)
     assert len(lat) == len(reqs) and all(l > 0 for l in lat) and mk > 0
     mixed = [[x["out"].clone() for x in apps] for apps in reqs]
     for apps in reqs:                      # each request alone, one after another

@@ -187,3 +187,24 @@ def test_same_vector_split_no_squaring(dtype):
     ref = phiks_ref.same(A, 1e-4, v, 3, 0, 10, nscales=1)[1:]
     errs = [rel_inf(out[k], ref[k]) for k in range(out.shape[0])]
     assert max(errs) < 4 * TOL[dtype], errs
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dims", [(56, 40, 24), (96, 200)])
+def test_mixed_batches_with_ragged_fibre_counts(dtype, dims):
+    """Node batches with each node's matrices on shapes whose fibre counts
+    N / n_mu are not multiples of 128 (each tensor tiled on its own) against
+    the oracle's step-by-step phiks at the same (s, q)."""
+    alpha = (4.0, -6.0, 2.0)[: len(dims)]
+    A = [wk.fd_adr_dirichlet(m, 1.0, a, 0.3) for m, a in zip(dims, alpha)]
+    N = int(np.prod(dims))
+    v = wk.normal(77, N).astype(np.float32).astype(np.float64)
+    wl = wk.Workload("t", A, 2e-4, 3, "same", 2, [v], skip_phi0=True)
+    out, plan = run_workload(wl, dtype=dtype)
+    pk.phiks_device_status(plan.handle)
+    s, q, _, _ = plan.last_params()
+    ref = phiks_ref.same(A, 2e-4, v, 3, s, q, nscales=2, skip_phi0=True)
+    errs = [rel_inf(out[k], ref[k]) for k in range(out.shape[0])]
+    print("mixed ragged %s dtype %d (s,q)=(%d,%d) errs %s" % (dims, dtype, s, q, ["%.2e" % e for e in errs]))
+    assert max(errs) < 4 * TOL[dtype]
+    plan.close()
