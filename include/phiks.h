@@ -392,7 +392,8 @@ phiks_status phiks_integrate(phiks_plan_t plan, const int64_t* n, int d, int sch
  *                 (entries past d are ignored; phiks_get_tuning sets them -1)
  *   emu_cols      FP64_EMU GEMM pass: rows of L per tile, 16 or 32
  *   split_ntiles  split dtypes: GEMM column tiles per pass as a multiple of
- *                 ceil(n_pad / 256): 1, 2 or 4 */
+ *                 ceil(n_pad / 256): 1, 2 or 4 (0: by size, narrower tiles
+ *                 when a pass has fewer row tiles than SMs) */
 typedef struct {
   int fused;
   int fused_rows;

@@ -447,7 +447,7 @@ struct TcState {
   int batch = 0;     // tensors the bound workspace holds
   int last_res = 1;  // plane set holding the last call's results
   int smem_optin = 0;
-  int ntiles_mult = 1;  // tuned: N tiles per pass, times the minimum
+  int ntiles_mult = 0;  // tuned: N tiles per pass, times the minimum (0: by size)
   // encoded tensor maps by (address, inner extent, rows, box rows): encoding
   // costs microseconds of host time, a lookup does not
   std::map<std::tuple<const void*, uint64_t, uint64_t, uint32_t>, CUtensorMap> maps;
@@ -668,8 +668,15 @@ cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const TcMats* mats, co
     const int n = (int)s->n[mu], np = pad16(n);
     const int64_t M2 = N / n;
     const int64_t rows = (int64_t)B * M2;
-    // N tiles of at most 256 rows (times the tuned multiplier, at least 16 rows each)
-    const int nnt = std::min((np + 255) / 256 * std::max(s->ntiles_mult, 1), std::max(np / 16, 1));
+    // N tiles of at most 256 rows of L.  Tuned: the minimum count times the
+    // multiplier (tiles of at least 16 rows).  By size: when the row tiles
+    // alone would leave SMs idle (few fibres, large n_mu), more and narrower
+    // N tiles (at least 64 rows each) until the pass has about one tile per SM.
+    const int64_t row_tiles = mixed ? (int64_t)B * ((M2 + BM - 1) / BM) : (rows + BM - 1) / BM;
+    int mult = std::max(s->ntiles_mult, 1);
+    if (s->ntiles_mult == 0)
+      while (row_tiles * ((np + 255) / 256) * mult < 152 && (np + 255) / 256 * mult * 2 <= np / 64) mult *= 2;
+    const int nnt = std::min((np + 255) / 256 * mult, std::max(np / 16, 1));
     const int ntile = pad16((np + nnt - 1) / nnt);
     CUtensorMap mA[2];
     TcMapsB mB;
@@ -746,7 +753,7 @@ cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const TcMats* mats, co
 
 int* tc_status_word(TcState* s) { return s->status; }
 
-void tc_set_ntiles(TcState* s, int mult) { s->ntiles_mult = (mult == 2 || mult == 4) ? mult : 1; }
+void tc_set_ntiles(TcState* s, int mult) { s->ntiles_mult = (mult == 1 || mult == 2 || mult == 4) ? mult : 0; }
 
 int tc_read_status(TcState* s, cudaStream_t st) {
   int h = 0;

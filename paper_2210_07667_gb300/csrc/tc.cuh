@@ -81,7 +81,8 @@ cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const TcMats* mats, co
 // flag is cleared by the read).  Synchronises the stream.
 int tc_read_status(TcState* s, cudaStream_t st);
 // N tiles per GEMM pass as a multiple of the minimum ceil(n_pad / 256):
-// 1, 2 or 4 (smaller tiles, more CTAs); 0 = 1.
+// 1, 2 or 4 (smaller tiles, more CTAs); 0 = by size (narrower tiles when the
+// row tiles alone leave SMs idle).
 void tc_set_ntiles(TcState* s, int mult);
 // The device status word the kernels record a failed wait in.
 int* tc_status_word(TcState* s);
