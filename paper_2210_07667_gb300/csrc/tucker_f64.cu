@@ -344,13 +344,19 @@ __global__ void combine_batch_kernel(EpiBatch eb, int64_t N) {
     epi_apply(e, idx, 0.0);
 }
 
-// The common case of one FP64 output from FP64 sources: out = sum_k c_k src_k,
-// two elements per thread with 16-byte loads, no local arrays.
+// The common case of one output: out = sum_k c_k src_k in FP64 arithmetic,
+// sources and output each double or float (the split dtypes' results and
+// outputs are float), two elements per thread with 16- or 8-byte loads and
+// no local arrays (the general epilogue indexes its sources dynamically,
+// which puts them in local memory).
 struct Lin1 {
   int nterm;
-  const double* src[kMaxSrc];
+  unsigned srcf32;  // bit k: src[k] is float
+  int outf32;
+  const void* src[kMaxSrc];
   double c[kMaxSrc];
-  double* out;
+  float chi[kMaxSrc], clo[kMaxSrc];  // c = chi + clo (rounded to 48 bits), for lincomb1_f32_kernel
+  void* out;
 };
 struct Lin1Batch {
   Lin1 l[kMaxEpiBatch];
@@ -365,25 +371,82 @@ __global__ void lincomb1_kernel(Lin1Batch lb, int64_t N2) {
     // unrolled by four: four independent loads in flight ahead of their FMAs
 #pragma unroll 4
     for (int k = 0; k < L.nterm; ++k) {
-      const double2 x = __ldg(reinterpret_cast<const double2*>(L.src[k]) + i);
-      ox = fma(L.c[k], x.x, ox);
-      oy = fma(L.c[k], x.y, oy);
+      double x0, x1;
+      if ((L.srcf32 >> k) & 1) {
+        const float2 f = __ldg(reinterpret_cast<const float2*>(L.src[k]) + i);
+        x0 = f.x;
+        x1 = f.y;
+      } else {
+        const double2 x = __ldg(reinterpret_cast<const double2*>(L.src[k]) + i);
+        x0 = x.x;
+        x1 = x.y;
+      }
+      ox = fma(L.c[k], x0, ox);
+      oy = fma(L.c[k], x1, oy);
     }
-    reinterpret_cast<double2*>(L.out)[i] = make_double2(ox, oy);
+    if (L.outf32) reinterpret_cast<float2*>(L.out)[i] = make_float2((float)ox, (float)oy);
+    else reinterpret_cast<double2*>(L.out)[i] = make_double2(ox, oy);
   }
 }
 
-// One combination as a Lin1 when it has a single FP64 output, FP64 sources,
-// no product term and 16-byte aligned pointers (N even).
+// An all-float combination with a float output (the split dtypes' sums of
+// their FP32 Tucker results), in compensated FP32 arithmetic instead of on
+// GB300's FP64 pipe (two DFMA per clock per SM against 128 FP32 FMAs): each
+// product c x is formed without error as chi x = p + e (the FMA gives e
+// exactly) plus clo x, and the running sum is kept as an unevaluated pair
+// (hi, lo) with error-free additions (Knuth's two-sum).  The pair carries
+// about 44 significant bits, far beyond the float the result is rounded to.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__global__ void lincomb1_f32_kernel(Lin1Batch lb, int64_t N2) {
+  pdl_wait();
+  const Lin1& L = lb.l[blockIdx.y];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N2;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < L.nterm; ++k) {
+      const float2 x = __ldg(reinterpret_cast<const float2*>(L.src[k]) + i);
+      const float ch = L.chi[k], cl = L.clo[k];
+      float p, e, s, t;
+      p = ch * x.x;
+      e = fmaf(ch, x.x, -p) + cl * x.x;
+      two_sum(hx, p, s, t);
+      hx = s;
+      lx += t + e;
+      p = ch * x.y;
+      e = fmaf(ch, x.y, -p) + cl * x.y;
+      two_sum(hy, p, s, t);
+      hy = s;
+      ly += t + e;
+    }
+    reinterpret_cast<float2*>(L.out)[i] = make_float2(hx + lx, hy + ly);
+  }
+}
+
+// One combination as a Lin1 when it has a single output, no product term,
+// an even N and pointers aligned for the paired loads and stores.
 bool as_lin1(const Epi& e, int64_t N, Lin1* l) {
-  if (e.nout != 1 || e.bnz || e.out_f32mask || e.src_f32mask || (N & 1)) return false;
-  if (((uintptr_t)e.out[0] & 15) != 0) return false;
+  if (e.nout != 1 || e.bnz || (N & 1)) return false;
+  const bool of = (e.out_f32mask & 1) != 0;
+  if (((uintptr_t)e.out[0] & (of ? 7 : 15)) != 0) return false;
   l->nterm = e.nterm;
   l->out = e.out[0];
+  l->outf32 = of ? 1 : 0;
+  l->srcf32 = 0;
   for (int k = 0; k < e.nterm; ++k) {
-    l->src[k] = e.src[e.term_m[k]];
+    const int m = e.term_m[k];
+    const bool sf = ((e.src_f32mask >> m) & 1) != 0;
+    l->src[k] = e.src[m];
     l->c[k] = e.term_c[k];
-    if (((uintptr_t)l->src[k] & 15) != 0) return false;
+    l->chi[k] = (float)e.term_c[k];
+    l->clo[k] = (float)(e.term_c[k] - (double)l->chi[k]);
+    if (sf) l->srcf32 |= 1u << k;
+    if (((uintptr_t)l->src[k] & (sf ? 7 : 15)) != 0) return false;
   }
   return true;
 }
@@ -489,6 +552,10 @@ cudaError_t launch_combine_batch(const Epi* e0, int B, int64_t N, cudaStream_t s
   if (lin) {
     int gx = grid_for(N / 2, 256) / B;
     if (gx < 1) gx = 1;
+    bool f32 = true;  // every combination all-float with a float output
+    for (int b = 0; b < B; ++b)
+      f32 = f32 && lb.l[b].outf32 && lb.l[b].srcf32 == (lb.l[b].nterm >= 32 ? ~0u : (1u << lb.l[b].nterm) - 1);
+    if (f32) return launch_pdl(lincomb1_f32_kernel, dim3(gx, B), dim3(256), 0, st, lb, N / 2);
     return launch_pdl(lincomb1_kernel, dim3(gx, B), dim3(256), 0, st, lb, N / 2);
   }
   int gx = grid_for(N, 256) / B;
@@ -505,6 +572,9 @@ cudaError_t launch_combine(const Epi& e0, int64_t N, cudaStream_t st) {
   Lin1Batch lb;
   if (as_lin1(e, N, &lb.l[0])) {
     count_launch();
+    const Lin1& l = lb.l[0];
+    if (l.outf32 && l.nterm > 0 && l.srcf32 == (1u << l.nterm) - 1)
+      return launch_pdl(lincomb1_f32_kernel, dim3(grid_for(N / 2, 256)), dim3(256), 0, st, lb, N / 2);
     return launch_pdl(lincomb1_kernel, dim3(grid_for(N / 2, 256)), dim3(256), 0, st, lb, N / 2);
   }
   count_launch();
