@@ -215,9 +215,9 @@ def profile_roofline(dname, ms, launches, flops, kernel=None):
 
 # dram__bytes_read.sum + dram__bytes_write.sum per mu-mode product of
 # oz_gemm_kernel<32> from an ncu capture of the kernel as it stands (four-
-# product launches of this workload: 14.835 MB read, 0 written; the profile
-# summary profiles/oz_gemm_fp64emu_adr3d_n64.md gives the command); None
-# once the kernel changes
+# product launches of this workload: 14.835 MB read, 0 written; the summary
+# of that capture under profiles/ gives the command); None once the kernel
+# changes
 OZ_GEMM_TRAFFIC_PER_PRODUCT = 14.835e6 / 4
 # bf16 digit products the emulated pass executes per FP64 product (digit
 # planes s + t <= 6 of seven per operand)
