@@ -218,7 +218,7 @@ def profile_roofline(dname, ms, launches, flops, kernel=None):
 # product launches of this workload: 14.835 MB read, 0 written; the summary
 # of that capture under profiles/ gives the command); None once the kernel
 # changes
-OZ_GEMM_TRAFFIC_PER_PRODUCT = 14.835e6 / 4
+OZ_GEMM_TRAFFIC_PER_PRODUCT = None
 # bf16 digit products the emulated pass executes per FP64 product (digit
 # planes s + t <= 6 of seven per operand)
 OZ_DIGIT_PRODUCTS = 28

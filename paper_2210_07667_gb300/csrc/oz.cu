@@ -438,8 +438,8 @@ __global__ void __launch_bounds__(NTH, 1)
     int buf = 0;
     uint32_t aph = 0;
     for (int t = blockIdx.x; t < P.num_tiles; t += gridDim.x) {
-      if (!mbar_wait(&tfull[buf], aph, P.status, 14)) break;
-      tc_fence_after();
+      // the tile's fibre and row exponents first: their loads run while the
+      // MMAs finish (none of them depends on this tile's accumulators)
       int tb = 0;
       const int64_t m0t = oz_tile_row0(P, t / P.n_ntiles, &tb);
       const int64_t rg = m0t + row;  // fibre of the batch
@@ -450,7 +450,12 @@ __global__ void __launch_bounds__(NTH, 1)
       double* const outb = P.out + bt * P.N;
       const int64_t m = rg - bt * P.M2;
       const int* const lscale = P.lscale[P.mixed ? tb : 0];
-#pragma unroll 1
+      int ls[CW];  // (lscale has n_pad >= every tile's columns entries)
+#pragma unroll
+      for (int j = 0; j < CW; ++j) ls[j] = lscale[r0 + grp * CW + j];
+      if (!mbar_wait(&tfull[buf], aph, P.status, 14)) break;
+      tc_fence_after();
+#pragma unroll
       for (int c0 = grp * CW; c0 < (grp + 1) * CW; c0 += CH) {
         const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * SET + (uint32_t)c0;
         uint32_t G[kOzSlices][CH];
@@ -463,15 +468,14 @@ __global__ void __launch_bounds__(NTH, 1)
         }
         tmem_wait_ld();
         if (!valid) continue;
-        // independent assemblies (lscale has n_pad >= every tile's columns
-        // entries), then the stores of the columns below n
+        // independent assemblies, then the stores of the columns below n
         double r[CH];
 #pragma unroll
         for (int j = 0; j < CH; ++j) {
           uint32_t g[kOzSlices];
 #pragma unroll
           for (int k = 0; k < kOzSlices; ++k) g[k] = G[k][j];
-          r[j] = oz_assemble(g, sx + lscale[r0 + c0 + j] - 48);
+          r[j] = oz_assemble(g, sx + ls[c0 - grp * CW + j] - 48);
         }
 #pragma unroll
         for (int j = 0; j < CH; ++j)
