@@ -260,6 +260,7 @@ struct OzParams {
   const int* xscale;
   int mixed;      // tensors with their own matrices: every tile within one tensor
   int64_t tpt;    // mixed: row tiles per tensor, ceil(M2 / 128) (the last one partial)
+  int shared_a;   // mixed, first pass: every tensor's input is tensor 0's (planes and exponents)
   const int* lscale[kOzMaxBatch];  // row exponents of tensor b's matrix (entry 0 unless mixed)
   int* status;
 };
@@ -350,7 +351,8 @@ __global__ void __launch_bounds__(NTH, 1)
       int issued = 0;
       for (int t = blockIdx.x; t < P.num_tiles; t += gridDim.x) {
         int tb = 0;
-        const int m0 = (int)oz_tile_row0(P, t / P.n_ntiles, &tb);
+        int m0 = (int)oz_tile_row0(P, t / P.n_ntiles, &tb);
+        if (P.shared_a) m0 -= (int)(tb * P.M2);  // the one split input
         const int r0 = (t % P.n_ntiles) * NT;
         const CUtensorMap* mapB = &mapsB.b[tb];
         bool ok = true;
@@ -445,7 +447,7 @@ __global__ void __launch_bounds__(NTH, 1)
       const int64_t rg = m0t + row;  // fibre of the batch
       const int r0 = (t % P.n_ntiles) * NT;
       const bool valid = P.mixed ? (rg - (int64_t)tb * P.M2 < P.M2) : (rg < P.rows);
-      const int sx = valid ? P.xscale[rg] : 0;
+      const int sx = valid ? P.xscale[P.shared_a ? rg - (int64_t)tb * P.M2 : rg] : 0;
       const int64_t bt = valid ? (P.mixed ? tb : rg / P.M2) : 0;
       double* const outb = P.out + bt * P.N;
       const int64_t m = rg - bt * P.M2;
@@ -676,6 +678,16 @@ bool cached(OzState* s, CUtensorMap* m, const void* base, uint64_t inner, uint64
 
 }  // namespace
 
+namespace {
+// Whether two input combinations are the same tensors with the same weights.
+bool same_combo(const Combo& a, const Combo& b) {
+  if (a.nsrc != b.nsrc || a.f32mask != b.f32mask) return false;
+  for (int m = 0; m < a.nsrc; ++m)
+    if (a.src[m] != b.src[m] || a.coef[m] != b.coef[m]) return false;
+  return true;
+}
+}  // namespace
+
 bool oz_mixed_ok(const OzState* s) {
   (void)s;  // every shape: mixed batches tile each tensor on its own
   return true;
@@ -694,14 +706,21 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, co
   const int64_t PS = (int64_t)s->batch * N;  // elements between digit planes
   __nv_bfloat16* planes = (__nv_bfloat16*)s->ws;
   int* xscale = (int*)(s->ws + up1k((size_t)kOzSlices * PS * 2));
+  // tensors with their own matrices and one and the same input (the
+  // quadrature nodes of a same-vector call): the first pass splits that input
+  // once and every tensor's tiles read it
+  bool shared = mixed && B > 1;
+  for (int b = 1; b < B && shared; ++b)
+    shared = same_combo(in[b], in[0]) && !(pro && pro->store[b]);
+  const int nsplit = shared ? 1 : B;
   SplitJobs cur;
   std::memset(&cur, 0, sizeof cur);
-  for (int b = 0; b < B; ++b) {
+  for (int b = 0; b < nsplit; ++b) {
     cur.c[b] = in[b];
     cur.store[b] = pro ? pro->store[b] : nullptr;
   }
-  cur.ntensor = B;
-  int rows0 = B;  // grid rows of the first split
+  cur.ntensor = nsplit;
+  int rows0 = nsplit;  // grid rows of the first split
   if (pro)
     for (int k = 0; k < pro->nside; ++k, ++rows0) {
       cur.c[rows0] = pro->side[k];
@@ -756,6 +775,7 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, co
     P.out = dst;
     P.xscale = xscale;
     P.mixed = mixed ? 1 : 0;
+    P.shared_a = (mu == 0 && shared) ? 1 : 0;
     P.status = s->status;
     if (ev) {
       cudaError_t e = cudaEventRecord(ev[2 * mu], st);

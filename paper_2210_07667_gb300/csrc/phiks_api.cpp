@@ -1845,21 +1845,45 @@ struct Pending {
 
 // The last batch's pending outputs: one combination pass (outputs float for
 // the split dtypes).
+// (split dtypes: outputs sharing their sources are grouped, up to four per
+// combination over the union of their sources, so that the compensated FP32
+// pass, bound by memory, reads each source once for the group; FP64 outputs
+// stay one per combination, whose FP64 arithmetic spreads over more CTAs)
 phiks_status flush_pending(Ctx& c, const std::vector<Pending>& pout) {
+  const bool f32 = split_dtype(c.P);
+  const int kGroup = f32 ? 4 : 1;
   std::vector<Epi> es;
+  Epi e = make_epi();
+  auto close = [&]() {
+    if (e.nout) es.push_back(e);
+    e = make_epi();
+  };
   for (auto& x : pout) {
-    Epi e = make_epi();
-    e.nout = 1;
-    e.out[0] = (double*)x.out;
-    e.out_f32mask = split_dtype(c.P) ? 1 : 0;
-    e.nsrc = x.x.nsrc;
-    e.src_f32mask = x.x.f32mask;
-    for (int m = 0; m < e.nsrc; ++m) {
-      e.src[m] = x.x.src[m];
-      e.a[0][m] = x.x.coef[m];
+    // sources of x not yet in the group
+    int extra = 0;
+    for (int m = 0; m < x.x.nsrc; ++m) {
+      bool found = false;
+      for (int k = 0; k < e.nsrc && !found; ++k)
+        found = e.src[k] == x.x.src[m] && ((e.src_f32mask >> k) & 1) == ((x.x.f32mask >> m) & 1);
+      extra += found ? 0 : 1;
     }
-    es.push_back(e);
+    if (e.nout == kGroup || e.nsrc + extra > kMaxSrc) close();
+    const int t = e.nout++;
+    e.out[t] = (double*)x.out;
+    if (f32) e.out_f32mask |= 1 << t;
+    for (int m = 0; m < x.x.nsrc; ++m) {
+      const int fm = (x.x.f32mask >> m) & 1;
+      int k = 0;
+      while (k < e.nsrc && !(e.src[k] == x.x.src[m] && ((e.src_f32mask >> k) & 1) == fm)) ++k;
+      if (k == e.nsrc) {
+        e.src[k] = x.x.src[m];
+        e.src_f32mask |= fm << k;
+        e.nsrc++;
+      }
+      e.a[t][k] += x.x.coef[m];
+    }
   }
+  close();
   return combine_many(c, es.data(), (int)es.size());
 }
 

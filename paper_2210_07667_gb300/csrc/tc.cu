@@ -96,6 +96,7 @@ struct GemmParams {
   int last;       // 0: write planes for the next pass; 1: write FP32 results to out0
   int mixed;      // tensors with their own matrices: every tile within one tensor
   int64_t tpt;    // mixed: row tiles per tensor, ceil(M2 / 128) (the last one partial)
+  int shared_a;   // mixed, first pass: every tensor's input is tensor 0's planes
   void* out0;
   void* out1;
   int* status;
@@ -173,7 +174,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       for (int t = blockIdx.x; t < P.num_tiles && ok; t += gridDim.x) {
         int mi = 0;
-        const int m0 = (int)tc_tile_row0(P, t / P.n_ntiles, &mi);
+        int m0 = (int)tc_tile_row0(P, t / P.n_ntiles, &mi);
+        if (P.shared_a) m0 -= (int)(mi * P.M2);  // the one split input
         const int r0 = (t % P.n_ntiles) * P.ntile;
         const CUtensorMap* mapB0 = &mapsB.b[mi][0];
         const CUtensorMap* mapB1 = &mapsB.b[mi][1];
@@ -478,6 +480,16 @@ size_t tc_workspace_bytes(int64_t N, int batch) {
   return 4 * plane + 1024;
 }
 
+namespace {
+// Whether two input combinations are the same tensors with the same weights.
+bool same_combo(const Combo& a, const Combo& b) {
+  if (a.nsrc != b.nsrc || a.f32mask != b.f32mask) return false;
+  for (int m = 0; m < a.nsrc; ++m)
+    if (a.src[m] != b.src[m] || a.coef[m] != b.coef[m]) return false;
+  return true;
+}
+}  // namespace
+
 bool tc_mixed_ok(const TcState* s) {
   (void)s;  // every shape: mixed batches tile each tensor on its own
   return true;
@@ -639,15 +651,22 @@ cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const TcMats* mats, co
   // contiguous, tensor b at element b N of every plane; into the set that
   // does not hold the last call's results, which the inputs may read
   int cur = 1 - s->last_res;
+  // tensors with their own matrices and one and the same input (the
+  // quadrature nodes of a same-vector call): that input is split once and
+  // every tensor's tiles of the first pass read it
+  bool shared = mixed && B > 1;
+  for (int b = 1; b < B && shared; ++b)
+    shared = same_combo(in[b], in[0]) && !(pro && pro->store[b]);
   {
+    const int nsplit = shared ? 1 : B;
     TcSplitJobs jb;
     std::memset(&jb, 0, sizeof jb);
-    for (int b = 0; b < B; ++b) {
+    for (int b = 0; b < nsplit; ++b) {
       jb.c[b] = in[b];
       jb.store[b] = pro ? pro->store[b] : nullptr;
     }
-    jb.ntensor = B;
-    int rows = B;
+    jb.ntensor = nsplit;
+    int rows = nsplit;
     if (pro)
       for (int k = 0; k < pro->nside; ++k, ++rows) {
         jb.c[rows] = pro->side[k];
@@ -716,6 +735,7 @@ cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const TcMats* mats, co
     P.tmem_cols = cols;
     P.last = (mu == s->d - 1);
     P.mixed = mixed ? 1 : 0;
+    P.shared_a = (mu == 0 && shared) ? 1 : 0;
     P.out0 = set[1 - cur][0];
     P.out1 = set[1 - cur][1];
     P.status = s->status;

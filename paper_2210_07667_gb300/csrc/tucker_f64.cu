@@ -13,6 +13,7 @@
 // a CTA computes a TI x TC tile of outputs (rows i of L, "columns" c = x + a y)
 // by staging KC-deep slices of L and of the fibres V(x, :, y) in shared memory.
 #include <atomic>
+#include <cstring>
 
 #include "kernels.cuh"
 #include "pdl.cuh"
@@ -451,6 +452,119 @@ bool as_lin1(const Epi& e, int64_t N, Lin1* l) {
   return true;
 }
 
+// Several outputs over one list of sources (the pending outputs of a batch,
+// which read the same node results with other weights): every source is read
+// once for all outputs.  out[t] = sum_k c[t][k] src[k], t < nout <= kLinMOut,
+// FP64 arithmetic, or compensated FP32 when every source and output is float.
+constexpr int kLinMOut = 4;
+struct LinM {
+  int nout, nterm;
+  unsigned srcf32;
+  int outf32;
+  const void* src[kMaxSrc];
+  double c[kLinMOut][kMaxSrc];
+  float chi[kLinMOut][kMaxSrc], clo[kLinMOut][kMaxSrc];
+  void* out[kLinMOut];
+};
+struct LinMBatch {
+  LinM l[kMaxEpiBatch];
+};
+
+__global__ void lincombm_kernel(const __grid_constant__ LinMBatch lb, int64_t N2) {
+  pdl_wait();
+  const LinM& L = lb.l[blockIdx.y];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N2;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double ox[kLinMOut] = {0.0, 0.0, 0.0, 0.0}, oy[kLinMOut] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 2
+    for (int k = 0; k < L.nterm; ++k) {
+      double x0, x1;
+      if ((L.srcf32 >> k) & 1) {
+        const float2 f = __ldg(reinterpret_cast<const float2*>(L.src[k]) + i);
+        x0 = f.x;
+        x1 = f.y;
+      } else {
+        const double2 x = __ldg(reinterpret_cast<const double2*>(L.src[k]) + i);
+        x0 = x.x;
+        x1 = x.y;
+      }
+#pragma unroll
+      for (int t = 0; t < kLinMOut; ++t)
+        if (t < L.nout && L.c[t][k] != 0.0) {  // (uniform branches: no predicated-off DFMA)
+          ox[t] = fma(L.c[t][k], x0, ox[t]);
+          oy[t] = fma(L.c[t][k], x1, oy[t]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < kLinMOut; ++t)
+      if (t < L.nout) {
+        if (L.outf32) reinterpret_cast<float2*>(L.out[t])[i] = make_float2((float)ox[t], (float)oy[t]);
+        else reinterpret_cast<double2*>(L.out[t])[i] = make_double2(ox[t], oy[t]);
+      }
+  }
+}
+
+__global__ void lincombm_f32_kernel(const __grid_constant__ LinMBatch lb, int64_t N2) {
+  pdl_wait();
+  const LinM& L = lb.l[blockIdx.y];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N2;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float hx[kLinMOut] = {0.f, 0.f, 0.f, 0.f}, lx[kLinMOut] = {0.f, 0.f, 0.f, 0.f};
+    float hy[kLinMOut] = {0.f, 0.f, 0.f, 0.f}, ly[kLinMOut] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+    for (int k = 0; k < L.nterm; ++k) {
+      const float2 x = __ldg(reinterpret_cast<const float2*>(L.src[k]) + i);
+#pragma unroll
+      for (int t = 0; t < kLinMOut; ++t) {
+        if (t >= L.nout) break;
+        const float ch = L.chi[t][k], cl = L.clo[t][k];
+        float p, e, sm, tt;
+        p = ch * x.x;
+        e = fmaf(ch, x.x, -p) + cl * x.x;
+        two_sum(hx[t], p, sm, tt);
+        hx[t] = sm;
+        lx[t] += tt + e;
+        p = ch * x.y;
+        e = fmaf(ch, x.y, -p) + cl * x.y;
+        two_sum(hy[t], p, sm, tt);
+        hy[t] = sm;
+        ly[t] += tt + e;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kLinMOut; ++t)
+      if (t < L.nout) reinterpret_cast<float2*>(L.out[t])[i] = make_float2(hx[t] + lx[t], hy[t] + ly[t]);
+  }
+}
+
+// A combination with 1..kLinMOut outputs as a LinM: no product term, every
+// output of one element type, an even N, aligned pointers.
+bool as_linm(const Epi& e, int64_t N, LinM* l) {
+  if (e.nout < 1 || e.nout > kLinMOut || e.bnz || (N & 1)) return false;
+  const bool of = (e.out_f32mask & 1) != 0;
+  if (e.out_f32mask != (of ? (1 << e.nout) - 1 : 0)) return false;
+  std::memset(l, 0, sizeof *l);
+  l->nout = e.nout;
+  l->nterm = e.nsrc;
+  l->outf32 = of ? 1 : 0;
+  for (int t = 0; t < e.nout; ++t) {
+    l->out[t] = e.out[t];
+    if (((uintptr_t)e.out[t] & (of ? 7 : 15)) != 0) return false;
+  }
+  for (int m = 0; m < e.nsrc; ++m) {
+    const bool sf = ((e.src_f32mask >> m) & 1) != 0;
+    l->src[m] = e.src[m];
+    if (sf) l->srcf32 |= 1u << m;
+    if (((uintptr_t)e.src[m] & (sf ? 7 : 15)) != 0) return false;
+    for (int t = 0; t < e.nout; ++t) {
+      l->c[t][m] = e.a[t][m];
+      l->chi[t][m] = (float)e.a[t][m];
+      l->clo[t][m] = (float)(e.a[t][m] - (double)l->chi[t][m]);
+    }
+  }
+  return true;
+}
+
 __global__ void combine_kernel(Epi e, int64_t N) {
   pdl_wait();
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
@@ -541,14 +655,25 @@ cudaError_t launch_combine_batch(const Epi* e0, int B, int64_t N, cudaStream_t s
   if (B > kMaxEpiBatch) return cudaErrorInvalidValue;
   EpiBatch eb;
   Lin1Batch lb;
-  bool lin = true;
+  bool lin = true, linm = true;
+  LinMBatch mb;
   for (int b = 0; b < B; ++b) {
     eb.e[b] = e0[b];
     for (int t = 0; t < kMaxOut; ++t) eb.e[b].b[t] = 0.0;  // no product result here
     epi_finalize(eb.e[b]);
     lin = lin && as_lin1(eb.e[b], N, &lb.l[b]);
+    linm = linm && as_linm(eb.e[b], N, &mb.l[b]);
   }
   count_launch();
+  if (linm && !lin) {
+    int gx = grid_for(N / 2, 256) / B;
+    if (gx < 1) gx = 1;
+    bool f32 = true;
+    for (int b = 0; b < B; ++b)
+      f32 = f32 && mb.l[b].outf32 && mb.l[b].srcf32 == (1u << mb.l[b].nterm) - 1;
+    if (f32) return launch_pdl(lincombm_f32_kernel, dim3(gx, B), dim3(256), 0, st, mb, N / 2);
+    return launch_pdl(lincombm_kernel, dim3(gx, B), dim3(256), 0, st, mb, N / 2);
+  }
   if (lin) {
     int gx = grid_for(N / 2, 256) / B;
     if (gx < 1) gx = 1;
