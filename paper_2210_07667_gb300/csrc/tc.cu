@@ -325,7 +325,16 @@ struct TcSplitJobs {
   void* store[kTcMaxBatch + kTcMaxSide];
   unsigned store_f32;
   int ntensor;
+  // each coefficient as chi + clo (floats), for combinations of float sources
+  float chi[kTcMaxBatch + kTcMaxSide][kMaxSrc], clo[kTcMaxBatch + kTcMaxSide][kMaxSrc];
 };
+
+// Knuth's two-sum: s + e = a + b exactly.
+__device__ __forceinline__ void tc_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
 
 template <int KIND, int NP>
 __global__ void tc_split_kernel(const __grid_constant__ TcSplitJobs jb, int64_t N, void* p0, void* p1) {
@@ -338,16 +347,42 @@ __global__ void tc_split_kernel(const __grid_constant__ TcSplitJobs jb, int64_t 
   const int64_t off = (int64_t)y * N;  // tensor b's elements in the planes
   const bool plain = in.nsrc == 1 && in.coef[0] == 1.0 && !xout;
   const bool f32 = in.f32mask & 1;
+  // all sources float (quadrature inputs and sums of FP32 Tucker results):
+  // compensated FP32 as in the combination kernels (error-free products,
+  // two-sum, about 44 bits), off GB300's slow FP64 pipe; a source in FP64
+  // (the squaring's accumulators, eq. (simul) / eq. (comb)) keeps the
+  // combination in FP64
+  const bool allf32 = in.nsrc > 0 && (unsigned)in.f32mask == (1u << in.nsrc) - 1;
+  const float* const chi = jb.chi[y];
+  const float* const clo = jb.clo[y];
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
        idx += (int64_t)gridDim.x * blockDim.x) {
     float xf;
     if (plain) {
       xf = f32 ? ((const float*)in.src[0])[idx] : (float)in.src[0][idx];
+    } else if (allf32) {
+      float hi = 0.f, lo = 0.f;
+#pragma unroll 4
+      for (int m = 0; m < in.nsrc; ++m) {
+        const float v = __ldg((const float*)in.src[m] + idx);
+        const float p = chi[m] * v;
+        const float e = fmaf(chi[m], v, -p) + clo[m] * v;
+        float s, t;
+        tc_two_sum(hi, p, s, t);
+        hi = s;
+        lo += t + e;
+      }
+      xf = hi + lo;
+      if (xout) {
+        if (out32) ((float*)xout)[idx] = xf;
+        else ((double*)xout)[idx] = (double)hi + (double)lo;
+      }
     } else {
       double x = 0.0;
+#pragma unroll 4
       for (int m = 0; m < in.nsrc; ++m) {
         const double v =
-            ((in.f32mask >> m) & 1) ? (double)((const float*)in.src[m])[idx] : in.src[m][idx];
+            ((in.f32mask >> m) & 1) ? (double)__ldg((const float*)in.src[m] + idx) : __ldg(in.src[m] + idx);
         x = fma(in.coef[m], v, x);
       }
       if (xout) {
@@ -358,6 +393,15 @@ __global__ void tc_split_kernel(const __grid_constant__ TcSplitJobs jb, int64_t 
     }
     if (split) split_store_f<KIND, NP>(p0, p1, off + idx, xf);
   }
+}
+
+// Fills the float splits of every row's coefficients.
+void tc_split_coefs(TcSplitJobs& jb, int rows) {
+  for (int y = 0; y < rows; ++y)
+    for (int m = 0; m < jb.c[y].nsrc && m < kMaxSrc; ++m) {
+      jb.chi[y][m] = (float)jb.c[y].coef[m];
+      jb.clo[y][m] = (float)(jb.c[y].coef[m] - (double)jb.chi[y][m]);
+    }
 }
 
 // B planes of an FP64 column-major n x n matrix: plane[i * n_pad + k] from L[i, k].
@@ -673,6 +717,7 @@ cudaError_t tc_tucker(TcState* s, int B, const Combo* in, const TcMats* mats, co
         jb.store[rows] = pro->side_out[k];
         if ((pro->side_f32 >> k) & 1) jb.store_f32 |= 1u << rows;
       }
+    tc_split_coefs(jb, rows);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 152 * 8 / rows));
     count_launch();
     void *q0 = set[cur][0], *q1 = set[cur][1], *none = nullptr;
