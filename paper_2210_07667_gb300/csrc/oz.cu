@@ -227,10 +227,19 @@ __global__ void oz_prep_b_kernel(PrepBatch pb) {
 // |T| < 2^70 for n <= 128, S = floor(T / 2^8) fits 63 bits; its conversion
 // to double rounds to nearest (an error below (1/2 + 2^-8) ulp of T 2^e in
 // all), and 2^(e + 8) enters the exponent field.
+//
+// The first NM accumulators are bounded by |G_k| <= (k + 1) n 2^14 <= 2^22
+// (k + 1 digit products per term, each at most 2^14 in magnitude, n terms):
+// for them G_k + 1.5 2^23 is exact and lies in [2^23, 2^24], so its bit
+// pattern minus that of 1.5 2^23 is G_k (one FP32 add on the FMA pipe in
+// place of a float-to-integer conversion).
+template <int NM>
 __device__ __forceinline__ double oz_assemble(const uint32_t* G, int e) {
   int g[kOzSlices];
 #pragma unroll
-  for (int k = 0; k < kOzSlices; ++k) g[k] = __float2int_rn(__uint_as_float(G[k]));
+  for (int k = 0; k < kOzSlices; ++k)
+    g[k] = k < NM ? __float_as_int(__uint_as_float(G[k]) + 12582912.0f) - 0x4B400000
+                  : __float2int_rn(__uint_as_float(G[k]));
   long long hi = (long long)(g[0] * 256 + g[1]);
   hi = hi * 256 + g[2];
   hi = hi * 256 + g[3];
@@ -256,6 +265,8 @@ struct OzParams {
   int num_tiles;
   int tmem_cols;
   int nbuf;       // TMEM accumulator sets (1 or 2)
+  int resident;   // nk == 1: A kept across a row tile's column tiles, B per tensor
+  uint32_t stage_bytes;  // shared memory of the A and B planes
   double* out;    // FP64 result of tensor b, rotated layout: out[b N + m + M2 i]
   const int* xscale;
   int mixed;      // tensors with their own matrices: every tile within one tensor
@@ -287,6 +298,16 @@ __device__ __forceinline__ int64_t oz_tile_row0(const OzParams& P, int64_t rt, i
 
 constexpr int kOzEpiWarps = 16;
 constexpr int NTH = 64 + 32 * kOzEpiWarps;
+constexpr int kOzMaxColTiles = 4;  // column tiles of a resident B (n <= 64, NT >= 16)
+
+// This CTA's tiles: a contiguous range of the tile order (row tile major), so
+// that consecutive tiles of a CTA mostly share their row tile.
+__device__ __forceinline__ void oz_tile_range(const OzParams& P, int* t0, int* t1) {
+  const int G = (int)gridDim.x, c = (int)blockIdx.x;
+  const int base = P.num_tiles / G, rem = P.num_tiles % G;
+  *t0 = c * base + min(c, rem);
+  *t1 = *t0 + base + (c < rem ? 1 : 0);
+}
 
 // Per tile: A = 7 digit planes of 128 fibres x 64 K, B = 7 digit planes of
 // NT rows x 64 K stored back to back, so that one MMA multiplies A plane t by
@@ -295,11 +316,18 @@ constexpr int NTH = 64 + 32 * kOzEpiWarps;
 //     G_k = sum_{s + t = k} B_s A_t^T,  k = 0..6,
 // with 7 MMAs per 16-wide K step instead of 28 (the first, t = 0, covers all
 // seven blocks and starts them).  A planes land on their own barriers, so
-// the MMAs of plane t start once it is in.  One shared-memory stage (112 KiB
-// of A digits per 64-wide K chunk).  Warp 0 issues the copies, one thread of
-// warp 1 the MMAs, and the kOzEpiWarps warps from 2 on the epilogue
-// (kOzEpiWarps / 4 warps per TMEM lane quarter, each taking an equal share
-// of the NT columns).
+// the MMAs of plane t start once it is in.  Warp 0 issues the copies, one
+// thread of warp 1 the MMAs, and the kOzEpiWarps warps from 2 on the
+// epilogue (kOzEpiWarps / 4 warps per TMEM lane quarter, each taking an
+// equal share of the NT columns); two TMEM accumulator sets let a tile's
+// MMAs run during the previous tile's epilogue.
+//
+// Resident form (n <= 64: one K chunk): a CTA's tiles are consecutive, the
+// A planes of a row tile (112 KiB) are loaded once for all of its column
+// tiles, and each column tile's B planes once per tensor (one slot and one
+// barrier per column tile), so that the copies of the next row tile overlap
+// the epilogues of the current one.  Streaming form (n > 64): every tile
+// streams its K chunks of A and B through the one stage.
 
 template <int NT>
 __global__ void __launch_bounds__(NTH, 1)
@@ -310,11 +338,10 @@ __global__ void __launch_bounds__(NTH, 1)
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr uint32_t A_SLICE = BM * 128;  // bytes of one digit plane of the A tile
   constexpr uint32_t B_SLICE = NT * 128;
-  constexpr uint32_t STAGE = kOzSlices * (A_SLICE + B_SLICE);
   constexpr uint32_t SET = kOzSlices * NT;  // TMEM columns of one accumulator set
-  uint64_t* fullA = (uint64_t*)(smem + STAGE);  // [7]: plane t of A landed
-  uint64_t* fullB = fullA + kOzSlices;          // all planes of B landed
-  uint64_t* empty = fullB + 1;
+  uint64_t* fullA = (uint64_t*)(smem + P.stage_bytes);  // [7]: plane t of A landed
+  uint64_t* fullB = fullA + kOzSlices;  // [kOzMaxColTiles]: the B planes of a column tile landed
+  uint64_t* empty = fullB + kOzMaxColTiles;
   uint64_t* tfull = empty + 1;
   uint64_t* tempty = tfull + 2;
   uint64_t* mdone = tempty + 2;  // the MMA warp's issued MMAs finished (failure path)
@@ -322,7 +349,7 @@ __global__ void __launch_bounds__(NTH, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int t = 0; t < kOzSlices; ++t) mbar_init(&fullA[t], 1);
-    mbar_init(fullB, 1);
+    for (int c = 0; c < kOzMaxColTiles; ++c) mbar_init(&fullB[c], 1);
     mbar_init(empty, 1);
     mbar_init(mdone, 1);
     for (int b = 0; b < 2; ++b) {
@@ -345,11 +372,57 @@ __global__ void __launch_bounds__(NTH, 1)
   const uint32_t tmem_base = *tmem_slot;
   pdl_wait();  // the digit planes and scales come from the kernels before
 
+  int t_begin = 0, t_end = 0;
+  oz_tile_range(P, &t_begin, &t_end);
+  uint8_t* const smemB = smem + kOzSlices * A_SLICE;
   if (warp == 0) {
-    if (lane == 0) {
+    if (lane == 0 && P.resident) {
+      uint32_t eph = 0, bmask = 0, bever = 0, bph = 0;  // per column tile: loaded, parity of the next load
+      int nA = 0;
+      int prev_rt = -1, prev_tb = -1;
+      for (int t = t_begin; t < t_end; ++t) {
+        const int rt = t / P.n_ntiles, ct = t % P.n_ntiles;
+        int tb = 0;
+        int m0 = (int)oz_tile_row0(P, rt, &tb);
+        if (rt != prev_rt) {
+          if (prev_rt >= 0) {  // the MMAs on the previous row tile's planes finished
+            if (!mbar_wait(empty, eph, P.status, 11)) break;
+            eph ^= 1;
+          }
+          if (tb != prev_tb) {  // another tensor's matrix: every B slot is stale
+            bmask = 0;
+            prev_tb = tb;
+          }
+        }
+        if (!((bmask >> ct) & 1u)) {  // B first: the tile's first MMA needs it and A plane 0
+          mbar_arrive_expect_tx(&fullB[ct], kOzSlices * B_SLICE);
+#pragma unroll 1
+          for (int s = 0; s < kOzSlices; ++s)
+            tma_load_3d(smemB + (ct * kOzSlices + s) * B_SLICE, &mapsB.b[tb], &fullB[ct], 0, ct * NT, s);
+          bmask |= 1u << ct;
+          bever |= 1u << ct;
+          bph ^= 1u << ct;
+        }
+        if (rt != prev_rt) {
+          if (P.shared_a) m0 -= (int)(tb * P.M2);  // the one split input
+#pragma unroll 1
+          for (int s = 0; s < kOzSlices; ++s) {
+            mbar_arrive_expect_tx(&fullA[s], A_SLICE);
+            tma_load_3d(smem + s * A_SLICE, &mapA, &fullA[s], 0, m0, s);
+          }
+          ++nA;
+          prev_rt = rt;
+        }
+      }
+      // the last copies landed (also after another role gave up)
+      if (nA)
+        for (int s = 0; s < kOzSlices; ++s) (void)mbar_drain(&fullA[s], (uint32_t)(nA - 1) & 1u);
+      for (int c = 0; c < kOzMaxColTiles; ++c)
+        if ((bever >> c) & 1u) (void)mbar_drain(&fullB[c], ((bph >> c) & 1u) ^ 1u);
+    } else if (lane == 0) {
       uint32_t ph = 0;
       int issued = 0;
-      for (int t = blockIdx.x; t < P.num_tiles; t += gridDim.x) {
+      for (int t = t_begin; t < t_end; ++t) {
         int tb = 0;
         int m0 = (int)oz_tile_row0(P, t / P.n_ntiles, &tb);
         if (P.shared_a) m0 -= (int)(tb * P.M2);  // the one split input
@@ -364,7 +437,7 @@ __global__ void __launch_bounds__(NTH, 1)
           mbar_arrive_expect_tx(fullB, kOzSlices * B_SLICE);
 #pragma unroll 1
           for (int s = 0; s < kOzSlices; ++s)
-            tma_load_3d(smem + kOzSlices * A_SLICE + s * B_SLICE, mapB, fullB, kc * 64, r0, s);
+            tma_load_3d(smemB + s * B_SLICE, mapB, fullB, kc * 64, r0, s);
 #pragma unroll 1
           for (int s = 0; s < kOzSlices; ++s) {
             mbar_arrive_expect_tx(&fullA[s], A_SLICE);
@@ -382,42 +455,87 @@ __global__ void __launch_bounds__(NTH, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      uint32_t ph = 0, aph = 0;
-      int buf = 0;
+      uint32_t ph = 0, aph = 0, apar = 0, bmask = 0, bpar = 0;
+      int buf = 0, prev_rt = -1, prev_tb = -1;
       bool ok = true, any = false;
-      for (int t = blockIdx.x; t < P.num_tiles && ok; t += gridDim.x) {
+      for (int t = t_begin; t < t_end && ok; ++t) {
+        const int rt = t / P.n_ntiles, ct = t % P.n_ntiles;
         if (!mbar_wait(&tempty[buf], aph ^ 1, P.status, 12)) {
           ok = false;
           break;
         }
         tc_fence_after();
         const uint32_t d0 = tmem_base + (uint32_t)buf * SET;
-        for (int kc = 0; kc < P.nk && ok; ++kc) {
-          const uint32_t a0 = smem_u32(smem), b0 = a0 + kOzSlices * A_SLICE;
-          if (!mbar_wait(fullB, ph, P.status, 13)) {
-            ok = false;
-            break;
+        const uint32_t a0 = smem_u32(smem);
+        if (P.resident) {
+          int tb = 0;
+          (void)oz_tile_row0(P, rt, &tb);
+          const bool newA = rt != prev_rt;
+          if (newA && tb != prev_tb) {
+            bmask = 0;
+            prev_tb = tb;
           }
-#pragma unroll 1
+          if (!((bmask >> ct) & 1u)) {
+            if (!mbar_wait(&fullB[ct], (bpar >> ct) & 1u, P.status, 13)) {
+              ok = false;
+              break;
+            }
+            bpar ^= 1u << ct;
+            bmask |= 1u << ct;
+          }
+          // descriptors of plane 0 / K step 0; the others differ in the start
+          // address field only (16-byte units, no carry out of the field)
+          const uint64_t da = sdesc_sw128(a0);
+          const uint64_t db = sdesc_sw128(smem_u32(smemB) + (uint32_t)(ct * kOzSlices) * B_SLICE);
+#pragma unroll
           for (int at = 0; at < kOzSlices; ++at) {  // digit plane at of X times every plane of L
-            if (!mbar_wait(&fullA[at], ph, P.status, 13)) {
+            if (newA && !mbar_wait(&fullA[at], apar, P.status, 13)) {
               ok = false;
               break;
             }
             tc_fence_after();
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint32_t first = (kc == 0 && kk == 0 && at == 0) ? 0u : 1u;
-              umma<0>(d0 + (uint32_t)(at * NT), sdesc_sw128(a0 + at * A_SLICE + kk * 32),
-                      sdesc_sw128(b0 + kk * 32), idesc_make(1, (kOzSlices - at) * NT), first);
-            }
+            for (int kk = 0; kk < 4; ++kk)
+              umma<0>(d0 + (uint32_t)(at * NT), da + (uint64_t)((at * A_SLICE + kk * 32) >> 4),
+                      db + (uint64_t)((kk * 32) >> 4), idesc_make(1, (kOzSlices - at) * NT),
+                      (kk == 0 && at == 0) ? 0u : 1u);
             any = true;
           }
           if (!ok) break;
-          umma_commit(empty);
-          ph ^= 1;
+          if (newA) {
+            apar ^= 1;
+            prev_rt = rt;
+          }
+          // the last tile on these A planes: the stage is free for the next row tile
+          if (t + 1 < t_end && (t + 1) / P.n_ntiles != rt) umma_commit(empty);
+        } else {
+          const uint32_t b0 = smem_u32(smemB);
+          for (int kc = 0; kc < P.nk && ok; ++kc) {
+            if (!mbar_wait(fullB, ph, P.status, 13)) {
+              ok = false;
+              break;
+            }
+#pragma unroll 1
+            for (int at = 0; at < kOzSlices; ++at) {  // digit plane at of X times every plane of L
+              if (!mbar_wait(&fullA[at], ph, P.status, 13)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t first = (kc == 0 && kk == 0 && at == 0) ? 0u : 1u;
+                umma<0>(d0 + (uint32_t)(at * NT), sdesc_sw128(a0 + at * A_SLICE + kk * 32),
+                        sdesc_sw128(b0 + kk * 32), idesc_make(1, (kOzSlices - at) * NT), first);
+              }
+              any = true;
+            }
+            if (!ok) break;
+            umma_commit(empty);
+            ph ^= 1;
+          }
+          if (!ok) break;
         }
-        if (!ok) break;
         umma_commit(&tfull[buf]);
         if (++buf == P.nbuf) {
           buf = 0;
@@ -432,14 +550,13 @@ __global__ void __launch_bounds__(NTH, 1)
   } else {
     const int q = warp & 3;  // TMEM lane quarter of this warp
     constexpr int GROUPS = kOzEpiWarps / 4;   // warps per lane quarter
-    constexpr int CW = NT / GROUPS;           // columns per warp
-    constexpr int CH = CW >= 8 ? 8 : 4;       // columns per TMEM load
-    static_assert(CW % CH == 0, "epilogue column split");
+    constexpr int CW = NT / GROUPS;           // columns per warp: one TMEM load per block
+    static_assert(CW == 8 || CW == 4, "epilogue column split");
     const int grp = (warp - 2) >> 2;
     const int row = q * 32 + lane;
     int buf = 0;
     uint32_t aph = 0;
-    for (int t = blockIdx.x; t < P.num_tiles; t += gridDim.x) {
+    for (int t = t_begin; t < t_end; ++t) {
       // the tile's fibre and row exponents first: their loads run while the
       // MMAs finish (none of them depends on this tile's accumulators)
       int tb = 0;
@@ -457,34 +574,56 @@ __global__ void __launch_bounds__(NTH, 1)
       for (int j = 0; j < CW; ++j) ls[j] = lscale[r0 + grp * CW + j];
       if (!mbar_wait(&tfull[buf], aph, P.status, 14)) break;
       tc_fence_after();
+      const int c0 = grp * CW;
+      uint32_t G[kOzSlices][CW];
+      {
+        const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * SET + (uint32_t)c0;
+        if constexpr (CW == 8) {
 #pragma unroll
-      for (int c0 = grp * CW; c0 < (grp + 1) * CW; c0 += CH) {
-        const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * SET + (uint32_t)c0;
-        uint32_t G[kOzSlices][CH];
-        if constexpr (CH == 8) {
-#pragma unroll
-          for (int k = 0; k < kOzSlices; ++k) tmem_ld8_nowait(tb + (uint32_t)(k * NT), G[k]);
+          for (int k = 0; k < kOzSlices; ++k) tmem_ld8_nowait(ta + (uint32_t)(k * NT), G[k]);
         } else {
 #pragma unroll
-          for (int k = 0; k < kOzSlices; ++k) tmem_ld4_nowait(tb + (uint32_t)(k * NT), G[k]);
+          for (int k = 0; k < kOzSlices; ++k) tmem_ld4_nowait(ta + (uint32_t)(k * NT), G[k]);
         }
         tmem_wait_ld();
-        if (!valid) continue;
-        // independent assemblies, then the stores of the columns below n
-        double r[CH];
-#pragma unroll
-        for (int j = 0; j < CH; ++j) {
-          uint32_t g[kOzSlices];
-#pragma unroll
-          for (int k = 0; k < kOzSlices; ++k) g[k] = G[k][j];
-          r[j] = oz_assemble(g, sx + ls[c0 - grp * CW + j] - 48);
-        }
-#pragma unroll
-        for (int j = 0; j < CH; ++j)
-          if (r0 + c0 + j < P.n) outb[m + P.M2 * (int64_t)(r0 + c0 + j)] = r[j];
       }
+      // the accumulators are in registers: the set is free for the MMAs of a
+      // later tile (which frees this row tile's A planes sooner)
       tc_fence_before();
       mbar_arrive(&tempty[buf]);
+      if (valid) {
+        // independent assemblies, then the stores of the columns below n
+        double r[CW];
+        // accumulators small enough for the exact FP32 conversion: (k + 1) n <= 256
+        if (P.n <= 36) {
+#pragma unroll
+          for (int j = 0; j < CW; ++j) {
+            uint32_t g[kOzSlices];
+#pragma unroll
+            for (int k = 0; k < kOzSlices; ++k) g[k] = G[k][j];
+            r[j] = oz_assemble<7>(g, sx + ls[j] - 48);
+          }
+        } else if (P.n <= 64) {
+#pragma unroll
+          for (int j = 0; j < CW; ++j) {
+            uint32_t g[kOzSlices];
+#pragma unroll
+            for (int k = 0; k < kOzSlices; ++k) g[k] = G[k][j];
+            r[j] = oz_assemble<4>(g, sx + ls[j] - 48);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < CW; ++j) {
+            uint32_t g[kOzSlices];
+#pragma unroll
+            for (int k = 0; k < kOzSlices; ++k) g[k] = G[k][j];
+            r[j] = oz_assemble<2>(g, sx + ls[j] - 48);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < CW; ++j)
+          if (r0 + c0 + j < P.n) outb[m + P.M2 * (int64_t)(r0 + c0 + j)] = r[j];
+      }
       if (++buf == P.nbuf) {
         buf = 0;
         aph ^= 1;
@@ -554,6 +693,7 @@ struct OzState {
   double* tmp[2] = {nullptr, nullptr};
   int batch = 0;  // tensors the bound workspace holds
   int smem_optin = 0;
+  int sms = 0;    // streaming multiprocessors of the device
   int ntile = 0;  // rows of L per GEMM tile (0: by size)
   std::map<std::tuple<const void*, uint64_t, uint64_t, uint32_t, uint64_t>, CUtensorMap> maps;
 };
@@ -588,6 +728,7 @@ phiks_status oz_create(OzState** out, int d, const int64_t* n, int64_t N) {
   for (int mu = 0; mu < d; ++mu) s->n[mu] = n[mu];
   s->N = N;
   s->smem_optin = (int)prop.sharedMemPerBlockOptin;
+  s->sms = prop.multiProcessorCount;
   if (dev_malloc((void**)&s->status, sizeof(int)) != cudaSuccess ||
       cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess) {
     dev_free(s->status);
@@ -644,8 +785,7 @@ namespace {
 template <int NT>
 cudaError_t run_oz_gemm(OzState* s, const CUtensorMap& mA, const OzMaps& mB, const OzParams& P,
                         cudaStream_t st) {
-  constexpr uint32_t STAGE = kOzSlices * (BM * 128 + NT * 128);
-  const size_t smem = STAGE + 1024 + 256;  // alignment slack, barriers
+  const size_t smem = P.stage_bytes + 1024 + 256;  // alignment slack, barriers
   if ((int)smem > s->smem_optin) return cudaErrorInvalidConfiguration;
   auto kern = oz_gemm_kernel<NT>;
   static int set[64] = {0};
@@ -657,7 +797,12 @@ cudaError_t run_oz_gemm(OzState* s, const CUtensorMap& mA, const OzMaps& mB, con
     if (e != cudaSuccess) return e;
     set[dev] = 1;
   }
-  const int grid = P.num_tiles < 152 ? P.num_tiles : 152;
+  // the fewest CTAs that still give every CTA at most ceil(tiles / SMs)
+  // tiles: the same makespan, and the SMs left over take the work that runs
+  // beside the pass (the next squaring level's small exponentials)
+  const int sms = s->sms > 0 ? s->sms : 152;
+  const int per = (P.num_tiles + sms - 1) / sms;
+  const int grid = (P.num_tiles + per - 1) / per;
   count_launch();
   return launch_pdl(kern, dim3(grid), dim3(NTH), smem, st, mA, mB, P);
 }
@@ -769,6 +914,8 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, co
     P.tpt = (M2 + BM - 1) / BM;
     P.num_tiles = (int)((mixed ? B * P.tpt : (rows + BM - 1) / BM) * P.n_ntiles);
     P.nbuf = (2 * kOzSlices * NT <= 512) ? 2 : 1;
+    P.resident = (P.nk == 1 && P.n_ntiles <= kOzMaxColTiles) ? 1 : 0;
+    P.stage_bytes = (uint32_t)kOzSlices * (BM * 128 + (P.resident ? P.n_ntiles : 1) * NT * 128);
     int cols = 32;
     while (cols < P.nbuf * kOzSlices * NT) cols <<= 1;
     P.tmem_cols = cols;
