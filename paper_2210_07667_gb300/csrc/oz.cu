@@ -240,12 +240,21 @@ __device__ __forceinline__ double oz_assemble(const uint32_t* G, int e) {
   for (int k = 0; k < kOzSlices; ++k)
     g[k] = k < NM ? __float_as_int(__uint_as_float(G[k]) + 12582912.0f) - 0x4B400000
                   : __float2int_rn(__uint_as_float(G[k]));
-  long long hi = (long long)(g[0] * 256 + g[1]);
-  hi = hi * 256 + g[2];
-  hi = hi * 256 + g[3];
-  long long lo = (long long)g[4] * 256 + g[5];
-  lo = lo * 256 + g[6];
-  const long long S = hi * 65536 + (lo >> 8);
+  long long S;
+  if constexpr (NM >= 4) {
+    // n <= 64, |G_k| <= (k + 1) 2^20: with T = A 2^40 + B 2^24 + C 2^8 + G_6,
+    // A = 2^8 G_0 + G_1, B = 2^8 G_2 + G_3, C = 2^8 G_4 + G_5, the partial
+    // sums and C + floor(G_6 / 2^8) fit 32 bits (below 2^31 in magnitude)
+    const int A = g[0] * 256 + g[1], B = g[2] * 256 + g[3], C = g[4] * 256 + g[5] + (g[6] >> 8);
+    S = (long long)A * 4294967296ll + (long long)B * 65536ll + (long long)C;
+  } else {
+    long long hi = (long long)(g[0] * 256 + g[1]);
+    hi = hi * 256 + g[2];
+    hi = hi * 256 + g[3];
+    long long lo = (long long)g[4] * 256 + g[5];
+    lo = lo * 256 + g[6];
+    S = hi * 65536 + (lo >> 8);
+  }
   if (S == 0) return 0.0;
   const long long d = __double_as_longlong(__ll2double_rn(S));
   const int be = (int)((d >> 52) & 0x7FF) + e + 8;  // biased exponent of the result
@@ -300,13 +309,21 @@ constexpr int kOzEpiWarps = 16;
 constexpr int NTH = 64 + 32 * kOzEpiWarps;
 constexpr int kOzMaxColTiles = 4;  // column tiles of a resident B (n <= 64, NT >= 16)
 
-// This CTA's tiles: a contiguous range of the tile order (row tile major), so
-// that consecutive tiles of a CTA mostly share their row tile.
-__device__ __forceinline__ void oz_tile_range(const OzParams& P, int* t0, int* t1) {
+// This CTA's tiles t0, t0 + step, ... below t1.  Resident form: a contiguous
+// range of the tile order (row tile major), so that consecutive tiles of a
+// CTA mostly share their row tile; streaming form: every gridDim-th tile.
+__device__ __forceinline__ void oz_tile_range(const OzParams& P, int* t0, int* t1, int* step) {
   const int G = (int)gridDim.x, c = (int)blockIdx.x;
+  if (!P.resident) {
+    *t0 = c;
+    *t1 = P.num_tiles;
+    *step = G;
+    return;
+  }
   const int base = P.num_tiles / G, rem = P.num_tiles % G;
   *t0 = c * base + min(c, rem);
   *t1 = *t0 + base + (c < rem ? 1 : 0);
+  *step = 1;
 }
 
 // Per tile: A = 7 digit planes of 128 fibres x 64 K, B = 7 digit planes of
@@ -372,8 +389,8 @@ __global__ void __launch_bounds__(NTH, 1)
   const uint32_t tmem_base = *tmem_slot;
   pdl_wait();  // the digit planes and scales come from the kernels before
 
-  int t_begin = 0, t_end = 0;
-  oz_tile_range(P, &t_begin, &t_end);
+  int t_begin = 0, t_end = 0, t_step = 1;
+  oz_tile_range(P, &t_begin, &t_end, &t_step);
   uint8_t* const smemB = smem + kOzSlices * A_SLICE;
   if (warp == 0) {
     if (lane == 0 && P.resident) {
@@ -422,7 +439,7 @@ __global__ void __launch_bounds__(NTH, 1)
     } else if (lane == 0) {
       uint32_t ph = 0;
       int issued = 0;
-      for (int t = t_begin; t < t_end; ++t) {
+      for (int t = t_begin; t < t_end; t += t_step) {
         int tb = 0;
         int m0 = (int)oz_tile_row0(P, t / P.n_ntiles, &tb);
         if (P.shared_a) m0 -= (int)(tb * P.M2);  // the one split input
@@ -458,7 +475,7 @@ __global__ void __launch_bounds__(NTH, 1)
       uint32_t ph = 0, aph = 0, apar = 0, bmask = 0, bpar = 0;
       int buf = 0, prev_rt = -1, prev_tb = -1;
       bool ok = true, any = false;
-      for (int t = t_begin; t < t_end && ok; ++t) {
+      for (int t = t_begin; t < t_end && ok; t += t_step) {
         const int rt = t / P.n_ntiles, ct = t % P.n_ntiles;
         if (!mbar_wait(&tempty[buf], aph ^ 1, P.status, 12)) {
           ok = false;
@@ -556,7 +573,7 @@ __global__ void __launch_bounds__(NTH, 1)
     const int row = q * 32 + lane;
     int buf = 0;
     uint32_t aph = 0;
-    for (int t = t_begin; t < t_end; ++t) {
+    for (int t = t_begin; t < t_end; t += t_step) {
       // the tile's fibre and row exponents first: their loads run while the
       // MMAs finish (none of them depends on this tile's accumulators)
       int tb = 0;
@@ -797,12 +814,13 @@ cudaError_t run_oz_gemm(OzState* s, const CUtensorMap& mA, const OzMaps& mB, con
     if (e != cudaSuccess) return e;
     set[dev] = 1;
   }
-  // the fewest CTAs that still give every CTA at most ceil(tiles / SMs)
-  // tiles: the same makespan, and the SMs left over take the work that runs
-  // beside the pass (the next squaring level's small exponentials)
+  // resident form: the fewest CTAs that still give every CTA at most
+  // ceil(tiles / SMs) tiles: the same makespan, and the SMs left over take
+  // the work that runs beside the pass (the next squaring level's small
+  // exponentials); the streaming form, bound by its copies, takes every SM
   const int sms = s->sms > 0 ? s->sms : 152;
   const int per = (P.num_tiles + sms - 1) / sms;
-  const int grid = (P.num_tiles + per - 1) / per;
+  const int grid = P.resident ? (P.num_tiles + per - 1) / per : std::min(P.num_tiles, sms);
   count_launch();
   return launch_pdl(kern, dim3(grid), dim3(NTH), smem, st, mA, mB, P);
 }

@@ -493,7 +493,6 @@ struct TcState {
   int batch = 0;     // tensors the bound workspace holds
   int last_res = 1;  // plane set holding the last call's results
   int smem_optin = 0;
-  int sms = 0;  // streaming multiprocessors of the device
   int ntiles_mult = 0;  // tuned: N tiles per pass, times the minimum (0: by size)
   // encoded tensor maps by (address, inner extent, rows, box rows): encoding
   // costs microseconds of host time, a lookup does not
@@ -570,7 +569,6 @@ phiks_status tc_create(TcState** out, int dtype, int d, const int64_t* n, int64_
   for (int mu = 0; mu < d; ++mu) s->n[mu] = n[mu];
   s->N = N;
   s->smem_optin = (int)prop.sharedMemPerBlockOptin;
-  s->sms = prop.multiProcessorCount;
   if (dev_malloc((void**)&s->status, sizeof(int)) != cudaSuccess ||
       cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess) {
     dev_free(s->status);
@@ -672,12 +670,7 @@ cudaError_t run_gemm(TcState* s, const CUtensorMap* mA, const TcMapsB& mB, GemmP
   }
   // With 512 TMEM columns the shared memory (>= 4 x 34 KiB) already keeps a
   // second CTA off the SM, so co-resident CTAs never oversubscribe TMEM.
-  // the fewest CTAs that still give every CTA at most ceil(tiles / SMs)
-  // tiles (strided): the same makespan, and the SMs left over take the work
-  // that runs beside the pass (the next squaring level's small exponentials)
-  const int sms = s->sms > 0 ? s->sms : 152;
-  const int per = (P.num_tiles + sms - 1) / sms;
-  const int grid = (P.num_tiles + per - 1) / per;
+  int grid = P.num_tiles < 152 ? P.num_tiles : 152;
   count_launch();
   return launch_pdl(kern, dim3(grid), dim3(NTHREADS), smem, st, mA[0], mA[1], mB, P);
 }

@@ -178,3 +178,53 @@ def test_a_dropped_term_breaks_the_bound():
     T = sum(g << (8 * (DIGITS - 1 - k)) for k, g in enumerate(G))
     wrong = math.ldexp(float(T >> 8), kx + kl + 56)
     assert abs(Fraction(wrong) - exact_dot(x, l)) > Fraction(bound(x, l, wrong))
+
+
+def _as_f32_bits(v):
+    return int(np.array([v], dtype=np.float32).view(np.int32)[0])
+
+
+@pytest.mark.parametrize("n", [8, 36, 64, 128])
+def test_fp32_add_conversion_is_exact_where_the_epilogue_uses_it(n):
+    """G_k + 1.5 2^23 in FP32, minus the bit pattern of 1.5 2^23, is G_k for
+    |G_k| <= 2^22: the epilogue uses it for the accumulators k with
+    (k + 1) n <= 256 (all seven for n <= 36, four for n <= 64, two for n <= 128)."""
+    nm = {8: 7, 36: 7, 64: 4, 128: 2}[n]
+    magic = _as_f32_bits(12582912.0)
+    assert magic == 0x4B400000
+    for k in range(nm):
+        bound = (k + 1) * n * 2 ** 14
+        assert bound <= 2 ** 22
+        for g in (-bound, -bound + 1, -1, 0, 1, bound - 1, bound, 12345, -777777):
+            if abs(g) > bound:
+                continue
+            s = np.float32(g) + np.float32(12582912.0)
+            assert _as_f32_bits(s) - magic == g, (k, g)
+    # one past the bound would not be exact: 2^22 + 1 lands above 2^24
+    s = np.float32(2 ** 22 + 1) + np.float32(12582912.0)
+    assert _as_f32_bits(s) - magic != 2 ** 22 + 1
+
+
+def _i32(v):
+    assert -2 ** 31 <= v < 2 ** 31, v   # the kernel's 32-bit partial sums must not wrap
+    return v
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_partial_sum_assembly_matches_the_64_bit_one(seed):
+    """For n <= 64 the epilogue forms S = floor(T / 2^8) from 32-bit partial
+    sums A = 2^8 G_0 + G_1, B = 2^8 G_2 + G_3, C = 2^8 G_4 + G_5 + floor(G_6 / 2^8)
+    as S = A 2^32 + B 2^16 + C; this is the sum T = sum_k 2^(8 (6 - k)) G_k
+    floored, and no partial sum leaves 32 bits at the largest |G_k|."""
+    rng = random.Random(seed)
+    n = 64
+    bounds = [(k + 1) * n * 2 ** 14 for k in range(DIGITS)]
+    cases = [[b for b in bounds], [-b for b in bounds], [0] * DIGITS]
+    cases += [[rng.randint(-b, b) for b in bounds] for _ in range(2000)]
+    for g in cases:
+        A = _i32(g[0] * 256 + g[1])
+        B = _i32(g[2] * 256 + g[3])
+        C = _i32(g[4] * 256 + g[5] + (g[6] >> 8))
+        S = A * 2 ** 32 + B * 2 ** 16 + C
+        T = sum(gk * 2 ** (8 * (6 - k)) for k, gk in enumerate(g))
+        assert S == T // 256
