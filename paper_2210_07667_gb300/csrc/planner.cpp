@@ -9,8 +9,10 @@
 // | int_0^{2 pi} k_q(z) f_l(z, w) (r e^{i zeta} - e^{-i zeta}/(16 r)) dzeta |,
 // f_l(z, w) = z^{l-1}/(l-1)! exp((1 - z) w).
 //
-// Readings of what the paper leaves open: r minimised over 24 log-spaced
-// values in [0.3, 8] separately for each (q, s, l); the boundary of Xi sampled
+// Readings of what the paper leaves open: the integral does not depend on r
+// (Cauchy), so each trapezoidal value plus its estimated numerical error is
+// minimised over 24 log-spaced values of r in [0.3, 8] separately for each
+// (q, s, l); the boundary of Xi sampled
 // with 64 points per side; the zeta integral by the 128-point trapezoidal
 // rule; k_q by 128-point Gauss-Legendre in t; stopping rule: s = 0, 1, ...,
 // q_s the smallest feasible q, stop at the first s whose T# exceeds the
@@ -447,15 +449,16 @@ void remainder_bounds(const Rect& xi, int s, const std::vector<int>& qs, int p, 
       z[m] = r * e + 0.5 + ei / (16.0 * r);
       dz[m] = r * e - ei / (16.0 * r);
     }
-    // exp((1 - z_m) w) as separate real and imaginary arrays, [w][m]
-    std::vector<double> Er(nw * kNZeta), Ei(nw * kNZeta);
+    // exp((1 - z_m) w) as separate real and imaginary arrays and moduli, [w][m]
+    std::vector<double> Er(nw * kNZeta), Ei(nw * kNZeta), Ea(nw * kNZeta);
     for (size_t iw = 0; iw < nw; ++iw)
       for (int m = 0; m < kNZeta; ++m) {
         cd e = std::exp((1.0 - z[m]) * w[iw]);
         Er[iw * kNZeta + m] = e.real();
         Ei[iw * kNZeta + m] = e.imag();
+        Ea[iw * kNZeta + m] = std::abs(e);
       }
-    std::vector<double> cr(kNZeta), ci(kNZeta);
+    std::vector<double> cr(kNZeta), ci(kNZeta), ca(kNZeta);
     for (size_t iq = 0; iq < nq; ++iq) {
       const std::vector<cd>& k = cached_kernel(rule, qs[iq], ir, z);
       for (int l = 1; l <= p; ++l) {
@@ -464,18 +467,32 @@ void remainder_bounds(const Rect& xi, int s, const std::vector<int>& qs, int p, 
           cd c = k[m] * std::pow(z[m], l - 1) / fl * dz[m];
           cr[m] = c.real();
           ci[m] = c.imag();
+          ca[m] = std::abs(c);
         }
+        // the integral is the same for every r (Cauchy): each value carries
+        // its estimated numerical error, the rule on every other node
+        // (|I_N - I_N/2|) and rounding (N 2^-53 sum |terms|), so that a value
+        // small only because it is inaccurate is not the minimum over r
         double mx = 0;
         bool bad = false;
         for (size_t iw = 0; iw < nw; ++iw) {
           const double* er = &Er[iw * kNZeta];
           const double* ei = &Ei[iw * kNZeta];
-          double sr = 0, si = 0;
+          const double* ea = &Ea[iw * kNZeta];
+          double sr = 0, si = 0, hr = 0, hi = 0, sa = 0;
           for (int m = 0; m < kNZeta; ++m) {
-            sr += cr[m] * er[m] - ci[m] * ei[m];
-            si += cr[m] * ei[m] + ci[m] * er[m];
+            const double tr = cr[m] * er[m] - ci[m] * ei[m];
+            const double ti = cr[m] * ei[m] + ci[m] * er[m];
+            sr += tr;
+            si += ti;
+            if ((m & 1) == 0) {
+              hr += tr;
+              hi += ti;
+            }
+            sa += ca[m] * ea[m];
           }
-          const double a = std::hypot(sr, si);
+          const double a = std::hypot(sr, si) + std::hypot(sr - 2.0 * hr, si - 2.0 * hi) +
+                           kNZeta * std::ldexp(1.0, -53) * sa;
           if (!std::isfinite(a)) {
             bad = true;
             break;

@@ -354,3 +354,57 @@ def test_numerical_range_rectangle_contains_spectrum_and_range():
         x = rng.standard_normal(15) + 1j * rng.standard_normal(15)
         r = np.vdot(x, A @ x) / np.vdot(x, x)
         assert xlo - 1e-9 <= r.real <= xhi + 1e-9 and ylo - 1e-9 <= r.imag <= yhi + 1e-9
+
+
+def _scalar_remainder(w, q, l, rule="gll"):
+    """|R_q(f_l(., w))| for a scalar w: the exact integral
+    int_0^1 t^(l-1)/(l-1)! exp((1-t) w) dt (= phi_l(w)) minus the rule, in
+    40-digit arithmetic (nodes and weights as the oracle stores them)."""
+    nodes, weights = quadrature.rule(rule, q)
+    wm = mp.mpc(w)
+    f = lambda t: t ** (l - 1) / mp.factorial(l - 1) * mp.exp((1 - t) * wm)
+    with mp.workdps(40):
+        exact = mp.quad(f, [0, 1])
+        approx = mp.fsum(mp.mpf(float(c)) * f(mp.mpf(float(t))) for t, c in zip(nodes, weights))
+        return float(abs(exact - approx))
+
+
+@pytest.mark.parametrize("w", [-5.0, -1.5 + 2j, 0.3, -20.0, 3.0, -0.5j, -40.0, 8.0, -10 + 10j])
+@pytest.mark.parametrize("rule", ["gll", "gl"])
+def test_remainder_bound_is_the_crouzeix_palencia_constant_times_the_scalar_remainder(w, rule):
+    """For a scalar operator the contour integral of eq. (CPestimate) is the
+    quadrature remainder itself (Cauchy), so the estimate must be (1 + sqrt 2)
+    times |R_q(f_l(., w/2^s))|: this pins the constant, the kernel k_q, f_l,
+    the contour and the scaling by 2^s at once, and shows the estimate
+    dominates the remainder.  Cases whose remainder is below 1e-12 are left
+    out (the rule's stored nodes and weights carry errors of order 1e-16)."""
+    w = complex(w)
+    rect = (w.real, w.real, w.imag, w.imag)
+    checked = 0
+    for s in (0, 2):
+        for q in (3, 5, 8, 12):
+            b = params.remainder_bounds(rect, s, q, 3, rule)
+            for l in range(1, 4):
+                true = _scalar_remainder(w / 2 ** s, q, l, rule)
+                if true < 1e-12:
+                    continue
+                ratio = b[l - 1] / true
+                assert 2.40 <= ratio <= 2.42, (w, s, q, l, b[l - 1], true)
+                checked += 1
+    assert checked >= 3
+
+
+def test_remainder_bound_dominates_on_a_diagonal_operator():
+    """A diagonal K (eigenvalues on a segment of the real axis and on a
+    vertical segment): the estimate bounds ||R_q(f_l(., K))||_2 = max_i
+    |R_q(f_l(., lambda_i))| and exceeds it by at most (1 + sqrt 2) times the
+    largest remainder on the rectangle's sampled boundary."""
+    for lam in (np.linspace(-30.0, -0.5, 7), 1j * np.linspace(-6.0, 6.0, 5) - 2.0):
+        rect = (lam.real.min(), lam.real.max(), lam.imag.min(), lam.imag.max())
+        for s, q in ((0, 6), (1, 5), (3, 4)):
+            b = params.remainder_bounds(rect, s, q, 2)
+            for l in (1, 2):
+                rem = [_scalar_remainder(x / 2 ** s, q, l) for x in lam]
+                on_boundary = [_scalar_remainder(x / 2 ** s, q, l) for x in params.rect_boundary(rect)[::8]]
+                assert b[l - 1] >= max(rem), (s, q, l)
+                assert b[l - 1] <= 2.42 * max(on_boundary + rem) * 1.05, (s, q, l)
