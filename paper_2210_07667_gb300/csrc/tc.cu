@@ -230,16 +230,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           tc_fence_after();
           const uint32_t st = smem_u32(smem + (size_t)s * stage_bytes);
-          const uint32_t a0 = st, a1 = st + a_plane;
-          const uint32_t b0 = st + NP * a_plane, b1 = b0 + b_plane;
+          // descriptors of the stage's planes at K step 0; a K step moves the
+          // start address field only (16-byte units, no carry out of it)
+          const uint64_t da0 = sdesc_sw128(st), da1 = sdesc_sw128(st + a_plane);
+          const uint64_t db0 = sdesc_sw128(st + NP * a_plane), db1 = sdesc_sw128(st + NP * a_plane + b_plane);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {  // 4 x 32-byte K steps per 128-byte chunk
-            const uint32_t off = kk * 32;
+            const uint64_t off = (uint64_t)((kk * 32) >> 4);
             const uint32_t acc = (kc | kk) != 0;
-            umma<KIND>(dtm, sdesc_sw128(a0 + off), sdesc_sw128(b0 + off), idesc, acc);
+            umma<KIND>(dtm, da0 + off, db0 + off, idesc, acc);
             if (NP == 2) {
-              umma<KIND>(dtm, sdesc_sw128(a0 + off), sdesc_sw128(b1 + off), idesc, 1);
-              umma<KIND>(dtm, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, 1);
+              umma<KIND>(dtm, da0 + off, db1 + off, idesc, 1);
+              umma<KIND>(dtm, da1 + off, db0 + off, idesc, 1);
             }
           }
           any = true;
@@ -280,21 +282,51 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int64_t bt = valid ? (P.mixed ? tb : colb / P.M2) : 0;
       const int64_t col = colb - bt * P.M2 + bt * P.N;  // tensor b's elements start at b N
       const int cend = P.n - r0 < P.ntile ? P.n - r0 : P.ntile;
-      for (int c0 = 16 * grp; c0 < cend; c0 += 16 * GROUPS) {
-        float v[16];
-        tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * P.ntile + c0), v);
-        if (!valid) continue;
+      const uint32_t tl = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * P.ntile);
+      if (P.ntile <= 32 * GROUPS) {
+        // at most two 16-column chunks per warp: both in registers, then the
+        // TMEM set is released before the stores (a later tile's MMAs run
+        // under them)
+        uint32_t u[2][16];
+        const int c0 = 16 * grp, c1 = c0 + 16 * GROUPS;
+        if (c0 < cend) tmem_ld16_nowait(tl + (uint32_t)c0, u[0]);
+        if (c1 < cend) tmem_ld16_nowait(tl + (uint32_t)c1, u[1]);
+        tmem_wait_ld();
+        tc_fence_before();
+        mbar_arrive(&tempty[buf]);
+        if (valid) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int i = r0 + c0 + j;
-          if (i >= P.n) break;
-          const int64_t idx = col + P.M2 * (int64_t)i;
-          if (!P.last) split_store_f<KIND, NP>(P.out0, P.out1, idx, v[j]);
-          else ((float*)P.out0)[idx] = v[j];
+          for (int h = 0; h < 2; ++h) {
+            const int cb = h ? c1 : c0;
+            if (cb >= cend) break;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int i = r0 + cb + j;
+              if (i >= P.n) break;
+              const int64_t idx = col + P.M2 * (int64_t)i;
+              const float x = __uint_as_float(u[h][j]);
+              if (!P.last) split_store_f<KIND, NP>(P.out0, P.out1, idx, x);
+              else ((float*)P.out0)[idx] = x;
+            }
+          }
         }
+      } else {
+        for (int c0 = 16 * grp; c0 < cend; c0 += 16 * GROUPS) {
+          float v[16];
+          tmem_ld16(tl + (uint32_t)c0, v);
+          if (!valid) continue;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int i = r0 + c0 + j;
+            if (i >= P.n) break;
+            const int64_t idx = col + P.M2 * (int64_t)i;
+            if (!P.last) split_store_f<KIND, NP>(P.out0, P.out1, idx, v[j]);
+            else ((float*)P.out0)[idx] = v[j];
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty[buf]);
       }
-      tc_fence_before();
-      mbar_arrive(&tempty[buf]);
       if (++buf == 2) {
         buf = 0;
         aph ^= 1;
