@@ -309,21 +309,13 @@ constexpr int kOzEpiWarps = 16;
 constexpr int NTH = 64 + 32 * kOzEpiWarps;
 constexpr int kOzMaxColTiles = 4;  // column tiles of a resident B (n <= 64, NT >= 16)
 
-// This CTA's tiles t0, t0 + step, ... below t1.  Resident form: a contiguous
-// range of the tile order (row tile major), so that consecutive tiles of a
-// CTA mostly share their row tile; streaming form: every gridDim-th tile.
-__device__ __forceinline__ void oz_tile_range(const OzParams& P, int* t0, int* t1, int* step) {
+// This CTA's tiles: a contiguous range of the tile order (row tile major), so
+// that consecutive tiles of a CTA mostly share their row tile.
+__device__ __forceinline__ void oz_tile_range(const OzParams& P, int* t0, int* t1) {
   const int G = (int)gridDim.x, c = (int)blockIdx.x;
-  if (!P.resident) {
-    *t0 = c;
-    *t1 = P.num_tiles;
-    *step = G;
-    return;
-  }
   const int base = P.num_tiles / G, rem = P.num_tiles % G;
   *t0 = c * base + min(c, rem);
   *t1 = *t0 + base + (c < rem ? 1 : 0);
-  *step = 1;
 }
 
 // Per tile: A = 7 digit planes of 128 fibres x 64 K, B = 7 digit planes of
@@ -339,12 +331,13 @@ __device__ __forceinline__ void oz_tile_range(const OzParams& P, int* t0, int* t
 // equal share of the NT columns); two TMEM accumulator sets let a tile's
 // MMAs run during the previous tile's epilogue.
 //
-// Resident form (n <= 64: one K chunk): a CTA's tiles are consecutive, the
-// A planes of a row tile (112 KiB) are loaded once for all of its column
-// tiles, and each column tile's B planes once per tensor (one slot and one
-// barrier per column tile), so that the copies of the next row tile overlap
-// the epilogues of the current one.  Streaming form (n > 64): every tile
-// streams its K chunks of A and B through the one stage.
+// This kernel is the resident form (n <= 64: one K chunk): a CTA's tiles are
+// consecutive, the A planes of a row tile (112 KiB) are loaded once for all of
+// its column tiles, and each column tile's B planes once per tensor (one slot
+// and one barrier per column tile), so that the copies of the next row tile
+// overlap the epilogues of the current one.  n > 64 runs
+// oz_gemm_stream_kernel below, which streams every tile's K chunks of A and B
+// through one stage.
 
 template <int NT>
 __global__ void __launch_bounds__(NTH, 1)
@@ -389,11 +382,11 @@ __global__ void __launch_bounds__(NTH, 1)
   const uint32_t tmem_base = *tmem_slot;
   pdl_wait();  // the digit planes and scales come from the kernels before
 
-  int t_begin = 0, t_end = 0, t_step = 1;
-  oz_tile_range(P, &t_begin, &t_end, &t_step);
+  int t_begin = 0, t_end = 0;
+  oz_tile_range(P, &t_begin, &t_end);
   uint8_t* const smemB = smem + kOzSlices * A_SLICE;
   if (warp == 0) {
-    if (lane == 0 && P.resident) {
+    if (lane == 0) {
       uint32_t eph = 0, bmask = 0, bever = 0, bph = 0;  // per column tile: loaded, parity of the next load
       int nA = 0;
       int prev_rt = -1, prev_tb = -1;
@@ -436,46 +429,13 @@ __global__ void __launch_bounds__(NTH, 1)
         for (int s = 0; s < kOzSlices; ++s) (void)mbar_drain(&fullA[s], (uint32_t)(nA - 1) & 1u);
       for (int c = 0; c < kOzMaxColTiles; ++c)
         if ((bever >> c) & 1u) (void)mbar_drain(&fullB[c], ((bph >> c) & 1u) ^ 1u);
-    } else if (lane == 0) {
-      uint32_t ph = 0;
-      int issued = 0;
-      for (int t = t_begin; t < t_end; t += t_step) {
-        int tb = 0;
-        int m0 = (int)oz_tile_row0(P, t / P.n_ntiles, &tb);
-        if (P.shared_a) m0 -= (int)(tb * P.M2);  // the one split input
-        const int r0 = (t % P.n_ntiles) * NT;
-        const CUtensorMap* mapB = &mapsB.b[tb];
-        bool ok = true;
-        for (int kc = 0; kc < P.nk; ++kc) {
-          if (!mbar_wait(empty, ph ^ 1, P.status, 11)) {
-            ok = false;
-            break;
-          }
-          mbar_arrive_expect_tx(fullB, kOzSlices * B_SLICE);
-#pragma unroll 1
-          for (int s = 0; s < kOzSlices; ++s)
-            tma_load_3d(smemB + s * B_SLICE, mapB, fullB, kc * 64, r0, s);
-#pragma unroll 1
-          for (int s = 0; s < kOzSlices; ++s) {
-            mbar_arrive_expect_tx(&fullA[s], A_SLICE);
-            tma_load_3d(smem + s * A_SLICE, &mapA, &fullA[s], kc * 64, m0, s);
-          }
-          ph ^= 1;
-          ++issued;
-        }
-        if (!ok) break;
-      }
-      if (issued) {  // the last copies landed (also after another role gave up)
-        (void)mbar_drain(fullB, ph ^ 1);
-        for (int s = 0; s < kOzSlices; ++s) (void)mbar_drain(&fullA[s], ph ^ 1);
-      }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      uint32_t ph = 0, aph = 0, apar = 0, bmask = 0, bpar = 0;
+      uint32_t aph = 0, apar = 0, bmask = 0, bpar = 0;
       int buf = 0, prev_rt = -1, prev_tb = -1;
       bool ok = true, any = false;
-      for (int t = t_begin; t < t_end && ok; t += t_step) {
+      for (int t = t_begin; t < t_end && ok; ++t) {
         const int rt = t / P.n_ntiles, ct = t % P.n_ntiles;
         if (!mbar_wait(&tempty[buf], aph ^ 1, P.status, 12)) {
           ok = false;
@@ -484,7 +444,7 @@ __global__ void __launch_bounds__(NTH, 1)
         tc_fence_after();
         const uint32_t d0 = tmem_base + (uint32_t)buf * SET;
         const uint32_t a0 = smem_u32(smem);
-        if (P.resident) {
+        {
           int tb = 0;
           (void)oz_tile_row0(P, rt, &tb);
           const bool newA = rt != prev_rt;
@@ -525,33 +485,6 @@ __global__ void __launch_bounds__(NTH, 1)
           }
           // the last tile on these A planes: the stage is free for the next row tile
           if (t + 1 < t_end && (t + 1) / P.n_ntiles != rt) umma_commit(empty);
-        } else {
-          const uint32_t b0 = smem_u32(smemB);
-          for (int kc = 0; kc < P.nk && ok; ++kc) {
-            if (!mbar_wait(fullB, ph, P.status, 13)) {
-              ok = false;
-              break;
-            }
-#pragma unroll 1
-            for (int at = 0; at < kOzSlices; ++at) {  // digit plane at of X times every plane of L
-              if (!mbar_wait(&fullA[at], ph, P.status, 13)) {
-                ok = false;
-                break;
-              }
-              tc_fence_after();
-#pragma unroll
-              for (int kk = 0; kk < 4; ++kk) {
-                const uint32_t first = (kc == 0 && kk == 0 && at == 0) ? 0u : 1u;
-                umma<0>(d0 + (uint32_t)(at * NT), sdesc_sw128(a0 + at * A_SLICE + kk * 32),
-                        sdesc_sw128(b0 + kk * 32), idesc_make(1, (kOzSlices - at) * NT), first);
-              }
-              any = true;
-            }
-            if (!ok) break;
-            umma_commit(empty);
-            ph ^= 1;
-          }
-          if (!ok) break;
         }
         umma_commit(&tfull[buf]);
         if (++buf == P.nbuf) {
@@ -573,7 +506,7 @@ __global__ void __launch_bounds__(NTH, 1)
     const int row = q * 32 + lane;
     int buf = 0;
     uint32_t aph = 0;
-    for (int t = t_begin; t < t_end; t += t_step) {
+    for (int t = t_begin; t < t_end; ++t) {
       // the tile's fibre and row exponents first: their loads run while the
       // MMAs finish (none of them depends on this tile's accumulators)
       int tb = 0;
@@ -620,7 +553,7 @@ __global__ void __launch_bounds__(NTH, 1)
             for (int k = 0; k < kOzSlices; ++k) g[k] = G[k][j];
             r[j] = oz_assemble<7>(g, sx + ls[j] - 48);
           }
-        } else if (P.n <= 64) {
+        } else {  // n <= 64
 #pragma unroll
           for (int j = 0; j < CW; ++j) {
             uint32_t g[kOzSlices];
@@ -628,19 +561,216 @@ __global__ void __launch_bounds__(NTH, 1)
             for (int k = 0; k < kOzSlices; ++k) g[k] = G[k][j];
             r[j] = oz_assemble<4>(g, sx + ls[j] - 48);
           }
-        } else {
-#pragma unroll
-          for (int j = 0; j < CW; ++j) {
-            uint32_t g[kOzSlices];
-#pragma unroll
-            for (int k = 0; k < kOzSlices; ++k) g[k] = G[k][j];
-            r[j] = oz_assemble<2>(g, sx + ls[j] - 48);
-          }
         }
 #pragma unroll
         for (int j = 0; j < CW; ++j)
           if (r0 + c0 + j < P.n) outb[m + P.M2 * (int64_t)(r0 + c0 + j)] = r[j];
       }
+      if (++buf == P.nbuf) {
+        buf = 0;
+        aph ^= 1;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(P.tmem_cols)
+                 : "memory");
+  }
+}
+
+// The streaming form for n > 64 (several 64-wide K chunks): every gridDim-th
+// tile streams its K chunks of A and B through one shared-memory stage
+// (112 KiB of A digits per chunk); otherwise as above (seven A-plane barriers,
+// two TMEM accumulator sets, 16 epilogue warps) with every accumulator
+// converted by a float-to-integer conversion.
+template <int NT>
+__global__ void __launch_bounds__(NTH, 1)
+    oz_gemm_stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ OzMaps mapsB,
+                   const __grid_constant__ OzParams P) {
+  static_assert(kOzSlices * NT <= 256 && (kOzSlices * NT) % 16 == 0, "MMA N out of range");
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr uint32_t A_SLICE = BM * 128;  // bytes of one digit plane of the A tile
+  constexpr uint32_t B_SLICE = NT * 128;
+  constexpr uint32_t STAGE = kOzSlices * (A_SLICE + B_SLICE);
+  constexpr uint32_t SET = kOzSlices * NT;  // TMEM columns of one accumulator set
+  uint64_t* fullA = (uint64_t*)(smem + STAGE);  // [7]: plane t of A landed
+  uint64_t* fullB = fullA + kOzSlices;          // all planes of B landed
+  uint64_t* empty = fullB + 1;
+  uint64_t* tfull = empty + 1;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* mdone = tempty + 2;  // the MMA warp's issued MMAs finished (failure path)
+  uint32_t* tmem_slot = (uint32_t*)(mdone + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < kOzSlices; ++t) mbar_init(&fullA[t], 1);
+    mbar_init(fullB, 1);
+    mbar_init(empty, 1);
+    mbar_init(mdone, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 32 * kOzEpiWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(P.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  pdl_wait();  // the digit planes and scales come from the kernels before
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t ph = 0;
+      int issued = 0;
+      for (int t = blockIdx.x; t < P.num_tiles; t += gridDim.x) {
+        int tb = 0;
+        int m0 = (int)oz_tile_row0(P, t / P.n_ntiles, &tb);
+        if (P.shared_a) m0 -= (int)(tb * P.M2);  // the one split input
+        const int r0 = (t % P.n_ntiles) * NT;
+        const CUtensorMap* mapB = &mapsB.b[tb];
+        bool ok = true;
+        for (int kc = 0; kc < P.nk; ++kc) {
+          if (!mbar_wait(empty, ph ^ 1, P.status, 11)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(fullB, kOzSlices * B_SLICE);
+#pragma unroll 1
+          for (int s = 0; s < kOzSlices; ++s)
+            tma_load_3d(smem + kOzSlices * A_SLICE + s * B_SLICE, mapB, fullB, kc * 64, r0, s);
+#pragma unroll 1
+          for (int s = 0; s < kOzSlices; ++s) {
+            mbar_arrive_expect_tx(&fullA[s], A_SLICE);
+            tma_load_3d(smem + s * A_SLICE, &mapA, &fullA[s], kc * 64, m0, s);
+          }
+          ph ^= 1;
+          ++issued;
+        }
+        if (!ok) break;
+      }
+      if (issued) {  // the last copies landed (also after another role gave up)
+        (void)mbar_drain(fullB, ph ^ 1);
+        for (int s = 0; s < kOzSlices; ++s) (void)mbar_drain(&fullA[s], ph ^ 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t ph = 0, aph = 0;
+      int buf = 0;
+      bool ok = true, any = false;
+      for (int t = blockIdx.x; t < P.num_tiles && ok; t += gridDim.x) {
+        if (!mbar_wait(&tempty[buf], aph ^ 1, P.status, 12)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d0 = tmem_base + (uint32_t)buf * SET;
+        for (int kc = 0; kc < P.nk && ok; ++kc) {
+          const uint32_t a0 = smem_u32(smem), b0 = a0 + kOzSlices * A_SLICE;
+          if (!mbar_wait(fullB, ph, P.status, 13)) {
+            ok = false;
+            break;
+          }
+#pragma unroll 1
+          for (int at = 0; at < kOzSlices; ++at) {  // digit plane at of X times every plane of L
+            if (!mbar_wait(&fullA[at], ph, P.status, 13)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t first = (kc == 0 && kk == 0 && at == 0) ? 0u : 1u;
+              umma<0>(d0 + (uint32_t)(at * NT), sdesc_sw128(a0 + at * A_SLICE + kk * 32),
+                      sdesc_sw128(b0 + kk * 32), idesc_make(1, (kOzSlices - at) * NT), first);
+            }
+            any = true;
+          }
+          if (!ok) break;
+          umma_commit(empty);
+          ph ^= 1;
+        }
+        if (!ok) break;
+        umma_commit(&tfull[buf]);
+        if (++buf == P.nbuf) {
+          buf = 0;
+          aph ^= 1;
+        }
+      }
+      if (!ok && any) {  // given up: the MMAs already issued finish before TMEM is freed
+        umma_commit(mdone);
+        (void)mbar_drain(mdone, 0);
+      }
+    }
+  } else {
+    const int q = warp & 3;  // TMEM lane quarter of this warp
+    constexpr int GROUPS = kOzEpiWarps / 4;   // warps per lane quarter
+    constexpr int CW = NT / GROUPS;           // columns per warp
+    constexpr int CH = CW >= 8 ? 8 : 4;       // columns per TMEM load
+    static_assert(CW % CH == 0, "epilogue column split");
+    const int grp = (warp - 2) >> 2;
+    const int row = q * 32 + lane;
+    int buf = 0;
+    uint32_t aph = 0;
+    for (int t = blockIdx.x; t < P.num_tiles; t += gridDim.x) {
+      // the tile's fibre and row exponents first: their loads run while the
+      // MMAs finish (none of them depends on this tile's accumulators)
+      int tb = 0;
+      const int64_t m0t = oz_tile_row0(P, t / P.n_ntiles, &tb);
+      const int64_t rg = m0t + row;  // fibre of the batch
+      const int r0 = (t % P.n_ntiles) * NT;
+      const bool valid = P.mixed ? (rg - (int64_t)tb * P.M2 < P.M2) : (rg < P.rows);
+      const int sx = valid ? P.xscale[P.shared_a ? rg - (int64_t)tb * P.M2 : rg] : 0;
+      const int64_t bt = valid ? (P.mixed ? tb : rg / P.M2) : 0;
+      double* const outb = P.out + bt * P.N;
+      const int64_t m = rg - bt * P.M2;
+      const int* const lscale = P.lscale[P.mixed ? tb : 0];
+      int ls[CW];  // (lscale has n_pad >= every tile's columns entries)
+#pragma unroll
+      for (int j = 0; j < CW; ++j) ls[j] = lscale[r0 + grp * CW + j];
+      if (!mbar_wait(&tfull[buf], aph, P.status, 14)) break;
+      tc_fence_after();
+#pragma unroll
+      for (int c0 = grp * CW; c0 < (grp + 1) * CW; c0 += CH) {
+        const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * SET + (uint32_t)c0;
+        uint32_t G[kOzSlices][CH];
+        if constexpr (CH == 8) {
+#pragma unroll
+          for (int k = 0; k < kOzSlices; ++k) tmem_ld8_nowait(tb + (uint32_t)(k * NT), G[k]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < kOzSlices; ++k) tmem_ld4_nowait(tb + (uint32_t)(k * NT), G[k]);
+        }
+        tmem_wait_ld();
+        if (!valid) continue;
+        // independent assemblies, then the stores of the columns below n
+        double r[CH];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+          uint32_t g[kOzSlices];
+#pragma unroll
+          for (int k = 0; k < kOzSlices; ++k) g[k] = G[k][j];
+          r[j] = oz_assemble<0>(g, sx + ls[c0 - grp * CW + j] - 48);
+        }
+#pragma unroll
+        for (int j = 0; j < CH; ++j)
+          if (r0 + c0 + j < P.n) outb[m + P.M2 * (int64_t)(r0 + c0 + j)] = r[j];
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[buf]);
       if (++buf == P.nbuf) {
         buf = 0;
         aph ^= 1;
@@ -804,15 +934,15 @@ cudaError_t run_oz_gemm(OzState* s, const CUtensorMap& mA, const OzMaps& mB, con
                         cudaStream_t st) {
   const size_t smem = P.stage_bytes + 1024 + 256;  // alignment slack, barriers
   if ((int)smem > s->smem_optin) return cudaErrorInvalidConfiguration;
-  auto kern = oz_gemm_kernel<NT>;
-  static int set[64] = {0};
+  auto kern = P.resident ? oz_gemm_kernel<NT> : oz_gemm_stream_kernel<NT>;
+  static int set[2][64] = {{0}};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  if (!set[dev]) {
+  if (!set[P.resident][dev]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, s->smem_optin);
     if (e != cudaSuccess) return e;
-    set[dev] = 1;
+    set[P.resident][dev] = 1;
   }
   // resident form: the fewest CTAs that still give every CTA at most
   // ceil(tiles / SMs) tiles: the same makespan, and the SMs left over take
