@@ -188,6 +188,107 @@ __global__ void __launch_bounds__(kSplitThreads) oz_split_kernel(const __grid_co
   if (t == fl * cpf) scale[m] = E - 1029;
 }
 
+// Fibre exponent of an all-zero fibre in the split of exact sums (below any
+// element's; the GEMM pass then assembles S = 0 for it).
+constexpr int kOzZeroExp = -(1 << 28);
+
+// Q = S 2^(e - (E - 1077)) rounded half away from zero (the fixed point of
+// oz_fixed for the value S 2^e and the fibre exponent E, with E at least the
+// biased exponent the value would have as a double: |Q| < 2^55).
+__device__ __forceinline__ long long oz_fixed_sum(long long S, int e, int E) {
+  if (S == 0) return 0;
+  const unsigned long long u = S < 0 ? 0ull - (unsigned long long)S : (unsigned long long)S;
+  const int sh = E - 1077 - e;
+  unsigned long long q;
+  if (sh <= 0) q = u << (-sh);
+  else if (sh < 64) q = (u >> sh) + ((u >> (sh - 1)) & 1ull);
+  else q = 0;
+  return S < 0 ? -(long long)q : (long long)q;
+}
+
+// The previous pass's exact sums: element idx of tensor b is S[b N + idx],
+// value S 2^(xs[m] + ls[i] - 40) with m = idx mod M2p, i = idx / M2p (the
+// previous pass's fibre and output row of its matrix).
+struct SplitSums {
+  const long long* S;
+  const int* xs;               // the previous pass's fibre exponents (row b M2p + m, or m when shared)
+  const int* ls[kOzMaxBatch];  // row exponents of tensor b's matrix of the previous mode (entry 0 unless mixed)
+  int64_t M2p;
+  uint32_t fpr;  // fibres of this pass per row i of the previous pass: M2p / n
+  int shared;
+  int mixed;
+};
+
+// The split of oz_split_kernel for a pass whose input is the previous pass's
+// exact sums (no combination): the same threads, exponents and digit planes,
+// the fibre exponent the largest value's biased exponent as a double, each
+// value rounded once to the fibre's fixed point.
+__global__ void __launch_bounds__(kSplitThreads) oz_split_sums_kernel(const __grid_constant__ SplitSums in, int n,
+                                                                      int64_t M2, int fpb, __nv_bfloat16* planes,
+                                                                      int64_t N, int64_t PS, int* scale) {
+  __shared__ int emax[kSplitThreads];
+  pdl_wait();
+  const int y = blockIdx.y;
+  planes += (int64_t)y * N;
+  scale += (int64_t)y * M2;
+  const int cpf = n >> 3;
+  const int t = threadIdx.x;
+  const int fl = t / cpf;
+  const int64_t m = (int64_t)blockIdx.x * fpb + fl;
+  const bool active = fl < fpb && m < M2;
+  const int64_t base = m * n + (int64_t)(t - fl * cpf) * 8;
+  if (t < fpb) emax[t] = kOzZeroExp;
+  long long S[8];
+  int e[8];
+  int E = kOzZeroExp;
+  if (active) {
+    const long long* p = in.S + (int64_t)y * N + base;
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      const longlong2 v = __ldg(reinterpret_cast<const longlong2*>(p + j));
+      S[j] = v.x;
+      S[j + 1] = v.y;
+    }
+    // row i of the previous pass: M2p / n whole fibres each (m < 2^32 here)
+    const uint32_t i = (uint32_t)m / in.fpr;
+    const int64_t m0 = base - (int64_t)i * in.M2p;
+    const int ls = __ldg(in.ls[in.mixed ? y : 0] + i);
+    const int4* xs = reinterpret_cast<const int4*>(in.xs + (in.shared ? 0 : (int64_t)y * in.M2p) + m0);
+    const int4 xa = __ldg(xs), xb = __ldg(xs + 1);
+    const int xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      e[j] = xv[j] + ls - 40;
+      if (S[j] != 0) {
+        const unsigned long long u = S[j] < 0 ? 0ull - (unsigned long long)S[j] : (unsigned long long)S[j];
+        E = max(E, (64 - __clzll((long long)u)) + e[j] + 1022);
+      }
+    }
+  }
+  if ((cpf & (cpf - 1)) == 0) {  // (uniform) a fibre's threads are cpf <= 32 consecutive lanes
+    for (int o = 1; o < cpf; o <<= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+  } else {
+    __syncthreads();
+    if (active) atomicMax(&emax[fl], E);
+    __syncthreads();
+    E = emax[fl];
+  }
+  if (!active) return;
+  uint32_t w[kOzSlices][4];
+#pragma unroll
+  for (int j = 0; j < 8; j += 2) {
+    float c0[kOzSlices], c1[kOzSlices];
+    oz_digits(oz_fixed_sum(S[j], e[j], E), c0);
+    oz_digits(oz_fixed_sum(S[j + 1], e[j + 1], E), c1);
+#pragma unroll
+    for (int s = 0; s < kOzSlices; ++s) w[s][j >> 1] = pack_bf16x2(c0[s], c1[s]);
+  }
+#pragma unroll
+  for (int s = 0; s < kOzSlices; ++s)
+    *reinterpret_cast<uint4*>(planes + s * PS + base) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+  if (t == fl * cpf) scale[m] = E - 1029;
+}
+
 // B digits: row i of L (column-major n x n), row-major planes n_pad x n_pad;
 // one warp per row, one grid row (blockIdx.y) per matrix of the batch.
 constexpr int kPrepBatch = 32;
@@ -234,7 +335,7 @@ __global__ void oz_prep_b_kernel(PrepBatch pb) {
 // pattern minus that of 1.5 2^23 is G_k (one FP32 add on the FMA pipe in
 // place of a float-to-integer conversion).
 template <int NM>
-__device__ __forceinline__ double oz_assemble(const uint32_t* G, int e) {
+__device__ __forceinline__ long long oz_digit_sum(const uint32_t* G) {
   int g[kOzSlices];
 #pragma unroll
   for (int k = 0; k < kOzSlices; ++k)
@@ -255,6 +356,12 @@ __device__ __forceinline__ double oz_assemble(const uint32_t* G, int e) {
     lo = lo * 256 + g[6];
     S = hi * 65536 + (lo >> 8);
   }
+  return S;
+}
+
+template <int NM>
+__device__ __forceinline__ double oz_assemble(const uint32_t* G, int e) {
+  const long long S = oz_digit_sum<NM>(G);
   if (S == 0) return 0.0;
   const long long d = __double_as_longlong(__ll2double_rn(S));
   const int be = (int)((d >> 52) & 0x7FF) + e + 8;  // biased exponent of the result
@@ -275,6 +382,8 @@ struct OzParams {
   int tmem_cols;
   int nbuf;       // TMEM accumulator sets (1 or 2)
   int resident;   // nk == 1: A kept across a row tile's column tiles, B per tensor
+  int int_out;    // store the exact digit sums S (int64, value S 2^(sx + ls - 40)) for
+                  // the next pass's split instead of rounded doubles
   uint32_t stage_bytes;  // shared memory of the A and B planes
   double* out;    // FP64 result of tensor b, rotated layout: out[b N + m + M2 i]
   const int* xscale;
@@ -541,7 +650,31 @@ __global__ void __launch_bounds__(NTH, 1)
       // later tile (which frees this row tile's A planes sooner)
       tc_fence_before();
       mbar_arrive(&tempty[buf]);
-      if (valid) {
+      if (valid && P.int_out) {
+        // the exact sums: the next pass's split takes them with their scale
+        long long* const outi = reinterpret_cast<long long*>(outb);
+        long long r[CW];
+        if (P.n <= 36) {
+#pragma unroll
+          for (int j = 0; j < CW; ++j) {
+            uint32_t g[kOzSlices];
+#pragma unroll
+            for (int k = 0; k < kOzSlices; ++k) g[k] = G[k][j];
+            r[j] = oz_digit_sum<7>(g);
+          }
+        } else {  // n <= 64
+#pragma unroll
+          for (int j = 0; j < CW; ++j) {
+            uint32_t g[kOzSlices];
+#pragma unroll
+            for (int k = 0; k < kOzSlices; ++k) g[k] = G[k][j];
+            r[j] = oz_digit_sum<4>(g);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < CW; ++j)
+          if (r0 + c0 + j < P.n) outi[m + P.M2 * (int64_t)(r0 + c0 + j)] = r[j];
+      } else if (valid) {
         // independent assemblies, then the stores of the columns below n
         double r[CW];
         // accumulators small enough for the exact FP32 conversion: (k + 1) n <= 256
@@ -845,11 +978,12 @@ struct OzState {
   std::map<std::tuple<const void*, uint64_t, uint64_t, uint32_t, uint64_t>, CUtensorMap> maps;
 };
 
-// Digit planes and fibre exponents of `batch` tensors.
+// Digit planes and two sets of fibre exponents (a pass's and its
+// predecessor's) of `batch` tensors.
 size_t oz_workspace_bytes(int d, const int64_t* n, int64_t N, int batch) {
   int64_t m2 = 0;
   for (int mu = 0; mu < d; ++mu) m2 = std::max<int64_t>(m2, N / n[mu]);
-  return up1k((size_t)kOzSlices * batch * N * 2) + up1k((size_t)batch * m2 * 4) + 1024;
+  return up1k((size_t)kOzSlices * batch * N * 2) + 2 * up1k((size_t)batch * m2 * 4) + 1024;
 }
 
 phiks_status oz_create(OzState** out, int d, const int64_t* n, int64_t N) {
@@ -998,7 +1132,13 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, co
   const int64_t N = s->N;
   const int64_t PS = (int64_t)s->batch * N;  // elements between digit planes
   __nv_bfloat16* planes = (__nv_bfloat16*)s->ws;
-  int* xscale = (int*)(s->ws + up1k((size_t)kOzSlices * PS * 2));
+  int64_t m2max = 0;
+  for (int mu = 0; mu < s->d; ++mu) m2max = std::max<int64_t>(m2max, N / s->n[mu]);
+  // fibre exponents of pass mu in xs[mu & 1]: the split of exact sums reads
+  // the previous pass's
+  int* xs[2];
+  xs[0] = (int*)(s->ws + up1k((size_t)kOzSlices * PS * 2));
+  xs[1] = (int*)((uint8_t*)xs[0] + up1k((size_t)s->batch * m2max * 4));
   // tensors with their own matrices and one and the same input (the
   // quadrature nodes of a same-vector call): the first pass splits that input
   // once and every tensor's tiles read it
@@ -1020,17 +1160,23 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, co
       cur.store[rows0] = pro->side_out[k];
     }
   double* dst = nullptr;
+  bool sums_in = false;  // the previous pass left exact sums (sin) rather than doubles
+  SplitSums sin;
+  std::memset(&sin, 0, sizeof sin);
   for (int mu = 0; mu < s->d; ++mu) {
     const int n = (int)s->n[mu];
     const int64_t M2 = N / n;
     const int64_t rows = (int64_t)B * M2;
+    int* const xscale = xs[mu & 1];
     {  // split: n / 8 threads per fibre, whole fibres per block, one grid row per tensor
       const int fpb = kSplitThreads / (n / 8);
       const int64_t blocks = (M2 + fpb - 1) / fpb;
       count_launch();
-      cudaError_t e = launch_pdl(oz_split_kernel, dim3((unsigned)blocks, (unsigned)(mu == 0 ? rows0 : B)),
-                                 dim3(kSplitThreads), 0,
-                                 st, cur, n, M2, fpb, planes, N, PS, xscale);
+      cudaError_t e =
+          sums_in ? launch_pdl(oz_split_sums_kernel, dim3((unsigned)blocks, (unsigned)B), dim3(kSplitThreads), 0, st,
+                               sin, n, M2, fpb, planes, N, PS, xscale)
+                  : launch_pdl(oz_split_kernel, dim3((unsigned)blocks, (unsigned)(mu == 0 ? rows0 : B)),
+                               dim3(kSplitThreads), 0, st, cur, n, M2, fpb, planes, N, PS, xscale);
       if (e != cudaSuccess) return e;
     }
     const int np = (n + 63) / 64 * 64;
@@ -1064,6 +1210,8 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, co
     P.nbuf = (2 * kOzSlices * NT <= 512) ? 2 : 1;
     P.resident = (P.nk == 1 && P.n_ntiles <= kOzMaxColTiles) ? 1 : 0;
     P.stage_bytes = (uint32_t)kOzSlices * (BM * 128 + (P.resident ? P.n_ntiles : 1) * NT * 128);
+    // every pass but the last leaves exact sums for the next split (resident form)
+    P.int_out = (mu + 1 < s->d && P.resident && N / s->n[mu + 1] < (1ll << 32)) ? 1 : 0;
     int cols = 32;
     while (cols < P.nbuf * kOzSlices * NT) cols <<= 1;
     P.tmem_cols = cols;
@@ -1081,6 +1229,18 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, co
     if (ev) {
       e = cudaEventRecord(ev[2 * mu + 1], st);
       if (e != cudaSuccess) return e;
+    }
+    sums_in = P.int_out != 0;
+    if (sums_in) {
+      std::memset(&sin, 0, sizeof sin);
+      sin.S = reinterpret_cast<const long long*>(dst);
+      sin.xs = xscale;
+      for (int b = 0; b < nmat; ++b) sin.ls[b] = P.lscale[b];
+      sin.M2p = M2;
+      sin.shared = P.shared_a;
+      // (the next pass's fibre count per row; its fibres number below 2^32)
+      sin.fpr = (uint32_t)(M2 / s->n[mu + 1]);
+      sin.mixed = P.mixed;
     }
     std::memset(&cur, 0, sizeof cur);
     for (int b = 0; b < B; ++b) {

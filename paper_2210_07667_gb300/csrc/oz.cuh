@@ -16,6 +16,9 @@
 // rounding x and l to the fibre's fixed point costs 2^-54 max|x| max|l| per
 // term, the dropped digit products with s + t >= 7 at most 6.03 2^-54 per
 // term (only when the low digit products all share a sign), the floor 2^-52.
+// Between the passes of one Tucker operator (n_mu <= 64) the sum is kept
+// exact: the next split takes S with its scale and rounds it once to that
+// pass's fibre fixed point, so the last term applies to the last pass only.
 #pragma once
 
 #include <cstdint>
@@ -54,8 +57,7 @@ struct OzMats {
 };
 
 // Whether the tensors of one oz_tucker call may have different matrices:
-// every mode's fibre count N / n_mu a multiple of 128 (no tile spans two
-// tensors).
+// always (every tensor is tiled on its own, its last row tile partial).
 bool oz_mixed_ok(const OzState* s);
 
 // B Tucker operators run together (B at most the `batch` given to

@@ -228,3 +228,56 @@ def test_partial_sum_assembly_matches_the_64_bit_one(seed):
         S = A * 2 ** 32 + B * 2 ** 16 + C
         T = sum(gk * 2 ** (8 * (6 - k)) for k, gk in enumerate(g))
         assert S == T // 256
+
+
+def _fixed_from_sum(S, e, E):
+    """The split of exact sums: Q = S 2^(e - (E - 1077)) rounded half away
+    from zero, by the shifts the kernel uses (arbitrary-precision integers)."""
+    if S == 0:
+        return 0
+    u = abs(S)
+    sh = E - 1077 - e
+    if sh <= 0:
+        q = u << (-sh)
+    elif sh < 64:
+        q = (u >> sh) + ((u >> (sh - 1)) & 1)
+    else:
+        q = 0
+    return -q if S < 0 else q
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_fixed_point_of_exact_sums(seed):
+    """The pass after a resident GEMM pass takes the exact sums S with value
+    S 2^e (e = fibre exponent + row exponent - 40) instead of rounded
+    doubles: the fibre exponent is the largest value's biased exponent as a
+    double, E = max(bitlength(S) + e + 1022), and every Q is the value in
+    units of 2^(E - 1077), rounded half away from zero, with |Q| <= 2^55: the
+    same fixed point the double path reaches (one rounding less)."""
+    rng = random.Random(seed)
+    for _ in range(300):
+        fib = []
+        for _ in range(8):
+            L = rng.randint(0, 62)
+            S = 0 if L == 0 else rng.choice((-1, 1)) * rng.randint(2 ** (L - 1), 2 ** L - 1)
+            fib.append((S, rng.randint(-80, 40)))
+        nz = [(S, e) for S, e in fib if S]
+        if not nz:
+            continue
+        E = max(abs(S).bit_length() + e + 1022 for S, e in nz)
+        for S, e in fib:
+            q = _fixed_from_sum(S, e, E)
+            assert abs(q) <= 2 ** 55
+            exact = Fraction(S) * Fraction(2) ** (e + 1077 - E)
+            want = math.floor(abs(exact) + Fraction(1, 2)) * (1 if exact >= 0 else -1)
+            assert q == want, (S, e, E)
+        # the largest value uses the top of the range: 2^54 <= |Q| <= 2^55
+        assert max(abs(_fixed_from_sum(S, e, E)) for S, e in nz) >= 2 ** 54
+        # as a double the same value gives the same Q once it is exactly representable
+        for S, e in nz:
+            if abs(S) < 2 ** 53 and -1000 < abs(S).bit_length() + e + 1022 < 2000:
+                x = math.ldexp(float(S), e)
+                if x != 0.0 and math.isfinite(x):
+                    m, ex = math.frexp(abs(x))                     # |x| = m 2^ex, m in [1/2, 1)
+                    bexp = ex + 1022                               # biased exponent of x
+                    assert bexp == abs(S).bit_length() + e + 1022
