@@ -215,10 +215,10 @@ def profile_roofline(dname, ms, launches, flops, kernel=None):
 
 # dram__bytes_read.sum + dram__bytes_write.sum per mu-mode product of
 # oz_gemm_kernel<32> from an ncu capture of the kernel as it stands (six
-# four-product launches of this workload, cold caches: 14.854 MB read, 0
+# four-product launches of this workload, cold caches: 14.861 MB read, 0
 # written; the summary of that capture under profiles/ gives the command);
 # None once the kernel changes
-OZ_GEMM_TRAFFIC_PER_PRODUCT = 14.854e6 / 4
+OZ_GEMM_TRAFFIC_PER_PRODUCT = 14.861e6 / 4
 # bf16 digit products the emulated pass executes per FP64 product (digit
 # planes s + t <= 6 of seven per operand)
 OZ_DIGIT_PRODUCTS = 28
