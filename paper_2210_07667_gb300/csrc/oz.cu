@@ -889,6 +889,21 @@ __global__ void __launch_bounds__(NTH, 1)
         }
         tmem_wait_ld();
         if (!valid) continue;
+        if (P.int_out) {  // the exact sums for the next pass's split ((k + 1) n <= 256 for k < 2)
+          long long* const outi = reinterpret_cast<long long*>(outb);
+          long long r[CH];
+#pragma unroll
+          for (int j = 0; j < CH; ++j) {
+            uint32_t g[kOzSlices];
+#pragma unroll
+            for (int k = 0; k < kOzSlices; ++k) g[k] = G[k][j];
+            r[j] = oz_digit_sum<2>(g);
+          }
+#pragma unroll
+          for (int j = 0; j < CH; ++j)
+            if (r0 + c0 + j < P.n) outi[m + P.M2 * (int64_t)(r0 + c0 + j)] = r[j];
+          continue;
+        }
         // independent assemblies, then the stores of the columns below n
         double r[CH];
 #pragma unroll
@@ -1210,8 +1225,8 @@ cudaError_t oz_tucker(OzState* s, int B, const Combo* in, const OzMats* mats, co
     P.nbuf = (2 * kOzSlices * NT <= 512) ? 2 : 1;
     P.resident = (P.nk == 1 && P.n_ntiles <= kOzMaxColTiles) ? 1 : 0;
     P.stage_bytes = (uint32_t)kOzSlices * (BM * 128 + (P.resident ? P.n_ntiles : 1) * NT * 128);
-    // every pass but the last leaves exact sums for the next split (resident form)
-    P.int_out = (mu + 1 < s->d && P.resident && N / s->n[mu + 1] < (1ll << 32)) ? 1 : 0;
+    // every pass but the last leaves exact sums for the next split
+    P.int_out = (mu + 1 < s->d && N / s->n[mu + 1] < (1ll << 32)) ? 1 : 0;
     int cols = 32;
     while (cols < P.nbuf * kOzSlices * NT) cols <<= 1;
     P.tmem_cols = cols;
