@@ -176,6 +176,11 @@ struct phiks_plan_s {
   int64_t m[PHIKS_MAX_D] = {0};
   std::vector<std::vector<double>> A;
   double sigma[PHIKS_MAX_D] = {0};
+  // alias[mu]: the first mode with the same matrix as mode mu (mu itself if
+  // none): identical modes (an isotropic operator, such as the Laplacian in
+  // every direction) share their small exponentials and B-operand planes,
+  // computed once
+  int alias[PHIKS_MAX_D] = {0};
   double norm1_shifted[PHIKS_MAX_D] = {0};
   Rect rect[PHIKS_MAX_D];
   double* dAs = nullptr;  // device: A_mu - sigma_mu I, concatenated
@@ -781,6 +786,10 @@ phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool 
   size_t tot = 0;
   for (int b = 0; b < nbk; ++b)
     for (int mu = 0; mu < P->d; ++mu) {
+      if (P->alias[mu] != mu) {  // the same matrix as an earlier mode: its exponentials
+        nb.off[b][mu] = nb.off[b][P->alias[mu]];
+        continue;
+      }
       nb.off[b][mu] = tot;
       tot += (size_t)P->m[mu] * P->m[mu];
     }
@@ -816,6 +825,7 @@ phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool 
   const double scale = std::ldexp(tau, -s);
   for (int b = 0; b < nbk; ++b)
     for (int mu = 0; mu < P->d; ++mu) {
+      if (P->alias[mu] != mu) continue;
       ExpmJob j;
       j.n = (int)P->m[mu];
       j.Ashift = P->dAs + P->offA[mu];
@@ -849,6 +859,10 @@ phiks_status get_bank(phiks_plan_s* P, double tau, int s, int q, int rule, bool 
     std::vector<void*> dsts;
     for (int b = 0; b < nbk; ++b)
       for (int mu = 0; mu < P->d; ++mu) {
+        if (P->alias[mu] != mu) {
+          nb.tcoff[b][mu] = nb.tcoff[b][P->alias[mu]];
+          continue;
+        }
         nb.tcoff[b][mu] = (size_t)b * P->tcb_bytes + P->tcb_off[mu];
         srcs.push_back(nb.dev + nb.off[b][mu]);
         ns.push_back((int)P->n[mu]);
@@ -1301,15 +1315,17 @@ phiks_status square_modes(Ctx& c, Mats& M, int& cur_buf) {
   // (the launches below go to c.st)
   phiks_plan_s* P = c.P;
   GemmBatch gb = gemm_batch0();
-  gb.count = P->d;
   size_t off = 0;
-  for (int mu = 0; mu < P->d; ++mu) {
-    gb.n[mu] = (int)P->m[mu];
-    gb.A[mu] = M.L[mu];
-    gb.B[mu] = M.L[mu];
-    gb.C[mu] = c.msq[cur_buf] + off;
-    gb.alpha[mu] = 1.0;
-    gb.beta_I[mu] = 0.0;
+  for (int mu = 0; mu < P->d; ++mu) {  // modes sharing a matrix square it once
+    if (P->alias[mu] == mu) {
+      const int k = gb.count++;
+      gb.n[k] = (int)P->m[mu];
+      gb.A[k] = M.L[mu];
+      gb.B[k] = M.L[mu];
+      gb.C[k] = c.msq[cur_buf] + off;
+      gb.alpha[k] = 1.0;
+      gb.beta_I[k] = 0.0;
+    }
     off += (size_t)P->m[mu] * P->m[mu];
   }
   CK(launch_gemm_batch_f64(gb, P->nmax, c.st));
@@ -1317,19 +1333,28 @@ phiks_status square_modes(Ctx& c, Mats& M, int& cur_buf) {
   const double* srcs[PHIKS_MAX_D];
   int ns[PHIKS_MAX_D];
   void* dsts[PHIKS_MAX_D];
+  int nprep = 0;
   for (int mu = 0; mu < P->d; ++mu) {
+    const int a = P->alias[mu];
+    if (a != mu) {
+      M.L[mu] = M.L[a];
+      M.B[mu] = M.B[a];
+      off += (size_t)P->m[mu] * P->m[mu];
+      continue;
+    }
     M.L[mu] = c.msq[cur_buf] + off;
     off += (size_t)P->m[mu] * P->m[mu];
     if (tc_path(P)) {
       uint8_t* dst = c.msq_tcb[cur_buf] + P->tcb_off[mu];
-      srcs[mu] = M.L[mu];
-      ns[mu] = (int)P->n[mu];
-      dsts[mu] = dst;
+      srcs[nprep] = M.L[mu];
+      ns[nprep] = (int)P->n[mu];
+      dsts[nprep] = dst;
+      ++nprep;
       M.B[mu] = dst;
     }
   }
-  if (emu_dtype(P)) CK(oz_prepare_b(P->d, srcs, ns, dsts, c.st));
-  else if (tc_path(P)) CK(tc_prepare_b_many(P->dtype, P->d, srcs, ns, dsts, c.st));
+  if (emu_dtype(P)) CK(oz_prepare_b(nprep, srcs, ns, dsts, c.st));
+  else if (tc_path(P)) CK(tc_prepare_b_many(P->dtype, nprep, srcs, ns, dsts, c.st));
   cur_buf = 1 - cur_buf;
   return PHIKS_OK;
 }
@@ -2396,6 +2421,14 @@ phiks_status phiks_plan(int d, const int64_t* n, const double* const* A, int dty
     tot += (size_t)m * m;
   }
   P->sum_n2 = tot;
+  for (int mu = 0; mu < d; ++mu) {
+    P->alias[mu] = mu;
+    for (int nu = 0; nu < mu; ++nu)
+      if (P->alias[nu] == nu && P->m[nu] == P->m[mu] && P->A[nu] == P->A[mu]) {
+        P->alias[mu] = nu;
+        break;
+      }
+  }
   CK(dev_malloc((void**)&P->dAs, tot * 8));
   for (int mu = 0; mu < d; ++mu) {
     const int64_t m = P->m[mu];
