@@ -305,3 +305,36 @@ def test_batch_apply_and_graph_match_single_calls():
     ex = dense.same(w.A, w.tau, w.vs[0], w.p)
     for l in range(w.p + 1):
         assert rel_inf(o1.cpu().numpy()[l * w.N:(l + 1) * w.N], ex[l]) < TOL_EXACT
+
+
+@pytest.mark.parametrize("dtype", [pk.PHIKS_FP64, pk.PHIKS_FP64_EMU, pk.PHIKS_BF16X3])
+def test_modes_sharing_a_matrix(dtype):
+    """Modes 0 and 2 with the same matrix and mode 1 with another, and a plan
+    whose three modes share one matrix: the plan computes each distinct
+    matrix's small exponentials and planes once.  Both against the O3 oracle
+    at the dtype's call tolerance, with squaring levels (s >= 1)."""
+    n = 32
+    A0 = wk.fd_adr_dirichlet(n, 1.0, 4.0, 0.3)
+    A1 = wk.fd_adr_dirichlet(n, 1.0, -7.0, 0.3)
+    tau, p = 3e-3, 3
+    f64 = dtype in (pk.PHIKS_FP64, pk.PHIKS_FP64_EMU)
+    tol = 1e-12 if f64 else 8e-4
+    tdt = torch.float64 if f64 else torch.float32
+    for A in ([A0, A1, A0], [A1, A1, A1]):
+        N = n ** 3
+        vs = [wk.normal(70 + l, N) for l in range(p + 1)]
+        if not f64:
+            vs = [v.astype(np.float32).astype(np.float64) for v in vs]
+        plan = pk.Plan(A, dtype)
+        out = torch.full((N,), float("nan"), device="cuda", dtype=tdt)
+        kw = {} if f64 else {"tol": 1e-6 * max(float(np.linalg.norm(v)) for v in vs)}
+        plan.apply(tau, p, [dev(v, tdt) for v in vs], out, **kw)
+        torch.cuda.synchronize()
+        pk.phiks_device_status(plan.handle)
+        s, q, _, _ = plan.last_params()
+        plan.close()
+        ex = ta.lincomb(A, tau, vs)
+        err = rel_inf(out.double().cpu().numpy(), ex)
+        print("shared modes dtype %d (s,q)=(%d,%d) err %.2e" % (dtype, s, q, err))
+        assert s >= 1
+        assert err < tol
