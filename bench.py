@@ -360,24 +360,26 @@ def run_phiks(args):
     cms = timed_calls(plan, out, opts_c, args.steps)
 
     # ---- end to end through the C ABI with host buffers
-    hv = [torch.from_numpy(v).pin_memory() for v in wl.vs]
+    # the step's inputs as one pinned block and one device block (one copy in)
+    nvec = len(wl.vs)
+    hv = torch.from_numpy(np.concatenate(wl.vs)).pin_memory()
     hout = torch.empty(wl.nscales * N, dtype=torch.float64).pin_memory()
-    dv = [torch.empty(N, device="cuda", dtype=torch.float64) for _ in wl.vs]
+    dbuf = torch.empty(nvec * N, device="cuda", dtype=torch.float64)
+    dv = [dbuf[i * N:(i + 1) * N] for i in range(nvec)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_ms = 0.0
     for k in range(args.steps + 2):   # two untimed calls capture the graph for dv
         with torch.cuda.stream(stream):
             flush.fill_(k & 0xFF)
             e0.record(stream)
-            for h, d in zip(hv, dv):
-                d.copy_(h, non_blocking=True)
+            dbuf.copy_(hv, non_blocking=True)
             pk.phiks_apply_ex(plan.handle, wl.tau, wl.p, dv, out, stream, opts=opts)
             hout.copy_(out, non_blocking=True)
             e1.record(stream)
         torch.cuda.synchronize()
         if k >= 2:
             e2e_ms += e0.elapsed_time(e1)
-    h2d = sum(v.nbytes for v in wl.vs)
+    h2d = hv.numel() * 8
     d2h = hout.numel() * 8
 
     emu = main_dtype == pk.PHIKS_FP64_EMU
@@ -490,8 +492,12 @@ def run_precision(args):
         dt = pk.DTYPES[name]
         tdt = torch.float64 if name in ("fp64", "fp64emu") else torch.float32
         plan = pk.Plan(wl.A, dt)
-        vs = [torch.from_numpy(v).to(device="cuda", dtype=tdt) for v in wl.vs]
-        outs = [torch.empty(p * N, device="cuda", dtype=tdt) for _ in vs]
+        # inputs and outputs as views of one device block each (one copy in,
+        # one copy out in the end-to-end figure)
+        vbuf = torch.from_numpy(np.concatenate(wl.vs)).to(device="cuda", dtype=tdt)
+        vs = [vbuf[i * N:(i + 1) * N] for i in range(len(wl.vs))]
+        obuf = torch.empty(len(wl.vs) * p * N, device="cuda", dtype=tdt)
+        outs = [obuf[i * p * N:(i + 1) * p * N] for i in range(len(wl.vs))]
         norms = [float(np.linalg.norm(v.astype(np.float32) if tdt == torch.float32 else v)) for v in wl.vs]
         kw = dict(skip_phi0=1)
         if PRECISION_TOL[name] is not None:
@@ -546,19 +552,17 @@ def run_precision(args):
         if name == head:
             # end to end through the C ABI: the 8 inputs from pinned host
             # memory and the 24 outputs back inside the timed region
-            hv = [torch.from_numpy(v).to(dtype=tdt).pin_memory() for v in wl.vs]
-            ho = [torch.empty(p * N, dtype=tdt).pin_memory() for _ in vs]
+            hv = torch.from_numpy(np.concatenate(wl.vs)).to(dtype=tdt).pin_memory()
+            ho = torch.empty(len(vs) * p * N, dtype=tdt).pin_memory()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e2e_ms = 0.0
             for k in range(2):
                 with torch.cuda.stream(stream):
                     flush.fill_(k & 0xFF)
                     e0.record(stream)
-                    for h, d in zip(hv, vs):
-                        d.copy_(h, non_blocking=True)
+                    vbuf.copy_(hv, non_blocking=True)
                     step()
-                    for h, o in zip(ho, outs):
-                        h.copy_(o, non_blocking=True)
+                    ho.copy_(obuf, non_blocking=True)
                     e1.record(stream)
                 torch.cuda.synchronize()
                 e2e_ms += e0.elapsed_time(e1) / 2
