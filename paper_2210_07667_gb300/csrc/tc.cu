@@ -100,6 +100,7 @@ struct GemmParams {
   void* out0;
   void* out1;
   int* status;
+  uint32_t b_bytes;  // resident form: shared memory of B (every K chunk and plane)
 };
 
 // TMA maps of the B planes (hi, lo) of tensor b's matrix (entry 0 unless mixed).
@@ -344,6 +345,270 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
+// Resident form (one N tile per row block: a tensor's tiles all use the
+// whole of its matrix): a CTA takes a contiguous range of tiles and keeps its
+// tensor's B planes, every K chunk, in shared memory (loaded once per tensor,
+// after the MMAs on the previous tensor's finished); only the A planes stream
+// through the S stages.  Roles, TMEM sets and the epilogue as in
+// tc_gemm_kernel.
+template <int KIND, int NP>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    tc_gemm_res_kernel(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
+                       const __grid_constant__ TcMapsB mapsB, const __grid_constant__ GemmParams P) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int S = P.stages;
+  const uint32_t a_plane = BM * 128;                 // bytes of one A plane per stage
+  const uint32_t b_plane = (uint32_t)P.ntile * 128;  // bytes of one B plane per K chunk
+  const uint32_t stage_bytes = NP * a_plane;
+  uint8_t* const sB = smem;                // [kc][plane]
+  uint8_t* const sA = smem + P.b_bytes;    // S stages of NP A planes
+  uint64_t* full = (uint64_t*)(sA + (size_t)S * stage_bytes);
+  uint64_t* empty = full + S;
+  uint64_t* tfull = empty + S;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* mdone = tempty + 2;  // the MMA warp's issued MMAs finished (failure path)
+  uint64_t* fullB = mdone + 1;   // the current tensor's B planes landed
+  uint64_t* emptyB = fullB + 1;  // the MMAs on the previous tensor's B planes finished
+  uint32_t* tmem_slot = (uint32_t*)(emptyB + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], kTcEpiWarps * 32);
+    }
+    mbar_init(mdone, 1);
+    mbar_init(fullB, 1);
+    mbar_init(emptyB, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(P.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  pdl_wait();  // operand planes come from the kernels before
+
+  // this CTA's tiles: a contiguous range of the row tiles
+  const int G = (int)gridDim.x, cta = (int)blockIdx.x;
+  const int tbase = P.num_tiles / G, trem = P.num_tiles % G;
+  const int t_begin = cta * tbase + min(cta, trem);
+  const int t_end = t_begin + tbase + (cta < trem ? 1 : 0);
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0, eph = 0;
+      int nB = 0, prev_tb = -1;
+      bool ok = true;
+      for (int t = t_begin; t < t_end && ok; ++t) {
+        int mi = 0;
+        int m0 = (int)tc_tile_row0(P, t, &mi);
+        if (mi != prev_tb) {  // this tensor's B planes, every K chunk
+          if (prev_tb >= 0) {
+            if (!mbar_wait(emptyB, eph, P.status, 1)) break;
+            eph ^= 1;
+          }
+          mbar_arrive_expect_tx(fullB, (uint32_t)P.nk * NP * b_plane);
+          for (int kc = 0; kc < P.nk; ++kc) {
+            const int x = kc * (128 / (KIND == 0 ? 2 : 4));
+            tma_load_2d(sB + (size_t)(kc * NP) * b_plane, &mapsB.b[mi][0], fullB, x, 0);
+            if (NP == 2) tma_load_2d(sB + (size_t)(kc * NP + 1) * b_plane, &mapsB.b[mi][1], fullB, x, 0);
+          }
+          ++nB;
+          prev_tb = mi;
+        }
+        if (P.shared_a) m0 -= (int)(mi * P.M2);  // the one split input
+        for (int kc = 0; kc < P.nk && ok; ++kc) {
+          if (!mbar_wait(&empty[s], ph ^ 1, P.status, 1)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = sA + (size_t)s * stage_bytes;
+          mbar_arrive_expect_tx(&full[s], stage_bytes);
+          const int x = kc * (128 / (KIND == 0 ? 2 : 4));
+          tma_load_2d(st, &mapA0, &full[s], x, m0);
+          if (NP == 2) tma_load_2d(st + a_plane, &mapA1, &full[s], x, m0);
+          if (++s == S) {
+            s = 0;
+            ph ^= 1;
+          }
+        }
+      }
+      // let the copies already issued land before the CTA may leave (also
+      // after another role gave up)
+      for (int k = 0; k < S; ++k) {
+        if (--s < 0) {
+          s = S - 1;
+          ph ^= 1;
+        }
+        (void)mbar_drain(&full[s], ph);
+      }
+      if (nB) (void)mbar_drain(fullB, (uint32_t)(nB - 1) & 1u);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_make(KIND == 0 ? 1 : 2, P.ntile);
+      int s = 0;
+      uint32_t ph = 0, bpar = 0;
+      int buf = 0, prev_tb = -1;
+      uint32_t aph = 0;
+      bool ok = true, any = false;
+      const uint32_t sb = smem_u32(sB);
+      for (int t = t_begin; t < t_end && ok; ++t) {
+        int mi = 0;
+        (void)tc_tile_row0(P, t, &mi);
+        if (!mbar_wait(&tempty[buf], aph ^ 1, P.status, 2)) {
+          ok = false;
+          break;
+        }
+        if (mi != prev_tb) {
+          if (!mbar_wait(fullB, bpar, P.status, 3)) {
+            ok = false;
+            break;
+          }
+          bpar ^= 1;
+          prev_tb = mi;
+        }
+        tc_fence_after();
+        const uint32_t dtm = tmem_base + (uint32_t)(buf * P.ntile);
+        for (int kc = 0; kc < P.nk; ++kc) {
+          if (!mbar_wait(&full[s], ph, P.status, 3)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_u32(sA + (size_t)s * stage_bytes);
+          const uint64_t da0 = sdesc_sw128(st), da1 = sdesc_sw128(st + a_plane);
+          const uint64_t db0 = sdesc_sw128(sb + (uint32_t)(kc * NP) * b_plane);
+          const uint64_t db1 = sdesc_sw128(sb + (uint32_t)(kc * NP + (NP == 2 ? 1 : 0)) * b_plane);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {  // 4 x 32-byte K steps per 128-byte chunk
+            const uint64_t off = (uint64_t)((kk * 32) >> 4);
+            const uint32_t acc = (kc | kk) != 0;
+            umma<KIND>(dtm, da0 + off, db0 + off, idesc, acc);
+            if (NP == 2) {
+              umma<KIND>(dtm, da0 + off, db1 + off, idesc, 1);
+              umma<KIND>(dtm, da1 + off, db0 + off, idesc, 1);
+            }
+          }
+          any = true;
+          umma_commit(&empty[s]);
+          if (++s == S) {
+            s = 0;
+            ph ^= 1;
+          }
+        }
+        if (!ok) break;
+        umma_commit(&tfull[buf]);
+        // the last tile on these B planes: they may be replaced
+        if (t + 1 < t_end) {
+          int mn = 0;
+          (void)tc_tile_row0(P, t + 1, &mn);
+          if (mn != mi) umma_commit(emptyB);
+        }
+        if (++buf == 2) {
+          buf = 0;
+          aph ^= 1;
+        }
+      }
+      if (!ok && any) {  // given up: the MMAs already issued finish before TMEM is freed
+        umma_commit(mdone);
+        (void)mbar_drain(mdone, 0);
+      }
+    }
+  } else {
+    // ---------------- epilogue (as in tc_gemm_kernel)
+    const int q = warp & 3;
+    const int grp = (warp - 2) >> 2;
+    constexpr int GROUPS = kTcEpiWarps / 4;
+    const int row = q * 32 + lane;
+    int buf = 0;
+    uint32_t aph = 0;
+    for (int t = t_begin; t < t_end; ++t) {
+      if (!mbar_wait(&tfull[buf], aph, P.status, 4)) break;
+      tc_fence_after();
+      int tb = 0;
+      const int64_t colb = tc_tile_row0(P, t, &tb) + row;  // fibre of the batch
+      const bool valid = P.mixed ? (colb - (int64_t)tb * P.M2 < P.M2) : (colb < P.rows);
+      const int64_t bt = valid ? (P.mixed ? tb : colb / P.M2) : 0;
+      const int64_t col = colb - bt * P.M2 + bt * P.N;  // tensor b's elements start at b N
+      const int cend = P.n < P.ntile ? P.n : P.ntile;
+      const uint32_t tl = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * P.ntile);
+      if (P.ntile <= 32 * GROUPS) {
+        uint32_t u[2][16];
+        const int c0 = 16 * grp, c1 = c0 + 16 * GROUPS;
+        if (c0 < cend) tmem_ld16_nowait(tl + (uint32_t)c0, u[0]);
+        if (c1 < cend) tmem_ld16_nowait(tl + (uint32_t)c1, u[1]);
+        tmem_wait_ld();
+        tc_fence_before();
+        mbar_arrive(&tempty[buf]);
+        if (valid) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int cb = h ? c1 : c0;
+            if (cb >= cend) break;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int i = cb + j;
+              if (i >= P.n) break;
+              const int64_t idx = col + P.M2 * (int64_t)i;
+              const float x = __uint_as_float(u[h][j]);
+              if (!P.last) split_store_f<KIND, NP>(P.out0, P.out1, idx, x);
+              else ((float*)P.out0)[idx] = x;
+            }
+          }
+        }
+      } else {
+        for (int c0 = 16 * grp; c0 < cend; c0 += 16 * GROUPS) {
+          float v[16];
+          tmem_ld16(tl + (uint32_t)c0, v);
+          if (!valid) continue;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int i = c0 + j;
+            if (i >= P.n) break;
+            const int64_t idx = col + P.M2 * (int64_t)i;
+            if (!P.last) split_store_f<KIND, NP>(P.out0, P.out1, idx, v[j]);
+            else ((float*)P.out0)[idx] = v[j];
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty[buf]);
+      }
+      if (++buf == 2) {
+        buf = 0;
+        aph ^= 1;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(P.tmem_cols)
+                 : "memory");
+  }
+}
+
 // x = sum_m coef_m src_m (float or double sources) split into planes.  The
 // combination is formed in FP64 only when it has more than one term or a
 // coefficient other than one; the split itself runs in FP32 (the planes carry
@@ -525,6 +790,7 @@ struct TcState {
   int batch = 0;     // tensors the bound workspace holds
   int last_res = 1;  // plane set holding the last call's results
   int smem_optin = 0;
+  int sms = 0;          // streaming multiprocessors of the device
   int ntiles_mult = 0;  // tuned: N tiles per pass, times the minimum (0: by size)
   // encoded tensor maps by (address, inner extent, rows, box rows): encoding
   // costs microseconds of host time, a lookup does not
@@ -601,6 +867,7 @@ phiks_status tc_create(TcState** out, int dtype, int d, const int64_t* n, int64_
   for (int mu = 0; mu < d; ++mu) s->n[mu] = n[mu];
   s->N = N;
   s->smem_optin = (int)prop.sharedMemPerBlockOptin;
+  s->sms = prop.multiProcessorCount;
   if (dev_malloc((void**)&s->status, sizeof(int)) != cudaSuccess ||
       cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess) {
     dev_free(s->status);
@@ -680,6 +947,34 @@ namespace {
 template <int KIND, int NP>
 cudaError_t run_gemm(TcState* s, const CUtensorMap* mA, const TcMapsB& mB, GemmParams& P,
                      cudaStream_t st) {
+  {  // resident form: one N tile, B (every K chunk) and at least two A stages fit
+    const size_t extra = 1024 + 64 * 8 + 64;
+    const uint32_t b_bytes = (uint32_t)P.nk * NP * (uint32_t)P.ntile * 128;
+    const uint32_t a_stage = NP * BM * 128;
+    if (P.n_ntiles == 1 && (size_t)b_bytes + 2 * a_stage + extra <= (size_t)s->smem_optin) {
+      int stages = (int)(((size_t)s->smem_optin - extra - b_bytes) / a_stage);
+      if (stages > 4) stages = 4;
+      P.stages = stages;
+      P.b_bytes = b_bytes;
+      const size_t smem = (size_t)b_bytes + (size_t)stages * a_stage + extra;
+      auto kern = tc_gemm_res_kernel<KIND, NP>;
+      static int smem_set_r[64] = {0};
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+      if (smem_set_r[dev] < (int)smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, s->smem_optin);
+        if (e != cudaSuccess) return e;
+        smem_set_r[dev] = s->smem_optin;
+      }
+      // the fewest CTAs that keep the makespan (ceil(tiles / SMs) each)
+      const int sms = s->sms > 0 ? s->sms : 152;
+      const int per = (P.num_tiles + sms - 1) / sms;
+      const int grid = (P.num_tiles + per - 1) / per;
+      count_launch();
+      return launch_pdl(kern, dim3(grid), dim3(NTHREADS), smem, st, mA[0], mA[1], mB, P);
+    }
+  }
   const uint32_t stage_bytes = NP * (BM * 128 + (uint32_t)P.ntile * 128);
   const size_t extra = 1024 + 64 * 8 + 64;
   int stages = (int)((size_t)(s->smem_optin - extra) / stage_bytes);
