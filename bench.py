@@ -186,8 +186,12 @@ def measured_peaks():
 # dense peak each runs against (tf32 from the measured bf16 peak times the
 # nominal tf32 / bf16 ratio, 1.1 / 2.25 PFLOP/s)
 TC_MULT = {"bf16x3": 3, "tf32x3": 3, "tf32": 1, "fp64emu": 28}
-TC_KERNEL = {"bf16x3": "tc_gemm_kernel<0,2>", "tf32x3": "tc_gemm_kernel<1,2>", "tf32": "tc_gemm_kernel<1,1>",
-             "fp64emu": "oz_gemm_kernel"}
+# (the resident form when one N tile covers a matrix, the streaming form otherwise;
+# the brackets time every GEMM pass of either)
+TC_KERNEL = {"bf16x3": "tc_gemm_res_kernel<0,2> / tc_gemm_kernel<0,2>",
+             "tf32x3": "tc_gemm_res_kernel<1,2> / tc_gemm_kernel<1,2>",
+             "tf32": "tc_gemm_res_kernel<1,1> / tc_gemm_kernel<1,1>",
+             "fp64emu": "oz_gemm_kernel / oz_gemm_stream_kernel"}
 
 
 def profile_roofline(dname, ms, launches, flops, kernel=None):
