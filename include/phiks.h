@@ -75,8 +75,10 @@ typedef enum {
  * compensated products, hi*hi + hi*lo + lo*hi, FP32 accumulation).
  * FP64_EMU: vectors double, products on the tensor cores as exact sums of
  * bf16 digit products (seven base-256 digits per operand, FP32 accumulation
- * that stays exact for n_mu <= 128), rounded once to FP64; needs every n_mu a
- * multiple of 8 and at most 128.  C128: complex A_mu and vectors (the
+ * that stays exact for n_mu <= 128); a Tucker operator's intermediate products
+ * pass their exact sums to the next mode, which rounds them once to its fixed
+ * point, and the last is rounded once to FP64; needs every n_mu a multiple of 8
+ * and at most 128.  C128: complex A_mu and vectors (the
  * validation operator of Sec. 4.1), complex FP64 products on the FP64 pipe;
  * vectors are N complex numbers stored as 2 N doubles (real, imaginary).
  * Small exponentials, their squaring and the doubling-formula combination
