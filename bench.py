@@ -223,6 +223,11 @@ def profile_roofline(dname, ms, launches, flops, kernel=None):
 # written; the summary of that capture under profiles/ gives the command);
 # None once the kernel changes
 OZ_GEMM_TRAFFIC_PER_PRODUCT = 14.861e6 / 4
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of tc_gemm_res_kernel<0,2>
+# on the precision form's Chebyshev 128^3 operator (each launch a nine-tensor batch),
+# from an ncu capture of the kernel as it stands (two launches, 102.0 and 96.8 MB; the
+# summary under profiles/ gives the command); None once the kernel changes
+TC_RES_BF16X3_CHEB128_TRAFFIC_PER_LAUNCH = 99.4e6
 # bf16 digit products the emulated pass executes per FP64 product (digit
 # planes s + t <= 6 of seven per operand)
 OZ_DIGIT_PRODUCTS = 28
@@ -553,6 +558,9 @@ def run_precision(args):
                          "mu_mode_tflops_algorithmic": kfl / max(kms, 1e-9) / 1e9,
                          "mu_mode_ms_per_call": kms / len(vs), "gpu_launches_per_step": launches // args.steps,
                          "roofline": profile_roofline(name, kms, kl, kfl)}
+        roof = results[name]["roofline"]
+        if roof and name == "bf16x3" and args.variant == "cheb" and args.n == 128:
+            roof["traffic"] = TC_RES_BF16X3_CHEB128_TRAFFIC_PER_LAUNCH
         if name == head:
             # end to end through the C ABI: the 8 inputs from pinned host
             # memory and the 24 outputs back inside the timed region
