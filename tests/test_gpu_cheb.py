@@ -104,15 +104,18 @@ def test_cheb_n64_scale_outputs_vs_oracle(dtype):
     assert max(errs) < TOL_CALL[dtype]
 
 
-@pytest.mark.parametrize("dtype", [pk.PHIKS_FP64, pk.PHIKS_FP64_EMU])
+@pytest.mark.parametrize("dtype", ALL)
 def test_cheb_n128_full_size_vs_oracle(dtype):
     """The precision configuration's full size (N = 2,097,152, tau = 5e-7),
-    one right-hand side; phi_1 checked against the oracle (one O3 call)."""
+    one right-hand side, every dtype (the split dtypes with the selection
+    tolerance the precision configuration gives them); phi_1 checked against
+    the oracle (one O3 call, shared by the dtypes)."""
     tau = 5e-7
     got, (s, q, T, tk) = _run(128, tau, dtype)
     ex = _exact(128, tau, (1,))
     err = rel_inf(got[0], ex[0])
     print("cheb n=128 dtype %d (s,q,T#)=(%d,%d,%d) phi_1 err %.2e" % (dtype, s, q, T, err))
-    assert s >= 1
+    if dtype in (pk.PHIKS_FP64, pk.PHIKS_FP64_EMU):
+        assert s >= 1   # (the split dtypes' looser tolerance needs no squaring here)
     assert np.isfinite(got).all()
     assert err < TOL_CALL[dtype]
