@@ -54,6 +54,52 @@ def test_parameter_selection_matches_oracle(pk, case, rule):
     assert got == (ref.s, ref.q, ref.tcount)
 
 
+def _workload_cases():
+    """The measured configurations' operators: a spread of the uneven batched
+    instances (their own tau), the served classes at small, middle and large
+    sizes (AC, anisotropic ADR, both Brusselator blocks) with p = 2..4 and
+    linear-combination norms, and the Chebyshev operator of the precision form
+    at its two step sizes, FP64 and split-dtype tolerances."""
+    insts = wk.batched_instances(256)
+    for k in range(0, 256, 23):
+        w = insts[k]
+        yield w.name, w.A, w.tau, 3, [float(np.linalg.norm(w.vs[0]))], None
+    sizes = {"ac": (128, 576, 1024), "adr": (32, 112, 192), "bru": (128, 320, 512)}
+    for cls, ns in sizes.items():
+        tau = wk.SERVED_CLASSES[cls]["tau"]
+        for j, n in enumerate(ns):
+            p = 2 + j
+            vn = [float(np.linalg.norm(wk.normal(300 + 7 * j + l, 4096))) for l in range(p + 1)]
+            if cls == "ac":
+                ops = [wk.ac_operator(n)]
+            elif cls == "adr":
+                ops = [[wk.fd_adr_dirichlet(n, 1.0, a, 2.0 / 3) for a in (10.0, -20.0, 5.0)]]
+            else:
+                ops = list(wk.brusselator_operators(n))
+            for b, A in enumerate(ops):
+                yield "%s%d_%d" % (cls, n, b), A, tau, p, vn, None
+    for n, tau in ((64, 8e-6), (128, 5e-7)):
+        A = [wk.cheb_d2_dirichlet(n)] * 3
+        vn = [float(np.linalg.norm(wk.normal(10, n ** 3)))]
+        yield "cheb%d" % n, A, tau, 3, vn, None
+        yield "cheb%d_bf16x3" % n, A, tau, 3, vn, 1e-6 * vn[0]
+
+
+_WORKLOAD_CASES = list(_workload_cases())
+
+
+@pytest.mark.parametrize("case", range(len(_WORKLOAD_CASES)), ids=[c[0] for c in _WORKLOAD_CASES])
+def test_parameter_selection_matches_oracle_on_the_measured_operators(pk, case):
+    _, A, tau, p, vn, tol = _WORKLOAD_CASES[case]
+    kind = "same" if len(vn) == 1 else "lincomb"
+    kw = {} if tol is None else {"tol": tol}
+    for rule in (0, 1):
+        got = pk.phiks_choose_params(A, tau, p, vn, rule=rule, **kw)
+        ref = params.select(params.kron_sum_rect(A, tau), p, kind, vn,
+                            rule="gll" if rule == 0 else "gl", **kw)
+        assert got == (ref.s, ref.q, ref.tcount), rule
+
+
 def test_parameter_selection_tolerance_and_range(pk):
     wl = wk.small_same(16)
     vn = [float(np.linalg.norm(wl.vs[0]))]
