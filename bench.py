@@ -217,6 +217,38 @@ def profile_roofline(dname, ms, launches, flops, kernel=None):
             else ("bf16_tflops of %s peaks x 1.1/2.25 (nominal tf32/bf16)" % src)}
 
 
+# bytes per element one split-dtype mode pass moves: its input planes read,
+# the next pass's planes (or the last pass's FP32 result) written
+SPLIT_PASS_BYTES = {"bf16x3": 4 + 4, "tf32x3": 8 + 8, "tf32": 4 + 4}
+
+
+def split_ceiling(dname, roof, n, d, N, tuckers, ms, hbm_gbs):
+    """The split dtypes' ceiling, min(tensor peak / products per algorithmic
+    product, HBM x arithmetic intensity), in algorithmic TFLOP/s (2 N n_mu
+    per mode pass):
+      * GEMM passes: intensity 2 n / (bytes one mode pass moves per element),
+        against the GEMM passes' own rate;
+      * whole call: a Tucker operator fused over its d modes would move 4 + 4
+        bytes per element (FP32 in and out) for 2 N sum(n) flops, against the
+        Tucker flops of the step over its time.
+    (The 129 MB L2 can hold part of a batch's planes, so the measured rate
+    may exceed the per-pass HBM figure.)"""
+    if not roof or dname not in SPLIT_PASS_BYTES:
+        return None
+    tensor = roof["peak"] / TC_MULT[dname]
+    hbm_pass = hbm_gbs * 1e9 * (2.0 * n / SPLIT_PASS_BYTES[dname]) / 1e12
+    hbm_fused = hbm_gbs * 1e9 * (2.0 * d * n / 8.0) / 1e12
+    pass_rate = roof["achieved"] / TC_MULT[dname]
+    call_rate = tuckers * 2.0 * N * d * n / (ms * 1e-3) / 1e12
+    c_pass, c_call = min(tensor, hbm_pass), min(tensor, hbm_fused)
+    return {"unit": "TFLOP/s (algorithmic)", "tensor_over_products": tensor,
+            "hbm_mode_pass": hbm_pass, "hbm_fused_tucker": hbm_fused,
+            "gemm_passes": {"achieved": pass_rate, "ceiling": c_pass, "frac": pass_rate / c_pass,
+                            "bound": "tensor" if tensor <= hbm_pass else "hbm"},
+            "call": {"achieved": call_rate, "ceiling": c_call, "frac": call_rate / c_call,
+                     "bound": "tensor" if tensor <= hbm_fused else "hbm"}}
+
+
 # dram__bytes_read.sum + dram__bytes_write.sum per mu-mode product of
 # oz_gemm_kernel<32> from an ncu capture of the kernel as it stands (six
 # four-product launches of this workload, cold caches: 14.861 MB read, 0
@@ -561,6 +593,8 @@ def run_precision(args):
         roof = results[name]["roofline"]
         if roof and name == "bf16x3" and args.variant == "cheb" and args.n == 128:
             roof["traffic"] = TC_RES_BF16X3_CHEB128_TRAFFIC_PER_LAUNCH
+        results[name]["ceiling"] = split_ceiling(name, roof, args.n, 3, N, tk * len(vs), ms,
+                                                 measured_peaks()[0]["hbm_gbs"])
         if name == head:
             # end to end through the C ABI: the 8 inputs from pinned host
             # memory and the 24 outputs back inside the timed region
@@ -615,7 +649,8 @@ def run_precision(args):
             "rel_err_vs_fp64": h["rel_err_vs_fp64"], "rel_err_vs_oracle": h.get("rel_err_vs_oracle"),
             "oracle_check": {"output": "phi_1(tau K) v_0 (one of 24 per step)", "oracle": "O3 Taylor action",
                              "seconds": oracle_s},
-            "roofline": h.get("roofline"), "e2e": head_e2e, "gpu_launches": head_launches,
+            "roofline": h.get("roofline"), "ceiling": h.get("ceiling"), "e2e": head_e2e,
+            "gpu_launches": head_launches,
             "cpu_baseline": None if oracle_s is None else
             {"value": 2.0 / oracle_s, "unit": "phi-actions/s", "cores": oracle_threads(), "kind": "oracle",
              "sample": "phi_1(tau K) v_0 twice (the input as FP64 and as FP32 saw it), O3 Taylor action, "

@@ -37,3 +37,24 @@ def test_reference_arm_other_ranks_exit_without_work():
     r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_split_ceiling_arithmetic():
+    """The precision form's ceiling: BF16X3 at n = 128 has three tensor-core
+    products per algorithmic one and moves 8 bytes per element per mode pass
+    (2 n / 8 = 32 flop per byte), a fused Tucker 8 bytes per element for
+    2 d n flops (96 flop per byte)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    roof = {"peak": 1800.0, "achieved": 450.0}
+    c = bench.split_ceiling("bf16x3", roof, 128, 3, 128 ** 3, 72, 1.0, 6000.0)
+    assert abs(c["tensor_over_products"] - 600.0) < 1e-9
+    assert abs(c["hbm_mode_pass"] - 6000.0 * 32 / 1000) < 1e-9
+    assert abs(c["hbm_fused_tucker"] - 6000.0 * 96 / 1000) < 1e-9
+    assert c["gemm_passes"]["bound"] == "hbm" and abs(c["gemm_passes"]["achieved"] - 150.0) < 1e-9
+    assert abs(c["gemm_passes"]["frac"] - 150.0 / 192.0) < 1e-12
+    # 72 Tucker operators of 2 N (3 n) flops in 1 ms
+    rate = 72 * 2.0 * 128 ** 3 * 384 / 1e-3 / 1e12
+    assert abs(c["call"]["achieved"] - rate) < 1e-9 and c["call"]["bound"] == "hbm"
+    assert abs(c["call"]["frac"] - rate / 576.0) < 1e-12
+    assert bench.split_ceiling("fp64", roof, 128, 3, 128 ** 3, 72, 1.0, 6000.0) is None
