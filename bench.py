@@ -728,7 +728,10 @@ def run_batched(args):
     torch.cuda.synchronize()
     l0 = pk.phiks_kernel_launches()
     ms_graph = timed(lambda: batch.launch(graph, stream), args.steps)
-    tucks = sum(r[0].last_params()[3] for r in rows)
+    tk_list = [r[0].last_params()[3] for r in rows]
+    tucks = sum(tk_list)
+    bound_ms, bound_fl = batched_bound(insts, tk_list, tensor_ceiling_tflops(name),
+                                       measured_peaks()[0]["hbm_gbs"], rows[0][4].element_size())
     for r in rows:
         pk.phiks_device_status(r[0].handle, stream)
     out_split = [r[4].double().cpu().numpy() for r in rows]
@@ -814,6 +817,10 @@ def run_batched(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": name,
             "data": "synthetic", "rel_err_vs_oracle": h.get("oracle_check", {}).get("max_rel_err"),
             "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
+            "aggregate_bound": {"ms": bound_ms, "frac": bound_ms / h["ms_per_step"],
+                                "achieved_tflops_algorithmic": bound_fl / (h["ms_per_step"] * 1e-3) / 1e12,
+                                "definition": "sum over instances of max(Tucker flops / tensor ceiling, "
+                                              "Tucker bytes / HBM), fused Tucker operators"},
             "gpu_launches": launches_per_step * args.steps, "launches_per_step": launches_per_step,
             "config": {"workload": "batched_adr_%d_instances" % len(insts), "instances": len(insts),
                        "d2_n": "64..512 step 32", "d3_n": "16..96 step 8", "p": 3, "skip_phi0": True,
@@ -822,6 +829,30 @@ def run_batched(args):
             "per_variant": res}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def batched_bound(insts, tuckers, tensor_tflops, hbm_gbs, elt):
+    """The batched form's bound: the sum over instances of max(Tucker flops /
+    tensor ceiling, Tucker bytes / HBM), every Tucker operator fused over its
+    modes (input read and output written once: 2 elt bytes per element for
+    2 N sum(n) flops).  Returns (bound in ms, algorithmic flops)."""
+    t = fl = 0.0
+    for w, tk in zip(insts, tuckers):
+        f = tk * 2.0 * w.N * sum(a.shape[0] for a in w.A)
+        b = tk * 2.0 * elt * w.N
+        t += max(f / (tensor_tflops * 1e12), b / (hbm_gbs * 1e9))
+        fl += f
+    return t * 1e3, fl
+
+
+def tensor_ceiling_tflops(dname):
+    """Algorithmic TFLOP/s ceiling of a dtype's products: the FP64 peak, or
+    the measured bf16 peak (tf32 at the nominal 1.1 / 2.25 ratio) over the
+    tensor-core products per algorithmic product."""
+    if dname == "fp64":
+        return PEAK_FP64_TFLOPS
+    peaks, _ = measured_peaks()
+    return peaks["bf16_tflops"] * (1.0 if dname in ("bf16x3", "fp64emu") else 1.1 / 2.25) / TC_MULT[dname]
 
 
 def o3_cost(A, tau, N):
@@ -915,7 +946,8 @@ def build_served(pk, torch, arrivals, specs, dtype_name, tol_rel, ring=64):
                 outs[pkey].append(torch.empty(N, device="cuda", dtype=tdt))
             out = outs[pkey][g % ring]
             x = {"plan": plans[pkey].handle, "tau": wk.SERVED_CLASSES[cls]["tau"], "p": p,
-                 "v": vdev[: p + 1], "out": out, "vnorms": vn[: p + 1]}
+                 "v": vdev[: p + 1], "out": out, "vnorms": vn[: p + 1],
+                 "flops_per_tucker": 2.0 * N * sum(a.shape[0] for a in A)}
             if tol_rel is not None:
                 x["tol"] = tol_rel * max(vn[: p + 1])
             apps.append(x)
@@ -926,19 +958,26 @@ def build_served(pk, torch, arrivals, specs, dtype_name, tol_rel, ring=64):
 
 def warm_served(pk, torch, requests):
     """One apply per distinct (plan, p): parameter search and exponentials
-    happen here, not while serving."""
-    seen = set()
+    happen here, not while serving.  Records each apply's Tucker operators
+    (the same for every apply of one (plan, p): one tau and one input set per
+    class and size)."""
+    tuckers = {}
     for apps in requests:
         for x in apps:
             key = (x["plan"], x["p"])
-            if key in seen:
-                continue
-            seen.add(key)
-            kw = dict(vnorms=x["vnorms"])
-            if "tol" in x:
-                kw["tol"] = x["tol"]
-            pk.phiks_apply_ex(x["plan"], x["tau"], x["p"], x["v"], x["out"], None, **kw)
+            if key not in tuckers:
+                kw = dict(vnorms=x["vnorms"])
+                if "tol" in x:
+                    kw["tol"] = x["tol"]
+                pk.phiks_apply_ex(x["plan"], x["tau"], x["p"], x["v"], x["out"], None, **kw)
+                tuckers[key] = pk.phiks_last_params(x["plan"])[3]
+            x["tuckers"] = tuckers[key]
     torch.cuda.synchronize()
+
+
+def served_flops(requests):
+    """Algorithmic Tucker flops of a trace: T# x 2 N sum(n) per apply."""
+    return sum(x["tuckers"] * x["flops_per_tucker"] for apps in requests for x in apps)
 
 
 def run_served(args):
@@ -1064,6 +1103,10 @@ def run_served(args):
                            "offered_80pct_of_saturated_per_s": res[name + "_80pct"]["offered_rate_per_s"],
                            "p50_at_80pct": res[name + "_80pct"]["p50_ms"],
                            "p99_at_80pct": res[name + "_80pct"]["p99_ms"]},
+            "aggregate_tflops": {"unit": "TFLOP/s (algorithmic Tucker flops, T# x 2 N sum(n) per apply)",
+                                 "saturated": served_flops(requests) / mkb / 1e12,
+                                 "offered_rate": served_flops(requests) / mk / 1e12,
+                                 "at_80pct": served_flops(requests) / mk8 / 1e12},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": None, "e2e_note": "the served form keeps plans, inputs and outputs resident on the device",
             "gpu_launches": launches_sat, "clocks": clk,

@@ -58,3 +58,26 @@ def test_split_ceiling_arithmetic():
     assert abs(c["call"]["achieved"] - rate) < 1e-9 and c["call"]["bound"] == "hbm"
     assert abs(c["call"]["frac"] - rate / 576.0) < 1e-12
     assert bench.split_ceiling("fp64", roof, 128, 3, 128 ** 3, 72, 1.0, 6000.0) is None
+
+
+def test_batched_bound_and_served_flops_arithmetic():
+    """The batched form's bound sums, per instance, the larger of its Tucker
+    flops over the tensor ceiling and its Tucker bytes over HBM; the served
+    form's flops are T# x 2 N sum(n) per apply."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+
+    class W:
+        def __init__(self, dims):
+            self.A = [np.zeros((m, m)) for m in dims]
+            self.N = int(np.prod(dims))
+    insts = [W((512, 512)), W((16, 16, 16))]
+    ms, fl = bench.batched_bound(insts, [10, 4], 600.0, 6000.0, 4)
+    f0, f1 = 10 * 2.0 * 512 ** 2 * 1024, 4 * 2.0 * 16 ** 3 * 48
+    b0, b1 = 10 * 8.0 * 512 ** 2, 4 * 8.0 * 16 ** 3
+    want = max(f0 / 600e12, b0 / 6000e9) + max(f1 / 600e12, b1 / 6000e9)
+    assert abs(ms - 1e3 * want) < 1e-12 and fl == f0 + f1
+    reqs = [[{"tuckers": 3, "flops_per_tucker": 10.0}, {"tuckers": 2, "flops_per_tucker": 5.0}],
+            [{"tuckers": 1, "flops_per_tucker": 7.0}]]
+    assert bench.served_flops(reqs) == 3 * 10.0 + 2 * 5.0 + 7.0
