@@ -200,6 +200,20 @@ def test_eig_vs_taylor_symmetric_3d():
         assert rel(o3[i], o2[l].astype(float)) < 1e-14
 
 
+def test_taylor_action_vs_eigenbasis_at_a_large_norm():
+    """O3 where tau ||K||_1 is about 40 (as at the measured configurations),
+    against the exact sine eigenbasis in extended precision: a Taylor action
+    without its scaling would lose every digit to cancellation here."""
+    A = [wk.fd_adr_dirichlet(m, 1.0, a) for m, a in ((12, 0.0), (10, 4.0), (14, 0.0))]
+    tau = 0.02
+    assert 35 < tau * sum(float(np.abs(a).sum(0).max()) for a in A) < 45
+    v = wk.normal(9, 12 * 10 * 14)
+    o2 = eig.phi_actions(A, tau, v, [0, 1, 3])
+    o3 = ta.same(A, tau, v, 3, ells=[0, 1, 3])
+    for i, l in enumerate([0, 1, 3]):
+        assert rel(o3[i], o2[l].astype(float)) < 1e-13
+
+
 # ---------------------------------------------------------------- consistency
 def test_same_vs_lincomb_and_scales():
     wl = wk.small_same(7, p=3)
@@ -408,3 +422,26 @@ def test_remainder_bound_dominates_on_a_diagonal_operator():
                 on_boundary = [_scalar_remainder(x / 2 ** s, q, l) for x in params.rect_boundary(rect)[::8]]
                 assert b[l - 1] >= max(rem), (s, q, l)
                 assert b[l - 1] <= 2.42 * max(on_boundary + rem) * 1.05, (s, q, l)
+
+
+@pytest.mark.parametrize("rule", ["gll", "gl"])
+def test_tucker_count_is_the_operators_the_restatement_applies(rule, monkeypatch):
+    """eq. (Tpsv) / eq. (Tlcp) count one Tucker operator per quadrature node,
+    p per squaring step and one per scale; the step-by-step restatement
+    applies exactly that many, less the free theta = 1 node of GLL (one
+    operator in the same-vector task, p in the linear combination)."""
+    calls = [0]
+    orig = phiks_ref.tucker
+
+    def counting(V, L):
+        calls[0] += 1
+        return orig(V, L)
+    monkeypatch.setattr(phiks_ref, "tucker", counting)
+    A = [wk.fd_adr_dirichlet(4, 1.0, 1.0), wk.fd_adr_dirichlet(3, 1.0, 0.0)]
+    for p, s, q, ns in [(3, 0, 5, 1), (3, 2, 6, 2), (4, 3, 4, 3), (1, 1, 7, 2)]:
+        calls[0] = 0
+        phiks_ref.same(A, 1e-3, wk.normal(1, 12), p, s, q, nscales=ns, rule=rule)
+        assert calls[0] == params.tucker_count("same", s, ns, q, p) - (rule == "gll")
+        calls[0] = 0
+        phiks_ref.lincomb(A, 1e-3, [wk.normal(2 + l, 12) for l in range(p + 1)], s, q, nscales=ns, rule=rule)
+        assert calls[0] == params.tucker_count("lincomb", s, ns, q, p) - (p if rule == "gll" else 0)
