@@ -81,3 +81,42 @@ def test_batched_bound_and_served_flops_arithmetic():
     reqs = [[{"tuckers": 3, "flops_per_tucker": 10.0}, {"tuckers": 2, "flops_per_tucker": 5.0}],
             [{"tuckers": 1, "flops_per_tucker": 7.0}]]
     assert bench.served_flops(reqs) == 3 * 10.0 + 2 * 5.0 + 7.0
+
+
+def test_warm_served_records_tucker_counts_per_apply():
+    """warm_served applies each distinct (plan, p) once and gives every apply
+    of that key the Tucker count the library reported for it (stubs stand
+    in for the library and torch)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    calls = []
+
+    class PK:
+        @staticmethod
+        def phiks_apply_ex(plan, tau, p, v, out, stream, **kw):
+            calls.append((plan, p, kw.get("tol")))
+
+        @staticmethod
+        def phiks_last_params(plan):
+            plan_, p, _ = calls[-1]
+            return (1, 5, 0, 10 * plan_ + p)
+
+    class Torch:
+        class cuda:
+            @staticmethod
+            def synchronize():
+                pass
+
+    def app(plan, p, tol=None):
+        x = {"plan": plan, "tau": 1e-3, "p": p, "v": [], "out": None, "vnorms": [1.0] * (p + 1),
+             "flops_per_tucker": 2.0}
+        if tol is not None:
+            x["tol"] = tol
+        return x
+    reqs = [[app(1, 2), app(2, 2)], [app(1, 3, 1e-6)], [app(1, 2)], [app(2, 2), app(1, 3, 1e-6)]]
+    bench.warm_served(PK, Torch, reqs)
+    assert [(c[0], c[1]) for c in calls] == [(1, 2), (2, 2), (1, 3)]
+    assert calls[2][2] == 1e-6
+    assert [[x["tuckers"] for x in r] for r in reqs] == [[12, 22], [13], [12], [22, 13]]
+    assert bench.served_flops(reqs) == 2.0 * (12 + 22 + 13 + 12 + 22 + 13)
