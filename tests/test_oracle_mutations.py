@@ -18,6 +18,7 @@ import pytest
 from oracle import dense, eig, expm, integrators, kron, params, phi_scalar, phiks_ref, quadrature
 from oracle import taylor_action as ta
 
+import test_complex_oracle as cpins
 import test_integrators as ipins
 import test_oracle_pins as pins
 
@@ -133,6 +134,17 @@ def test_eigenbasis_with_n_in_place_of_n_plus_one(monkeypatch):
 def test_eigenbasis_similarity_inverted(monkeypatch):
     plant(monkeypatch, eig, "eig_factors", "r = np.sqrt(a_ / c_)", "r = np.sqrt(c_ / a_)")
     fails(pins.test_sine_eigenbasis)
+
+
+def test_complex_eigenbasis_with_zeta_conjugated(monkeypatch):
+    plant(monkeypatch, eig, "scaled_phi_actions", "complex(c) * tau * complex(zeta) * Z",
+          "complex(c) * tau * complex(zeta).conjugate() * Z")
+    fails(cpins.test_eigenbasis_matches_dense_exponential)
+
+
+def test_complex_eigenbasis_without_the_scale_power(monkeypatch):
+    plant(monkeypatch, eig, "scaled_lincomb", "acc = acc + c ** l *", "acc = acc +")
+    fails(cpins.test_eigenbasis_matches_taylor_action, 7, 2)
 
 
 # ------------------------------------------------------------------ quadrature
