@@ -68,6 +68,25 @@ def test_orders_fourth_order_schemes_block_diagonal():
         assert lo < e[0] / e[1] < hi, (sch, e)
 
 
+@pytest.mark.parametrize("scheme", ["expeuler", "etd2rk", "exprk3", "exprk4s5", "exprk4s6"])
+def test_steady_states_are_kept(scheme):
+    """Homogeneous steady states of the semidiscrete problems (the Neumann
+    Laplacians annihilate constants): Allen-Cahn u = 1, where K 1 = 1/eps^2 =
+    -g(1), and the Brusselator (u, v) = (a, b/a), where -(b+1) a + a + a^2 b/a
+    = 0 and b a - a^2 b/a = 0.  Every stage of eq. (RK) then equals u_n
+    (exp(X) = I + X phi_1(X)), so each scheme keeps them to rounding; a wrong
+    sign or role in g, or a dropped phi_1 g term, does not."""
+    A, u0 = wk.ac_paper(9, 0.05)
+    one = np.ones_like(u0)
+    out = it.integrate_problem([A], it.ac_g(0.05), one, 0.0, 1e-4, 4, scheme)
+    assert np.abs(out - one).max() < 1e-11
+    blocks, w0 = wk.brusselator3d(5)
+    N = w0.size // 2
+    w = np.concatenate([np.full(N, 1.0), np.full(N, 3.0)])
+    out = it.integrate_problem(blocks, it.bruss_g(1.0, 3.0), w, 0.0, 0.5, 4, scheme)
+    assert np.abs(out - w).max() < 1e-11
+
+
 def test_block_diagonal_phi_actions_vs_dense():
     """The block-by-block phi-actions equal the top rows of one dense
     exponential of the augmented matrix of the whole block-diagonal K (Sec. 2

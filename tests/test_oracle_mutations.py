@@ -228,6 +228,23 @@ def test_exponential_euler_without_the_nonlinear_term(monkeypatch):
     fails(ipins.test_oracle_reproduces_printed_errors, "expeuler", 300, 1e-7)
 
 
+def test_allen_cahn_nonlinearity_with_the_wrong_sign(monkeypatch):
+    plant(monkeypatch, integrators, "ac_g", "return -(u * u * u) / (eps * eps)", "return (u * u * u) / (eps * eps)")
+    fails(ipins.test_steady_states_are_kept, "etd2rk")
+
+
+def test_brusselator_nonlinearity_with_the_species_swapped(monkeypatch):
+    plant(monkeypatch, integrators, "bruss_g", "np.concatenate([a + uuv, b * u - uuv])",
+          "np.concatenate([b * u - uuv, a + uuv])")
+    fails(ipins.test_steady_states_are_kept, "exprk3")
+
+
+def test_stages_without_the_phi_1_term(monkeypatch):
+    plant(monkeypatch, integrators, "exprk_step", "x = lc(blocks, ci * tau, [u, ci * tau * gn])",
+          "x = lc(blocks, ci * tau, [u])")
+    fails(ipins.test_steady_states_are_kept, "exprk4s6")
+
+
 def test_exprk3_with_the_sign_of_gamma_flipped(monkeypatch):
     bad = plant(monkeypatch, integrators, "_exprk3", "gam = (3 * c3 - 2) * c3", "gam = -(3 * c3 - 2) * c3")
     monkeypatch.setitem(integrators.TABLEAUX, "exprk3", bad())
